@@ -1,0 +1,380 @@
+"""Benchmark: simulated instructions per second of SimNet's lock-step sub-trace
+simulation on one B300 (or N independent replicas under torchrun).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--precision bf16]
+    python bench.py --impl reference ...      # the FP64 CPU oracle on the host cores
+
+One step = one full simnet_simulate call over the workload's whole trace:
+every lock-step iteration (gather, conv GEMMs, FC1, head + queue update), the
+drains and the per-sub-trace cycle counts.  Inputs are resident in HBM before
+the timed region; L2 is flushed (512 MB write) before every timed step and the
+flush is outside the step's CUDA-event pair.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2105_05821_b300 import inputs as I  # noqa: E402
+
+METRIC = "simulated instr/sec on 1 B300 (BF16/FP8 vs FP32 form) at stated CPI error"
+UNIT = "inst/s"
+FP32_FMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
+# keyed by (workload, precision, kernel); from the capture summarised in profiles/.
+TRAFFIC = {}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], p["bf16_tflops"], p["bf16_tflops_sustained"], "measured"
+    except Exception:
+        return 6400.0, 1800.0, 1400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.idx = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_rate(w: I.Workload, trace: I.Trace, blob, ids, threads=0):
+    """Instructions/s of the FP64 oracle on the listed sub-traces (host cores)."""
+    import oracle
+    cfg = oracle.Config.of(w.arch, retire_width=w.retire_width)
+    n = int(sum(trace.offsets[i + 1] - trace.offsets[i] for i in ids))
+    t0 = time.perf_counter()
+    r = oracle.simulate(cfg, trace.records, trace.offsets, blob, subset=ids, n_threads=threads)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, r
+
+
+def host_cores():
+    """CPUs this process may really use: affinity mask, capped by a cgroup CPU quota."""
+    n = len(os.sched_getaffinity(0))
+    try:
+        q, per = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if q != "max":
+            n = min(n, max(1, int(-(-int(q) // int(per)))))
+    except Exception:
+        pass
+    return n
+
+
+def cpu_sample_ids(w, trace, blob, target_s=15.0):
+    """A bounded sample of whole sub-traces sized for ~target_s of oracle work,
+    calibrated on one wave of sub-traces (one per thread)."""
+    threads = host_cores()
+    ids = list(range(min(threads, trace.n_subtraces)))
+    rate, _, dt, _ = oracle_rate(w, trace, blob, ids, threads=threads)
+    avg_len = trace.n_instructions / trace.n_subtraces
+    n = int(min(trace.n_subtraces, rate * target_s / avg_len))
+    n = max(len(ids), (n // threads) * threads)
+    return list(range(min(n, trace.n_subtraces))), threads
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = I.WORKLOADS[args.workload]
+    trace = I.make_trace(w)
+    blob = I.workload_weights(w)
+    threads = host_cores()
+    per_step = threads                      # one sub-trace per host thread per step
+    times, insts = [], []
+    for s in range(args.warmup + args.steps):
+        lo = (s * per_step) % trace.n_subtraces
+        ids = [(lo + j) % trace.n_subtraces for j in range(per_step)]
+        rate, n, dt, _ = oracle_rate(w, trace, blob, ids, threads=threads)
+        if s >= args.warmup:
+            times.append(dt)
+            insts.append(n)
+    value = sum(insts) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w, args, note="each step a sample of "
+                                                          f"{per_step} whole sub-traces"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} whole sub-traces per step, {args.steps} steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, args, note=""):
+    c = {"workload": f"{w.name}: {w.description}", "n_subtraces": w.n_subtraces,
+         "instructions_per_step": None, "window": w.arch.window, "n_conv": w.arch.n_conv,
+         "channels": w.arch.channels, "fc_hidden": w.arch.hidden, "retire_width": w.retire_width,
+         "precision": args.precision, "l2": "flushed (512 MB write) before every timed step"}
+    if note:
+        c["note"] = note
+    return c
+
+
+# ----------------------------------------------------------------------------- our arm
+def algorithmic_units(w: I.Workload, kind: int, n_active: float, prec: str):
+    """(amount, unit, bound) per launch of kernel `kind` for n_active sub-traces."""
+    a = w.arch
+    es = {"fp32": 4, "bf16": 2, "fp8": 1}[prec]
+    if 1 <= kind <= a.n_conv + 1:
+        l = kind - 1
+        if l < a.n_conv:
+            rows = a.window >> (l + 1)
+            cin = I.N_FEATURES if l == 0 else a.channels
+            macs = rows * a.channels * cin * 2
+        else:
+            macs = a.fc1_in * a.hidden
+        return 2.0 * macs * n_active, "flop", ("alu" if prec == "fp32" else "tensor")
+    if kind == 0:   # gather: feature tile written, ring + record + scalars read
+        per = a.window * 64 * es + (a.window - 1) * 8 + 4 + 16
+        return per * n_active, "byte", "hbm"
+    if kind == 10:  # head + update: FC1 activations read, ring scan, append, scalars
+        per = a.hidden * 4 + 8 * 8 + 8 + 4 + 32
+        return per * n_active, "byte", "hbm"
+    return 0.0, "byte", "hbm"
+
+
+KIND_NAMES = {0: "gather", 10: "head_update", 11: "compact"}
+
+
+def kind_name(w, k):
+    if k in KIND_NAMES:
+        return KIND_NAMES[k]
+    l = k - 1
+    return f"conv{l + 1}_gemm" if l < w.arch.n_conv else "fc1_gemm"
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_2105_05821_b300.simnet import Simnet
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = I.WORKLOADS[args.workload]
+    trace = I.make_trace(w)
+    blob32 = I.workload_weights(w).astype(np.float32)
+    N, B = trace.n_instructions, trace.n_subtraces
+
+    rec_h = torch.from_numpy(trace.records.view(np.int32).copy()).pin_memory()
+    off_h = torch.from_numpy(trace.offsets.copy()).pin_memory()
+    rec = rec_h.to(dev)
+    off = off_h.to(dev)
+    cyc = torch.empty(B, dtype=torch.int64, device=dev)
+    cyc_h = torch.empty(B, dtype=torch.int64).pin_memory()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.int32, device=dev)   # 512 MB > L2
+
+    def sync_all():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_run(sim, steps, warmup, e2e=False):
+        for _ in range(warmup):
+            sim.simulate(rec, off, cycles_out=cyc, stats=False)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        sync_all()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record()
+            if e2e:
+                rec.copy_(rec_h, non_blocking=True)
+                off.copy_(off_h, non_blocking=True)
+            sim.simulate(rec, off, cycles_out=cyc, stats=False)
+            if e2e:
+                cyc_h.copy_(cyc, non_blocking=True)
+            evs[i][1].record()
+        sync_all()
+        wall = time.perf_counter() - t0
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        return ms, wall
+
+    sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width)
+    sim.load_weights(blob32)
+    st = sim.simulate(rec, off, cycles_out=cyc, stats=True)          # compile graphs, count launches
+    launches_per_step = st.kernel_launches
+
+    with ClockSampler(dev.index) as clk:
+        ms, wall = timed_run(sim, args.steps, args.warmup)
+    clocks = clk.summary()
+    # max over ranks
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_per_step = ms_max / args.steps
+    value = world * N / (ms_per_step / 1e3)
+
+    # end to end through host buffers (pinned H2D of the trace, D2H of the cycle counts)
+    ms_e2e, _ = timed_run(sim, max(2, args.steps // 2), 1, e2e=True)
+    t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = world * N / (float(t.item()) / max(2, args.steps // 2) / 1e3)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+           "config": workload_config(w, args), "clocks": clocks,
+           "gpu_launches": int(launches_per_step * args.steps),
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * N + 8 * (B + 1)),
+                   "d2h_bytes_per_step": int(8 * B)},
+           "wall_s_timed": wall}
+    out["config"]["instructions_per_step"] = N
+    out["total_cycles"] = int(st.total_cycles)
+    out["cpi"] = st.total_cycles / N
+
+    if rank == 0 and not args.no_breakdown:
+        out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B)
+    if rank == 0 and args.precision != "fp32" and not args.no_fp32:
+        s32 = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
+        s32.load_weights(blob32)
+        m32, _ = timed_run(s32, max(2, args.steps // 3), 1)
+        out["fp32_form"] = {"value": N / (m32 / max(2, args.steps // 3) / 1e3), "unit": UNIT}
+        s32.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ids, threads = cpu_sample_ids(w, trace, I.workload_weights(w))
+        rate, n, dt, r = oracle_rate(w, trace, I.workload_weights(w), ids, threads=threads)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                               "sample": f"{len(ids)} whole sub-traces ({n} instructions) of the same "
+                                         f"workload, {dt:.1f} s, FP64"}
+        gcyc = cyc.cpu().numpy()[ids]
+        out["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids),
+                                      "cpi_error": abs(float(gcyc.sum()) / float(r.cycles.sum()) - 1.0)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def roofline(w, args, blob32, rec, off, cyc, B):
+    """Per-kernel CUDA-event times from one extra full step with an event pair
+    around every launch; roofline of the kernel with the largest share."""
+    from paper_2105_05821_b300.simnet import Simnet
+    hbm, bf16_burst, bf16_sus, src = peaks()
+    sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
+                          kernel_events=True)
+    sim.load_weights(blob32)
+    sim.simulate(rec, off, cycles_out=cyc, stats=True)
+    ms, n = sim.kernel_times()
+    sim.close()
+    total = sum(ms)
+    steps = max(n[0], 1)
+    kernels = {}
+    for k in range(len(ms)):
+        if n[k] == 0:
+            continue
+        amt, unit, bound = algorithmic_units(w, k, B, args.precision)
+        kernels[kind_name(w, k)] = {"launches": n[k], "ms_total": ms[k], "share": ms[k] / total,
+                                    "avg_us": 1e3 * ms[k] / n[k], "bound": bound}
+    dom = max(range(len(ms)), key=lambda k: ms[k])
+    amt, unit, bound = algorithmic_units(w, dom, B, args.precision)
+    avg_s = ms[dom] / n[dom] / 1e3
+    if unit == "flop":
+        achieved = amt / avg_s / 1e12
+        if bound == "alu":
+            peak, punit, note = FP32_FMA_PEAK_TFLOPS, "TFLOP/s", "FP32 FMA peak at max SM clock"
+        else:
+            scale = 2.0 if args.precision == "fp8" else 1.0
+            peak, punit, note = bf16_sus * scale, "TFLOP/s", f"{src} bf16 sustained" + (
+                " x2 (fp8 nominal ratio)" if scale > 1 else "")
+    else:
+        achieved = amt / avg_s / 1e9
+        peak, punit, note = hbm, "GB/s", f"{src} HBM copy"
+    traffic = TRAFFIC.get((w.name, args.precision, kind_name(w, dom)))
+    roof = {"kernel": kind_name(w, dom), "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": punit, "frac": achieved / peak, "peak_source": note, "traffic": traffic,
+            "avg_launch_us": avg_s * 1e6, "algorithmic_per_launch": amt, "algorithmic_unit": unit,
+            "share_of_step": ms[dom] / total, "steps_timed": steps}
+    return roof, kernels
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c4", "c5"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-breakdown", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

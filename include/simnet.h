@@ -1,0 +1,205 @@
+/*
+ * simnet.h -- C ABI of libsimnet, a B300 (sm_103a) implementation of SimNet's
+ * data-parallel simulation loop (Li et al., "SimNet: Accurate and
+ * High-Performance Computer Architecture Simulation using Deep Learning",
+ * arXiv 2105.05821).
+ *
+ * The library simulates many independent sub-traces in lock step (Sec. 3.3).
+ * Every step, for every sub-trace that still has instructions:
+ *   1. gather the current instruction and its context instructions (the
+ *      processor queue, newest first) into a W x 50 feature matrix (Sec. 2.2);
+ *   2. run the CNN latency predictor on the whole batch (Sec. 2.3): k=2,
+ *      stride-2 convolutions with ReLU, flatten, FC + ReLU, FC to the fetch
+ *      and execution latencies, softplus, clamp to [0, 255], round half to
+ *      even;
+ *   3. advance the sub-trace's curTick by the fetch latency, retire ready
+ *      queue entries in order within the retire bandwidth, evict the oldest
+ *      entry of a full queue, append the instruction (Sec. 3.2);
+ * and after a sub-trace's last instruction, advance its clock until the queue
+ * is empty, so that its cycle count is sum(F) + Delta (Sec. 3.1, Eq. 1).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device addresses on the current device; host
+ *     pointers are ordinary process memory.  Each argument says which.
+ *   - The caller owns every buffer it passes.  The context owns its weights,
+ *     workspaces, CUDA graphs and device status word.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; a call returns before the GPU has
+ *     finished unless it fills a host output (stats, loss), in which case it
+ *     synchronises the stream first.
+ *   - Every call returns a simnet_status; no C++ exception crosses the ABI.
+ *     On failure simnet_last_error() describes the cause.  A device-side wait
+ *     that exceeds its bound makes the call return SIMNET_ETIMEOUT.
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef SIMNET_H
+#define SIMNET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SIMNET_ABI_VERSION 1
+#define SIMNET_N_FEATURES 50 /* features per instruction row (Sec. 2.2) */
+
+typedef struct simnet_ctx simnet_ctx;
+
+typedef enum {
+    SIMNET_OK = 0,
+    SIMNET_EINVAL = 1,      /* bad argument: null pointer, size out of range, bad config */
+    SIMNET_ENOMEM = 2,      /* device or pinned host allocation failed */
+    SIMNET_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+    SIMNET_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    SIMNET_ESTATE = 5,      /* call out of order (e.g. simulate before load_weights) */
+    SIMNET_EUNSUPPORTED = 6 /* shape/precision this build does not handle */
+} simnet_status;
+
+/* Arithmetic of the CNN.  All of them accumulate in FP32; the integer clock and
+ * queue work is exact in every mode. */
+typedef enum {
+    SIMNET_FP32 = 0,     /* CUDA-core FFMA GEMMs */
+    SIMNET_BF16 = 1,     /* tcgen05 tensor-core GEMMs, BF16 operands */
+    SIMNET_FP8_E4M3 = 2  /* tcgen05 tensor-core GEMMs, FP8 e4m3 operands, per-channel scales */
+} simnet_precision;
+
+/* simnet_config.flags */
+#define SIMNET_FLAG_RETIRE_STRICT 0x1u /* an entry is ready when residence > E (default: >=) */
+#define SIMNET_FLAG_NO_GRAPH 0x2u      /* launch each step's kernels directly, no CUDA graph */
+#define SIMNET_FLAG_KERNEL_EVENTS 0x4u /* direct launches with a CUDA event pair around each kernel;
+                                          per-kernel device times via simnet_kernel_times() */
+
+/*
+ * Model and simulator shape.  The CNN sees `window` rows: the current
+ * instruction and up to window-1 context instructions, so the processor queue
+ * holds at most window-1 entries.  `window` must be divisible by 2^n_conv.
+ * Limits of this build: 2 <= window <= 256 (window-1 <= 255 queue entries),
+ * 1 <= n_conv <= 8, conv_channels in {64, 128, 256}, fc_hidden a multiple of
+ * 64 up to 2048, 1 <= retire_width <= 255.
+ */
+typedef struct {
+    int32_t window;        /* W: rows given to the CNN */
+    int32_t n_conv;        /* number of k=2, stride-2 conv layers */
+    int32_t conv_channels; /* output channels of every conv layer */
+    int32_t fc_hidden;     /* width of the first FC layer */
+    int32_t retire_width;  /* processor-queue retire bandwidth, entries per cycle */
+    int32_t precision;     /* simnet_precision */
+    uint32_t flags;        /* SIMNET_FLAG_* */
+    int32_t reserved;
+    int64_t spin_limit_ns; /* bound on any device-side wait; <= 0 selects 2 s */
+} simnet_config;
+
+/*
+ * A trace already resident on the device.  Instruction record, one uint32 per
+ * instruction: bits 0-4 opcode class, 5-9 src0, 10-14 src1, 15-19 dst,
+ * 20 is_load, 21 is_store, 22 is_branch, 23-24 cache level (0 L1, 1 L2,
+ * 2 memory), 25 mispredict; bits 26-31 must be zero.  Sub-trace b is
+ * records[offsets[b] .. offsets[b+1]); offsets must be non-decreasing with
+ * offsets[0] = 0 and offsets[n_subtraces] = n_instructions.  A sub-trace may
+ * be empty (0 cycles) and may hold at most 4,194,303 instructions.
+ */
+typedef struct {
+    const uint32_t *records; /* device [n_instructions] */
+    const int64_t *offsets;  /* device [n_subtraces + 1] */
+    int32_t n_subtraces;
+    int32_t reserved;
+    int64_t n_instructions;
+} simnet_trace;
+
+typedef struct {
+    int64_t total_cycles; /* sum over sub-traces of their final curTick (Sec. 3.3) */
+    int64_t instructions; /* instructions simulated */
+    int64_t steps;        /* lock-step iterations run */
+    int64_t evictions;    /* queue entries dropped at capacity */
+    int64_t kernel_launches; /* kernels the call launched (graph replays counted per kernel) */
+    float ms_total;          /* device time of the call, CUDA events */
+    float reserved[3];
+} simnet_stats;
+
+/* Kernel kinds reported by simnet_kernel_times(). */
+#define SIMNET_KERNEL_GATHER 0          /* context gather into the feature tile */
+#define SIMNET_KERNEL_LAYER0 1          /* GEMM of layer l is SIMNET_KERNEL_LAYER0 + l (conv..., FC1) */
+#define SIMNET_KERNEL_KINDS 12          /* GATHER, up to 9 GEMM layers, HEAD_UPDATE, COMPACT */
+#define SIMNET_KERNEL_HEAD_UPDATE 10    /* FC2 head + clock/queue update (+ drain) */
+#define SIMNET_KERNEL_COMPACT 11        /* active-set compaction */
+
+/* ABI version of the loaded library (SIMNET_ABI_VERSION of its build). */
+int32_t simnet_abi_version(void);
+
+/*
+ * Create a context on the current CUDA device.  `cfg` (host) is copied.
+ * Allocates nothing on the device until weights or a trace arrive.
+ * Errors: EINVAL for a config outside the limits above, ECUDA without a device.
+ */
+simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out);
+
+/* Release every resource of the context; NULL is ignored. */
+void simnet_destroy(simnet_ctx *ctx);
+
+/* Text of the last error raised on this context (never NULL; "" if none). */
+const char *simnet_last_error(const simnet_ctx *ctx);
+
+/* Number of FP32 values in the canonical weight blob of this config. */
+int64_t simnet_weight_count(const simnet_ctx *ctx);
+
+/*
+ * Load the CNN weights (Sec. 2.3).  `blob` is a HOST array of `n_values`
+ * float32 in canonical order and PyTorch shapes: for k = 1..n_conv
+ * conv_k.weight [C, C_in, 2] (C_in = 50 for k = 1, else C), conv_k.bias [C];
+ * then fc1.weight [H, C * (W >> n_conv)] whose input index is
+ * channel * (W >> n_conv) + row; fc1.bias [H]; fc2.weight [2, H]; fc2.bias [2]
+ * (output 0 = fetch latency, 1 = execution latency).  The library copies,
+ * re-lays out and converts it to the context's precision; for FP8 it also
+ * derives per-channel weight scales and, from a calibration pass over
+ * synthetic context rows, per-channel activation scales.
+ * Errors: EINVAL if n_values != simnet_weight_count(ctx) or blob is NULL.
+ */
+simnet_status simnet_load_weights(simnet_ctx *ctx, const float *blob, int64_t n_values);
+
+/*
+ * Simulate every sub-trace of `trace` to completion from an empty queue and
+ * curTick = 0 (Sec. 3.2-3.3).
+ *   cycles_out  device int64 [n_subtraces]: final curTick of each sub-trace.
+ *   lat_log     device uint8 [n_instructions][2] or NULL: the integer (F, E)
+ *               each instruction received.
+ *   pre_log     device float [n_instructions][2] or NULL: softplus outputs
+ *               before clamping and rounding (NaN where `lat_replay` skipped
+ *               nothing: always written when non-NULL).
+ *   lat_replay  device uint8 [n_instructions][2] or NULL: teacher forcing; the
+ *               CNN still runs (and pre_log records it) but the clock and
+ *               queue use these latencies.
+ *   stats       host, or NULL.  When given the call synchronises `stream`.
+ * Workspaces are (re)allocated on the first call with a larger batch.
+ * Errors: EINVAL (bad trace, sub-trace longer than the limit), ESTATE (no
+ * weights loaded), ENOMEM, ECUDA, ETIMEOUT.
+ */
+simnet_status simnet_simulate(simnet_ctx *ctx, const simnet_trace *trace, int64_t *cycles_out,
+                              uint8_t *lat_log, float *pre_log, const uint8_t *lat_replay,
+                              simnet_stats *stats, void *stream);
+
+/*
+ * Run the CNN alone on feature matrices (Sec. 2.3).
+ *   x  device float [n][window][50]: rows as the simulator builds them.
+ *   z  device float [n][2]: outputs before softplus.
+ * Uses the context's precision (inputs are rounded to it).
+ * Errors: EINVAL (n < 0 or null pointers), ESTATE (no weights).
+ */
+simnet_status simnet_cnn_forward(simnet_ctx *ctx, const float *x, float *z, int32_t n,
+                                 void *stream);
+
+/*
+ * Per-kernel device time of the last simnet_simulate call made with
+ * SIMNET_FLAG_KERNEL_EVENTS: for each kind k < n_kinds, ms_out[k] = summed
+ * CUDA-event time of its launches (milliseconds) and launches_out[k] = their
+ * number (host arrays of n_kinds entries, n_kinds <= SIMNET_KERNEL_KINDS).
+ * Synchronises the device.  Errors: EINVAL (bad arguments), ESTATE (no such
+ * call yet).
+ */
+simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launches_out, int32_t n_kinds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIMNET_H */

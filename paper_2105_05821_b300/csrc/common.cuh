@@ -1,0 +1,69 @@
+// common.cuh -- types shared by libsimnet's translation units (device side and host side).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "simnet.h"
+
+namespace simnet {
+
+constexpr int kNF = SIMNET_N_FEATURES;  // real features per row (Sec. 2.2)
+constexpr int kNFP = 64;                // features per row in device layout (zero padded)
+constexpr int kMaxConv = 8;
+
+// Device status word values (written by kernels, read by the host after a call).
+enum : int32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadTrace = 2 };
+
+// Ring entry of the processor queue: record (26 bits) | E (8 bits) << 26 | fetch tick (30 bits) << 34.
+__host__ __device__ __forceinline__ uint64_t pack_entry(uint32_t rec, uint32_t e, uint32_t tick) {
+    return (uint64_t)(rec & 0x3ffffffu) | ((uint64_t)(e & 0xffu) << 26) | ((uint64_t)tick << 34);
+}
+__host__ __device__ __forceinline__ uint32_t entry_rec(uint64_t v) { return (uint32_t)(v & 0x3ffffffu); }
+__host__ __device__ __forceinline__ uint32_t entry_e(uint64_t v) { return (uint32_t)((v >> 26) & 0xffu); }
+__host__ __device__ __forceinline__ uint32_t entry_tick(uint64_t v) { return (uint32_t)(v >> 34); }
+
+// Everything a step's simulation kernels need; lives in device memory so that a
+// captured CUDA graph stays valid when the caller passes new trace buffers.
+struct StepArgs {
+    // the call
+    const uint32_t *records;
+    const int64_t *offsets;
+    int64_t *cycles_out;
+    uint8_t *lat_log;
+    float *pre_log;
+    const uint8_t *replay;
+    // per-sub-trace state [B]
+    int32_t *tick;
+    int32_t *pos;
+    int32_t *qstart;
+    int32_t *qlen;
+    int32_t *evict;
+    uint64_t *ring;  // [B][cap]
+    // batch slots
+    int32_t *active;    // [B] slot -> sub-trace
+    int32_t *n_active;  // [1]
+    int32_t *status;    // [1]
+    // shapes
+    int32_t n_sub;
+    int32_t window;
+    int32_t cap;
+    int32_t retire_width;
+    int32_t strict;
+    int32_t hidden;
+};
+
+// A GEMM layer C[M, N] = act(A[M, K] * B[N, K]^T * scale + bias), M = n_active * m_mult.
+struct GemmLayer {
+    int m_mult;    // output rows per sub-trace
+    int K;         // reduction length (padded)
+    int N;         // output columns
+    int relu;
+    const void *B; // weights [N][K] in the layer's precision
+    const float *bias;   // [N]
+    const float *scale;  // [N] per-output-channel dequant scale (FP8) or nullptr
+    const float *oscale; // [N] multiplier applied before storing (FP8 requant) or nullptr
+};
+
+}  // namespace simnet

@@ -1,0 +1,20 @@
+// kernels.cuh -- host-side launchers of libsimnet's kernels.
+#pragma once
+#include "common.cuh"
+
+namespace simnet {
+
+template <typename T> void launch_gather(const StepArgs *A, T *X, int n_slots, int window, cudaStream_t s);
+template <typename T> void launch_pack_x(const float *x, T *X, int64_t rows, cudaStream_t s);
+void launch_head_update(const StepArgs *A, const float *h, const float *w2, const float *b2, int n_slots,
+                        cudaStream_t s);
+void launch_head_z(const float *h, const float *w2, const float *b2, float *z, int n, int H, cudaStream_t s);
+void launch_init_state(const StepArgs *A, int n_sub, cudaStream_t s);
+void launch_compact(const StepArgs *A, cudaStream_t s);
+void launch_totals(const StepArgs *A, unsigned long long *out, int n_sub, cudaStream_t s);
+
+// FP32 CUDA-core GEMM: C[M,N] = act(A[M,K] * B[N,K]^T + bias), M = min(*n_active * m_mult, m_cap).
+void launch_gemm_f32(const float *A, const float *B, const float *bias, float *C, const int32_t *n_active,
+                     int m_mult, int m_cap, int N, int K, int relu, cudaStream_t s);
+
+}  // namespace simnet

@@ -1,0 +1,537 @@
+// simnet.cu -- the C ABI of libsimnet (include/simnet.h): context, weights,
+// workspaces and the lock-step simulation loop of Sec. 3.3, replayed as CUDA
+// graphs of whole steps (gather -> conv GEMMs -> FC1 -> head + queue update).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_gemm.cuh"
+
+using namespace simnet;
+
+struct simnet_ctx {
+    simnet_config cfg{};
+    int cap = 0, rows_n = 0, fc1_in = 0, n_layers = 0;
+    int64_t n_weights = 0;
+    std::string err;
+    bool has_weights = false;
+    int device = 0;
+
+    // weights in GEMM layout ([N][K], layer precision) + FP32 biases; FC2 in FP32
+    void *Wl[kMaxConv + 1] = {};
+    float *bias[kMaxConv + 1] = {};
+    float *wscale[kMaxConv + 1] = {};  // FP8: per-output-channel dequant scale
+    float *oscale[kMaxConv + 1] = {};  // FP8: per-output-channel requant multiplier (1/next act scale)
+    float *w2 = nullptr, *b2 = nullptr;
+    GemmLayer layer[kMaxConv + 1];
+    TcPlan plan[kMaxConv + 1];
+
+    // workspace, sized for ws_B sub-traces
+    int ws_B = 0;
+    void *X = nullptr, *act[2] = {nullptr, nullptr};
+    float *h1 = nullptr;
+    int32_t *tick = nullptr, *pos = nullptr, *qstart = nullptr, *qlen = nullptr, *evict = nullptr;
+    int32_t *active = nullptr, *n_active = nullptr, *status = nullptr, *cnt = nullptr;
+    uint64_t *ring = nullptr;
+    unsigned long long *totals = nullptr;
+    StepArgs *d_args = nullptr, *h_args = nullptr;
+    int64_t *h_offsets = nullptr;
+    size_t h_offsets_cap = 0;
+    unsigned long long *h_totals = nullptr;
+    int32_t *h_status = nullptr;
+    cudaEvent_t args_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
+    bool args_pending = false;
+    cudaStream_t cap_stream = nullptr;
+
+    // captured step graphs: [0] = kGraphSteps steps, [1] = one step
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int g_B = -1, g_compact = -1;
+
+    // per-kernel CUDA-event timing (SIMNET_FLAG_KERNEL_EVENTS)
+    std::vector<cudaEvent_t> evpool;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    bool kt_valid = false;
+};
+
+// Records an event pair around each kernel when timing is on.
+struct KTimer {
+    simnet_ctx *c = nullptr;
+    cudaStream_t s = nullptr;
+    bool ok = true;
+    void begin(int kind) {
+        if (!c) return;
+        if (c->ev_used + 2 > c->evpool.size()) {
+            for (int i = 0; i < 256; i++) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) { ok = false; return; }
+                c->evpool.push_back(e);
+            }
+            c->ev_kind.resize(c->evpool.size());
+        }
+        c->ev_kind[c->ev_used] = kind;
+        cudaEventRecord(c->evpool[c->ev_used++], s);
+    }
+    void end() {
+        if (!c || !ok) return;
+        cudaEventRecord(c->evpool[c->ev_used++], s);
+    }
+};
+
+static constexpr int kGraphSteps = 16;
+
+static simnet_status fail(simnet_ctx *c, simnet_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? SIMNET_ENOMEM : SIMNET_ECUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+static size_t elem_size(int prec) { return prec == SIMNET_FP32 ? 4 : prec == SIMNET_BF16 ? 2 : 1; }
+
+extern "C" int32_t simnet_abi_version(void) { return SIMNET_ABI_VERSION; }
+
+extern "C" const char *simnet_last_error(const simnet_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" int64_t simnet_weight_count(const simnet_ctx *c) { return c ? c->n_weights : -1; }
+
+extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out) {
+    if (!cfg || !out) return SIMNET_EINVAL;
+    *out = nullptr;
+    const simnet_config &k = *cfg;
+    if (k.window < 2 || k.window > 256 || k.n_conv < 1 || k.n_conv > kMaxConv ||
+        ((k.window >> k.n_conv) << k.n_conv) != k.window ||
+        !(k.conv_channels == 64 || k.conv_channels == 128 || k.conv_channels == 256) || k.fc_hidden < 64 ||
+        k.fc_hidden > 2048 || k.fc_hidden % 64 != 0 || k.retire_width < 1 || k.retire_width > 255 ||
+        k.precision < SIMNET_FP32 || k.precision > SIMNET_FP8_E4M3)
+        return SIMNET_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return SIMNET_ECUDA;
+    simnet_ctx *c = new simnet_ctx();
+    c->cfg = k;
+    if (c->cfg.spin_limit_ns <= 0) c->cfg.spin_limit_ns = 2000000000LL;
+    cudaGetDevice(&c->device);
+    c->cap = k.window - 1;
+    c->rows_n = k.window >> k.n_conv;
+    c->fc1_in = c->rows_n * k.conv_channels;
+    c->n_layers = k.n_conv + 1;
+    int64_t n = 0, cin = kNF;
+    for (int l = 0; l < k.n_conv; l++) {
+        n += (int64_t)k.conv_channels * cin * 2 + k.conv_channels;
+        cin = k.conv_channels;
+    }
+    n += (int64_t)c->fc1_in * k.fc_hidden + k.fc_hidden + 2LL * k.fc_hidden + 2;
+    c->n_weights = n;
+    for (int l = 0; l < c->n_layers; l++) {
+        GemmLayer &g = c->layer[l];
+        if (l < k.n_conv) {
+            g.m_mult = k.window >> (l + 1);
+            g.K = l == 0 ? 2 * kNFP : 2 * k.conv_channels;
+            g.N = k.conv_channels;
+        } else {
+            g.m_mult = 1;
+            g.K = c->fc1_in;
+            g.N = k.fc_hidden;
+        }
+        g.relu = 1;
+    }
+    *out = c;
+    return SIMNET_OK;
+}
+
+static void free_workspace(simnet_ctx *c) {
+    void *bufs[] = {c->X, c->act[0], c->act[1], c->h1, c->tick, c->pos, c->qstart, c->qlen, c->evict,
+                    c->active, c->n_active, c->status, c->cnt, c->ring, c->totals, c->d_args};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    c->X = c->act[0] = c->act[1] = nullptr;
+    c->h1 = nullptr;
+    c->tick = c->pos = c->qstart = c->qlen = c->evict = c->active = c->n_active = c->status = c->cnt = nullptr;
+    c->ring = nullptr;
+    c->totals = nullptr;
+    c->d_args = nullptr;
+    c->ws_B = 0;
+    for (auto &g : c->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    c->g_B = -1;
+}
+
+extern "C" void simnet_destroy(simnet_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_workspace(c);
+    for (int l = 0; l <= kMaxConv; l++) {
+        if (c->Wl[l]) cudaFree(c->Wl[l]);
+        if (c->bias[l]) cudaFree(c->bias[l]);
+        if (c->wscale[l]) cudaFree(c->wscale[l]);
+        if (c->oscale[l]) cudaFree(c->oscale[l]);
+    }
+    if (c->w2) cudaFree(c->w2);
+    if (c->b2) cudaFree(c->b2);
+    if (c->h_args) cudaFreeHost(c->h_args);
+    if (c->h_offsets) cudaFreeHost(c->h_offsets);
+    if (c->h_totals) cudaFreeHost(c->h_totals);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->args_ev) cudaEventDestroy(c->args_ev);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    delete c;
+}
+
+template <typename T>
+static simnet_status upload(simnet_ctx *c, void **dst, const std::vector<T> &v) {
+    if (*dst) { cudaFree(*dst); *dst = nullptr; }
+    CK(cudaMalloc(dst, v.size() * sizeof(T)));
+    CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return SIMNET_OK;
+}
+
+// Re-lay the canonical PyTorch-shaped weights into GEMM operands [N][K]:
+// conv k: K index = t * Cin_pad + ci for kernel tap t of input channel ci
+// (rows 2l and 2l+1 of the input are adjacent, so a conv output row is one dot
+// product with a contiguous 2*Cin_pad slice); FC1: K index = l * C + c for the
+// canonical input index c * L_n + l (the device flatten keeps rows outermost).
+extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, int64_t n_values) {
+    if (!c) return SIMNET_EINVAL;
+    if (!blob) return fail(c, SIMNET_EINVAL, "load_weights: blob is NULL");
+    if (n_values != c->n_weights)
+        return fail(c, SIMNET_EINVAL, "load_weights: got %lld values, config needs %lld", (long long)n_values,
+                    (long long)c->n_weights);
+    const simnet_config &k = c->cfg;
+    const int C = k.conv_channels, H = k.fc_hidden, Ln = c->rows_n;
+    std::vector<std::vector<float>> Wg(c->n_layers), Bg(c->n_layers);
+    const float *p = blob;
+    int cin = kNF;
+    for (int l = 0; l < k.n_conv; l++) {
+        const int cin_pad = l == 0 ? kNFP : C, K = 2 * cin_pad;
+        Wg[l].assign((size_t)C * K, 0.f);
+        for (int co = 0; co < C; co++)
+            for (int ci = 0; ci < cin; ci++)
+                for (int t = 0; t < 2; t++) Wg[l][(size_t)co * K + t * cin_pad + ci] = p[((size_t)co * cin + ci) * 2 + t];
+        p += (size_t)C * cin * 2;
+        Bg[l].assign(p, p + C);
+        p += C;
+        cin = C;
+    }
+    {
+        const int l = k.n_conv, K = c->fc1_in;
+        Wg[l].assign((size_t)H * K, 0.f);
+        for (int h = 0; h < H; h++)
+            for (int ch = 0; ch < C; ch++)
+                for (int r = 0; r < Ln; r++) Wg[l][(size_t)h * K + r * C + ch] = p[(size_t)h * K + (size_t)ch * Ln + r];
+        p += (size_t)H * K;
+        Bg[l].assign(p, p + H);
+        p += H;
+    }
+    std::vector<float> w2(p, p + 2 * H), b2(p + 2 * H, p + 2 * H + 2);
+    simnet_status st;
+    for (int l = 0; l < c->n_layers; l++) {
+        if (k.precision == SIMNET_FP32) {
+            if ((st = upload(c, &c->Wl[l], Wg[l])) != SIMNET_OK) return st;
+        } else if (k.precision == SIMNET_BF16) {
+            std::vector<__nv_bfloat16> wb(Wg[l].size());
+            for (size_t i = 0; i < wb.size(); i++) wb[i] = __float2bfloat16_rn(Wg[l][i]);
+            if ((st = upload(c, &c->Wl[l], wb)) != SIMNET_OK) return st;
+        } else {
+            return fail(c, SIMNET_EUNSUPPORTED, "FP8 weights: not built yet");
+        }
+        if ((st = upload(c, (void **)&c->bias[l], Bg[l])) != SIMNET_OK) return st;
+        c->layer[l].B = c->Wl[l];
+        c->layer[l].bias = c->bias[l];
+        c->layer[l].scale = c->wscale[l];
+        c->layer[l].oscale = c->oscale[l];
+    }
+    if ((st = upload(c, (void **)&c->w2, w2)) != SIMNET_OK) return st;
+    if ((st = upload(c, (void **)&c->b2, b2)) != SIMNET_OK) return st;
+    c->has_weights = true;
+    for (auto &g : c->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    c->g_B = -1;
+    return SIMNET_OK;
+}
+
+static simnet_status ensure_workspace(simnet_ctx *c, int B) {
+    if (B <= c->ws_B) return SIMNET_OK;
+    CK(cudaDeviceSynchronize());
+    free_workspace(c);
+    const simnet_config &k = c->cfg;
+    const size_t es = elem_size(k.precision);
+    const size_t xb = (size_t)B * k.window * kNFP * es;
+    const size_t ab = (size_t)B * (k.window / 2) * k.conv_channels * es;
+    CK(cudaMalloc(&c->X, xb));
+    CK(cudaMalloc(&c->act[0], ab));
+    CK(cudaMalloc(&c->act[1], ab));
+    CK(cudaMalloc(&c->h1, (size_t)B * k.fc_hidden * sizeof(float)));
+    CK(cudaMalloc(&c->tick, (size_t)B * 4));
+    CK(cudaMalloc(&c->pos, (size_t)B * 4));
+    CK(cudaMalloc(&c->qstart, (size_t)B * 4));
+    CK(cudaMalloc(&c->qlen, (size_t)B * 4));
+    CK(cudaMalloc(&c->evict, (size_t)B * 4));
+    CK(cudaMalloc(&c->active, (size_t)B * 4));
+    CK(cudaMalloc(&c->n_active, 4));
+    CK(cudaMalloc(&c->status, 4));
+    CK(cudaMalloc(&c->cnt, 4));
+    CK(cudaMalloc(&c->ring, (size_t)B * c->cap * sizeof(uint64_t)));
+    CK(cudaMalloc(&c->totals, 2 * sizeof(unsigned long long)));
+    CK(cudaMalloc(&c->d_args, sizeof(StepArgs)));
+    if (!c->h_args) {
+        CK(cudaMallocHost(&c->h_args, sizeof(StepArgs)));
+        CK(cudaMallocHost(&c->h_totals, 2 * sizeof(unsigned long long)));
+        CK(cudaMallocHost(&c->h_status, sizeof(int32_t)));
+        CK(cudaEventCreateWithFlags(&c->args_ev, cudaEventDisableTiming));
+        CK(cudaEventCreate(&c->ev0));
+        CK(cudaEventCreate(&c->ev1));
+        CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    }
+    c->ws_B = B;
+    return SIMNET_OK;
+}
+
+// The CNN on the batch already in c->X: conv GEMMs, then FC1 into c->h1.
+// `count` is a device int of active rows-groups (sub-traces or windows).
+static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t s, KTimer *kt = nullptr) {
+    const simnet_config &k = c->cfg;
+    const void *in = c->X;
+    for (int l = 0; l < c->n_layers; l++) {
+        if (kt) kt->begin(SIMNET_KERNEL_LAYER0 + l);
+        const GemmLayer &g = c->layer[l];
+        const bool last = l == c->n_layers - 1;
+        void *out = last ? (void *)c->h1 : c->act[l & 1];
+        const int m_cap = B * g.m_mult;
+        if (k.precision == SIMNET_FP32) {
+            launch_gemm_f32((const float *)in, (const float *)g.B, g.bias, (float *)out, count, g.m_mult, m_cap, g.N,
+                            g.K, g.relu, s);
+        } else {
+            launch_tc_gemm(c->plan[l], in, g, out, last, count, m_cap, s);
+        }
+        if (kt) kt->end();
+        in = out;
+    }
+}
+
+static int launches_per_step(const simnet_ctx *c) { return c->n_layers + 2; }
+
+static void enqueue_step(simnet_ctx *c, int B, cudaStream_t s, KTimer *kt = nullptr) {
+    if (kt) kt->begin(SIMNET_KERNEL_GATHER);
+    switch (c->cfg.precision) {
+        case SIMNET_FP32: launch_gather<float>(c->d_args, (float *)c->X, B, c->cfg.window, s); break;
+        case SIMNET_BF16: launch_gather<__nv_bfloat16>(c->d_args, (__nv_bfloat16 *)c->X, B, c->cfg.window, s); break;
+        default: launch_gather<__nv_fp8_e4m3>(c->d_args, (__nv_fp8_e4m3 *)c->X, B, c->cfg.window, s); break;
+    }
+    if (kt) kt->end();
+    enqueue_cnn(c, c->n_active, B, s, kt);
+    if (kt) kt->begin(SIMNET_KERNEL_HEAD_UPDATE);
+    launch_head_update(c->d_args, c->h1, c->w2, c->b2, B, s);
+    if (kt) kt->end();
+}
+
+static simnet_status prepare_plans(simnet_ctx *c, int B) {
+    if (c->cfg.precision == SIMNET_FP32) return SIMNET_OK;
+    for (int l = 0; l < c->n_layers; l++) {
+        const GemmLayer &g = c->layer[l];
+        const bool last = l == c->n_layers - 1;
+        const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
+        void *out = last ? (void *)c->h1 : c->act[l & 1];
+        std::string why;
+        if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, last, B * g.m_mult, c->cfg.spin_limit_ns,
+                          c->status, why))
+            return fail(c, SIMNET_ECUDA, "tensor-core plan for layer %d: %s", l, why.c_str());
+    }
+    return SIMNET_OK;
+}
+
+static simnet_status capture_graphs(simnet_ctx *c, int B, bool compact) {
+    for (auto &g : c->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (int gi = 0; gi < 2; gi++) {
+        const int steps = gi == 0 ? kGraphSteps : 1;
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < steps; i++) enqueue_step(c, B, c->cap_stream);
+        if (compact) launch_compact(c->d_args, c->cap_stream);
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (e != cudaSuccess) return fail(c, SIMNET_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->gexec[gi], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(c, SIMNET_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    c->g_B = B;
+    c->g_compact = compact;
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, int64_t *cycles_out,
+                                         uint8_t *lat_log, float *pre_log, const uint8_t *lat_replay,
+                                         simnet_stats *stats, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!t || !cycles_out || t->n_subtraces < 0 || t->n_instructions < 0)
+        return fail(c, SIMNET_EINVAL, "simulate: null trace/cycles_out or negative sizes");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "simulate: no weights loaded");
+    if (t->n_subtraces > 0 && (!t->offsets || (t->n_instructions > 0 && !t->records)))
+        return fail(c, SIMNET_EINVAL, "simulate: null records/offsets");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int B = t->n_subtraces;
+    if (stats) memset(stats, 0, sizeof *stats);
+    if (B == 0) return SIMNET_OK;
+
+    // offsets -> host: validate and find the number of lock-step iterations
+    if ((size_t)(B + 1) > c->h_offsets_cap) {
+        if (c->h_offsets) cudaFreeHost(c->h_offsets);
+        c->h_offsets = nullptr;
+        CK(cudaMallocHost(&c->h_offsets, (size_t)(B + 1) * sizeof(int64_t)));
+        c->h_offsets_cap = (size_t)B + 1;
+    }
+    CK(cudaMemcpyAsync(c->h_offsets, t->offsets, (size_t)(B + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (c->h_offsets[0] != 0 || c->h_offsets[B] != t->n_instructions)
+        return fail(c, SIMNET_EINVAL, "simulate: offsets[0] must be 0 and offsets[B] = n_instructions");
+    int64_t max_len = 0, min_len = INT64_MAX;
+    for (int b = 0; b < B; b++) {
+        const int64_t n = c->h_offsets[b + 1] - c->h_offsets[b];
+        if (n < 0) return fail(c, SIMNET_EINVAL, "simulate: offsets decrease at sub-trace %d", b);
+        if (n > 4194303) return fail(c, SIMNET_EINVAL, "simulate: sub-trace %d has %lld instructions (max 4194303)", b, (long long)n);
+        max_len = n > max_len ? n : max_len;
+        min_len = n < min_len ? n : min_len;
+    }
+    simnet_status st = ensure_workspace(c, B);
+    if (st != SIMNET_OK) return st;
+
+    // per-call arguments -> device (the pinned staging buffer is reused once its last copy is done)
+    if (c->args_pending) CK(cudaEventSynchronize(c->args_ev));
+    StepArgs &a = *c->h_args;
+    a.records = t->records;
+    a.offsets = t->offsets;
+    a.cycles_out = cycles_out;
+    a.lat_log = lat_log;
+    a.pre_log = pre_log;
+    a.replay = lat_replay;
+    a.tick = c->tick;
+    a.pos = c->pos;
+    a.qstart = c->qstart;
+    a.qlen = c->qlen;
+    a.evict = c->evict;
+    a.ring = c->ring;
+    a.active = c->active;
+    a.n_active = c->n_active;
+    a.status = c->status;
+    a.n_sub = B;
+    a.window = c->cfg.window;
+    a.cap = c->cap;
+    a.retire_width = c->cfg.retire_width;
+    a.strict = (c->cfg.flags & SIMNET_FLAG_RETIRE_STRICT) ? 1 : 0;
+    a.hidden = c->cfg.fc_hidden;
+    CK(cudaEventRecord(c->ev0, s));
+    CK(cudaMemcpyAsync(c->d_args, c->h_args, sizeof(StepArgs), cudaMemcpyHostToDevice, s));
+    CK(cudaEventRecord(c->args_ev, s));
+    c->args_pending = true;
+    launch_init_state(c->d_args, B, s);
+
+    const bool uneven = min_len != max_len;
+    if ((st = prepare_plans(c, B)) != SIMNET_OK) return st;
+    int64_t launches = 1 + (int64_t)max_len * launches_per_step(c);
+    const bool timed = (c->cfg.flags & SIMNET_FLAG_KERNEL_EVENTS) != 0;
+    if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
+        KTimer kt;
+        kt.c = timed ? c : nullptr;
+        kt.s = s;
+        c->ev_used = 0;
+        c->kt_valid = false;
+        for (int64_t i = 0; i < max_len; i++) {
+            enqueue_step(c, B, s, timed ? &kt : nullptr);
+            if (uneven && (i % kGraphSteps) == kGraphSteps - 1) {
+                if (timed) kt.begin(SIMNET_KERNEL_COMPACT);
+                launch_compact(c->d_args, s);
+                if (timed) kt.end();
+                launches++;
+            }
+        }
+        if (timed && !kt.ok) return fail(c, SIMNET_ENOMEM, "kernel timing: event pool exhausted");
+        c->kt_valid = timed;
+    } else {
+        if (c->g_B != B || c->g_compact != (int)uneven || !c->gexec[0])
+            if ((st = capture_graphs(c, B, uneven)) != SIMNET_OK) return st;
+        const int64_t full = max_len / kGraphSteps, rest = max_len % kGraphSteps;
+        for (int64_t i = 0; i < full; i++) CK(cudaGraphLaunch(c->gexec[0], s));
+        for (int64_t i = 0; i < rest; i++) CK(cudaGraphLaunch(c->gexec[1], s));
+        if (uneven) launches += full + rest;
+    }
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c->ev1, s));
+    if (stats) {
+        CK(cudaMemsetAsync(c->totals, 0, 2 * sizeof(unsigned long long), s));
+        launch_totals(c->d_args, c->totals, B, s);
+        CK(cudaMemcpyAsync(c->h_totals, c->totals, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(c->h_status, c->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        stats->total_cycles = (int64_t)c->h_totals[0];
+        stats->evictions = (int64_t)c->h_totals[1];
+        stats->instructions = t->n_instructions;
+        stats->steps = max_len;
+        stats->kernel_launches = launches;
+        stats->ms_total = ms;
+        if (*c->h_status == kStatusTimeout) return fail(c, SIMNET_ETIMEOUT, "a device-side wait exceeded its bound");
+        if (*c->h_status != kStatusOk) return fail(c, SIMNET_ECUDA, "device status %d", *c->h_status);
+    }
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_cnn_forward(simnet_ctx *c, const float *x, float *z, int32_t n, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (n < 0 || (n > 0 && (!x || !z))) return fail(c, SIMNET_EINVAL, "cnn_forward: bad arguments");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "cnn_forward: no weights loaded");
+    if (n == 0) return SIMNET_OK;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    simnet_status st = ensure_workspace(c, n);
+    if (st != SIMNET_OK) return st;
+    CK(cudaMemcpyAsync(c->cnt, &n, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // `n` lives on the host stack
+    const int64_t rows = (int64_t)n * c->cfg.window;
+    switch (c->cfg.precision) {
+        case SIMNET_FP32: launch_pack_x<float>(x, (float *)c->X, rows, s); break;
+        case SIMNET_BF16: launch_pack_x<__nv_bfloat16>(x, (__nv_bfloat16 *)c->X, rows, s); break;
+        default: launch_pack_x<__nv_fp8_e4m3>(x, (__nv_fp8_e4m3 *)c->X, rows, s); break;
+    }
+    if ((st = prepare_plans(c, n)) != SIMNET_OK) return st;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int32_t), s));
+    enqueue_cnn(c, c->cnt, n, s);
+    launch_head_z(c->h1, c->w2, c->b2, z, n, c->cfg.fc_hidden, s);
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_kernel_times(simnet_ctx *c, float *ms_out, int64_t *launches_out, int32_t n_kinds) {
+    if (!c) return SIMNET_EINVAL;
+    if (!ms_out || !launches_out || n_kinds < 1 || n_kinds > SIMNET_KERNEL_KINDS)
+        return fail(c, SIMNET_EINVAL, "kernel_times: bad arguments");
+    if (!c->kt_valid) return fail(c, SIMNET_ESTATE, "kernel_times: no timed simulate call");
+    CK(cudaDeviceSynchronize());
+    for (int k = 0; k < n_kinds; k++) { ms_out[k] = 0.f; launches_out[k] = 0; }
+    for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+        const int k = c->ev_kind[i];
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]));
+        if (k < n_kinds) { ms_out[k] += ms; launches_out[k]++; }
+    }
+    return SIMNET_OK;
+}

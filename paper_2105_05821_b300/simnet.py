@@ -1,0 +1,191 @@
+"""Python binding of libsimnet's C ABI (include/simnet.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels.  PyTorch is
+used for device memory and streams; tensors are passed as raw pointers.  There
+is no fallback: if libsimnet.so is missing or cannot load, importing the
+binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsimnet.so")
+
+FP32, BF16, FP8 = 0, 1, 2
+PRECISIONS = {"fp32": FP32, "bf16": BF16, "fp8": FP8}
+FLAG_RETIRE_STRICT = 0x1
+FLAG_NO_GRAPH = 0x2
+FLAG_KERNEL_EVENTS = 0x4
+KERNEL_KINDS = 12
+KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE", 6: "EUNSUPPORTED"}
+
+EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_error",
+           "simnet_weight_count", "simnet_load_weights", "simnet_simulate", "simnet_cnn_forward",
+           "simnet_kernel_times"]
+
+
+class SimnetError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(C.Structure):
+    _fields_ = [("window", C.c_int32), ("n_conv", C.c_int32), ("conv_channels", C.c_int32),
+                ("fc_hidden", C.c_int32), ("retire_width", C.c_int32), ("precision", C.c_int32),
+                ("flags", C.c_uint32), ("reserved", C.c_int32), ("spin_limit_ns", C.c_int64)]
+
+
+class _Trace(C.Structure):
+    _fields_ = [("records", C.c_void_p), ("offsets", C.c_void_p), ("n_subtraces", C.c_int32),
+                ("reserved", C.c_int32), ("n_instructions", C.c_int64)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("total_cycles", C.c_int64), ("instructions", C.c_int64), ("steps", C.c_int64),
+                ("evictions", C.c_int64), ("kernel_launches", C.c_int64), ("ms_total", C.c_float),
+                ("reserved", C.c_float * 3)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libsimnet.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -m paper_2105_05821_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.simnet_abi_version.restype = C.c_int32
+        L.simnet_init.restype = C.c_int
+        L.simnet_init.argtypes = [C.POINTER(_Config), C.POINTER(P)]
+        L.simnet_destroy.restype = None
+        L.simnet_destroy.argtypes = [P]
+        L.simnet_last_error.restype = C.c_char_p
+        L.simnet_last_error.argtypes = [P]
+        L.simnet_weight_count.restype = C.c_int64
+        L.simnet_weight_count.argtypes = [P]
+        L.simnet_load_weights.restype = C.c_int
+        L.simnet_load_weights.argtypes = [P, P, C.c_int64]
+        L.simnet_simulate.restype = C.c_int
+        L.simnet_simulate.argtypes = [P, C.POINTER(_Trace), P, P, P, P, C.POINTER(_Stats), P]
+        L.simnet_cnn_forward.restype = C.c_int
+        L.simnet_cnn_forward.argtypes = [P, P, P, C.c_int32, P]
+        L.simnet_kernel_times.restype = C.c_int
+        L.simnet_kernel_times.argtypes = [P, P, P, C.c_int32]
+        _lib = L
+    return _lib
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class Stats:
+    total_cycles: int
+    instructions: int
+    steps: int
+    evictions: int
+    kernel_launches: int
+    ms_total: float
+
+
+class Simnet:
+    """One libsimnet context: a CNN shape, a precision and its loaded weights."""
+
+    def __init__(self, window: int, n_conv: int, channels: int, hidden: int,
+                 precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
+                 graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False):
+        L = lib()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
+                 | (FLAG_KERNEL_EVENTS if kernel_events else 0))
+        self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, 0,
+                            spin_limit_ns)
+        self.window = window
+        self.precision = prec
+        h = C.c_void_p()
+        st = L.simnet_init(C.byref(self._cfg), C.byref(h))
+        if st != 0:
+            raise SimnetError(st, "simnet_init rejected the config")
+        self._h = h
+
+    @classmethod
+    def for_arch(cls, arch, **kw) -> "Simnet":
+        return cls(arch.window, arch.n_conv, arch.channels, arch.hidden, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().simnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise SimnetError(st, lib().simnet_last_error(self._h).decode())
+
+    @property
+    def weight_count(self) -> int:
+        return int(lib().simnet_weight_count(self._h))
+
+    def load_weights(self, blob: np.ndarray) -> None:
+        """Canonical FP32 blob (host), PyTorch shapes in layer order."""
+        w = np.ascontiguousarray(blob, dtype=np.float32)
+        self._check(lib().simnet_load_weights(self._h, w.ctypes.data_as(C.c_void_p), len(w)))
+
+    def simulate(self, records, offsets, cycles_out=None, lat_log=None, pre_log=None, replay=None,
+                 stats: bool = True, stream=None) -> Optional[Stats]:
+        """Simulate every sub-trace.  records: cuda int32/uint32 [N]; offsets: cuda int64 [B+1];
+        cycles_out: cuda int64 [B] (allocated if None and returned in .cycles)."""
+        import torch
+        B = offsets.numel() - 1
+        if cycles_out is None:
+            cycles_out = torch.empty(B, dtype=torch.int64, device=offsets.device)
+        self.cycles = cycles_out
+        tr = _Trace(_ptr(records), _ptr(offsets), B, 0, records.numel())
+        st = _Stats()
+        self._check(lib().simnet_simulate(self._h, C.byref(tr), _ptr(cycles_out), _ptr(lat_log),
+                                          _ptr(pre_log), _ptr(replay),
+                                          C.byref(st) if stats else None, _stream(stream)))
+        if not stats:
+            return None
+        return Stats(st.total_cycles, st.instructions, st.steps, st.evictions, st.kernel_launches,
+                     st.ms_total)
+
+    def kernel_times(self):
+        """(ms, launches) per kernel kind of the last simulate with kernel_events=True."""
+        ms = (C.c_float * KERNEL_KINDS)()
+        n = (C.c_int64 * KERNEL_KINDS)()
+        self._check(lib().simnet_kernel_times(self._h, ms, n, KERNEL_KINDS))
+        return list(ms), list(n)
+
+    def cnn_forward(self, x, z=None, stream=None):
+        """Pre-softplus CNN outputs [n, 2] for cuda float32 features [n, W, 50]."""
+        import torch
+        n = x.shape[0]
+        assert x.is_contiguous() and x.dtype == torch.float32 and tuple(x.shape[1:]) == (self.window, 50)
+        if z is None:
+            z = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+        self._check(lib().simnet_cnn_forward(self._h, _ptr(x), _ptr(z), n, _stream(stream)))
+        return z

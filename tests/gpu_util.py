@@ -1,0 +1,47 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path and the oracle on
+the same seeded inputs."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2105_05821_b300 import inputs as I
+from paper_2105_05821_b300.simnet import Simnet
+
+
+def latency_error(gpu, ref):
+    """The paper's prediction error form |f - y| / (y + 1) (Sec. 2.5), on the
+    softplus outputs before rounding."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.abs(gpu - ref) / (np.abs(ref) + 1.0)
+
+
+def to_dev(trace: I.Trace):
+    rec = torch.from_numpy(trace.records.view(np.int32).copy()).cuda()
+    off = torch.from_numpy(trace.offsets.copy()).cuda()
+    return rec, off
+
+
+def run_gpu(sim: Simnet, trace: I.Trace, replay=None, logs=True):
+    rec, off = to_dev(trace)
+    N = trace.n_instructions
+    lat = torch.zeros((max(N, 1), 2), dtype=torch.uint8, device="cuda") if logs else None
+    pre = torch.full((max(N, 1), 2), float("nan"), dtype=torch.float32, device="cuda") if logs else None
+    rp = None
+    if replay is not None:
+        rp = torch.from_numpy(np.ascontiguousarray(replay, dtype=np.uint8)).cuda()
+    st = sim.simulate(rec, off, lat_log=lat, pre_log=pre, replay=rp)
+    torch.cuda.synchronize()
+    out = {"cycles": sim.cycles.cpu().numpy(), "stats": st}
+    if logs:
+        out["lat"] = lat.cpu().numpy()[:N]
+        out["pre"] = pre.cpu().numpy()[:N]
+    return out
+
+
+def make_sim(arch, precision="fp32", blob=None, seed=None, **kw):
+    sim = Simnet.for_arch(arch, precision=precision, **kw)
+    if blob is None:
+        blob = I.workload_weights(I.Workload("x", arch, 1, 1, seed=seed or 1))
+    sim.load_weights(blob.astype(np.float32))
+    return sim, blob

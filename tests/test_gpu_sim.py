@@ -1,0 +1,132 @@
+"""GPU parity of the CUDA simulation path against the FP64 oracle.
+
+Integer state (F/E, curTick, queue, cycle counts) must be bit-exact when both
+sides use the same integer latencies (teacher forcing, both directions).  The
+predicted latencies (softplus outputs before rounding) must agree within 1e-3
+in the paper's error form |f - y| / (y + 1) for FP32.  Free-running cycle
+counts must agree within 0.1% (FP32).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2105_05821_b300 import inputs as I
+from paper_2105_05821_b300.simnet import Simnet, SimnetError
+
+from gpu_util import latency_error, make_sim, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP32_LAT_TOL = 1e-3
+FP32_CPI_TOL = 1e-3
+
+
+def teacher_forced_check(arch, trace, precision, blob, lat_tol, rw=8, strict=False, graph=True):
+    cfg = oracle.Config.of(arch, retire_width=rw, retire_strict=strict)
+    ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, logs=True)
+    sim, _ = make_sim(arch, precision, blob=blob, retire_width=rw, strict=strict, graph=graph)
+    # GPU replays the oracle's latencies: every integer must match
+    g = run_gpu(sim, trace, replay=ref.lat)
+    np.testing.assert_array_equal(g["cycles"], ref.cycles)
+    np.testing.assert_array_equal(g["lat"], ref.lat)
+    assert g["stats"].evictions == int(ref.evictions.sum())
+    assert g["stats"].total_cycles == int(ref.cycles.sum())
+    err = latency_error(g["pre"], ref.pre)
+    assert np.isfinite(g["pre"]).all()
+    assert err.max() <= lat_tol, (err.max(), np.percentile(err, 99))
+    # oracle replays the GPU's free-running latencies: every integer must match
+    f = run_gpu(sim, trace)
+    back = oracle.simulate(cfg, trace.records, trace.offsets, replay=f["lat"], logs=True)
+    np.testing.assert_array_equal(back.cycles, f["cycles"])
+    return ref, f, err
+
+
+def test_c1_fp32_teacher_forced_and_free_running():
+    w = I.WORKLOADS["c1"]
+    trace = I.make_trace(w)
+    blob = I.workload_weights(w)
+    ref, free, err = teacher_forced_check(w.arch, trace, "fp32", blob, FP32_LAT_TOL)
+    # free-running: same CNN on its own trajectory
+    cpi_err = abs(free["cycles"].sum() / ref.cycles.sum() - 1.0)
+    assert cpi_err <= FP32_CPI_TOL
+    agree = (free["lat"] == ref.lat).mean()
+    assert agree > 0.99
+
+
+@pytest.mark.parametrize("lengths", [[0, 1, 5, 33, 130, 7, 64, 0], [1], [257]])
+def test_ragged_subtraces_fp32(lengths):
+    arch = I.ARCH_SMALL(32)
+    trace = I.small_trace(lengths, seed=sum(lengths) + 3)
+    blob = I.workload_weights(I.Workload("r", arch, 1, 1, seed=17))
+    teacher_forced_check(arch, trace, "fp32", blob, FP32_LAT_TOL)
+
+
+@pytest.mark.parametrize("rw,strict,graph", [(1, False, True), (3, True, False), (8, True, True)])
+def test_retire_rules_fp32(rw, strict, graph):
+    arch = I.Arch(window=16, n_conv=1, channels=64, hidden=64)
+    trace = I.small_trace([200, 31, 90], seed=5)
+    blob = I.workload_weights(I.Workload("r", arch, 1, 1, seed=23))
+    teacher_forced_check(arch, trace, "fp32", blob, FP32_LAT_TOL, rw=rw, strict=strict, graph=graph)
+
+
+def test_c2_arch_fp32_small():
+    w = I.WORKLOADS["c2"]
+    full = I.make_trace(w, n_subtraces=4)
+    offs = np.minimum(full.offsets, 1200)                      # lengths 1000, 200, 0, 0
+    trace = I.Trace(full.records[:1200].copy(), offs)
+    blob = I.workload_weights(w)
+    teacher_forced_check(w.arch, trace, "fp32", blob, FP32_LAT_TOL)
+
+
+def test_graph_and_direct_launch_identical():
+    w = I.WORKLOADS["c1"]
+    trace = I.make_trace(w)
+    blob = I.workload_weights(w)
+    a, _ = make_sim(w.arch, "fp32", blob=blob, graph=True)
+    b, _ = make_sim(w.arch, "fp32", blob=blob, graph=False)
+    ra, ra2, rb = run_gpu(a, trace), run_gpu(a, trace), run_gpu(b, trace)
+    np.testing.assert_array_equal(ra["lat"], rb["lat"])
+    np.testing.assert_array_equal(ra["cycles"], rb["cycles"])
+    np.testing.assert_array_equal(ra["pre"], ra2["pre"])     # run-to-run bit identical
+
+
+def test_uneven_lengths_compaction():
+    """Log-normal-like uneven lengths exercise the active-set compaction; the
+    result must not depend on it (sub-traces are independent, Sec. 3.3)."""
+    arch = I.ARCH_SMALL(32)
+    rng = np.random.default_rng(4)
+    lengths = np.clip(np.rint(np.exp(rng.normal(np.log(60), 0.8, 40))), 1, 400).astype(int).tolist()
+    trace = I.small_trace(lengths, seed=44)
+    blob = I.workload_weights(I.Workload("u", arch, 1, 1, seed=4))
+    teacher_forced_check(arch, trace, "fp32", blob, FP32_LAT_TOL)
+
+
+def test_cnn_forward_fp32_matches_oracle():
+    for arch in (I.ARCH_SMALL(32), I.ARCH_MID, I.ARCH_WIDE):
+        blob = I.workload_weights(I.Workload("x", arch, 1, 1, seed=9))
+        sim, _ = make_sim(arch, "fp32", blob=blob)
+        x = I.random_windows(333, arch, 10)   # 333 windows: several tiles and a ragged tail
+        z = sim.cnn_forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
+        zr = oracle.cnn_forward(oracle.Config.of(arch), blob, x)
+        err = latency_error(oracle.softplus(z), oracle.softplus(zr))
+        assert err.max() <= FP32_LAT_TOL, err.max()
+
+
+def test_errors_reported():
+    arch = I.ARCH_SMALL(32)
+    sim = Simnet.for_arch(arch)
+    trace = I.small_trace([10, 10], seed=1)
+    rec = torch.from_numpy(trace.records.view(np.int32)).cuda()
+    off = torch.from_numpy(trace.offsets).cuda()
+    with pytest.raises(SimnetError) as e:
+        sim.simulate(rec, off)
+    assert e.value.status == 5                                  # ESTATE: no weights
+    with pytest.raises(SimnetError) as e:
+        sim.load_weights(np.zeros(10, np.float32))
+    assert e.value.status == 1                                  # EINVAL: wrong blob size
+    sim.load_weights(I.workload_weights(I.Workload("x", arch, 1, 1, seed=1)).astype(np.float32))
+    bad = torch.tensor([0, 21, 20], dtype=torch.int64, device="cuda")   # offsets decrease
+    with pytest.raises(SimnetError) as e:
+        sim.simulate(rec, bad)
+    assert e.value.status == 1
