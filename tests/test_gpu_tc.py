@@ -33,21 +33,33 @@ def torch_bf16_reference(arch, blob, x):
     return Fn.linear(h, ws["fc2.weight"], ws["fc2.bias"]).numpy()
 
 
+def real_windows(arch, seed, n_sub=3, length=120):
+    """Feature matrices the simulator really builds: the oracle's per-step
+    inputs on a short synthetic trace."""
+    trace = I.small_trace([length] * n_sub, seed=seed)
+    blob = I.workload_weights(I.Workload("x", arch, 1, 1, seed=9))
+    r = oracle.simulate(oracle.Config.of(arch), trace.records, trace.offsets, blob, features=True)
+    return r.feat, blob
+
+
 @pytest.mark.parametrize("arch", [I.ARCH_SMALL(32), I.ARCH_MID, I.ARCH_WIDE, I.ARCH_SMALL(96)])
 def test_cnn_forward_bf16(arch):
     """The tcgen05 GEMM chain against a PyTorch CPU reference with the same BF16
     rounding points (tight), and its distance to the FP64 oracle (reported)."""
-    blob = I.workload_weights(I.Workload("x", arch, 1, 1, seed=9))
+    x, blob = real_windows(arch, seed=arch.window + arch.n_conv)
     sim, _ = make_sim(arch, "bf16", blob=blob)
-    x = I.random_windows(333, arch, 10)
     z = sim.cnn_forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
     ze = torch_bf16_reference(arch, blob, x)
     d = np.abs(z - ze) / (np.abs(ze) + 1.0)
     zr = oracle.cnn_forward(oracle.Config.of(arch), blob, x)
     err = latency_error(oracle.softplus(z), oracle.softplus(zr))
-    print(f"\nbf16 cnn {arch}: vs bf16 reference median {np.median(d):.2e} max {d.max():.2e}; "
-          f"vs fp64 oracle p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e}")
-    assert np.median(d) <= 1e-4 and d.max() <= 2e-2
+    print(f"\nbf16 cnn {arch}: vs bf16 reference median {np.median(d):.2e} p99 {np.percentile(d, 99):.2e} "
+          f"max {d.max():.2e}; vs fp64 oracle p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} "
+          f"max {err.max():.2e}")
+    # same rounding points, different FP32 summation order inside the tensor core:
+    # an occasional BF16 rounding flip of one activation propagates to the output
+    assert np.median(d) <= 1e-4 and np.percentile(d, 99) <= 5e-3 and d.max() <= 5e-2
+    assert err.max() <= BF16_LAT_TOL
 
 
 def test_c1_bf16_teacher_forced():
