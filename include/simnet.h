@@ -199,6 +199,33 @@ simnet_status simnet_cnn_forward(simnet_ctx *ctx, const float *x, float *z, int3
  */
 simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launches_out, int32_t n_kinds);
 
+/*
+ * simnet_cnn_forward_noalloc: simnet_cnn_forward for callers that cannot
+ * allocate device memory while they run (inside an allocator or memory-pool
+ * callback, under a device-memory budget reserved up front by another
+ * framework, or in a latency-critical loop that cannot take cudaMalloc's
+ * implicit synchronisation).  The paper has no counterpart; it is a property
+ * of this library's interface.
+ *   x, z, n, stream  as simnet_cnn_forward (x device float [n][window][50],
+ *                    z device float [n][2], outputs before softplus).
+ * The context must use SIMNET_FP32 and have weights loaded, else
+ * SIMNET_EUNSUPPORTED.  The call allocates nothing: its workspace is a
+ * file-scope device array of SIMNET_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until process exit.  It needs
+ *   256 + 4*n*window*64 + 2*4*n*(window/2)*conv_channels + 4*n*fc_hidden
+ * bytes (each term rounded up to 256); a larger n returns SIMNET_EINVAL with
+ * the sizes in simnet_last_error().  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture that should contain this entry point.  All calls
+ * share the array and it keeps the previous call's contents (each call
+ * overwrites every byte it reads); calls whose GPU work overlaps race on it.
+ */
+#define SIMNET_NOALLOC_SCRATCH_BYTES (16u << 20)
+simnet_status simnet_cnn_forward_noalloc(simnet_ctx *ctx, const float *x, float *z, int32_t n,
+                                         void *stream);
+/* Size in bytes of the fixed scratch array behind simnet_cnn_forward_noalloc. */
+size_t simnet_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

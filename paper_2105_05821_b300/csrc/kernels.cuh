@@ -17,4 +17,13 @@ void launch_totals(const StepArgs *A, unsigned long long *out, int n_sub, cudaSt
 void launch_gemm_f32(const float *A, const float *B, const float *bias, float *C, const int32_t *n_active,
                      int m_mult, int m_cap, int N, int K, int relu, cudaStream_t s);
 
+// FP32 weights of a context, for entry points defined outside simnet.cu.
+struct CtxFp32View {
+    int window = 0, hidden = 0, n_layers = 0, device = 0;
+    GemmLayer layer[kMaxConv + 1];
+    const float *w2 = nullptr, *b2 = nullptr;
+};
+bool ctx_fp32_view(const simnet_ctx *c, CtxFp32View &v);
+void ctx_set_error(simnet_ctx *c, const char *msg);
+
 }  // namespace simnet

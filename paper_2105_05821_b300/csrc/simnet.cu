@@ -84,6 +84,24 @@ struct KTimer {
 
 static constexpr int kGraphSteps = 16;
 
+// Read-only view of a context's FP32 weights for entry points in other files.
+namespace simnet {
+bool ctx_fp32_view(const simnet_ctx *c, CtxFp32View &v) {
+    if (!c || !c->has_weights || c->cfg.precision != SIMNET_FP32) return false;
+    v.window = c->cfg.window;
+    v.hidden = c->cfg.fc_hidden;
+    v.n_layers = c->n_layers;
+    for (int l = 0; l < c->n_layers; l++) v.layer[l] = c->layer[l];
+    v.w2 = c->w2;
+    v.b2 = c->b2;
+    v.device = c->device;
+    return true;
+}
+void ctx_set_error(simnet_ctx *c, const char *msg) {
+    if (c) c->err = msg;
+}
+}  // namespace simnet
+
 static simnet_status fail(simnet_ctx *c, simnet_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;

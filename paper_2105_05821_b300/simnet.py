@@ -28,7 +28,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTA
 
 EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_error",
            "simnet_weight_count", "simnet_load_weights", "simnet_simulate", "simnet_cnn_forward",
-           "simnet_kernel_times"]
+           "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes"]
 
 
 class SimnetError(RuntimeError):
@@ -82,6 +82,10 @@ def lib() -> C.CDLL:
         L.simnet_cnn_forward.argtypes = [P, P, P, C.c_int32, P]
         L.simnet_kernel_times.restype = C.c_int
         L.simnet_kernel_times.argtypes = [P, P, P, C.c_int32]
+        L.simnet_cnn_forward_noalloc.restype = C.c_int
+        L.simnet_cnn_forward_noalloc.argtypes = [P, P, P, C.c_int32, P]
+        L.simnet_noalloc_scratch_bytes.restype = C.c_size_t
+        L.simnet_noalloc_scratch_bytes.argtypes = []
         _lib = L
     return _lib
 
@@ -179,6 +183,13 @@ class Simnet:
         n = (C.c_int64 * KERNEL_KINDS)()
         self._check(lib().simnet_kernel_times(self._h, ms, n, KERNEL_KINDS))
         return list(ms), list(n)
+
+    def cnn_forward_noalloc(self, x, z, stream=None):
+        """cnn_forward using the library's fixed scratch array instead of allocated
+        workspace (FP32 contexts; the caller provides z)."""
+        self._check(lib().simnet_cnn_forward_noalloc(self._h, _ptr(x), _ptr(z), x.shape[0],
+                                                     _stream(stream)))
+        return z
 
     def cnn_forward(self, x, z=None, stream=None):
         """Pre-softplus CNN outputs [n, 2] for cuda float32 features [n, W, 50]."""
