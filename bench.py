@@ -186,8 +186,9 @@ def algorithmic_units(w: I.Workload, kind: int, n_active: float, prec: str):
     if kind == 0:   # gather: feature tile written, ring + record + scalars read
         per = a.window * 64 * es + (a.window - 1) * 8 + 4 + 16
         return per * n_active, "byte", "hbm"
-    if kind == 10:  # head + update: FC1 activations read, ring scan, append, scalars
-        per = a.hidden * 4 + 8 * 8 + 8 + 4 + 32
+    if kind == 10:  # head + update + next gather: FC2 partials, ring, append, scalars, next tile rows
+        parts = a.hidden // 64
+        per = parts * 8 + (a.window - 1) * 8 + 8 + 4 + 32 + a.window * 64 * es
         return per * n_active, "byte", "hbm"
     return 0.0, "byte", "hbm"
 

@@ -70,6 +70,7 @@ typedef enum {
 #define SIMNET_FLAG_NO_GRAPH 0x2u      /* launch each step's kernels directly, no CUDA graph */
 #define SIMNET_FLAG_KERNEL_EVENTS 0x4u /* direct launches with a CUDA event pair around each kernel;
                                           per-kernel device times via simnet_kernel_times() */
+#define SIMNET_FLAG_NO_PDL 0x8u        /* no programmatic dependent launch between a step's kernels */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -119,10 +120,11 @@ typedef struct {
 } simnet_stats;
 
 /* Kernel kinds reported by simnet_kernel_times(). */
-#define SIMNET_KERNEL_GATHER 0          /* context gather into the feature tile */
+#define SIMNET_KERNEL_GATHER 0          /* context gather (first step, after compaction; other steps'
+                                           rows come from HEAD_UPDATE) */
 #define SIMNET_KERNEL_LAYER0 1          /* GEMM of layer l is SIMNET_KERNEL_LAYER0 + l (conv..., FC1) */
 #define SIMNET_KERNEL_KINDS 12          /* GATHER, up to 9 GEMM layers, HEAD_UPDATE, COMPACT */
-#define SIMNET_KERNEL_HEAD_UPDATE 10    /* FC2 head + clock/queue update (+ drain) */
+#define SIMNET_KERNEL_HEAD_UPDATE 10    /* FC2 head + clock/queue update (+ drain) + next gather */
 #define SIMNET_KERNEL_COMPACT 11        /* active-set compaction */
 
 /* ABI version of the loaded library (SIMNET_ABI_VERSION of its build). */

@@ -66,4 +66,23 @@ struct GemmLayer {
     const float *oscale; // [N] multiplier applied before storing (FP8 requant) or nullptr
 };
 
+// Launch a kernel, optionally as a programmatic dependent launch: it may start
+// while the previous kernel in the stream finishes; every kernel of this
+// library executes griddepcontrol.wait before touching data other kernels write.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 }  // namespace simnet

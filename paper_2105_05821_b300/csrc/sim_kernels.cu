@@ -78,6 +78,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) gather_kernel(const StepArgs *__restrict__ A, T *__restrict__ X,
                                                      int n_slots) {
     constexpr int V = Vec<T>::N, CH = kNFP / V;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int W = A->window;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)n_slots * W * CH;
@@ -118,6 +120,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) pack_x_kernel(const float *__restrict__ x, T *__restrict__ X,
                                                      int64_t rows) {
     constexpr int V = Vec<T>::N, CH = kNFP / V;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= rows * CH) return;
     const int chunk = (int)(gid % CH);
@@ -171,14 +175,20 @@ __device__ __forceinline__ int retire_run(const uint64_t *__restrict__ ring, int
     return min(k, lim);
 }
 
-// One warp per active slot: FC2 on the FC1 activations, softplus, clamp, round;
+// One warp per active slot.  FC2 arrives as P partial dot products (one per
+// FC1 column block) which are summed with the bias; softplus, clamp, round;
 // then curTick += F, retire (budget RW*F), evict at capacity, append with
 // residence 0; after the last instruction, drain one cycle at a time (budget
-// RW) and write the sub-trace's cycle count.
+// RW) and write the sub-trace's cycle count.  Otherwise the warp writes the
+// slot's feature rows for the next step (the gather, fused here).
+template <typename T>
 __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__restrict__ A,
-                                                          const float *__restrict__ h,
-                                                          const float *__restrict__ w2,
-                                                          const float *__restrict__ b2) {
+                                                          const float2 *__restrict__ part, int P,
+                                                          int part_stride, const float *__restrict__ b2,
+                                                          T *__restrict__ X) {
+    __shared__ uint64_t s_ring[8][256];   // newest-first queue copy per warp (capacity <= 255)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int slot = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (slot >= *A->n_active) return;
@@ -186,13 +196,11 @@ __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__rest
     const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
     int p = A->pos[b];
     if (p >= n) return;
-    const int H = A->hidden;
-    const float *hv = h + (size_t)slot * H;
     float zf = 0.f, ze = 0.f;
-    for (int j = lane; j < H; j += 32) {
-        const float x = hv[j];
-        zf = fmaf(x, w2[j], zf);
-        ze = fmaf(x, w2[H + j], ze);
+    for (int i = lane; i < P; i += 32) {
+        const float2 v = part[(size_t)i * part_stride + slot];
+        zf += v.x;
+        ze += v.y;
     }
     zf = warp_sum(zf) + b2[0];
     ze = warp_sum(ze) + b2[1];
@@ -230,8 +238,8 @@ __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__rest
     }
     ql++;
     p++;
+    __syncwarp();
     if (p == n) {  // drain: Delta of Eq. 1
-        __syncwarp();
         while (ql > 0) {
             tick += 1;
             const int kk = retire_run(ring, cap, qs, min(ql, RW), tick, strict, lane);
@@ -240,6 +248,38 @@ __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__rest
             ql -= kk;
         }
         if (lane == 0) A->cycles_out[b] = tick;
+    } else if (X) {
+        // next step's input rows of this slot: row 0 = instruction p, row r = r-th newest entry.
+        // The queue is copied newest-first into shared memory with independent loads first.
+        uint64_t *sq = s_ring[threadIdx.x >> 5];
+        for (int r = lane + 1; r <= ql; r += 32) {
+            int idx = qs + ql - r;
+            if (idx >= cap) idx -= cap;
+            sq[r] = ring[idx];
+        }
+        __syncwarp();
+        constexpr int V = Vec<T>::N, CH = kNFP / V, RPP = 32 / CH;
+        const int W = A->window;
+        const uint32_t cur = A->records[o + p];
+        const int chunk = lane % CH;
+        T *xs = X + (size_t)slot * W * kNFP;
+        for (int r0 = 0; r0 < W; r0 += RPP) {
+            const int r = r0 + lane / CH;
+            float v[V];
+#pragma unroll
+            for (int j = 0; j < V; j++) v[j] = 0.f;
+            if (r == 0) {
+#pragma unroll
+                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, cur, cur, false, 0, 0);
+            } else if (r <= ql) {
+                const uint64_t ent = sq[r];
+                const int32_t res = tick - (int32_t)entry_tick(ent);
+                const uint32_t rec = entry_rec(ent), e = entry_e(ent);
+#pragma unroll
+                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, rec, cur, true, res, e);
+            }
+            if (r < W) store16<T>(xs + (size_t)r * kNFP + chunk * V, v);
+        }
     }
     if (lane == 0) {
         A->tick[b] = tick;
@@ -247,6 +287,28 @@ __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__rest
         A->qstart[b] = qs;
         A->qlen[b] = ql;
         A->evict[b] += ev;
+    }
+}
+
+// FC2 from partial dot products: z = b2 + sum of P partials (pre-softplus), one warp per row.
+__global__ void __launch_bounds__(256) head_part_z_kernel(const float2 *__restrict__ part, int P, int part_stride,
+                                                          const float *__restrict__ b2, float *__restrict__ z,
+                                                          int n) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    float zf = 0.f, ze = 0.f;
+    for (int i = lane; i < P; i += 32) {
+        const float2 v = part[(size_t)i * part_stride + row];
+        zf += v.x;
+        ze += v.y;
+    }
+    zf = warp_sum(zf);
+    ze = warp_sum(ze);
+    if (lane == 0) {
+        z[2 * row] = zf + b2[0];
+        z[2 * row + 1] = ze + b2[1];
     }
 }
 
@@ -273,6 +335,7 @@ __global__ void __launch_bounds__(256) head_z_kernel(const float *__restrict__ h
 
 // ------------------------------------------------------------------ set-up, compaction, totals
 __global__ void init_state_kernel(const StepArgs *__restrict__ A) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b == 0) { *A->n_active = A->n_sub; *A->status = kStatusOk; }
     if (b >= A->n_sub) return;
@@ -290,6 +353,7 @@ __global__ void init_state_kernel(const StepArgs *__restrict__ A) {
 __global__ void __launch_bounds__(1024) compact_kernel(const StepArgs *__restrict__ A) {
     __shared__ int wsum[32];
     __shared__ int base;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int n = *A->n_active;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) base = 0;
@@ -326,6 +390,7 @@ __global__ void __launch_bounds__(1024) compact_kernel(const StepArgs *__restric
 }
 
 __global__ void totals_kernel(const StepArgs *__restrict__ A, unsigned long long *__restrict__ out) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     unsigned long long cyc = 0, ev = 0;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < A->n_sub; b += gridDim.x * blockDim.x) {
         cyc += (unsigned long long)A->cycles_out[b];
@@ -342,15 +407,30 @@ __global__ void totals_kernel(const StepArgs *__restrict__ A, unsigned long long
     }
 }
 
-// ------------------------------------------------------------------ launchers
-template <typename T>
-void launch_gather(const StepArgs *A, T *X, int n_slots, int window, cudaStream_t s) {
-    const int64_t total = (int64_t)n_slots * window * (kNFP / Vec<T>::N);
-    gather_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(A, X, n_slots);
+// Per-column maximum of non-negative values y [rows][C] into out[C] (float bits;
+// monotone as unsigned for x >= 0).  Used by the FP8 calibration pass.
+__global__ void channel_amax_kernel(const float *__restrict__ y, int64_t rows, int C, unsigned *__restrict__ out) {
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float m = 0.f;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) m = fmaxf(m, fabsf(y[r * C + c]));
+    atomicMax(out + c, __float_as_uint(m));
 }
-template void launch_gather<float>(const StepArgs *, float *, int, int, cudaStream_t);
-template void launch_gather<__nv_bfloat16>(const StepArgs *, __nv_bfloat16 *, int, int, cudaStream_t);
-template void launch_gather<__nv_fp8_e4m3>(const StepArgs *, __nv_fp8_e4m3 *, int, int, cudaStream_t);
+
+// ------------------------------------------------------------------ launchers
+void launch_channel_amax(const float *y, int64_t rows, int C, unsigned *out, cudaStream_t s) {
+    dim3 g(128, (C + 127) / 128);
+    channel_amax_kernel<<<g, 128, 0, s>>>(y, rows, C, out);
+}
+
+template <typename T>
+void launch_gather(const StepArgs *A, T *X, int n_slots, int window, cudaStream_t s, bool pdl) {
+    const int64_t total = (int64_t)n_slots * window * (kNFP / Vec<T>::N);
+    launch_k(pdl, gather_kernel<T>, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, s, A, X, n_slots);
+}
+template void launch_gather<float>(const StepArgs *, float *, int, int, cudaStream_t, bool);
+template void launch_gather<__nv_bfloat16>(const StepArgs *, __nv_bfloat16 *, int, int, cudaStream_t, bool);
+template void launch_gather<__nv_fp8_e4m3>(const StepArgs *, __nv_fp8_e4m3 *, int, int, cudaStream_t, bool);
 
 template <typename T>
 void launch_pack_x(const float *x, T *X, int64_t rows, cudaStream_t s) {
@@ -361,22 +441,38 @@ template void launch_pack_x<float>(const float *, float *, int64_t, cudaStream_t
 template void launch_pack_x<__nv_bfloat16>(const float *, __nv_bfloat16 *, int64_t, cudaStream_t);
 template void launch_pack_x<__nv_fp8_e4m3>(const float *, __nv_fp8_e4m3 *, int64_t, cudaStream_t);
 
-void launch_head_update(const StepArgs *A, const float *h, const float *w2, const float *b2, int n_slots,
-                        cudaStream_t s) {
+template <typename T>
+void launch_head_update(const StepArgs *A, const float2 *part, int P, int part_stride, const float *b2, T *X,
+                        int n_slots, cudaStream_t s, bool pdl) {
     const int64_t threads = (int64_t)n_slots * 32;
-    head_update_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(A, h, w2, b2);
+    launch_k(pdl, head_update_kernel<T>, dim3((unsigned)((threads + 255) / 256)), dim3(256), 0, s, A, part, P,
+             part_stride, b2, X);
 }
+template void launch_head_update<float>(const StepArgs *, const float2 *, int, int, const float *, float *, int,
+                                        cudaStream_t, bool);
+template void launch_head_update<__nv_bfloat16>(const StepArgs *, const float2 *, int, int, const float *,
+                                                __nv_bfloat16 *, int, cudaStream_t, bool);
+template void launch_head_update<__nv_fp8_e4m3>(const StepArgs *, const float2 *, int, int, const float *,
+                                                __nv_fp8_e4m3 *, int, cudaStream_t, bool);
 
 void launch_head_z(const float *h, const float *w2, const float *b2, float *z, int n, int H, cudaStream_t s) {
     const int64_t threads = (int64_t)n * 32;
     if (n > 0) head_z_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(h, w2, b2, z, n, H);
 }
 
+void launch_head_part_z(const float2 *part, int P, int part_stride, const float *b2, float *z, int n,
+                        cudaStream_t s) {
+    const int64_t threads = (int64_t)n * 32;
+    if (n > 0) head_part_z_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(part, P, part_stride, b2, z, n);
+}
+
 void launch_init_state(const StepArgs *A, int n_sub, cudaStream_t s) {
     init_state_kernel<<<(n_sub + 255) / 256 + 1, 256, 0, s>>>(A);
 }
 
-void launch_compact(const StepArgs *A, cudaStream_t s) { compact_kernel<<<1, 1024, 0, s>>>(A); }
+void launch_compact(const StepArgs *A, cudaStream_t s, bool pdl) {
+    launch_k(pdl, compact_kernel, dim3(1), dim3(1024), 0, s, A);
+}
 
 void launch_totals(const StepArgs *A, unsigned long long *out, int n_sub, cudaStream_t s) {
     int blocks = (n_sub + 255) / 256;

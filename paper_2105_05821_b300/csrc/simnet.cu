@@ -3,6 +3,8 @@
 // graphs of whole steps (gather -> conv GEMMs -> FC1 -> head + queue update).
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -33,7 +35,9 @@ struct simnet_ctx {
     // workspace, sized for ws_B sub-traces
     int ws_B = 0;
     void *X = nullptr, *act[2] = {nullptr, nullptr};
-    float *h1 = nullptr;
+    float *h1 = nullptr;  // FC2 partial sums [n_part][B] float2 (sized as the FC1 output)
+    int n_part = 0;
+    bool pdl = true;
     int32_t *tick = nullptr, *pos = nullptr, *qstart = nullptr, *qlen = nullptr, *evict = nullptr;
     int32_t *active = nullptr, *n_active = nullptr, *status = nullptr, *cnt = nullptr;
     uint64_t *ring = nullptr;
@@ -143,6 +147,7 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
     simnet_ctx *c = new simnet_ctx();
     c->cfg = k;
     if (c->cfg.spin_limit_ns <= 0) c->cfg.spin_limit_ns = 2000000000LL;
+    c->pdl = (k.flags & SIMNET_FLAG_NO_PDL) == 0;
     cudaGetDevice(&c->device);
     c->cap = k.window - 1;
     c->rows_n = k.window >> k.n_conv;
@@ -221,6 +226,92 @@ static simnet_status upload(simnet_ctx *c, void **dst, const std::vector<T> &v) 
     return SIMNET_OK;
 }
 
+// Synthetic context rows for the FP8 calibration pass: a current instruction and
+// a random number of context rows with the feature encoding's value ranges
+// (one-hots, register ids / 32, flags, residence and execution latency / 64).
+static void synthetic_windows(int n, int W, std::vector<float> &x) {
+    x.assign((size_t)n * W * kNFP, 0.f);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&st]() {  // xorshift64*
+        st ^= st >> 12;
+        st ^= st << 25;
+        st ^= st >> 27;
+        return (uint32_t)((st * 0x2545F4914F6CDD1Dull) >> 32);
+    };
+    auto uni = [&]() { return (rnd() >> 8) * (1.0f / 16777216.0f); };
+    for (int i = 0; i < n; i++) {
+        const int len = (int)(rnd() % (uint32_t)W);
+        for (int r = 0; r <= len && r < W; r++) {
+            float *row = &x[((size_t)i * W + r) * kNFP];
+            row[rnd() % 32] = 1.f;
+            for (int j = 32; j < 35; j++) row[j] = (float)(rnd() % 32) / 32.f;
+            row[35] = uni() < 0.25f;
+            row[36] = uni() < 0.10f;
+            row[37] = uni() < 0.15f;
+            row[38 + rnd() % 3] = 1.f;
+            row[41] = uni() < 0.05f;
+            if (r > 0) {
+                const float u = uni();
+                row[42] = u * u * 4.f;           // residence up to 256 cycles, mostly short
+                row[43] = (float)(rnd() % 64) / 64.f;
+                for (int j = 45; j < 48; j++) row[j] = uni() < 0.03125f;
+                row[48] = uni() < 0.1f;
+            }
+        }
+    }
+}
+
+// FP8 activation scales: run the FP32 layers on synthetic rows and take each
+// conv output channel's maximum (x2 margin) / 448, the e4m3 maximum.
+static simnet_status calibrate_fp8(simnet_ctx *c, const std::vector<std::vector<float>> &Wg,
+                                   const std::vector<std::vector<float>> &Bg, std::vector<std::vector<float>> &s_act) {
+    const simnet_config &k = c->cfg;
+    const int n = 512, W = k.window, C = k.conv_channels;
+    std::vector<float> xh;
+    synthetic_windows(n, W, xh);
+    float *x = nullptr, *y[2] = {nullptr, nullptr}, *w = nullptr, *b = nullptr;
+    int32_t *cnt = nullptr;
+    unsigned *amax = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(x); cudaFree(y[0]); cudaFree(y[1]); cudaFree(w); cudaFree(b); cudaFree(cnt); cudaFree(amax);
+    };
+    const size_t ybytes = (size_t)n * (W / 2) * C * sizeof(float);
+    size_t wmax = 0;
+    for (int l = 0; l < k.n_conv; l++) wmax = std::max(wmax, Wg[l].size());
+    if (cudaMalloc(&x, xh.size() * 4) != cudaSuccess || cudaMalloc(&y[0], ybytes) != cudaSuccess ||
+        cudaMalloc(&y[1], ybytes) != cudaSuccess || cudaMalloc(&w, wmax * 4) != cudaSuccess ||
+        cudaMalloc(&b, (size_t)C * 4) != cudaSuccess || cudaMalloc(&cnt, 4) != cudaSuccess ||
+        cudaMalloc(&amax, (size_t)C * 4) != cudaSuccess) {
+        cleanup();
+        return fail(c, SIMNET_ENOMEM, "FP8 calibration: allocation failed");
+    }
+    cudaMemcpy(x, xh.data(), xh.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(cnt, &n, 4, cudaMemcpyHostToDevice);
+    s_act.assign(k.n_conv, std::vector<float>(C, 1.f));
+    const float *in = x;
+    for (int l = 0; l < k.n_conv; l++) {
+        const GemmLayer &g = c->layer[l];
+        cudaMemcpy(w, Wg[l].data(), Wg[l].size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(b, Bg[l].data(), (size_t)C * 4, cudaMemcpyHostToDevice);
+        launch_gemm_f32(in, w, b, y[l & 1], cnt, g.m_mult, n * g.m_mult, g.N, g.K, 1, 0);
+        cudaMemset(amax, 0, (size_t)C * 4);
+        launch_channel_amax(y[l & 1], (int64_t)n * g.m_mult, C, amax, 0);
+        std::vector<unsigned> am(C);
+        if (cudaMemcpy(am.data(), amax, (size_t)C * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cleanup();
+            return fail(c, SIMNET_ECUDA, "FP8 calibration failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        for (int ch = 0; ch < C; ch++) {
+            float m;
+            memcpy(&m, &am[ch], 4);
+            s_act[l][ch] = m > 0.f ? 2.f * m / 448.f : 1.f;
+        }
+        in = y[l & 1];
+    }
+    cleanup();
+    return SIMNET_OK;
+}
+
 // Re-lay the canonical PyTorch-shaped weights into GEMM operands [N][K]:
 // conv k: K index = t * Cin_pad + ci for kernel tap t of input channel ci
 // (rows 2l and 2l+1 of the input are adjacent, so a conv output row is one dot
@@ -260,15 +351,42 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     }
     std::vector<float> w2(p, p + 2 * H), b2(p + 2 * H, p + 2 * H + 2);
     simnet_status st;
+    std::vector<std::vector<float>> s_act;
+    if (k.precision == SIMNET_FP8_E4M3 && (st = calibrate_fp8(c, Wg, Bg, s_act)) != SIMNET_OK) return st;
     for (int l = 0; l < c->n_layers; l++) {
-        if (k.precision == SIMNET_FP32) {
+        if (k.precision == SIMNET_FP8_E4M3) {
+            // B[n][k] = W[n][k] * s_in[k] / s_w[n]: the input's per-channel scale folded
+            // along K, a per-output-channel scale s_w taken back out in the epilogue,
+            // which also divides by the next layer's input scale (oscale).
+            const GemmLayer &g = c->layer[l];
+            const int K = g.K, Nn = g.N, cin_pad = l == 0 ? kNFP : C;
+            std::vector<float> sin(K, 1.f), sw(Nn), os(Nn);
+            if (l > 0)
+                for (int kk = 0; kk < K; kk++) sin[kk] = s_act[l - 1][kk % cin_pad];
+            std::vector<__nv_fp8_storage_t> wq((size_t)Nn * K);
+            for (int n = 0; n < Nn; n++) {
+                float mx = 0.f;
+                for (int kk = 0; kk < K; kk++) mx = fmaxf(mx, fabsf(Wg[l][(size_t)n * K + kk] * sin[kk]));
+                sw[n] = mx > 0.f ? mx / 448.f : 1.f;
+                for (int kk = 0; kk < K; kk++)
+                    wq[(size_t)n * K + kk] =
+                        __nv_cvt_float_to_fp8(Wg[l][(size_t)n * K + kk] * sin[kk] / sw[n], __NV_SATFINITE, __NV_E4M3);
+                os[n] = l < k.n_conv ? 1.f / s_act[l][n] : 1.f;
+            }
+            if ((st = upload(c, &c->Wl[l], wq)) != SIMNET_OK) return st;
+            if ((st = upload(c, (void **)&c->wscale[l], sw)) != SIMNET_OK) return st;
+            if (l < k.n_conv) {
+                if ((st = upload(c, (void **)&c->oscale[l], os)) != SIMNET_OK) return st;
+            } else if (c->oscale[l]) {
+                cudaFree(c->oscale[l]);
+                c->oscale[l] = nullptr;
+            }
+        } else if (k.precision == SIMNET_FP32) {
             if ((st = upload(c, &c->Wl[l], Wg[l])) != SIMNET_OK) return st;
         } else if (k.precision == SIMNET_BF16) {
             std::vector<__nv_bfloat16> wb(Wg[l].size());
             for (size_t i = 0; i < wb.size(); i++) wb[i] = __float2bfloat16_rn(Wg[l][i]);
             if ((st = upload(c, &c->Wl[l], wb)) != SIMNET_OK) return st;
-        } else {
-            return fail(c, SIMNET_EUNSUPPORTED, "FP8 weights: not built yet");
         }
         if ((st = upload(c, (void **)&c->bias[l], Bg[l])) != SIMNET_OK) return st;
         c->layer[l].B = c->Wl[l];
@@ -324,7 +442,10 @@ static simnet_status ensure_workspace(simnet_ctx *c, int B) {
 
 // The CNN on the batch already in c->X: conv GEMMs, then FC1 into c->h1.
 // `count` is a device int of active rows-groups (sub-traces or windows).
-static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t s, KTimer *kt = nullptr) {
+// The CNN on the batch already in c->X: conv GEMMs, then FC1 with FC2 folded
+// into its epilogue, leaving c->n_part partial sums per row in c->h1.
+static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t s, bool pdl,
+                        KTimer *kt = nullptr) {
     const simnet_config &k = c->cfg;
     const void *in = c->X;
     for (int l = 0; l < c->n_layers; l++) {
@@ -334,44 +455,79 @@ static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t
         void *out = last ? (void *)c->h1 : c->act[l & 1];
         const int m_cap = B * g.m_mult;
         if (k.precision == SIMNET_FP32) {
-            launch_gemm_f32((const float *)in, (const float *)g.B, g.bias, (float *)out, count, g.m_mult, m_cap, g.N,
-                            g.K, g.relu, s);
+            if (last)
+                launch_gemm_f32_part((const float *)in, (const float *)g.B, g.bias, c->w2, (float2 *)out, B, count,
+                                     g.m_mult, m_cap, g.N, g.K, g.relu, s, pdl);
+            else
+                launch_gemm_f32((const float *)in, (const float *)g.B, g.bias, (float *)out, count, g.m_mult, m_cap,
+                                g.N, g.K, g.relu, s, pdl);
         } else {
-            launch_tc_gemm(c->plan[l], in, g, out, last, count, m_cap, s);
+            launch_tc_gemm(c->plan[l], g, count, c->w2, s);
         }
         if (kt) kt->end();
         in = out;
     }
 }
 
-static int launches_per_step(const simnet_ctx *c) { return c->n_layers + 2; }
+static int launches_per_step(const simnet_ctx *c) { return c->n_layers + 1; }
 
-static void enqueue_step(simnet_ctx *c, int B, cudaStream_t s, KTimer *kt = nullptr) {
+// Context gather of every slot into c->X (first step, and after a compaction
+// has moved sub-traces to new slots); other steps get their rows from the
+// previous step's head/update kernel.
+static void enqueue_gather(simnet_ctx *c, int B, cudaStream_t s, bool pdl, KTimer *kt = nullptr) {
     if (kt) kt->begin(SIMNET_KERNEL_GATHER);
     switch (c->cfg.precision) {
-        case SIMNET_FP32: launch_gather<float>(c->d_args, (float *)c->X, B, c->cfg.window, s); break;
-        case SIMNET_BF16: launch_gather<__nv_bfloat16>(c->d_args, (__nv_bfloat16 *)c->X, B, c->cfg.window, s); break;
-        default: launch_gather<__nv_fp8_e4m3>(c->d_args, (__nv_fp8_e4m3 *)c->X, B, c->cfg.window, s); break;
+        case SIMNET_FP32: launch_gather<float>(c->d_args, (float *)c->X, B, c->cfg.window, s, pdl); break;
+        case SIMNET_BF16:
+            launch_gather<__nv_bfloat16>(c->d_args, (__nv_bfloat16 *)c->X, B, c->cfg.window, s, pdl);
+            break;
+        default: launch_gather<__nv_fp8_e4m3>(c->d_args, (__nv_fp8_e4m3 *)c->X, B, c->cfg.window, s, pdl); break;
     }
-    if (kt) kt->end();
-    enqueue_cnn(c, c->n_active, B, s, kt);
-    if (kt) kt->begin(SIMNET_KERNEL_HEAD_UPDATE);
-    launch_head_update(c->d_args, c->h1, c->w2, c->b2, B, s);
     if (kt) kt->end();
 }
 
-static simnet_status prepare_plans(simnet_ctx *c, int B) {
-    if (c->cfg.precision == SIMNET_FP32) return SIMNET_OK;
+static void enqueue_step(simnet_ctx *c, int B, cudaStream_t s, bool pdl, KTimer *kt = nullptr) {
+    enqueue_cnn(c, c->n_active, B, s, pdl, kt);
+    if (kt) kt->begin(SIMNET_KERNEL_HEAD_UPDATE);
+    const float2 *part = (const float2 *)c->h1;
+    switch (c->cfg.precision) {
+        case SIMNET_FP32:
+            launch_head_update<float>(c->d_args, part, c->n_part, B, c->b2, (float *)c->X, B, s, pdl);
+            break;
+        case SIMNET_BF16:
+            launch_head_update<__nv_bfloat16>(c->d_args, part, c->n_part, B, c->b2, (__nv_bfloat16 *)c->X, B, s, pdl);
+            break;
+        default:
+            launch_head_update<__nv_fp8_e4m3>(c->d_args, part, c->n_part, B, c->b2, (__nv_fp8_e4m3 *)c->X, B, s, pdl);
+            break;
+    }
+    if (kt) kt->end();
+}
+
+static void enqueue_compact(simnet_ctx *c, int B, cudaStream_t s, bool pdl, KTimer *kt = nullptr) {
+    if (kt) kt->begin(SIMNET_KERNEL_COMPACT);
+    launch_compact(c->d_args, s, pdl);
+    if (kt) kt->end();
+    enqueue_gather(c, B, s, pdl, kt);
+}
+
+static simnet_status prepare_plans(simnet_ctx *c, int B, bool pdl) {
+    const GemmLayer &fc1 = c->layer[c->n_layers - 1];
+    if (c->cfg.precision == SIMNET_FP32) {
+        c->n_part = gemm_f32_part_blocks(fc1.N);
+        return SIMNET_OK;
+    }
     for (int l = 0; l < c->n_layers; l++) {
         const GemmLayer &g = c->layer[l];
         const bool last = l == c->n_layers - 1;
         const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
         void *out = last ? (void *)c->h1 : c->act[l & 1];
         std::string why;
-        if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, last, B * g.m_mult, c->cfg.spin_limit_ns,
-                          c->status, why))
+        if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, last ? TC_OUT_PART : TC_OUT_ACT, B * g.m_mult,
+                          c->cfg.spin_limit_ns, c->status, pdl, why))
             return fail(c, SIMNET_ECUDA, "tensor-core plan for layer %d: %s", l, why.c_str());
     }
+    c->n_part = 2 * (fc1.N / c->plan[c->n_layers - 1].BN);   // two column halves per block
     return SIMNET_OK;
 }
 
@@ -382,8 +538,8 @@ static simnet_status capture_graphs(simnet_ctx *c, int B, bool compact) {
         const int steps = gi == 0 ? kGraphSteps : 1;
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        for (int i = 0; i < steps; i++) enqueue_step(c, B, c->cap_stream);
-        if (compact) launch_compact(c->d_args, c->cap_stream);
+        for (int i = 0; i < steps; i++) enqueue_step(c, B, c->cap_stream, c->pdl && i > 0);
+        if (compact) enqueue_compact(c, B, c->cap_stream, c->pdl);
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
         if (e != cudaSuccess) return fail(c, SIMNET_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         e = cudaGraphInstantiate(&c->gexec[gi], graph, 0);
@@ -463,22 +619,24 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
     launch_init_state(c->d_args, B, s);
 
     const bool uneven = min_len != max_len;
-    if ((st = prepare_plans(c, B)) != SIMNET_OK) return st;
-    int64_t launches = 1 + (int64_t)max_len * launches_per_step(c);
     const bool timed = (c->cfg.flags & SIMNET_FLAG_KERNEL_EVENTS) != 0;
-    if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
-        KTimer kt;
-        kt.c = timed ? c : nullptr;
-        kt.s = s;
+    const bool pdl = c->pdl && !timed;
+    if ((st = prepare_plans(c, B, pdl)) != SIMNET_OK) return st;
+    int64_t launches = 2 + (int64_t)max_len * launches_per_step(c);
+    KTimer kt;
+    kt.c = timed ? c : nullptr;
+    kt.s = s;
+    if (timed) {
         c->ev_used = 0;
         c->kt_valid = false;
+    }
+    enqueue_gather(c, B, s, false, timed ? &kt : nullptr);
+    if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
         for (int64_t i = 0; i < max_len; i++) {
-            enqueue_step(c, B, s, timed ? &kt : nullptr);
+            enqueue_step(c, B, s, pdl, timed ? &kt : nullptr);
             if (uneven && (i % kGraphSteps) == kGraphSteps - 1) {
-                if (timed) kt.begin(SIMNET_KERNEL_COMPACT);
-                launch_compact(c->d_args, s);
-                if (timed) kt.end();
-                launches++;
+                enqueue_compact(c, B, s, pdl, timed ? &kt : nullptr);
+                launches += 2;
             }
         }
         if (timed && !kt.ok) return fail(c, SIMNET_ENOMEM, "kernel timing: event pool exhausted");
@@ -489,7 +647,7 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
         const int64_t full = max_len / kGraphSteps, rest = max_len % kGraphSteps;
         for (int64_t i = 0; i < full; i++) CK(cudaGraphLaunch(c->gexec[0], s));
         for (int64_t i = 0; i < rest; i++) CK(cudaGraphLaunch(c->gexec[1], s));
-        if (uneven) launches += full + rest;
+        if (uneven) launches += 2 * (full + rest);
     }
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev1, s));
@@ -530,10 +688,10 @@ extern "C" simnet_status simnet_cnn_forward(simnet_ctx *c, const float *x, float
         case SIMNET_BF16: launch_pack_x<__nv_bfloat16>(x, (__nv_bfloat16 *)c->X, rows, s); break;
         default: launch_pack_x<__nv_fp8_e4m3>(x, (__nv_fp8_e4m3 *)c->X, rows, s); break;
     }
-    if ((st = prepare_plans(c, n)) != SIMNET_OK) return st;
+    if ((st = prepare_plans(c, n, false)) != SIMNET_OK) return st;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int32_t), s));
-    enqueue_cnn(c, c->cnt, n, s);
-    launch_head_z(c->h1, c->w2, c->b2, z, n, c->cfg.fc_hidden, s);
+    enqueue_cnn(c, c->cnt, n, s, false);
+    launch_head_part_z((const float2 *)c->h1, c->n_part, n, c->b2, z, n, s);
     CK(cudaGetLastError());
     return SIMNET_OK;
 }

@@ -8,6 +8,13 @@
 
 namespace simnet {
 
+// What the epilogue writes.
+enum TcOut : int {
+    TC_OUT_ACT = 0,   // activations [M][N] in the layer precision (BF16, or FP8 e4m3)
+    TC_OUT_F32 = 1,   // FP32 [M][N]
+    TC_OUT_PART = 3,  // FC2 partial dot products [2*N/BN][m_cap] float2 (fetch, execution)
+};
+
 // Everything one layer's tensor-core launch needs; built once per
 // (buffers, batch capacity) and reused by every step.
 struct TcPlan {
@@ -15,8 +22,11 @@ struct TcPlan {
     int prec = 0;           // SIMNET_BF16 or SIMNET_FP8_E4M3
     int BN = 0, stages = 0, grid = 0;
     int m_cap = 0, K = 0, N = 0;
-    bool out_f32 = false;
+    int out_kind = TC_OUT_ACT;
+    int prm_floats = 0;
+    bool pdl = false;
     const void *in = nullptr;
+    const void *wB = nullptr;
     void *out = nullptr;
     size_t smem = 0;
     int64_t spin_ns = 0;
@@ -26,15 +36,15 @@ struct TcPlan {
 
 // Choose tile shape and encode the TMA descriptors.  Returns false (and a
 // reason) for shapes this kernel does not handle.
-bool make_tc_plan(TcPlan &p, int prec, const void *in, const GemmLayer &g, void *out, bool out_f32, int m_cap,
-                  int64_t spin_ns, int32_t *status, std::string &why);
+bool make_tc_plan(TcPlan &p, int prec, const void *in, const GemmLayer &g, void *out, int out_kind, int m_cap,
+                  int64_t spin_ns, int32_t *status, bool pdl, std::string &why);
 
-// Force a tile width / stage count (the autotuner's knob); re-encodes B's map.
-bool retune_tc_plan(TcPlan &p, const GemmLayer &g, int BN, int stages, std::string &why);
+// Force a tile width (the autotuner's knob); re-encodes B's map.
+bool retune_tc_plan(TcPlan &p, const GemmLayer &g, int BN, std::string &why);
 
-// C = act(A * B^T * scale + bias) * oscale for M = min(*count * m_mult, m_cap) rows.
-void launch_tc_gemm(const TcPlan &p, const void *in, const GemmLayer &g, void *out, bool out_f32,
-                    const int32_t *count, int m_cap, cudaStream_t s);
+// C = act(A * B^T * scale + bias) * oscale for M = min(*count * m_mult, m_cap)
+// rows; TC_OUT_PART folds FC2 (`w2` [2][N]) into the epilogue instead.
+void launch_tc_gemm(const TcPlan &p, const GemmLayer &g, const int32_t *count, const float *w2, cudaStream_t s);
 
 int num_sms();
 

@@ -91,6 +91,22 @@ def test_graph_and_direct_launch_identical():
     np.testing.assert_array_equal(ra["pre"], ra2["pre"])     # run-to-run bit identical
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_pdl_graph_direct_identical(precision):
+    """Programmatic dependent launch, CUDA graphs and plain launches must give
+    bit-identical logs on a workload with compaction (uneven lengths)."""
+    arch = I.ARCH_SMALL(32)
+    trace = I.small_trace([50, 300, 7, 160, 0, 90] * 4, seed=12)
+    blob = I.workload_weights(I.Workload("p", arch, 1, 1, seed=12))
+    runs = []
+    for graph, pdl in ((True, True), (True, False), (False, True), (False, False)):
+        sim, _ = make_sim(arch, precision, blob=blob, graph=graph, pdl=pdl)
+        runs.append(run_gpu(sim, trace))
+    for r in runs[1:]:
+        np.testing.assert_array_equal(r["pre"], runs[0]["pre"])
+        np.testing.assert_array_equal(r["cycles"], runs[0]["cycles"])
+
+
 def test_uneven_lengths_compaction():
     """Log-normal-like uneven lengths exercise the active-set compaction; the
     result must not depend on it (sub-traces are independent, Sec. 3.3)."""
