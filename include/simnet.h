@@ -201,6 +201,69 @@ simnet_status simnet_cnn_forward(simnet_ctx *ctx, const float *x, float *z, int3
  */
 simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launches_out, int32_t n_kinds);
 
+/* ------------------------------------------------------------------ training (Sec. 2.4) */
+
+/*
+ * A trace labelled by a timing model, resident on the device (all arrays
+ * [n_records], indexed by instruction):
+ *   fetch      cycle each instruction was fetched (non-decreasing);
+ *   e_label    its execution latency label, the context feature of later windows;
+ *   ctx_begin  first instruction still in flight when the previous one was
+ *              fetched: the window of i holds i, then i-1 ... max(ctx_begin[i],
+ *              i-window+1), with residence fetch[i-1] - fetch[j];
+ *   labels     [n_records][2] (fetch, execution) latency targets.
+ */
+typedef struct {
+    const uint32_t *records;
+    const int64_t *fetch;
+    const uint8_t *e_label;
+    const int64_t *ctx_begin;
+    const uint8_t *labels;
+    int64_t n_records;
+} simnet_windows;
+
+/*
+ * Feature matrices of the windows idx[0..n) (device int64, each in
+ * [0, n_records)) into x_out (device float [n][window][50]), the same rows the
+ * simulator builds.  Errors: EINVAL, ESTATE (no weights loaded).
+ */
+simnet_status simnet_gather_windows(simnet_ctx *ctx, const simnet_windows *w, const int64_t *idx, int32_t n,
+                                    float *x_out, void *stream);
+
+/*
+ * CNN forward for training: x device float [n][window][50], z device float
+ * [n][2] (before softplus).  Keeps every layer's output for the next
+ * simnet_train_backward (one forward is kept per context).  FP32 contexts
+ * compute in FP32; BF16 contexts round GEMM operands to BF16 and accumulate
+ * in FP32 (autocast numerics).  Errors: EINVAL, ESTATE, EUNSUPPORTED (FP8).
+ */
+simnet_status simnet_train_forward(simnet_ctx *ctx, const float *x, float *z, int32_t n, void *stream);
+
+/*
+ * Backward of the last simnet_train_forward: dz device float [n][2] (dLoss/dz),
+ * grad device float [simnet_weight_count] receives dLoss/dtheta in the
+ * canonical blob layout of simnet_load_weights (overwritten).
+ * Errors: EINVAL, ESTATE (no forward yet).
+ */
+simnet_status simnet_train_backward(simnet_ctx *ctx, const float *dz, float *grad, void *stream);
+
+/*
+ * One training step on the windows idx[0..batch) (device int64): gather, forward,
+ * loss = mean over the 2*batch outputs of (softplus(z) - label)^2 (labels are
+ * 0..255), backward, and an Adam step (beta 0.9/0.999, eps 1e-8, no weight
+ * decay) with learning rate lr on FP32 master weights; a BF16 context's BF16
+ * weights are refreshed from them.  loss_out (host) or NULL; when given the call
+ * synchronises `stream`.  Later simulate/cnn_forward calls use the new weights.
+ */
+simnet_status simnet_train_step(simnet_ctx *ctx, const simnet_windows *w, const int64_t *idx, int32_t batch,
+                                float lr, float *loss_out, void *stream);
+
+/* Replace the weights from a DEVICE blob in canonical layout (FP32/BF16 contexts). */
+simnet_status simnet_set_weights_device(simnet_ctx *ctx, const float *blob, void *stream);
+
+/* Current weights (FP32 master copy) into a HOST blob in canonical layout.  Synchronises. */
+simnet_status simnet_get_weights(simnet_ctx *ctx, float *blob);
+
 /*
  * simnet_cnn_forward_noalloc: simnet_cnn_forward for callers that cannot
  * allocate device memory while they run (inside an allocator or memory-pool

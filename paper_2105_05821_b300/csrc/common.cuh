@@ -66,6 +66,40 @@ struct GemmLayer {
     const float *oscale; // [N] multiplier applied before storing (FP8 requant) or nullptr
 };
 
+// ------------------------------------------------------------------ feature encoding (Sec. 2.2)
+// Channel c of a row.  `rec` is the row's instruction; for a context row (ctx)
+// `cur` is the instruction being predicted, `res` its residence and `e` its
+// execution latency.  Layout: 0-31 opcode one-hot; 32-34 src0/src1/dst / 32;
+// 35-37 load/store/branch; 38-40 cache-level one-hot; 41 mispredict;
+// 42 min(res,4095)/64; 43 E/64; 44 store latency (0); 45-47 rec.dst equals
+// cur.src0/src1/dst; 48 both memory ops at one cache level; 49-63 zero.
+__device__ __forceinline__ float feature(int c, uint32_t rec, uint32_t cur, bool ctx, int32_t res,
+                                         uint32_t e) {
+    if (c < 32) return (rec & 31u) == (uint32_t)c ? 1.f : 0.f;
+    const uint32_t dst = (rec >> 15) & 31u;
+    switch (c) {
+        case 32: return (float)((rec >> 5) & 31u) * 0.03125f;
+        case 33: return (float)((rec >> 10) & 31u) * 0.03125f;
+        case 34: return (float)dst * 0.03125f;
+        case 35: return (float)((rec >> 20) & 1u);
+        case 36: return (float)((rec >> 21) & 1u);
+        case 37: return (float)((rec >> 22) & 1u);
+        case 38: case 39: case 40: return ((rec >> 23) & 3u) == (uint32_t)(c - 38) ? 1.f : 0.f;
+        case 41: return (float)((rec >> 25) & 1u);
+        case 42: return ctx ? (float)min(res, 4095) * 0.015625f : 0.f;
+        case 43: return ctx ? (float)e * 0.015625f : 0.f;
+        case 45: return (ctx && dst == ((cur >> 5) & 31u)) ? 1.f : 0.f;
+        case 46: return (ctx && dst == ((cur >> 10) & 31u)) ? 1.f : 0.f;
+        case 47: return (ctx && dst == ((cur >> 15) & 31u)) ? 1.f : 0.f;
+        case 48: {
+            const bool m0 = (rec >> 20) & 3u, m1 = (cur >> 20) & 3u;  // load or store
+            return (ctx && m0 && m1 && ((rec >> 23) & 3u) == ((cur >> 23) & 3u)) ? 1.f : 0.f;
+        }
+        default: return 0.f;
+    }
+}
+
+
 // Launch a kernel, optionally as a programmatic dependent launch: it may start
 // while the previous kernel in the stream finishes; every kernel of this
 // library executes griddepcontrol.wait before touching data other kernels write.

@@ -1,0 +1,133 @@
+// ctx.cuh -- the library context (simnet_ctx) shared by the host-side files.
+#pragma once
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tc_gemm.cuh"
+
+using namespace simnet;
+
+// Training state: Adam moments, gradients and the saved activations of the last
+// training forward (the FP32 master weights are the context's W32/bias/w2/b2).
+struct TrainState {
+    bool ready = false;
+    int n_cap = 0;                     // windows the buffers hold
+    int64_t step = 0;                  // Adam step counter
+    float *gW[kMaxConv + 1] = {}, *gb[kMaxConv + 1] = {};    // gradients
+    float *mW[kMaxConv + 1] = {}, *vW[kMaxConv + 1] = {};    // Adam moments (weights)
+    float *mb[kMaxConv + 1] = {}, *vb[kMaxConv + 1] = {};    // Adam moments (biases)
+    float *gw2 = nullptr, *gb2 = nullptr;
+    float *mw2 = nullptr, *vw2 = nullptr, *mb2 = nullptr, *vb2 = nullptr;
+    float *X = nullptr;                // packed input [n][W][64]
+    float *Y[kMaxConv + 1] = {};       // outputs of every layer (post-ReLU); Y[L] = FC1 [n][H]
+    float *dA = nullptr, *dB = nullptr;  // gradient ping-pong buffers (largest activation)
+    float *z = nullptr, *dz = nullptr; // [n][2]
+    double *loss = nullptr;            // device scalar
+    int n_last = 0;                    // windows of the last forward
+};
+
+struct simnet_ctx {
+    simnet_config cfg{};
+    int cap = 0, rows_n = 0, fc1_in = 0, n_layers = 0;
+    int64_t n_weights = 0;
+    std::string err;
+    bool has_weights = false;
+    int device = 0;
+
+    // weights in GEMM layout ([N][K], layer precision) + FP32 biases; FC2 in FP32
+    void *Wl[kMaxConv + 1] = {};
+    float *bias[kMaxConv + 1] = {};
+    float *wscale[kMaxConv + 1] = {};  // FP8: per-output-channel dequant scale
+    float *oscale[kMaxConv + 1] = {};  // FP8: per-output-channel requant multiplier (1/next act scale)
+    float *W32[kMaxConv + 1] = {};     // FP32 GEMM-layout weights (aliases Wl for FP32 contexts)
+    float *w2 = nullptr, *b2 = nullptr;
+    GemmLayer layer[kMaxConv + 1];
+    TcPlan plan[kMaxConv + 1];
+
+    // workspace, sized for ws_B sub-traces
+    int ws_B = 0;
+    void *X = nullptr, *act[2] = {nullptr, nullptr};
+    float *h1 = nullptr;  // FC2 partial sums [n_part][B] float2 (sized as the FC1 output)
+    int n_part = 0;
+    bool pdl = true;
+    int32_t *tick = nullptr, *pos = nullptr, *qstart = nullptr, *qlen = nullptr, *evict = nullptr;
+    int32_t *active = nullptr, *n_active = nullptr, *status = nullptr, *cnt = nullptr;
+    uint64_t *ring = nullptr;
+    unsigned long long *totals = nullptr;
+    StepArgs *d_args = nullptr, *h_args = nullptr;
+    int64_t *h_offsets = nullptr;
+    size_t h_offsets_cap = 0;
+    unsigned long long *h_totals = nullptr;
+    int32_t *h_status = nullptr;
+    cudaEvent_t args_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
+    bool args_pending = false;
+    cudaStream_t cap_stream = nullptr;
+
+    // captured step graphs: [0] = kGraphSteps steps, [1] = one step
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int g_B = -1, g_compact = -1;
+
+    // per-kernel CUDA-event timing (SIMNET_FLAG_KERNEL_EVENTS)
+    std::vector<cudaEvent_t> evpool;
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+    bool kt_valid = false;
+
+    TrainState tr;
+};
+
+// Records an event pair around each kernel when timing is on.
+struct KTimer {
+    simnet_ctx *c = nullptr;
+    cudaStream_t s = nullptr;
+    bool ok = true;
+    void begin(int kind) {
+        if (!c) return;
+        if (c->ev_used + 2 > c->evpool.size()) {
+            for (int i = 0; i < 256; i++) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) { ok = false; return; }
+                c->evpool.push_back(e);
+            }
+            c->ev_kind.resize(c->evpool.size());
+        }
+        c->ev_kind[c->ev_used] = kind;
+        cudaEventRecord(c->evpool[c->ev_used++], s);
+    }
+    void end() {
+        if (!c || !ok) return;
+        cudaEventRecord(c->evpool[c->ev_used++], s);
+    }
+};
+
+
+static inline simnet_status fail(simnet_ctx *c, simnet_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? SIMNET_ENOMEM : SIMNET_ECUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(c, e_ == cudaErrorMemoryAllocation ? SIMNET_ENOMEM : SIMNET_ECUDA,        \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)

@@ -11,80 +11,10 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "ctx.cuh"
 #include "tc_gemm.cuh"
 
 using namespace simnet;
-
-struct simnet_ctx {
-    simnet_config cfg{};
-    int cap = 0, rows_n = 0, fc1_in = 0, n_layers = 0;
-    int64_t n_weights = 0;
-    std::string err;
-    bool has_weights = false;
-    int device = 0;
-
-    // weights in GEMM layout ([N][K], layer precision) + FP32 biases; FC2 in FP32
-    void *Wl[kMaxConv + 1] = {};
-    float *bias[kMaxConv + 1] = {};
-    float *wscale[kMaxConv + 1] = {};  // FP8: per-output-channel dequant scale
-    float *oscale[kMaxConv + 1] = {};  // FP8: per-output-channel requant multiplier (1/next act scale)
-    float *w2 = nullptr, *b2 = nullptr;
-    GemmLayer layer[kMaxConv + 1];
-    TcPlan plan[kMaxConv + 1];
-
-    // workspace, sized for ws_B sub-traces
-    int ws_B = 0;
-    void *X = nullptr, *act[2] = {nullptr, nullptr};
-    float *h1 = nullptr;  // FC2 partial sums [n_part][B] float2 (sized as the FC1 output)
-    int n_part = 0;
-    bool pdl = true;
-    int32_t *tick = nullptr, *pos = nullptr, *qstart = nullptr, *qlen = nullptr, *evict = nullptr;
-    int32_t *active = nullptr, *n_active = nullptr, *status = nullptr, *cnt = nullptr;
-    uint64_t *ring = nullptr;
-    unsigned long long *totals = nullptr;
-    StepArgs *d_args = nullptr, *h_args = nullptr;
-    int64_t *h_offsets = nullptr;
-    size_t h_offsets_cap = 0;
-    unsigned long long *h_totals = nullptr;
-    int32_t *h_status = nullptr;
-    cudaEvent_t args_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
-    bool args_pending = false;
-    cudaStream_t cap_stream = nullptr;
-
-    // captured step graphs: [0] = kGraphSteps steps, [1] = one step
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int g_B = -1, g_compact = -1;
-
-    // per-kernel CUDA-event timing (SIMNET_FLAG_KERNEL_EVENTS)
-    std::vector<cudaEvent_t> evpool;
-    std::vector<int> ev_kind;
-    size_t ev_used = 0;
-    bool kt_valid = false;
-};
-
-// Records an event pair around each kernel when timing is on.
-struct KTimer {
-    simnet_ctx *c = nullptr;
-    cudaStream_t s = nullptr;
-    bool ok = true;
-    void begin(int kind) {
-        if (!c) return;
-        if (c->ev_used + 2 > c->evpool.size()) {
-            for (int i = 0; i < 256; i++) {
-                cudaEvent_t e;
-                if (cudaEventCreate(&e) != cudaSuccess) { ok = false; return; }
-                c->evpool.push_back(e);
-            }
-            c->ev_kind.resize(c->evpool.size());
-        }
-        c->ev_kind[c->ev_used] = kind;
-        cudaEventRecord(c->evpool[c->ev_used++], s);
-    }
-    void end() {
-        if (!c || !ok) return;
-        cudaEventRecord(c->evpool[c->ev_used++], s);
-    }
-};
 
 static constexpr int kGraphSteps = 16;
 
@@ -105,24 +35,6 @@ void ctx_set_error(simnet_ctx *c, const char *msg) {
     if (c) c->err = msg;
 }
 }  // namespace simnet
-
-static simnet_status fail(simnet_ctx *c, simnet_status st, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    if (c) c->err = buf;
-    return st;
-}
-
-#define CK(call)                                                                                  \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
-            return fail(c, e_ == cudaErrorMemoryAllocation ? SIMNET_ENOMEM : SIMNET_ECUDA,        \
-                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
 
 static size_t elem_size(int prec) { return prec == SIMNET_FP32 ? 4 : prec == SIMNET_BF16 ? 2 : 1; }
 
@@ -198,6 +110,18 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     free_workspace(c);
+    TrainState &t = c->tr;
+    for (int l = 0; l <= kMaxConv; l++) {
+        void *tb[] = {t.gW[l], t.gb[l], t.mW[l], t.vW[l], t.mb[l], t.vb[l], t.Y[l]};
+        for (void *q : tb)
+            if (q) cudaFree(q);
+        if (c->W32[l] && (void *)c->W32[l] != c->Wl[l]) cudaFree(c->W32[l]);
+    }
+    {
+        void *tb[] = {t.gw2, t.gb2, t.mw2, t.vw2, t.mb2, t.vb2, t.X, t.dA, t.dB, t.z, t.dz, t.loss};
+        for (void *q : tb)
+            if (q) cudaFree(q);
+    }
     for (int l = 0; l <= kMaxConv; l++) {
         if (c->Wl[l]) cudaFree(c->Wl[l]);
         if (c->bias[l]) cudaFree(c->bias[l]);
@@ -383,10 +307,12 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
             }
         } else if (k.precision == SIMNET_FP32) {
             if ((st = upload(c, &c->Wl[l], Wg[l])) != SIMNET_OK) return st;
+            c->W32[l] = (float *)c->Wl[l];
         } else if (k.precision == SIMNET_BF16) {
             std::vector<__nv_bfloat16> wb(Wg[l].size());
             for (size_t i = 0; i < wb.size(); i++) wb[i] = __float2bfloat16_rn(Wg[l][i]);
             if ((st = upload(c, &c->Wl[l], wb)) != SIMNET_OK) return st;
+            if ((st = upload(c, (void **)&c->W32[l], Wg[l])) != SIMNET_OK) return st;
         }
         if ((st = upload(c, (void **)&c->bias[l], Bg[l])) != SIMNET_OK) return st;
         c->layer[l].B = c->Wl[l];
@@ -397,6 +323,21 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     if ((st = upload(c, (void **)&c->w2, w2)) != SIMNET_OK) return st;
     if ((st = upload(c, (void **)&c->b2, b2)) != SIMNET_OK) return st;
     c->has_weights = true;
+    if (c->tr.ready) {  // new weights: restart the optimiser
+        TrainState &t = c->tr;
+        t.step = 0;
+        for (int l = 0; l < c->n_layers; l++) {
+            const size_t wn = (size_t)c->layer[l].N * c->layer[l].K;
+            cudaMemset(t.mW[l], 0, wn * 4);
+            cudaMemset(t.vW[l], 0, wn * 4);
+            cudaMemset(t.mb[l], 0, (size_t)c->layer[l].N * 4);
+            cudaMemset(t.vb[l], 0, (size_t)c->layer[l].N * 4);
+        }
+        cudaMemset(t.mw2, 0, 2 * (size_t)k.fc_hidden * 4);
+        cudaMemset(t.vw2, 0, 2 * (size_t)k.fc_hidden * 4);
+        cudaMemset(t.mb2, 0, 8);
+        cudaMemset(t.vb2, 0, 8);
+    }
     for (auto &g : c->gexec)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     c->g_B = -1;

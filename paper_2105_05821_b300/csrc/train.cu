@@ -1,0 +1,520 @@
+// train.cu -- training the latency predictor (Sec. 2.4): windows labelled by a
+// timing model, the CNN forward with saved activations, hand-written backward
+// kernels for the loss, FC and k=2/stride-2 conv layers, and Adam.
+//
+// All GEMMs here are one strided FP32 kernel (CUDA cores) covering the three
+// forms a layer needs: Y = A W^T (forward), dA = dY W (input gradient) and
+// dW = dY^T A (weight gradient, split over rows with atomic accumulation).
+// With a BF16 context the operands are rounded to BF16 on load and the sums
+// stay FP32 (autocast numerics); master weights, moments and gradients are FP32.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+
+namespace simnet {
+namespace {
+
+// ------------------------------------------------------------------ windows
+// X [n][W][64] (and optionally x50 [n][W][50]): row 0 = instruction i, row r =
+// instruction i-r while i-r >= ctx_begin[i], residence fetch[i-1] - fetch[i-r].
+__global__ void window_gather_kernel(const uint32_t *__restrict__ rec, const int64_t *__restrict__ fetch,
+                                     const uint8_t *__restrict__ e_label, const int64_t *__restrict__ ctx_begin,
+                                     const int64_t *__restrict__ idx, int n, int W, float *__restrict__ X,
+                                     float *__restrict__ x50) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * W * 16) return;
+    const int chunk = (int)(gid & 15);
+    const int64_t rowid = gid >> 4;
+    const int r = (int)(rowid % W);
+    const int s = (int)(rowid / W);
+    const int64_t i = idx[s];
+    const uint32_t cur = rec[i];
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r == 0) {
+        for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, cur, cur, false, 0, 0);
+    } else if (i - r >= ctx_begin[i]) {
+        const int64_t jj = i - r;
+        const int64_t now = i > 0 ? fetch[i - 1] : 0;
+        const int64_t res = now - fetch[jj];
+        const int32_t res32 = (int32_t)(res > 4095 ? 4095 : res);
+        for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, rec[jj], cur, true, res32, e_label[jj]);
+    }
+    *reinterpret_cast<float4 *>(X + rowid * kNFP + chunk * 4) = make_float4(v[0], v[1], v[2], v[3]);
+    if (x50)
+        for (int j = 0; j < 4; j++)
+            if (chunk * 4 + j < kNF) x50[rowid * kNF + chunk * 4 + j] = v[j];
+}
+
+// ------------------------------------------------------------------ strided GEMM
+// C(m, n) = sum_k A(m, k) B(k, n), A(m, k) = A[m*sam + k*sak], B(k, n) = B[k*sbk + n*sbn].
+// K is split over gridDim.z; with `accumulate` every split atomically adds
+// into C (which the caller zeroes), else the single split stores C, + bias, ReLU.
+template <bool ROUND>
+__global__ void __launch_bounds__(256) gemm_strided_kernel(const float *__restrict__ A, int64_t sam, int64_t sak,
+                                                           const float *__restrict__ B, int64_t sbk, int64_t sbn,
+                                                           float *__restrict__ C, int64_t ldc, int M, int N, int K,
+                                                           int k_chunk, const float *__restrict__ bias, int relu,
+                                                           int accumulate) {
+    constexpr int T = 64, BK = 16;
+    __shared__ float As[BK][T + 4], Bs[BK][T + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * T, n0 = blockIdx.x * T;
+    const int k_lo = blockIdx.z * k_chunk, k_hi = min(K, k_lo + k_chunk);
+    const bool a_kfast = sak == 1, b_nfast = sbn == 1;
+    float acc[4][4] = {};
+    for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int e = tid + 256 * q;
+            int mm, kk;
+            if (a_kfast) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            float a = (gm < M && gk < k_hi) ? A[gm * sam + gk * sak] : 0.f;
+            if (ROUND) a = __bfloat162float(__float2bfloat16_rn(a));
+            As[kk][mm] = a;
+            int nn, kb;
+            if (b_nfast) { nn = e & 63; kb = e >> 6; } else { kb = e & 15; nn = e >> 4; }
+            const int gn = n0 + nn, gkb = k0 + kb;
+            float b = (gn < N && gkb < k_hi) ? B[gkb * sbk + gn * sbn] : 0.f;
+            if (ROUND) b = __bfloat162float(__float2bfloat16_rn(b));
+            Bs[kb][nn] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < BK; k++) {
+            const float4 a4 = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+            const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float a[4] = {a4.x, a4.y, a4.z, a4.w}, b[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            if (accumulate) {
+                atomicAdd(C + (int64_t)m * ldc + n, acc[i][j]);
+            } else {
+                float v = acc[i][j] + (bias ? bias[n] : 0.f);
+                if (relu) v = fmaxf(v, 0.f);
+                C[(int64_t)m * ldc + n] = v;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ elementwise
+__global__ void relu_mask_kernel(float *__restrict__ d, const float *__restrict__ y, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(y[i] > 0.f)) d[i] = 0.f;
+}
+
+// out[c] += sum over rows of d[r][c]
+__global__ void colsum_kernel(const float *__restrict__ d, int64_t rows, int C, float *__restrict__ out) {
+    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) s += d[r * C + c];
+    atomicAdd(out + c, s);
+}
+
+// z -> softplus; loss += (y - t)^2 / (2n) with t the label clamped to [0, 255];
+// dz = (y - t) / n * sigmoid(z) (1 above the softplus threshold).
+__global__ void mse_softplus_kernel(const float *__restrict__ z, const uint8_t *__restrict__ labels,
+                                    const int64_t *__restrict__ idx, int n, float *__restrict__ dz,
+                                    double *__restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < 2 * n) {
+        const int r = i >> 1, k = i & 1;
+        const float x = z[i];
+        const float y = x > 20.f ? x : log1pf(expf(x));
+        const float t = (float)labels[2 * idx[r] + k];
+        const float diff = y - t;
+        const float sg = x > 20.f ? 1.f : 1.f / (1.f + expf(-x));
+        dz[i] = diff / (float)n * sg;
+        l = (double)diff * diff / (2.0 * n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
+}
+
+__global__ void adam_kernel(float *__restrict__ th, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// Canonical PyTorch layout <-> GEMM layout of one layer's weights.
+// conv: canonical [co][ci][t] <-> gemm [co][t*cin_pad + ci] (ci < cin)
+// fc1:  canonical [h][ch*Ln + r] <-> gemm [h][r*C + ch]
+__global__ void relayout_kernel(const float *__restrict__ src, float *__restrict__ dst, int is_conv, int rows,
+                                int a, int b, int cin_pad, int to_gemm) {
+    // conv: a = cin, b = 2 taps; fc1: a = C, b = Ln.  One thread per canonical element.
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)a * b;
+    if (i >= (int64_t)rows * per) return;
+    const int64_t row = i / per, rem = i % per;
+    const int x = (int)(rem / b), y = (int)(rem % b);
+    int64_t g;
+    if (is_conv) g = row * (2 * cin_pad) + (int64_t)y * cin_pad + x;   // x = ci, y = t
+    else g = row * per + (int64_t)y * a + x;                             // x = ch, y = r
+    if (to_gemm) dst[g] = src[i];
+    else dst[i] = src[g];
+}
+
+unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+}  // namespace simnet
+
+using namespace simnet;
+
+static void gemm(bool round, const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn,
+                 float *C, int64_t ldc, int M, int N, int K, const float *bias, int relu, bool accumulate,
+                 cudaStream_t s) {
+    int splits = 1, chunk = K;
+    if (accumulate) {  // long reductions (weight gradients): split the rows over blocks
+        const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
+        splits = std::max(1, std::min((K + 255) / 256, 4 * 148 / std::max(tiles, 1)));
+        chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+        splits = (K + chunk - 1) / chunk;
+    }
+    dim3 g((N + 63) / 64, (M + 63) / 64, splits);
+    if (round)
+        gemm_strided_kernel<true><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, chunk, bias, relu,
+                                                    accumulate);
+    else
+        gemm_strided_kernel<false><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, chunk, bias, relu,
+                                                     accumulate);
+}
+
+static int64_t layer_rows(const simnet_ctx *c, int l, int n) { return (int64_t)n * c->layer[l].m_mult; }
+
+// Allocate training buffers for n windows (and master-weight bookkeeping once).
+static simnet_status ensure_train(simnet_ctx *c, int n) {
+    TrainState &t = c->tr;
+    const simnet_config &k = c->cfg;
+    if (!t.ready) {
+        for (int l = 0; l < c->n_layers; l++) {
+            const GemmLayer &g = c->layer[l];
+            const size_t wn = (size_t)g.N * g.K;
+            CK(cudaMalloc(&t.gW[l], wn * 4));
+            CK(cudaMalloc(&t.mW[l], wn * 4));
+            CK(cudaMalloc(&t.vW[l], wn * 4));
+            CK(cudaMalloc(&t.gb[l], (size_t)g.N * 4));
+            CK(cudaMalloc(&t.mb[l], (size_t)g.N * 4));
+            CK(cudaMalloc(&t.vb[l], (size_t)g.N * 4));
+            CK(cudaMemset(t.mW[l], 0, wn * 4));
+            CK(cudaMemset(t.vW[l], 0, wn * 4));
+            CK(cudaMemset(t.mb[l], 0, (size_t)g.N * 4));
+            CK(cudaMemset(t.vb[l], 0, (size_t)g.N * 4));
+        }
+        const size_t h2 = 2 * (size_t)k.fc_hidden;
+        CK(cudaMalloc(&t.gw2, h2 * 4));
+        CK(cudaMalloc(&t.mw2, h2 * 4));
+        CK(cudaMalloc(&t.vw2, h2 * 4));
+        CK(cudaMalloc(&t.gb2, 8));
+        CK(cudaMalloc(&t.mb2, 8));
+        CK(cudaMalloc(&t.vb2, 8));
+        CK(cudaMemset(t.mw2, 0, h2 * 4));
+        CK(cudaMemset(t.vw2, 0, h2 * 4));
+        CK(cudaMemset(t.mb2, 0, 8));
+        CK(cudaMemset(t.vb2, 0, 8));
+        CK(cudaMalloc(&t.loss, sizeof(double)));
+        t.ready = true;
+    }
+    if (n <= t.n_cap) return SIMNET_OK;
+    CK(cudaDeviceSynchronize());
+    cudaFree(t.X);
+    cudaFree(t.dA);
+    cudaFree(t.dB);
+    cudaFree(t.z);
+    cudaFree(t.dz);
+    for (int l = 0; l < c->n_layers; l++) cudaFree(t.Y[l]);
+    CK(cudaMalloc(&t.X, (size_t)n * k.window * kNFP * 4));
+    size_t big = (size_t)n * k.window * kNFP;
+    for (int l = 0; l < c->n_layers; l++) {
+        const size_t e = (size_t)layer_rows(c, l, n) * c->layer[l].N;
+        CK(cudaMalloc(&t.Y[l], e * 4));
+        big = std::max(big, e);
+    }
+    CK(cudaMalloc(&t.dA, big * 4));
+    CK(cudaMalloc(&t.dB, big * 4));
+    CK(cudaMalloc(&t.z, (size_t)n * 2 * 4));
+    CK(cudaMalloc(&t.dz, (size_t)n * 2 * 4));
+    t.n_cap = n;
+    return SIMNET_OK;
+}
+
+static bool train_precision_ok(const simnet_ctx *c) {
+    return c->cfg.precision == SIMNET_FP32 || c->cfg.precision == SIMNET_BF16;
+}
+
+// Forward over t.X (already packed): every layer's output kept; z = FC2.
+static void train_forward_enqueue(simnet_ctx *c, int n, cudaStream_t s) {
+    TrainState &t = c->tr;
+    const bool round = c->cfg.precision == SIMNET_BF16;
+    const float *in = t.X;
+    for (int l = 0; l < c->n_layers; l++) {
+        const GemmLayer &g = c->layer[l];
+        const int R = (int)layer_rows(c, l, n);
+        gemm(round, in, g.K, 1, c->W32[l], 1, g.K, t.Y[l], g.N, R, g.N, g.K, c->bias[l], 1, false, s);
+        in = t.Y[l];
+    }
+    launch_head_z(t.Y[c->n_layers - 1], c->w2, c->b2, t.z, n, c->cfg.fc_hidden, s);
+    t.n_last = n;
+}
+
+// Backward from t.dz through the saved activations; gradients (GEMM layout) in t.g*.
+static void train_backward_enqueue(simnet_ctx *c, cudaStream_t s) {
+    TrainState &t = c->tr;
+    const int n = t.n_last, H = c->cfg.fc_hidden, L = c->n_layers;
+    const bool round = c->cfg.precision == SIMNET_BF16;
+    for (int l = 0; l < L; l++) {
+        cudaMemsetAsync(t.gW[l], 0, (size_t)c->layer[l].N * c->layer[l].K * 4, s);
+        cudaMemsetAsync(t.gb[l], 0, (size_t)c->layer[l].N * 4, s);
+    }
+    cudaMemsetAsync(t.gw2, 0, 2 * (size_t)H * 4, s);
+    cudaMemsetAsync(t.gb2, 0, 8, s);
+    // FC2: dW2 = dz^T H, db2 = sum dz, dH = dz W2 (masked by ReLU of FC1)
+    const float *Hh = t.Y[L - 1];
+    gemm(false, t.dz, 1, 2, Hh, H, 1, t.gw2, H, 2, H, n, nullptr, 0, true, s);
+    colsum_kernel<<<dim3(64, 1), 32, 0, s>>>(t.dz, n, 2, t.gb2);
+    float *d = t.dA, *d2 = t.dB;
+    gemm(false, t.dz, 2, 1, c->w2, H, 1, d, H, n, H, 2, nullptr, 0, false, s);
+    relu_mask_kernel<<<blocks((int64_t)n * H), 256, 0, s>>>(d, Hh, (int64_t)n * H);
+    // FC1 and the conv layers, last to first: dW = dY^T A, db = sum dY, dA = dY W
+    for (int l = L - 1; l >= 0; l--) {
+        const GemmLayer &g = c->layer[l];
+        const int R = (int)layer_rows(c, l, n);
+        const float *A = l == 0 ? t.X : t.Y[l - 1];
+        gemm(round, d, 1, g.N, A, g.K, 1, t.gW[l], g.K, g.N, g.K, R, nullptr, 0, true, s);
+        colsum_kernel<<<dim3(std::min(R, 512), (g.N + 127) / 128), 128, 0, s>>>(d, R, g.N, t.gb[l]);
+        if (l > 0) {
+            gemm(round, d, g.N, 1, c->W32[l], g.K, 1, d2, g.K, R, g.K, g.N, nullptr, 0, false, s);
+            const int64_t e = layer_rows(c, l - 1, n) * c->layer[l - 1].N;
+            relu_mask_kernel<<<blocks(e), 256, 0, s>>>(d2, t.Y[l - 1], e);
+            std::swap(d, d2);
+        }
+    }
+}
+
+// GEMM-layout gradients -> canonical blob layout (device).
+static void grads_to_canonical(simnet_ctx *c, float *out, cudaStream_t s) {
+    TrainState &t = c->tr;
+    const simnet_config &k = c->cfg;
+    const int C = k.conv_channels, H = k.fc_hidden, Ln = c->rows_n;
+    float *p = out;
+    int cin = kNF;
+    for (int l = 0; l < k.n_conv; l++) {
+        const int cin_pad = l == 0 ? kNFP : C;
+        const int64_t cnt = (int64_t)C * cin * 2;
+        relayout_kernel<<<blocks(cnt), 256, 0, s>>>(t.gW[l], p, 1, C, cin, 2, cin_pad, 0);
+        p += cnt;
+        cudaMemcpyAsync(p, t.gb[l], (size_t)C * 4, cudaMemcpyDeviceToDevice, s);
+        p += C;
+        cin = C;
+    }
+    const int64_t cnt = (int64_t)H * C * Ln;
+    relayout_kernel<<<blocks(cnt), 256, 0, s>>>(t.gW[k.n_conv], p, 0, H, C, Ln, 0, 0);
+    p += cnt;
+    cudaMemcpyAsync(p, t.gb[k.n_conv], (size_t)H * 4, cudaMemcpyDeviceToDevice, s);
+    p += H;
+    cudaMemcpyAsync(p, t.gw2, 2 * (size_t)H * 4, cudaMemcpyDeviceToDevice, s);
+    p += 2 * H;
+    cudaMemcpyAsync(p, t.gb2, 8, cudaMemcpyDeviceToDevice, s);
+}
+
+static void refresh_shadow(simnet_ctx *c, cudaStream_t s) {
+    if (c->cfg.precision != SIMNET_BF16) return;
+    for (int l = 0; l < c->n_layers; l++) {
+        const int64_t e = (int64_t)c->layer[l].N * c->layer[l].K;
+        to_bf16_kernel<<<blocks(e), 256, 0, s>>>(c->W32[l], (__nv_bfloat16 *)c->Wl[l], e);
+    }
+}
+
+static void invalidate_plans(simnet_ctx *c) {
+    for (auto &g : c->gexec)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    c->g_B = -1;
+}
+
+extern "C" simnet_status simnet_gather_windows(simnet_ctx *c, const simnet_windows *w, const int64_t *idx, int32_t n,
+                                               float *x_out, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!w || !idx || !x_out || n < 0 || !w->records || !w->fetch || !w->e_label || !w->ctx_begin)
+        return fail(c, SIMNET_EINVAL, "gather_windows: bad arguments");
+    if (n == 0) return SIMNET_OK;
+    CK(cudaSetDevice(c->device));
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "gather_windows: no weights loaded");
+    simnet_status st = ensure_train(c, n);
+    if (st != SIMNET_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    window_gather_kernel<<<blocks((int64_t)n * c->cfg.window * 16), 256, 0, s>>>(
+        w->records, w->fetch, w->e_label, w->ctx_begin, idx, n, c->cfg.window, c->tr.X, x_out);
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_train_forward(simnet_ctx *c, const float *x, float *z, int32_t n, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!x || !z || n <= 0) return fail(c, SIMNET_EINVAL, "train_forward: bad arguments");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "train_forward: no weights loaded");
+    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context");
+    CK(cudaSetDevice(c->device));
+    simnet_status st = ensure_train(c, n);
+    if (st != SIMNET_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_pack_x<float>(x, c->tr.X, (int64_t)n * c->cfg.window, s);
+    train_forward_enqueue(c, n, s);
+    CK(cudaMemcpyAsync(z, c->tr.z, (size_t)n * 2 * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_train_backward(simnet_ctx *c, const float *dz, float *grad, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!dz || !grad) return fail(c, SIMNET_EINVAL, "train_backward: bad arguments");
+    if (!c->tr.ready || c->tr.n_last <= 0) return fail(c, SIMNET_ESTATE, "train_backward: no forward to differentiate");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(c->tr.dz, dz, (size_t)c->tr.n_last * 2 * 4, cudaMemcpyDeviceToDevice, s));
+    train_backward_enqueue(c, s);
+    grads_to_canonical(c, grad, s);
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *w, const int64_t *idx, int32_t batch,
+                                           float lr, float *loss_out, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!w || !idx || batch <= 0 || !w->labels || !(lr >= 0.f))
+        return fail(c, SIMNET_EINVAL, "train_step: bad arguments");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "train_step: no weights loaded");
+    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context");
+    CK(cudaSetDevice(c->device));
+    simnet_status st = ensure_train(c, batch);
+    if (st != SIMNET_OK) return st;
+    TrainState &t = c->tr;
+    cudaStream_t s = (cudaStream_t)stream;
+    window_gather_kernel<<<blocks((int64_t)batch * c->cfg.window * 16), 256, 0, s>>>(
+        w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X, nullptr);
+    train_forward_enqueue(c, batch, s);
+    CK(cudaMemsetAsync(t.loss, 0, sizeof(double), s));
+    mse_softplus_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
+    train_backward_enqueue(c, s);
+    // Adam (beta 0.9 / 0.999, eps 1e-8, no weight decay) on every parameter
+    t.step++;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)t.step), c2 = 1.f - powf(b2, (float)t.step);
+    for (int l = 0; l < c->n_layers; l++) {
+        const int64_t e = (int64_t)c->layer[l].N * c->layer[l].K, nb = c->layer[l].N;
+        adam_kernel<<<blocks(e), 256, 0, s>>>(c->W32[l], t.mW[l], t.vW[l], t.gW[l], e, lr, b1, b2, eps, c1, c2);
+        adam_kernel<<<blocks(nb), 256, 0, s>>>(c->bias[l], t.mb[l], t.vb[l], t.gb[l], nb, lr, b1, b2, eps, c1, c2);
+    }
+    const int64_t h2 = 2 * (int64_t)c->cfg.fc_hidden;
+    adam_kernel<<<blocks(h2), 256, 0, s>>>(c->w2, t.mw2, t.vw2, t.gw2, h2, lr, b1, b2, eps, c1, c2);
+    adam_kernel<<<1, 32, 0, s>>>(c->b2, t.mb2, t.vb2, t.gb2, 2, lr, b1, b2, eps, c1, c2);
+    refresh_shadow(c, s);
+    invalidate_plans(c);
+    if (loss_out) {
+        double l = 0.0;
+        CK(cudaMemcpyAsync(&l, t.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        *loss_out = (float)l;
+    }
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_set_weights_device(simnet_ctx *c, const float *blob, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!blob) return fail(c, SIMNET_EINVAL, "set_weights_device: blob is NULL");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "set_weights_device: load weights once first");
+    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "needs an FP32 or BF16 context");
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const simnet_config &k = c->cfg;
+    const int C = k.conv_channels, H = k.fc_hidden, Ln = c->rows_n;
+    const float *p = blob;
+    int cin = kNF;
+    for (int l = 0; l < k.n_conv; l++) {
+        const int cin_pad = l == 0 ? kNFP : C;
+        const int64_t cnt = (int64_t)C * cin * 2;
+        relayout_kernel<<<blocks(cnt), 256, 0, s>>>(p, c->W32[l], 1, C, cin, 2, cin_pad, 1);
+        p += cnt;
+        CK(cudaMemcpyAsync(c->bias[l], p, (size_t)C * 4, cudaMemcpyDeviceToDevice, s));
+        p += C;
+        cin = C;
+    }
+    const int64_t cnt = (int64_t)H * C * Ln;
+    relayout_kernel<<<blocks(cnt), 256, 0, s>>>(p, c->W32[k.n_conv], 0, H, C, Ln, 0, 1);
+    p += cnt;
+    CK(cudaMemcpyAsync(c->bias[k.n_conv], p, (size_t)H * 4, cudaMemcpyDeviceToDevice, s));
+    p += H;
+    CK(cudaMemcpyAsync(c->w2, p, 2 * (size_t)H * 4, cudaMemcpyDeviceToDevice, s));
+    p += 2 * H;
+    CK(cudaMemcpyAsync(c->b2, p, 8, cudaMemcpyDeviceToDevice, s));
+    refresh_shadow(c, s);
+    invalidate_plans(c);
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_get_weights(simnet_ctx *c, float *blob) {
+    if (!c) return SIMNET_EINVAL;
+    if (!blob) return fail(c, SIMNET_EINVAL, "get_weights: blob is NULL");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "get_weights: no weights loaded");
+    CK(cudaSetDevice(c->device));
+    const simnet_config &k = c->cfg;
+    const int C = k.conv_channels, H = k.fc_hidden, Ln = c->rows_n;
+    float *dev = nullptr;
+    CK(cudaMalloc(&dev, (size_t)c->n_weights * 4));
+    float *p = dev;
+    int cin = kNF;
+    for (int l = 0; l < k.n_conv; l++) {
+        const int cin_pad = l == 0 ? kNFP : C;
+        const int64_t cnt = (int64_t)C * cin * 2;
+        relayout_kernel<<<blocks(cnt), 256>>>(c->W32[l], p, 1, C, cin, 2, cin_pad, 0);
+        p += cnt;
+        cudaMemcpy(p, c->bias[l], (size_t)C * 4, cudaMemcpyDeviceToDevice);
+        p += C;
+        cin = C;
+    }
+    const int64_t cnt = (int64_t)H * C * Ln;
+    relayout_kernel<<<blocks(cnt), 256>>>(c->W32[k.n_conv], p, 0, H, C, Ln, 0, 0);
+    p += cnt;
+    cudaMemcpy(p, c->bias[k.n_conv], (size_t)H * 4, cudaMemcpyDeviceToDevice);
+    p += H;
+    cudaMemcpy(p, c->w2, 2 * (size_t)H * 4, cudaMemcpyDeviceToDevice);
+    p += 2 * H;
+    cudaMemcpy(p, c->b2, 8, cudaMemcpyDeviceToDevice);
+    cudaError_t e = cudaMemcpy(blob, dev, (size_t)c->n_weights * 4, cudaMemcpyDeviceToHost);
+    cudaFree(dev);
+    if (e != cudaSuccess) return fail(c, SIMNET_ECUDA, "get_weights: %s", cudaGetErrorString(e));
+    return SIMNET_OK;
+}

@@ -27,6 +27,9 @@ first ``N mod B`` sub-traces take one more instruction) or log-normal lengths.
 """
 from __future__ import annotations
 
+import ctypes as _C
+import os as _os
+import subprocess as _sp
 from dataclasses import dataclass, field
 from typing import Dict, List, Tuple
 
@@ -302,3 +305,46 @@ def random_windows(n: int, arch: Arch, seed: int) -> np.ndarray:
     x[:, :, 45:49] = rng.random((n, arch.window, 4)) < 0.1
     x[:, 0, 42:] = 0.0
     return x
+
+
+# ----------------------------------------------------------------------------- training labels
+_TOY_SRC = _os.path.join(_os.path.dirname(_os.path.abspath(__file__)), "toy_pipeline.c")
+_TOY_LIB = _os.path.join(_os.path.dirname(_os.path.abspath(__file__)), "libtoypipe.so")
+_toy = None
+
+
+def build_toy(force: bool = False) -> str:
+    """Compile the toy pipeline timing model (gcc) next to its source."""
+    if force or not _os.path.exists(_TOY_LIB) or _os.path.getmtime(_TOY_LIB) < _os.path.getmtime(_TOY_SRC):
+        tmp = _TOY_LIB + f".tmp{_os.getpid()}"
+        _sp.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _TOY_SRC])
+        _os.replace(tmp, _TOY_LIB)
+    return _TOY_LIB
+
+
+@dataclass
+class Labels:
+    fetch: np.ndarray       # int64 [N] fetch cycle
+    complete: np.ndarray    # int64 [N]
+    commit: np.ndarray      # int64 [N]
+    F: np.ndarray           # uint8 [N] fetch latency label
+    E: np.ndarray           # uint8 [N] execution latency label
+    ctx_begin: np.ndarray   # int64 [N] first context instruction of each window
+
+
+def toy_labels(records: np.ndarray) -> Labels:
+    """Run the toy 4-wide, 64-entry-ROB pipeline model over one trace."""
+    global _toy
+    if _toy is None:
+        _toy = _C.CDLL(build_toy())
+        _toy.toy_pipeline.restype = _C.c_int
+        _toy.toy_pipeline.argtypes = [_C.c_void_p, _C.c_int64] + [_C.c_void_p] * 6
+    rec = np.ascontiguousarray(records, dtype=np.uint32)
+    n = len(rec)
+    out = Labels(np.zeros(n, np.int64), np.zeros(n, np.int64), np.zeros(n, np.int64),
+                 np.zeros(n, np.uint8), np.zeros(n, np.uint8), np.zeros(n, np.int64))
+    p = lambda a: a.ctypes.data_as(_C.c_void_p)  # noqa: E731
+    if _toy.toy_pipeline(p(rec), n, p(out.fetch), p(out.complete), p(out.commit), p(out.F), p(out.E),
+                         p(out.ctx_begin)) != 0:
+        raise MemoryError("toy_pipeline: allocation failed")
+    return out

@@ -29,7 +29,9 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTA
 
 EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_error",
            "simnet_weight_count", "simnet_load_weights", "simnet_simulate", "simnet_cnn_forward",
-           "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes"]
+           "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes",
+           "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
+           "simnet_set_weights_device", "simnet_get_weights"]
 
 
 class SimnetError(RuntimeError):
@@ -53,6 +55,11 @@ class _Stats(C.Structure):
     _fields_ = [("total_cycles", C.c_int64), ("instructions", C.c_int64), ("steps", C.c_int64),
                 ("evictions", C.c_int64), ("kernel_launches", C.c_int64), ("ms_total", C.c_float),
                 ("reserved", C.c_float * 3)]
+
+
+class _Windows(C.Structure):
+    _fields_ = [("records", C.c_void_p), ("fetch", C.c_void_p), ("e_label", C.c_void_p),
+                ("ctx_begin", C.c_void_p), ("labels", C.c_void_p), ("n_records", C.c_int64)]
 
 
 _lib = None
@@ -87,6 +94,18 @@ def lib() -> C.CDLL:
         L.simnet_cnn_forward_noalloc.argtypes = [P, P, P, C.c_int32, P]
         L.simnet_noalloc_scratch_bytes.restype = C.c_size_t
         L.simnet_noalloc_scratch_bytes.argtypes = []
+        L.simnet_gather_windows.restype = C.c_int
+        L.simnet_gather_windows.argtypes = [P, C.POINTER(_Windows), P, C.c_int32, P, P]
+        L.simnet_train_forward.restype = C.c_int
+        L.simnet_train_forward.argtypes = [P, P, P, C.c_int32, P]
+        L.simnet_train_backward.restype = C.c_int
+        L.simnet_train_backward.argtypes = [P, P, P, P]
+        L.simnet_train_step.restype = C.c_int
+        L.simnet_train_step.argtypes = [P, C.POINTER(_Windows), P, C.c_int32, C.c_float, P, P]
+        L.simnet_set_weights_device.restype = C.c_int
+        L.simnet_set_weights_device.argtypes = [P, P, P]
+        L.simnet_get_weights.restype = C.c_int
+        L.simnet_get_weights.argtypes = [P, P]
         _lib = L
     return _lib
 
@@ -202,3 +221,45 @@ class Simnet:
             z = torch.empty((n, 2), dtype=torch.float32, device=x.device)
         self._check(lib().simnet_cnn_forward(self._h, _ptr(x), _ptr(z), n, _stream(stream)))
         return z
+
+    # ------------------------------------------------------------------ training
+    def _win(self, w) -> "_Windows":
+        return _Windows(_ptr(w.records), _ptr(w.fetch), _ptr(w.e_label), _ptr(w.ctx_begin),
+                        _ptr(w.labels), w.records.numel())
+
+    def gather_windows(self, w, idx, stream=None):
+        """Feature matrices [n, W, 50] of the windows idx (cuda int64) of a labelled trace."""
+        import torch
+        x = torch.empty((idx.numel(), self.window, 50), dtype=torch.float32, device=idx.device)
+        win = self._win(w)
+        self._check(lib().simnet_gather_windows(self._h, C.byref(win), _ptr(idx), idx.numel(), _ptr(x),
+                                                _stream(stream)))
+        return x
+
+    def train_forward(self, x, stream=None):
+        import torch
+        z = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+        self._check(lib().simnet_train_forward(self._h, _ptr(x), _ptr(z), x.shape[0], _stream(stream)))
+        return z
+
+    def train_backward(self, dz, grad=None, stream=None):
+        import torch
+        if grad is None:
+            grad = torch.empty(self.weight_count, dtype=torch.float32, device=dz.device)
+        self._check(lib().simnet_train_backward(self._h, _ptr(dz), _ptr(grad), _stream(stream)))
+        return grad
+
+    def train_step(self, w, idx, lr=1e-3, stream=None) -> float:
+        win = self._win(w)
+        loss = C.c_float(0.0)
+        self._check(lib().simnet_train_step(self._h, C.byref(win), _ptr(idx), idx.numel(), float(lr),
+                                            C.byref(loss), _stream(stream)))
+        return float(loss.value)
+
+    def set_weights_device(self, blob, stream=None):
+        self._check(lib().simnet_set_weights_device(self._h, _ptr(blob), _stream(stream)))
+
+    def get_weights(self) -> np.ndarray:
+        out = np.zeros(self.weight_count, dtype=np.float32)
+        self._check(lib().simnet_get_weights(self._h, out.ctypes.data_as(C.c_void_p)))
+        return out
