@@ -203,6 +203,13 @@ def kind_name(w, k):
     return f"conv{l + 1}_gemm" if l < w.arch.n_conv else "fc1_gemm"
 
 
+def truncate(trace: I.Trace, n: int) -> I.Trace:
+    lens = np.minimum(trace.lengths(), n)
+    parts = [trace.records[trace.offsets[b]:trace.offsets[b] + lens[b]] for b in range(trace.n_subtraces)]
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    return I.Trace(np.concatenate(parts).astype(np.uint32), offs)
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -212,6 +219,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     w = I.WORKLOADS[args.workload]
     trace = I.make_trace(w)
+    if args.subtrace_len:
+        trace = truncate(trace, args.subtrace_len)
     blob32 = I.workload_weights(w).astype(np.float32)
     N, B = trace.n_instructions, trace.n_subtraces
 
@@ -251,8 +260,10 @@ def run_ours(args, rank, world):
         ms = sum(a.elapsed_time(b) for a, b in evs)
         return ms, wall
 
-    sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width)
+    sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
+                          persistent=args.persistent)
     sim.load_weights(blob32)
+    tiles = sim.autotune(B) if (args.precision != "fp32" and not args.no_autotune) else []
     st = sim.simulate(rec, off, cycles_out=cyc, stats=True)          # compile graphs, count launches
     launches_per_step = st.kernel_launches
 
@@ -281,7 +292,9 @@ def run_ours(args, rank, world):
            "gpu_launches": int(launches_per_step * args.steps),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * N + 8 * (B + 1)),
                    "d2h_bytes_per_step": int(8 * B)},
-           "wall_s_timed": wall}
+           "wall_s_timed": wall,
+           "tile_widths": tiles[:w.arch.n_conv + 1],
+           "kernel_mode": "persistent" if args.persistent and args.precision != "fp32" else "per-layer kernels"}
     out["config"]["instructions_per_step"] = N
     out["total_cycles"] = int(st.total_cycles)
     out["cpi"] = st.total_cycles / N
@@ -313,8 +326,10 @@ def roofline(w, args, blob32, rec, off, cyc, B):
     from paper_2105_05821_b300.simnet import Simnet
     hbm, bf16_burst, bf16_sus, src = peaks()
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          kernel_events=True)
+                          kernel_events=True, persistent=args.persistent)
     sim.load_weights(blob32)
+    if args.precision != "fp32" and not args.no_autotune:
+        sim.autotune(B)
     sim.simulate(rec, off, cycles_out=cyc, stats=True)
     ms, n = sim.kernel_times()
     sim.close()
@@ -360,6 +375,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--persistent", action="store_true",
+                    help="BF16/FP8: one persistent cooperative kernel for the whole call")
+    ap.add_argument("--subtrace-len", type=int, default=0,
+                    help="keep only the first N instructions of every sub-trace (profiling runs)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -71,6 +71,9 @@ typedef enum {
 #define SIMNET_FLAG_KERNEL_EVENTS 0x4u /* direct launches with a CUDA event pair around each kernel;
                                           per-kernel device times via simnet_kernel_times() */
 #define SIMNET_FLAG_NO_PDL 0x8u        /* no programmatic dependent launch between a step's kernels */
+#define SIMNET_FLAG_PERSISTENT 0x10u   /* BF16/FP8: run every step of a call in one persistent
+                                          cooperative kernel (phases separated by grid barriers)
+                                          instead of one kernel per layer and step */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -126,6 +129,18 @@ typedef struct {
 #define SIMNET_KERNEL_KINDS 12          /* GATHER, up to 9 GEMM layers, HEAD_UPDATE, COMPACT */
 #define SIMNET_KERNEL_HEAD_UPDATE 10    /* FC2 head + clock/queue update (+ drain) + next gather */
 #define SIMNET_KERNEL_COMPACT 11        /* active-set compaction */
+
+/*
+ * Autotuner: for batches of n_subtraces sub-traces, time every tile width
+ * (64, 128, 256 output columns) of every tensor-core layer, one layer after
+ * another, on a synthetic trace of `steps` instructions per sub-trace, and keep
+ * the fastest whole simnet_simulate call.  Later calls with the same batch size
+ * use the choice.  bn_out (host, n_conv + 1 entries) or NULL receives the
+ * widths.  FP32 contexts have nothing to tune (returns OK).  Synchronises.
+ * Errors: EINVAL, ESTATE (no weights), ENOMEM.
+ */
+simnet_status simnet_autotune(simnet_ctx *ctx, int32_t n_subtraces, int32_t steps, int32_t *bn_out,
+                              void *stream);
 
 /* ABI version of the loaded library (SIMNET_ABI_VERSION of its build). */
 int32_t simnet_abi_version(void);
@@ -196,10 +211,22 @@ simnet_status simnet_cnn_forward(simnet_ctx *ctx, const float *x, float *z, int3
  * SIMNET_FLAG_KERNEL_EVENTS: for each kind k < n_kinds, ms_out[k] = summed
  * CUDA-event time of its launches (milliseconds) and launches_out[k] = their
  * number (host arrays of n_kinds entries, n_kinds <= SIMNET_KERNEL_KINDS).
+ * For the persistent kernel (SIMNET_FLAG_PERSISTENT) the kinds
+ * are its phases, timed by CTA 0 from barrier to barrier (globaltimer), and
+ * launches_out counts phases.
  * Synchronises the device.  Errors: EINVAL (bad arguments), ESTATE (no such
  * call yet).
  */
 simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launches_out, int32_t n_kinds);
+
+/*
+ * Diagnostics of the last timed persistent-kernel call: out (host, n <= 48
+ * entries) receives, for GEMM layer l, out[4l + k] = summed nanoseconds from
+ * the start of the layer's phase in CTA 0 to k = 0 its first operand tile
+ * arriving, 1 its last MMA commit, 2 its epilogue done, 3 the grid barrier
+ * passed.  Synchronises.  Errors: EINVAL, ESTATE (no such call).
+ */
+simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */
 

@@ -78,7 +78,21 @@ struct simnet_ctx {
     bool kt_valid = false;
 
     TrainState tr;
+
+    // persistent kernel: grid barrier counter, abort flag, per-phase times (CTA 0)
+    unsigned *bar = nullptr;
+    int *bar_abort = nullptr;
+    unsigned long long *phase_ns = nullptr, *phase_n = nullptr;
+    bool phase_on = false, phase_valid = false;
+
+    // autotuned tile widths: tuned_bn[l] applies to batches of tuned_B sub-traces
+    int tuned_B = -1;
+    int tuned_bn[kMaxConv + 1] = {};
 };
+
+namespace simnet {
+bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaStream_t s, std::string &why);
+}
 
 // Records an event pair around each kernel when timing is on.
 struct KTimer {

@@ -1,0 +1,437 @@
+// persist.cu -- the whole lock-step simulation of one simnet_simulate call in a
+// single persistent, cooperative kernel (one CTA per SM).
+//
+// Every step runs as phases separated by grid-wide barriers:
+//   GEMM phase per CNN layer (Sec. 2.3): the layer's 128-row tiles are spread
+//     over the CTAs; inside a CTA the roles of the tensor-core GEMM kernel work
+//     as usual (warp 0 TMA producer, warp 1 tcgen05.mma issuer, warps 2-9
+//     TMEM epilogue) and their pipeline counters carry over from phase to
+//     phase, so the shared-memory ring, mbarriers and TMEM (allocated once)
+//     stay in use for the whole call;
+//   head phase: every warp of the grid takes active sub-traces: FC2 from the
+//     FC1 epilogue's partial sums, softplus/round, clock and queue update,
+//     drain, and the feature rows of the next step (Sec. 3.2, Eq. 1);
+//   every `compact_every` steps (uneven lengths): CTA 0 compacts the active
+//     list, then all threads re-gather the feature tile.
+// The barrier is a monotone counter with release/acquire at GPU scope and a
+// bounded spin; on expiry the kernel records a timeout, every CTA leaves the
+// step loop, frees TMEM and returns.  Stores that a later TMA load reads are
+// followed by a generic-to-async proxy fence.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+
+#include "ctx.cuh"
+#include "sim_device.cuh"
+#include "tc_ptx.cuh"
+
+namespace simnet {
+
+struct PLayer {
+    CUtensorMap tA, tB;
+    const float *bias, *scale, *oscale;
+    void *out;           // activations [M][N], or FC2 partials [2*N/BN][B] float2
+    int m_mult, K, N, BN, out_part, n_tiles_n;
+};
+
+struct PArgs {
+    PLayer layer[kMaxConv + 1];
+    const StepArgs *A;
+    void *X;
+    const float2 *part;
+    const float *w2, *b2;
+    unsigned *bar_counter;        // zero at launch
+    int *abort_g;                 // zero at launch
+    int32_t *status;
+    unsigned long long *phase_ns; // [SIMNET_KERNEL_KINDS] summed phase times (CTA 0), or null
+    unsigned long long *phase_n;  // [SIMNET_KERNEL_KINDS] phase counts
+    unsigned long long *detail;   // [kMaxConv+1][4] CTA 0, ns after each GEMM phase starts: first data,
+                                  // last MMA commit, epilogue done, barrier passed (or null)
+    int64_t n_steps;
+    int64_t spin_ns;
+    int n_layers, B, P, compact_every, stages, stage_bytes, prm_floats;
+};
+
+namespace {
+using namespace tcx;
+
+constexpr int kThreads = 320, kWarps = 10, kEpiWarps = 8;
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier; false when the kernel is aborting (timeout here or elsewhere).
+__device__ bool grid_sync(const PArgs &a, unsigned &target, volatile int *cta_abort) {
+    asm volatile("fence.proxy.async;" ::: "memory");   // generic writes (global and shared) before async-proxy use
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (*cta_abort) atomicExch(a.abort_g, 1);   // a bounded wait in this CTA gave up: stop everyone
+        target += gridDim.x;
+        __threadfence();
+        atomicAdd(a.bar_counter, 1u);
+        const uint64_t t0 = gtimer();
+        while (ld_acquire(a.bar_counter) < target) {
+            if (*(volatile int *)a.abort_g) { *cta_abort = 1; break; }
+            if ((int64_t)(gtimer() - t0) > a.spin_ns) {
+                atomicExch(a.abort_g, 1);
+                atomicExch(a.status, kStatusTimeout);
+                *cta_abort = 1;
+                break;
+            }
+        }
+        if (*(volatile int *)a.abort_g) *cta_abort = 1;
+    }
+    __syncthreads();
+    return *cta_abort == 0;
+}
+
+// All warps of the grid gather 32-row groups through their staging buffers
+// (the stage ring is free between GEMM phases).
+template <typename T>
+__device__ void gather_phase(const PArgs &a, uint8_t *ring) {
+    const int64_t total = (int64_t)a.B * a.A->window;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *stg = ring + warp * (32 * stage_row_bytes<T>());
+    for (int64_t row0 = ((int64_t)blockIdx.x * kWarps + warp) * 32; row0 < total;
+         row0 += (int64_t)gridDim.x * kWarps * 32)
+        gather_rows_warp<T>(a.A, reinterpret_cast<T *>(a.X), row0, total, stg, lane);
+}
+
+struct Pipe {  // pipeline counters that carry over between GEMM phases
+    int prod_it = 0, mma_it = 0, mma_tc = 0, epi_tc = 0;
+};
+
+template <bool FP8>
+__device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *bars, float *prm, uint8_t *staging,
+                           uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
+    const PLayer &L = a.layer[l];
+    constexpr int BK = FP8 ? 128 : 64;
+    const int S = a.stages, N = L.N, BN = L.BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s_bias = prm, *s_scale = prm + N, *s_oscale = prm + 2 * N, *s_w2 = prm + 3 * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        s_bias[i] = L.bias[i];
+        if (FP8) {
+            s_scale[i] = L.scale[i];
+            s_oscale[i] = L.oscale ? L.oscale[i] : 1.f;
+        }
+        if (L.out_part) {
+            s_w2[i] = a.w2[i];
+            s_w2[N + i] = a.w2[N + i];
+        }
+    }
+    __syncthreads();
+    const uint32_t smem_base = smem_u32(smem);
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[S + s]); };
+    auto tfull = [&](int x) { return smem_u32(&bars[2 * S + x]); };
+    auto tempty = [&](int x) { return smem_u32(&bars[2 * S + 2 + x]); };
+    const int M = min(*a.A->n_active * L.m_mult, a.B * L.m_mult);
+    const int n_tiles = ((M + BM - 1) / BM) * L.n_tiles_n;
+    const int KB = L.K / BK;
+    const int64_t lim = a.spin_ns;
+    const uint32_t stage_tx = (uint32_t)(A_BYTES + BN * ROW_BYTES);
+    const bool det = a.detail && blockIdx.x == 0;
+    const uint64_t t_phase = det ? gtimer() : 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                const int m0 = (t / L.n_tiles_n) * BM, n0 = (t % L.n_tiles_n) * BN;
+                for (int kb = 0; kb < KB; kb++, pp.prod_it++) {
+                    const int s = pp.prod_it % S;
+                    const uint32_t ph = (uint32_t)(pp.prod_it / S) & 1u;
+                    if (!mbar_wait(empty(s), ph ^ 1u, lim, cta_abort, a.status)) { ok = false; break; }
+                    const uint32_t sa = smem_base + s * a.stage_bytes;
+                    mbar_expect_tx(full(s), stage_tx);
+                    tma_load_2d(sa, &L.tA, full(s), kb * BK, m0);
+                    tma_load_2d(sa + A_BYTES, &L.tB, full(s), kb * BK, n0);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t ID = idesc_rt(BN, FP8);
+            bool ok = true;
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, pp.mma_tc++) {
+                const int acc = pp.mma_tc & 1;
+                const uint32_t aph = (uint32_t)(pp.mma_tc >> 1) & 1u;
+                if (!mbar_wait(tempty(acc), aph ^ 1u, lim, cta_abort, a.status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * 256);
+                for (int kb = 0; kb < KB; kb++, pp.mma_it++) {
+                    const int s = pp.mma_it % S;
+                    const uint32_t ph = (uint32_t)(pp.mma_it / S) & 1u;
+                    if (!mbar_wait(full(s), ph, lim, cta_abort, a.status)) { ok = false; break; }
+                    tc_fence_after();
+                    if (det && t == (int)blockIdx.x && kb == 0) atomicAdd(&a.detail[4 * l + 0], gtimer() - t_phase);
+                    const uint32_t sa = smem_base + s * a.stage_bytes;
+                    const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        umma<FP8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (kb | k) != 0 ? 1u : 0u);
+                    umma_commit(empty(s));
+                }
+                if (ok) umma_commit(tfull(acc));
+            }
+            if (det) atomicAdd(&a.detail[4 * l + 1], gtimer() - t_phase);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        const int CPW = BN / 64;
+        constexpr int OES = FP8 ? 1 : 2;
+        constexpr int CB = 32 * OES, SROW = CB + 16;
+        uint8_t *stg = staging + (warp - 2) * 32 * SROW;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, pp.epi_tc++) {
+            const int mt = t / L.n_tiles_n, nt = t % L.n_tiles_n;
+            const int m0 = mt * BM, n0 = nt * BN;
+            const int acc = pp.epi_tc & 1;
+            const uint32_t aph = (uint32_t)(pp.epi_tc >> 1) & 1u;
+            if (!mbar_wait(tfull(acc), aph, lim, cta_abort, a.status)) break;
+            tc_fence_after();
+            const int row = m0 + q * 32 + lane;
+            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256 + half * (BN / 2));
+            float pf = 0.f, pe = 0.f;
+            for (int c = 0; c < CPW; c++) {
+                uint32_t r[32];
+                tmem_ld32(tbase + (uint32_t)(c * 32), r);
+                const int col0 = n0 + half * (BN / 2) + c * 32;
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    float x = __uint_as_float(r[j]);
+                    if (FP8) x *= s_scale[col0 + j];
+                    x = fmaxf(x + s_bias[col0 + j], 0.f);
+                    if (FP8 && !L.out_part) x *= s_oscale[col0 + j];
+                    v[j] = x;
+                }
+                if (L.out_part) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        pf = fmaf(v[j], s_w2[col0 + j], pf);
+                        pe = fmaf(v[j], s_w2[N + col0 + j], pe);
+                    }
+                } else {
+                    uint4 *dst = reinterpret_cast<uint4 *>(stg + lane * SROW);
+                    if constexpr (FP8) {
+#pragma unroll
+                        for (int j = 0; j < 2; j++) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                const int o = 16 * j + 4 * h;
+                                const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[o], v[o + 1]), __NV_SATFINITE, __NV_E4M3);
+                                const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[o + 2], v[o + 3]), __NV_SATFINITE, __NV_E4M3);
+                                w[h] = (lo & 0xffffu) | (hi << 16);
+                            }
+                            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; j++) {
+                            uint32_t w[4];
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * j + 2 * h], v[8 * j + 2 * h + 1]);
+                                w[h] = *reinterpret_cast<uint32_t *>(&b2);
+                            }
+                            dst[j] = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
+                    __syncwarp();
+                    constexpr int U = CB / 16, RPP = 32 / U;
+                    const int rr = lane / U, u = lane % U;
+                    uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) + (size_t)col0 * OES + u * 16;
+#pragma unroll
+                    for (int pass = 0; pass < U; pass++) {
+                        const int r_in = pass * RPP + rr;
+                        const int grow = m0 + q * 32 + r_in;
+                        const uint4 val = *reinterpret_cast<const uint4 *>(stg + r_in * SROW + u * 16);
+                        if (grow < M) *reinterpret_cast<uint4 *>(gbase + (size_t)grow * N * OES) = val;
+                    }
+                    __syncwarp();
+                }
+            }
+            if (L.out_part && row < M)
+                reinterpret_cast<float2 *>(L.out)[(size_t)(2 * nt + half) * a.B + row] = make_float2(pf, pe);
+            tc_fence_before();
+            mbar_arrive(tempty(acc));
+        }
+        if (det && warp == 2 && lane == 0) atomicAdd(&a.detail[4 * l + 2], gtimer() - t_phase);
+    }
+    return t_phase;
+}
+
+template <bool FP8>
+__global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_constant__ PArgs a) {
+    using T = typename std::conditional<FP8, __nv_fp8_e4m3, __nv_bfloat16>::type;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int S = a.stages;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * a.stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 4);
+    volatile int *cta_abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    float *prm = reinterpret_cast<float *>(smem + S * a.stage_bytes + (2 * S + 4) * 8 + 16);
+    uint8_t *staging = reinterpret_cast<uint8_t *>(prm + a.prm_floats);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[S + s]), 1);
+        }
+        for (int x = 0; x < 2; x++) {
+            mbar_init(smem_u32(&bars[2 * S + x]), 1);
+            mbar_init(smem_u32(&bars[2 * S + 2 + x]), 32 * kEpiWarps);
+        }
+        *cta_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    unsigned target = 0;
+    Pipe pp;
+    uint64_t t_prev = gtimer();
+    auto mark = [&](int kind) {  // CTA 0 attributes the time since the last barrier to `kind`
+        if (blockIdx.x == 0 && threadIdx.x == 0 && a.phase_ns) {
+            const uint64_t t = gtimer();
+            a.phase_ns[kind] += t - t_prev;
+            a.phase_n[kind] += 1;
+            t_prev = t;
+        }
+    };
+    gather_phase<T>(a, smem);
+    bool ok = grid_sync(a, target, cta_abort);
+    mark(SIMNET_KERNEL_GATHER);
+    for (int64_t step = 0; step < a.n_steps && ok; step++) {
+        for (int l = 0; l < a.n_layers && ok; l++) {
+            const uint64_t tp = gemm_phase<FP8>(a, l, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+            ok = grid_sync(a, target, cta_abort);
+            if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
+            mark(SIMNET_KERNEL_LAYER0 + l);
+        }
+        if (!ok) break;
+        {   // head phase: every warp of the grid takes slots; the stage ring is its scratch
+            constexpr int PER = 256 * 8 + 32 * stage_row_bytes<T>();
+            uint8_t *mine = smem + warp * PER;
+            const int n_act = *a.A->n_active;
+            for (int slot = blockIdx.x * kWarps + warp; slot < n_act; slot += gridDim.x * kWarps)
+                head_update_warp<T>(a.A, slot, lane, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
+                                    reinterpret_cast<uint64_t *>(mine), mine + 256 * 8);
+        }
+        ok = grid_sync(a, target, cta_abort);
+        mark(SIMNET_KERNEL_HEAD_UPDATE);
+        if (ok && a.compact_every > 0 && (step + 1) % a.compact_every == 0 && step + 1 < a.n_steps) {
+            if (blockIdx.x == 0) compact_block(a.A);
+            ok = grid_sync(a, target, cta_abort);
+            mark(SIMNET_KERNEL_COMPACT);
+            if (!ok) break;
+            gather_phase<T>(a, smem);
+            ok = grid_sync(a, target, cta_abort);
+            mark(SIMNET_KERNEL_GATHER);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
+    }
+}
+
+}  // namespace
+
+// Host side: fill the argument block from the layer plans and launch.
+bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaStream_t s, std::string &why) {
+    PArgs a;
+    memset(&a, 0, sizeof a);
+    const bool fp8 = c->cfg.precision == SIMNET_FP8_E4M3;
+    int bn_max = 64, n_max = 0;
+    for (int l = 0; l < c->n_layers; l++) {
+        const TcPlan &p = c->plan[l];
+        const GemmLayer &g = c->layer[l];
+        PLayer &L = a.layer[l];
+        L.tA = p.tA;
+        L.tB = p.tB;
+        L.bias = g.bias;
+        L.scale = g.scale;
+        L.oscale = g.oscale;
+        L.out = p.out;
+        L.m_mult = g.m_mult;
+        L.K = g.K;
+        L.N = g.N;
+        L.BN = p.BN;
+        L.out_part = l == c->n_layers - 1;
+        L.n_tiles_n = g.N / p.BN;
+        bn_max = std::max(bn_max, p.BN);
+        n_max = std::max(n_max, g.N);
+    }
+    a.A = c->d_args;
+    a.X = c->X;
+    a.part = (const float2 *)c->h1;
+    a.w2 = c->w2;
+    a.b2 = c->b2;
+    a.bar_counter = c->bar;
+    a.abort_g = c->bar_abort;
+    a.status = c->status;
+    a.phase_ns = c->phase_on ? c->phase_ns : nullptr;
+    a.phase_n = c->phase_on ? c->phase_n : nullptr;
+    a.detail = c->phase_on ? c->phase_ns + 16 : nullptr;
+    a.n_steps = n_steps;
+    a.spin_ns = c->cfg.spin_limit_ns;
+    a.n_layers = c->n_layers;
+    a.B = B;
+    a.P = c->n_part;
+    a.compact_every = uneven ? 16 : 0;
+    a.stage_bytes = A_BYTES + bn_max * ROW_BYTES;
+    a.prm_floats = 5 * n_max;
+    const size_t staging = (size_t)kEpiWarps * 32 * (32 * (fp8 ? 1 : 2) + 16);
+    const size_t fixed = 1024 + 256 + (size_t)a.prm_floats * 4 + staging;
+    const size_t budget = 232448 - 1024;   // minus the static shared memory of the compaction
+    a.stages = (int)std::min<size_t>(6, (budget - fixed) / a.stage_bytes);
+    if (a.stages < 2) { why = "shared memory budget"; return false; }
+    // the head phase reuses the stage ring as 10 x 256 queue entries
+    if ((size_t)a.stages * a.stage_bytes < (size_t)kWarps * (256 * 8 + 32 * (kNFP * 4 + 16))) {
+        why = "ring too small for the head and gather scratch";
+        return false;
+    }
+    const size_t smem = (size_t)a.stages * a.stage_bytes + fixed;
+    auto k = fp8 ? persist_kernel<true> : persist_kernel<false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
+    if (per_sm < 1) { why = "persistent kernel does not fit on an SM"; return false; }
+    cudaMemsetAsync(c->bar, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(c->bar_abort, 0, sizeof(int), s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(num_sms());
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
+    return true;
+}
+
+}  // namespace simnet

@@ -1,0 +1,423 @@
+// sim_device.cuh -- device-side pieces of a simulation step shared by the
+// per-step kernels and the persistent kernel: context gather (Sec. 2.2), the
+// latency head and processor-queue / curTick update (Sec. 3.2), the drain of
+// Eq. 1 (Sec. 3.1) and active-set compaction (Sec. 3.3).
+#pragma once
+#include "common.cuh"
+
+namespace simnet {
+
+// ------------------------------------------------------------------ vector stores per precision
+template <typename T> struct Vec;
+template <> struct Vec<float> { static constexpr int N = 4; };
+template <> struct Vec<__nv_bfloat16> { static constexpr int N = 8; };
+template <> struct Vec<__nv_fp8_e4m3> { static constexpr int N = 16; };
+
+template <typename T> __device__ __forceinline__ void store16(T *dst, const float *v);
+
+template <> __device__ __forceinline__ void store16<float>(float *dst, const float *v) {
+    *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <> __device__ __forceinline__ void store16<__nv_bfloat16>(__nv_bfloat16 *dst, const float *v) {
+    uint4 u;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+    u.x = *reinterpret_cast<uint32_t *>(&p0);
+    u.y = *reinterpret_cast<uint32_t *>(&p1);
+    u.z = *reinterpret_cast<uint32_t *>(&p2);
+    u.w = *reinterpret_cast<uint32_t *>(&p3);
+    *reinterpret_cast<uint4 *>(dst) = u;
+}
+template <> __device__ __forceinline__ void store16<__nv_fp8_e4m3>(__nv_fp8_e4m3 *dst, const float *v) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * q], v[4 * q + 1]), __NV_SATFINITE, __NV_E4M3);
+        uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * q + 2], v[4 * q + 3]), __NV_SATFINITE, __NV_E4M3);
+        w[q] = (lo & 0xffffu) | (hi << 16);
+    }
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// ------------------------------------------------------------------ whole-row feature writer
+// Channels 32..63 of a row (the part after the opcode one-hot), as floats.
+__device__ __forceinline__ void row_tail(uint32_t rec, uint32_t cur, bool ctx, int32_t res, uint32_t e,
+                                         float (&t)[32]) {
+#pragma unroll
+    for (int j = 0; j < 32; j++) t[j] = 0.f;
+    const uint32_t dst = (rec >> 15) & 31u, lvl = (rec >> 23) & 3u;
+    t[0] = (float)((rec >> 5) & 31u) * 0.03125f;
+    t[1] = (float)((rec >> 10) & 31u) * 0.03125f;
+    t[2] = (float)dst * 0.03125f;
+    t[3] = (float)((rec >> 20) & 1u);
+    t[4] = (float)((rec >> 21) & 1u);
+    t[5] = (float)((rec >> 22) & 1u);
+    t[6] = lvl == 0u ? 1.f : 0.f;
+    t[7] = lvl == 1u ? 1.f : 0.f;
+    t[8] = lvl == 2u ? 1.f : 0.f;
+    t[9] = (float)((rec >> 25) & 1u);
+    if (ctx) {
+        t[10] = (float)min(res, 4095) * 0.015625f;
+        t[11] = (float)e * 0.015625f;
+        t[13] = dst == ((cur >> 5) & 31u) ? 1.f : 0.f;
+        t[14] = dst == ((cur >> 10) & 31u) ? 1.f : 0.f;
+        t[15] = dst == ((cur >> 15) & 31u) ? 1.f : 0.f;
+        const bool m0 = (rec >> 20) & 3u, m1 = (cur >> 20) & 3u;
+        t[16] = (m0 && m1 && lvl == ((cur >> 23) & 3u)) ? 1.f : 0.f;
+    }
+}
+
+// Write one whole 64-channel row (same values as `feature` channel by channel).
+template <typename T> __device__ __forceinline__ void write_row(T *dst, uint32_t rec, uint32_t cur, bool ctx,
+                                                               int32_t res, uint32_t e);
+
+template <> __device__ __forceinline__ void write_row<__nv_bfloat16>(__nv_bfloat16 *dst, uint32_t rec, uint32_t cur,
+                                                                     bool ctx, int32_t res, uint32_t e) {
+    const uint32_t op = rec & 31u;
+    uint32_t w[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) w[i] = (op >> 1) == (uint32_t)i ? ((op & 1u) ? 0x3F800000u : 0x00003F80u) : 0u;
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; i++) d4[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    float t[32];
+    row_tail(rec, cur, ctx, res, e, t);
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        __nv_bfloat162 b = __floats2bfloat162_rn(t[2 * i], t[2 * i + 1]);
+        w[i] = *reinterpret_cast<uint32_t *>(&b);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) d4[4 + i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+}
+
+template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4m3 *dst, uint32_t rec, uint32_t cur,
+                                                                     bool ctx, int32_t res, uint32_t e) {
+    const uint32_t op = rec & 31u;
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) w[i] = (op >> 2) == (uint32_t)i ? (0x38u << (8 * (op & 3u))) : 0u;  // e4m3 1.0
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    float t[32];
+    row_tail(rec, cur, ctx, res, e, t);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(t[4 * i], t[4 * i + 1]), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(t[4 * i + 2], t[4 * i + 3]), __NV_SATFINITE, __NV_E4M3);
+        w[i] = (lo & 0xffffu) | (hi << 16);
+    }
+    d4[2] = make_uint4(w[0], w[1], w[2], w[3]);
+    d4[3] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+template <> __device__ __forceinline__ void write_row<float>(float *dst, uint32_t rec, uint32_t cur, bool ctx,
+                                                             int32_t res, uint32_t e) {
+    const uint32_t op = rec & 31u;
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) v[j] = op == (uint32_t)(4 * i + j) ? 1.f : 0.f;
+        d4[i] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    float t[32];
+    row_tail(rec, cur, ctx, res, e, t);
+#pragma unroll
+    for (int i = 0; i < 8; i++) d4[8 + i] = make_float4(t[4 * i], t[4 * i + 1], t[4 * i + 2], t[4 * i + 3]);
+}
+
+__device__ __forceinline__ void zero_row_bytes(void *dst, int bytes) {
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int i = 0; i < bytes / 16; i++) d4[i] = make_uint4(0, 0, 0, 0);
+}
+
+// ------------------------------------------------------------------ head + queue update (Sec. 3.2)
+__device__ __forceinline__ float softplus_f(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+
+// clamp to [0, 255], round half to even; NaN -> 255
+__device__ __forceinline__ uint32_t to_cycles(float y) {
+    if (isnan(y)) return 255u;
+    y = fminf(fmaxf(y, 0.f), 255.f);
+    return (uint32_t)__float2int_rn(y);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Length of the run of ready entries from the oldest, at most `lim`; in-order
+// retire means the first not-ready entry stops it.  Whole warp participates.
+__device__ __forceinline__ int retire_run(const uint64_t *__restrict__ ring, int cap, int qs, int lim,
+                                          int32_t tick, int strict, int lane) {
+    int k = 0;
+    while (k < lim) {
+        const int i = k + lane;
+        bool rd = false;
+        if (i < lim) {
+            int idx = qs + i;
+            if (idx >= cap) idx -= cap;
+            const uint64_t v = ring[idx];
+            const int32_t res = tick - (int32_t)entry_tick(v);
+            const int32_t e = (int32_t)entry_e(v);
+            rd = strict ? (res > e) : (res >= e);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, rd);
+        const int run = (m == 0xffffffffu) ? 32 : (__ffs(~m) - 1);
+        k += run;
+        if (run < 32) break;
+    }
+    return min(k, lim);
+}
+
+// One element of the context gather: thread `gid` of (slot, row, 16-byte chunk).
+// Row 0 = current instruction, row j = j-th newest queue entry, rows past the
+// queue length are zero, and an inactive slot (sub-trace finished) gets zero rows.
+template <typename T>
+__device__ __forceinline__ void gather_elem(const StepArgs *__restrict__ A, T *__restrict__ X, int64_t gid) {
+    constexpr int V = Vec<T>::N, CH = kNFP / V;
+    const int W = A->window;
+    const int chunk = (int)(gid % CH);
+    const int64_t rowid = gid / CH;
+    const int r = (int)(rowid % W);
+    const int slot = (int)(rowid / W);
+    float v[V];
+#pragma unroll
+    for (int j = 0; j < V; j++) v[j] = 0.f;
+    if (slot < *A->n_active) {
+        const int b = A->active[slot];
+        const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
+        const int p = A->pos[b];
+        if (p < n) {
+            const uint32_t cur = A->records[o + p];
+            if (r == 0) {
+#pragma unroll
+                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, cur, cur, false, 0, 0);
+            } else if (r <= A->qlen[b]) {
+                const int cap = A->cap;
+                int idx = A->qstart[b] + A->qlen[b] - r;
+                if (idx >= cap) idx -= cap;
+                const uint64_t ent = A->ring[(size_t)b * cap + idx];
+                const int32_t res = A->tick[b] - (int32_t)entry_tick(ent);
+                const uint32_t rec = entry_rec(ent), e = entry_e(ent);
+#pragma unroll
+                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, rec, cur, true, res, e);
+            }
+        }
+    }
+    store16<T>(X + rowid * kNFP + chunk * V, v);
+}
+
+// Bytes of one staged row: a 64-channel row plus 16 bytes of padding, so that
+// lanes writing whole rows to shared memory do not collide on banks.
+template <typename T> __host__ __device__ constexpr int stage_row_bytes() { return kNFP * (int)sizeof(T) + 16; }
+
+// Copy n (<= 32) staged rows to X rows row0.. with every store instruction
+// covering whole contiguous rows (U lanes per row).
+template <typename T>
+__device__ __forceinline__ void flush_rows(const uint8_t *__restrict__ stg, T *__restrict__ X, int64_t row0, int n,
+                                           int lane) {
+    constexpr int RB = kNFP * (int)sizeof(T), SR = stage_row_bytes<T>(), U = RB / 16, RPP = 32 / U;
+    const int rr = lane / U, u = lane % U;
+    uint8_t *g = reinterpret_cast<uint8_t *>(X) + row0 * RB + u * 16;
+#pragma unroll 4
+    for (int pass = 0; pass < U; pass++) {
+        const int r = pass * RPP + rr;
+        if (r < n) *reinterpret_cast<uint4 *>(g + (int64_t)r * RB) = *reinterpret_cast<const uint4 *>(stg + r * SR + u * 16);
+    }
+}
+
+// One row of the context gather, built into `dst` (row 0 = current instruction,
+// row j = j-th newest queue entry; rows past the queue length and rows of an
+// inactive slot are zero).
+template <typename T>
+__device__ __forceinline__ void gather_row_into(const StepArgs *__restrict__ A, int64_t rowid, T *dst) {
+    const int W = A->window;
+    const int r = (int)(rowid % W);
+    const int slot = (int)(rowid / W);
+    if (slot < *A->n_active) {
+        const int b = A->active[slot];
+        const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
+        const int p = A->pos[b];
+        if (p < n) {
+            const uint32_t cur = A->records[o + p];
+            if (r == 0) {
+                write_row<T>(dst, cur, cur, false, 0, 0);
+                return;
+            }
+            if (r <= A->qlen[b]) {
+                const int cap = A->cap;
+                int idx = A->qstart[b] + A->qlen[b] - r;
+                if (idx >= cap) idx -= cap;
+                const uint64_t ent = A->ring[(size_t)b * cap + idx];
+                write_row<T>(dst, entry_rec(ent), cur, true, A->tick[b] - (int32_t)entry_tick(ent), entry_e(ent));
+                return;
+            }
+        }
+    }
+    zero_row_bytes(dst, kNFP * (int)sizeof(T));
+}
+
+// A warp gathers rows row0 .. row0+31 (< total) through its staging buffer.
+template <typename T>
+__device__ __forceinline__ void gather_rows_warp(const StepArgs *__restrict__ A, T *__restrict__ X, int64_t row0,
+                                                 int64_t total, uint8_t *__restrict__ stg, int lane) {
+    const int n = (int)min((int64_t)32, total - row0);
+    if (lane < n) gather_row_into<T>(A, row0 + lane, reinterpret_cast<T *>(stg + lane * stage_row_bytes<T>()));
+    __syncwarp();
+    flush_rows<T>(stg, X, row0, n, lane);
+    __syncwarp();
+}
+
+// One warp, one active slot.  FC2 arrives as P partial dot products (one per
+// FC1 column block) which are summed with the bias; softplus, clamp, round;
+// then curTick += F, retire (budget RW*F), evict at capacity, append with
+// residence 0; after the last instruction, drain one cycle at a time (budget
+// RW) and write the sub-trace's cycle count.  Otherwise the warp writes the
+// slot's feature rows for the next step (the gather, fused here); `sq` is this
+// warp's shared-memory scratch of 256 queue entries.
+template <typename T>
+__device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A, int slot, int lane,
+                                                 const float2 *__restrict__ part, int P, int part_stride,
+                                                 const float *__restrict__ b2, T *__restrict__ X,
+                                                 uint64_t *__restrict__ sq, uint8_t *__restrict__ stg) {
+    const int b = A->active[slot];
+    const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
+    int p = A->pos[b];
+    if (p >= n) return;
+    float zf = 0.f, ze = 0.f;
+    for (int i = lane; i < P; i += 32) {
+        const float2 v = part[(size_t)i * part_stride + slot];
+        zf += v.x;
+        ze += v.y;
+    }
+    zf = warp_sum(zf) + b2[0];
+    ze = warp_sum(ze) + b2[1];
+    const float yf = softplus_f(zf), ye = softplus_f(ze);
+    const int64_t gi = o + p;
+    uint32_t F, E;
+    if (A->replay) {
+        F = A->replay[2 * gi];
+        E = A->replay[2 * gi + 1];
+    } else {
+        F = to_cycles(yf);
+        E = to_cycles(ye);
+    }
+    if (lane == 0) {
+        if (A->pre_log) { A->pre_log[2 * gi] = yf; A->pre_log[2 * gi + 1] = ye; }
+        if (A->lat_log) { A->lat_log[2 * gi] = (uint8_t)F; A->lat_log[2 * gi + 1] = (uint8_t)E; }
+    }
+    const int cap = A->cap, RW = A->retire_width, strict = A->strict;
+    uint64_t *ring = A->ring + (size_t)b * cap;
+    int qs = A->qstart[b], ql = A->qlen[b], ev = 0;
+    int32_t tick = A->tick[b] + (int32_t)F;
+    const int k = retire_run(ring, cap, qs, min(ql, RW * (int)F), tick, strict, lane);
+    qs += k;
+    if (qs >= cap) qs -= cap;
+    ql -= k;
+    if (ql == cap) {  // full: drop the oldest
+        qs = (qs + 1 == cap) ? 0 : qs + 1;
+        ql--;
+        ev = 1;
+    }
+    if (lane == 0) {
+        int idx = qs + ql;
+        if (idx >= cap) idx -= cap;
+        ring[idx] = pack_entry(A->records[gi], E, (uint32_t)tick);
+    }
+    ql++;
+    p++;
+    __syncwarp();
+    if (p == n) {  // drain: Delta of Eq. 1
+        while (ql > 0) {
+            tick += 1;
+            const int kk = retire_run(ring, cap, qs, min(ql, RW), tick, strict, lane);
+            qs += kk;
+            if (qs >= cap) qs -= cap;
+            ql -= kk;
+        }
+        if (lane == 0) A->cycles_out[b] = tick;
+    } else if (X) {
+        // next step's input rows of this slot: row 0 = instruction p, row r = r-th newest entry.
+        // The queue is copied newest-first into shared memory with independent loads first.
+        for (int r = lane + 1; r <= ql; r += 32) {
+            int idx = qs + ql - r;
+            if (idx >= cap) idx -= cap;
+            sq[r] = ring[idx];
+        }
+        __syncwarp();
+        const int W = A->window;
+        const uint32_t cur = A->records[o + p];
+        constexpr int SR = stage_row_bytes<T>();
+        for (int r0 = 0; r0 < W; r0 += 32) {   // a lane builds a row, the warp stores rows whole
+            const int r = r0 + lane;
+            T *row = reinterpret_cast<T *>(stg + lane * SR);
+            if (r < W) {
+                if (r == 0) {
+                    write_row<T>(row, cur, cur, false, 0, 0);
+                } else if (r <= ql) {
+                    const uint64_t ent = sq[r];
+                    write_row<T>(row, entry_rec(ent), cur, true, tick - (int32_t)entry_tick(ent), entry_e(ent));
+                } else {
+                    zero_row_bytes(row, kNFP * (int)sizeof(T));
+                }
+            }
+            __syncwarp();
+            flush_rows<T>(stg, X, (int64_t)slot * W + r0, min(32, W - r0), lane);
+            __syncwarp();
+        }
+    }
+    if (lane == 0) {
+        A->tick[b] = tick;
+        A->pos[b] = p;
+        A->qstart[b] = qs;
+        A->qlen[b] = ql;
+        A->evict[b] += ev;
+    }
+}
+
+// Stable in-place compaction of the active list, one block (any size that is a
+// multiple of 32, at most 1024): drop finished sub-traces so the batch stays dense.
+__device__ __forceinline__ void compact_block(const StepArgs *__restrict__ A) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int n = *A->n_active;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        int b = -1;
+        bool keep = false;
+        if (i < n) {
+            b = A->active[i];
+            keep = A->pos[b] < (int)(A->offsets[b + 1] - A->offsets[b]);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        const int pre = __popc(m & ((1u << lane) - 1u));
+        if (lane == 0) wsum[w] = __popc(m);
+        __syncthreads();
+        if (w == 0) {
+            int v = lane < nw ? wsum[lane] : 0, x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane < nw) wsum[lane] = x - v;  // exclusive prefix over warps
+        }
+        __syncthreads();
+        const int dst = base + wsum[w] + pre;
+        if (keep) A->active[dst] = b;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) base = dst + (keep ? 1 : 0);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *A->n_active = base;
+}
+
+}  // namespace simnet

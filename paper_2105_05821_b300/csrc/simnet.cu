@@ -139,6 +139,10 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    if (c->bar) cudaFree(c->bar);
+    if (c->bar_abort) cudaFree(c->bar_abort);
+    if (c->phase_ns) cudaFree(c->phase_ns);
+    if (c->phase_n) cudaFree(c->phase_n);
     delete c;
 }
 
@@ -368,6 +372,12 @@ static simnet_status ensure_workspace(simnet_ctx *c, int B) {
     CK(cudaMalloc(&c->ring, (size_t)B * c->cap * sizeof(uint64_t)));
     CK(cudaMalloc(&c->totals, 2 * sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_args, sizeof(StepArgs)));
+    if (!c->bar) {
+        CK(cudaMalloc(&c->bar, sizeof(unsigned)));
+        CK(cudaMalloc(&c->bar_abort, sizeof(int)));
+        CK(cudaMalloc(&c->phase_ns, 64 * sizeof(unsigned long long)));
+        CK(cudaMalloc(&c->phase_n, SIMNET_KERNEL_KINDS * sizeof(unsigned long long)));
+    }
     if (!c->h_args) {
         CK(cudaMallocHost(&c->h_args, sizeof(StepArgs)));
         CK(cudaMallocHost(&c->h_totals, 2 * sizeof(unsigned long long)));
@@ -467,6 +477,9 @@ static simnet_status prepare_plans(simnet_ctx *c, int B, bool pdl) {
         if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, last ? TC_OUT_PART : TC_OUT_ACT, B * g.m_mult,
                           c->cfg.spin_limit_ns, c->status, pdl, why))
             return fail(c, SIMNET_ECUDA, "tensor-core plan for layer %d: %s", l, why.c_str());
+        if (c->tuned_B == B && c->tuned_bn[l] && c->tuned_bn[l] != c->plan[l].BN &&
+            !retune_tc_plan(c->plan[l], g, c->tuned_bn[l], why))
+            return fail(c, SIMNET_ECUDA, "tuned tile for layer %d: %s", l, why.c_str());
     }
     c->n_part = 2 * (fc1.N / c->plan[c->n_layers - 1].BN);   // two column halves per block
     return SIMNET_OK;
@@ -571,6 +584,21 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
         c->ev_used = 0;
         c->kt_valid = false;
     }
+    c->phase_valid = false;
+    const bool persistent = c->cfg.precision != SIMNET_FP32 && (c->cfg.flags & SIMNET_FLAG_PERSISTENT);
+    if (persistent) {
+        // one cooperative kernel runs every step; its phases are timed by CTA 0 on request
+        c->phase_on = timed;
+        if (timed) {
+            CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(c->phase_n, 0, SIMNET_KERNEL_KINDS * sizeof(unsigned long long), s));
+        }
+        std::string why;
+        if (!launch_persistent(c, B, max_len, uneven, s, why))
+            return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
+        launches = 2;
+        c->phase_valid = timed;
+    } else {
     enqueue_gather(c, B, s, false, timed ? &kt : nullptr);
     if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
         for (int64_t i = 0; i < max_len; i++) {
@@ -589,6 +617,7 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
         for (int64_t i = 0; i < full; i++) CK(cudaGraphLaunch(c->gexec[0], s));
         for (int64_t i = 0; i < rest; i++) CK(cudaGraphLaunch(c->gexec[1], s));
         if (uneven) launches += 2 * (full + rest);
+    }
     }
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev1, s));
@@ -641,6 +670,14 @@ extern "C" simnet_status simnet_kernel_times(simnet_ctx *c, float *ms_out, int64
     if (!c) return SIMNET_EINVAL;
     if (!ms_out || !launches_out || n_kinds < 1 || n_kinds > SIMNET_KERNEL_KINDS)
         return fail(c, SIMNET_EINVAL, "kernel_times: bad arguments");
+    if (c->phase_valid) {  // persistent kernel: per-phase times measured by CTA 0 (globaltimer)
+        unsigned long long ns[SIMNET_KERNEL_KINDS], cnt[SIMNET_KERNEL_KINDS];
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpy(ns, c->phase_ns, sizeof ns, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(cnt, c->phase_n, sizeof cnt, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < n_kinds; k++) { ms_out[k] = (float)(ns[k] * 1e-6); launches_out[k] = (int64_t)cnt[k]; }
+        return SIMNET_OK;
+    }
     if (!c->kt_valid) return fail(c, SIMNET_ESTATE, "kernel_times: no timed simulate call");
     CK(cudaDeviceSynchronize());
     for (int k = 0; k < n_kinds; k++) { ms_out[k] = 0.f; launches_out[k] = 0; }
@@ -650,5 +687,82 @@ extern "C" simnet_status simnet_kernel_times(simnet_ctx *c, float *ms_out, int64
         CK(cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]));
         if (k < n_kinds) { ms_out[k] += ms; launches_out[k]++; }
     }
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_phase_detail(simnet_ctx *c, uint64_t *out, int32_t n) {
+    if (!c) return SIMNET_EINVAL;
+    if (!out || n < 1 || n > 48) return fail(c, SIMNET_EINVAL, "phase_detail: bad arguments");
+    if (!c->phase_valid) return fail(c, SIMNET_ESTATE, "phase_detail: no timed persistent run");
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(out, c->phase_ns + 16, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return SIMNET_OK;
+}
+
+// Autotuner: for a batch of n_sub sub-traces, try every tile width of every
+// tensor-core layer (coordinate descent, layer by layer) on a short synthetic
+// trace and keep the fastest whole-call device time.
+extern "C" simnet_status simnet_autotune(simnet_ctx *c, int32_t n_sub, int32_t steps, int32_t *bn_out,
+                                         void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (n_sub < 1 || steps < 1 || steps > 4096) return fail(c, SIMNET_EINVAL, "autotune: bad arguments");
+    if (!c->has_weights) return fail(c, SIMNET_ESTATE, "autotune: no weights loaded");
+    if (c->cfg.precision == SIMNET_FP32) return SIMNET_OK;   // the FP32 form has no tile choice
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // synthetic records (xorshift), equal sub-traces of `steps` instructions
+    const int64_t N = (int64_t)n_sub * steps;
+    std::vector<uint32_t> rec(N);
+    uint64_t st = 0x2545F4914F6CDD1Dull;
+    for (int64_t i = 0; i < N; i++) {
+        st ^= st << 13;
+        st ^= st >> 7;
+        st ^= st << 17;
+        rec[i] = (uint32_t)(st & 0x3ffffffu) & ~(3u << 23) | ((uint32_t)((st >> 40) % 3) << 23);
+    }
+    std::vector<int64_t> off(n_sub + 1);
+    for (int b = 0; b <= n_sub; b++) off[b] = (int64_t)b * steps;
+    uint32_t *d_rec = nullptr;
+    int64_t *d_off = nullptr, *d_cyc = nullptr;
+    auto cleanup = [&]() { cudaFree(d_rec); cudaFree(d_off); cudaFree(d_cyc); };
+    if (cudaMalloc(&d_rec, N * 4) != cudaSuccess || cudaMalloc(&d_off, (n_sub + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&d_cyc, (size_t)n_sub * 8) != cudaSuccess) {
+        cleanup();
+        return fail(c, SIMNET_ENOMEM, "autotune: allocation failed");
+    }
+    cudaMemcpy(d_rec, rec.data(), N * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(d_off, off.data(), (n_sub + 1) * 8, cudaMemcpyHostToDevice);
+    simnet_trace tr{d_rec, d_off, n_sub, 0, N};
+    auto run = [&](float &ms) -> simnet_status {
+        simnet_stats sts;
+        simnet_status r = simnet_simulate(c, &tr, d_cyc, nullptr, nullptr, nullptr, &sts, s);
+        if (r != SIMNET_OK) return r;
+        r = simnet_simulate(c, &tr, d_cyc, nullptr, nullptr, nullptr, &sts, s);
+        ms = sts.ms_total;
+        return r;
+    };
+    // start from the heuristic plans
+    c->tuned_B = -1;
+    simnet_status r = prepare_plans(c, n_sub, c->pdl);
+    if (r != SIMNET_OK) { cleanup(); return r; }
+    int cur[kMaxConv + 1];
+    for (int l = 0; l < c->n_layers; l++) cur[l] = c->plan[l].BN;
+    c->tuned_B = n_sub;
+    for (int l = 0; l < c->n_layers; l++) c->tuned_bn[l] = cur[l];
+    float best = 1e30f;
+    if ((r = run(best)) != SIMNET_OK) { cleanup(); return r; }
+    for (int l = 0; l < c->n_layers; l++) {
+        for (int bn : {64, 128, 256}) {
+            if (bn == cur[l] || c->layer[l].N % bn) continue;
+            c->tuned_bn[l] = bn;
+            float ms = 0.f;
+            if ((r = run(ms)) != SIMNET_OK) { cleanup(); return r; }
+            if (ms < best) { best = ms; cur[l] = bn; }
+        }
+        c->tuned_bn[l] = cur[l];
+    }
+    cleanup();
+    if (bn_out)
+        for (int l = 0; l < c->n_layers; l++) bn_out[l] = cur[l];
     return SIMNET_OK;
 }

@@ -23,6 +23,7 @@ FLAG_RETIRE_STRICT = 0x1
 FLAG_NO_GRAPH = 0x2
 FLAG_KERNEL_EVENTS = 0x4
 FLAG_NO_PDL = 0x8
+FLAG_PERSISTENT = 0x10
 KERNEL_KINDS = 12
 KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE", 6: "EUNSUPPORTED"}
@@ -31,7 +32,7 @@ EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_e
            "simnet_weight_count", "simnet_load_weights", "simnet_simulate", "simnet_cnn_forward",
            "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes",
            "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
-           "simnet_set_weights_device", "simnet_get_weights"]
+           "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune"]
 
 
 class SimnetError(RuntimeError):
@@ -106,6 +107,10 @@ def lib() -> C.CDLL:
         L.simnet_set_weights_device.argtypes = [P, P, P]
         L.simnet_get_weights.restype = C.c_int
         L.simnet_get_weights.argtypes = [P, P]
+        L.simnet_autotune.restype = C.c_int
+        L.simnet_autotune.argtypes = [P, C.c_int32, C.c_int32, P, P]
+        L.simnet_phase_detail.restype = C.c_int
+        L.simnet_phase_detail.argtypes = [P, P, C.c_int32]
         _lib = L
     return _lib
 
@@ -136,11 +141,12 @@ class Simnet:
     def __init__(self, window: int, n_conv: int, channels: int, hidden: int,
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
-                 pdl: bool = True):
+                 pdl: bool = True, persistent: bool = False):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
-                 | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL))
+                 | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
+                 | (FLAG_PERSISTENT if persistent else 0))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, 0,
                             spin_limit_ns)
         self.window = window
@@ -197,6 +203,18 @@ class Simnet:
             return None
         return Stats(st.total_cycles, st.instructions, st.steps, st.evictions, st.kernel_launches,
                      st.ms_total)
+
+    def phase_detail(self, n_layers):
+        """Per GEMM layer: summed ns to first data, last MMA, epilogue done, barrier passed (CTA 0)."""
+        out = np.zeros(4 * n_layers, dtype=np.uint64)
+        self._check(lib().simnet_phase_detail(self._h, out.ctypes.data_as(C.c_void_p), 4 * n_layers))
+        return out.reshape(n_layers, 4)
+
+    def autotune(self, n_subtraces: int, steps: int = 24, stream=None):
+        """Pick per-layer tile widths for this batch size by timing; returns them."""
+        out = (C.c_int32 * 16)()
+        self._check(lib().simnet_autotune(self._h, n_subtraces, steps, out, _stream(stream)))
+        return list(out)
 
     def kernel_times(self):
         """(ms, launches) per kernel kind of the last simulate with kernel_events=True."""

@@ -91,16 +91,19 @@ def test_graph_and_direct_launch_identical():
     np.testing.assert_array_equal(ra["pre"], ra2["pre"])     # run-to-run bit identical
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_pdl_graph_direct_identical(precision):
-    """Programmatic dependent launch, CUDA graphs and plain launches must give
-    bit-identical logs on a workload with compaction (uneven lengths)."""
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_launch_modes_identical(precision):
+    """The persistent cooperative kernel, per-layer kernels with programmatic
+    dependent launch, CUDA graphs and plain launches must give bit-identical
+    logs on a workload with compaction (uneven lengths)."""
     arch = I.ARCH_SMALL(32)
     trace = I.small_trace([50, 300, 7, 160, 0, 90] * 4, seed=12)
     blob = I.workload_weights(I.Workload("p", arch, 1, 1, seed=12))
     runs = []
-    for graph, pdl in ((True, True), (True, False), (False, True), (False, False)):
-        sim, _ = make_sim(arch, precision, blob=blob, graph=graph, pdl=pdl)
+    modes = [(True, True, False), (True, False, False), (False, True, False), (False, False, False),
+             (True, True, True)]
+    for graph, pdl, persistent in modes:
+        sim, _ = make_sim(arch, precision, blob=blob, graph=graph, pdl=pdl, persistent=persistent)
         runs.append(run_gpu(sim, trace))
     for r in runs[1:]:
         np.testing.assert_array_equal(r["pre"], runs[0]["pre"])
