@@ -32,7 +32,11 @@ UNIT = "inst/s"
 FP32_FMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 flop x max SM clock
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
 # keyed by (workload, precision, kernel); from the capture summarised in profiles/.
-TRAFFIC = {}
+TRAFFIC = {
+    # persist_kernel, c2 BF16: 1.32 MB of DRAM traffic over 20 steps in the capture of
+    # profiles/persist_kernel_c2_bf16.md, scaled by steps to the 1,000-step launch
+    ("c2", "bf16", "persist_kernel"): 1.317e6 * 1000 / 20,
+}
 
 
 def peaks():
@@ -261,7 +265,7 @@ def run_ours(args, rank, world):
         return ms, wall
 
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          persistent=args.persistent)
+                          persistent=not args.layerwise)
     sim.load_weights(blob32)
     tiles = sim.autotune(B) if (args.precision != "fp32" and not args.no_autotune) else []
     st = sim.simulate(rec, off, cycles_out=cyc, stats=True)          # compile graphs, count launches
@@ -294,13 +298,29 @@ def run_ours(args, rank, world):
                    "d2h_bytes_per_step": int(8 * B)},
            "wall_s_timed": wall,
            "tile_widths": tiles[:w.arch.n_conv + 1],
-           "kernel_mode": "persistent" if args.persistent and args.precision != "fp32" else "per-layer kernels"}
+           "kernel_mode": "per-layer kernels" if args.layerwise or args.precision == "fp32" else "persistent"}
     out["config"]["instructions_per_step"] = N
     out["total_cycles"] = int(st.total_cycles)
     out["cpi"] = st.total_cycles / N
 
     if rank == 0 and not args.no_breakdown:
         out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B)
+        if out["kernel_mode"] == "persistent":
+            # one launch does every step: its roofline is the whole call's algorithmic
+            # work over its device time; the per-phase table above explains the split
+            hbm, bf16_burst, bf16_sus, src = peaks()
+            flops = 2.0 * w.arch.macs_per_inference() * N
+            scale = 2.0 if args.precision == "fp8" else 1.0
+            ach = flops / (ms_per_step / 1e3) / 1e12
+            peak = bf16_sus * scale
+            phase = out["roofline"]
+            out["roofline"] = {"kernel": "persist_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                               "unit": "TFLOP/s", "frac": ach / peak,
+                               "peak_source": f"{src} bf16 sustained" + (" x2 (fp8 nominal ratio)" if scale > 1 else ""),
+                               "traffic": TRAFFIC.get((w.name, args.precision, "persist_kernel")),
+                               "avg_launch_us": ms_per_step * 1e3, "algorithmic_per_launch": flops,
+                               "algorithmic_unit": "flop", "share_of_step": 1.0,
+                               "dominant_phase": phase}
     if rank == 0 and args.precision != "fp32" and not args.no_fp32:
         s32 = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
         s32.load_weights(blob32)
@@ -326,7 +346,7 @@ def roofline(w, args, blob32, rec, off, cyc, B):
     from paper_2105_05821_b300.simnet import Simnet
     hbm, bf16_burst, bf16_sus, src = peaks()
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          kernel_events=True, persistent=args.persistent)
+                          kernel_events=True, persistent=not args.layerwise)
     sim.load_weights(blob32)
     if args.precision != "fp32" and not args.no_autotune:
         sim.autotune(B)
@@ -376,8 +396,8 @@ def main():
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--persistent", action="store_true",
-                    help="BF16/FP8: one persistent cooperative kernel for the whole call")
+    ap.add_argument("--layerwise", action="store_true",
+                    help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
     ap.add_argument("--subtrace-len", type=int, default=0,
                     help="keep only the first N instructions of every sub-trace (profiling runs)")
     args = ap.parse_args()

@@ -71,9 +71,9 @@ typedef enum {
 #define SIMNET_FLAG_KERNEL_EVENTS 0x4u /* direct launches with a CUDA event pair around each kernel;
                                           per-kernel device times via simnet_kernel_times() */
 #define SIMNET_FLAG_NO_PDL 0x8u        /* no programmatic dependent launch between a step's kernels */
-#define SIMNET_FLAG_PERSISTENT 0x10u   /* BF16/FP8: run every step of a call in one persistent
-                                          cooperative kernel (phases separated by grid barriers)
-                                          instead of one kernel per layer and step */
+#define SIMNET_FLAG_LAYERWISE 0x10u    /* BF16/FP8: one kernel per layer and step (CUDA graphs,
+                                          PDL, dense padding rows) instead of the default single
+                                          persistent cooperative kernel that skips the padding */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -211,7 +211,7 @@ simnet_status simnet_cnn_forward(simnet_ctx *ctx, const float *x, float *z, int3
  * SIMNET_FLAG_KERNEL_EVENTS: for each kind k < n_kinds, ms_out[k] = summed
  * CUDA-event time of its launches (milliseconds) and launches_out[k] = their
  * number (host arrays of n_kinds entries, n_kinds <= SIMNET_KERNEL_KINDS).
- * For the persistent kernel (SIMNET_FLAG_PERSISTENT) the kinds
+ * For the persistent kernel (BF16/FP8 without SIMNET_FLAG_LAYERWISE) the kinds
  * are its phases, timed by CTA 0 from barrier to barrier (globaltimer), and
  * launches_out counts phases.
  * Synchronises the device.  Errors: EINVAL (bad arguments), ESTATE (no such

@@ -85,6 +85,12 @@ struct simnet_ctx {
     unsigned long long *phase_ns = nullptr, *phase_n = nullptr;
     bool phase_on = false, phase_valid = false;
 
+    // padding-extent path of the persistent kernel: FC1 contribution of the
+    // constant rows past the extent, S[e][n] for e = 0..rows_n ([rows_n+1][H]),
+    // and the batch extent per step parity
+    float *fc1_const = nullptr;
+    int *ext = nullptr;
+
     // autotuned tile widths: tuned_bn[l] applies to batches of tuned_B sub-traces
     int tuned_B = -1;
     int tuned_bn[kMaxConv + 1] = {};

@@ -13,6 +13,14 @@
 //     drain, and the feature rows of the next step (Sec. 3.2, Eq. 1);
 //   every `compact_every` steps (uneven lengths): CTA 0 compacts the active
 //     list, then all threads re-gather the feature tile.
+// Padding extent: rows past every queue are zero features, so each conv layer
+// maps them to one constant row (per layer) and FC1 sees that constant at every
+// padded position.  The kernel therefore computes, each step, only the row
+// positions below the batch extent e (the longest queue + 1, rounded up to a
+// whole conv-output row), and FC1's epilogue adds S[e], the precomputed FC1
+// contribution of the constant rows at positions >= e.  Activations are stored
+// pair-major ([row pair][slot][2C]) so that the two rows a k=2/stride-2
+// convolution combines are one contiguous K run of a 2D TMA box.
 // The barrier is a monotone counter with release/acquire at GPU scope and a
 // bounded spin; on expiry the kernel records a timeout, every CTA leaves the
 // step loop, frees TMEM and returns.  Stores that a later TMA load reads are
@@ -30,10 +38,12 @@
 namespace simnet {
 
 struct PLayer {
-    CUtensorMap tA, tB;
+    CUtensorMap tA, tB;  // A: pair-major input [pairs * B][2 * C_in]; B: weights [N][K]
     const float *bias, *scale, *oscale;
-    void *out;           // activations [M][N], or FC2 partials [2*N/BN][B] float2
-    int m_mult, K, N, BN, out_part, n_tiles_n;
+    void *out;           // pair-major activations [pairs * B][2N], or FC2 partials [2*N/BN][B] float2
+    int K, N, BN, out_part, n_tiles_n;
+    int cin;             // input row width in elements (FC1: channels of one input row)
+    int pos_shift;       // conv: output positions computed = e << pos_shift
 };
 
 struct PArgs {
@@ -42,6 +52,8 @@ struct PArgs {
     void *X;
     const float2 *part;
     const float *w2, *b2;
+    const float *fc1_const;       // [rows_n + 1][H]
+    int *ext;                     // [2] batch extent per step parity
     unsigned *bar_counter;        // zero at launch
     int *abort_g;                 // zero at launch
     int32_t *status;
@@ -52,6 +64,7 @@ struct PArgs {
     int64_t n_steps;
     int64_t spin_ns;
     int n_layers, B, P, compact_every, stages, stage_bytes, prm_floats;
+    int rows_n, e_round;          // last conv rows; FC1 k-block rows (extent granularity)
 };
 
 namespace {
@@ -90,16 +103,17 @@ __device__ bool grid_sync(const PArgs &a, unsigned &target, volatile int *cta_ab
     return *cta_abort == 0;
 }
 
-// All warps of the grid gather 32-row groups through their staging buffers
-// (the stage ring is free between GEMM phases).
+// All warps of the grid gather 32-row groups (every row of every slot) into
+// the pair-major tile through their staging buffers (the stage ring is free
+// between GEMM phases), raising the extent `ext`.
 template <typename T>
-__device__ void gather_phase(const PArgs &a, uint8_t *ring) {
+__device__ void gather_phase(const PArgs &a, uint8_t *ring, int *ext) {
     const int64_t total = (int64_t)a.B * a.A->window;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint8_t *stg = ring + warp * (32 * stage_row_bytes<T>());
     for (int64_t row0 = ((int64_t)blockIdx.x * kWarps + warp) * 32; row0 < total;
          row0 += (int64_t)gridDim.x * kWarps * 32)
-        gather_rows_warp<T>(a.A, reinterpret_cast<T *>(a.X), row0, total, stg, lane);
+        gather_rows_warp_pm<T>(a.A, reinterpret_cast<T *>(a.X), a.B, row0, total, stg, lane, ext);
 }
 
 struct Pipe {  // pipeline counters that carry over between GEMM phases
@@ -107,15 +121,16 @@ struct Pipe {  // pipeline counters that carry over between GEMM phases
 };
 
 template <bool FP8>
-__device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *bars, float *prm, uint8_t *staging,
-                           uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
+__device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint64_t *bars, float *prm,
+                               uint8_t *staging, uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
     const PLayer &L = a.layer[l];
     constexpr int BK = FP8 ? 128 : 64;
     const int S = a.stages, N = L.N, BN = L.BN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *s_bias = prm, *s_scale = prm + N, *s_oscale = prm + 2 * N, *s_w2 = prm + 3 * N;
+    float *s_bias = prm, *s_scale = prm + N, *s_oscale = prm + 2 * N, *s_w2 = prm + 3 * N, *s_cst = prm + 5 * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         s_bias[i] = L.bias[i];
+        if (L.out_part) s_cst[i] = a.fc1_const[(size_t)e * N + i];
         if (FP8) {
             s_scale[i] = L.scale[i];
             s_oscale[i] = L.oscale ? L.oscale[i] : 1.f;
@@ -131,9 +146,17 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *b
     auto empty = [&](int s) { return smem_u32(&bars[S + s]); };
     auto tfull = [&](int x) { return smem_u32(&bars[2 * S + x]); };
     auto tempty = [&](int x) { return smem_u32(&bars[2 * S + 2 + x]); };
-    const int M = min(*a.A->n_active * L.m_mult, a.B * L.m_mult);
-    const int n_tiles = ((M + BM - 1) / BM) * L.n_tiles_n;
-    const int KB = L.K / BK;
+    const int M = min(*a.A->n_active, a.B);                 // slots
+    const int n_sb = (M + BM - 1) / BM;
+    const int n_pos = L.out_part ? 1 : (e << L.pos_shift);  // output row positions computed
+    const int n_tiles = n_pos * n_sb * L.n_tiles_n;
+    const int KB = L.out_part ? e * L.cin / BK : L.K / BK;
+    auto tile_of = [&](int t, int &pos, int &sb, int &nt) {
+        nt = t % L.n_tiles_n;
+        const int r = t / L.n_tiles_n;
+        sb = r % n_sb;
+        pos = r / n_sb;
+    };
     const int64_t lim = a.spin_ns;
     const uint32_t stage_tx = (uint32_t)(A_BYTES + BN * ROW_BYTES);
     const bool det = a.detail && blockIdx.x == 0;
@@ -143,14 +166,26 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *b
             asm volatile("fence.proxy.async.global;" ::: "memory");
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                const int m0 = (t / L.n_tiles_n) * BM, n0 = (t % L.n_tiles_n) * BN;
+                int pos, sb, nt;
+                tile_of(t, pos, sb, nt);
+                const int n0 = nt * BN;
                 for (int kb = 0; kb < KB; kb++, pp.prod_it++) {
                     const int s = pp.prod_it % S;
                     const uint32_t ph = (uint32_t)(pp.prod_it / S) & 1u;
                     if (!mbar_wait(empty(s), ph ^ 1u, lim, cta_abort, a.status)) { ok = false; break; }
                     const uint32_t sa = smem_base + s * a.stage_bytes;
+                    // A: conv -> input pair `pos`; FC1 -> the input row holding this K slice
+                    int ax, ay;
+                    if (L.out_part) {
+                        const int kk = kb * BK, row = kk / L.cin;
+                        ax = (row & 1) * L.cin + kk % L.cin;
+                        ay = (row >> 1) * a.B + sb * BM;
+                    } else {
+                        ax = kb * BK;
+                        ay = pos * a.B + sb * BM;
+                    }
                     mbar_expect_tx(full(s), stage_tx);
-                    tma_load_2d(sa, &L.tA, full(s), kb * BK, m0);
+                    tma_load_2d(sa, &L.tA, full(s), ax, ay);
                     tma_load_2d(sa + A_BYTES, &L.tB, full(s), kb * BK, n0);
                 }
             }
@@ -190,8 +225,9 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *b
         constexpr int CB = 32 * OES, SROW = CB + 16;
         uint8_t *stg = staging + (warp - 2) * 32 * SROW;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, pp.epi_tc++) {
-            const int mt = t / L.n_tiles_n, nt = t % L.n_tiles_n;
-            const int m0 = mt * BM, n0 = nt * BN;
+            int pos, sb, nt;
+            tile_of(t, pos, sb, nt);
+            const int m0 = sb * BM, n0 = nt * BN;
             const int acc = pp.epi_tc & 1;
             const uint32_t aph = (uint32_t)(pp.epi_tc >> 1) & 1u;
             if (!mbar_wait(tfull(acc), aph, lim, cta_abort, a.status)) break;
@@ -208,6 +244,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *b
                 for (int j = 0; j < 32; j++) {
                     float x = __uint_as_float(r[j]);
                     if (FP8) x *= s_scale[col0 + j];
+                    if (L.out_part) x += s_cst[col0 + j];   // FC1: the constant rows past the extent
                     x = fmaxf(x + s_bias[col0 + j], 0.f);
                     if (FP8 && !L.out_part) x *= s_oscale[col0 + j];
                     v[j] = x;
@@ -248,13 +285,15 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, uint8_t *smem, uint64_t *b
                     __syncwarp();
                     constexpr int U = CB / 16, RPP = 32 / U;
                     const int rr = lane / U, u = lane % U;
-                    uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) + (size_t)col0 * OES + u * 16;
+                    // pair-major destination of output position `pos` of each slot
+                    uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) +
+                                     ((size_t)(pos >> 1) * a.B * 2 * N + (size_t)(pos & 1) * N + col0) * OES + u * 16;
 #pragma unroll
                     for (int pass = 0; pass < U; pass++) {
                         const int r_in = pass * RPP + rr;
-                        const int grow = m0 + q * 32 + r_in;
+                        const int slot = m0 + q * 32 + r_in;
                         const uint4 val = *reinterpret_cast<const uint4 *>(stg + r_in * SROW + u * 16);
-                        if (grow < M) *reinterpret_cast<uint4 *>(gbase + (size_t)grow * N * OES) = val;
+                        if (slot < M) *reinterpret_cast<uint4 *>(gbase + (size_t)slot * 2 * N * OES) = val;
                     }
                     __syncwarp();
                 }
@@ -316,12 +355,17 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             t_prev = t;
         }
     };
-    gather_phase<T>(a, smem);
+    gather_phase<T>(a, smem, a.ext);
     bool ok = grid_sync(a, target, cta_abort);
     mark(SIMNET_KERNEL_GATHER);
     for (int64_t step = 0; step < a.n_steps && ok; step++) {
+        int *ext_now = a.ext + (step & 1), *ext_next = a.ext + ((step + 1) & 1);
+        int e = (*(volatile int *)ext_now + (1 << (a.n_layers - 1)) - 1) >> (a.n_layers - 1);  // conv-output rows
+        e = (e + a.e_round - 1) / a.e_round * a.e_round;
+        e = max(1, min(e, a.rows_n));
+        if (blockIdx.x == 0 && threadIdx.x == 0) *ext_next = 0;   // the head phase raises it
         for (int l = 0; l < a.n_layers && ok; l++) {
-            const uint64_t tp = gemm_phase<FP8>(a, l, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+            const uint64_t tp = gemm_phase<FP8>(a, l, e, smem, bars, prm, staging, tmem_base, cta_abort, pp);
             ok = grid_sync(a, target, cta_abort);
             if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
             mark(SIMNET_KERNEL_LAYER0 + l);
@@ -333,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             const int n_act = *a.A->n_active;
             for (int slot = blockIdx.x * kWarps + warp; slot < n_act; slot += gridDim.x * kWarps)
                 head_update_warp<T>(a.A, slot, lane, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
-                                    reinterpret_cast<uint64_t *>(mine), mine + 256 * 8);
+                                    reinterpret_cast<uint64_t *>(mine), mine + 256 * 8, a.B, ext_next);
         }
         ok = grid_sync(a, target, cta_abort);
         mark(SIMNET_KERNEL_HEAD_UPDATE);
@@ -342,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             ok = grid_sync(a, target, cta_abort);
             mark(SIMNET_KERNEL_COMPACT);
             if (!ok) break;
-            gather_phase<T>(a, smem);
+            gather_phase<T>(a, smem, ext_next);
             ok = grid_sync(a, target, cta_abort);
             mark(SIMNET_KERNEL_GATHER);
         }
@@ -363,25 +407,39 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     memset(&a, 0, sizeof a);
     const bool fp8 = c->cfg.precision == SIMNET_FP8_E4M3;
     int bn_max = 64, n_max = 0;
+    const int BK = fp8 ? 128 : 64;
+    const int C = c->cfg.conv_channels, W = c->cfg.window;
     for (int l = 0; l < c->n_layers; l++) {
         const TcPlan &p = c->plan[l];
         const GemmLayer &g = c->layer[l];
         PLayer &L = a.layer[l];
-        L.tA = p.tA;
+        const bool fc1 = l == c->n_layers - 1;
+        // input rows of this layer and its pair-major view [pairs * B][2 * row width]
+        const int in_rows = W >> l;
+        const int row_w = l == 0 ? kNFP : C;
+        const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
+        if (!encode_map_2d(L.tA, c->cfg.precision, in, (uint64_t)2 * row_w, (uint64_t)((in_rows + 1) / 2) * B, BK,
+                           BM, why))
+            return false;
         L.tB = p.tB;
         L.bias = g.bias;
         L.scale = g.scale;
         L.oscale = g.oscale;
-        L.out = p.out;
-        L.m_mult = g.m_mult;
+        L.out = fc1 ? (void *)c->h1 : c->act[l & 1];
         L.K = g.K;
         L.N = g.N;
         L.BN = p.BN;
-        L.out_part = l == c->n_layers - 1;
+        L.out_part = fc1;
         L.n_tiles_n = g.N / p.BN;
+        L.cin = row_w;
+        L.pos_shift = fc1 ? 0 : c->cfg.n_conv - 1 - l;
         bn_max = std::max(bn_max, p.BN);
         n_max = std::max(n_max, g.N);
     }
+    a.fc1_const = c->fc1_const;
+    a.ext = c->ext;
+    a.rows_n = c->rows_n;
+    a.e_round = std::max(1, BK / C);
     a.A = c->d_args;
     a.X = c->X;
     a.part = (const float2 *)c->h1;
@@ -400,7 +458,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.P = c->n_part;
     a.compact_every = uneven ? 16 : 0;
     a.stage_bytes = A_BYTES + bn_max * ROW_BYTES;
-    a.prm_floats = 5 * n_max;
+    a.prm_floats = 6 * n_max;
     const size_t staging = (size_t)kEpiWarps * 32 * (32 * (fp8 ? 1 : 2) + 16);
     const size_t fixed = 1024 + 256 + (size_t)a.prm_floats * 4 + staging;
     const size_t budget = 232448 - 1024;   // minus the static shared memory of the compaction
@@ -418,6 +476,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);
     if (per_sm < 1) { why = "persistent kernel does not fit on an SM"; return false; }
     cudaMemsetAsync(c->bar, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(c->ext, 0, 2 * sizeof(int), s);
     cudaMemsetAsync(c->bar_abort, 0, sizeof(int), s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(num_sms());

@@ -273,6 +273,54 @@ __device__ __forceinline__ void gather_rows_warp(const StepArgs *__restrict__ A,
     __syncwarp();
 }
 
+// Pair-major feature tile (the persistent kernel's layout): row r of slot s is
+// the half (r & 1) of row ((r >> 1) * Bs + s) of a [W/2 * Bs][2 * 64] array, so
+// the two rows a k=2/stride-2 convolution combines are one contiguous K run.
+template <typename T>
+__device__ __forceinline__ T *pm_row(T *X, int Bs, int slot, int r) {
+    return X + ((size_t)(r >> 1) * Bs + slot) * (2 * kNFP) + (size_t)(r & 1) * kNFP;
+}
+
+// Store n staged rows (row ids row0.., slot-major over W rows per slot) into
+// the pair-major tile, U lanes per row.
+template <typename T>
+__device__ __forceinline__ void flush_rows_pm(const uint8_t *__restrict__ stg, T *__restrict__ X, int Bs, int W,
+                                              int64_t row0, int n, int lane) {
+    constexpr int RB = kNFP * (int)sizeof(T), SR = stage_row_bytes<T>(), U = RB / 16, RPP = 32 / U;
+    const int rr = lane / U, u = lane % U;
+#pragma unroll 4
+    for (int pass = 0; pass < U; pass++) {
+        const int r = pass * RPP + rr;
+        if (r < n) {
+            const int64_t id = row0 + r;
+            uint8_t *g = reinterpret_cast<uint8_t *>(pm_row<T>(X, Bs, (int)(id / W), (int)(id % W))) + u * 16;
+            *reinterpret_cast<uint4 *>(g) = *reinterpret_cast<const uint4 *>(stg + r * SR + u * 16);
+        }
+    }
+}
+
+// Dense gather of 32 rows into the pair-major tile; the lane holding row 0 of
+// an active sub-trace raises the batch extent to its queue length + 1.
+template <typename T>
+__device__ __forceinline__ void gather_rows_warp_pm(const StepArgs *__restrict__ A, T *__restrict__ X, int Bs,
+                                                    int64_t row0, int64_t total, uint8_t *__restrict__ stg, int lane,
+                                                    int *ext) {
+    const int W = A->window;
+    const int n = (int)min((int64_t)32, total - row0);
+    if (lane < n) {
+        const int64_t id = row0 + lane;
+        gather_row_into<T>(A, id, reinterpret_cast<T *>(stg + lane * stage_row_bytes<T>()));
+        const int slot = (int)(id / W);
+        if (id % W == 0 && slot < *A->n_active) {
+            const int b = A->active[slot];
+            if (A->pos[b] < (int)(A->offsets[b + 1] - A->offsets[b])) atomicMax(ext, A->qlen[b] + 1);
+        }
+    }
+    __syncwarp();
+    flush_rows_pm<T>(stg, X, Bs, W, row0, n, lane);
+    __syncwarp();
+}
+
 // One warp, one active slot.  FC2 arrives as P partial dot products (one per
 // FC1 column block) which are summed with the bias; softplus, clamp, round;
 // then curTick += F, retire (budget RW*F), evict at capacity, append with
@@ -280,11 +328,16 @@ __device__ __forceinline__ void gather_rows_warp(const StepArgs *__restrict__ A,
 // RW) and write the sub-trace's cycle count.  Otherwise the warp writes the
 // slot's feature rows for the next step (the gather, fused here); `sq` is this
 // warp's shared-memory scratch of 256 queue entries.
+// With `pm_slots` > 0 the feature tile is pair-major over that many slots:
+// only rows 0 .. max(old, new queue length) are written (rows past a queue are
+// kept zero) and the next step's batch extent `ext` is raised to the new queue
+// length + 1.
 template <typename T>
 __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A, int slot, int lane,
                                                  const float2 *__restrict__ part, int P, int part_stride,
                                                  const float *__restrict__ b2, T *__restrict__ X,
-                                                 uint64_t *__restrict__ sq, uint8_t *__restrict__ stg) {
+                                                 uint64_t *__restrict__ sq, uint8_t *__restrict__ stg,
+                                                 int pm_slots = 0, int *ext = nullptr) {
     const int b = A->active[slot];
     const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
     int p = A->pos[b];
@@ -314,6 +367,7 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
     const int cap = A->cap, RW = A->retire_width, strict = A->strict;
     uint64_t *ring = A->ring + (size_t)b * cap;
     int qs = A->qstart[b], ql = A->qlen[b], ev = 0;
+    const int ql_old = ql;
     int32_t tick = A->tick[b] + (int32_t)F;
     const int k = retire_run(ring, cap, qs, min(ql, RW * (int)F), tick, strict, lane);
     qs += k;
@@ -353,10 +407,12 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
         const int W = A->window;
         const uint32_t cur = A->records[o + p];
         constexpr int SR = stage_row_bytes<T>();
-        for (int r0 = 0; r0 < W; r0 += 32) {   // a lane builds a row, the warp stores rows whole
+        const int rows = pm_slots > 0 ? min(W, max(ql_old, ql) + 1) : W;
+        if (pm_slots > 0 && lane == 0) atomicMax(ext, ql + 1);
+        for (int r0 = 0; r0 < rows; r0 += 32) {   // a lane builds a row, the warp stores rows whole
             const int r = r0 + lane;
             T *row = reinterpret_cast<T *>(stg + lane * SR);
-            if (r < W) {
+            if (r < rows) {
                 if (r == 0) {
                     write_row<T>(row, cur, cur, false, 0, 0);
                 } else if (r <= ql) {
@@ -367,7 +423,10 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
                 }
             }
             __syncwarp();
-            flush_rows<T>(stg, X, (int64_t)slot * W + r0, min(32, W - r0), lane);
+            if (pm_slots > 0)
+                flush_rows_pm<T>(stg, X, pm_slots, W, (int64_t)slot * W + r0, min(32, rows - r0), lane);
+            else
+                flush_rows<T>(stg, X, (int64_t)slot * W + r0, min(32, rows - r0), lane);
             __syncwarp();
         }
     }

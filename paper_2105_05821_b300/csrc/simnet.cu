@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cuda_fp16.h>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,8 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     if (c->bar_abort) cudaFree(c->bar_abort);
     if (c->phase_ns) cudaFree(c->phase_ns);
     if (c->phase_n) cudaFree(c->phase_n);
+    if (c->fc1_const) cudaFree(c->fc1_const);
+    if (c->ext) cudaFree(c->ext);
     delete c;
 }
 
@@ -281,6 +284,9 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     simnet_status st;
     std::vector<std::vector<float>> s_act;
     if (k.precision == SIMNET_FP8_E4M3 && (st = calibrate_fp8(c, Wg, Bg, s_act)) != SIMNET_OK) return st;
+    // what the kernels multiply by, in true units (GEMM layout), and how each
+    // layer's stored activations round: for the padding constants below
+    std::vector<std::vector<float>> Wdeq(c->n_layers), osc(c->n_layers);
     for (int l = 0; l < c->n_layers; l++) {
         if (k.precision == SIMNET_FP8_E4M3) {
             // B[n][k] = W[n][k] * s_in[k] / s_w[n]: the input's per-channel scale folded
@@ -301,6 +307,13 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
                         __nv_cvt_float_to_fp8(Wg[l][(size_t)n * K + kk] * sin[kk] / sw[n], __NV_SATFINITE, __NV_E4M3);
                 os[n] = l < k.n_conv ? 1.f / s_act[l][n] : 1.f;
             }
+            Wdeq[l].resize(wq.size());
+            for (int n = 0; n < Nn; n++)
+                for (int kk = 0; kk < K; kk++) {
+                    const __half_raw hr = __nv_cvt_fp8_to_halfraw(wq[(size_t)n * K + kk], __NV_E4M3);
+                    Wdeq[l][(size_t)n * K + kk] = __half2float(__half(hr)) * sw[n] / sin[kk];
+                }
+            osc[l] = os;
             if ((st = upload(c, &c->Wl[l], wq)) != SIMNET_OK) return st;
             if ((st = upload(c, (void **)&c->wscale[l], sw)) != SIMNET_OK) return st;
             if (l < k.n_conv) {
@@ -314,7 +327,11 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
             c->W32[l] = (float *)c->Wl[l];
         } else if (k.precision == SIMNET_BF16) {
             std::vector<__nv_bfloat16> wb(Wg[l].size());
-            for (size_t i = 0; i < wb.size(); i++) wb[i] = __float2bfloat16_rn(Wg[l][i]);
+            Wdeq[l].resize(wb.size());
+            for (size_t i = 0; i < wb.size(); i++) {
+                wb[i] = __float2bfloat16_rn(Wg[l][i]);
+                Wdeq[l][i] = __bfloat162float(wb[i]);
+            }
             if ((st = upload(c, &c->Wl[l], wb)) != SIMNET_OK) return st;
             if ((st = upload(c, (void **)&c->W32[l], Wg[l])) != SIMNET_OK) return st;
         }
@@ -326,6 +343,41 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     }
     if ((st = upload(c, (void **)&c->w2, w2)) != SIMNET_OK) return st;
     if ((st = upload(c, (void **)&c->b2, b2)) != SIMNET_OK) return st;
+    if (k.precision != SIMNET_FP32) {
+        // Rows past every queue are zero features, so every conv layer maps them to
+        // one constant row; FC1 then sees that row at each padded position.  Follow
+        // the constant through the layers with the stored precision's rounding and
+        // tabulate S[e] = sum over positions l >= e of FC1's weights times it.
+        auto quant = [&](int l, int n, double x) -> double {
+            if (k.precision == SIMNET_BF16) return (double)__bfloat162float(__float2bfloat16_rn((float)x));
+            const float o = osc[l][n];
+            const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8((float)x * o, __NV_SATFINITE, __NV_E4M3);
+            return (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) / o;
+        };
+        std::vector<double> cst(kNFP, 0.0);
+        int cin_pad = kNFP;
+        for (int l = 0; l < k.n_conv; l++) {
+            const int K = c->layer[l].K;
+            std::vector<double> nxt(C);
+            for (int n = 0; n < C; n++) {
+                double acc = Bg[l][n];
+                for (int kk = 0; kk < K; kk++) acc += (double)Wdeq[l][(size_t)n * K + kk] * cst[kk % cin_pad];
+                nxt[n] = quant(l, n, acc > 0.0 ? acc : 0.0);
+            }
+            cst = nxt;
+            cin_pad = C;
+        }
+        const int L = k.n_conv, K1 = c->fc1_in;
+        std::vector<float> S((size_t)(Ln + 1) * H, 0.f);
+        for (int n = 0; n < H; n++) {
+            double run = 0.0;
+            for (int e = Ln - 1; e >= 0; e--) {
+                for (int ch = 0; ch < C; ch++) run += (double)Wdeq[L][(size_t)n * K1 + (size_t)e * C + ch] * cst[ch];
+                S[(size_t)e * H + n] = (float)run;
+            }
+        }
+        if ((st = upload(c, (void **)&c->fc1_const, S)) != SIMNET_OK) return st;
+    }
     c->has_weights = true;
     if (c->tr.ready) {  // new weights: restart the optimiser
         TrainState &t = c->tr;
@@ -355,7 +407,7 @@ static simnet_status ensure_workspace(simnet_ctx *c, int B) {
     const simnet_config &k = c->cfg;
     const size_t es = elem_size(k.precision);
     const size_t xb = (size_t)B * k.window * kNFP * es;
-    const size_t ab = (size_t)B * (k.window / 2) * k.conv_channels * es;
+    const size_t ab = (size_t)B * std::max(k.window / 2, 2) * k.conv_channels * es;
     CK(cudaMalloc(&c->X, xb));
     CK(cudaMalloc(&c->act[0], ab));
     CK(cudaMalloc(&c->act[1], ab));
@@ -377,6 +429,7 @@ static simnet_status ensure_workspace(simnet_ctx *c, int B) {
         CK(cudaMalloc(&c->bar_abort, sizeof(int)));
         CK(cudaMalloc(&c->phase_ns, 64 * sizeof(unsigned long long)));
         CK(cudaMalloc(&c->phase_n, SIMNET_KERNEL_KINDS * sizeof(unsigned long long)));
+        CK(cudaMalloc(&c->ext, 4 * sizeof(int)));
     }
     if (!c->h_args) {
         CK(cudaMallocHost(&c->h_args, sizeof(StepArgs)));
@@ -572,7 +625,8 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
     c->args_pending = true;
     launch_init_state(c->d_args, B, s);
 
-    const bool uneven = min_len != max_len;
+    // compaction pays off only when sub-traces finish well apart
+    const bool uneven = max_len - min_len > std::max<int64_t>(16, max_len / 8);
     const bool timed = (c->cfg.flags & SIMNET_FLAG_KERNEL_EVENTS) != 0;
     const bool pdl = c->pdl && !timed;
     if ((st = prepare_plans(c, B, pdl)) != SIMNET_OK) return st;
@@ -585,7 +639,7 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
         c->kt_valid = false;
     }
     c->phase_valid = false;
-    const bool persistent = c->cfg.precision != SIMNET_FP32 && (c->cfg.flags & SIMNET_FLAG_PERSISTENT);
+    const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE);
     if (persistent) {
         // one cooperative kernel runs every step; its phases are timed by CTA 0 on request
         c->phase_on = timed;

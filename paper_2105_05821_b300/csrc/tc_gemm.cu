@@ -372,6 +372,11 @@ int out_es(int out_kind, int prec) {
 
 }  // namespace
 
+bool encode_map_2d(CUtensorMap &m, int prec, const void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                   uint32_t box_outer, std::string &why) {
+    return encode_2d(m, prec, base, inner, outer, box_inner, box_outer, why);
+}
+
 int num_sms() {
     static int n = 0;
     if (!n) {

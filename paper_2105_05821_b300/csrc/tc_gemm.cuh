@@ -48,4 +48,8 @@ void launch_tc_gemm(const TcPlan &p, const GemmLayer &g, const int32_t *count, c
 
 int num_sms();
 
+// 2D tiled TMA map (128-byte swizzle) over a row-major [outer][inner] array.
+bool encode_map_2d(CUtensorMap &m, int prec, const void *base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                   uint32_t box_outer, std::string &why);
+
 }  // namespace simnet

@@ -23,7 +23,7 @@ FLAG_RETIRE_STRICT = 0x1
 FLAG_NO_GRAPH = 0x2
 FLAG_KERNEL_EVENTS = 0x4
 FLAG_NO_PDL = 0x8
-FLAG_PERSISTENT = 0x10
+FLAG_LAYERWISE = 0x10
 KERNEL_KINDS = 12
 KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE", 6: "EUNSUPPORTED"}
@@ -141,12 +141,12 @@ class Simnet:
     def __init__(self, window: int, n_conv: int, channels: int, hidden: int,
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
-                 pdl: bool = True, persistent: bool = False):
+                 pdl: bool = True, persistent: bool = True):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
-                 | (FLAG_PERSISTENT if persistent else 0))
+                 | (0 if persistent else FLAG_LAYERWISE))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, 0,
                             spin_limit_ns)
         self.window = window

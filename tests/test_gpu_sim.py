@@ -22,10 +22,11 @@ FP32_LAT_TOL = 1e-3
 FP32_CPI_TOL = 1e-3
 
 
-def teacher_forced_check(arch, trace, precision, blob, lat_tol, rw=8, strict=False, graph=True):
+def teacher_forced_check(arch, trace, precision, blob, lat_tol, rw=8, strict=False, graph=True, persistent=True):
     cfg = oracle.Config.of(arch, retire_width=rw, retire_strict=strict)
     ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, logs=True)
-    sim, _ = make_sim(arch, precision, blob=blob, retire_width=rw, strict=strict, graph=graph)
+    sim, _ = make_sim(arch, precision, blob=blob, retire_width=rw, strict=strict, graph=graph,
+                      persistent=persistent)
     # GPU replays the oracle's latencies: every integer must match
     g = run_gpu(sim, trace, replay=ref.lat)
     np.testing.assert_array_equal(g["cycles"], ref.cycles)
@@ -93,21 +94,49 @@ def test_graph_and_direct_launch_identical():
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_launch_modes_identical(precision):
-    """The persistent cooperative kernel, per-layer kernels with programmatic
-    dependent launch, CUDA graphs and plain launches must give bit-identical
-    logs on a workload with compaction (uneven lengths)."""
+    """Per-layer kernels with programmatic dependent launch, CUDA graphs and
+    plain launches must give bit-identical logs on a workload with compaction
+    (uneven lengths)."""
     arch = I.ARCH_SMALL(32)
     trace = I.small_trace([50, 300, 7, 160, 0, 90] * 4, seed=12)
     blob = I.workload_weights(I.Workload("p", arch, 1, 1, seed=12))
     runs = []
-    modes = [(True, True, False), (True, False, False), (False, True, False), (False, False, False),
-             (True, True, True)]
-    for graph, pdl, persistent in modes:
-        sim, _ = make_sim(arch, precision, blob=blob, graph=graph, pdl=pdl, persistent=persistent)
+    for graph, pdl in ((True, True), (True, False), (False, True), (False, False)):
+        sim, _ = make_sim(arch, precision, blob=blob, graph=graph, pdl=pdl, persistent=False)
         runs.append(run_gpu(sim, trace))
     for r in runs[1:]:
         np.testing.assert_array_equal(r["pre"], runs[0]["pre"])
         np.testing.assert_array_equal(r["cycles"], runs[0]["cycles"])
+
+
+@pytest.mark.parametrize("precision,tol", [("bf16", 5e-2), ("fp8", 0.6)])
+@pytest.mark.parametrize("case", ["c1", "ragged", "uneven", "c2arch"])
+def test_persistent_kernel_teacher_forced(precision, tol, case):
+    """The persistent kernel (padding-extent skipping, pair-major layout,
+    compaction inside the kernel) against the oracle: integer state bit-exact
+    under teacher forcing both ways, latencies within the precision's bound,
+    and close to the per-layer path on identical states."""
+    if case == "c1":
+        w = I.WORKLOADS["c1"]
+        arch, trace, blob = w.arch, I.make_trace(w), I.workload_weights(w)
+    elif case == "c2arch":
+        w = I.WORKLOADS["c2"]
+        arch, blob = w.arch, I.workload_weights(w)
+        trace = I.small_trace([400, 37, 250, 0, 128], seed=21)
+    else:
+        arch = I.ARCH_SMALL(32)
+        lengths = [0, 1, 5, 33, 130, 7, 64, 0] if case == "ragged" else \
+            np.clip(np.rint(np.exp(np.random.default_rng(4).normal(np.log(60), 0.8, 300))), 1, 400).astype(int).tolist()
+        trace = I.small_trace(lengths, seed=len(lengths))
+        blob = I.workload_weights(I.Workload("u", arch, 1, 1, seed=4))
+    ref, _, err = teacher_forced_check(arch, trace, precision, blob, tol, persistent=True)
+    lw, _ = make_sim(arch, precision, blob=blob, persistent=False)
+    g = run_gpu(lw, trace, replay=ref.lat)
+    ps, _ = make_sim(arch, precision, blob=blob, persistent=True)
+    h = run_gpu(ps, trace, replay=ref.lat)
+    np.testing.assert_array_equal(h["cycles"], g["cycles"])
+    d = np.abs(h["pre"] - g["pre"]) / (np.abs(g["pre"]) + 1.0)
+    assert np.median(d) < 1e-3 and d.max() < 0.1, (np.median(d), d.max())
 
 
 def test_uneven_lengths_compaction():
