@@ -207,6 +207,19 @@ def kind_name(w, k):
     return f"conv{l + 1}_gemm" if l < w.arch.n_conv else "fc1_gemm"
 
 
+def aggregate(ms_total: float, steps: int, inst_per_step: int, world: int, device):
+    """Whole-job throughput of `world` replicas, each timing `steps` steps of
+    `inst_per_step` instructions: the slowest rank's time (max over ranks)
+    divides all ranks' instructions.  Returns (ms per step, inst/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_per_step = float(t.item()) / steps
+    return ms_per_step, world * inst_per_step / (ms_per_step / 1e3)
+
+
 def truncate(trace: I.Trace, n: int) -> I.Trace:
     lens = np.minimum(trace.lengths(), n)
     parts = [trace.records[trace.offsets[b]:trace.offsets[b] + lens[b]] for b in range(trace.n_subtraces)]
@@ -274,20 +287,11 @@ def run_ours(args, rank, world):
     with ClockSampler(dev.index) as clk:
         ms, wall = timed_run(sim, args.steps, args.warmup)
     clocks = clk.summary()
-    # max over ranks
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    ms_per_step = ms_max / args.steps
-    value = world * N / (ms_per_step / 1e3)
+    ms_per_step, value = aggregate(ms, args.steps, N, world, dev)
 
     # end to end through host buffers (pinned H2D of the trace, D2H of the cycle counts)
     ms_e2e, _ = timed_run(sim, max(2, args.steps // 2), 1, e2e=True)
-    t = torch.tensor([ms_e2e], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = world * N / (float(t.item()) / max(2, args.steps // 2) / 1e3)
+    _, e2e_value = aggregate(ms_e2e, max(2, args.steps // 2), N, world, dev)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,

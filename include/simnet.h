@@ -91,7 +91,10 @@ typedef struct {
     int32_t retire_width;  /* processor-queue retire bandwidth, entries per cycle */
     int32_t precision;     /* simnet_precision */
     uint32_t flags;        /* SIMNET_FLAG_* */
-    int32_t reserved;
+    int32_t barrier_limit_us; /* bound on the persistent kernel's grid-barrier waits (microseconds);
+                                 <= 0 uses spin_limit_ns.  When a barrier wait gives up, every CTA
+                                 leaves at its next barrier (no copy in flight there) and the call
+                                 returns SIMNET_ETIMEOUT; the context stays usable */
     int64_t spin_limit_ns; /* bound on any device-side wait; <= 0 selects 2 s */
 } simnet_config;
 

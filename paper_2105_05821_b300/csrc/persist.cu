@@ -63,6 +63,7 @@ struct PArgs {
                                   // last MMA commit, epilogue done, barrier passed (or null)
     int64_t n_steps;
     int64_t spin_ns;
+    int64_t bar_spin_ns;          // grid-barrier wait bound
     int n_layers, B, P, compact_every, stages, stage_bytes, prm_floats;
     int rows_n, e_round;          // last conv rows; FC1 k-block rows (extent granularity)
 };
@@ -90,7 +91,7 @@ __device__ bool grid_sync(const PArgs &a, unsigned &target, volatile int *cta_ab
         const uint64_t t0 = gtimer();
         while (ld_acquire(a.bar_counter) < target) {
             if (*(volatile int *)a.abort_g) { *cta_abort = 1; break; }
-            if ((int64_t)(gtimer() - t0) > a.spin_ns) {
+            if ((int64_t)(gtimer() - t0) > a.bar_spin_ns) {
                 atomicExch(a.abort_g, 1);
                 atomicExch(a.status, kStatusTimeout);
                 *cta_abort = 1;
@@ -453,6 +454,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.detail = c->phase_on ? c->phase_ns + 16 : nullptr;
     a.n_steps = n_steps;
     a.spin_ns = c->cfg.spin_limit_ns;
+    a.bar_spin_ns = c->cfg.barrier_limit_us > 0 ? (int64_t)c->cfg.barrier_limit_us * 1000 : c->cfg.spin_limit_ns;
     a.n_layers = c->n_layers;
     a.B = B;
     a.P = c->n_part;

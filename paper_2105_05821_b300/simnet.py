@@ -44,7 +44,7 @@ class SimnetError(RuntimeError):
 class _Config(C.Structure):
     _fields_ = [("window", C.c_int32), ("n_conv", C.c_int32), ("conv_channels", C.c_int32),
                 ("fc_hidden", C.c_int32), ("retire_width", C.c_int32), ("precision", C.c_int32),
-                ("flags", C.c_uint32), ("reserved", C.c_int32), ("spin_limit_ns", C.c_int64)]
+                ("flags", C.c_uint32), ("barrier_limit_us", C.c_int32), ("spin_limit_ns", C.c_int64)]
 
 
 class _Trace(C.Structure):
@@ -141,13 +141,13 @@ class Simnet:
     def __init__(self, window: int, n_conv: int, channels: int, hidden: int,
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
-                 pdl: bool = True, persistent: bool = True):
+                 pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
                  | (0 if persistent else FLAG_LAYERWISE))
-        self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, 0,
+        self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, barrier_limit_us,
                             spin_limit_ns)
         self.window = window
         self.precision = prec

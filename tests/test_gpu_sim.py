@@ -178,3 +178,23 @@ def test_errors_reported():
     with pytest.raises(SimnetError) as e:
         sim.simulate(rec, bad)
     assert e.value.status == 1
+
+
+def test_barrier_timeout_reported_and_context_recovers():
+    """Failure detection without a fault: the persistent kernel's grid-barrier
+    waits get a 1 us bound (a barrier over 148 CTAs takes longer), so a wait
+    gives up, every CTA leaves at a barrier and the call returns ETIMEOUT.  The
+    device stays usable: a normal context then reproduces the oracle."""
+    w = I.WORKLOADS["c1"]
+    trace = I.make_trace(w)
+    blob = I.workload_weights(w)
+    bad, _ = make_sim(w.arch, "bf16", blob=blob, barrier_limit_us=1)
+    with pytest.raises(SimnetError) as e:
+        run_gpu(bad, trace)
+    assert e.value.status == 4                       # ETIMEOUT
+    assert "bound" in str(e.value)
+    cfg = oracle.Config.of(w.arch)
+    ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, logs=True)
+    good, _ = make_sim(w.arch, "bf16", blob=blob)
+    g = run_gpu(good, trace, replay=ref.lat)
+    np.testing.assert_array_equal(g["cycles"], ref.cycles)
