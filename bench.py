@@ -329,8 +329,18 @@ def run_ours(args, rank, world):
         s32 = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
         s32.load_weights(blob32)
         m32, _ = timed_run(s32, max(2, args.steps // 3), 1)
-        out["fp32_form"] = {"value": N / (m32 / max(2, args.steps // 3) / 1e3), "unit": UNIT}
+        out["fp32_form"] = {"value": N / (m32 / max(2, args.steps // 3) / 1e3), "unit": UNIT,
+                            "note": "FFMA CUDA-core GEMMs, per-layer kernels, same workload and timing"}
         s32.close()
+    if rank == 0 and args.precision == "bf16" and not args.no_fp32:
+        s8 = Simnet.for_arch(w.arch, precision="fp8", retire_width=w.retire_width, persistent=not args.layerwise)
+        s8.load_weights(blob32)
+        if not args.no_autotune:
+            s8.autotune(B)
+        m8, _ = timed_run(s8, args.steps, args.warmup)
+        out["fp8_form"] = {"value": N / (m8 / args.steps / 1e3), "unit": UNIT,
+                           "note": "FP8 e4m3 tcgen05 path, same workload and timing"}
+        s8.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ids, threads = cpu_sample_ids(w, trace, I.workload_weights(w))
         rate, n, dt, r = oracle_rate(w, trace, I.workload_weights(w), ids, threads=threads)
@@ -388,13 +398,43 @@ def roofline(w, args, blob32, rec, off, cyc, B):
     return roof, kernels
 
 
+def run_training(args):
+    """Training throughput on the training workload (windows/s of fused library
+    steps: gather, forward, MSE, hand-written backward, Adam); a side measurement,
+    not the simulation metric."""
+    import torch
+    from paper_2105_05821_b300.simnet import Simnet
+    from paper_2105_05821_b300.train import Windows
+    w = I.WORKLOADS["c3"]
+    rec = I.make_records(w.n_instructions, w.seed)
+    win = Windows.from_labels(rec, I.toy_labels(rec))
+    sim = Simnet.for_arch(w.arch, precision=args.precision if args.precision != "fp8" else "bf16")
+    sim.load_weights(I.workload_weights(w).astype(np.float32))
+    batch = 4096
+    g = torch.Generator(device="cuda").manual_seed(0)
+    idx = [torch.randint(0, len(win), (batch,), device="cuda", generator=g) for _ in range(args.warmup + args.steps)]
+    for i in range(args.warmup):
+        sim.train_step(win, idx[i], 1e-3)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    losses = [sim.train_step(win, idx[args.warmup + i], 1e-3) for i in range(args.steps)]
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / args.steps
+    print(json.dumps({"metric": "training windows/s (fused gather, forward, backward, Adam)",
+                      "value": batch / (ms / 1e3), "unit": "windows/s", "ms_per_step": ms, "batch": batch,
+                      "dtype": sim.precision, "loss_first": losses[0], "loss_last": losses[-1],
+                      "config": {"workload": f"c3: {w.description}"}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")
@@ -409,6 +449,9 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "c3":
+        run_training(args)
         return
     if world > 1:
         import torch
