@@ -220,6 +220,28 @@ def aggregate(ms_total: float, steps: int, inst_per_step: int, world: int, devic
     return ms_per_step, world * inst_per_step / (ms_per_step / 1e3)
 
 
+def train_predictor(w: I.Workload, steps: int):
+    """The uneven-batching workload uses a trained CNN: train its architecture
+    (window 96) with the library's fused steps on toy-pipeline labels of the
+    training workload's trace (batch 4096, Adam lr 1e-3)."""
+    import torch
+    from paper_2105_05821_b300.simnet import Simnet
+    from paper_2105_05821_b300.train import Windows, train
+    tw = I.WORKLOADS["c3"]
+    rec = I.make_records(tw.n_instructions, tw.seed)
+    win = Windows.from_labels(rec, I.toy_labels(rec))
+    sim = Simnet.for_arch(w.arch, precision="fp32")
+    sim.load_weights(I.workload_weights(w).astype(np.float32))
+    t0 = time.perf_counter()
+    losses = train(sim, win, steps, 4096, lr=1e-3, seed=w.seed)
+    torch.cuda.synchronize()
+    info = {"steps": steps, "batch": 4096, "loss_first": losses[0], "loss_last": float(np.mean(losses[-10:])),
+            "seconds": time.perf_counter() - t0, "labels": "toy pipeline model on the training trace (2M)"}
+    blob = sim.get_weights()
+    sim.close()
+    return blob, info
+
+
 def truncate(trace: I.Trace, n: int) -> I.Trace:
     lens = np.minimum(trace.lengths(), n)
     parts = [trace.records[trace.offsets[b]:trace.offsets[b] + lens[b]] for b in range(trace.n_subtraces)]
@@ -239,6 +261,9 @@ def run_ours(args, rank, world):
     if args.subtrace_len:
         trace = truncate(trace, args.subtrace_len)
     blob32 = I.workload_weights(w).astype(np.float32)
+    train_info = None
+    if args.workload == "c4" and not args.untrained:
+        blob32, train_info = train_predictor(w, args.train_steps)
     N, B = trace.n_instructions, trace.n_subtraces
 
     rec_h = torch.from_numpy(trace.records.view(np.int32).copy()).pin_memory()
@@ -341,9 +366,16 @@ def run_ours(args, rank, world):
         out["fp8_form"] = {"value": N / (m8 / args.steps / 1e3), "unit": UNIT,
                            "note": "FP8 e4m3 tcgen05 path, same workload and timing"}
         s8.close()
+    if train_info:
+        out["trained_predictor"] = train_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ids, threads = cpu_sample_ids(w, trace, I.workload_weights(w))
-        rate, n, dt, r = oracle_rate(w, trace, I.workload_weights(w), ids, threads=threads)
+        blob64 = blob32.astype(np.float64) if train_info else I.workload_weights(w)
+        if args.workload == "c4":   # the configuration's own check: 64 sampled sub-traces
+            ids = sorted(np.random.default_rng(w.seed).choice(trace.n_subtraces, 64, replace=False).tolist())
+            threads = host_cores()
+        else:
+            ids, threads = cpu_sample_ids(w, trace, blob64)
+        rate, n, dt, r = oracle_rate(w, trace, blob64, ids, threads=threads)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"{len(ids)} whole sub-traces ({n} instructions) of the same "
                                          f"workload, {dt:.1f} s, FP64"}
@@ -442,6 +474,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--layerwise", action="store_true",
                     help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
+    ap.add_argument("--untrained", action="store_true", help="c4: keep the seeded weights")
+    ap.add_argument("--train-steps", type=int, default=300, help="c4: training steps before simulating")
     ap.add_argument("--subtrace-len", type=int, default=0,
                     help="keep only the first N instructions of every sub-trace (profiling runs)")
     args = ap.parse_args()
