@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define SIMNET_ABI_VERSION 1
+#define SIMNET_ABI_VERSION 2
 #define SIMNET_N_FEATURES 50 /* features per instruction row (Sec. 2.2) */
 
 typedef struct simnet_ctx simnet_ctx;
@@ -122,7 +122,8 @@ typedef struct {
     int64_t evictions;    /* queue entries dropped at capacity */
     int64_t kernel_launches; /* kernels the call launched (graph replays counted per kernel) */
     float ms_total;          /* device time of the call, CUDA events */
-    float reserved[3];
+    int32_t pending;         /* sub-traces not yet finished (0 once the trace is done) */
+    int64_t steps_done;      /* lock-steps run since the state was initialised */
 } simnet_stats;
 
 /* Kernel kinds reported by simnet_kernel_times(). */
@@ -198,6 +199,65 @@ simnet_status simnet_load_weights(simnet_ctx *ctx, const float *blob, int64_t n_
 simnet_status simnet_simulate(simnet_ctx *ctx, const simnet_trace *trace, int64_t *cycles_out,
                               uint8_t *lat_log, float *pre_log, const uint8_t *lat_replay,
                               simnet_stats *stats, void *stream);
+
+/*
+ * Bounded, resumable form of simnet_simulate (checkpoint / resume of the
+ * lock-step loop of Sec. 3.3).  Runs at most `max_steps` lock-step iterations
+ * (max_steps < 0: until every sub-trace has finished and drained).
+ *   resume = 0  start from an empty queue and curTick = 0 for every sub-trace;
+ *   resume = 1  continue from the state this context holds: the state left by
+ *               its previous simulate call or put there by simnet_state_load.
+ *               The trace must have the same sub-trace offsets (checked by a
+ *               fingerprint of `offsets` and n_instructions; the records are
+ *               not checked and must be the same) and the context the same
+ *               weights (checked by a fingerprint of the FP32 weights).
+ * cycles_out (device int64 [n_subtraces]) receives, after every call, the
+ * final curTick of each finished sub-trace and 0 for the others; lat_log,
+ * pre_log and lat_replay are indexed by instruction, so a resumed call writes
+ * the remaining entries of the same arrays.  stats->pending counts sub-traces
+ * not yet finished; stats->steps is the iterations run by this call and
+ * stats->steps_done the total since the state was initialised.  A split run
+ * gives results bit-identical to an unsplit one: each row of every GEMM and
+ * the FC2 partial sums depend only on the row's own inputs, and the next
+ * step's feature rows are a function of the saved state alone.
+ * Errors: as simnet_simulate; EINVAL for max_steps == 0 with resume == 0 is
+ * not raised (the call only initialises the state); ESTATE for resume without
+ * a state, with another trace or other weights.
+ */
+simnet_status simnet_simulate_steps(simnet_ctx *ctx, const simnet_trace *trace, int64_t *cycles_out,
+                                    uint8_t *lat_log, float *pre_log, const uint8_t *lat_replay,
+                                    int64_t max_steps, int32_t resume, simnet_stats *stats, void *stream);
+
+/* Kinds of state exported by simnet_state_save. */
+#define SIMNET_STATE_SIM 0   /* per-sub-trace curTick, position, queue ring, eviction counts,
+                                active list and finished cycle counts */
+#define SIMNET_STATE_TRAIN 1 /* FP32 master weights (canonical order), Adam moments and step */
+
+/*
+ * Export the context's state of kind `kind` into a HOST buffer.  With
+ * host_buf == NULL only *bytes is set, to the size needed; otherwise *bytes
+ * is the buffer's capacity on entry and the bytes written on return.  The
+ * format is a versioned header (magic "SIMNETS1", the config fields that
+ * shape the state, the trace and weight fingerprints) followed by the raw
+ * arrays in little-endian order; it loads only into a context of the same
+ * window, CNN shape and retire settings.  Synchronises `stream`.
+ * Errors: EINVAL (bad kind, NULL bytes, capacity too small), ESTATE (no such
+ * state: no simulate call yet, or no weights), ECUDA.
+ */
+simnet_status simnet_state_save(simnet_ctx *ctx, int32_t kind, void *host_buf, size_t *bytes, void *stream);
+
+/*
+ * Import a state written by simnet_state_save.  SIMNET_STATE_SIM: the next
+ * simnet_simulate_steps(..., resume = 1) continues it (workspaces are sized
+ * for its batch).  SIMNET_STATE_TRAIN: loads the weights as
+ * simnet_load_weights does, then restores the Adam moments and step count
+ * (ignored by FP8 contexts, which do not train).  Synchronises `stream`.
+ * Errors: EINVAL (NULL buffer, wrong magic, version, kind or size, a state of
+ * another window / CNN shape / retire setting or queue capacity), ENOMEM,
+ * ECUDA.  Whether the weights match a SIM state is checked when it resumes.
+ */
+simnet_status simnet_state_load(simnet_ctx *ctx, int32_t kind, const void *host_buf, size_t bytes,
+                                void *stream);
 
 /*
  * Run the CNN alone on feature matrices (Sec. 2.3).

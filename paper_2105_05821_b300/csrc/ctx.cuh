@@ -94,10 +94,46 @@ struct simnet_ctx {
     // autotuned tile widths: tuned_bn[l] applies to batches of tuned_B sub-traces
     int tuned_B = -1;
     int tuned_bn[kMaxConv + 1] = {};
+
+    // resumable simulation state: the workspace arrays tick/pos/qstart/qlen/
+    // evict/ring/active/n_active plus the finished cycle counts `cyc`
+    int64_t *cyc = nullptr;   // [ws_B]
+    bool sim_valid = false;
+    int sim_B = 0;
+    int64_t sim_steps = 0, sim_max_len = 0, sim_n_inst = 0;
+    uint64_t sim_trace_fp = 0, sim_weights_fp = 0;
+
+    // fingerprint of the FP32 weights (recomputed lazily after on-device updates)
+    uint64_t weights_fp = 0;
+    bool weights_fp_dirty = false;
+    // the padding-constant table fc1_const no longer matches the weights (set by
+    // on-device weight updates; rebuilt before the next persistent run)
+    bool const_stale = false;
 };
 
 namespace simnet {
 bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaStream_t s, std::string &why);
+}
+
+// Training buffers for n windows (and the optimiser state, once); train.cu.
+simnet_status ensure_train(simnet_ctx *c, int n);
+// Simulation workspaces for B sub-traces (reallocating drops a held state).
+simnet_status ensure_workspace(simnet_ctx *c, int B);
+// Fingerprint of the FP32 weights in canonical order (0 if they cannot be read).
+uint64_t weights_fingerprint(simnet_ctx *c);
+// Tabulate fc1_const from FP32 biases and the weights as the kernels use them
+// (GEMM layout, dequantised); osc = FP8 requant multipliers (empty otherwise).
+simnet_status build_fc1_const(simnet_ctx *c, const std::vector<std::vector<float>> &Bg,
+                              const std::vector<std::vector<float>> &Wdeq,
+                              const std::vector<std::vector<float>> &osc);
+// Rebuild fc1_const from the FP32 master weights on the device (BF16 contexts
+// after on-device updates).
+simnet_status refresh_fc1_const(simnet_ctx *c);
+// 64-bit FNV-1a of a byte range, continuing from h.
+inline uint64_t fnv1a(const void *p, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+    const uint8_t *b = (const uint8_t *)p;
+    for (size_t i = 0; i < n; i++) { h ^= b[i]; h *= 0x100000001b3ull; }
+    return h;
 }
 
 // Records an event pair around each kernel when timing is on.
@@ -143,11 +179,3 @@ static inline simnet_status fail(simnet_ctx *c, simnet_status st, const char *fm
                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-
-#define CK(call)                                                                                  \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess)                                                                    \
-            return fail(c, e_ == cudaErrorMemoryAllocation ? SIMNET_ENOMEM : SIMNET_ECUDA,        \
-                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)

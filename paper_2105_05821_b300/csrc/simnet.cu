@@ -92,13 +92,14 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
 
 static void free_workspace(simnet_ctx *c) {
     void *bufs[] = {c->X, c->act[0], c->act[1], c->h1, c->tick, c->pos, c->qstart, c->qlen, c->evict,
-                    c->active, c->n_active, c->status, c->cnt, c->ring, c->totals, c->d_args};
+                    c->active, c->n_active, c->status, c->cnt, c->ring, c->totals, c->d_args, c->cyc};
     for (void *p : bufs)
         if (p) cudaFree(p);
     c->X = c->act[0] = c->act[1] = nullptr;
     c->h1 = nullptr;
     c->tick = c->pos = c->qstart = c->qlen = c->evict = c->active = c->n_active = c->status = c->cnt = nullptr;
     c->ring = nullptr;
+    c->cyc = nullptr;
     c->totals = nullptr;
     c->d_args = nullptr;
     c->ws_B = 0;
@@ -248,6 +249,77 @@ static simnet_status calibrate_fp8(simnet_ctx *c, const std::vector<std::vector<
 // (rows 2l and 2l+1 of the input are adjacent, so a conv output row is one dot
 // product with a contiguous 2*Cin_pad slice); FC1: K index = l * C + c for the
 // canonical input index c * L_n + l (the device flatten keeps rows outermost).
+// Rows past every queue are zero features, so every conv layer maps them to
+// one constant row; FC1 then sees that row at each padded position.  Follow
+// the constant through the layers with the stored precision's rounding and
+// tabulate S[e] = sum over positions l >= e of FC1's weights times it.
+simnet_status build_fc1_const(simnet_ctx *c, const std::vector<std::vector<float>> &Bg,
+                              const std::vector<std::vector<float>> &Wdeq,
+                              const std::vector<std::vector<float>> &osc) {
+    const simnet_config &k = c->cfg;
+    const int C = k.conv_channels, H = k.fc_hidden, Ln = c->rows_n;
+    auto quant = [&](int l, int n, double x) -> double {
+        if (k.precision == SIMNET_BF16) return (double)__bfloat162float(__float2bfloat16_rn((float)x));
+        const float o = osc[l][n];
+        const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8((float)x * o, __NV_SATFINITE, __NV_E4M3);
+        return (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) / o;
+    };
+    std::vector<double> cst(kNFP, 0.0);
+    int cin_pad = kNFP;
+    for (int l = 0; l < k.n_conv; l++) {
+        const int K = c->layer[l].K;
+        std::vector<double> nxt(C);
+        for (int n = 0; n < C; n++) {
+            double acc = Bg[l][n];
+            for (int kk = 0; kk < K; kk++) acc += (double)Wdeq[l][(size_t)n * K + kk] * cst[kk % cin_pad];
+            nxt[n] = quant(l, n, acc > 0.0 ? acc : 0.0);
+        }
+        cst = nxt;
+        cin_pad = C;
+    }
+    const int L = k.n_conv, K1 = c->fc1_in;
+    std::vector<float> S((size_t)(Ln + 1) * H, 0.f);
+    for (int n = 0; n < H; n++) {
+        double run = 0.0;
+        for (int e = Ln - 1; e >= 0; e--) {
+            for (int ch = 0; ch < C; ch++) run += (double)Wdeq[L][(size_t)n * K1 + (size_t)e * C + ch] * cst[ch];
+            S[(size_t)e * H + n] = (float)run;
+        }
+    }
+    return upload(c, (void **)&c->fc1_const, S);
+}
+
+// BF16 contexts whose FP32 masters changed on the device (training steps, new
+// device weights): the kernels use bf16(W32), so the table follows from those.
+simnet_status refresh_fc1_const(simnet_ctx *c) {
+    if (c->cfg.precision != SIMNET_BF16) return fail(c, SIMNET_ESTATE, "padding table: only BF16 weights change on the device");
+    CK(cudaDeviceSynchronize());
+    std::vector<std::vector<float>> Bg(c->n_layers), Wdeq(c->n_layers), osc;
+    for (int l = 0; l < c->n_layers; l++) {
+        const GemmLayer &g = c->layer[l];
+        Wdeq[l].resize((size_t)g.N * g.K);
+        Bg[l].resize(g.N);
+        CK(cudaMemcpy(Wdeq[l].data(), c->W32[l], Wdeq[l].size() * 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(Bg[l].data(), c->bias[l], (size_t)g.N * 4, cudaMemcpyDeviceToHost));
+        for (float &w : Wdeq[l]) w = __bfloat162float(__float2bfloat16_rn(w));
+    }
+    simnet_status st = build_fc1_const(c, Bg, Wdeq, osc);
+    if (st == SIMNET_OK) c->const_stale = false;
+    return st;
+}
+
+// Fingerprint of the FP32 weights in canonical order (the loaded blob's, or of
+// the current device masters after on-device updates).
+uint64_t weights_fingerprint(simnet_ctx *c) {
+    if (c->weights_fp_dirty) {
+        std::vector<float> blob((size_t)c->n_weights);
+        if (simnet_get_weights(c, blob.data()) != SIMNET_OK) return 0;
+        c->weights_fp = fnv1a(blob.data(), blob.size() * sizeof(float));
+        c->weights_fp_dirty = false;
+    }
+    return c->weights_fp;
+}
+
 extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, int64_t n_values) {
     if (!c) return SIMNET_EINVAL;
     if (!blob) return fail(c, SIMNET_EINVAL, "load_weights: blob is NULL");
@@ -343,41 +415,10 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     }
     if ((st = upload(c, (void **)&c->w2, w2)) != SIMNET_OK) return st;
     if ((st = upload(c, (void **)&c->b2, b2)) != SIMNET_OK) return st;
-    if (k.precision != SIMNET_FP32) {
-        // Rows past every queue are zero features, so every conv layer maps them to
-        // one constant row; FC1 then sees that row at each padded position.  Follow
-        // the constant through the layers with the stored precision's rounding and
-        // tabulate S[e] = sum over positions l >= e of FC1's weights times it.
-        auto quant = [&](int l, int n, double x) -> double {
-            if (k.precision == SIMNET_BF16) return (double)__bfloat162float(__float2bfloat16_rn((float)x));
-            const float o = osc[l][n];
-            const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8((float)x * o, __NV_SATFINITE, __NV_E4M3);
-            return (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) / o;
-        };
-        std::vector<double> cst(kNFP, 0.0);
-        int cin_pad = kNFP;
-        for (int l = 0; l < k.n_conv; l++) {
-            const int K = c->layer[l].K;
-            std::vector<double> nxt(C);
-            for (int n = 0; n < C; n++) {
-                double acc = Bg[l][n];
-                for (int kk = 0; kk < K; kk++) acc += (double)Wdeq[l][(size_t)n * K + kk] * cst[kk % cin_pad];
-                nxt[n] = quant(l, n, acc > 0.0 ? acc : 0.0);
-            }
-            cst = nxt;
-            cin_pad = C;
-        }
-        const int L = k.n_conv, K1 = c->fc1_in;
-        std::vector<float> S((size_t)(Ln + 1) * H, 0.f);
-        for (int n = 0; n < H; n++) {
-            double run = 0.0;
-            for (int e = Ln - 1; e >= 0; e--) {
-                for (int ch = 0; ch < C; ch++) run += (double)Wdeq[L][(size_t)n * K1 + (size_t)e * C + ch] * cst[ch];
-                S[(size_t)e * H + n] = (float)run;
-            }
-        }
-        if ((st = upload(c, (void **)&c->fc1_const, S)) != SIMNET_OK) return st;
-    }
+    if (k.precision != SIMNET_FP32 && (st = build_fc1_const(c, Bg, Wdeq, osc)) != SIMNET_OK) return st;
+    c->weights_fp = fnv1a(blob, (size_t)n_values * sizeof(float));
+    c->weights_fp_dirty = false;
+    c->const_stale = false;
     c->has_weights = true;
     if (c->tr.ready) {  // new weights: restart the optimiser
         TrainState &t = c->tr;
@@ -400,10 +441,11 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     return SIMNET_OK;
 }
 
-static simnet_status ensure_workspace(simnet_ctx *c, int B) {
+simnet_status ensure_workspace(simnet_ctx *c, int B) {
     if (B <= c->ws_B) return SIMNET_OK;
     CK(cudaDeviceSynchronize());
     free_workspace(c);
+    c->sim_valid = false;
     const simnet_config &k = c->cfg;
     const size_t es = elem_size(k.precision);
     const size_t xb = (size_t)B * k.window * kNFP * es;
@@ -422,6 +464,7 @@ static simnet_status ensure_workspace(simnet_ctx *c, int B) {
     CK(cudaMalloc(&c->status, 4));
     CK(cudaMalloc(&c->cnt, 4));
     CK(cudaMalloc(&c->ring, (size_t)B * c->cap * sizeof(uint64_t)));
+    CK(cudaMalloc(&c->cyc, (size_t)B * sizeof(int64_t)));
     CK(cudaMalloc(&c->totals, 2 * sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_args, sizeof(StepArgs)));
     if (!c->bar) {
@@ -561,6 +604,13 @@ static simnet_status capture_graphs(simnet_ctx *c, int B, bool compact) {
 extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, int64_t *cycles_out,
                                          uint8_t *lat_log, float *pre_log, const uint8_t *lat_replay,
                                          simnet_stats *stats, void *stream) {
+    return simnet_simulate_steps(c, t, cycles_out, lat_log, pre_log, lat_replay, -1, 0, stats, stream);
+}
+
+extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace *t, int64_t *cycles_out,
+                                               uint8_t *lat_log, float *pre_log, const uint8_t *lat_replay,
+                                               int64_t max_steps, int32_t resume, simnet_stats *stats,
+                                               void *stream) {
     if (!c) return SIMNET_EINVAL;
     if (!t || !cycles_out || t->n_subtraces < 0 || t->n_instructions < 0)
         return fail(c, SIMNET_EINVAL, "simulate: null trace/cycles_out or negative sizes");
@@ -592,15 +642,26 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
         max_len = n > max_len ? n : max_len;
         min_len = n < min_len ? n : min_len;
     }
+    const uint64_t trace_fp = fnv1a(c->h_offsets, (size_t)(B + 1) * sizeof(int64_t));
+    if (resume) {
+        if (!c->sim_valid) return fail(c, SIMNET_ESTATE, "simulate: no simulation state to resume");
+        if (c->sim_B != B || c->sim_n_inst != t->n_instructions || c->sim_trace_fp != trace_fp)
+            return fail(c, SIMNET_ESTATE, "simulate: the trace differs from the one of the held state");
+        if (c->sim_weights_fp != weights_fingerprint(c))
+            return fail(c, SIMNET_ESTATE, "simulate: the weights differ from the ones of the held state");
+    }
     simnet_status st = ensure_workspace(c, B);
     if (st != SIMNET_OK) return st;
+    if (c->const_stale && c->cfg.precision != SIMNET_FP32 && (st = refresh_fc1_const(c)) != SIMNET_OK) return st;
+    const int64_t done_before = resume ? c->sim_steps : 0;
+    const int64_t n_steps = max_steps < 0 ? max_len - done_before : std::min(max_steps, max_len - done_before);
 
     // per-call arguments -> device (the pinned staging buffer is reused once its last copy is done)
     if (c->args_pending) CK(cudaEventSynchronize(c->args_ev));
     StepArgs &a = *c->h_args;
     a.records = t->records;
     a.offsets = t->offsets;
-    a.cycles_out = cycles_out;
+    a.cycles_out = c->cyc;
     a.lat_log = lat_log;
     a.pre_log = pre_log;
     a.replay = lat_replay;
@@ -623,14 +684,25 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
     CK(cudaMemcpyAsync(c->d_args, c->h_args, sizeof(StepArgs), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->args_ev, s));
     c->args_pending = true;
-    launch_init_state(c->d_args, B, s);
+    if (resume) {
+        CK(cudaMemsetAsync(c->status, 0, sizeof(int32_t), s));
+    } else {
+        launch_init_state(c->d_args, B, s);
+        c->sim_valid = true;
+        c->sim_B = B;
+        c->sim_steps = 0;
+        c->sim_max_len = max_len;
+        c->sim_n_inst = t->n_instructions;
+        c->sim_trace_fp = trace_fp;
+        c->sim_weights_fp = weights_fingerprint(c);
+    }
 
     // compaction pays off only when sub-traces finish well apart
     const bool uneven = max_len - min_len > std::max<int64_t>(16, max_len / 8);
     const bool timed = (c->cfg.flags & SIMNET_FLAG_KERNEL_EVENTS) != 0;
     const bool pdl = c->pdl && !timed;
     if ((st = prepare_plans(c, B, pdl)) != SIMNET_OK) return st;
-    int64_t launches = 2 + (int64_t)max_len * launches_per_step(c);
+    int64_t launches = (resume ? 1 : 2) + n_steps * launches_per_step(c);
     KTimer kt;
     kt.c = timed ? c : nullptr;
     kt.s = s;
@@ -640,7 +712,9 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
     }
     c->phase_valid = false;
     const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE);
-    if (persistent) {
+    if (n_steps <= 0) {
+        launches = resume ? 0 : 1;
+    } else if (persistent) {
         // one cooperative kernel runs every step; its phases are timed by CTA 0 on request
         c->phase_on = timed;
         if (timed) {
@@ -648,33 +722,36 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
             CK(cudaMemsetAsync(c->phase_n, 0, SIMNET_KERNEL_KINDS * sizeof(unsigned long long), s));
         }
         std::string why;
-        if (!launch_persistent(c, B, max_len, uneven, s, why))
+        if (!launch_persistent(c, B, n_steps, uneven, s, why))
             return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
-        launches = 2;
+        launches = resume ? 1 : 2;
         c->phase_valid = timed;
     } else {
-    enqueue_gather(c, B, s, false, timed ? &kt : nullptr);
-    if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
-        for (int64_t i = 0; i < max_len; i++) {
-            enqueue_step(c, B, s, pdl, timed ? &kt : nullptr);
-            if (uneven && (i % kGraphSteps) == kGraphSteps - 1) {
-                enqueue_compact(c, B, s, pdl, timed ? &kt : nullptr);
-                launches += 2;
+        enqueue_gather(c, B, s, false, timed ? &kt : nullptr);
+        if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
+            for (int64_t i = 0; i < n_steps; i++) {
+                enqueue_step(c, B, s, pdl, timed ? &kt : nullptr);
+                if (uneven && (i % kGraphSteps) == kGraphSteps - 1) {
+                    enqueue_compact(c, B, s, pdl, timed ? &kt : nullptr);
+                    launches += 2;
+                }
             }
+            if (timed && !kt.ok) return fail(c, SIMNET_ENOMEM, "kernel timing: event pool exhausted");
+            c->kt_valid = timed;
+        } else {
+            if (c->g_B != B || c->g_compact != (int)uneven || !c->gexec[0])
+                if ((st = capture_graphs(c, B, uneven)) != SIMNET_OK) return st;
+            const int64_t full = n_steps / kGraphSteps, rest = n_steps % kGraphSteps;
+            for (int64_t i = 0; i < full; i++) CK(cudaGraphLaunch(c->gexec[0], s));
+            for (int64_t i = 0; i < rest; i++) CK(cudaGraphLaunch(c->gexec[1], s));
+            if (uneven) launches += 2 * (full + rest);
         }
-        if (timed && !kt.ok) return fail(c, SIMNET_ENOMEM, "kernel timing: event pool exhausted");
-        c->kt_valid = timed;
-    } else {
-        if (c->g_B != B || c->g_compact != (int)uneven || !c->gexec[0])
-            if ((st = capture_graphs(c, B, uneven)) != SIMNET_OK) return st;
-        const int64_t full = max_len / kGraphSteps, rest = max_len % kGraphSteps;
-        for (int64_t i = 0; i < full; i++) CK(cudaGraphLaunch(c->gexec[0], s));
-        for (int64_t i = 0; i < rest; i++) CK(cudaGraphLaunch(c->gexec[1], s));
-        if (uneven) launches += 2 * (full + rest);
-    }
     }
     CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(cycles_out, c->cyc, (size_t)B * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(c->ev1, s));
+    const int64_t done = done_before + std::max<int64_t>(n_steps, 0);
+    c->sim_steps = done;
     if (stats) {
         CK(cudaMemsetAsync(c->totals, 0, 2 * sizeof(unsigned long long), s));
         launch_totals(c->d_args, c->totals, B, s);
@@ -683,12 +760,22 @@ extern "C" simnet_status simnet_simulate(simnet_ctx *c, const simnet_trace *t, i
         CK(cudaStreamSynchronize(s));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        int64_t inst = 0;
+        int32_t pending = 0;
+        for (int b = 0; b < B; b++) {
+            const int64_t n = c->h_offsets[b + 1] - c->h_offsets[b];
+            inst += std::max<int64_t>(0, std::min(n, done) - done_before);
+            pending += n > done ? 1 : 0;
+        }
         stats->total_cycles = (int64_t)c->h_totals[0];
         stats->evictions = (int64_t)c->h_totals[1];
-        stats->instructions = t->n_instructions;
-        stats->steps = max_len;
+        stats->instructions = inst;
+        stats->steps = std::max<int64_t>(n_steps, 0);
+        stats->steps_done = done;
+        stats->pending = pending;
         stats->kernel_launches = launches;
         stats->ms_total = ms;
+        if (*c->h_status != kStatusOk) c->sim_valid = false;
         if (*c->h_status == kStatusTimeout) return fail(c, SIMNET_ETIMEOUT, "a device-side wait exceeded its bound");
         if (*c->h_status != kStatusOk) return fail(c, SIMNET_ECUDA, "device status %d", *c->h_status);
     }

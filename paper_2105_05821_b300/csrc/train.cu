@@ -215,7 +215,7 @@ static void gemm(bool round, const float *A, int64_t sam, int64_t sak, const flo
 static int64_t layer_rows(const simnet_ctx *c, int l, int n) { return (int64_t)n * c->layer[l].m_mult; }
 
 // Allocate training buffers for n windows (and master-weight bookkeeping once).
-static simnet_status ensure_train(simnet_ctx *c, int n) {
+simnet_status ensure_train(simnet_ctx *c, int n) {
     TrainState &t = c->tr;
     const simnet_config &k = c->cfg;
     if (!t.ready) {
@@ -441,6 +441,8 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
     adam_kernel<<<1, 32, 0, s>>>(c->b2, t.mb2, t.vb2, t.gb2, 2, lr, b1, b2, eps, c1, c2);
     refresh_shadow(c, s);
     invalidate_plans(c);
+    c->weights_fp_dirty = true;
+    c->const_stale = true;
     if (loss_out) {
         double l = 0.0;
         CK(cudaMemcpyAsync(&l, t.loss, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -481,6 +483,8 @@ extern "C" simnet_status simnet_set_weights_device(simnet_ctx *c, const float *b
     CK(cudaMemcpyAsync(c->b2, p, 8, cudaMemcpyDeviceToDevice, s));
     refresh_shadow(c, s);
     invalidate_plans(c);
+    c->weights_fp_dirty = true;
+    c->const_stale = true;
     CK(cudaGetLastError());
     return SIMNET_OK;
 }

@@ -32,7 +32,9 @@ EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_e
            "simnet_weight_count", "simnet_load_weights", "simnet_simulate", "simnet_cnn_forward",
            "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes",
            "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
-           "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune"]
+           "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune",
+           "simnet_simulate_steps", "simnet_state_save", "simnet_state_load"]
+STATE_KINDS = {"sim": 0, "train": 1}
 
 
 class SimnetError(RuntimeError):
@@ -55,7 +57,7 @@ class _Trace(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("total_cycles", C.c_int64), ("instructions", C.c_int64), ("steps", C.c_int64),
                 ("evictions", C.c_int64), ("kernel_launches", C.c_int64), ("ms_total", C.c_float),
-                ("reserved", C.c_float * 3)]
+                ("pending", C.c_int32), ("steps_done", C.c_int64)]
 
 
 class _Windows(C.Structure):
@@ -111,6 +113,13 @@ def lib() -> C.CDLL:
         L.simnet_autotune.argtypes = [P, C.c_int32, C.c_int32, P, P]
         L.simnet_phase_detail.restype = C.c_int
         L.simnet_phase_detail.argtypes = [P, P, C.c_int32]
+        L.simnet_simulate_steps.restype = C.c_int
+        L.simnet_simulate_steps.argtypes = [P, C.POINTER(_Trace), P, P, P, P, C.c_int64, C.c_int32,
+                                            C.POINTER(_Stats), P]
+        L.simnet_state_save.restype = C.c_int
+        L.simnet_state_save.argtypes = [P, C.c_int32, P, C.POINTER(C.c_size_t), P]
+        L.simnet_state_load.restype = C.c_int
+        L.simnet_state_load.argtypes = [P, C.c_int32, P, C.c_size_t, P]
         _lib = L
     return _lib
 
@@ -133,6 +142,8 @@ class Stats:
     evictions: int
     kernel_launches: int
     ms_total: float
+    pending: int = 0
+    steps_done: int = 0
 
 
 class Simnet:
@@ -186,9 +197,11 @@ class Simnet:
         self._check(lib().simnet_load_weights(self._h, w.ctypes.data_as(C.c_void_p), len(w)))
 
     def simulate(self, records, offsets, cycles_out=None, lat_log=None, pre_log=None, replay=None,
-                 stats: bool = True, stream=None) -> Optional[Stats]:
-        """Simulate every sub-trace.  records: cuda int32/uint32 [N]; offsets: cuda int64 [B+1];
-        cycles_out: cuda int64 [B] (allocated if None and returned in .cycles)."""
+                 stats: bool = True, stream=None, max_steps: Optional[int] = None,
+                 resume: bool = False) -> Optional[Stats]:
+        """Simulate the sub-traces.  records: cuda int32/uint32 [N]; offsets: cuda int64 [B+1];
+        cycles_out: cuda int64 [B] (allocated if None and returned in .cycles).  With
+        max_steps, run at most that many lock-steps; resume=True continues the held state."""
         import torch
         B = offsets.numel() - 1
         if cycles_out is None:
@@ -196,13 +209,28 @@ class Simnet:
         self.cycles = cycles_out
         tr = _Trace(_ptr(records), _ptr(offsets), B, 0, records.numel())
         st = _Stats()
-        self._check(lib().simnet_simulate(self._h, C.byref(tr), _ptr(cycles_out), _ptr(lat_log),
-                                          _ptr(pre_log), _ptr(replay),
-                                          C.byref(st) if stats else None, _stream(stream)))
+        self._check(lib().simnet_simulate_steps(self._h, C.byref(tr), _ptr(cycles_out), _ptr(lat_log),
+                                                _ptr(pre_log), _ptr(replay),
+                                                -1 if max_steps is None else int(max_steps), int(resume),
+                                                C.byref(st) if stats else None, _stream(stream)))
         if not stats:
             return None
         return Stats(st.total_cycles, st.instructions, st.steps, st.evictions, st.kernel_launches,
-                     st.ms_total)
+                     st.ms_total, st.pending, st.steps_done)
+
+    def state_save(self, kind: str = "sim", stream=None) -> bytes:
+        """The context's simulation ("sim") or training ("train") state as bytes."""
+        n = C.c_size_t(0)
+        k = STATE_KINDS[kind]
+        self._check(lib().simnet_state_save(self._h, k, None, C.byref(n), _stream(stream)))
+        buf = C.create_string_buffer(n.value)
+        self._check(lib().simnet_state_save(self._h, k, buf, C.byref(n), _stream(stream)))
+        return buf.raw[:n.value]
+
+    def state_load(self, data: bytes, kind: str = "sim", stream=None) -> None:
+        """Import a state written by state_save (resume with simulate(..., resume=True))."""
+        buf = C.create_string_buffer(bytes(data), len(data))
+        self._check(lib().simnet_state_load(self._h, STATE_KINDS[kind], buf, len(data), _stream(stream)))
 
     def phase_detail(self, n_layers):
         """Per GEMM layer: summed ns to first data, last MMA, epilogue done, barrier passed (CTA 0)."""
