@@ -303,10 +303,14 @@ def run_ours(args, rank, world):
         return ms, wall
 
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          persistent=not args.layerwise)
+                          persistent=not args.layerwise, cluster=not args.no_cluster)
     sim.load_weights(blob32)
-    tiles = sim.autotune(B) if (args.precision != "fp32" and not args.no_autotune) else []
     st = sim.simulate(rec, off, cycles_out=cyc, stats=True)          # compile graphs, count launches
+    path = sim.kernel_path
+    tiles = []
+    if args.precision != "fp32" and not args.no_autotune and path != "cluster":
+        tiles = sim.autotune(B)                                      # tile widths of the tcgen05 GEMM phases
+        st = sim.simulate(rec, off, cycles_out=cyc, stats=True)
     launches_per_step = st.kernel_launches
 
     with ClockSampler(dev.index) as clk:
@@ -327,12 +331,24 @@ def run_ours(args, rank, world):
                    "d2h_bytes_per_step": int(8 * B)},
            "wall_s_timed": wall,
            "tile_widths": tiles[:w.arch.n_conv + 1],
-           "kernel_mode": "per-layer kernels" if args.layerwise or args.precision == "fp32" else "persistent"}
+           "kernel_mode": {"layerwise": "per-layer kernels", "persistent": "persistent",
+                           "cluster": "cluster"}.get(path, path)}
     out["config"]["instructions_per_step"] = N
     out["total_cycles"] = int(st.total_cycles)
     out["cpi"] = st.total_cycles / N
 
-    if rank == 0 and not args.no_breakdown:
+    if rank == 0 and not args.no_breakdown and path == "cluster":
+        # one launch does every step: the whole call's algorithmic work over its device time
+        hbm, bf16_burst, bf16_sus, src = peaks()
+        flops = 2.0 * w.arch.macs_per_inference() * N
+        ach = flops / (ms_per_step / 1e3) / 1e12
+        out["roofline"] = {"kernel": "cluster_kernel", "bound": "tensor", "achieved": ach, "peak": bf16_sus,
+                           "unit": "TFLOP/s", "frac": ach / bf16_sus, "peak_source": f"{src} bf16 sustained",
+                           "traffic": TRAFFIC.get((w.name, args.precision, "cluster_kernel")),
+                           "avg_launch_us": ms_per_step * 1e3, "algorithmic_per_launch": flops,
+                           "algorithmic_unit": "flop", "share_of_step": 1.0}
+        out["phases_us_per_step"] = cluster_phases(w, args, blob32, rec, off, cyc)
+    elif rank == 0 and not args.no_breakdown:
         out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B)
         if out["kernel_mode"] == "persistent":
             # one launch does every step: its roofline is the whole call's algorithmic
@@ -384,6 +400,28 @@ def run_ours(args, rank, world):
                                       "cpi_error": abs(float(gcyc.sum()) / float(r.cycles.sum()) - 1.0)}
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+CLUSTER_PHASES = ["step start", "feature rows", "wait conv1", "epilogue conv1", "wait conv2", "epilogue conv2",
+                  "wait conv3", "epilogue conv3", "wait FC1", "FC1 epilogue", "wait partials", "head", "extent"]
+
+
+def cluster_phases(w, args, blob32, rec, off, cyc):
+    """CTA 0's time per phase of the cluster kernel (globaltimer, one extra
+    timed call), in microseconds per lock-step."""
+    from paper_2105_05821_b300.simnet import Simnet
+    sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width, kernel_events=True)
+    sim.load_weights(blob32)
+    sim.simulate(rec, off, cycles_out=cyc, stats=True)
+    d = sim.phase_detail(8).reshape(-1)
+    sim.close()
+    steps = max(int(d[14]), 1)
+    names = [n for n in CLUSTER_PHASES]
+    if w.arch.n_conv == 2:   # the third conv layer's slots stay empty
+        names = names[:6] + ["-", "-"] + names[8:]
+    out = {n: float(d[k]) / steps / 1e3 for k, n in enumerate(names) if n != "-"}
+    out["positions_per_step"] = float(d[15]) / steps
+    return out
 
 
 def roofline(w, args, blob32, rec, off, cyc, B):
@@ -472,6 +510,7 @@ def main():
     ap.add_argument("--no-breakdown", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-cluster", action="store_true", help="BF16: the grid-wide persistent kernel")
     ap.add_argument("--layerwise", action="store_true",
                     help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
     ap.add_argument("--untrained", action="store_true", help="c4: keep the seeded weights")

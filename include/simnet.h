@@ -73,7 +73,9 @@ typedef enum {
 #define SIMNET_FLAG_NO_PDL 0x8u        /* no programmatic dependent launch between a step's kernels */
 #define SIMNET_FLAG_LAYERWISE 0x10u    /* BF16/FP8: one kernel per layer and step (CUDA graphs,
                                           PDL, dense padding rows) instead of the default single
-                                          persistent cooperative kernel that skips the padding */
+                                          persistent kernel that skips the padding */
+#define SIMNET_FLAG_NO_CLUSTER 0x20u   /* BF16: the grid-wide persistent kernel even where the
+                                          cluster kernel (SIMNET_PATH_CLUSTER) applies */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -287,9 +289,28 @@ simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launc
  * entries) receives, for GEMM layer l, out[4l + k] = summed nanoseconds from
  * the start of the layer's phase in CTA 0 to k = 0 its first operand tile
  * arriving, 1 its last MMA commit, 2 its epilogue done, 3 the grid barrier
- * passed.  Synchronises.  Errors: EINVAL, ESTATE (no such call).
+ * passed.  For the cluster kernel (SIMNET_PATH_CLUSTER) out[k], k < 32, is
+ * the summed ns of CTA 0's phase k instead: 0 step start (extent exchange),
+ * 1 feature rows, 2/4/6 waiting for conv layer 1/2/3, 3/5/7 their epilogues
+ * (7 includes the exchange of the last layer's rows), 8 waiting for FC1,
+ * 9 FC1 epilogue and partial sums, 10 waiting for the partial sums, 11 head
+ * and queue update, 12 extent exchange; 14 steps, 15 positions computed;
+ * 16-19 the MMA thread's waits for operands, weight tiles, the exchanged rows
+ * and FC1's weight tiles.
+ * Synchronises.  Errors: EINVAL, ESTATE (no such call).
  */
 simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
+
+/* Kernel paths of simnet_simulate. */
+#define SIMNET_PATH_NONE 0       /* no simulate call yet */
+#define SIMNET_PATH_LAYERWISE 1  /* one kernel per layer and step (CUDA graphs) */
+#define SIMNET_PATH_PERSISTENT 2 /* one cooperative kernel, grid-wide barriers between phases */
+#define SIMNET_PATH_CLUSTER 3    /* clusters of 4 CTAs each owning 128 sub-traces for the whole
+                                    call, no grid-wide synchronisation (BF16; 2-3 conv layers of
+                                    64 or 128 channels; FC1 width 256 or 512) */
+
+/* Path the last simnet_simulate call took (SIMNET_PATH_*), or -1 for a NULL context. */
+int32_t simnet_kernel_path(const simnet_ctx *ctx);
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */
 

@@ -1,0 +1,785 @@
+// cluster.cu -- the whole lock-step simulation of one simnet_simulate call as
+// independent thread-block clusters (BF16 CNNs with 2 or 3 conv layers of 64
+// or 128 channels).
+//
+// Sub-traces never interact (Sec. 3.3), so a cluster of 4 CTAs takes 128
+// batch slots for the whole call, 32 per CTA, and needs no grid-wide
+// synchronisation at all:
+//   * each CTA keeps its slots' state in shared memory: position, curTick, the
+//     processor-queue ring and its counters (Sec. 3.2), and the instruction
+//     records, fetched two steps ahead with cp.async;
+//   * per step the last-conv output positions below the cluster's padding
+//     extent are processed in passes of up to 256 first-layer rows: a CTA
+//     writes the feature rows (Sec. 2.2) of its slots that those positions
+//     depend on straight into shared memory and runs the k=2 / stride-2 conv
+//     pyramid on them (Sec. 2.3), one tcgen05 MMA per 128-row tile and layer
+//     (rows as A, the layer's weights streamed by TMA as B); layer l's
+//     epilogue writes layer l+1's operand in place, rows 2j and 2j+1 of a slot
+//     side by side along K;
+//   * the last conv layer's rows of all 128 slots are exchanged through
+//     distributed shared memory and every CTA accumulates FC1 for its quarter
+//     of the hidden neurons in TMEM over the passes; positions at or past the
+//     extent are constant rows whose FC1 contribution S[e] was tabulated when
+//     the weights were loaded;
+//   * the FC1 epilogue folds FC2 into per-slot partial sums that go to each
+//     slot's owner CTA, where one thread per slot runs the head, the clock and
+//     queue update and the drain (Eq. 1); the CTA then shares its new extent
+//     with the cluster.
+// Every wait is bounded (globaltimer); an expired wait records a timeout and
+// the CTA leaves at the next step boundary; a final cluster barrier keeps each
+// CTA's shared memory alive until its peers no longer write to it.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "ctx.cuh"
+#include "sim_device.cuh"
+#include "tc_ptx.cuh"
+
+namespace simnet {
+
+struct CArgs {
+    CUtensorMap tW[3];   // conv weights [C][K_l] (BF16, GEMM layout), box C rows x 64 columns
+    CUtensorMap tF;      // FC1 weights [H][K1], box H/4 rows x 64 columns
+    const float *cbias[3];
+    const float *fbias, *w2, *b2, *fc1_const;
+    const StepArgs *A;
+    int32_t *status;
+    unsigned long long *prof;   // [32] summed ns per phase in CTA 0 (or null), see cluster_phase_names
+    int64_t n_steps, spin_ns;
+    int L, C, H, cap, rows_n, stages;
+};
+
+namespace {
+using namespace tcx;
+
+constexpr int kCS = 4;            // CTAs per cluster
+constexpr int kSPC = 32;          // batch slots per CTA
+constexpr int kCThreads = 320;    // warp 0 TMA, warp 1 MMA, warps 2-9 workers
+constexpr int kWk = 256;          // worker threads
+constexpr int kStage = 16384;     // one weight panel: 128 rows x 64 BF16
+constexpr int kTmemCols = 512;
+
+__host__ __device__ inline uint32_t al_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Last-conv positions per pass: the first layer's rows of a pass (positions x
+// 2^(L-1) pairs x 32 slots) fill at most two 128-row MMA tiles.
+__host__ __device__ inline int pass_positions(int L) { return 8 >> (L - 1); }
+
+// Shared-memory layout, offsets from the 1024-byte aligned base.
+struct CLay {
+    uint32_t ring, act, fc1a, qring, rec, part, prm, slot, misc, bars, total;
+};
+
+__host__ __device__ inline CLay c_layout(int L, int C, int H, int cap, int stages) {
+    CLay y;
+    const int HN = H / kCS;
+    uint32_t actb = 256u * 256u;                                            // layer 0: 256 rows of two feature rows
+    if (128u * 4u * (uint32_t)C > actb) actb = 128u * 4u * (uint32_t)C;     // later layers: one 128-row tile of 2C
+    y.ring = 0;
+    y.act = (uint32_t)stages * kStage;
+    y.fc1a = al_up(y.act + actb, 1024);
+    y.qring = y.fc1a + 256u * (uint32_t)(pass_positions(L) * C);           // 128 slots x positions x C BF16
+    y.rec = y.qring + (uint32_t)kSPC * cap * 8;
+    y.part = al_up(y.rec + kSPC * 4 * 4, 16);
+    y.prm = y.part + 8 * kSPC * 8;
+    const uint32_t prm_floats = (uint32_t)(L * C + 4 * HN + 2);
+    y.slot = al_up(y.prm + prm_floats * 4, 16);
+    y.misc = y.slot + kSPC * 8 + 8 * kSPC * 4;
+    y.bars = al_up(y.misc + 160, 8);
+    y.total = y.bars + (2 * stages + 12) * 8;
+    return y;
+}
+
+// ------------------------------------------------------------------ cluster PTX
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `r` of the cluster
+__device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t r) {
+    uint32_t o;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(o) : "r"(a), "r"(r));
+    return o;
+}
+__device__ __forceinline__ void cl_st_v4(uint32_t a, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void cl_st_v2f(uint32_t a, float x, float y) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+__device__ __forceinline__ void cl_st_v2i(uint32_t a, int x, int y) {
+    asm volatile("st.shared::cluster.v2.u32 [%0], {%1,%2};" ::"r"(a), "r"(x), "r"(y) : "memory");
+}
+__device__ __forceinline__ void cl_arrive(uint32_t remote_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+}
+__device__ __forceinline__ bool cl_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on a phase of a barrier that other CTAs of the cluster arrive on.
+__device__ __noinline__ bool cl_wait(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
+                                     int32_t *status) {
+    if (cl_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (cl_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if ((int64_t)(gtimer() - t0) > limit) {
+            *abort_flag = 1;
+            atomicExch(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+// Wait for copies or MMAs this CTA started to land, also after an abort (they
+// write shared memory or TMEM that is released afterwards); bounded, silent.
+__device__ __noinline__ void drain_wait(uint32_t bar, uint32_t parity, int64_t limit) {
+    const uint64_t t0 = gtimer();
+    while (!cl_try(bar, parity) && (int64_t)(gtimer() - t0) < limit) {
+    }
+}
+// Arrive (once) on the barrier at this offset in every CTA of `mask` when this
+// thread's earlier tcgen05 operations have completed.
+__device__ __forceinline__ void commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     bar),
+                 "h"(mask)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_cluster() {
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Byte offset of element k of row n in a K-major operand of `rows` rows laid
+// out as 64-element panels with the 128-byte swizzle (BF16).
+__device__ __forceinline__ uint32_t sw_off(int n, int k, int rows) {
+    return (uint32_t)(k >> 6) * (uint32_t)rows * 128u + (uint32_t)n * 128u +
+           ((uint32_t)(((k >> 3) & 7) ^ (n & 7)) << 4) + ((uint32_t)(k & 7) << 1);
+}
+
+// Cluster extent from the four CTAs' (longest queue + 1, live slots).
+__device__ __forceinline__ void read_ext(const int2 *ext_in, int b, int &E, int &AL) {
+    E = 0;
+    AL = 0;
+    for (int r = 0; r < kCS; r++) {
+        const volatile int *v = reinterpret_cast<const volatile int *>(&ext_in[b * kCS + r]);
+        E = max(E, v[0]);
+        AL += v[1];
+    }
+}
+__device__ __forceinline__ int positions_of(int E, int L, int rows_n) {
+    const int span = 1 << L;
+    return max(1, min((E + span - 1) / span, rows_n));
+}
+
+__global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_constant__ CArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int L = a.L, C = a.C, HN = a.H / kCS, S = a.stages, cap = a.cap, PM = pass_positions(L);
+    const CLay y = c_layout(L, C, a.H, cap, S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cl_rank();
+    const int slot0 = (int)(blockIdx.x / kCS) * (kCS * kSPC) + (int)rank * kSPC;
+    const StepArgs *A = a.A;
+    const int64_t lim = a.spin_ns;
+    const int64_t drain_ns = lim > 200000000 ? lim : 200000000;   // 0.2 s at least
+
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + y.bars);
+    auto bar = [&](int i) { return smem_u32(&bars[i]); };
+    const int B_ACT = 2 * S, B_D = 2 * S + 1, B_FULL = 2 * S + 2, B_EMPTY = 2 * S + 3, B_DFC = 2 * S + 4,
+              B_DFCE = 2 * S + 5, B_PART = 2 * S + 6, B_EXT = 2 * S + 7, B_FIN = 2 * S + 9;
+    float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
+    float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
+    float *s_w2f = s_fb + HN, *s_w2e = s_w2f + HN;          // FC2 rows for those neurons
+    float *s_Se = s_w2e + HN;                                // [HN] S[e] of the current step
+    float *s_b2 = s_Se + HN;
+    int64_t *s_o = reinterpret_cast<int64_t *>(sm + y.slot);
+    int32_t *s_b = reinterpret_cast<int32_t *>(s_o + kSPC), *s_n = s_b + kSPC, *s_p = s_n + kSPC,
+            *s_tick = s_p + kSPC, *s_qs = s_tick + kSPC, *s_ql = s_qs + kSPC, *s_ev = s_ql + kSPC,
+            *s_al = s_ev + kSPC;
+    uint64_t *qring = reinterpret_cast<uint64_t *>(sm + y.qring);
+    uint32_t *recb = reinterpret_cast<uint32_t *>(sm + y.rec);   // [slot][position & 3]
+    float2 *part = reinterpret_cast<float2 *>(sm + y.part);     // [source CTA * 2 + half][slot]
+    int2 *ext_in = reinterpret_cast<int2 *>(sm + y.misc);       // [step parity][source CTA]
+    volatile int *ctl = reinterpret_cast<volatile int *>(sm + y.misc + 128);   // positions, stop
+    volatile int *abort_f = ctl + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + y.misc + 148);
+    int *cnt = reinterpret_cast<int *>(sm + y.misc + 152);      // weight panels issued, consumed
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(bar(s), 1);
+            mbar_init(bar(S + s), 1);
+        }
+        mbar_init(bar(B_ACT), 8);
+        mbar_init(bar(B_D), 1);
+        mbar_init(bar(B_FULL), kCS * 8);
+        mbar_init(bar(B_EMPTY), kCS);
+        mbar_init(bar(B_DFC), 1);
+        mbar_init(bar(B_DFCE), 8);
+        mbar_init(bar(B_PART), kCS * 2);
+        mbar_init(bar(B_EXT), kCS);
+        mbar_init(bar(B_EXT + 1), kCS);
+        mbar_init(bar(B_FIN), 1);
+        *abort_f = 0;
+        cnt[0] = cnt[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // constants of this CTA's share
+    for (int i = threadIdx.x; i < L * C; i += blockDim.x) s_cb[i] = a.cbias[i / C][i % C];
+    for (int j = threadIdx.x; j < HN; j += blockDim.x) {
+        const int nn = (int)rank * HN + j;
+        s_fb[j] = a.fbias[nn];
+        s_w2f[j] = a.w2[nn];
+        s_w2e[j] = a.w2[a.H + nn];
+    }
+    if (threadIdx.x < 2) s_b2[threadIdx.x] = a.b2[threadIdx.x];
+    // slot state (workers: warp w takes slots w-2, w+6, w+14, w+22)
+    if (warp >= 2) {
+        const int n_act = min(*A->n_active, A->n_sub);
+        for (int j = 0; j < 4; j++) {
+            const int s = (warp - 2) + 8 * j, g = slot0 + s;
+            int b = -1;
+            int64_t o = 0;
+            int n = 0, p = 0;
+            if (g < n_act) {
+                b = A->active[g];
+                o = A->offsets[b];
+                n = (int)(A->offsets[b + 1] - o);
+                p = A->pos[b];
+                for (int i = lane; i < cap; i += 32) qring[s * cap + i] = A->ring[(size_t)b * cap + i];
+            }
+            if (lane == 0) {
+                s_b[s] = b;
+                s_o[s] = o;
+                s_n[s] = n;
+                s_p[s] = p;
+                s_tick[s] = b >= 0 ? A->tick[b] : 0;
+                s_qs[s] = b >= 0 ? A->qstart[b] : 0;
+                s_ql[s] = b >= 0 ? A->qlen[b] : 0;
+                s_ev[s] = b >= 0 ? A->evict[b] : 0;
+                s_al[s] = (b >= 0 && p < n) ? 1 : 0;
+                if (p < n) recb[s * 4 + (p & 3)] = A->records[o + p];
+                if (p + 1 < n) recb[s * 4 + ((p + 1) & 3)] = A->records[o + p + 1];
+            }
+        }
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    cluster_sync_all();   // every CTA's barriers are initialised before anyone arrives remotely
+
+    const uint32_t ring0 = smem_u32(sm + y.ring), act0 = smem_u32(sm + y.act), fc0 = smem_u32(sm + y.fc1a);
+    // TMEM columns: layer 0 tiles at 0 (two tiles of C), odd layers at 256, even layers >= 2 at 0, FC1 at 384
+    auto dcol = [&](int l) -> uint32_t { return l == 0 ? 0u : ((l & 1) ? 256u : 0u); };
+    auto rows_of = [&](int l, int P) { return P * (1 << (L - 1 - l)) * kSPC; };   // layer l's A rows
+    auto tiles_of = [&](int l, int P) { return (rows_of(l, P) + 127) / 128; };
+    auto panels_of = [&](int l) { return l == 0 ? 2 : C / 32; };                   // K / 64
+    if (warp == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            auto load = [&](const CUtensorMap *m, int x, int yy, uint32_t bytes) {
+                const int s = it % S;
+                if (!mbar_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status)) {
+                    ok = false;
+                    return;
+                }
+                mbar_expect_tx(bar(s), bytes);
+                tma_load_2d(ring0 + s * kStage, m, bar(s), x, yy);
+                it++;
+            };
+            auto conv_panels = [&]() {   // every conv layer's weights, in consumption order
+                for (int l = 0; l < L && ok; l++)
+                    for (int pi = 0; pi < panels_of(l) && ok; pi++) load(&a.tW[l], pi * 64, 0, (uint32_t)C * 128u);
+            };
+            if (a.n_steps > 0) conv_panels();
+            for (int64_t t = 0; t < a.n_steps && ok; t++) {
+                if (!cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status)) break;
+                int E, AL;
+                read_ext(ext_in, (int)(t & 1), E, AL);
+                if (AL == 0) break;
+                const int eL = positions_of(E, L, a.rows_n);
+                for (int q0 = 0; q0 < eL && ok; q0 += PM) {
+                    const int P = min(PM, eL - q0);
+                    if (q0 > 0) conv_panels();
+                    for (int pi = 0; pi < P * C / 64 && ok; pi++)
+                        load(&a.tF, q0 * C + pi * 64, (int)rank * HN, (uint32_t)HN * 128u);
+                }
+                if (t + 1 < a.n_steps) conv_panels();   // the next step's first pass, before its extent is known
+            }
+            cnt[0] = it;
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int it = 0, act_uses = 0;
+            int64_t R = 0;
+            bool ok = true;
+            auto take = [&](int &s) -> bool {   // next weight panel
+                s = it % S;
+                const uint64_t tw = a.prof ? gtimer() : 0;
+                if (!mbar_wait(bar(s), (uint32_t)(it / S) & 1u, lim, abort_f, a.status)) return false;
+                if (a.prof && blockIdx.x == 0) a.prof[17] += gtimer() - tw;
+                tc_fence_after();
+                return true;
+            };
+            for (int64_t t = 0; t < a.n_steps && ok; t++) {
+                if (!cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status)) break;
+                int E, AL;
+                read_ext(ext_in, (int)(t & 1), E, AL);
+                if (AL == 0) break;
+                const int eL = positions_of(E, L, a.rows_n);
+                for (int q0 = 0; q0 < eL && ok; q0 += PM) {
+                    const int P = min(PM, eL - q0);
+                    for (int l = 0; l < L && ok; l++) {
+                        uint64_t tw = a.prof ? gtimer() : 0;
+                        if (!mbar_wait(bar(B_ACT), (uint32_t)act_uses & 1u, lim, abort_f, a.status)) { ok = false; break; }
+                        if (a.prof && blockIdx.x == 0) a.prof[16] += gtimer() - tw;
+                        act_uses++;
+                        tc_fence_after();
+                        fence_async_smem();
+                        const int T = tiles_of(l, P);
+                        const uint32_t ID = idesc_rt(C, false);
+                        for (int pi = 0; pi < panels_of(l); pi++, it++) {
+                            int s;
+                            if (!take(s)) { ok = false; break; }
+                            const uint64_t bd = sdesc(ring0 + s * kStage);
+                            for (int tt = 0; tt < T; tt++) {
+                                const uint64_t ad = sdesc(act0 + (uint32_t)(pi * T + tt) * 16384u);
+                                const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
+#pragma unroll
+                                for (int k = 0; k < 4; k++)
+                                    umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
+                            }
+                            umma_commit(bar(S + s));
+                        }
+                        if (ok) umma_commit(bar(B_D));
+                    }
+                    if (!ok) break;
+                    // FC1 over this pass's positions: every CTA's rows of them must be in
+                    uint64_t tw = a.prof ? gtimer() : 0;
+                    if (!cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status)) break;
+                    if (a.prof && blockIdx.x == 0) a.prof[18] += gtimer() - tw;
+                    fence_async_smem();
+                    tc_fence_after();
+                    if (q0 == 0 && t > 0) {
+                        if (!mbar_wait(bar(B_DFCE), (uint32_t)(t - 1) & 1u, lim, abort_f, a.status)) break;
+                        tc_fence_after();
+                    }
+                    const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
+                    for (int pi = 0; pi < P * C / 64; pi++, it++) {
+                        int s;
+                        if (!take(s)) { ok = false; break; }
+                        const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u), bd = sdesc(ring0 + s * kStage);
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (q0 | pi | k) != 0 ? 1u : 0u);
+                        umma_commit(bar(S + s));
+                    }
+                    if (!ok) break;
+                    commit_mc(bar(B_EMPTY), (uint16_t)((1u << kCS) - 1u));
+                    R++;
+                }
+                if (ok) umma_commit(bar(B_DFC));
+            }
+            cnt[1] = it;
+            umma_commit(bar(B_FIN));   // every MMA of this thread done before TMEM is released
+            drain_wait(bar(B_FIN), 0u, drain_ns);
+        }
+        __syncwarp();
+    } else {
+        // ---------------------------------------------------------------- workers
+        const int wi = warp - 2, qd = warp & 3, half = wi >> 2, tid = threadIdx.x - 64;
+        int d_uses = 0;
+        int64_t R = 0;
+        const StepArgs &As = *A;
+        const int RW = As.retire_width, strict = As.strict;
+        const bool prof = a.prof && blockIdx.x == 0 && tid == 0;
+        uint64_t tp = prof ? gtimer() : 0;
+        auto mark = [&](int k) {
+            if (prof) {
+                const uint64_t tn = gtimer();
+                a.prof[k] += tn - tp;
+                tp = tn;
+            }
+        };
+        // extent of this CTA's slots (longest queue + 1) and live count, to every CTA of the cluster
+        auto send_ext = [&](int nb) {   // warp 2 only
+            int mx = 0, al = 0;
+            if (s_al[lane]) { mx = s_ql[lane] + 1; al = 1; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                al += __shfl_xor_sync(0xffffffffu, al, o);
+            }
+            if (lane < kCS) {   // one lane per destination CTA: the release arrives overlap
+                cl_st_v2i(cl_map(smem_u32(&ext_in[nb * kCS + rank]), (uint32_t)lane), mx, al);
+                cl_arrive(cl_map(bar(B_EXT + nb), (uint32_t)lane));
+            }
+        };
+        if (wi == 0) send_ext(0);
+        for (int64_t t = 0; t < a.n_steps; t++) {
+            if (tid == 0) {
+                const bool ok = cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status);
+                int E, AL;
+                read_ext(ext_in, (int)(t & 1), E, AL);
+                ctl[0] = positions_of(E, L, a.rows_n);
+                ctl[1] = (!ok || AL == 0 || *abort_f) ? 1 : 0;
+            }
+            workers_sync();
+            const int eL = ctl[0];
+            if (ctl[1]) break;
+            mark(0);
+            if (prof) { a.prof[14] += 1; a.prof[15] += (unsigned long long)eL; }
+            if (tid >= 128 && tid < 128 + HN) {   // S[e] for this CTA's neurons, needed by the FC1 epilogue
+                cp_async4(smem_u32(&s_Se[tid - 128]), a.fc1_const + (size_t)eL * a.H + (int)rank * HN + (tid - 128));
+                cp_commit();
+            }
+            for (int q0 = 0; q0 < eL; q0 += PM) {
+                const int P = min(PM, eL - q0), T0 = tiles_of(0, P);
+                // feature rows of the pass: layer-0 A row (pair, slot), K = the pair's two rows
+                for (int f = tid; f < P * (1 << L) * kSPC; f += kWk) {
+                    const int s = f & 31, rr = f >> 5, r = q0 * (1 << L) + rr;
+                    const int m = (rr >> 1) * kSPC + s;
+                    uint4 ch[8];
+                    const int ql = s_ql[s];
+                    if (s_al[s] && r <= ql) {
+                        const uint32_t cur = recb[s * 4 + (s_p[s] & 3)];
+                        if (r == 0) {
+                            row_chunks_bf16(cur, cur, false, 0, 0u, ch);
+                        } else {
+                            int idx = s_qs[s] + ql - r;
+                            if (idx >= cap) idx -= cap;
+                            const uint64_t ent = qring[s * cap + idx];
+                            row_chunks_bf16(entry_rec(ent), cur, true, s_tick[s] - (int32_t)entry_tick(ent),
+                                            entry_e(ent), ch);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; j++) ch[j] = make_uint4(0, 0, 0, 0);
+                    }
+                    uint8_t *dst = sm + y.act + (uint32_t)(rr & 1) * (uint32_t)(T0 * 16384) + (uint32_t)m * 128u;
+#pragma unroll
+                    for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(dst + ((j ^ (m & 7)) << 4)) = ch[j];
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(B_ACT));
+                mark(1);
+                for (int l = 0; l < L; l++) {
+                    const bool last = l == L - 1;
+                    bool ok = mbar_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status);
+                    d_uses++;
+                    if (last && R >= 1 && ok)   // every CTA has consumed the previous pass's exchanged rows
+                        ok = cl_wait(bar(B_EMPTY), (uint32_t)((R - 1) & 1), lim, abort_f, a.status);
+                    ok = __all_sync(0xffffffffu, ok);
+                    tc_fence_after();
+                    mark(2 + 2 * l);
+                    const int T = tiles_of(l, P), Rl = rows_of(l, P), Tn = last ? 0 : tiles_of(l + 1, P);
+                    for (int tt = 0; tt < T && ok; tt++) {
+                        const int m = tt * 128 + qd * 32 + lane;   // this lane's row of the tile
+                        if (tt * 128 + qd * 32 >= Rl) continue;    // warp-uniform: rows past the pass
+                        const int p = m >> 5, s = m & 31;
+                        for (int cb = half * (C / 2); cb < (half + 1) * (C / 2); cb += 32) {
+                            uint32_t r32[32];
+                            tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + cb), r32);
+                            uint32_t w[16];
+#pragma unroll
+                            for (int j = 0; j < 16; j++) {
+                                const float v0 = fmaxf(__uint_as_float(r32[2 * j]) + s_cb[l * C + cb + 2 * j], 0.f);
+                                const float v1 = fmaxf(__uint_as_float(r32[2 * j + 1]) + s_cb[l * C + cb + 2 * j + 1], 0.f);
+                                __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
+                                w[j] = *reinterpret_cast<uint32_t *>(&b2);
+                            }
+                            int row, k0;
+                            uint32_t base, pstride;
+                            if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
+                                row = ((p >> 1) << 5) + s;
+                                k0 = (p & 1) * C + cb;
+                                base = y.act;
+                                pstride = (uint32_t)Tn * 16384u;
+                            } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
+                                row = (int)rank * kSPC + s;
+                                k0 = p * C + cb;
+                                base = y.fc1a;
+                                pstride = 16384u;
+                            }
+#pragma unroll
+                            for (int j = 0; j < 4; j++) {
+                                const int k = k0 + 8 * j;
+                                const uint32_t off = base + (uint32_t)(k >> 6) * pstride + (uint32_t)row * 128u +
+                                                     ((uint32_t)(((k >> 3) & 7) ^ (row & 7)) << 4);
+                                *reinterpret_cast<uint4 *>(sm + off) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                            }
+                        }
+                    }
+                    if (!last) {
+                        fence_async_smem();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(bar(B_ACT));
+                    } else {
+                        if (tid >= 128 && tid < 128 + HN) cp_wait<0>();   // S[e] landed (read after the barrier)
+                        workers_sync();   // this CTA's rows of the pass are all in its own buffer
+                        const int n16 = P * C / 64 * 256;   // 16-byte chunks of this CTA's 32 rows
+                        for (int i = tid; i < n16; i += kWk) {
+                            const uint32_t off = (uint32_t)(i >> 8) * 16384u + rank * (kSPC * 128) + (uint32_t)(i & 255) * 16u;
+                            const uint4 v = *reinterpret_cast<const uint4 *>(sm + y.fc1a + off);
+                            for (int r = 1; r < kCS; r++) cl_st_v4(cl_map(fc0 + off, (rank + r) % kCS), v);
+                        }
+                        fence_async_cluster();
+                        fence_async_smem();
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane < kCS) cl_arrive(cl_map(bar(B_FULL), (uint32_t)lane));
+                        R++;
+                    }
+                    mark(3 + 2 * l);
+                }
+            }
+            // FC1 epilogue: ReLU(FC1 + bias + S[e]) folded into FC2 partials per slot
+            {
+                bool ok = mbar_wait(bar(B_DFC), (uint32_t)(t & 1), lim, abort_f, a.status);
+                ok = __all_sync(0xffffffffu, ok);
+                tc_fence_after();
+                mark(8);
+                float pf = 0.f, pe = 0.f;
+                if (ok) {
+                    const int cols = HN / 2, j0 = half * cols;
+                    for (int cc = 0; cc < cols; cc += 32) {
+                        uint32_t r32[32];
+                        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)(j0 + cc), r32);
+#pragma unroll
+                        for (int jj = 0; jj < 32; jj++) {
+                            const int j = j0 + cc + jj;
+                            const float v = fmaxf(__uint_as_float(r32[jj]) + s_fb[j] + s_Se[j], 0.f);
+                            pf = fmaf(v, s_w2f[j], pf);
+                            pe = fmaf(v, s_w2e[j], pe);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar(B_DFCE));
+                // slot qd * 32 + lane of the cluster belongs to CTA qd, where it is slot `lane`
+                cl_st_v2f(cl_map(smem_u32(&part[((int)rank * 2 + half) * kSPC + lane]), (uint32_t)qd), pf, pe);
+                __syncwarp();
+                if (lane == 0) cl_arrive(cl_map(bar(B_PART), (uint32_t)qd));
+                mark(9);
+            }
+            // head, clock and queue update, drain: one thread per slot (warp 2)
+            if (wi == 0) {
+                bool ok = cl_wait(bar(B_PART), (uint32_t)(t & 1), lim, abort_f, a.status);
+                ok = __all_sync(0xffffffffu, ok);
+                mark(10);
+                const int s = lane;
+                if (ok && s_al[s]) {
+                    const int64_t o = s_o[s];
+                    const int n = s_n[s];
+                    int p = s_p[s];
+                    float zf = s_b2[0], ze = s_b2[1];
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const float2 v = part[i * kSPC + s];
+                        zf += v.x;
+                        ze += v.y;
+                    }
+                    const float yf = softplus_f(zf), ye = softplus_f(ze);
+                    const int64_t gi = o + p;
+                    uint32_t F, E;
+                    if (As.replay) {
+                        F = As.replay[2 * gi];
+                        E = As.replay[2 * gi + 1];
+                    } else {
+                        F = to_cycles(yf);
+                        E = to_cycles(ye);
+                    }
+                    if (As.pre_log) { As.pre_log[2 * gi] = yf; As.pre_log[2 * gi + 1] = ye; }
+                    if (As.lat_log) { As.lat_log[2 * gi] = (uint8_t)F; As.lat_log[2 * gi + 1] = (uint8_t)E; }
+                    uint64_t *qr = qring + s * cap;
+                    int qs = s_qs[s], ql = s_ql[s], ev = 0;
+                    int32_t tick = s_tick[s] + (int32_t)F;
+                    // in-order retire from the oldest, at most RW * F entries
+                    auto retire = [&](int lim_n) {
+                        int k = 0;
+                        while (k < lim_n) {
+                            int idx = qs + k;
+                            if (idx >= cap) idx -= cap;
+                            const uint64_t v = qr[idx];
+                            const int32_t res = tick - (int32_t)entry_tick(v), e = (int32_t)entry_e(v);
+                            if (strict ? res <= e : res < e) break;
+                            k++;
+                        }
+                        qs += k;
+                        if (qs >= cap) qs -= cap;
+                        ql -= k;
+                    };
+                    retire(min(ql, RW * (int)F));
+                    if (ql == cap) {   // full: drop the oldest
+                        qs = (qs + 1 == cap) ? 0 : qs + 1;
+                        ql--;
+                        ev = 1;
+                    }
+                    {
+                        int idx = qs + ql;
+                        if (idx >= cap) idx -= cap;
+                        qr[idx] = pack_entry(recb[s * 4 + (p & 3)], E, (uint32_t)tick);
+                    }
+                    ql++;
+                    p++;
+                    if (p == n) {   // drain: Delta of Eq. 1
+                        while (ql > 0) {
+                            tick += 1;
+                            retire(min(ql, RW));
+                        }
+                        As.cycles_out[s_b[s]] = tick;
+                    }
+                    s_tick[s] = tick;
+                    s_p[s] = p;
+                    s_qs[s] = qs;
+                    s_ql[s] = ql;
+                    s_ev[s] += ev;
+                    s_al[s] = p < n ? 1 : 0;
+                    if (p + 1 < n)   // record of the position two steps ahead
+                        cp_async4(smem_u32(&recb[s * 4 + ((p + 1) & 3)]), As.records + o + p + 1);
+                }
+                cp_commit();      // one group per step, empty or not
+                cp_wait<1>();     // the record fetched one step ago has landed
+                mark(11);
+                __syncwarp();
+                send_ext((int)((t + 1) & 1));
+                mark(12);
+            }
+        }
+        // state back to device memory (resumable), outstanding record copies drained; the
+        // barrier orders the last step's head (warp 2) before the other warps read its state
+        cp_wait<0>();
+        workers_sync();
+        for (int j = 0; j < 4; j++) {
+            const int s = wi + 8 * j, b = s_b[s];
+            if (b < 0) continue;
+            for (int i = lane; i < cap; i += 32) A->ring[(size_t)b * cap + i] = qring[s * cap + i];
+            if (lane == 0) {
+                A->tick[b] = s_tick[s];
+                A->pos[b] = s_p[s];
+                A->qstart[b] = s_qs[s];
+                A->qlen[b] = s_ql[s];
+                A->evict[b] = s_ev[s];
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane == 0) {   // weight panels issued but never consumed (early exit) land first
+        for (int it = cnt[1]; it < cnt[0]; it++) drain_wait(bar(it % S), (uint32_t)(it / S) & 1u, drain_ns);
+    }
+    __syncthreads();
+    cluster_sync_all();   // no peer writes into this CTA's shared memory any more
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+// Shapes this kernel handles: BF16; 2 or 3 conv layers of 64 or 128 channels;
+// FC1 width 256 or 512 (a quarter per CTA); queue capacity below 256.
+bool cluster_eligible(const simnet_ctx *c, std::string &why) {
+    const simnet_config &k = c->cfg;
+    if (k.precision != SIMNET_BF16) { why = "not BF16"; return false; }
+    if (k.n_conv < 2 || k.n_conv > 3) { why = "conv depth"; return false; }
+    if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
+    if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }
+    if (c->cap > 255 || c->rows_n < 1) { why = "window"; return false; }
+    const CLay y = c_layout(k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2);
+    if (y.total + 1024 > 232448) { why = "shared memory"; return false; }
+    return true;
+}
+
+bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::string &why) {
+    if (!cluster_eligible(c, why)) return false;
+    const simnet_config &k = c->cfg;
+    CArgs a;
+    memset(&a, 0, sizeof a);
+    a.L = k.n_conv;
+    a.C = k.conv_channels;
+    a.H = k.fc_hidden;
+    a.cap = c->cap;
+    a.rows_n = c->rows_n;
+    for (int l = 0; l < a.L; l++) {
+        if (!encode_map_2d(a.tW[l], SIMNET_BF16, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, 64, (uint32_t)a.C, why))
+            return false;
+        a.cbias[l] = c->bias[l];
+    }
+    if (!encode_map_2d(a.tF, SIMNET_BF16, c->Wl[a.L], (uint64_t)c->fc1_in, (uint64_t)a.H, 64, (uint32_t)(a.H / kCS), why))
+        return false;
+    a.fbias = c->bias[a.L];
+    a.w2 = c->w2;
+    a.b2 = c->b2;
+    a.fc1_const = c->fc1_const;
+    a.A = c->d_args;
+    a.status = c->status;
+    a.prof = c->phase_on ? c->phase_ns : nullptr;
+    a.n_steps = n_steps;
+    a.spin_ns = c->cfg.spin_limit_ns;
+    int stages = 6;
+    while (stages > 2 && c_layout(a.L, a.C, a.H, a.cap, stages).total + 1024 > 232448) stages--;
+    a.stages = stages;
+    const size_t smem = c_layout(a.L, a.C, a.H, a.cap, stages).total + 1024;
+    cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
+    const int n_clusters = (B + kCS * kSPC - 1) / (kCS * kSPC);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_clusters * kCS);
+    cfg.blockDim = dim3(kCThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kCS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, cluster_kernel, a);
+    if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
+    return true;
+}
+
+}  // namespace simnet

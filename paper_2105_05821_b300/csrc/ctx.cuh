@@ -109,10 +109,15 @@ struct simnet_ctx {
     // the padding-constant table fc1_const no longer matches the weights (set by
     // on-device weight updates; rebuilt before the next persistent run)
     bool const_stale = false;
+    int path = SIMNET_PATH_NONE;   // kernel path of the last simulate call
 };
 
 namespace simnet {
 bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaStream_t s, std::string &why);
+// Cluster kernel (cluster.cu): every simulate step without grid-wide barriers,
+// for the shapes cluster_eligible accepts.
+bool cluster_eligible(const simnet_ctx *c, std::string &why);
+bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::string &why);
 }
 
 // Training buffers for n windows (and the optimiser state, once); train.cu.

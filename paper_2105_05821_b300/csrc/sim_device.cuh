@@ -71,15 +71,15 @@ __device__ __forceinline__ void row_tail(uint32_t rec, uint32_t cur, bool ctx, i
 template <typename T> __device__ __forceinline__ void write_row(T *dst, uint32_t rec, uint32_t cur, bool ctx,
                                                                int32_t res, uint32_t e);
 
-template <> __device__ __forceinline__ void write_row<__nv_bfloat16>(__nv_bfloat16 *dst, uint32_t rec, uint32_t cur,
-                                                                     bool ctx, int32_t res, uint32_t e) {
+// A BF16 row as its eight 16-byte chunks (channels 8j .. 8j+7 in chunk j).
+__device__ __forceinline__ void row_chunks_bf16(uint32_t rec, uint32_t cur, bool ctx, int32_t res, uint32_t e,
+                                                uint4 (&o)[8]) {
     const uint32_t op = rec & 31u;
     uint32_t w[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) w[i] = (op >> 1) == (uint32_t)i ? ((op & 1u) ? 0x3F800000u : 0x00003F80u) : 0u;
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
-    for (int i = 0; i < 4; i++) d4[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    for (int i = 0; i < 4; i++) o[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
     float t[32];
     row_tail(rec, cur, ctx, res, e, t);
 #pragma unroll
@@ -88,7 +88,16 @@ template <> __device__ __forceinline__ void write_row<__nv_bfloat16>(__nv_bfloat
         w[i] = *reinterpret_cast<uint32_t *>(&b);
     }
 #pragma unroll
-    for (int i = 0; i < 4; i++) d4[4 + i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    for (int i = 0; i < 4; i++) o[4 + i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+}
+
+template <> __device__ __forceinline__ void write_row<__nv_bfloat16>(__nv_bfloat16 *dst, uint32_t rec, uint32_t cur,
+                                                                     bool ctx, int32_t res, uint32_t e) {
+    uint4 o[8];
+    row_chunks_bf16(rec, cur, ctx, res, e, o);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 8; i++) d4[i] = o[i];
 }
 
 template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4m3 *dst, uint32_t rec, uint32_t cur,

@@ -712,8 +712,18 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
     }
     c->phase_valid = false;
     const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE);
+    std::string why_not_cluster;
     if (n_steps <= 0) {
         launches = resume ? 0 : 1;
+    } else if (persistent && !(c->cfg.flags & SIMNET_FLAG_NO_CLUSTER) && cluster_eligible(c, why_not_cluster)) {
+        // clusters own their sub-traces for the whole call: no grid-wide barriers
+        c->phase_on = timed;
+        if (timed) CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
+        c->phase_valid = timed;
+        std::string why;
+        if (!launch_cluster(c, B, n_steps, s, why)) return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
+        launches = resume ? 1 : 2;
+        c->path = SIMNET_PATH_CLUSTER;
     } else if (persistent) {
         // one cooperative kernel runs every step; its phases are timed by CTA 0 on request
         c->phase_on = timed;
@@ -726,7 +736,9 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
             return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
         launches = resume ? 1 : 2;
         c->phase_valid = timed;
+        c->path = SIMNET_PATH_PERSISTENT;
     } else {
+        c->path = SIMNET_PATH_LAYERWISE;
         enqueue_gather(c, B, s, false, timed ? &kt : nullptr);
         if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
             for (int64_t i = 0; i < n_steps; i++) {
@@ -811,6 +823,8 @@ extern "C" simnet_status simnet_kernel_times(simnet_ctx *c, float *ms_out, int64
     if (!c) return SIMNET_EINVAL;
     if (!ms_out || !launches_out || n_kinds < 1 || n_kinds > SIMNET_KERNEL_KINDS)
         return fail(c, SIMNET_EINVAL, "kernel_times: bad arguments");
+    if (c->phase_valid && c->path == SIMNET_PATH_CLUSTER)
+        return fail(c, SIMNET_ESTATE, "kernel_times: the cluster kernel reports phases through simnet_phase_detail");
     if (c->phase_valid) {  // persistent kernel: per-phase times measured by CTA 0 (globaltimer)
         unsigned long long ns[SIMNET_KERNEL_KINDS], cnt[SIMNET_KERNEL_KINDS];
         CK(cudaDeviceSynchronize());
@@ -831,12 +845,15 @@ extern "C" simnet_status simnet_kernel_times(simnet_ctx *c, float *ms_out, int64
     return SIMNET_OK;
 }
 
+extern "C" int32_t simnet_kernel_path(const simnet_ctx *c) { return c ? c->path : -1; }
+
 extern "C" simnet_status simnet_phase_detail(simnet_ctx *c, uint64_t *out, int32_t n) {
     if (!c) return SIMNET_EINVAL;
     if (!out || n < 1 || n > 48) return fail(c, SIMNET_EINVAL, "phase_detail: bad arguments");
     if (!c->phase_valid) return fail(c, SIMNET_ESTATE, "phase_detail: no timed persistent run");
     CK(cudaDeviceSynchronize());
-    CK(cudaMemcpy(out, c->phase_ns + 16, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const int off = c->path == SIMNET_PATH_CLUSTER ? 0 : 16;
+    CK(cudaMemcpy(out, c->phase_ns + off, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     return SIMNET_OK;
 }
 

@@ -24,6 +24,8 @@ FLAG_NO_GRAPH = 0x2
 FLAG_KERNEL_EVENTS = 0x4
 FLAG_NO_PDL = 0x8
 FLAG_LAYERWISE = 0x10
+FLAG_NO_CLUSTER = 0x20
+PATHS = {0: "none", 1: "layerwise", 2: "persistent", 3: "cluster"}
 KERNEL_KINDS = 12
 KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE", 6: "EUNSUPPORTED"}
@@ -33,7 +35,7 @@ EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_e
            "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes",
            "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
            "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune",
-           "simnet_simulate_steps", "simnet_state_save", "simnet_state_load"]
+           "simnet_simulate_steps", "simnet_state_save", "simnet_state_load", "simnet_kernel_path"]
 STATE_KINDS = {"sim": 0, "train": 1}
 
 
@@ -120,6 +122,8 @@ def lib() -> C.CDLL:
         L.simnet_state_save.argtypes = [P, C.c_int32, P, C.POINTER(C.c_size_t), P]
         L.simnet_state_load.restype = C.c_int
         L.simnet_state_load.argtypes = [P, C.c_int32, P, C.c_size_t, P]
+        L.simnet_kernel_path.restype = C.c_int32
+        L.simnet_kernel_path.argtypes = [P]
         _lib = L
     return _lib
 
@@ -152,12 +156,13 @@ class Simnet:
     def __init__(self, window: int, n_conv: int, channels: int, hidden: int,
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
-                 pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0):
+                 pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0,
+                 cluster: bool = True):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
-                 | (0 if persistent else FLAG_LAYERWISE))
+                 | (0 if persistent else FLAG_LAYERWISE) | (0 if cluster else FLAG_NO_CLUSTER))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, barrier_limit_us,
                             spin_limit_ns)
         self.window = window
@@ -231,6 +236,11 @@ class Simnet:
         """Import a state written by state_save (resume with simulate(..., resume=True))."""
         buf = C.create_string_buffer(bytes(data), len(data))
         self._check(lib().simnet_state_load(self._h, STATE_KINDS[kind], buf, len(data), _stream(stream)))
+
+    @property
+    def kernel_path(self) -> str:
+        """Kernel path of the last simulate call: layerwise, persistent or cluster."""
+        return PATHS.get(int(lib().simnet_kernel_path(self._h)), "none")
 
     def phase_detail(self, n_layers):
         """Per GEMM layer: summed ns to first data, last MMA, epilogue done, barrier passed (CTA 0)."""

@@ -22,7 +22,14 @@ pytestmark = pytest.mark.gpu
 
 # uneven lengths (compaction runs mid-trace), an empty and a one-instruction sub-trace
 LENGTHS = [0, 1, 37, 300, 41, 512, 90, 5, 260, 128, 64, 7, 1000, 3, 222, 99]
-MODES = [("fp32", False), ("bf16", True), ("bf16", False), ("fp8", True)]
+MODES = [("fp32", "layerwise"), ("bf16", "cluster"), ("bf16", "persistent"), ("bf16", "layerwise"),
+         ("fp8", "persistent")]
+
+
+def sim_for(arch, precision, mode, **kw):
+    sim, blob = make_sim(arch, precision, persistent=mode != "layerwise", cluster=mode == "cluster", **kw)
+    sim.mode = mode
+    return sim, blob
 
 
 def run(sim, rec, off, N, chunks=None, state_via=None):
@@ -52,10 +59,10 @@ def trace():
     return I.small_trace(LENGTHS, seed=11)
 
 
-@pytest.mark.parametrize("precision,persistent", MODES)
-def test_split_run_equals_unsplit(trace, precision, persistent):
+@pytest.mark.parametrize("precision,mode", MODES)
+def test_split_run_equals_unsplit(trace, precision, mode):
     arch = I.ARCH_MID
-    sim, blob = make_sim(arch, precision, seed=3, persistent=persistent)
+    sim, blob = sim_for(arch, precision, mode, seed=3)
     rec, off = to_dev(trace)
     N = trace.n_instructions
     c0, l0, p0, st0 = run(sim, rec, off, N)
@@ -65,19 +72,20 @@ def test_split_run_equals_unsplit(trace, precision, persistent):
     np.testing.assert_array_equal(p1.view(np.uint32), p0.view(np.uint32))
     assert st1.steps_done == max(LENGTHS) and st1.total_cycles == st0.total_cycles
     assert st1.evictions == st0.evictions
+    assert sim.kernel_path == mode
 
 
-@pytest.mark.parametrize("precision,persistent", [("fp32", False), ("bf16", True)])
-def test_saved_state_resumes_in_a_fresh_context(trace, precision, persistent):
+@pytest.mark.parametrize("precision,mode", [("fp32", "layerwise"), ("bf16", "cluster"), ("bf16", "persistent")])
+def test_saved_state_resumes_in_a_fresh_context(trace, precision, mode):
     arch = I.ARCH_SMALL(32)
-    sim, blob = make_sim(arch, precision, seed=5, persistent=persistent)
+    sim, blob = sim_for(arch, precision, mode, seed=5)
     rec, off = to_dev(trace)
     N = trace.n_instructions
     c0, l0, p0, _ = run(sim, rec, off, N)
 
     def move(old):
         data = old.state_save("sim")
-        new, _ = make_sim(arch, precision, blob=blob, persistent=persistent)
+        new, _ = sim_for(arch, precision, mode, blob=blob)
         new.state_load(data, "sim")
         old.close()
         return new
@@ -158,18 +166,19 @@ def test_training_state_round_trip(precision):
     assert np.mean(np.abs(wb - d.get_weights()) <= 1e-5 + 1e-4 * np.abs(wb)) < 0.9
 
 
-def test_bf16_padding_table_follows_device_weight_updates(trace):
+@pytest.mark.parametrize("mode", ["cluster", "persistent"])
+def test_bf16_padding_table_follows_device_weight_updates(trace, mode):
     """A BF16 context trained on the device simulates exactly as a fresh BF16
-    context loaded with the trained weights (the persistent kernel's table of
-    padding-row FC1 sums is rebuilt from the updated masters)."""
+    context loaded with the trained weights (the single-launch kernels' table
+    of padding-row FC1 sums is rebuilt from the updated masters)."""
     arch = I.ARCH_MID
     rec_t = I.make_records(3000, 4)
     w = Windows.from_labels(rec_t, I.toy_labels(rec_t))
-    a, _ = make_sim(arch, "bf16", seed=12)
+    a, _ = sim_for(arch, "bf16", mode, seed=12)
     gen = torch.Generator(device="cuda").manual_seed(3)
     for _ in range(5):
         a.train_step(w, torch.randint(0, len(w), (128,), device="cuda", generator=gen), 1e-2)
-    b, _ = make_sim(arch, "bf16", blob=a.get_weights())
+    b, _ = sim_for(arch, "bf16", mode, blob=a.get_weights())
     rec, off = to_dev(trace)
     N = trace.n_instructions
     ca, la, pa, _ = run(a, rec, off, N)

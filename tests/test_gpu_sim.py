@@ -22,13 +22,16 @@ FP32_LAT_TOL = 1e-3
 FP32_CPI_TOL = 1e-3
 
 
-def teacher_forced_check(arch, trace, precision, blob, lat_tol, rw=8, strict=False, graph=True, persistent=True):
+def teacher_forced_check(arch, trace, precision, blob, lat_tol, rw=8, strict=False, graph=True, persistent=True,
+                         cluster=True, path=None):
     cfg = oracle.Config.of(arch, retire_width=rw, retire_strict=strict)
     ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, logs=True)
     sim, _ = make_sim(arch, precision, blob=blob, retire_width=rw, strict=strict, graph=graph,
-                      persistent=persistent)
+                      persistent=persistent, cluster=cluster)
     # GPU replays the oracle's latencies: every integer must match
     g = run_gpu(sim, trace, replay=ref.lat)
+    if path is not None:
+        assert sim.kernel_path == path
     np.testing.assert_array_equal(g["cycles"], ref.cycles)
     np.testing.assert_array_equal(g["lat"], ref.lat)
     assert g["stats"].evictions == int(ref.evictions.sum())
@@ -109,13 +112,17 @@ def test_launch_modes_identical(precision):
         np.testing.assert_array_equal(r["cycles"], runs[0]["cycles"])
 
 
-@pytest.mark.parametrize("precision,tol", [("bf16", 5e-2), ("fp8", 0.6)])
+@pytest.mark.parametrize("precision,tol,kernel", [("bf16", 5e-2, "cluster"), ("bf16", 5e-2, "persistent"),
+                                                  ("fp8", 0.6, "persistent")])
 @pytest.mark.parametrize("case", ["c1", "ragged", "uneven", "c2arch"])
-def test_persistent_kernel_teacher_forced(precision, tol, case):
-    """The persistent kernel (padding-extent skipping, pair-major layout,
-    compaction inside the kernel) against the oracle: integer state bit-exact
-    under teacher forcing both ways, latencies within the precision's bound,
-    and close to the per-layer path on identical states."""
+def test_persistent_kernel_teacher_forced(precision, tol, kernel, case):
+    """The single-launch kernels against the oracle: the cluster kernel (slots
+    owned by clusters of 4 CTAs, state in shared memory, conv pyramid on chip)
+    and the grid-wide persistent kernel (padding-extent skipping, pair-major
+    layout, compaction inside the kernel).  Integer state bit-exact under
+    teacher forcing both ways, latencies within the precision's bound, and
+    close to the per-layer path on identical states.  The uneven case has 300
+    sub-traces: three clusters, the last one partly empty."""
     if case == "c1":
         w = I.WORKLOADS["c1"]
         arch, trace, blob = w.arch, I.make_trace(w), I.workload_weights(w)
@@ -129,11 +136,13 @@ def test_persistent_kernel_teacher_forced(precision, tol, case):
             np.clip(np.rint(np.exp(np.random.default_rng(4).normal(np.log(60), 0.8, 300))), 1, 400).astype(int).tolist()
         trace = I.small_trace(lengths, seed=len(lengths))
         blob = I.workload_weights(I.Workload("u", arch, 1, 1, seed=4))
-    ref, _, err = teacher_forced_check(arch, trace, precision, blob, tol, persistent=True)
+    cl = kernel == "cluster"
+    ref, _, err = teacher_forced_check(arch, trace, precision, blob, tol, persistent=True, cluster=cl, path=kernel)
     lw, _ = make_sim(arch, precision, blob=blob, persistent=False)
     g = run_gpu(lw, trace, replay=ref.lat)
-    ps, _ = make_sim(arch, precision, blob=blob, persistent=True)
+    ps, _ = make_sim(arch, precision, blob=blob, persistent=True, cluster=cl)
     h = run_gpu(ps, trace, replay=ref.lat)
+    assert ps.kernel_path == kernel
     np.testing.assert_array_equal(h["cycles"], g["cycles"])
     d = np.abs(h["pre"] - g["pre"]) / (np.abs(g["pre"]) + 1.0)
     assert np.median(d) < 1e-3 and d.max() < 0.1, (np.median(d), d.max())
@@ -188,13 +197,37 @@ def test_barrier_timeout_reported_and_context_recovers():
     w = I.WORKLOADS["c1"]
     trace = I.make_trace(w)
     blob = I.workload_weights(w)
-    bad, _ = make_sim(w.arch, "bf16", blob=blob, barrier_limit_us=1)
+    bad, _ = make_sim(w.arch, "bf16", blob=blob, barrier_limit_us=1, cluster=False)
     with pytest.raises(SimnetError) as e:
         run_gpu(bad, trace)
     assert e.value.status == 4                       # ETIMEOUT
     assert "bound" in str(e.value)
     cfg = oracle.Config.of(w.arch)
     ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, logs=True)
+    good, _ = make_sim(w.arch, "bf16", blob=blob, cluster=False)
+    g = run_gpu(good, trace, replay=ref.lat)
+    np.testing.assert_array_equal(g["cycles"], ref.cycles)
+    assert good.kernel_path == "persistent"
+
+
+def test_cluster_wait_timeout_reported_and_context_recovers():
+    """The cluster kernel's waits (on its own pipeline and on the other CTAs
+    of the cluster) get a 100 ns bound, so one gives up at once: the CTA
+    records a timeout, lets its copies and MMAs land, every CTA leaves at the
+    next step boundary, and the call returns ETIMEOUT.  A normal context on the
+    same device then reproduces the oracle, and so does the cluster kernel
+    given the default bound."""
+    w = I.WORKLOADS["c1"]
+    trace = I.make_trace(w)
+    blob = I.workload_weights(w)
+    bad, _ = make_sim(w.arch, "bf16", blob=blob, spin_limit_ns=100)
+    with pytest.raises(SimnetError) as e:
+        run_gpu(bad, trace)
+    assert e.value.status == 4                       # ETIMEOUT
+    assert bad.kernel_path == "cluster"
+    cfg = oracle.Config.of(w.arch)
+    ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, logs=True)
     good, _ = make_sim(w.arch, "bf16", blob=blob)
     g = run_gpu(good, trace, replay=ref.lat)
+    assert good.kernel_path == "cluster"
     np.testing.assert_array_equal(g["cycles"], ref.cycles)
