@@ -39,7 +39,7 @@
 namespace simnet {
 
 struct CArgs {
-    CUtensorMap tW[3];   // conv weights [C][K_l] (BF16, GEMM layout), box C rows x 64 columns
+    CUtensorMap tW[3];   // conv weights [C][K_l] (BF16, GEMM layout), box C/4 rows x 64 columns
     CUtensorMap tF;      // FC1 weights [H][K1], box H/4 rows x 64 columns
     const float *cbias[3];
     const float *fbias, *w2, *b2, *fc1_const;
@@ -156,13 +156,43 @@ __device__ __forceinline__ void commit_mc(uint32_t bar, uint16_t mask) {
                  "h"(mask)
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 2D TMA load of one box into the same shared-memory offset of every CTA in
+// `mask`, each CTA's barrier at `bar`'s offset receiving the bytes.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
+                                               uint16_t mask) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+// 64 consecutive TMEM columns of this warp's 32 lanes (two 32x32b loads, one
+// wait, in one statement so that no use of the registers precedes the wait).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[2][32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%65];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+          "=r"(r[0][7]), "=r"(r[0][8]), "=r"(r[0][9]), "=r"(r[0][10]), "=r"(r[0][11]), "=r"(r[0][12]),
+          "=r"(r[0][13]), "=r"(r[0][14]), "=r"(r[0][15]), "=r"(r[0][16]), "=r"(r[0][17]), "=r"(r[0][18]),
+          "=r"(r[0][19]), "=r"(r[0][20]), "=r"(r[0][21]), "=r"(r[0][22]), "=r"(r[0][23]), "=r"(r[0][24]),
+          "=r"(r[0][25]), "=r"(r[0][26]), "=r"(r[0][27]), "=r"(r[0][28]), "=r"(r[0][29]), "=r"(r[0][30]),
+          "=r"(r[0][31]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+          "=r"(r[1][6]), "=r"(r[1][7]), "=r"(r[1][8]), "=r"(r[1][9]), "=r"(r[1][10]), "=r"(r[1][11]),
+          "=r"(r[1][12]), "=r"(r[1][13]), "=r"(r[1][14]), "=r"(r[1][15]), "=r"(r[1][16]), "=r"(r[1][17]),
+          "=r"(r[1][18]), "=r"(r[1][19]), "=r"(r[1][20]), "=r"(r[1][21]), "=r"(r[1][22]), "=r"(r[1][23]),
+          "=r"(r[1][24]), "=r"(r[1][25]), "=r"(r[1][26]), "=r"(r[1][27]), "=r"(r[1][28]), "=r"(r[1][29]),
+          "=r"(r[1][30]), "=r"(r[1][31])
+        : "r"(taddr), "r"(taddr + 32u)
+        : "memory");
+}
+// 32 or 64 columns from taddr into r[0] (and r[1]).
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int cols, uint32_t (&r)[2][32]) {
+    if (cols > 32) tmem_ld64(taddr, r);
+    else tmem_ld32(taddr, r[0]);
 }
 __device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void cluster_sync_all() {
@@ -178,12 +208,6 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Byte offset of element k of row n in a K-major operand of `rows` rows laid
-// out as 64-element panels with the 128-byte swizzle (BF16).
-__device__ __forceinline__ uint32_t sw_off(int n, int k, int rows) {
-    return (uint32_t)(k >> 6) * (uint32_t)rows * 128u + (uint32_t)n * 128u +
-           ((uint32_t)(((k >> 3) & 7) ^ (n & 7)) << 4) + ((uint32_t)(k & 7) << 1);
-}
 
 // Cluster extent from the four CTAs' (longest queue + 1, live slots).
 __device__ __forceinline__ void read_ext(const int2 *ext_in, int b, int &E, int &AL) {
@@ -214,8 +238,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + y.bars);
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
-    const int B_ACT = 2 * S, B_D = 2 * S + 1, B_FULL = 2 * S + 2, B_EMPTY = 2 * S + 3, B_DFC = 2 * S + 4,
-              B_DFCE = 2 * S + 5, B_PART = 2 * S + 6, B_EXT = 2 * S + 7, B_FIN = 2 * S + 9;
+    // 0..S-1 weight panel full, S..2S-1 empty; then:
+    const int B_D = 2 * S, B_FULL = 2 * S + 1, B_EMPTY = 2 * S + 2, B_DFC = 2 * S + 3, B_PART = 2 * S + 4,
+              B_EXT = 2 * S + 5, B_FIN = 2 * S + 7;
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
     float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
     float *s_w2f = s_fb + HN, *s_w2e = s_w2f + HN;          // FC2 rows for those neurons
@@ -237,14 +262,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; s++) {
             mbar_init(bar(s), 1);
-            mbar_init(bar(S + s), 1);
+            mbar_init(bar(S + s), kCS);   // a stage is free once every CTA's MMAs have read it
         }
-        mbar_init(bar(B_ACT), 8);
         mbar_init(bar(B_D), 1);
         mbar_init(bar(B_FULL), kCS * 8);
         mbar_init(bar(B_EMPTY), kCS);
         mbar_init(bar(B_DFC), 1);
-        mbar_init(bar(B_DFCE), 8);
         mbar_init(bar(B_PART), kCS * 2);
         mbar_init(bar(B_EXT), kCS);
         mbar_init(bar(B_EXT + 1), kCS);
@@ -314,19 +337,26 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            auto load = [&](const CUtensorMap *m, int x, int yy, uint32_t bytes) {
+            // conv panels: this CTA loads rows [rank C/4, (rank+1) C/4) of each into all four
+            // CTAs (every CTA of the cluster needs the same weights); FC1 panels are its own
+            auto load = [&](const CUtensorMap *m, int x, int yy, uint32_t bytes, bool shared_panel) {
                 const int s = it % S;
-                if (!mbar_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status)) {
+                if (!cl_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status)) {
                     ok = false;
                     return;
                 }
                 mbar_expect_tx(bar(s), bytes);
-                tma_load_2d(ring0 + s * kStage, m, bar(s), x, yy);
+                if (shared_panel)
+                    tma_load_2d_mc(ring0 + s * kStage + rank * (uint32_t)(C / kCS) * 128u, m, bar(s), x, yy,
+                                   (uint16_t)((1u << kCS) - 1u));
+                else
+                    tma_load_2d(ring0 + s * kStage, m, bar(s), x, yy);
                 it++;
             };
             auto conv_panels = [&]() {   // every conv layer's weights, in consumption order
                 for (int l = 0; l < L && ok; l++)
-                    for (int pi = 0; pi < panels_of(l) && ok; pi++) load(&a.tW[l], pi * 64, 0, (uint32_t)C * 128u);
+                    for (int pi = 0; pi < panels_of(l) && ok; pi++)
+                        load(&a.tW[l], pi * 64, (int)rank * (C / kCS), (uint32_t)C * 128u, true);
             };
             if (a.n_steps > 0) conv_panels();
             for (int64_t t = 0; t < a.n_steps && ok; t++) {
@@ -339,95 +369,18 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     const int P = min(PM, eL - q0);
                     if (q0 > 0) conv_panels();
                     for (int pi = 0; pi < P * C / 64 && ok; pi++)
-                        load(&a.tF, q0 * C + pi * 64, (int)rank * HN, (uint32_t)HN * 128u);
+                        load(&a.tF, q0 * C + pi * 64, (int)rank * HN, (uint32_t)HN * 128u, false);
                 }
                 if (t + 1 < a.n_steps) conv_panels();   // the next step's first pass, before its extent is known
             }
             cnt[0] = it;
         }
-    } else if (warp == 1) {
-        // ---------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            int it = 0, act_uses = 0;
-            int64_t R = 0;
-            bool ok = true;
-            auto take = [&](int &s) -> bool {   // next weight panel
-                s = it % S;
-                const uint64_t tw = a.prof ? gtimer() : 0;
-                if (!mbar_wait(bar(s), (uint32_t)(it / S) & 1u, lim, abort_f, a.status)) return false;
-                if (a.prof && blockIdx.x == 0) a.prof[17] += gtimer() - tw;
-                tc_fence_after();
-                return true;
-            };
-            for (int64_t t = 0; t < a.n_steps && ok; t++) {
-                if (!cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status)) break;
-                int E, AL;
-                read_ext(ext_in, (int)(t & 1), E, AL);
-                if (AL == 0) break;
-                const int eL = positions_of(E, L, a.rows_n);
-                for (int q0 = 0; q0 < eL && ok; q0 += PM) {
-                    const int P = min(PM, eL - q0);
-                    for (int l = 0; l < L && ok; l++) {
-                        uint64_t tw = a.prof ? gtimer() : 0;
-                        if (!mbar_wait(bar(B_ACT), (uint32_t)act_uses & 1u, lim, abort_f, a.status)) { ok = false; break; }
-                        if (a.prof && blockIdx.x == 0) a.prof[16] += gtimer() - tw;
-                        act_uses++;
-                        tc_fence_after();
-                        fence_async_smem();
-                        const int T = tiles_of(l, P);
-                        const uint32_t ID = idesc_rt(C, false);
-                        for (int pi = 0; pi < panels_of(l); pi++, it++) {
-                            int s;
-                            if (!take(s)) { ok = false; break; }
-                            const uint64_t bd = sdesc(ring0 + s * kStage);
-                            for (int tt = 0; tt < T; tt++) {
-                                const uint64_t ad = sdesc(act0 + (uint32_t)(pi * T + tt) * 16384u);
-                                const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
-#pragma unroll
-                                for (int k = 0; k < 4; k++)
-                                    umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
-                            }
-                            umma_commit(bar(S + s));
-                        }
-                        if (ok) umma_commit(bar(B_D));
-                    }
-                    if (!ok) break;
-                    // FC1 over this pass's positions: every CTA's rows of them must be in
-                    uint64_t tw = a.prof ? gtimer() : 0;
-                    if (!cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status)) break;
-                    if (a.prof && blockIdx.x == 0) a.prof[18] += gtimer() - tw;
-                    fence_async_smem();
-                    tc_fence_after();
-                    if (q0 == 0 && t > 0) {
-                        if (!mbar_wait(bar(B_DFCE), (uint32_t)(t - 1) & 1u, lim, abort_f, a.status)) break;
-                        tc_fence_after();
-                    }
-                    const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
-                    for (int pi = 0; pi < P * C / 64; pi++, it++) {
-                        int s;
-                        if (!take(s)) { ok = false; break; }
-                        const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u), bd = sdesc(ring0 + s * kStage);
-#pragma unroll
-                        for (int k = 0; k < 4; k++)
-                            umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (q0 | pi | k) != 0 ? 1u : 0u);
-                        umma_commit(bar(S + s));
-                    }
-                    if (!ok) break;
-                    commit_mc(bar(B_EMPTY), (uint16_t)((1u << kCS) - 1u));
-                    R++;
-                }
-                if (ok) umma_commit(bar(B_DFC));
-            }
-            cnt[1] = it;
-            umma_commit(bar(B_FIN));   // every MMA of this thread done before TMEM is released
-            drain_wait(bar(B_FIN), 0u, drain_ns);
-        }
-        __syncwarp();
-    } else {
-        // ---------------------------------------------------------------- workers
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------------- workers (thread 0 also issues the MMAs)
         const int wi = warp - 2, qd = warp & 3, half = wi >> 2, tid = threadIdx.x - 64;
-        int d_uses = 0;
-        int64_t R = 0;
+        int d_uses = 0, it = 0;    // it: weight panels consumed (thread 0)
+        int64_t R = 0;             // passes exchanged
+        bool mma_ok = true;        // thread 0: false after a bounded wait gave up
         const StepArgs &As = *A;
         const int RW = As.retire_width, strict = As.strict;
         const bool prof = a.prof && blockIdx.x == 0 && tid == 0;
@@ -438,6 +391,35 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 a.prof[k] += tn - tp;
                 tp = tn;
             }
+        };
+        auto take = [&](int &s) -> bool {   // thread 0: next weight panel
+            s = it % S;
+            const uint64_t tw = prof ? gtimer() : 0;
+            if (!mbar_wait(bar(s), (uint32_t)(it / S) & 1u, lim, abort_f, a.status)) return false;
+            if (prof) a.prof[17] += gtimer() - tw;
+            tc_fence_after();
+            return true;
+        };
+        // thread 0: the conv MMAs of layer l over T row tiles, committed to B_D
+        auto issue_conv = [&](int l, int T) {
+            tc_fence_after();
+            fence_async_smem();
+            const uint32_t ID = idesc_rt(C, false);
+            for (int pi = 0; pi < panels_of(l) && mma_ok; pi++) {
+                int s;
+                if (!take(s)) { mma_ok = false; break; }
+                const uint64_t bd = sdesc(ring0 + s * kStage);
+                for (int tt = 0; tt < T; tt++) {
+                    const uint64_t ad = sdesc(act0 + (uint32_t)(pi * T + tt) * 16384u);
+                    const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
+                }
+                commit_mc(bar(S + s), (uint16_t)((1u << kCS) - 1u));   // stage read here: tell every CTA
+                it++;
+            }
+            if (mma_ok) umma_commit(bar(B_D));
         };
         // extent of this CTA's slots (longest queue + 1) and live count, to every CTA of the cluster
         auto send_ext = [&](int nb) {   // warp 2 only
@@ -499,12 +481,20 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(dst + ((j ^ (m & 7)) << 4)) = ch[j];
                 }
                 fence_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(bar(B_ACT));
+                workers_sync();
                 mark(1);
                 for (int l = 0; l < L; l++) {
                     const bool last = l == L - 1;
+                    uint64_t ti0 = prof ? gtimer() : 0;
+                    if (tid == 0 && mma_ok) issue_conv(l, tiles_of(l, P));
+                    __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
+                    uint64_t ti1 = prof ? gtimer() : 0;
                     bool ok = mbar_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status);
+                    if (prof) {
+                        const uint64_t ti2 = gtimer();
+                        a.prof[20 + 2 * l] += ti1 - ti0;   // issue (incl. weight waits)
+                        a.prof[21 + 2 * l] += ti2 - ti1;   // last commit -> layer done seen
+                    }
                     d_uses++;
                     if (last && R >= 1 && ok)   // every CTA has consumed the previous pass's exchanged rows
                         ok = cl_wait(bar(B_EMPTY), (uint32_t)((R - 1) & 1), lim, abort_f, a.status);
@@ -516,44 +506,47 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         const int m = tt * 128 + qd * 32 + lane;   // this lane's row of the tile
                         if (tt * 128 + qd * 32 >= Rl) continue;    // warp-uniform: rows past the pass
                         const int p = m >> 5, s = m & 31;
-                        for (int cb = half * (C / 2); cb < (half + 1) * (C / 2); cb += 32) {
-                            uint32_t r32[32];
-                            tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + cb), r32);
+                        const int c0 = half * (C / 2), nb = C / 64;   // this warp's channels: nb blocks of 32
+                        uint32_t r32[2][32];
+                        tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0), C / 2, r32);
+                        int row;
+                        uint32_t base, pstride;
+                        if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
+                            row = ((p >> 1) << 5) + s;
+                            base = y.act;
+                            pstride = (uint32_t)Tn * 16384u;
+                        } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
+                            row = (int)rank * kSPC + s;
+                            base = y.fc1a;
+                            pstride = 16384u;
+                        }
+                        const int kb = last ? p * C + c0 : (p & 1) * C + c0;
+#pragma unroll
+                        for (int bi = 0; bi < 2; bi++) {
+                            if (bi >= nb) break;
                             uint32_t w[16];
 #pragma unroll
                             for (int j = 0; j < 16; j++) {
-                                const float v0 = fmaxf(__uint_as_float(r32[2 * j]) + s_cb[l * C + cb + 2 * j], 0.f);
-                                const float v1 = fmaxf(__uint_as_float(r32[2 * j + 1]) + s_cb[l * C + cb + 2 * j + 1], 0.f);
+                                const int ch = c0 + bi * 32 + 2 * j;
+                                const float v0 = fmaxf(__uint_as_float(r32[bi][2 * j]) + s_cb[l * C + ch], 0.f);
+                                const float v1 = fmaxf(__uint_as_float(r32[bi][2 * j + 1]) + s_cb[l * C + ch + 1], 0.f);
                                 __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
                                 w[j] = *reinterpret_cast<uint32_t *>(&b2);
                             }
-                            int row, k0;
-                            uint32_t base, pstride;
-                            if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
-                                row = ((p >> 1) << 5) + s;
-                                k0 = (p & 1) * C + cb;
-                                base = y.act;
-                                pstride = (uint32_t)Tn * 16384u;
-                            } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
-                                row = (int)rank * kSPC + s;
-                                k0 = p * C + cb;
-                                base = y.fc1a;
-                                pstride = 16384u;
-                            }
 #pragma unroll
                             for (int j = 0; j < 4; j++) {
-                                const int k = k0 + 8 * j;
+                                const int k = kb + bi * 32 + 8 * j;
                                 const uint32_t off = base + (uint32_t)(k >> 6) * pstride + (uint32_t)row * 128u +
                                                      ((uint32_t)(((k >> 3) & 7) ^ (row & 7)) << 4);
-                                *reinterpret_cast<uint4 *>(sm + off) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                                *reinterpret_cast<uint4 *>(sm + off) =
+                                    make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
                             }
                         }
                     }
+                    fence_async_smem();
+                    tc_fence_before();
                     if (!last) {
-                        fence_async_smem();
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(bar(B_ACT));
+                        workers_sync();
                     } else {
                         if (tid >= 128 && tid < 128 + HN) cp_wait<0>();   // S[e] landed (read after the barrier)
                         workers_sync();   // this CTA's rows of the pass are all in its own buffer
@@ -564,15 +557,37 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             for (int r = 1; r < kCS; r++) cl_st_v4(cl_map(fc0 + off, (rank + r) % kCS), v);
                         }
                         fence_async_cluster();
-                        fence_async_smem();
-                        tc_fence_before();
                         __syncwarp();
                         if (lane < kCS) cl_arrive(cl_map(bar(B_FULL), (uint32_t)lane));
+                        // FC1 over this pass's positions, once every CTA's rows are in (thread 0)
+                        if (tid == 0 && mma_ok) {
+                            const uint64_t tw = prof ? gtimer() : 0;
+                            if (!cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status)) mma_ok = false;
+                            if (prof) a.prof[18] += gtimer() - tw;
+                            fence_async_smem();
+                            tc_fence_after();
+                            const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
+                            for (int pi = 0; pi < P * C / 64 && mma_ok; pi++) {
+                                int s;
+                                if (!take(s)) { mma_ok = false; break; }
+                                const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u), bd = sdesc(ring0 + s * kStage);
+#pragma unroll
+                                for (int k = 0; k < 4; k++)
+                                    umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
+                                                (q0 | pi | k) != 0 ? 1u : 0u);
+                                commit_mc(bar(S + s), (uint16_t)((1u << kCS) - 1u));
+                                it++;
+                            }
+                            if (mma_ok) commit_mc(bar(B_EMPTY), (uint16_t)((1u << kCS) - 1u));
+                        }
+                        __syncwarp();
                         R++;
                     }
                     mark(3 + 2 * l);
                 }
             }
+            if (tid == 0 && mma_ok) umma_commit(bar(B_DFC));
+            __syncwarp();
             // FC1 epilogue: ReLU(FC1 + bias + S[e]) folded into FC2 partials per slot
             {
                 bool ok = mbar_wait(bar(B_DFC), (uint32_t)(t & 1), lim, abort_f, a.status);
@@ -582,21 +597,21 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 float pf = 0.f, pe = 0.f;
                 if (ok) {
                     const int cols = HN / 2, j0 = half * cols;
-                    for (int cc = 0; cc < cols; cc += 32) {
-                        uint32_t r32[32];
-                        tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)(j0 + cc), r32);
+                    uint32_t r32[2][32];
+                    tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)j0, cols, r32);
+#pragma unroll
+                    for (int bi = 0; bi < 2; bi++) {
+                        if (bi >= cols / 32) break;
 #pragma unroll
                         for (int jj = 0; jj < 32; jj++) {
-                            const int j = j0 + cc + jj;
-                            const float v = fmaxf(__uint_as_float(r32[jj]) + s_fb[j] + s_Se[j], 0.f);
+                            const int j = j0 + bi * 32 + jj;
+                            const float v = fmaxf(__uint_as_float(r32[bi][jj]) + s_fb[j] + s_Se[j], 0.f);
                             pf = fmaf(v, s_w2f[j], pf);
                             pe = fmaf(v, s_w2e[j], pe);
                         }
                     }
                 }
                 tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(bar(B_DFCE));
                 // slot qd * 32 + lane of the cluster belongs to CTA qd, where it is slot `lane`
                 cl_st_v2f(cl_map(smem_u32(&part[((int)rank * 2 + half) * kSPC + lane]), (uint32_t)qd), pf, pe);
                 __syncwarp();
@@ -635,7 +650,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     uint64_t *qr = qring + s * cap;
                     int qs = s_qs[s], ql = s_ql[s], ev = 0;
                     int32_t tick = s_tick[s] + (int32_t)F;
-                    // in-order retire from the oldest, at most RW * F entries
+                    // in-order retire from the oldest, at most lim_n entries
                     auto retire = [&](int lim_n) {
                         int k = 0;
                         while (k < lim_n) {
@@ -686,6 +701,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 send_ext((int)((t + 1) & 1));
                 mark(12);
             }
+        }
+        if (tid == 0) {   // every MMA done before TMEM is released
+            cnt[1] = it;
+            umma_commit(bar(B_FIN));
+            drain_wait(bar(B_FIN), 0u, drain_ns);
         }
         // state back to device memory (resumable), outstanding record copies drained; the
         // barrier orders the last step's head (warp 2) before the other warps read its state
@@ -743,7 +763,8 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.cap = c->cap;
     a.rows_n = c->rows_n;
     for (int l = 0; l < a.L; l++) {
-        if (!encode_map_2d(a.tW[l], SIMNET_BF16, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, 64, (uint32_t)a.C, why))
+        if (!encode_map_2d(a.tW[l], SIMNET_BF16, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, 64,
+                           (uint32_t)(a.C / kCS), why))
             return false;
         a.cbias[l] = c->bias[l];
     }
