@@ -347,7 +347,7 @@ def run_ours(args, rank, world):
                            "traffic": TRAFFIC.get((w.name, args.precision, "cluster_kernel")),
                            "avg_launch_us": ms_per_step * 1e3, "algorithmic_per_launch": flops,
                            "algorithmic_unit": "flop", "share_of_step": 1.0}
-        out["phases_us_per_step"] = cluster_phases(w, args, blob32, rec, off, cyc)
+        out["phases_us_per_step"] = cluster_phases(w, args, blob32, rec, off, cyc, clocks.get("sm_mhz") or 2032.0)
     elif rank == 0 and not args.no_breakdown:
         out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B)
         if out["kernel_mode"] == "persistent":
@@ -406,9 +406,10 @@ CLUSTER_PHASES = ["step start", "feature rows", "wait conv1", "epilogue conv1", 
                   "wait conv3", "epilogue conv3", "wait FC1", "FC1 epilogue", "wait partials", "head", "extent"]
 
 
-def cluster_phases(w, args, blob32, rec, off, cyc):
-    """CTA 0's time per phase of the cluster kernel (globaltimer, one extra
-    timed call), in microseconds per lock-step."""
+def cluster_phases(w, args, blob32, rec, off, cyc, sm_mhz):
+    """CTA 0's time per phase of the cluster kernel (SM clock cycles of one
+    extra timed call, converted at the sampled SM clock), in microseconds per
+    lock-step."""
     from paper_2105_05821_b300.simnet import Simnet
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width, kernel_events=True)
     sim.load_weights(blob32)
@@ -419,7 +420,7 @@ def cluster_phases(w, args, blob32, rec, off, cyc):
     names = [n for n in CLUSTER_PHASES]
     if w.arch.n_conv == 2:   # the third conv layer's slots stay empty
         names = names[:6] + ["-", "-"] + names[8:]
-    out = {n: float(d[k]) / steps / 1e3 for k, n in enumerate(names) if n != "-"}
+    out = {n: float(d[k]) / steps / sm_mhz for k, n in enumerate(names) if n != "-"}
     out["positions_per_step"] = float(d[15]) / steps
     return out
 

@@ -290,13 +290,14 @@ simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launc
  * the start of the layer's phase in CTA 0 to k = 0 its first operand tile
  * arriving, 1 its last MMA commit, 2 its epilogue done, 3 the grid barrier
  * passed.  For the cluster kernel (SIMNET_PATH_CLUSTER) out[k], k < 32, is
- * the summed ns of CTA 0's phase k instead: 0 step start (extent exchange),
+ * the summed SM clock cycles of CTA 0's phase k instead: 0 step start (extent exchange),
  * 1 feature rows, 2/4/6 waiting for conv layer 1/2/3, 3/5/7 their epilogues
  * (7 includes the exchange of the last layer's rows), 8 waiting for FC1,
  * 9 FC1 epilogue and partial sums, 10 waiting for the partial sums, 11 head
  * and queue update, 12 extent exchange; 14 steps, 15 positions computed;
- * 16-19 the MMA thread's waits for operands, weight tiles, the exchanged rows
- * and FC1's weight tiles.
+ * 18 waiting for the exchanged rows before FC1, 20 + 2l / 21 + 2l issuing
+ * conv layer l's MMAs / from the last issue to the layer seen done, 26 + l
+ * waiting for layer l's weight panels (26 + L: FC1's).
  * Synchronises.  Errors: EINVAL, ESTATE (no such call).
  */
 simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
@@ -305,11 +306,15 @@ simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
 #define SIMNET_PATH_NONE 0       /* no simulate call yet */
 #define SIMNET_PATH_LAYERWISE 1  /* one kernel per layer and step (CUDA graphs) */
 #define SIMNET_PATH_PERSISTENT 2 /* one cooperative kernel, grid-wide barriers between phases */
-#define SIMNET_PATH_CLUSTER 3    /* clusters of 4 CTAs each owning 128 sub-traces for the whole
-                                    call, no grid-wide synchronisation (BF16; 2-3 conv layers of
-                                    64 or 128 channels; FC1 width 256 or 512) */
+#define SIMNET_PATH_CLUSTER 3    /* clusters of 4 or 8 CTAs each owning 128 sub-traces for the
+                                    whole call, no grid-wide synchronisation (BF16; 2-3 conv
+                                    layers of 64 or 128 channels; FC1 width 256 or 512) */
 
-/* Path the last simnet_simulate call took (SIMNET_PATH_*), or -1 for a NULL context. */
+/* Path the last simnet_simulate call took (SIMNET_PATH_*), or -1 for a NULL context.  A
+ * BF16 call where the cluster kernel applies starts on it; if the call is longer than 512
+ * steps and steps 64-127 needed more than two passes of last-conv positions per step (long
+ * queues), the rest of the call runs on the grid-wide kernel and the call reports
+ * SIMNET_PATH_PERSISTENT. */
 int32_t simnet_kernel_path(const simnet_ctx *ctx);
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */

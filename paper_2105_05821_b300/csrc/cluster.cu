@@ -45,7 +45,9 @@ struct CArgs {
     const float *fbias, *w2, *b2, *fc1_const;
     const StepArgs *A;
     int32_t *status;
-    unsigned long long *prof;   // [32] summed ns per phase in CTA 0 (or null), see cluster_phase_names
+    unsigned long long *prof;   // [32] summed SM clock cycles per phase in CTA 0 (or null)
+    unsigned long long *tinfo;  // [4] first expired wait: site, CTA, step, pass (zero at launch)
+    unsigned long long *pos_sum;  // [2] positions computed and cluster-steps run (accumulated)
     int64_t n_steps, spin_ns;
     int L, C, H, cap, rows_n, stages;
 };
@@ -53,9 +55,9 @@ struct CArgs {
 namespace {
 using namespace tcx;
 
-constexpr int kCS = 4;            // CTAs per cluster
-constexpr int kSPC = 32;          // batch slots per CTA
-constexpr int kCThreads = 320;    // warp 0 TMA, warp 1 MMA, warps 2-9 workers
+// A cluster of CS CTAs (4 or 8) owns 128 batch slots, 128 / CS per CTA.
+constexpr int kCThreads = 320;
+constexpr bool kMulticastWeights = true;   // conv weight panels shared by TMA multicast, or loaded per CTA    // warp 0 TMA, warp 1 MMA, warps 2-9 workers
 constexpr int kWk = 256;          // worker threads
 constexpr int kStage = 16384;     // one weight panel: 128 rows x 64 BF16
 constexpr int kTmemCols = 512;
@@ -71,22 +73,26 @@ struct CLay {
     uint32_t ring, act, fc1a, qring, rec, part, prm, slot, misc, bars, total;
 };
 
-__host__ __device__ inline CLay c_layout(int L, int C, int H, int cap, int stages) {
+__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages) {
     CLay y;
-    const int HN = H / kCS;
-    uint32_t actb = 256u * 256u;                                            // layer 0: 256 rows of two feature rows
-    if (128u * 4u * (uint32_t)C > actb) actb = 128u * 4u * (uint32_t)C;     // later layers: one 128-row tile of 2C
+    const int HN = H / CS, SPC = 128 / CS, PM = pass_positions(L);
+    // operand of layer l: its rows (pass positions x pairs x slots) x K, in 64-column panels
+    uint32_t actb = (uint32_t)(PM * (1 << (L - 1)) * SPC) * 256u;
+    for (int l = 1; l < L; l++) {
+        const uint32_t b = (uint32_t)(PM * (1 << (L - 1 - l)) * SPC) * 4u * (uint32_t)C;
+        actb = b > actb ? b : actb;
+    }
     y.ring = 0;
     y.act = (uint32_t)stages * kStage;
     y.fc1a = al_up(y.act + actb, 1024);
     y.qring = y.fc1a + 256u * (uint32_t)(pass_positions(L) * C);           // 128 slots x positions x C BF16
-    y.rec = y.qring + (uint32_t)kSPC * cap * 8;
-    y.part = al_up(y.rec + kSPC * 4 * 4, 16);
-    y.prm = y.part + 8 * kSPC * 8;
+    y.rec = y.qring + (uint32_t)SPC * cap * 8;
+    y.part = al_up(y.rec + SPC * 4 * 4, 16);
+    y.prm = y.part + 2 * CS * SPC * 8;
     const uint32_t prm_floats = (uint32_t)(L * C + 4 * HN + 2);
     y.slot = al_up(y.prm + prm_floats * 4, 16);
-    y.misc = y.slot + kSPC * 8 + 8 * kSPC * 4;
-    y.bars = al_up(y.misc + 160, 8);
+    y.misc = y.slot + SPC * 8 + 8 * SPC * 4;
+    y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8, 8);   // + 32 phase counters (profiling)
     y.total = y.bars + (2 * stages + 12) * 8;
     return y;
 }
@@ -126,9 +132,54 @@ __device__ __forceinline__ bool cl_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// try_wait that lets the hardware suspend the thread (up to `hint_ns`) until the
+// phase completes, so that waiting warps do not take issue slots from working ones.
+__device__ __forceinline__ bool try_sleep(uint32_t bar, uint32_t parity, uint32_t hint_ns, bool cluster_scope) {
+    uint32_t ok;
+    if (cluster_scope)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(hint_ns)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(hint_ns)
+            : "memory");
+    return ok != 0;
+}
+// Bounded wait, suspending between polls.
+__device__ __noinline__ bool sleep_wait_slow(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
+                                             int32_t *status, bool cluster_scope) {
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (try_sleep(bar, parity, 20000u, cluster_scope)) return true;
+        if (*abort_flag) return false;
+        if ((int64_t)(gtimer() - t0) > limit) {
+            *abort_flag = 1;
+            atomicExch(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+// Non-blocking test of a phase that other CTAs of the cluster arrive on.
+__device__ __forceinline__ bool cl_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait on a phase of a barrier that other CTAs of the cluster arrive on.
-__device__ __noinline__ bool cl_wait(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
-                                     int32_t *status) {
+__device__ __noinline__ bool cl_wait_slow(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
+                                          int32_t *status) {
     if (cl_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
@@ -140,6 +191,16 @@ __device__ __noinline__ bool cl_wait(uint32_t bar, uint32_t parity, int64_t limi
             return false;
         }
     }
+}
+__device__ __forceinline__ bool cl_wait(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
+                                        int32_t *status) {
+    if (cl_test(bar, parity)) return true;
+    return cl_wait_slow(bar, parity, limit, abort_flag, status);
+}
+__device__ __forceinline__ bool sleep_wait(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
+                                           int32_t *status, bool cluster_scope) {
+    if (cluster_scope ? cl_test(bar, parity) : mbar_test(bar, parity)) return true;
+    return sleep_wait_slow(bar, parity, limit, abort_flag, status, cluster_scope);
 }
 // Wait for copies or MMAs this CTA started to land, also after an abort (they
 // write shared memory or TMEM that is released afterwards); bounded, silent.
@@ -209,12 +270,13 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 
-// Cluster extent from the four CTAs' (longest queue + 1, live slots).
+// Cluster extent from the CTAs' (longest queue + 1, live slots).
+template <int CS>
 __device__ __forceinline__ void read_ext(const int2 *ext_in, int b, int &E, int &AL) {
     E = 0;
     AL = 0;
-    for (int r = 0; r < kCS; r++) {
-        const volatile int *v = reinterpret_cast<const volatile int *>(&ext_in[b * kCS + r]);
+    for (int r = 0; r < CS; r++) {
+        const volatile int *v = reinterpret_cast<const volatile int *>(&ext_in[b * CS + r]);
         E = max(E, v[0]);
         AL += v[1];
     }
@@ -224,17 +286,32 @@ __device__ __forceinline__ int positions_of(int E, int L, int rows_n) {
     return max(1, min((E + span - 1) / span, rows_n));
 }
 
+template <int CS>
 __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_constant__ CArgs a) {
+    constexpr int SPC = 128 / CS;   // batch slots per CTA
+    constexpr uint16_t kAll = (uint16_t)((1u << CS) - 1u);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int L = a.L, C = a.C, HN = a.H / kCS, S = a.stages, cap = a.cap, PM = pass_positions(L);
-    const CLay y = c_layout(L, C, a.H, cap, S);
+    const int L = a.L, C = a.C, HN = a.H / CS, S = a.stages, cap = a.cap, PM = pass_positions(L);
+    const CLay y = c_layout(CS, L, C, a.H, cap, S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cl_rank();
-    const int slot0 = (int)(blockIdx.x / kCS) * (kCS * kSPC) + (int)rank * kSPC;
+    const int slot0 = (int)(blockIdx.x / CS) * 128 + (int)rank * SPC;
     const StepArgs *A = a.A;
     const int64_t lim = a.spin_ns;
     const int64_t drain_ns = lim > 200000000 ? lim : 200000000;   // 0.2 s at least
+    // Record where the first expired wait of the launch was (sites: 1 weight stage free,
+    // 2 extent (producer), 3 weight panel, 4 extent (workers), 5 conv layer done, 6 exchange
+    // buffer free, 7 exchanged rows in, 8 FC1 done, 9 FC2 partial sums in).
+    auto note = [&](bool ok, int site, int64_t step, int64_t pass) -> bool {
+        if (!ok && *(volatile int32_t *)a.status == kStatusTimeout &&
+            atomicCAS(&a.tinfo[0], 0ull, (unsigned long long)site) == 0ull) {
+            a.tinfo[1] = blockIdx.x;
+            a.tinfo[2] = (unsigned long long)step;
+            a.tinfo[3] = (unsigned long long)pass;
+        }
+        return ok;
+    };
 
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + y.bars);
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
@@ -247,33 +324,36 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     float *s_Se = s_w2e + HN;                                // [HN] S[e] of the current step
     float *s_b2 = s_Se + HN;
     int64_t *s_o = reinterpret_cast<int64_t *>(sm + y.slot);
-    int32_t *s_b = reinterpret_cast<int32_t *>(s_o + kSPC), *s_n = s_b + kSPC, *s_p = s_n + kSPC,
-            *s_tick = s_p + kSPC, *s_qs = s_tick + kSPC, *s_ql = s_qs + kSPC, *s_ev = s_ql + kSPC,
-            *s_al = s_ev + kSPC;
+    int32_t *s_b = reinterpret_cast<int32_t *>(s_o + SPC), *s_n = s_b + SPC, *s_p = s_n + SPC,
+            *s_tick = s_p + SPC, *s_qs = s_tick + SPC, *s_ql = s_qs + SPC, *s_ev = s_ql + SPC,
+            *s_al = s_ev + SPC;
     uint64_t *qring = reinterpret_cast<uint64_t *>(sm + y.qring);
     uint32_t *recb = reinterpret_cast<uint32_t *>(sm + y.rec);   // [slot][position & 3]
     float2 *part = reinterpret_cast<float2 *>(sm + y.part);     // [source CTA * 2 + half][slot]
     int2 *ext_in = reinterpret_cast<int2 *>(sm + y.misc);       // [step parity][source CTA]
-    volatile int *ctl = reinterpret_cast<volatile int *>(sm + y.misc + 128);   // positions, stop
+    volatile int *ctl = reinterpret_cast<volatile int *>(sm + y.misc + 16 * CS);   // positions, stop
     volatile int *abort_f = ctl + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + y.misc + 148);
-    int *cnt = reinterpret_cast<int *>(sm + y.misc + 152);      // weight panels issued, consumed
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + y.misc + 16 * CS + 20);
+    int *cnt = reinterpret_cast<int *>(sm + y.misc + 16 * CS + 24);   // weight panels issued, consumed
+    // phase counters (CTA 0, on request): shared-memory accumulators, written out at the end
+    unsigned long long *pacc = reinterpret_cast<unsigned long long *>(sm + y.misc + 16 * CS + 32);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; s++) {
             mbar_init(bar(s), 1);
-            mbar_init(bar(S + s), kCS);   // a stage is free once every CTA's MMAs have read it
+            mbar_init(bar(S + s), kMulticastWeights ? CS : 1);   // free once every reader has read it
         }
         mbar_init(bar(B_D), 1);
-        mbar_init(bar(B_FULL), kCS * 8);
-        mbar_init(bar(B_EMPTY), kCS);
+        mbar_init(bar(B_FULL), CS * 8);
+        mbar_init(bar(B_EMPTY), CS);
         mbar_init(bar(B_DFC), 1);
-        mbar_init(bar(B_PART), kCS * 2);
-        mbar_init(bar(B_EXT), kCS);
-        mbar_init(bar(B_EXT + 1), kCS);
+        mbar_init(bar(B_PART), CS * 2);
+        mbar_init(bar(B_EXT), CS);
+        mbar_init(bar(B_EXT + 1), CS);
         mbar_init(bar(B_FIN), 1);
         *abort_f = 0;
         cnt[0] = cnt[1] = 0;
+        for (int k = 0; k < 32; k++) pacc[k] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -291,10 +371,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         s_w2e[j] = a.w2[a.H + nn];
     }
     if (threadIdx.x < 2) s_b2[threadIdx.x] = a.b2[threadIdx.x];
-    // slot state (workers: warp w takes slots w-2, w+6, w+14, w+22)
+    // slot state (workers: warp w takes slots w-2, w+6, ...)
     if (warp >= 2) {
         const int n_act = min(*A->n_active, A->n_sub);
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < SPC / 8; j++) {
             const int s = (warp - 2) + 8 * j, g = slot0 + s;
             int b = -1;
             int64_t o = 0;
@@ -329,49 +409,71 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     const uint32_t ring0 = smem_u32(sm + y.ring), act0 = smem_u32(sm + y.act), fc0 = smem_u32(sm + y.fc1a);
     // TMEM columns: layer 0 tiles at 0 (two tiles of C), odd layers at 256, even layers >= 2 at 0, FC1 at 384
     auto dcol = [&](int l) -> uint32_t { return l == 0 ? 0u : ((l & 1) ? 256u : 0u); };
-    auto rows_of = [&](int l, int P) { return P * (1 << (L - 1 - l)) * kSPC; };   // layer l's A rows
+    auto rows_of = [&](int l, int P) { return P * (1 << (L - 1 - l)) * SPC; };    // layer l's A rows
     auto tiles_of = [&](int l, int P) { return (rows_of(l, P) + 127) / 128; };
+    // bytes between the 64-column K panels of layer l's operand: the panels hold just the
+    // pass's rows; an MMA tile past them reads neighbouring shared memory into rows it ignores
+    auto pstride_of = [&](int l, int P) { return (uint32_t)rows_of(l, P) * 128u; };
     auto panels_of = [&](int l) { return l == 0 ? 2 : C / 32; };                   // K / 64
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
             int it = 0;
             bool ok = true;
-            // conv panels: this CTA loads rows [rank C/4, (rank+1) C/4) of each into all four
-            // CTAs (every CTA of the cluster needs the same weights); FC1 panels are its own
+            // conv panels: this CTA loads rows [rank C/CS, (rank+1) C/CS) of each into every CTA
+            // of the cluster (all need the same weights); FC1 panels are its own
             auto load = [&](const CUtensorMap *m, int x, int yy, uint32_t bytes, bool shared_panel) {
                 const int s = it % S;
-                if (!cl_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status)) {
+                if (!note(cl_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
                     ok = false;
                     return;
                 }
                 mbar_expect_tx(bar(s), bytes);
                 if (shared_panel)
-                    tma_load_2d_mc(ring0 + s * kStage + rank * (uint32_t)(C / kCS) * 128u, m, bar(s), x, yy,
-                                   (uint16_t)((1u << kCS) - 1u));
+                    tma_load_2d_mc(ring0 + s * kStage + rank * (uint32_t)(C / CS) * 128u, m, bar(s), x, yy, kAll);
                 else
                     tma_load_2d(ring0 + s * kStage, m, bar(s), x, yy);
                 it++;
             };
-            auto conv_panels = [&]() {   // every conv layer's weights, in consumption order
+            // conv panel i of a pass (all layers' weights in consumption order), i in [from, to)
+            int n_conv_panels = 0;
+            for (int l = 0; l < L; l++) n_conv_panels += panels_of(l);
+            auto conv_panels = [&](int from, int to) {
+                int i = 0;
                 for (int l = 0; l < L && ok; l++)
-                    for (int pi = 0; pi < panels_of(l) && ok; pi++)
-                        load(&a.tW[l], pi * 64, (int)rank * (C / kCS), (uint32_t)C * 128u, true);
+                    for (int pi = 0; pi < panels_of(l) && ok; pi++, i++) {
+                        if (i < from || i >= to) continue;
+                        if (kMulticastWeights) load(&a.tW[l], pi * 64, (int)rank * (C / CS), (uint32_t)C * 128u, true);
+                        else for (int r = 0; r < CS && ok; r++) {   // the whole panel, slice by slice, locally
+                            const int s = it % S;
+                            if (r == 0) {
+                                if (!note(cl_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status), 1, -1, it)) { ok = false; break; }
+                                mbar_expect_tx(bar(s), (uint32_t)C * 128u);
+                            }
+                            tma_load_2d(ring0 + s * kStage + (uint32_t)r * (uint32_t)(C / CS) * 128u, &a.tW[l], bar(s),
+                                        pi * 64, r * (C / CS));
+                            if (r == CS - 1) it++;
+                        }
+                    }
             };
-            if (a.n_steps > 0) conv_panels();
+            // Before a step's extent is known only its first S panels are loaded: their stages
+            // are freed by the current step, which every CTA finishes; a stage holding one of
+            // those panels is freed only if the step runs (the cluster may be done by then).
+            const int pre = min(n_conv_panels, S);
+            if (a.n_steps > 0) conv_panels(0, pre);
             for (int64_t t = 0; t < a.n_steps && ok; t++) {
-                if (!cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status)) break;
+                if (!note(cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status), 2, t, 0)) break;
                 int E, AL;
-                read_ext(ext_in, (int)(t & 1), E, AL);
+                read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 if (AL == 0) break;
                 const int eL = positions_of(E, L, a.rows_n);
                 for (int q0 = 0; q0 < eL && ok; q0 += PM) {
                     const int P = min(PM, eL - q0);
-                    if (q0 > 0) conv_panels();
+                    conv_panels(q0 > 0 ? 0 : pre, n_conv_panels);
                     for (int pi = 0; pi < P * C / 64 && ok; pi++)
                         load(&a.tF, q0 * C + pi * 64, (int)rank * HN, (uint32_t)HN * 128u, false);
                 }
-                if (t + 1 < a.n_steps) conv_panels();   // the next step's first pass, before its extent is known
+                if (t + 1 < a.n_steps) conv_panels(0, pre);   // the next step's first panels
             }
             cnt[0] = it;
         }
@@ -384,39 +486,41 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         const StepArgs &As = *A;
         const int RW = As.retire_width, strict = As.strict;
         const bool prof = a.prof && blockIdx.x == 0 && tid == 0;
-        uint64_t tp = prof ? gtimer() : 0;
+        uint64_t tp = prof ? (uint64_t)clock64() : 0;
         auto mark = [&](int k) {
             if (prof) {
-                const uint64_t tn = gtimer();
-                a.prof[k] += tn - tp;
+                const uint64_t tn = (uint64_t)clock64();
+                pacc[k] += tn - tp;
                 tp = tn;
             }
         };
-        auto take = [&](int &s) -> bool {   // thread 0: next weight panel
+        auto take = [&](int &s, int who) -> bool {   // thread 0: next weight panel (who: layer, L = FC1)
             s = it % S;
-            const uint64_t tw = prof ? gtimer() : 0;
-            if (!mbar_wait(bar(s), (uint32_t)(it / S) & 1u, lim, abort_f, a.status)) return false;
-            if (prof) a.prof[17] += gtimer() - tw;
+            const uint64_t tw = prof ? (uint64_t)clock64() : 0;
+            if (!note(mbar_wait(bar(s), (uint32_t)(it / S) & 1u, lim, abort_f, a.status), 3, -1, it)) return false;
+            if (prof) pacc[26 + who] += (uint64_t)clock64() - tw;
             tc_fence_after();
             return true;
         };
-        // thread 0: the conv MMAs of layer l over T row tiles, committed to B_D
-        auto issue_conv = [&](int l, int T) {
+        // thread 0: the conv MMAs of layer l over the pass's row tiles (P positions), committed to B_D
+        auto issue_conv = [&](int l, int P) {
+            const int T = tiles_of(l, P);
             tc_fence_after();
             fence_async_smem();
             const uint32_t ID = idesc_rt(C, false);
             for (int pi = 0; pi < panels_of(l) && mma_ok; pi++) {
                 int s;
-                if (!take(s)) { mma_ok = false; break; }
+                if (!take(s, l)) { mma_ok = false; break; }
                 const uint64_t bd = sdesc(ring0 + s * kStage);
                 for (int tt = 0; tt < T; tt++) {
-                    const uint64_t ad = sdesc(act0 + (uint32_t)(pi * T + tt) * 16384u);
+                    const uint64_t ad = sdesc(act0 + (uint32_t)pi * pstride_of(l, P) + (uint32_t)tt * 16384u);
                     const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
 #pragma unroll
                     for (int k = 0; k < 4; k++)
                         umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
                 }
-                commit_mc(bar(S + s), (uint16_t)((1u << kCS) - 1u));   // stage read here: tell every CTA
+                if (kMulticastWeights) commit_mc(bar(S + s), kAll);   // stage read here: tell every CTA
+                else umma_commit(bar(S + s));
                 it++;
             }
             if (mma_ok) umma_commit(bar(B_D));
@@ -424,23 +528,23 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // extent of this CTA's slots (longest queue + 1) and live count, to every CTA of the cluster
         auto send_ext = [&](int nb) {   // warp 2 only
             int mx = 0, al = 0;
-            if (s_al[lane]) { mx = s_ql[lane] + 1; al = 1; }
+            if (lane < SPC && s_al[lane]) { mx = s_ql[lane] + 1; al = 1; }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
                 al += __shfl_xor_sync(0xffffffffu, al, o);
             }
-            if (lane < kCS) {   // one lane per destination CTA: the release arrives overlap
-                cl_st_v2i(cl_map(smem_u32(&ext_in[nb * kCS + rank]), (uint32_t)lane), mx, al);
+            if (lane < CS) {   // one lane per destination CTA: the release arrives overlap
+                cl_st_v2i(cl_map(smem_u32(&ext_in[nb * CS + rank]), (uint32_t)lane), mx, al);
                 cl_arrive(cl_map(bar(B_EXT + nb), (uint32_t)lane));
             }
         };
         if (wi == 0) send_ext(0);
         for (int64_t t = 0; t < a.n_steps; t++) {
             if (tid == 0) {
-                const bool ok = cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status);
+                const bool ok = note(sleep_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status, true), 4, t, 0);
                 int E, AL;
-                read_ext(ext_in, (int)(t & 1), E, AL);
+                read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 ctl[0] = positions_of(E, L, a.rows_n);
                 ctl[1] = (!ok || AL == 0 || *abort_f) ? 1 : 0;
             }
@@ -448,17 +552,21 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             const int eL = ctl[0];
             if (ctl[1]) break;
             mark(0);
-            if (prof) { a.prof[14] += 1; a.prof[15] += (unsigned long long)eL; }
+            if (prof) { pacc[14] += 1; pacc[15] += (unsigned long long)eL; }
+            if (tid == 0 && rank == 0 && 2 * t >= a.n_steps) {   // extent needed in the launch's second half
+                atomicAdd(&a.pos_sum[0], (unsigned long long)eL);
+                atomicAdd(&a.pos_sum[1], 1ull);
+            }
             if (tid >= 128 && tid < 128 + HN) {   // S[e] for this CTA's neurons, needed by the FC1 epilogue
                 cp_async4(smem_u32(&s_Se[tid - 128]), a.fc1_const + (size_t)eL * a.H + (int)rank * HN + (tid - 128));
                 cp_commit();
             }
             for (int q0 = 0; q0 < eL; q0 += PM) {
-                const int P = min(PM, eL - q0), T0 = tiles_of(0, P);
+                const int P = min(PM, eL - q0);
                 // feature rows of the pass: layer-0 A row (pair, slot), K = the pair's two rows
-                for (int f = tid; f < P * (1 << L) * kSPC; f += kWk) {
-                    const int s = f & 31, rr = f >> 5, r = q0 * (1 << L) + rr;
-                    const int m = (rr >> 1) * kSPC + s;
+                for (int f = tid; f < P * (1 << L) * SPC; f += kWk) {
+                    const int s = f % SPC, rr = f / SPC, r = q0 * (1 << L) + rr;
+                    const int m = (rr >> 1) * SPC + s;
                     uint4 ch[8];
                     const int ql = s_ql[s];
                     if (s_al[s] && r <= ql) {
@@ -476,7 +584,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 #pragma unroll
                         for (int j = 0; j < 8; j++) ch[j] = make_uint4(0, 0, 0, 0);
                     }
-                    uint8_t *dst = sm + y.act + (uint32_t)(rr & 1) * (uint32_t)(T0 * 16384) + (uint32_t)m * 128u;
+                    uint8_t *dst = sm + y.act + (uint32_t)(rr & 1) * pstride_of(0, P) + (uint32_t)m * 128u;
 #pragma unroll
                     for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(dst + ((j ^ (m & 7)) << 4)) = ch[j];
                 }
@@ -485,38 +593,39 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 mark(1);
                 for (int l = 0; l < L; l++) {
                     const bool last = l == L - 1;
-                    uint64_t ti0 = prof ? gtimer() : 0;
-                    if (tid == 0 && mma_ok) issue_conv(l, tiles_of(l, P));
+                    uint64_t ti0 = prof ? (uint64_t)clock64() : 0;
+                    if (tid == 0 && mma_ok) issue_conv(l, P);
                     __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
-                    uint64_t ti1 = prof ? gtimer() : 0;
-                    bool ok = mbar_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status);
+                    uint64_t ti1 = prof ? (uint64_t)clock64() : 0;
+                    bool ok = note(sleep_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status, false), 5, t, R);
                     if (prof) {
-                        const uint64_t ti2 = gtimer();
-                        a.prof[20 + 2 * l] += ti1 - ti0;   // issue (incl. weight waits)
-                        a.prof[21 + 2 * l] += ti2 - ti1;   // last commit -> layer done seen
+                        const uint64_t ti2 = (uint64_t)clock64();
+                        pacc[20 + 2 * l] += ti1 - ti0;   // issue (incl. weight waits)
+                        pacc[21 + 2 * l] += ti2 - ti1;   // last commit -> layer done seen
                     }
                     d_uses++;
                     if (last && R >= 1 && ok)   // every CTA has consumed the previous pass's exchanged rows
-                        ok = cl_wait(bar(B_EMPTY), (uint32_t)((R - 1) & 1), lim, abort_f, a.status);
+                        ok = note(cl_wait(bar(B_EMPTY), (uint32_t)((R - 1) & 1), lim, abort_f, a.status), 6, t, R);
                     ok = __all_sync(0xffffffffu, ok);
                     tc_fence_after();
                     mark(2 + 2 * l);
-                    const int T = tiles_of(l, P), Rl = rows_of(l, P), Tn = last ? 0 : tiles_of(l + 1, P);
+                    const int T = tiles_of(l, P), Rl = rows_of(l, P);
                     for (int tt = 0; tt < T && ok; tt++) {
                         const int m = tt * 128 + qd * 32 + lane;   // this lane's row of the tile
                         if (tt * 128 + qd * 32 >= Rl) continue;    // warp-uniform: rows past the pass
-                        const int p = m >> 5, s = m & 31;
+                        const bool valid = m < Rl;
+                        const int p = m / SPC, s = m % SPC;
                         const int c0 = half * (C / 2), nb = C / 64;   // this warp's channels: nb blocks of 32
                         uint32_t r32[2][32];
                         tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0), C / 2, r32);
                         int row;
                         uint32_t base, pstride;
                         if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
-                            row = ((p >> 1) << 5) + s;
+                            row = (p >> 1) * SPC + s;
                             base = y.act;
-                            pstride = (uint32_t)Tn * 16384u;
+                            pstride = pstride_of(l + 1, P);
                         } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
-                            row = (int)rank * kSPC + s;
+                            row = (int)rank * SPC + s;
                             base = y.fc1a;
                             pstride = 16384u;
                         }
@@ -538,8 +647,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                 const int k = kb + bi * 32 + 8 * j;
                                 const uint32_t off = base + (uint32_t)(k >> 6) * pstride + (uint32_t)row * 128u +
                                                      ((uint32_t)(((k >> 3) & 7) ^ (row & 7)) << 4);
-                                *reinterpret_cast<uint4 *>(sm + off) =
-                                    make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                                if (valid)
+                                    *reinterpret_cast<uint4 *>(sm + off) =
+                                        make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
                             }
                         }
                     }
@@ -550,35 +660,37 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     } else {
                         if (tid >= 128 && tid < 128 + HN) cp_wait<0>();   // S[e] landed (read after the barrier)
                         workers_sync();   // this CTA's rows of the pass are all in its own buffer
-                        const int n16 = P * C / 64 * 256;   // 16-byte chunks of this CTA's 32 rows
+                        constexpr int CPP = SPC * 8;        // 16-byte chunks of this CTA's rows per panel
+                        const int n16 = P * C / 64 * CPP;
                         for (int i = tid; i < n16; i += kWk) {
-                            const uint32_t off = (uint32_t)(i >> 8) * 16384u + rank * (kSPC * 128) + (uint32_t)(i & 255) * 16u;
+                            const uint32_t off = (uint32_t)(i / CPP) * 16384u + rank * (SPC * 128) + (uint32_t)(i % CPP) * 16u;
                             const uint4 v = *reinterpret_cast<const uint4 *>(sm + y.fc1a + off);
-                            for (int r = 1; r < kCS; r++) cl_st_v4(cl_map(fc0 + off, (rank + r) % kCS), v);
+                            for (int r = 1; r < CS; r++) cl_st_v4(cl_map(fc0 + off, (rank + r) % CS), v);
                         }
                         fence_async_cluster();
                         __syncwarp();
-                        if (lane < kCS) cl_arrive(cl_map(bar(B_FULL), (uint32_t)lane));
+                        if (lane < CS) cl_arrive(cl_map(bar(B_FULL), (uint32_t)lane));
                         // FC1 over this pass's positions, once every CTA's rows are in (thread 0)
                         if (tid == 0 && mma_ok) {
-                            const uint64_t tw = prof ? gtimer() : 0;
-                            if (!cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status)) mma_ok = false;
-                            if (prof) a.prof[18] += gtimer() - tw;
+                            const uint64_t tw = prof ? (uint64_t)clock64() : 0;
+                            if (!note(cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status), 7, t, R)) mma_ok = false;
+                            if (prof) pacc[18] += (uint64_t)clock64() - tw;
                             fence_async_smem();
                             tc_fence_after();
                             const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
                             for (int pi = 0; pi < P * C / 64 && mma_ok; pi++) {
                                 int s;
-                                if (!take(s)) { mma_ok = false; break; }
+                                if (!take(s, L)) { mma_ok = false; break; }
                                 const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u), bd = sdesc(ring0 + s * kStage);
 #pragma unroll
                                 for (int k = 0; k < 4; k++)
                                     umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
                                                 (q0 | pi | k) != 0 ? 1u : 0u);
-                                commit_mc(bar(S + s), (uint16_t)((1u << kCS) - 1u));
+                                if (kMulticastWeights) commit_mc(bar(S + s), kAll);
+                                else umma_commit(bar(S + s));
                                 it++;
                             }
-                            if (mma_ok) commit_mc(bar(B_EMPTY), (uint16_t)((1u << kCS) - 1u));
+                            if (mma_ok) commit_mc(bar(B_EMPTY), kAll);
                         }
                         __syncwarp();
                         R++;
@@ -590,7 +702,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             __syncwarp();
             // FC1 epilogue: ReLU(FC1 + bias + S[e]) folded into FC2 partials per slot
             {
-                bool ok = mbar_wait(bar(B_DFC), (uint32_t)(t & 1), lim, abort_f, a.status);
+                bool ok = note(sleep_wait(bar(B_DFC), (uint32_t)(t & 1), lim, abort_f, a.status, false), 8, t, R);
                 ok = __all_sync(0xffffffffu, ok);
                 tc_fence_after();
                 mark(8);
@@ -612,26 +724,27 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     }
                 }
                 tc_fence_before();
-                // slot qd * 32 + lane of the cluster belongs to CTA qd, where it is slot `lane`
-                cl_st_v2f(cl_map(smem_u32(&part[((int)rank * 2 + half) * kSPC + lane]), (uint32_t)qd), pf, pe);
+                // cluster slot g = qd * 32 + lane belongs to CTA g / SPC, where it is slot g % SPC
+                const int g = qd * 32 + lane, owner = g / SPC;
+                cl_st_v2f(cl_map(smem_u32(&part[((int)rank * 2 + half) * SPC + g % SPC]), (uint32_t)owner), pf, pe);
                 __syncwarp();
-                if (lane == 0) cl_arrive(cl_map(bar(B_PART), (uint32_t)qd));
+                if (g % SPC == 0) cl_arrive(cl_map(bar(B_PART), (uint32_t)owner));
                 mark(9);
             }
             // head, clock and queue update, drain: one thread per slot (warp 2)
             if (wi == 0) {
-                bool ok = cl_wait(bar(B_PART), (uint32_t)(t & 1), lim, abort_f, a.status);
+                bool ok = note(sleep_wait(bar(B_PART), (uint32_t)(t & 1), lim, abort_f, a.status, true), 9, t, R);
                 ok = __all_sync(0xffffffffu, ok);
                 mark(10);
                 const int s = lane;
-                if (ok && s_al[s]) {
+                if (ok && s < SPC && s_al[s]) {
                     const int64_t o = s_o[s];
                     const int n = s_n[s];
                     int p = s_p[s];
                     float zf = s_b2[0], ze = s_b2[1];
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const float2 v = part[i * kSPC + s];
+                    for (int i = 0; i < 2 * CS; i++) {
+                        const float2 v = part[i * SPC + s];
                         zf += v.x;
                         ze += v.y;
                     }
@@ -711,7 +824,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // barrier orders the last step's head (warp 2) before the other warps read its state
         cp_wait<0>();
         workers_sync();
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < SPC / 8; j++) {
             const int s = wi + 8 * j, b = s_b[s];
             if (b < 0) continue;
             for (int i = lane; i < cap; i += 32) A->ring[(size_t)b * cap + i] = qring[s * cap + i];
@@ -725,6 +838,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         }
     }
     __syncthreads();
+    if (a.prof && blockIdx.x == 0 && threadIdx.x < 32) a.prof[threadIdx.x] = pacc[threadIdx.x];
     if (warp == 0 && lane == 0) {   // weight panels issued but never consumed (early exit) land first
         for (int it = cnt[1]; it < cnt[0]; it++) drain_wait(bar(it % S), (uint32_t)(it / S) & 1u, drain_ns);
     }
@@ -738,8 +852,18 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 
 }  // namespace
 
+// Cluster size: 8 CTAs (16 slots each) when FC1 still gives each at least 64
+// neurons and the batch's clusters of 8 all fit on the GPU at once (every
+// cluster keeps its sub-traces for the whole call, so clusters that wait for
+// a free SM would run after the others); else 4 (32 slots each).
+static int cluster_size(const simnet_config &k, int B) {
+    if (k.fc_hidden / 8 < 64) return 4;
+    const int n_clusters = (B + 127) / 128;
+    return n_clusters * 8 <= num_sms() ? 8 : 4;
+}
+
 // Shapes this kernel handles: BF16; 2 or 3 conv layers of 64 or 128 channels;
-// FC1 width 256 or 512 (a quarter per CTA); queue capacity below 256.
+// FC1 width 256 or 512; queue capacity below 256.
 bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     const simnet_config &k = c->cfg;
     if (k.precision != SIMNET_BF16) { why = "not BF16"; return false; }
@@ -747,7 +871,7 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
     if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }
     if (c->cap > 255 || c->rows_n < 1) { why = "window"; return false; }
-    const CLay y = c_layout(k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2);
+    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2);   // the larger layout
     if (y.total + 1024 > 232448) { why = "shared memory"; return false; }
     return true;
 }
@@ -755,6 +879,7 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
 bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::string &why) {
     if (!cluster_eligible(c, why)) return false;
     const simnet_config &k = c->cfg;
+    const int CS = cluster_size(k, B);
     CArgs a;
     memset(&a, 0, sizeof a);
     a.L = k.n_conv;
@@ -764,11 +889,11 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.rows_n = c->rows_n;
     for (int l = 0; l < a.L; l++) {
         if (!encode_map_2d(a.tW[l], SIMNET_BF16, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, 64,
-                           (uint32_t)(a.C / kCS), why))
+                           (uint32_t)(a.C / CS), why))
             return false;
         a.cbias[l] = c->bias[l];
     }
-    if (!encode_map_2d(a.tF, SIMNET_BF16, c->Wl[a.L], (uint64_t)c->fc1_in, (uint64_t)a.H, 64, (uint32_t)(a.H / kCS), why))
+    if (!encode_map_2d(a.tF, SIMNET_BF16, c->Wl[a.L], (uint64_t)c->fc1_in, (uint64_t)a.H, 64, (uint32_t)(a.H / CS), why))
         return false;
     a.fbias = c->bias[a.L];
     a.w2 = c->w2;
@@ -777,28 +902,32 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.A = c->d_args;
     a.status = c->status;
     a.prof = c->phase_on ? c->phase_ns : nullptr;
+    a.tinfo = c->phase_ns + 48;
+    a.pos_sum = c->phase_ns + 56;
+    if (cudaMemsetAsync(a.tinfo, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) { why = "memset"; return false; }
     a.n_steps = n_steps;
     a.spin_ns = c->cfg.spin_limit_ns;
-    int stages = 6;
-    while (stages > 2 && c_layout(a.L, a.C, a.H, a.cap, stages).total + 1024 > 232448) stages--;
+    int stages = 8;
+    while (stages > 2 && c_layout(CS, a.L, a.C, a.H, a.cap, stages).total + 1024 > 232448) stages--;
     a.stages = stages;
-    const size_t smem = c_layout(a.L, a.C, a.H, a.cap, stages).total + 1024;
-    cudaError_t e = cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages).total + 1024;
+    auto kern = CS == 8 ? cluster_kernel<8> : cluster_kernel<4>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
-    const int n_clusters = (B + kCS * kSPC - 1) / (kCS * kSPC);
+    const int n_clusters = (B + 127) / 128;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_clusters * kCS);
+    cfg.gridDim = dim3(n_clusters * CS);
     cfg.blockDim = dim3(kCThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kCS;
+    at[0].val.clusterDim.x = CS;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, cluster_kernel, a);
+    e = cudaLaunchKernelEx(&cfg, kern, a);
     if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
     return true;
 }

@@ -716,14 +716,39 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
     if (n_steps <= 0) {
         launches = resume ? 0 : 1;
     } else if (persistent && !(c->cfg.flags & SIMNET_FLAG_NO_CLUSTER) && cluster_eligible(c, why_not_cluster)) {
-        // clusters own their sub-traces for the whole call: no grid-wide barriers
+        // Clusters own their sub-traces for the whole call: no grid-wide barriers.  Each
+        // cluster runs the last-conv positions below its padding extent in passes of a few
+        // positions, so when queues stay long the grid-wide kernel, which spreads the
+        // positions over every SM, is faster: the first kProbe steps (queues fill by at most
+        // one entry a step) measure the extent over their second half, and the rest of a
+        // long call continues on the grid kernel if that needed more than two passes a step
+        // (the state lives in the same device arrays either way).
+        constexpr int64_t kProbe = 128;
         c->phase_on = timed;
         if (timed) CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(c->phase_ns + 56, 0, 2 * sizeof(unsigned long long), s));
         c->phase_valid = timed;
         std::string why;
-        if (!launch_cluster(c, B, n_steps, s, why)) return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
+        const bool probe = !timed && n_steps > 4 * kProbe;
+        const int64_t first = probe ? kProbe : n_steps;
+        if (!launch_cluster(c, B, first, s, why)) return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
         launches = resume ? 1 : 2;
         c->path = SIMNET_PATH_CLUSTER;
+        if (probe) {
+            unsigned long long ps[2] = {0, 0};
+            CK(cudaMemcpyAsync(ps, c->phase_ns + 56, sizeof ps, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int pm = 8 >> (c->cfg.n_conv - 1);   // positions per pass
+            const bool long_queues = ps[1] > 0 && (double)ps[0] / (double)ps[1] > 2.0 * pm;
+            if (long_queues) {
+                if (!launch_persistent(c, B, n_steps - first, uneven, s, why))
+                    return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
+                c->path = SIMNET_PATH_PERSISTENT;
+            } else if (!launch_cluster(c, B, n_steps - first, s, why)) {
+                return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
+            }
+            launches += 1;
+        }
     } else if (persistent) {
         // one cooperative kernel runs every step; its phases are timed by CTA 0 on request
         c->phase_on = timed;
@@ -788,6 +813,13 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
         stats->kernel_launches = launches;
         stats->ms_total = ms;
         if (*c->h_status != kStatusOk) c->sim_valid = false;
+        if (*c->h_status == kStatusTimeout && c->path == SIMNET_PATH_CLUSTER) {
+            unsigned long long ti[4] = {0, 0, 0, 0};
+            cudaMemcpy(ti, c->phase_ns + 48, sizeof ti, cudaMemcpyDeviceToHost);
+            return fail(c, SIMNET_ETIMEOUT,
+                        "a device-side wait exceeded its bound (cluster kernel: wait site %llu, CTA %llu, step %lld, "
+                        "pass or panel %lld)", ti[0], ti[1], (long long)ti[2], (long long)ti[3]);
+        }
         if (*c->h_status == kStatusTimeout) return fail(c, SIMNET_ETIMEOUT, "a device-side wait exceeded its bound");
         if (*c->h_status != kStatusOk) return fail(c, SIMNET_ECUDA, "device status %d", *c->h_status);
     }

@@ -39,9 +39,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of a phase (inline: the common case of a phase that has
+// already completed costs no call).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait on a phase of an mbarrier; false if it gave up (or another role did).
-__device__ __noinline__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
-                                       int32_t *status) {
+__device__ __noinline__ inline bool mbar_wait_slow(uint32_t bar, uint32_t parity, int64_t limit,
+                                                   volatile int *abort_flag, int32_t *status) {
     if (mbar_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
@@ -53,6 +65,12 @@ __device__ __noinline__ inline bool mbar_wait(uint32_t bar, uint32_t parity, int
             return false;
         }
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t limit, volatile int *abort_flag,
+                                          int32_t *status) {
+    if (mbar_test(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, limit, abort_flag, status);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {

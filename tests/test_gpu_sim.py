@@ -148,6 +148,46 @@ def test_persistent_kernel_teacher_forced(precision, tol, kernel, case):
     assert np.median(d) < 1e-3 and d.max() < 0.1, (np.median(d), d.max())
 
 
+def test_cluster_kernel_large_batch_four_cta_clusters():
+    """2,500 sub-traces of the c2 CNN: 20 clusters, too many for clusters of 8
+    to be resident at once, so the kernel runs clusters of 4 CTAs (32 slots
+    each); the last cluster is partly empty.  Teacher-forced against the oracle
+    with integer state bit-exact."""
+    w = I.WORKLOADS["c2"]
+    rng = np.random.default_rng(25)
+    lengths = rng.integers(1, 24, 2500).tolist()
+    trace = I.small_trace(lengths, seed=25)
+    teacher_forced_check(w.arch, trace, "bf16", I.workload_weights(w), 5e-2, path="cluster")
+
+
+def test_cluster_done_before_the_call_ends():
+    """Two clusters of the c2 CNN, the first with sub-traces of 12 instructions
+    and the second of 150: the first cluster finishes while the call goes on
+    (its weight prefetch for a step that never comes must not block it).
+    Teacher-forced against the oracle."""
+    w = I.WORKLOADS["c2"]
+    trace = I.small_trace([12] * 128 + [150] * 128, seed=26)
+    teacher_forced_check(w.arch, trace, "bf16", I.workload_weights(w), 5e-2, path="cluster")
+
+
+def test_long_queues_move_to_the_grid_kernel():
+    """Replayed latencies F = 1, E = 200 fill every queue to capacity, so the
+    cluster kernel's probe (steps 64-127) sees more than two passes of
+    positions a step and the call continues on the grid-wide kernel from the
+    same device state; cycle counts and evictions stay bit-exact."""
+    w = I.WORKLOADS["c2"]
+    trace = I.small_trace([600] * 128, seed=27)
+    replay = np.zeros((trace.n_instructions, 2), np.uint8)
+    replay[:, 0], replay[:, 1] = 1, 200
+    cfg = oracle.Config.of(w.arch)
+    ref = oracle.simulate(cfg, trace.records, trace.offsets, replay=replay)
+    sim, _ = make_sim(w.arch, "bf16", blob=I.workload_weights(w))
+    g = run_gpu(sim, trace, replay=replay)
+    assert sim.kernel_path == "persistent"
+    np.testing.assert_array_equal(g["cycles"], ref.cycles)
+    assert g["stats"].evictions == int(ref.evictions.sum()) > 0
+
+
 def test_uneven_lengths_compaction():
     """Log-normal-like uneven lengths exercise the active-set compaction; the
     result must not depend on it (sub-traces are independent, Sec. 3.3)."""
