@@ -469,6 +469,47 @@ def roofline(w, args, blob32, rec, off, cyc, B):
     return roof, kernels
 
 
+def run_sweep(args):
+    """Sub-trace length against simulation error, the trade-off behind splitting
+    a trace for parallel simulation (Sec. 3.3): one synthetic trace of N
+    instructions with the c2 workload's record mix and CNN, simulated unsplit
+    (one sub-trace, FP32 form: the reference) and split into equal contiguous
+    sub-traces (BF16, default kernel path).  Each split sub-trace starts from
+    an empty queue and ends with its own drain, so its CPI drifts from the
+    unsplit CPI as sub-traces get shorter; prints one JSON line."""
+    import torch
+    from paper_2105_05821_b300.simnet import Simnet
+    w = I.WORKLOADS["c2"]
+    N = args.sweep_n
+    records = I.make_records(N, 7)
+    blob = I.workload_weights(w).astype(np.float32)
+    rec = torch.from_numpy(records.view(np.int32).copy()).cuda()
+
+    def run(sim, n_sub):
+        off = torch.from_numpy(I.equal_offsets(N, n_sub)).cuda()
+        sim.simulate(rec, off, stats=False)   # warm
+        torch.cuda.synchronize()
+        st = sim.simulate(rec, off)
+        return st.total_cycles / N, st.ms_total, sim.kernel_path
+
+    ref = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
+    ref.load_weights(blob)
+    cpi_ref, ms_ref, _ = run(ref, 1)
+    sim = Simnet.for_arch(w.arch, precision="bf16", retire_width=w.retire_width)
+    sim.load_weights(blob)
+    rows = []
+    length = N
+    while length >= args.sweep_min:
+        n_sub = N // length
+        cpi, ms, path = run(sim, n_sub)
+        rows.append({"subtrace_len": length, "n_subtraces": n_sub, "cpi": cpi, "cpi_error": cpi / cpi_ref - 1.0,
+                     "ms": ms, "inst_per_s": N / (ms / 1e3), "kernel_mode": path})
+        length //= 4
+    print(json.dumps({"metric": "CPI error of split simulation vs sub-trace length", "unit": "relative",
+                      "instructions": N, "reference": {"form": "FP32, one sub-trace", "cpi": cpi_ref, "ms": ms_ref},
+                      "data": "synthetic", "rows": rows}))
+
+
 def run_training(args):
     """Training throughput on the training workload (windows/s of fused library
     steps: gather, forward, MSE, hand-written backward, Adam); a side measurement,
@@ -516,6 +557,10 @@ def main():
                     help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
     ap.add_argument("--untrained", action="store_true", help="c4: keep the seeded weights")
     ap.add_argument("--train-steps", type=int, default=300, help="c4: training steps before simulating")
+    ap.add_argument("--sweep", action="store_true",
+                    help="CPI error against sub-trace length (one trace split into more and more parts)")
+    ap.add_argument("--sweep-n", type=int, default=65536, help="--sweep: trace length")
+    ap.add_argument("--sweep-min", type=int, default=64, help="--sweep: shortest sub-trace")
     ap.add_argument("--subtrace-len", type=int, default=0,
                     help="keep only the first N instructions of every sub-trace (profiling runs)")
     args = ap.parse_args()
@@ -526,6 +571,9 @@ def main():
         return
     if args.workload == "c3":
         run_training(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if world > 1:
         import torch

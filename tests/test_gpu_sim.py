@@ -188,6 +188,19 @@ def test_long_queues_move_to_the_grid_kernel():
     assert g["stats"].evictions == int(ref.evictions.sum()) > 0
 
 
+def test_single_long_subtrace_free_running_fp32():
+    """One sub-trace of 3,000 instructions (no splitting, B = 1: the reference
+    of the sub-trace-length sweep) free-running in FP32 against the FP64
+    oracle: CPI within 0.1 %."""
+    w = I.WORKLOADS["c2"]
+    trace = I.small_trace([3000], seed=28)
+    blob = I.workload_weights(w)
+    ref = oracle.simulate(oracle.Config.of(w.arch), trace.records, trace.offsets, blob)
+    sim, _ = make_sim(w.arch, "fp32", blob=blob)
+    g = run_gpu(sim, trace, logs=False)
+    assert abs(g["cycles"].sum() / ref.cycles.sum() - 1.0) <= FP32_CPI_TOL
+
+
 def test_uneven_lengths_compaction():
     """Log-normal-like uneven lengths exercise the active-set compaction; the
     result must not depend on it (sub-traces are independent, Sec. 3.3)."""
