@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
 
 class _Cfg(C.Structure):
     _fields_ = [("window", C.c_int32), ("n_conv", C.c_int32), ("channels", C.c_int32),
-                ("hidden", C.c_int32), ("retire_width", C.c_int32), ("retire_strict", C.c_int32)]
+                ("hidden", C.c_int32), ("retire_width", C.c_int32), ("retire_strict", C.c_int32),
+                ("hybrid", C.c_int32)]
 
 
 _lib = None
@@ -77,15 +78,20 @@ class Config:
     hidden: int
     retire_width: int = 8
     retire_strict: bool = False
+    hybrid: bool = False          # hybrid head (22 FC2 outputs) instead of regression (2)
+
+    @property
+    def n_out(self) -> int:
+        return 22 if self.hybrid else 2
 
     def c(self) -> _Cfg:
         return _Cfg(self.window, self.n_conv, self.channels, self.hidden, self.retire_width,
-                    int(self.retire_strict))
+                    int(self.retire_strict), int(self.hybrid))
 
     @staticmethod
     def of(arch, retire_width: int = 8, retire_strict: bool = False) -> "Config":
         return Config(arch.window, arch.n_conv, arch.channels, arch.hidden, retire_width,
-                      retire_strict)
+                      retire_strict, getattr(arch, "head", "regression") == "hybrid")
 
 
 def blob_size(cfg: Config) -> int:
@@ -140,12 +146,13 @@ def simulate(cfg: Config, records: np.ndarray, offsets: np.ndarray,
 
 
 def cnn_forward(cfg: Config, weights: np.ndarray, x: np.ndarray, n_threads: int = 0) -> np.ndarray:
-    """Pre-softplus CNN outputs z [n, 2] for feature matrices x [n, W, 50]."""
+    """FC2 outputs z [n, n_out] (before softplus / the class decision) for
+    feature matrices x [n, W, 50]."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     n = x.shape[0]
     assert x.shape[1:] == (cfg.window, NF)
     w = np.ascontiguousarray(weights, dtype=np.float64)
-    z = np.zeros((n, 2))
+    z = np.zeros((n, cfg.n_out))
     c = cfg.c()
     if _L().oracle_cnn_forward(C.byref(c), _p(w), _p(x), n, _p(z), int(n_threads)) != 0:
         raise ValueError("bad config")
@@ -173,7 +180,8 @@ def window_features(cfg: Config, records, fetch, e_label, ctx_begin, idx) -> np.
 
 
 def loss_grad(cfg: Config, weights: np.ndarray, x: np.ndarray, y: np.ndarray):
-    """(loss, grad) of the mean squared error of softplus(z) against y [n, 2]."""
+    """(loss, grad) for labels y [n, 2]: mean squared error of softplus(z), plus the
+    cross-entropy of the class logits for a hybrid head (oracle.c states the loss)."""
     w = np.ascontiguousarray(weights, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 2)

@@ -12,6 +12,9 @@
  *   - the CNN latency predictor: k=2 / stride-2 convolutions with ReLU,
  *     flatten, FC + ReLU, FC to (fetch, execution) (Sec. 2.3, Fig. 2);
  *   - latency = softplus(output), clamped to [0, 255] and rounded half-to-even;
+ *     or, with the hybrid head (Sec. 2.3), per latency the class with the
+ *     largest of 10 logits (0..8 cycles, or "more than 8", which takes the
+ *     regression output as above);
  *   - the processor queue and curTick clock: fetch latency advances curTick,
  *     in-order retire when residence reaches the execution latency, retire
  *     bandwidth, eviction at capacity, append with residence 0, and the drain
@@ -19,8 +22,9 @@
  *     the sum of fetch latencies plus Delta (Sec. 3.1, Eq. 1);
  *   - sub-traces simulated independently, each from an empty queue and
  *     curTick = 0 (Sec. 3.3);
- *   - the MSE training loss, its analytic FP64 gradient and an Adam step
- *     (Sec. 2.4).
+ *   - the MSE training loss (hybrid head: cross-entropy of the class logits
+ *     plus the squared error of the regression output), its analytic FP64
+ *     gradient and an Adam step (Sec. 2.4).
  *
  * Readings taken where the paper is silent (each also listed in the design
  * notes): L = W rows (current + W-1 context) and queue capacity W-1; an
@@ -59,7 +63,12 @@ typedef struct {
     int32_t hidden;        /* FC1 width */
     int32_t retire_width;  /* processor-queue retire bandwidth per cycle */
     int32_t retire_strict; /* 0: ready at residence >= E; 1: residence > E */
+    int32_t hybrid;        /* 0: regression head (2 outputs); 1: hybrid head (22 outputs) */
 } oracle_cfg;
+
+/* FC2 outputs: regression [fetch, execution]; hybrid, per latency t in {fetch,
+ * execution}: 10 class logits (0..8 cycles, "more than 8") then one value. */
+static int n_out(const oracle_cfg *c) { return c->hybrid ? 22 : 2; }
 
 /* ------------------------------------------------------------------ records */
 typedef struct { int op, s0, s1, dst, ld, st, br, lvl, mp; } inst_t;
@@ -125,7 +134,7 @@ static int64_t blob_size(const oracle_cfg *c)
         cin = c->channels;
     }
     int64_t fin = (int64_t)c->channels * (c->window >> c->n_conv);
-    n += fin * c->hidden + c->hidden + 2 * (int64_t)c->hidden + 2;
+    n += fin * c->hidden + c->hidden + (int64_t)n_out(c) * c->hidden + n_out(c);
     return n;
 }
 
@@ -142,7 +151,7 @@ static net_t net_view(const oracle_cfg *c, const double *blob)
     int64_t fin = (int64_t)c->channels * (c->window >> c->n_conv);
     n.w1 = p; p += fin * c->hidden;
     n.b1 = p; p += c->hidden;
-    n.w2 = p; p += 2 * (int64_t)c->hidden;
+    n.w2 = p; p += (int64_t)n_out(c) * c->hidden;
     n.b2 = p;
     return n;
 }
@@ -151,7 +160,7 @@ static net_t net_view(const oracle_cfg *c, const double *blob)
 typedef struct {
     double *act[MAXCONV + 1];  /* act[0] = input [W][NF]; act[k+1] = conv k out [W>>(k+1)][C] */
     double *hid;               /* FC1 output after ReLU [H] */
-    double z[2];               /* FC2 output (pre-softplus) */
+    double z[22];              /* FC2 outputs (before softplus / class decision) */
 } fwd_t;
 
 static size_t fwd_doubles(const oracle_cfg *c)
@@ -204,7 +213,7 @@ static void cnn_forward(const oracle_cfg *c, const net_t *n, fwd_t *f)
                 s += n->w1[h * fin + (int64_t)ch * rows + l] * a[(int64_t)l * cin + ch];
         f->hid[h] = s > 0.0 ? s : 0.0;
     }
-    for (int k = 0; k < 2; k++) {
+    for (int k = 0; k < n_out(c); k++) {
         double s = n->b2[k];
         for (int h = 0; h < c->hidden; h++) s += n->w2[(int64_t)k * c->hidden + h] * f->hid[h];
         f->z[k] = s;
@@ -222,6 +231,26 @@ static int to_cycles(double y)
     if (y < 0.0) y = 0.0;
     if (y > 255.0) y = 255.0;
     return (int)nearbyint(y);
+}
+
+/* Latency t (0 fetch, 1 execution) from the FC2 outputs z; *pre gets the
+ * regression output after softplus.  Regression head: that value, clamped and
+ * rounded.  Hybrid head (Sec. 2.3): the class with the largest logit of
+ * z[11t .. 11t+9], compared after rounding to FP32 as the kernels compute
+ * them (lowest class on ties); classes 0..8 are that many cycles, class 9
+ * ("more than 8") takes the regression output. */
+static int head_latency(const oracle_cfg *c, const double *z, int t, double *pre)
+{
+    if (!c->hybrid) {
+        *pre = softplus(z[t]);
+        return to_cycles(*pre);
+    }
+    const double *lg = z + 11 * t;
+    int k = 0;
+    for (int j = 1; j < 10; j++)
+        if ((float)lg[j] > (float)lg[k]) k = j;
+    *pre = softplus(lg[10]);
+    return k <= 8 ? k : to_cycles(*pre);
 }
 
 /* ------------------------------------------------------------------ queue + clock (Sec. 3.2) */
@@ -286,10 +315,10 @@ static int64_t simulate_one(const oracle_cfg *c, const net_t *net, const uint32_
         if (net) {
             fwd_bind(c, mem, X, &f);
             cnn_forward(c, net, &f);
-            double yf = softplus(f.z[0]), ye = softplus(f.z[1]);
+            double yf, ye;
+            F = head_latency(c, f.z, 0, &yf);
+            E = head_latency(c, f.z, 1, &ye);
             if (lg->pre_log) { lg->pre_log[2 * i] = yf; lg->pre_log[2 * i + 1] = ye; }
-            F = to_cycles(yf);
-            E = to_cycles(ye);
         }
         if (lg->replay) { F = lg->replay[2 * i]; E = lg->replay[2 * i + 1]; }
         if (lg->lat_log) { lg->lat_log[2 * i] = (uint8_t)F; lg->lat_log[2 * i + 1] = (uint8_t)E; }
@@ -369,7 +398,7 @@ int oracle_simulate(const oracle_cfg *c, const double *weights, const uint32_t *
     return 0;
 }
 
-/* CNN outputs for a batch of feature matrices x [n][W][NF]: z_out [n][2] before softplus. */
+/* CNN outputs for a batch of feature matrices x [n][W][NF]: z_out [n][n_out] (FC2 outputs). */
 int oracle_cnn_forward(const oracle_cfg *c, const double *weights, const double *x, int64_t n,
                        double *z_out, int32_t n_threads)
 {
@@ -388,8 +417,7 @@ int oracle_cnn_forward(const oracle_cfg *c, const double *weights, const double 
         for (int64_t i = 0; i < n; i++) {
             fwd_bind(c, mem, x + i * (int64_t)c->window * NF, &f);
             cnn_forward(c, &net, &f);
-            z_out[2 * i] = f.z[0];
-            z_out[2 * i + 1] = f.z[1];
+            for (int k = 0; k < n_out(c); k++) z_out[(int64_t)n_out(c) * i + k] = f.z[k];
         }
         free(mem);
     }
@@ -427,9 +455,12 @@ int oracle_window_features(const oracle_cfg *c, const uint32_t *records, int64_t
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */
 /*
- * Loss J = mean over the n*2 outputs of (softplus(z) - y)^2 with y the label
- * clamped to [0, 255] (squared-error loss, Sec. 2.4).  grad_out gets dJ/dtheta
- * in blob order (FP64, summed over the batch in sample order).
+ * Loss J = mean over the n*2 latencies of (softplus(z) - y)^2 with y the label
+ * clamped to [0, 255] (squared-error loss, Sec. 2.4).  Hybrid head: the same
+ * mean over the latencies of the cross-entropy of the 10 class logits against
+ * class min(y, 9) plus the squared error of softplus(regression output) (the
+ * paper gives no weighting; both terms count once).  grad_out gets dJ/dtheta in
+ * blob order (FP64, summed over the batch in sample order).
  */
 int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x,
                      const double *y, int64_t n, double *loss_out, double *grad_out)
@@ -453,21 +484,34 @@ int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x
         fwd_t f;
         fwd_bind(c, mem, x + i * (int64_t)W * NF, &f);
         cnn_forward(c, &net, &f);
-        double dz[2];
+        double dz[22];
         for (int k = 0; k < 2; k++) {
             double t = y[2 * i + k];
             t = t < 0 ? 0 : (t > 255 ? 255 : t);
-            double yhat = softplus(f.z[k]);
+            const int reg = c->hybrid ? 11 * k + 10 : k;   /* the regression output */
+            double yhat = softplus(f.z[reg]);
             double r = yhat - t;
             loss += r * r;
             /* d/dz softplus(z) = sigmoid(z), and 1 above the threshold */
-            double ds = f.z[k] > 20.0 ? 1.0 : sigmoid(f.z[k]);
-            dz[k] = 2.0 * r / (2.0 * (double)n) * ds;
+            double ds = f.z[reg] > 20.0 ? 1.0 : sigmoid(f.z[reg]);
+            dz[reg] = 2.0 * r / (2.0 * (double)n) * ds;
+            if (c->hybrid) {
+                /* cross-entropy: log-sum-exp of the logits minus the target class's */
+                const double *lg = f.z + 11 * k;
+                const int cls = t > 8.0 ? 9 : (int)t;
+                double mx = lg[0];
+                for (int j = 1; j < 10; j++) mx = lg[j] > mx ? lg[j] : mx;
+                double se = 0.0;
+                for (int j = 0; j < 10; j++) se += exp(lg[j] - mx);
+                loss += mx + log(se) - lg[cls];
+                for (int j = 0; j < 10; j++)
+                    dz[11 * k + j] = (exp(lg[j] - mx) / se - (j == cls ? 1.0 : 0.0)) / (2.0 * (double)n);
+            }
         }
         /* FC2 */
         double *dh = dcur;
         for (int h = 0; h < H; h++) dh[h] = 0.0;
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < n_out(c); k++) {
             ((double *)g.b2)[k] += dz[k];
             for (int h = 0; h < H; h++) {
                 ((double *)g.w2)[(int64_t)k * H + h] += dz[k] * f.hid[h];

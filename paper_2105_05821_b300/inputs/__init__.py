@@ -47,11 +47,21 @@ CHUNK = 1 << 22          # instructions drawn per chunk; part of the stream's de
 @dataclass(frozen=True)
 class Arch:
     """CNN shape: ``n_conv`` k=2/s=2 conv layers of ``channels`` outputs over
-    ``window`` rows, then FC ``hidden`` and FC 2 (Sec. 2.3)."""
+    ``window`` rows, then FC ``hidden`` and the output layer FC2 (Sec. 2.3).
+    ``head`` = "regression": FC2 gives one value per latency (fetch,
+    execution); "hybrid" (Sec. 2.3's hybrid scheme): per latency 10 class
+    logits (0..8 cycles and "more than 8") and one regression value, in the
+    order [fetch classes 0-9, fetch value, execution classes 0-9, execution
+    value]."""
     window: int
     n_conv: int
     channels: int
     hidden: int
+    head: str = "regression"
+
+    @property
+    def n_out(self) -> int:
+        return 22 if self.head == "hybrid" else 2
 
     @property
     def rows_out(self) -> int:
@@ -71,8 +81,8 @@ class Arch:
             cin = self.channels
         out.append(("fc1.weight", (self.hidden, self.fc1_in)))
         out.append(("fc1.bias", (self.hidden,)))
-        out.append(("fc2.weight", (2, self.hidden)))
-        out.append(("fc2.bias", (2,)))
+        out.append(("fc2.weight", (self.n_out, self.hidden)))
+        out.append(("fc2.bias", (self.n_out,)))
         return out
 
     def n_params(self) -> int:
@@ -85,7 +95,7 @@ class Arch:
             rows //= 2
             macs += rows * self.channels * cin * 2
             cin = self.channels
-        macs += self.fc1_in * self.hidden + self.hidden * 2
+        macs += self.fc1_in * self.hidden + self.hidden * self.n_out
         return macs
 
 
@@ -271,19 +281,38 @@ FC2_GAIN = (8.0, 25.0)    # scale of the fetch / execution rows of FC2
 FC2_BIAS = (0.3, 12.0)    # FC2 bias (fetch, execution)
 
 
+# Hybrid head: class-logit rows are scaled by HYB_CLASS_GAIN and biased
+# towards small fetch latencies and mid-range execution latencies (logit
+# bias per class 0..9).
+HYB_CLASS_GAIN = 6.0
+HYB_CLASS_BIAS = ((3.0, 2.5, 1.0, 0.0, -0.5, -1.0, -1.5, -2.0, -2.5, -3.0),
+                  (-2.0, 0.5, 1.0, 1.0, 0.8, 0.6, 0.4, 0.2, 0.0, 1.5))
+
+
 def workload_weights(w: Workload) -> np.ndarray:
     """FP64 master blob for a workload: He-normal from PCG64(seed), zero
-    biases, except that FC2's two rows are scaled by ``FC2_GAIN`` and biased by
-    ``FC2_BIAS``.  Plain He-init gives near-constant outputs (every F = 1,
-    E = 0, a queue of length one); this recipe gives the mixed trajectory a
-    trained predictor would (F mostly 0-1, E spread over 1-20 cycles, the queue
-    partly full, occasional evictions)."""
+    biases, except that FC2's regression rows (fetch, execution) are scaled by
+    ``FC2_GAIN`` and biased by ``FC2_BIAS``.  Plain He-init gives near-constant
+    outputs (every F = 1, E = 0, a queue of length one); this recipe gives the
+    mixed trajectory a trained predictor would (F mostly 0-1, E spread over
+    1-20 cycles, the queue partly full, occasional evictions).  For a hybrid
+    head the class-logit rows are scaled by ``HYB_CLASS_GAIN`` and biased by
+    ``HYB_CLASS_BIAS`` so that every class wins somewhere."""
     ws = he_weights(w.arch, w.seed)
     w2 = ws[-2][1].copy()
-    w2[0] *= FC2_GAIN[0]
-    w2[1] *= FC2_GAIN[1]
+    b2 = np.zeros(w.arch.n_out)
+    if w.arch.head == "hybrid":
+        for t in range(2):
+            w2[11 * t:11 * t + 10] *= HYB_CLASS_GAIN
+            b2[11 * t:11 * t + 10] = HYB_CLASS_BIAS[t]
+            w2[11 * t + 10] *= FC2_GAIN[t]
+            b2[11 * t + 10] = FC2_BIAS[t]
+    else:
+        w2[0] *= FC2_GAIN[0]
+        w2[1] *= FC2_GAIN[1]
+        b2[:] = FC2_BIAS
     ws[-2] = ("fc2.weight", w2)
-    ws[-1] = ("fc2.bias", np.array(FC2_BIAS, dtype=np.float64))
+    ws[-1] = ("fc2.bias", b2)
     return flatten_weights(ws)
 
 
