@@ -13,6 +13,7 @@ flush is outside the step's CUDA-event pair.  Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import subprocess
@@ -132,11 +133,20 @@ def cpu_sample_ids(w, trace, blob, target_s=15.0):
     return list(range(min(n, trace.n_subtraces))), threads
 
 
+def workload_of(args) -> I.Workload:
+    """The named workload, with the hybrid latency head (Sec. 2.3) on request."""
+    w = I.WORKLOADS[args.workload]
+    if getattr(args, "head", "regression") == "hybrid":
+        a = w.arch
+        w = dataclasses.replace(w, arch=I.Arch(a.window, a.n_conv, a.channels, a.hidden, "hybrid"))
+    return w
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    w = I.WORKLOADS[args.workload]
+    w = workload_of(args)
     trace = I.make_trace(w)
     blob = I.workload_weights(w)
     threads = host_cores()
@@ -167,7 +177,8 @@ def workload_config(w, args, note=""):
     c = {"workload": f"{w.name}: {w.description}", "n_subtraces": w.n_subtraces,
          "instructions_per_step": None, "window": w.arch.window, "n_conv": w.arch.n_conv,
          "channels": w.arch.channels, "fc_hidden": w.arch.hidden, "retire_width": w.retire_width,
-         "precision": args.precision, "l2": "flushed (512 MB write) before every timed step"}
+         "precision": args.precision, "head": w.arch.head,
+         "l2": "flushed (512 MB write) before every timed step"}
     if note:
         c["note"] = note
     return c
@@ -256,7 +267,7 @@ def run_ours(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w = I.WORKLOADS[args.workload]
+    w = workload_of(args)
     trace = I.make_trace(w)
     if args.subtrace_len:
         trace = truncate(trace, args.subtrace_len)
@@ -430,8 +441,10 @@ def roofline(w, args, blob32, rec, off, cyc, B):
     around every launch; roofline of the kernel with the largest share."""
     from paper_2105_05821_b300.simnet import Simnet
     hbm, bf16_burst, bf16_sus, src = peaks()
+    # the per-layer or grid-persistent path (a cluster call that hands its long
+    # queues to the grid kernel is measured here as the grid kernel)
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          kernel_events=True, persistent=not args.layerwise)
+                          kernel_events=True, persistent=not args.layerwise, cluster=False)
     sim.load_weights(blob32)
     if args.precision != "fp32" and not args.no_autotune:
         sim.autotune(B)
@@ -555,6 +568,8 @@ def main():
     ap.add_argument("--no-cluster", action="store_true", help="BF16: the grid-wide persistent kernel")
     ap.add_argument("--layerwise", action="store_true",
                     help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
+    ap.add_argument("--head", default="regression", choices=["regression", "hybrid"],
+                    help="latency head: regression (2 FC2 outputs) or the hybrid classes + regression (22)")
     ap.add_argument("--untrained", action="store_true", help="c4: keep the seeded weights")
     ap.add_argument("--train-steps", type=int, default=300, help="c4: training steps before simulating")
     ap.add_argument("--sweep", action="store_true",

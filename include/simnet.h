@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define SIMNET_ABI_VERSION 2
+#define SIMNET_ABI_VERSION 3
 #define SIMNET_N_FEATURES 50 /* features per instruction row (Sec. 2.2) */
 
 typedef struct simnet_ctx simnet_ctx;
@@ -76,6 +76,14 @@ typedef enum {
                                           persistent kernel that skips the padding */
 #define SIMNET_FLAG_NO_CLUSTER 0x20u   /* BF16: the grid-wide persistent kernel even where the
                                           cluster kernel (SIMNET_PATH_CLUSTER) applies */
+#define SIMNET_FLAG_HYBRID_HEAD 0x40u  /* hybrid latency head (Sec. 2.3): FC2 has 22 outputs, for
+                                          each latency t (0 fetch, 1 execution) ten class logits
+                                          z[11t+0..11t+9] and a regression output z[11t+10].  The
+                                          latency is the class with the largest logit (compared in
+                                          FP32, lowest index on ties) for classes 0..8, and
+                                          round(clamp(softplus(z[11t+10]), 0, 255)) for class 9
+                                          ("more than 8").  Without it FC2 has 2 outputs and
+                                          latency t is round(clamp(softplus(z[t]), 0, 255)). */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -172,8 +180,10 @@ int64_t simnet_weight_count(const simnet_ctx *ctx);
  * float32 in canonical order and PyTorch shapes: for k = 1..n_conv
  * conv_k.weight [C, C_in, 2] (C_in = 50 for k = 1, else C), conv_k.bias [C];
  * then fc1.weight [H, C * (W >> n_conv)] whose input index is
- * channel * (W >> n_conv) + row; fc1.bias [H]; fc2.weight [2, H]; fc2.bias [2]
- * (output 0 = fetch latency, 1 = execution latency).  The library copies,
+ * channel * (W >> n_conv) + row; fc1.bias [H]; fc2.weight [n_out, H];
+ * fc2.bias [n_out].  n_out = 2 (output 0 = fetch latency, 1 = execution
+ * latency), or 22 with SIMNET_FLAG_HYBRID_HEAD (outputs 11t..11t+10 for
+ * latency t, in the order given there).  The library copies,
  * re-lays out and converts it to the context's precision; for FP8 it also
  * derives per-channel weight scales and, from a calibration pass over
  * synthetic context rows, per-channel activation scales.
@@ -264,7 +274,8 @@ simnet_status simnet_state_load(simnet_ctx *ctx, int32_t kind, const void *host_
 /*
  * Run the CNN alone on feature matrices (Sec. 2.3).
  *   x  device float [n][window][50]: rows as the simulator builds them.
- *   z  device float [n][2]: outputs before softplus.
+ *   z  device float [n][n_out]: FC2 outputs before softplus and the class decision
+ *      (n_out = 2, or 22 with SIMNET_FLAG_HYBRID_HEAD).
  * Uses the context's precision (inputs are rounded to it).
  * Errors: EINVAL (n < 0 or null pointers), ESTATE (no weights).
  */
@@ -348,7 +359,7 @@ simnet_status simnet_gather_windows(simnet_ctx *ctx, const simnet_windows *w, co
 
 /*
  * CNN forward for training: x device float [n][window][50], z device float
- * [n][2] (before softplus).  Keeps every layer's output for the next
+ * [n][n_out] (FC2 outputs before softplus).  Keeps every layer's output for the next
  * simnet_train_backward (one forward is kept per context).  FP32 contexts
  * compute in FP32; BF16 contexts round GEMM operands to BF16 and accumulate
  * in FP32 (autocast numerics).  Errors: EINVAL, ESTATE, EUNSUPPORTED (FP8).
@@ -356,7 +367,7 @@ simnet_status simnet_gather_windows(simnet_ctx *ctx, const simnet_windows *w, co
 simnet_status simnet_train_forward(simnet_ctx *ctx, const float *x, float *z, int32_t n, void *stream);
 
 /*
- * Backward of the last simnet_train_forward: dz device float [n][2] (dLoss/dz),
+ * Backward of the last simnet_train_forward: dz device float [n][n_out] (dLoss/dz),
  * grad device float [simnet_weight_count] receives dLoss/dtheta in the
  * canonical blob layout of simnet_load_weights (overwritten).
  * Errors: EINVAL, ESTATE (no forward yet).
@@ -365,8 +376,10 @@ simnet_status simnet_train_backward(simnet_ctx *ctx, const float *dz, float *gra
 
 /*
  * One training step on the windows idx[0..batch) (device int64): gather, forward,
- * loss = mean over the 2*batch outputs of (softplus(z) - label)^2 (labels are
- * 0..255), backward, and an Adam step (beta 0.9/0.999, eps 1e-8, no weight
+ * loss = mean over the 2*batch latencies of (softplus(z) - label)^2 (labels are
+ * 0..255; z the regression output of the latency); with SIMNET_FLAG_HYBRID_HEAD
+ * each latency adds the cross-entropy of its ten class logits against class
+ * min(label, 9) (Sec. 2.3); backward, and an Adam step (beta 0.9/0.999, eps 1e-8, no weight
  * decay) with learning rate lr on FP32 master weights; a BF16 context's BF16
  * weights are refreshed from them.  loss_out (host) or NULL; when given the call
  * synchronises `stream`.  Later simulate/cnn_forward calls use the new weights.
@@ -388,7 +401,7 @@ simnet_status simnet_get_weights(simnet_ctx *ctx, float *blob);
  * implicit synchronisation).  The paper has no counterpart; it is a property
  * of this library's interface.
  *   x, z, n, stream  as simnet_cnn_forward (x device float [n][window][50],
- *                    z device float [n][2], outputs before softplus).
+ *                    z device float [n][n_out], FC2 outputs before softplus).
  * The context must use SIMNET_FP32 and have weights loaded, else
  * SIMNET_EUNSUPPORTED.  The call allocates nothing: its workspace is a
  * file-scope device array of SIMNET_NOALLOC_SCRATCH_BYTES that every GPU

@@ -55,6 +55,8 @@ def _L():
                                          P, P, P, P, P, C.c_int32]
         _lib.oracle_cnn_forward.restype = C.c_int
         _lib.oracle_cnn_forward.argtypes = [P, P, P, C.c_int64, P, C.c_int32]
+        _lib.oracle_head.restype = C.c_int
+        _lib.oracle_head.argtypes = [P, P, C.c_int64, P, P]
         _lib.oracle_window_features.restype = C.c_int
         _lib.oracle_window_features.argtypes = [P, P, C.c_int64, P, P, P, P, C.c_int64, P]
         _lib.oracle_loss_grad.restype = C.c_int
@@ -157,6 +159,20 @@ def cnn_forward(cfg: Config, weights: np.ndarray, x: np.ndarray, n_threads: int 
     if _L().oracle_cnn_forward(C.byref(c), _p(w), _p(x), n, _p(z), int(n_threads)) != 0:
         raise ValueError("bad config")
     return z
+
+
+def head(cfg: Config, z: np.ndarray):
+    """The head's latency decision on FC2 outputs z [n, n_out]: (lat [n, 2]
+    uint8, pre [n, 2] softplus of the regression output)."""
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    n = z.shape[0]
+    assert z.shape[1:] == (cfg.n_out,)
+    lat = np.zeros((n, 2), np.uint8)
+    pre = np.zeros((n, 2))
+    c = cfg.c()
+    if _L().oracle_head(C.byref(c), _p(z), n, _p(lat), _p(pre)) != 0:
+        raise ValueError("bad config")
+    return lat, pre
 
 
 def softplus(z: np.ndarray) -> np.ndarray:

@@ -424,6 +424,17 @@ int oracle_cnn_forward(const oracle_cfg *c, const double *weights, const double 
     return 0;
 }
 
+/* The latency decision of the head on given FC2 outputs z [n][n_out]: lat [n][2]
+ * (the integer latencies) and pre [n][2] (softplus of the regression output). */
+int oracle_head(const oracle_cfg *c, const double *z, int64_t n, uint8_t *lat, double *pre)
+{
+    if (!cfg_ok(c)) return -1;
+    for (int64_t i = 0; i < n; i++)
+        for (int t = 0; t < 2; t++)
+            lat[2 * i + t] = (uint8_t)head_latency(c, z + (int64_t)n_out(c) * i, t, &pre[2 * i + t]);
+    return 0;
+}
+
 /*
  * Teacher-forced training windows (labels from a timing model).  Window of
  * instruction i: row 0 = instruction i; rows 1.. = instructions i-1, i-2, ...

@@ -73,7 +73,16 @@ struct CLay {
     uint32_t ring, act, fc1a, qring, rec, part, prm, slot, misc, bars, total;
 };
 
-__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages) {
+// FC2 partial sums per (source CTA, column half, slot): 2 floats (regression
+// head), or the hybrid head's 22 padded to 24 (16-byte stores).
+__host__ __device__ inline int part_floats(int no) { return no == 2 ? 2 : 24; }
+// prm: conv biases [L*C] | FC1 bias [HN] | S[e] [HN] | b2 [24] | FC2 rows of this
+// CTA's neurons: [2][HN] (regression) or [HN][24] (hybrid, padded).
+__host__ __device__ inline int prm_floats(int L, int C, int HN, int no) {
+    return L * C + 2 * HN + 24 + (no == 2 ? 2 * HN : 24 * HN);
+}
+
+__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages, int no) {
     CLay y;
     const int HN = H / CS, SPC = 128 / CS, PM = pass_positions(L);
     // operand of layer l: its rows (pass positions x pairs x slots) x K, in 64-column panels
@@ -88,9 +97,8 @@ __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, i
     y.qring = y.fc1a + 256u * (uint32_t)(pass_positions(L) * C);           // 128 slots x positions x C BF16
     y.rec = y.qring + (uint32_t)SPC * cap * 8;
     y.part = al_up(y.rec + SPC * 4 * 4, 16);
-    y.prm = y.part + 2 * CS * SPC * 8;
-    const uint32_t prm_floats = (uint32_t)(L * C + 4 * HN + 2);
-    y.slot = al_up(y.prm + prm_floats * 4, 16);
+    y.prm = y.part + 2 * CS * SPC * 4 * part_floats(no);
+    y.slot = al_up(y.prm + (uint32_t)prm_floats(L, C, HN, no) * 4, 16);
     y.misc = y.slot + SPC * 8 + 8 * SPC * 4;
     y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8, 8);   // + 32 phase counters (profiling)
     y.total = y.bars + (2 * stages + 12) * 8;
@@ -286,14 +294,15 @@ __device__ __forceinline__ int positions_of(int E, int L, int rows_n) {
     return max(1, min((E + span - 1) / span, rows_n));
 }
 
-template <int CS>
+template <int CS, int NO>
 __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_constant__ CArgs a) {
     constexpr int SPC = 128 / CS;   // batch slots per CTA
     constexpr uint16_t kAll = (uint16_t)((1u << CS) - 1u);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int L = a.L, C = a.C, HN = a.H / CS, S = a.stages, cap = a.cap, PM = pass_positions(L);
-    const CLay y = c_layout(CS, L, C, a.H, cap, S);
+    constexpr int PF = NO == 2 ? 2 : 24;   // part_floats(NO)
+    const CLay y = c_layout(CS, L, C, a.H, cap, S, NO);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cl_rank();
     const int slot0 = (int)(blockIdx.x / CS) * 128 + (int)rank * SPC;
@@ -320,16 +329,17 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
               B_EXT = 2 * S + 5, B_FIN = 2 * S + 7;
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
     float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
-    float *s_w2f = s_fb + HN, *s_w2e = s_w2f + HN;          // FC2 rows for those neurons
-    float *s_Se = s_w2e + HN;                                // [HN] S[e] of the current step
-    float *s_b2 = s_Se + HN;
+    float *s_Se = s_fb + HN;                                 // [HN] S[e] of the current step
+    float *s_b2 = s_Se + HN;                                 // [24] FC2 bias
+    float *s_w2 = s_b2 + 24;                                 // FC2 rows for this CTA's neurons
+    float *s_w2f = s_w2, *s_w2e = s_w2 + HN;                 // regression: [2][HN]; hybrid: [HN][24]
     int64_t *s_o = reinterpret_cast<int64_t *>(sm + y.slot);
     int32_t *s_b = reinterpret_cast<int32_t *>(s_o + SPC), *s_n = s_b + SPC, *s_p = s_n + SPC,
             *s_tick = s_p + SPC, *s_qs = s_tick + SPC, *s_ql = s_qs + SPC, *s_ev = s_ql + SPC,
             *s_al = s_ev + SPC;
     uint64_t *qring = reinterpret_cast<uint64_t *>(sm + y.qring);
     uint32_t *recb = reinterpret_cast<uint32_t *>(sm + y.rec);   // [slot][position & 3]
-    float2 *part = reinterpret_cast<float2 *>(sm + y.part);     // [source CTA * 2 + half][slot]
+    float *part = reinterpret_cast<float *>(sm + y.part);       // [source CTA * 2 + half][slot][PF]
     int2 *ext_in = reinterpret_cast<int2 *>(sm + y.misc);       // [step parity][source CTA]
     volatile int *ctl = reinterpret_cast<volatile int *>(sm + y.misc + 16 * CS);   // positions, stop
     volatile int *abort_f = ctl + 4;
@@ -367,10 +377,17 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     for (int j = threadIdx.x; j < HN; j += blockDim.x) {
         const int nn = (int)rank * HN + j;
         s_fb[j] = a.fbias[nn];
-        s_w2f[j] = a.w2[nn];
-        s_w2e[j] = a.w2[a.H + nn];
+        if constexpr (NO == 2) {
+            s_w2f[j] = a.w2[nn];
+            s_w2e[j] = a.w2[a.H + nn];
+        }
     }
-    if (threadIdx.x < 2) s_b2[threadIdx.x] = a.b2[threadIdx.x];
+    if constexpr (NO != 2)
+        for (int i = threadIdx.x; i < HN * 24; i += blockDim.x) {
+            const int j = i / 24, o = i % 24;
+            s_w2[i] = o < NO ? a.w2[(size_t)o * a.H + (int)rank * HN + j] : 0.f;
+        }
+    if (threadIdx.x < 24) s_b2[threadIdx.x] = threadIdx.x < NO ? a.b2[threadIdx.x] : 0.f;
     // slot state (workers: warp w takes slots w-2, w+6, ...)
     if (warp >= 2) {
         const int n_act = min(*A->n_active, A->n_sub);
@@ -707,26 +724,64 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 tc_fence_after();
                 mark(8);
                 float pf = 0.f, pe = 0.f;
+                constexpr int NH = NO == 2 ? 1 : 24;
+                float ph[NH];
+#pragma unroll
+                for (int o = 0; o < NH; o++) ph[o] = 0.f;
                 if (ok) {
                     const int cols = HN / 2, j0 = half * cols;
-                    uint32_t r32[2][32];
-                    tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)j0, cols, r32);
+                    if constexpr (NO == 2) {
+                        uint32_t r32[2][32];
+                        tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)j0, cols, r32);
 #pragma unroll
-                    for (int bi = 0; bi < 2; bi++) {
-                        if (bi >= cols / 32) break;
+                        for (int bi = 0; bi < 2; bi++) {
+                            if (bi >= cols / 32) break;
 #pragma unroll
-                        for (int jj = 0; jj < 32; jj++) {
-                            const int j = j0 + bi * 32 + jj;
-                            const float v = fmaxf(__uint_as_float(r32[bi][jj]) + s_fb[j] + s_Se[j], 0.f);
-                            pf = fmaf(v, s_w2f[j], pf);
-                            pe = fmaf(v, s_w2e[j], pe);
+                            for (int jj = 0; jj < 32; jj++) {
+                                const int j = j0 + bi * 32 + jj;
+                                const float v = fmaxf(__uint_as_float(r32[bi][jj]) + s_fb[j] + s_Se[j], 0.f);
+                                pf = fmaf(v, s_w2f[j], pf);
+                                pe = fmaf(v, s_w2e[j], pe);
+                            }
+                        }
+                    } else {
+                        // 22 outputs per neuron: 32 TMEM columns at a time keeps the
+                        // accumulators and one chunk in registers
+#pragma unroll 1
+                        for (int bi = 0; bi < cols / 32; bi++) {
+                            uint32_t r32[32];
+                            tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)(j0 + bi * 32), r32);
+#pragma unroll
+                            for (int jj = 0; jj < 32; jj++) {
+                                const int j = j0 + bi * 32 + jj;
+                                const float v = fmaxf(__uint_as_float(r32[jj]) + s_fb[j] + s_Se[j], 0.f);
+                                const float4 *wv = reinterpret_cast<const float4 *>(s_w2 + j * 24);
+#pragma unroll
+                                for (int q4 = 0; q4 < 6; q4++) {
+                                    const float4 w = wv[q4];
+                                    ph[4 * q4] = fmaf(v, w.x, ph[4 * q4]);
+                                    ph[4 * q4 + 1] = fmaf(v, w.y, ph[4 * q4 + 1]);
+                                    if (4 * q4 + 2 < NO) ph[4 * q4 + 2] = fmaf(v, w.z, ph[4 * q4 + 2]);
+                                    if (4 * q4 + 3 < NO) ph[4 * q4 + 3] = fmaf(v, w.w, ph[4 * q4 + 3]);
+                                }
+                            }
                         }
                     }
                 }
                 tc_fence_before();
                 // cluster slot g = qd * 32 + lane belongs to CTA g / SPC, where it is slot g % SPC
                 const int g = qd * 32 + lane, owner = g / SPC;
-                cl_st_v2f(cl_map(smem_u32(&part[((int)rank * 2 + half) * SPC + g % SPC]), (uint32_t)owner), pf, pe);
+                const uint32_t dst =
+                    cl_map(smem_u32(&part[(((int)rank * 2 + half) * SPC + g % SPC) * PF]), (uint32_t)owner);
+                if constexpr (NO == 2) {
+                    cl_st_v2f(dst, pf, pe);
+                } else {
+#pragma unroll
+                    for (int q4 = 0; q4 < 6; q4++)
+                        cl_st_v4(dst + 16u * q4, make_uint4(__float_as_uint(ph[4 * q4]), __float_as_uint(ph[4 * q4 + 1]),
+                                                            __float_as_uint(ph[4 * q4 + 2]),
+                                                            __float_as_uint(ph[4 * q4 + 3])));
+                }
                 __syncwarp();
                 if (g % SPC == 0) cl_arrive(cl_map(bar(B_PART), (uint32_t)owner));
                 mark(9);
@@ -741,22 +796,39 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     const int64_t o = s_o[s];
                     const int n = s_n[s];
                     int p = s_p[s];
-                    float zf = s_b2[0], ze = s_b2[1];
+                    float z[NO];
+                    if constexpr (NO == 2) {
+                        float zf = s_b2[0], ze = s_b2[1];
 #pragma unroll
-                    for (int i = 0; i < 2 * CS; i++) {
-                        const float2 v = part[i * SPC + s];
-                        zf += v.x;
-                        ze += v.y;
+                        for (int i = 0; i < 2 * CS; i++) {
+                            const float2 v = reinterpret_cast<const float2 *>(part)[i * SPC + s];
+                            zf += v.x;
+                            ze += v.y;
+                        }
+                        z[0] = zf;
+                        z[1] = ze;
+                    } else {
+#pragma unroll
+                        for (int o2 = 0; o2 < NO; o2++) z[o2] = s_b2[o2];
+#pragma unroll
+                        for (int i = 0; i < 2 * CS; i++) {
+                            const float *pv = part + (i * SPC + s) * PF;
+#pragma unroll
+                            for (int q4 = 0; q4 < 6; q4++) {
+                                const float4 v = *reinterpret_cast<const float4 *>(pv + 4 * q4);
+                                z[4 * q4] += v.x;
+                                z[4 * q4 + 1] += v.y;
+                                if (4 * q4 + 2 < NO) z[min(4 * q4 + 2, NO - 1)] += v.z;
+                                if (4 * q4 + 3 < NO) z[min(4 * q4 + 3, NO - 1)] += v.w;
+                            }
+                        }
                     }
-                    const float yf = softplus_f(zf), ye = softplus_f(ze);
+                    float yf, ye;
+                    uint32_t F = head_latency<NO>(z, 0, yf), E = head_latency<NO>(z, 1, ye);
                     const int64_t gi = o + p;
-                    uint32_t F, E;
                     if (As.replay) {
                         F = As.replay[2 * gi];
                         E = As.replay[2 * gi + 1];
-                    } else {
-                        F = to_cycles(yf);
-                        E = to_cycles(ye);
                     }
                     if (As.pre_log) { As.pre_log[2 * gi] = yf; As.pre_log[2 * gi + 1] = ye; }
                     if (As.lat_log) { As.lat_log[2 * gi] = (uint8_t)F; As.lat_log[2 * gi + 1] = (uint8_t)E; }
@@ -871,7 +943,7 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
     if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }
     if (c->cap > 255 || c->rows_n < 1) { why = "window"; return false; }
-    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2);   // the larger layout
+    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2, c->n_out);   // the larger layout
     if (y.total + 1024 > 232448) { why = "shared memory"; return false; }
     return true;
 }
@@ -908,10 +980,12 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.n_steps = n_steps;
     a.spin_ns = c->cfg.spin_limit_ns;
     int stages = 8;
-    while (stages > 2 && c_layout(CS, a.L, a.C, a.H, a.cap, stages).total + 1024 > 232448) stages--;
+    const int no = c->n_out;
+    while (stages > 2 && c_layout(CS, a.L, a.C, a.H, a.cap, stages, no).total + 1024 > 232448) stages--;
     a.stages = stages;
-    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages).total + 1024;
-    auto kern = CS == 8 ? cluster_kernel<8> : cluster_kernel<4>;
+    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no).total + 1024;
+    auto kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid> : cluster_kernel<4, kOutHybrid>)
+                                 : (CS == 8 ? cluster_kernel<8, 2> : cluster_kernel<4, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
     const int n_clusters = (B + 127) / 128;

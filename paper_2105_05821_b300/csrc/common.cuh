@@ -12,6 +12,7 @@ namespace simnet {
 constexpr int kNF = SIMNET_N_FEATURES;  // real features per row (Sec. 2.2)
 constexpr int kNFP = 64;                // features per row in device layout (zero padded)
 constexpr int kMaxConv = 8;
+constexpr int kOutHybrid = 22;          // FC2 outputs of the hybrid head: per latency 10 class logits + 1 value
 
 // Device status word values (written by kernels, read by the host after a call).
 enum : int32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadTrace = 2 };

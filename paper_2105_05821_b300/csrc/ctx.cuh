@@ -25,7 +25,7 @@ struct TrainState {
     float *X = nullptr;                // packed input [n][W][64]
     float *Y[kMaxConv + 1] = {};       // outputs of every layer (post-ReLU); Y[L] = FC1 [n][H]
     float *dA = nullptr, *dB = nullptr;  // gradient ping-pong buffers (largest activation)
-    float *z = nullptr, *dz = nullptr; // [n][2]
+    float *z = nullptr, *dz = nullptr; // [n][n_out]
     double *loss = nullptr;            // device scalar
     int n_last = 0;                    // windows of the last forward
 };
@@ -33,6 +33,7 @@ struct TrainState {
 struct simnet_ctx {
     simnet_config cfg{};
     int cap = 0, rows_n = 0, fc1_in = 0, n_layers = 0;
+    int n_out = 2;   // FC2 outputs: 2 (regression head) or 22 (hybrid head)
     int64_t n_weights = 0;
     std::string err;
     bool has_weights = false;
@@ -51,7 +52,7 @@ struct simnet_ctx {
     // workspace, sized for ws_B sub-traces
     int ws_B = 0;
     void *X = nullptr, *act[2] = {nullptr, nullptr};
-    float *h1 = nullptr;  // FC2 partial sums [n_part][B] float2 (sized as the FC1 output)
+    float *h1 = nullptr;  // FC2 partial sums [n_part][B][n_out] float
     int n_part = 0;
     bool pdl = true;
     int32_t *tick = nullptr, *pos = nullptr, *qstart = nullptr, *qlen = nullptr, *evict = nullptr;

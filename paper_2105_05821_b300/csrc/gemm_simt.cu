@@ -9,9 +9,9 @@ namespace simnet {
 
 // 128 x BN tile, BK = 8, 256 threads; each thread owns an 8 x (BN/16) block of C.
 // Shared tiles are stored K-major so the inner loop reads float4 runs of M and N.
-// PART: instead of storing C, fold FC2 (w2 [2][N]) into the epilogue and write
-// per-column-block partial dot products C_part[blockIdx.y][row] = (fetch, execution).
-template <int BN, bool PART>
+// NO > 0: instead of storing C, fold FC2 (w2 [NO][N]) into the epilogue and write
+// per-column-block partial dot products C_part[blockIdx.y][row][0..NO).
+template <int BN, int NO>
 __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A, const float *__restrict__ B,
                                                     const float *__restrict__ bias, float *__restrict__ C,
                                                     const int32_t *__restrict__ n_active, int m_mult,
@@ -77,27 +77,32 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
             __syncthreads();
         }
     }
-    if constexpr (PART) {
+    if constexpr (NO > 0) {
 #pragma unroll
         for (int i = 0; i < TM; i++) {
-            float pf = 0.f, pe = 0.f;
+            float p[NO];
+#pragma unroll
+            for (int o = 0; o < NO; o++) p[o] = 0.f;
 #pragma unroll
             for (int j = 0; j < TN; j++) {
                 const int col = n0 + tx * TN + j;
                 float v = acc[i][j] + bias[col];
                 if (relu) v = fmaxf(v, 0.f);
-                pf = fmaf(v, w2[col], pf);
-                pe = fmaf(v, w2[N + col], pe);
+#pragma unroll
+                for (int o = 0; o < NO; o++) p[o] = fmaf(v, w2[(size_t)o * N + col], p[o]);
             }
             // the 16 threads of a row group sit in one half-warp
 #pragma unroll
-            for (int o = 1; o < 16; o <<= 1) {
-                pf += __shfl_xor_sync(0xffffffffu, pf, o);
-                pe += __shfl_xor_sync(0xffffffffu, pe, o);
-            }
+            for (int o = 0; o < NO; o++)
+#pragma unroll
+                for (int d = 1; d < 16; d <<= 1) p[o] += __shfl_xor_sync(0xffffffffu, p[o], d);
             const int row = m0 + ty * TM + i;
-            if (tx == 0 && row < M)
-                reinterpret_cast<float2 *>(C)[(size_t)blockIdx.y * part_stride + row] = make_float2(pf, pe);
+            if (row < M) {
+                float *dst = C + ((size_t)blockIdx.y * part_stride + row) * NO;
+#pragma unroll
+                for (int o = 0; o < NO; o++)
+                    if (tx == (o & 15)) dst[o] = p[o];
+            }
         }
         return;
     }
@@ -125,26 +130,36 @@ void launch_gemm_f32(const float *A, const float *B, const float *bias, float *C
     const unsigned gm = (unsigned)((m_cap + 127) / 128);
     if (gm == 0) return;
     if (N % 128 == 0)
-        launch_k(pdl, sgemm_kernel<128, false>, dim3(gm, N / 128), dim3(256), 0, s, A, B, bias, C, n_active, m_mult,
+        launch_k(pdl, sgemm_kernel<128, 0>, dim3(gm, N / 128), dim3(256), 0, s, A, B, bias, C, n_active, m_mult,
                  m_cap, N, K, relu, (const float *)nullptr, 0);
     else
-        launch_k(pdl, sgemm_kernel<64, false>, dim3(gm, (N + 63) / 64), dim3(256), 0, s, A, B, bias, C, n_active,
+        launch_k(pdl, sgemm_kernel<64, 0>, dim3(gm, (N + 63) / 64), dim3(256), 0, s, A, B, bias, C, n_active,
                  m_mult, m_cap, N, K, relu, (const float *)nullptr, 0);
 }
 
 int gemm_f32_part_blocks(int N) { return N % 128 == 0 ? N / 128 : (N + 63) / 64; }
 
-void launch_gemm_f32_part(const float *A, const float *B, const float *bias, const float *w2, float2 *part,
-                          int part_stride, const int32_t *n_active, int m_mult, int m_cap, int N, int K, int relu,
-                          cudaStream_t s, bool pdl) {
+template <int NO>
+static void launch_part_no(const float *A, const float *B, const float *bias, const float *w2, float *part,
+                           int part_stride, const int32_t *n_active, int m_mult, int m_cap, int N, int K, int relu,
+                           cudaStream_t s, bool pdl) {
     const unsigned gm = (unsigned)((m_cap + 127) / 128);
     if (gm == 0) return;
     if (N % 128 == 0)
-        launch_k(pdl, sgemm_kernel<128, true>, dim3(gm, N / 128), dim3(256), 0, s, A, B, bias, (float *)part,
-                 n_active, m_mult, m_cap, N, K, relu, w2, part_stride);
+        launch_k(pdl, sgemm_kernel<128, NO>, dim3(gm, N / 128), dim3(256), 0, s, A, B, bias, part, n_active, m_mult,
+                 m_cap, N, K, relu, w2, part_stride);
     else
-        launch_k(pdl, sgemm_kernel<64, true>, dim3(gm, (N + 63) / 64), dim3(256), 0, s, A, B, bias, (float *)part,
-                 n_active, m_mult, m_cap, N, K, relu, w2, part_stride);
+        launch_k(pdl, sgemm_kernel<64, NO>, dim3(gm, (N + 63) / 64), dim3(256), 0, s, A, B, bias, part, n_active,
+                 m_mult, m_cap, N, K, relu, w2, part_stride);
+}
+
+void launch_gemm_f32_part(const float *A, const float *B, const float *bias, const float *w2, float *part,
+                          int part_stride, const int32_t *n_active, int m_mult, int m_cap, int N, int K, int relu,
+                          int n_out, cudaStream_t s, bool pdl) {
+    if (n_out == kOutHybrid)
+        launch_part_no<kOutHybrid>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl);
+    else
+        launch_part_no<2>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl);
 }
 
 }  // namespace simnet

@@ -106,7 +106,7 @@ extern "C" simnet_status simnet_cnn_forward_noalloc(simnet_ctx *c, const float *
         launch_gemm_f32(in, (const float *)g.B, g.bias, out, count, g.m_mult, n * g.m_mult, g.N, g.K, g.relu, s);
         in = out;
     }
-    launch_head_z(h1, v.w2, v.b2, z, n, v.hidden, s);
+    launch_head_z(h1, v.w2, v.b2, z, n, v.hidden, v.n_out, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         char buf[160];

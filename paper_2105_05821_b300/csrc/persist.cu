@@ -40,7 +40,7 @@ namespace simnet {
 struct PLayer {
     CUtensorMap tA, tB;  // A: pair-major input [pairs * B][2 * C_in]; B: weights [N][K]
     const float *bias, *scale, *oscale;
-    void *out;           // pair-major activations [pairs * B][2N], or FC2 partials [2*N/BN][B] float2
+    void *out;           // pair-major activations [pairs * B][2N], or FC2 partials [2*N/BN][B][n_out] float
     int K, N, BN, out_part, n_tiles_n;
     int cin;             // input row width in elements (FC1: channels of one input row)
     int pos_shift;       // conv: output positions computed = e << pos_shift
@@ -50,7 +50,7 @@ struct PArgs {
     PLayer layer[kMaxConv + 1];
     const StepArgs *A;
     void *X;
-    const float2 *part;
+    const float *part;
     const float *w2, *b2;
     const float *fc1_const;       // [rows_n + 1][H]
     int *ext;                     // [2] batch extent per step parity
@@ -121,7 +121,7 @@ struct Pipe {  // pipeline counters that carry over between GEMM phases
     int prod_it = 0, mma_it = 0, mma_tc = 0, epi_tc = 0;
 };
 
-template <bool FP8>
+template <bool FP8, int NO>
 __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint64_t *bars, float *prm,
                                uint8_t *staging, uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
     const PLayer &L = a.layer[l];
@@ -136,7 +136,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
             s_scale[i] = L.scale[i];
             s_oscale[i] = L.oscale ? L.oscale[i] : 1.f;
         }
-        if (L.out_part) {
+        if (NO == 2 && L.out_part) {   // the hybrid head's 22 FC2 rows are read through L1
             s_w2[i] = a.w2[i];
             s_w2[N + i] = a.w2[N + i];
         }
@@ -236,6 +236,10 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
             const int row = m0 + q * 32 + lane;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256 + half * (BN / 2));
             float pf = 0.f, pe = 0.f;
+            constexpr int NH = NO == 2 ? 1 : NO;
+            float ph[NH];
+#pragma unroll
+            for (int o = 0; o < NH; o++) ph[o] = 0.f;
             for (int c = 0; c < CPW; c++) {
                 uint32_t r[32];
                 tmem_ld32(tbase + (uint32_t)(c * 32), r);
@@ -251,10 +255,23 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
                     v[j] = x;
                 }
                 if (L.out_part) {
+                    if constexpr (NO == 2) {
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        pf = fmaf(v[j], s_w2[col0 + j], pf);
-                        pe = fmaf(v[j], s_w2[N + col0 + j], pe);
+                        for (int j = 0; j < 32; j++) {
+                            pf = fmaf(v[j], s_w2[col0 + j], pf);
+                            pe = fmaf(v[j], s_w2[N + col0 + j], pe);
+                        }
+                    } else {
+#pragma unroll
+                        for (int o = 0; o < NH; o++) {
+                            const float4 *wr = reinterpret_cast<const float4 *>(a.w2 + (size_t)o * N + col0);
+#pragma unroll
+                            for (int j4 = 0; j4 < 8; j4++) {
+                                const float4 w = __ldg(wr + j4);
+                                ph[o] = fmaf(v[4 * j4], w.x, ph[o]); ph[o] = fmaf(v[4 * j4 + 1], w.y, ph[o]);
+                                ph[o] = fmaf(v[4 * j4 + 2], w.z, ph[o]); ph[o] = fmaf(v[4 * j4 + 3], w.w, ph[o]);
+                            }
+                        }
                     }
                 } else {
                     uint4 *dst = reinterpret_cast<uint4 *>(stg + lane * SROW);
@@ -299,8 +316,15 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
                     __syncwarp();
                 }
             }
-            if (L.out_part && row < M)
-                reinterpret_cast<float2 *>(L.out)[(size_t)(2 * nt + half) * a.B + row] = make_float2(pf, pe);
+            if (L.out_part && row < M) {
+                if constexpr (NO == 2) {
+                    reinterpret_cast<float2 *>(L.out)[(size_t)(2 * nt + half) * a.B + row] = make_float2(pf, pe);
+                } else {
+                    float *dst = reinterpret_cast<float *>(L.out) + ((size_t)(2 * nt + half) * a.B + row) * NO;
+#pragma unroll
+                    for (int o = 0; o < NO; o++) dst[o] = ph[o];
+                }
+            }
             tc_fence_before();
             mbar_arrive(tempty(acc));
         }
@@ -309,7 +333,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
     return t_phase;
 }
 
-template <bool FP8>
+template <bool FP8, int NO>
 __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_constant__ PArgs a) {
     using T = typename std::conditional<FP8, __nv_fp8_e4m3, __nv_bfloat16>::type;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -366,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         e = max(1, min(e, a.rows_n));
         if (blockIdx.x == 0 && threadIdx.x == 0) *ext_next = 0;   // the head phase raises it
         for (int l = 0; l < a.n_layers && ok; l++) {
-            const uint64_t tp = gemm_phase<FP8>(a, l, e, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+            const uint64_t tp = gemm_phase<FP8, NO>(a, l, e, smem, bars, prm, staging, tmem_base, cta_abort, pp);
             ok = grid_sync(a, target, cta_abort);
             if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
             mark(SIMNET_KERNEL_LAYER0 + l);
@@ -377,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             uint8_t *mine = smem + warp * PER;
             const int n_act = *a.A->n_active;
             for (int slot = blockIdx.x * kWarps + warp; slot < n_act; slot += gridDim.x * kWarps)
-                head_update_warp<T>(a.A, slot, lane, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
+                head_update_warp<T, NO>(a.A, slot, lane, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
                                     reinterpret_cast<uint64_t *>(mine), mine + 256 * 8, a.B, ext_next);
         }
         ok = grid_sync(a, target, cta_abort);
@@ -443,7 +467,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.e_round = std::max(1, BK / C);
     a.A = c->d_args;
     a.X = c->X;
-    a.part = (const float2 *)c->h1;
+    a.part = c->h1;
     a.w2 = c->w2;
     a.b2 = c->b2;
     a.bar_counter = c->bar;
@@ -472,7 +496,9 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         return false;
     }
     const size_t smem = (size_t)a.stages * a.stage_bytes + fixed;
-    auto k = fp8 ? persist_kernel<true> : persist_kernel<false>;
+    const bool hyb = c->n_out == kOutHybrid;
+    auto k = fp8 ? (hyb ? persist_kernel<true, kOutHybrid> : persist_kernel<true, 2>)
+                 : (hyb ? persist_kernel<false, kOutHybrid> : persist_kernel<false, 2>);
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);

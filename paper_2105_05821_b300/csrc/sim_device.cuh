@@ -159,6 +159,57 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// Latency t (0 fetch, 1 execution) from the FC2 outputs z[0..NO) (bias
+// included); `pre` receives the softplus value before clamping and rounding.
+// NO = 2, regression head: round(clamp(softplus(z[t]))).  NO = 22, hybrid head
+// (Sec. 2.3): the class k with the largest of the ten logits z[11t..11t+9],
+// compared in FP32 with the lowest index winning ties; classes 0..8 are the
+// latency itself, class 9 ("more than 8") takes the regression output z[11t+10].
+template <int NO>
+__device__ __forceinline__ uint32_t head_latency(const float (&z)[NO], int t, float &pre) {
+    if constexpr (NO == 2) {
+        pre = softplus_f(t ? z[1] : z[0]);
+        return to_cycles(pre);
+    } else {
+        float lg[11];
+#pragma unroll
+        for (int j = 0; j < 11; j++) lg[j] = t ? z[11 + j] : z[j];
+        float best = lg[0];
+        int k = 0;
+#pragma unroll
+        for (int j = 1; j < 10; j++)
+            if (lg[j] > best) { best = lg[j]; k = j; }
+        pre = softplus_f(lg[10]);
+        return k <= 8 ? (uint32_t)k : to_cycles(pre);
+    }
+}
+
+// FC2 outputs of one slot, in every lane of the warp: z[o] = b2[o] + the sum
+// over the P partials part[(i * part_stride + slot) * NO + o].
+template <int NO>
+__device__ __forceinline__ void head_sum_warp(const float *__restrict__ part, int P, int part_stride, int slot,
+                                              const float *__restrict__ b2, int lane, float (&z)[NO]) {
+    if constexpr (NO == 2) {
+        float zf = 0.f, ze = 0.f;
+        for (int i = lane; i < P; i += 32) {
+            const float2 v = reinterpret_cast<const float2 *>(part)[(size_t)i * part_stride + slot];
+            zf += v.x;
+            ze += v.y;
+        }
+        z[0] = warp_sum(zf) + b2[0];
+        z[1] = warp_sum(ze) + b2[1];
+    } else {
+        // lane o < NO adds output o over the partials, then every lane gets all NO
+        float acc = 0.f;
+        if (lane < NO) {
+            acc = b2[lane];
+            for (int i = 0; i < P; i++) acc += part[((size_t)i * part_stride + slot) * NO + lane];
+        }
+#pragma unroll
+        for (int o = 0; o < NO; o++) z[o] = __shfl_sync(0xffffffffu, acc, o);
+    }
+}
+
 // Length of the run of ready entries from the oldest, at most `lim`; in-order
 // retire means the first not-ready entry stops it.  Whole warp participates.
 __device__ __forceinline__ int retire_run(const uint64_t *__restrict__ ring, int cap, int qs, int lim,
@@ -330,8 +381,9 @@ __device__ __forceinline__ void gather_rows_warp_pm(const StepArgs *__restrict__
     __syncwarp();
 }
 
-// One warp, one active slot.  FC2 arrives as P partial dot products (one per
-// FC1 column block) which are summed with the bias; softplus, clamp, round;
+// One warp, one active slot.  FC2 arrives as P partial dot products per output
+// (one per FC1 column block) which are summed with the bias; the latencies
+// follow by head_latency (softplus, clamp, round; or the hybrid class rule);
 // then curTick += F, retire (budget RW*F), evict at capacity, append with
 // residence 0; after the last instruction, drain one cycle at a time (budget
 // RW) and write the sub-trace's cycle count.  Otherwise the warp writes the
@@ -341,9 +393,9 @@ __device__ __forceinline__ void gather_rows_warp_pm(const StepArgs *__restrict__
 // only rows 0 .. max(old, new queue length) are written (rows past a queue are
 // kept zero) and the next step's batch extent `ext` is raised to the new queue
 // length + 1.
-template <typename T>
+template <typename T, int NO = 2>
 __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A, int slot, int lane,
-                                                 const float2 *__restrict__ part, int P, int part_stride,
+                                                 const float *__restrict__ part, int P, int part_stride,
                                                  const float *__restrict__ b2, T *__restrict__ X,
                                                  uint64_t *__restrict__ sq, uint8_t *__restrict__ stg,
                                                  int pm_slots = 0, int *ext = nullptr) {
@@ -351,23 +403,14 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
     const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
     int p = A->pos[b];
     if (p >= n) return;
-    float zf = 0.f, ze = 0.f;
-    for (int i = lane; i < P; i += 32) {
-        const float2 v = part[(size_t)i * part_stride + slot];
-        zf += v.x;
-        ze += v.y;
-    }
-    zf = warp_sum(zf) + b2[0];
-    ze = warp_sum(ze) + b2[1];
-    const float yf = softplus_f(zf), ye = softplus_f(ze);
+    float z[NO];
+    head_sum_warp<NO>(part, P, part_stride, slot, b2, lane, z);
+    float yf, ye;
+    uint32_t F = head_latency<NO>(z, 0, yf), E = head_latency<NO>(z, 1, ye);
     const int64_t gi = o + p;
-    uint32_t F, E;
     if (A->replay) {
         F = A->replay[2 * gi];
         E = A->replay[2 * gi + 1];
-    } else {
-        F = to_cycles(yf);
-        E = to_cycles(ye);
     }
     if (lane == 0) {
         if (A->pre_log) { A->pre_log[2 * gi] = yf; A->pre_log[2 * gi + 1] = ye; }

@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(256) pack_x_kernel(const float *__restrict__ x
 
 // One warp per active slot (see head_update_warp); dynamic shared memory holds,
 // per warp, 256 queue entries and 32 staged rows.
-template <typename T>
+template <typename T, int NO>
 __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__restrict__ A,
-                                                          const float2 *__restrict__ part, int P,
+                                                          const float *__restrict__ part, int P,
                                                           int part_stride, const float *__restrict__ b2,
                                                           T *__restrict__ X) {
     extern __shared__ __align__(16) uint8_t hsm[];
@@ -55,49 +55,40 @@ __global__ void __launch_bounds__(256) head_update_kernel(const StepArgs *__rest
     if (slot >= *A->n_active) return;
     constexpr int PER = 256 * 8 + 32 * stage_row_bytes<T>();
     uint8_t *mine = hsm + w * PER;
-    head_update_warp<T>(A, slot, lane, part, P, part_stride, b2, X, reinterpret_cast<uint64_t *>(mine), mine + 256 * 8);
+    head_update_warp<T, NO>(A, slot, lane, part, P, part_stride, b2, X, reinterpret_cast<uint64_t *>(mine),
+                            mine + 256 * 8);
 }
 
 // FC2 from partial dot products: z = b2 + sum of P partials (pre-softplus), one warp per row.
-__global__ void __launch_bounds__(256) head_part_z_kernel(const float2 *__restrict__ part, int P, int part_stride,
+template <int NO>
+__global__ void __launch_bounds__(256) head_part_z_kernel(const float *__restrict__ part, int P, int part_stride,
                                                           const float *__restrict__ b2, float *__restrict__ z,
                                                           int n) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
-    float zf = 0.f, ze = 0.f;
-    for (int i = lane; i < P; i += 32) {
-        const float2 v = part[(size_t)i * part_stride + row];
-        zf += v.x;
-        ze += v.y;
-    }
-    zf = warp_sum(zf);
-    ze = warp_sum(ze);
-    if (lane == 0) {
-        z[2 * row] = zf + b2[0];
-        z[2 * row + 1] = ze + b2[1];
-    }
+    float zr[NO];
+    head_sum_warp<NO>(part, P, part_stride, row, b2, lane, zr);
+#pragma unroll
+    for (int o = 0; o < NO; o++)
+        if (lane == (o & 31)) z[(size_t)row * NO + o] = zr[o];
 }
 
-// FC2 only (pre-softplus outputs) for the CNN-only entry point.
+// FC2 only (pre-softplus outputs, w2 [n_out][H]) for the CNN-only entry points:
+// one warp per row, lanes over H, one output at a time.
 __global__ void __launch_bounds__(256) head_z_kernel(const float *__restrict__ h, const float *__restrict__ w2,
                                                      const float *__restrict__ b2, float *__restrict__ z,
-                                                     int n, int H) {
+                                                     int n, int H, int n_out) {
     const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
     const float *hv = h + (size_t)row * H;
-    float zf = 0.f, ze = 0.f;
-    for (int j = lane; j < H; j += 32) {
-        zf = fmaf(hv[j], w2[j], zf);
-        ze = fmaf(hv[j], w2[H + j], ze);
-    }
-    zf = warp_sum(zf);
-    ze = warp_sum(ze);
-    if (lane == 0) {
-        z[2 * row] = zf + b2[0];
-        z[2 * row + 1] = ze + b2[1];
+    for (int o = 0; o < n_out; o++) {
+        float acc = 0.f;
+        for (int j = lane; j < H; j += 32) acc = fmaf(hv[j], w2[(size_t)o * H + j], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) z[(size_t)row * n_out + o] = acc + b2[o];
     }
 }
 
@@ -173,35 +164,50 @@ template void launch_pack_x<float>(const float *, float *, int64_t, cudaStream_t
 template void launch_pack_x<__nv_bfloat16>(const float *, __nv_bfloat16 *, int64_t, cudaStream_t);
 template void launch_pack_x<__nv_fp8_e4m3>(const float *, __nv_fp8_e4m3 *, int64_t, cudaStream_t);
 
-template <typename T>
-void launch_head_update(const StepArgs *A, const float2 *part, int P, int part_stride, const float *b2, T *X,
-                        int n_slots, cudaStream_t s, bool pdl) {
+template <typename T, int NO>
+static void launch_head_update_no(const StepArgs *A, const float *part, int P, int part_stride, const float *b2,
+                                  T *X, int n_slots, cudaStream_t s, bool pdl) {
     const int64_t threads = (int64_t)n_slots * 32;
     const size_t smem = 8 * (256 * 8 + 32 * stage_row_bytes<T>());
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(head_update_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(head_update_kernel<T, NO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    launch_k(pdl, head_update_kernel<T>, dim3((unsigned)((threads + 255) / 256)), dim3(256), smem, s, A, part, P,
-             part_stride, b2, X);
+    launch_k(pdl, head_update_kernel<T, NO>, dim3((unsigned)((threads + 255) / 256)), dim3(256), smem, s, A, part,
+             P, part_stride, b2, X);
 }
-template void launch_head_update<float>(const StepArgs *, const float2 *, int, int, const float *, float *, int,
+
+template <typename T>
+void launch_head_update(const StepArgs *A, const float *part, int P, int part_stride, const float *b2, T *X,
+                        int n_slots, int n_out, cudaStream_t s, bool pdl) {
+    if (n_out == kOutHybrid)
+        launch_head_update_no<T, kOutHybrid>(A, part, P, part_stride, b2, X, n_slots, s, pdl);
+    else
+        launch_head_update_no<T, 2>(A, part, P, part_stride, b2, X, n_slots, s, pdl);
+}
+template void launch_head_update<float>(const StepArgs *, const float *, int, int, const float *, float *, int, int,
                                         cudaStream_t, bool);
-template void launch_head_update<__nv_bfloat16>(const StepArgs *, const float2 *, int, int, const float *,
-                                                __nv_bfloat16 *, int, cudaStream_t, bool);
-template void launch_head_update<__nv_fp8_e4m3>(const StepArgs *, const float2 *, int, int, const float *,
-                                                __nv_fp8_e4m3 *, int, cudaStream_t, bool);
+template void launch_head_update<__nv_bfloat16>(const StepArgs *, const float *, int, int, const float *,
+                                                __nv_bfloat16 *, int, int, cudaStream_t, bool);
+template void launch_head_update<__nv_fp8_e4m3>(const StepArgs *, const float *, int, int, const float *,
+                                                __nv_fp8_e4m3 *, int, int, cudaStream_t, bool);
 
-void launch_head_z(const float *h, const float *w2, const float *b2, float *z, int n, int H, cudaStream_t s) {
+void launch_head_z(const float *h, const float *w2, const float *b2, float *z, int n, int H, int n_out,
+                   cudaStream_t s) {
     const int64_t threads = (int64_t)n * 32;
-    if (n > 0) head_z_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(h, w2, b2, z, n, H);
+    if (n > 0) head_z_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(h, w2, b2, z, n, H, n_out);
 }
 
-void launch_head_part_z(const float2 *part, int P, int part_stride, const float *b2, float *z, int n,
+void launch_head_part_z(const float *part, int P, int part_stride, const float *b2, float *z, int n, int n_out,
                         cudaStream_t s) {
     const int64_t threads = (int64_t)n * 32;
-    if (n > 0) head_part_z_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(part, P, part_stride, b2, z, n);
+    if (n <= 0) return;
+    const unsigned g = (unsigned)((threads + 255) / 256);
+    if (n_out == kOutHybrid)
+        head_part_z_kernel<kOutHybrid><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n);
+    else
+        head_part_z_kernel<2><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n);
 }
 
 void launch_init_state(const StepArgs *A, int n_sub, cudaStream_t s) {

@@ -29,6 +29,7 @@ bool ctx_fp32_view(const simnet_ctx *c, CtxFp32View &v) {
     for (int l = 0; l < c->n_layers; l++) v.layer[l] = c->layer[l];
     v.w2 = c->w2;
     v.b2 = c->b2;
+    v.n_out = c->n_out;
     v.device = c->device;
     return true;
 }
@@ -66,12 +67,13 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
     c->rows_n = k.window >> k.n_conv;
     c->fc1_in = c->rows_n * k.conv_channels;
     c->n_layers = k.n_conv + 1;
+    c->n_out = (k.flags & SIMNET_FLAG_HYBRID_HEAD) ? kOutHybrid : 2;
     int64_t n = 0, cin = kNF;
     for (int l = 0; l < k.n_conv; l++) {
         n += (int64_t)k.conv_channels * cin * 2 + k.conv_channels;
         cin = k.conv_channels;
     }
-    n += (int64_t)c->fc1_in * k.fc_hidden + k.fc_hidden + 2LL * k.fc_hidden + 2;
+    n += (int64_t)c->fc1_in * k.fc_hidden + k.fc_hidden + (int64_t)c->n_out * k.fc_hidden + c->n_out;
     c->n_weights = n;
     for (int l = 0; l < c->n_layers; l++) {
         GemmLayer &g = c->layer[l];
@@ -352,7 +354,8 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
         Bg[l].assign(p, p + H);
         p += H;
     }
-    std::vector<float> w2(p, p + 2 * H), b2(p + 2 * H, p + 2 * H + 2);
+    const int NO = c->n_out;
+    std::vector<float> w2(p, p + (size_t)NO * H), b2(p + (size_t)NO * H, p + (size_t)NO * H + NO);
     simnet_status st;
     std::vector<std::vector<float>> s_act;
     if (k.precision == SIMNET_FP8_E4M3 && (st = calibrate_fp8(c, Wg, Bg, s_act)) != SIMNET_OK) return st;
@@ -430,10 +433,10 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
             cudaMemset(t.mb[l], 0, (size_t)c->layer[l].N * 4);
             cudaMemset(t.vb[l], 0, (size_t)c->layer[l].N * 4);
         }
-        cudaMemset(t.mw2, 0, 2 * (size_t)k.fc_hidden * 4);
-        cudaMemset(t.vw2, 0, 2 * (size_t)k.fc_hidden * 4);
-        cudaMemset(t.mb2, 0, 8);
-        cudaMemset(t.vb2, 0, 8);
+        cudaMemset(t.mw2, 0, (size_t)c->n_out * k.fc_hidden * 4);
+        cudaMemset(t.vw2, 0, (size_t)c->n_out * k.fc_hidden * 4);
+        cudaMemset(t.mb2, 0, (size_t)c->n_out * 4);
+        cudaMemset(t.vb2, 0, (size_t)c->n_out * 4);
     }
     for (auto &g : c->gexec)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
@@ -453,7 +456,9 @@ simnet_status ensure_workspace(simnet_ctx *c, int B) {
     CK(cudaMalloc(&c->X, xb));
     CK(cudaMalloc(&c->act[0], ab));
     CK(cudaMalloc(&c->act[1], ab));
-    CK(cudaMalloc(&c->h1, (size_t)B * k.fc_hidden * sizeof(float)));
+    // FC2 partials: at most fc_hidden / 32 column blocks (64-wide tiles, two halves) x n_out per row
+    const size_t h1n = std::max((size_t)k.fc_hidden, (size_t)(k.fc_hidden / 32) * c->n_out);
+    CK(cudaMalloc(&c->h1, (size_t)B * h1n * sizeof(float)));
     CK(cudaMalloc(&c->tick, (size_t)B * 4));
     CK(cudaMalloc(&c->pos, (size_t)B * 4));
     CK(cudaMalloc(&c->qstart, (size_t)B * 4));
@@ -503,8 +508,8 @@ static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t
         const int m_cap = B * g.m_mult;
         if (k.precision == SIMNET_FP32) {
             if (last)
-                launch_gemm_f32_part((const float *)in, (const float *)g.B, g.bias, c->w2, (float2 *)out, B, count,
-                                     g.m_mult, m_cap, g.N, g.K, g.relu, s, pdl);
+                launch_gemm_f32_part((const float *)in, (const float *)g.B, g.bias, c->w2, (float *)out, B, count,
+                                     g.m_mult, m_cap, g.N, g.K, g.relu, c->n_out, s, pdl);
             else
                 launch_gemm_f32((const float *)in, (const float *)g.B, g.bias, (float *)out, count, g.m_mult, m_cap,
                                 g.N, g.K, g.relu, s, pdl);
@@ -536,16 +541,19 @@ static void enqueue_gather(simnet_ctx *c, int B, cudaStream_t s, bool pdl, KTime
 static void enqueue_step(simnet_ctx *c, int B, cudaStream_t s, bool pdl, KTimer *kt = nullptr) {
     enqueue_cnn(c, c->n_active, B, s, pdl, kt);
     if (kt) kt->begin(SIMNET_KERNEL_HEAD_UPDATE);
-    const float2 *part = (const float2 *)c->h1;
+    const float *part = c->h1;
+    const int NO = c->n_out;
     switch (c->cfg.precision) {
         case SIMNET_FP32:
-            launch_head_update<float>(c->d_args, part, c->n_part, B, c->b2, (float *)c->X, B, s, pdl);
+            launch_head_update<float>(c->d_args, part, c->n_part, B, c->b2, (float *)c->X, B, NO, s, pdl);
             break;
         case SIMNET_BF16:
-            launch_head_update<__nv_bfloat16>(c->d_args, part, c->n_part, B, c->b2, (__nv_bfloat16 *)c->X, B, s, pdl);
+            launch_head_update<__nv_bfloat16>(c->d_args, part, c->n_part, B, c->b2, (__nv_bfloat16 *)c->X, B, NO, s,
+                                              pdl);
             break;
         default:
-            launch_head_update<__nv_fp8_e4m3>(c->d_args, part, c->n_part, B, c->b2, (__nv_fp8_e4m3 *)c->X, B, s, pdl);
+            launch_head_update<__nv_fp8_e4m3>(c->d_args, part, c->n_part, B, c->b2, (__nv_fp8_e4m3 *)c->X, B, NO, s,
+                                              pdl);
             break;
     }
     if (kt) kt->end();
@@ -570,7 +578,8 @@ static simnet_status prepare_plans(simnet_ctx *c, int B, bool pdl) {
         const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
         void *out = last ? (void *)c->h1 : c->act[l & 1];
         std::string why;
-        if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, last ? TC_OUT_PART : TC_OUT_ACT, B * g.m_mult,
+        const int ok_kind = !last ? TC_OUT_ACT : c->n_out == kOutHybrid ? TC_OUT_PART_HYBRID : TC_OUT_PART;
+        if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, ok_kind, B * g.m_mult,
                           c->cfg.spin_limit_ns, c->status, pdl, why))
             return fail(c, SIMNET_ECUDA, "tensor-core plan for layer %d: %s", l, why.c_str());
         if (c->tuned_B == B && c->tuned_bn[l] && c->tuned_bn[l] != c->plan[l].BN &&
@@ -846,7 +855,7 @@ extern "C" simnet_status simnet_cnn_forward(simnet_ctx *c, const float *x, float
     if ((st = prepare_plans(c, n, false)) != SIMNET_OK) return st;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int32_t), s));
     enqueue_cnn(c, c->cnt, n, s, false);
-    launch_head_part_z((const float2 *)c->h1, c->n_part, n, c->b2, z, n, s);
+    launch_head_part_z(c->h1, c->n_part, n, c->b2, z, n, c->n_out, s);
     CK(cudaGetLastError());
     return SIMNET_OK;
 }

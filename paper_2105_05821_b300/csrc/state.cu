@@ -21,7 +21,7 @@ struct StateHeader {
     int32_t version, kind;
     int32_t window, n_conv, conv_channels, fc_hidden;
     int32_t retire_width, strict, precision, n_sub;
-    int32_t cap, reserved;
+    int32_t cap, head;   // head: 0 regression FC2 (2 outputs), 1 hybrid (22)
     int64_t steps_done, max_len, n_instructions;
     uint64_t trace_fp, weights_fp;
     int64_t payload_bytes;
@@ -36,11 +36,11 @@ size_t sim_payload(int B, int cap) {
 
 // TRAIN payload: canonical FP32 weights [n_weights], step (int64), then per
 // GEMM layer l the Adam moments m, v of its weights (FP32 [N][K], GEMM
-// layout) and of its bias ([N]); then m, v of FC2's weights [2H] and bias [2].
+// layout) and of its bias ([N]); then m, v of FC2's weights [n_out*H] and bias [n_out].
 size_t train_payload(const simnet_ctx *c) {
     size_t n = (size_t)c->n_weights * 4 + 8;
     for (int l = 0; l < c->n_layers; l++) n += 2 * ((size_t)c->layer[l].N * c->layer[l].K + c->layer[l].N) * 4;
-    return n + 2 * (2 * (size_t)c->cfg.fc_hidden + 2) * 4;
+    return n + 2 * ((size_t)c->n_out * c->cfg.fc_hidden + c->n_out) * 4;
 }
 
 void fill_header(const simnet_ctx *c, int kind, StateHeader &h) {
@@ -56,6 +56,7 @@ void fill_header(const simnet_ctx *c, int kind, StateHeader &h) {
     h.strict = (c->cfg.flags & SIMNET_FLAG_RETIRE_STRICT) ? 1 : 0;
     h.precision = c->cfg.precision;
     h.cap = c->cap;
+    h.head = c->n_out == 22 ? 1 : 0;
 }
 
 }  // namespace
@@ -127,11 +128,11 @@ extern "C" simnet_status simnet_state_save(simnet_ctx *c, int32_t kind, void *ho
             CK(put(t.mb[l], nb));
             CK(put(t.vb[l], nb));
         }
-        const size_t h2 = 2 * (size_t)c->cfg.fc_hidden;
+        const size_t h2 = (size_t)c->n_out * c->cfg.fc_hidden;
         CK(put(t.mw2, h2));
         CK(put(t.vw2, h2));
-        CK(put(t.mb2, 2));
-        CK(put(t.vb2, 2));
+        CK(put(t.mb2, (size_t)c->n_out));
+        CK(put(t.vb2, (size_t)c->n_out));
     }
     memcpy(out, &h, sizeof h);
     *bytes = off;
@@ -152,9 +153,9 @@ extern "C" simnet_status simnet_state_load(simnet_ctx *c, int32_t kind, const vo
     StateHeader mine;
     fill_header(c, kind, mine);
     if (h.window != mine.window || h.n_conv != mine.n_conv || h.conv_channels != mine.conv_channels ||
-        h.fc_hidden != mine.fc_hidden)
-        return fail(c, SIMNET_EINVAL, "state_load: state of another CNN shape (W=%d, %d x conv%d, FC%d)", h.window,
-                    h.n_conv, h.conv_channels, h.fc_hidden);
+        h.fc_hidden != mine.fc_hidden || h.head != mine.head)
+        return fail(c, SIMNET_EINVAL, "state_load: state of another CNN shape (W=%d, %d x conv%d, FC%d, %s head)",
+                    h.window, h.n_conv, h.conv_channels, h.fc_hidden, h.head ? "hybrid" : "regression");
     const uint8_t *in = (const uint8_t *)host_buf;
     size_t off = sizeof h;
     CK(cudaSetDevice(c->device));
@@ -212,11 +213,11 @@ extern "C" simnet_status simnet_state_load(simnet_ctx *c, int32_t kind, const vo
         CK(put(t.mb[l], nb * 4));
         CK(put(t.vb[l], nb * 4));
     }
-    const size_t h2 = 2 * (size_t)c->cfg.fc_hidden;
+    const size_t h2 = (size_t)c->n_out * c->cfg.fc_hidden;
     CK(put(t.mw2, h2 * 4));
     CK(put(t.vw2, h2 * 4));
-    CK(put(t.mb2, 8));
-    CK(put(t.vb2, 8));
+    CK(put(t.mb2, (size_t)c->n_out * 4));
+    CK(put(t.vb2, (size_t)c->n_out * 4));
     t.step = step;
     return SIMNET_OK;
 }

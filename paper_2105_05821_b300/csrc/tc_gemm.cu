@@ -31,11 +31,11 @@ namespace {
 
 using namespace tcx;
 
-enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_FP8 = 2, OUT_FC2PART = 3 };
+enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_FP8 = 2, OUT_FC2PART = 3, OUT_FC2HYB = 4 };
 
 struct TcArgs {
     const float *bias, *scale, *oscale, *w2;
-    void *out;                 // [M][N] activations, or FC2 partials [n_tiles_n][part_stride] float2
+    void *out;                 // [M][N] activations, or FC2 partials [2 * n_tiles_n][part_stride][2 or 22] float
     const int32_t *count;
     int m_mult, m_cap, N, K, relu, n_tiles_n, part_stride, prm_floats;
     int64_t spin_ns;
@@ -54,7 +54,7 @@ struct TcLayout {
     static constexpr int CHUNK_BYTES = 32 * OUT_ES;        // 32 output columns of one row
     static constexpr int STAGE_ROW = CHUNK_BYTES + 16;     // padded: conflict-free 16-byte stores
     static constexpr int EPI_WARPS = 8;                    // two per TMEM lane quadrant
-    static constexpr int STAGING = OUT == OUT_FC2PART ? 0 : EPI_WARPS * 32 * STAGE_ROW;
+    static constexpr int STAGING = OUT >= OUT_FC2PART ? 0 : EPI_WARPS * 32 * STAGE_ROW;
 };
 
 template <int BN, int STAGES, bool FP8, int OUT>
@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(320, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     float *prm = reinterpret_cast<float *>(smem + L::RING + L::BARS);   // bias | scale | oscale | w2 (each N, w2 2N)
+    // (the hybrid head's 22 FC2 rows are read through L1 instead of being staged)
     const int N = args.N;
     float *s_bias = prm, *s_scale = prm + N, *s_oscale = prm + 2 * N, *s_w2 = prm + 3 * N;
     uint8_t *staging = smem + L::RING + L::BARS + args.prm_floats * 4;
@@ -197,6 +198,10 @@ __global__ void __launch_bounds__(320, 1)
             const int row = m0 + q * 32 + lane;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2));
             float pf = 0.f, pe = 0.f;
+            constexpr int NH = OUT == OUT_FC2HYB ? kOutHybrid : 1;
+            float ph[NH];
+#pragma unroll
+            for (int o = 0; o < NH; o++) ph[o] = 0.f;
 #pragma unroll 1
             for (int c = 0; c < CPW; c++) {
                 uint32_t r[32];
@@ -232,6 +237,18 @@ __global__ void __launch_bounds__(320, 1)
                         pf = fmaf(v[4 * j4 + 2], wf.z, pf); pf = fmaf(v[4 * j4 + 3], wf.w, pf);
                         pe = fmaf(v[4 * j4], we.x, pe); pe = fmaf(v[4 * j4 + 1], we.y, pe);
                         pe = fmaf(v[4 * j4 + 2], we.z, pe); pe = fmaf(v[4 * j4 + 3], we.w, pe);
+                    }
+                } else if constexpr (OUT == OUT_FC2HYB) {
+                    // every lane reads the same FC2 row segment: L1 broadcasts
+#pragma unroll
+                    for (int o = 0; o < NH; o++) {
+                        const float4 *wr = reinterpret_cast<const float4 *>(args.w2 + (size_t)o * N + col0);
+#pragma unroll
+                        for (int j4 = 0; j4 < 8; j4++) {
+                            const float4 w = __ldg(wr + j4);
+                            ph[o] = fmaf(v[4 * j4], w.x, ph[o]); ph[o] = fmaf(v[4 * j4 + 1], w.y, ph[o]);
+                            ph[o] = fmaf(v[4 * j4 + 2], w.z, ph[o]); ph[o] = fmaf(v[4 * j4 + 3], w.w, ph[o]);
+                        }
                     }
                 } else {
                     // this thread's row segment -> padded staging row `lane`
@@ -285,6 +302,14 @@ __global__ void __launch_bounds__(320, 1)
                 if (row < M)
                     reinterpret_cast<float2 *>(args.out)[(size_t)(2 * nt + half) * args.part_stride + row] =
                         make_float2(pf, pe);
+            }
+            if constexpr (OUT == OUT_FC2HYB) {
+                if (row < M) {
+                    float *dst = reinterpret_cast<float *>(args.out) +
+                                 ((size_t)(2 * nt + half) * args.part_stride + row) * NH;
+#pragma unroll
+                    for (int o = 0; o < NH; o++) dst[o] = ph[o];
+                }
             }
             tc_fence_before();
             mbar_arrive(tempty(acc));
@@ -367,7 +392,7 @@ void dispatch(const TcPlan &p, const TcArgs &a, cudaStream_t s) {
 int stages_for(int BN) { return BN == 64 ? 6 : BN == 128 ? 5 : 3; }
 
 int out_es(int out_kind, int prec) {
-    return out_kind == TC_OUT_F32 ? 4 : out_kind == TC_OUT_PART ? 0 : (prec == SIMNET_BF16 ? 2 : 1);
+    return out_kind == TC_OUT_F32 ? 4 : out_kind >= TC_OUT_PART ? 0 : (prec == SIMNET_BF16 ? 2 : 1);
 }
 
 }  // namespace
@@ -391,7 +416,7 @@ int num_sms() {
 static void finish_plan(TcPlan &p) {
     p.stages = stages_for(p.BN);
     const int es = out_es(p.out_kind, p.prec);
-    const size_t staging = p.out_kind == TC_OUT_PART ? 0 : (size_t)8 * 32 * (32 * es + 16);
+    const size_t staging = p.out_kind >= TC_OUT_PART ? 0 : (size_t)8 * 32 * (32 * es + 16);
     p.smem = (size_t)p.stages * (A_BYTES + p.BN * ROW_BYTES) + 1024 + ((2 * p.stages + 4) * 8 + 16) +
              (size_t)p.prm_floats * 4 + staging;
     const int m_tiles = (p.m_cap + BM - 1) / BM;
@@ -468,6 +493,10 @@ void launch_tc_gemm(const TcPlan &p, const GemmLayer &g, const int32_t *count, c
         case TC_OUT_PART:
             if (fp8) dispatch<true, OUT_FC2PART>(p, a, s);
             else dispatch<false, OUT_FC2PART>(p, a, s);
+            break;
+        case TC_OUT_PART_HYBRID:
+            if (fp8) dispatch<true, OUT_FC2HYB>(p, a, s);
+            else dispatch<false, OUT_FC2HYB>(p, a, s);
             break;
         default:
             if (fp8) dispatch<true, OUT_FP8>(p, a, s);

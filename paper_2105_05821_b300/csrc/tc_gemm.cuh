@@ -12,7 +12,8 @@ namespace simnet {
 enum TcOut : int {
     TC_OUT_ACT = 0,   // activations [M][N] in the layer precision (BF16, or FP8 e4m3)
     TC_OUT_F32 = 1,   // FP32 [M][N]
-    TC_OUT_PART = 3,  // FC2 partial dot products [2*N/BN][m_cap] float2 (fetch, execution)
+    TC_OUT_PART = 3,  // FC2 partial dot products [2*N/BN][m_cap][2] float (fetch, execution)
+    TC_OUT_PART_HYBRID = 4,  // the same for the hybrid head's 22 FC2 outputs: [2*N/BN][m_cap][22]
 };
 
 // Everything one layer's tensor-core launch needs; built once per
@@ -43,7 +44,8 @@ bool make_tc_plan(TcPlan &p, int prec, const void *in, const GemmLayer &g, void 
 bool retune_tc_plan(TcPlan &p, const GemmLayer &g, int BN, std::string &why);
 
 // C = act(A * B^T * scale + bias) * oscale for M = min(*count * m_mult, m_cap)
-// rows; TC_OUT_PART folds FC2 (`w2` [2][N]) into the epilogue instead.
+// rows; TC_OUT_PART / TC_OUT_PART_HYBRID fold FC2 (`w2` [2][N] / [22][N]) into
+// the epilogue instead.
 void launch_tc_gemm(const TcPlan &p, const GemmLayer &g, const int32_t *count, const float *w2, cudaStream_t s);
 
 int num_sms();

@@ -150,6 +150,41 @@ __global__ void mse_softplus_kernel(const float *__restrict__ z, const uint8_t *
     if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
 }
 
+// Hybrid head (Sec. 2.3), one thread per (window r, latency k): z holds 22
+// outputs per window, the ten class logits of latency k at 11k..11k+9 and its
+// regression output at 11k+10.  loss += (CE + (softplus(z_v) - t)^2) / (2n) with
+// CE = logsumexp(logits) - logit[min(t, 9)]; dz of the logits = (softmax - onehot)
+// / (2n), of the value (softplus(z_v) - t) / n * sigmoid(z_v).
+__global__ void hybrid_loss_kernel(const float *__restrict__ z, const uint8_t *__restrict__ labels,
+                                   const int64_t *__restrict__ idx, int n, float *__restrict__ dz,
+                                   double *__restrict__ loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < 2 * n) {
+        const int r = i >> 1, k = i & 1;
+        const float *lg = z + (size_t)r * kOutHybrid + 11 * k;
+        float *dl = dz + (size_t)r * kOutHybrid + 11 * k;
+        const int t = labels[2 * idx[r] + k];
+        const int cls = t > 8 ? 9 : t;
+        float mx = lg[0];
+        for (int j = 1; j < 10; j++) mx = fmaxf(mx, lg[j]);
+        float se = 0.f;
+        for (int j = 0; j < 10; j++) se += expf(lg[j] - mx);
+        const float inv2n = 1.f / (2.f * (float)n);
+        for (int j = 0; j < 10; j++) dl[j] = (expf(lg[j] - mx) / se - (j == cls ? 1.f : 0.f)) * inv2n;
+        const float x = lg[10];
+        const float y = x > 20.f ? x : log1pf(expf(x));
+        const float diff = y - (float)t;
+        const float sg = x > 20.f ? 1.f : 1.f / (1.f + expf(-x));
+        dl[10] = diff / (float)n * sg;
+        const double ce = (double)mx + log((double)se) - (double)lg[cls];
+        l = (ce + (double)diff * diff) / (2.0 * n);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
+}
+
 __global__ void adam_kernel(float *__restrict__ th, float *__restrict__ m, float *__restrict__ v,
                             const float *__restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
                             float c1, float c2) {
@@ -233,17 +268,17 @@ simnet_status ensure_train(simnet_ctx *c, int n) {
             CK(cudaMemset(t.mb[l], 0, (size_t)g.N * 4));
             CK(cudaMemset(t.vb[l], 0, (size_t)g.N * 4));
         }
-        const size_t h2 = 2 * (size_t)k.fc_hidden;
+        const size_t h2 = (size_t)c->n_out * k.fc_hidden, b2n = (size_t)c->n_out * 4;
         CK(cudaMalloc(&t.gw2, h2 * 4));
         CK(cudaMalloc(&t.mw2, h2 * 4));
         CK(cudaMalloc(&t.vw2, h2 * 4));
-        CK(cudaMalloc(&t.gb2, 8));
-        CK(cudaMalloc(&t.mb2, 8));
-        CK(cudaMalloc(&t.vb2, 8));
+        CK(cudaMalloc(&t.gb2, b2n));
+        CK(cudaMalloc(&t.mb2, b2n));
+        CK(cudaMalloc(&t.vb2, b2n));
         CK(cudaMemset(t.mw2, 0, h2 * 4));
         CK(cudaMemset(t.vw2, 0, h2 * 4));
-        CK(cudaMemset(t.mb2, 0, 8));
-        CK(cudaMemset(t.vb2, 0, 8));
+        CK(cudaMemset(t.mb2, 0, b2n));
+        CK(cudaMemset(t.vb2, 0, b2n));
         CK(cudaMalloc(&t.loss, sizeof(double)));
         t.ready = true;
     }
@@ -264,8 +299,8 @@ simnet_status ensure_train(simnet_ctx *c, int n) {
     }
     CK(cudaMalloc(&t.dA, big * 4));
     CK(cudaMalloc(&t.dB, big * 4));
-    CK(cudaMalloc(&t.z, (size_t)n * 2 * 4));
-    CK(cudaMalloc(&t.dz, (size_t)n * 2 * 4));
+    CK(cudaMalloc(&t.z, (size_t)n * c->n_out * 4));
+    CK(cudaMalloc(&t.dz, (size_t)n * c->n_out * 4));
     t.n_cap = n;
     return SIMNET_OK;
 }
@@ -285,27 +320,27 @@ static void train_forward_enqueue(simnet_ctx *c, int n, cudaStream_t s) {
         gemm(round, in, g.K, 1, c->W32[l], 1, g.K, t.Y[l], g.N, R, g.N, g.K, c->bias[l], 1, false, s);
         in = t.Y[l];
     }
-    launch_head_z(t.Y[c->n_layers - 1], c->w2, c->b2, t.z, n, c->cfg.fc_hidden, s);
+    launch_head_z(t.Y[c->n_layers - 1], c->w2, c->b2, t.z, n, c->cfg.fc_hidden, c->n_out, s);
     t.n_last = n;
 }
 
 // Backward from t.dz through the saved activations; gradients (GEMM layout) in t.g*.
 static void train_backward_enqueue(simnet_ctx *c, cudaStream_t s) {
     TrainState &t = c->tr;
-    const int n = t.n_last, H = c->cfg.fc_hidden, L = c->n_layers;
+    const int n = t.n_last, H = c->cfg.fc_hidden, L = c->n_layers, NO = c->n_out;
     const bool round = c->cfg.precision == SIMNET_BF16;
     for (int l = 0; l < L; l++) {
         cudaMemsetAsync(t.gW[l], 0, (size_t)c->layer[l].N * c->layer[l].K * 4, s);
         cudaMemsetAsync(t.gb[l], 0, (size_t)c->layer[l].N * 4, s);
     }
-    cudaMemsetAsync(t.gw2, 0, 2 * (size_t)H * 4, s);
-    cudaMemsetAsync(t.gb2, 0, 8, s);
+    cudaMemsetAsync(t.gw2, 0, (size_t)NO * H * 4, s);
+    cudaMemsetAsync(t.gb2, 0, (size_t)NO * 4, s);
     // FC2: dW2 = dz^T H, db2 = sum dz, dH = dz W2 (masked by ReLU of FC1)
     const float *Hh = t.Y[L - 1];
-    gemm(false, t.dz, 1, 2, Hh, H, 1, t.gw2, H, 2, H, n, nullptr, 0, true, s);
-    colsum_kernel<<<dim3(64, 1), 32, 0, s>>>(t.dz, n, 2, t.gb2);
+    gemm(false, t.dz, 1, NO, Hh, H, 1, t.gw2, H, NO, H, n, nullptr, 0, true, s);
+    colsum_kernel<<<dim3(64, 1), 32, 0, s>>>(t.dz, n, NO, t.gb2);
     float *d = t.dA, *d2 = t.dB;
-    gemm(false, t.dz, 2, 1, c->w2, H, 1, d, H, n, H, 2, nullptr, 0, false, s);
+    gemm(false, t.dz, NO, 1, c->w2, H, 1, d, H, n, H, NO, nullptr, 0, false, s);
     relu_mask_kernel<<<blocks((int64_t)n * H), 256, 0, s>>>(d, Hh, (int64_t)n * H);
     // FC1 and the conv layers, last to first: dW = dY^T A, db = sum dY, dA = dY W
     for (int l = L - 1; l >= 0; l--) {
@@ -344,9 +379,9 @@ static void grads_to_canonical(simnet_ctx *c, float *out, cudaStream_t s) {
     p += cnt;
     cudaMemcpyAsync(p, t.gb[k.n_conv], (size_t)H * 4, cudaMemcpyDeviceToDevice, s);
     p += H;
-    cudaMemcpyAsync(p, t.gw2, 2 * (size_t)H * 4, cudaMemcpyDeviceToDevice, s);
-    p += 2 * H;
-    cudaMemcpyAsync(p, t.gb2, 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(p, t.gw2, (size_t)c->n_out * H * 4, cudaMemcpyDeviceToDevice, s);
+    p += (size_t)c->n_out * H;
+    cudaMemcpyAsync(p, t.gb2, (size_t)c->n_out * 4, cudaMemcpyDeviceToDevice, s);
 }
 
 static void refresh_shadow(simnet_ctx *c, cudaStream_t s) {
@@ -391,7 +426,7 @@ extern "C" simnet_status simnet_train_forward(simnet_ctx *c, const float *x, flo
     cudaStream_t s = (cudaStream_t)stream;
     launch_pack_x<float>(x, c->tr.X, (int64_t)n * c->cfg.window, s);
     train_forward_enqueue(c, n, s);
-    CK(cudaMemcpyAsync(z, c->tr.z, (size_t)n * 2 * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(z, c->tr.z, (size_t)n * c->n_out * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaGetLastError());
     return SIMNET_OK;
 }
@@ -402,7 +437,7 @@ extern "C" simnet_status simnet_train_backward(simnet_ctx *c, const float *dz, f
     if (!c->tr.ready || c->tr.n_last <= 0) return fail(c, SIMNET_ESTATE, "train_backward: no forward to differentiate");
     CK(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(c->tr.dz, dz, (size_t)c->tr.n_last * 2 * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->tr.dz, dz, (size_t)c->tr.n_last * c->n_out * 4, cudaMemcpyDeviceToDevice, s));
     train_backward_enqueue(c, s);
     grads_to_canonical(c, grad, s);
     CK(cudaGetLastError());
@@ -425,7 +460,10 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
         w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X, nullptr);
     train_forward_enqueue(c, batch, s);
     CK(cudaMemsetAsync(t.loss, 0, sizeof(double), s));
-    mse_softplus_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
+    if (c->n_out == kOutHybrid)
+        hybrid_loss_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
+    else
+        mse_softplus_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
     train_backward_enqueue(c, s);
     // Adam (beta 0.9 / 0.999, eps 1e-8, no weight decay) on every parameter
     t.step++;
@@ -436,9 +474,9 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
         adam_kernel<<<blocks(e), 256, 0, s>>>(c->W32[l], t.mW[l], t.vW[l], t.gW[l], e, lr, b1, b2, eps, c1, c2);
         adam_kernel<<<blocks(nb), 256, 0, s>>>(c->bias[l], t.mb[l], t.vb[l], t.gb[l], nb, lr, b1, b2, eps, c1, c2);
     }
-    const int64_t h2 = 2 * (int64_t)c->cfg.fc_hidden;
+    const int64_t h2 = (int64_t)c->n_out * c->cfg.fc_hidden;
     adam_kernel<<<blocks(h2), 256, 0, s>>>(c->w2, t.mw2, t.vw2, t.gw2, h2, lr, b1, b2, eps, c1, c2);
-    adam_kernel<<<1, 32, 0, s>>>(c->b2, t.mb2, t.vb2, t.gb2, 2, lr, b1, b2, eps, c1, c2);
+    adam_kernel<<<1, 32, 0, s>>>(c->b2, t.mb2, t.vb2, t.gb2, c->n_out, lr, b1, b2, eps, c1, c2);
     refresh_shadow(c, s);
     invalidate_plans(c);
     c->weights_fp_dirty = true;
@@ -478,9 +516,9 @@ extern "C" simnet_status simnet_set_weights_device(simnet_ctx *c, const float *b
     p += cnt;
     CK(cudaMemcpyAsync(c->bias[k.n_conv], p, (size_t)H * 4, cudaMemcpyDeviceToDevice, s));
     p += H;
-    CK(cudaMemcpyAsync(c->w2, p, 2 * (size_t)H * 4, cudaMemcpyDeviceToDevice, s));
-    p += 2 * H;
-    CK(cudaMemcpyAsync(c->b2, p, 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c->w2, p, (size_t)c->n_out * H * 4, cudaMemcpyDeviceToDevice, s));
+    p += (size_t)c->n_out * H;
+    CK(cudaMemcpyAsync(c->b2, p, (size_t)c->n_out * 4, cudaMemcpyDeviceToDevice, s));
     refresh_shadow(c, s);
     invalidate_plans(c);
     c->weights_fp_dirty = true;
@@ -514,9 +552,9 @@ extern "C" simnet_status simnet_get_weights(simnet_ctx *c, float *blob) {
     p += cnt;
     cudaMemcpy(p, c->bias[k.n_conv], (size_t)H * 4, cudaMemcpyDeviceToDevice);
     p += H;
-    cudaMemcpy(p, c->w2, 2 * (size_t)H * 4, cudaMemcpyDeviceToDevice);
-    p += 2 * H;
-    cudaMemcpy(p, c->b2, 8, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(p, c->w2, (size_t)c->n_out * H * 4, cudaMemcpyDeviceToDevice);
+    p += (size_t)c->n_out * H;
+    cudaMemcpy(p, c->b2, (size_t)c->n_out * 4, cudaMemcpyDeviceToDevice);
     cudaError_t e = cudaMemcpy(blob, dev, (size_t)c->n_weights * 4, cudaMemcpyDeviceToHost);
     cudaFree(dev);
     if (e != cudaSuccess) return fail(c, SIMNET_ECUDA, "get_weights: %s", cudaGetErrorString(e));

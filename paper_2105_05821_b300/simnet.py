@@ -25,6 +25,7 @@ FLAG_KERNEL_EVENTS = 0x4
 FLAG_NO_PDL = 0x8
 FLAG_LAYERWISE = 0x10
 FLAG_NO_CLUSTER = 0x20
+FLAG_HYBRID_HEAD = 0x40
 PATHS = {0: "none", 1: "layerwise", 2: "persistent", 3: "cluster"}
 KERNEL_KINDS = 12
 KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
@@ -157,16 +158,19 @@ class Simnet:
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
                  pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0,
-                 cluster: bool = True):
+                 cluster: bool = True, hybrid: bool = False):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
-                 | (0 if persistent else FLAG_LAYERWISE) | (0 if cluster else FLAG_NO_CLUSTER))
+                 | (0 if persistent else FLAG_LAYERWISE) | (0 if cluster else FLAG_NO_CLUSTER)
+                 | (FLAG_HYBRID_HEAD if hybrid else 0))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, barrier_limit_us,
                             spin_limit_ns)
         self.window = window
         self.precision = prec
+        self.hybrid = bool(hybrid)
+        self.n_out = 22 if hybrid else 2      # FC2 outputs per window
         h = C.c_void_p()
         st = L.simnet_init(C.byref(self._cfg), C.byref(h))
         if st != 0:
@@ -175,6 +179,7 @@ class Simnet:
 
     @classmethod
     def for_arch(cls, arch, **kw) -> "Simnet":
+        kw.setdefault("hybrid", getattr(arch, "head", "regression") == "hybrid")
         return cls(arch.window, arch.n_conv, arch.channels, arch.hidden, **kw)
 
     def close(self):
@@ -269,12 +274,13 @@ class Simnet:
         return z
 
     def cnn_forward(self, x, z=None, stream=None):
-        """Pre-softplus CNN outputs [n, 2] for cuda float32 features [n, W, 50]."""
+        """FC2 outputs [n, n_out] (before softplus and the hybrid class decision)
+        for cuda float32 features [n, W, 50]."""
         import torch
         n = x.shape[0]
         assert x.is_contiguous() and x.dtype == torch.float32 and tuple(x.shape[1:]) == (self.window, 50)
         if z is None:
-            z = torch.empty((n, 2), dtype=torch.float32, device=x.device)
+            z = torch.empty((n, self.n_out), dtype=torch.float32, device=x.device)
         self._check(lib().simnet_cnn_forward(self._h, _ptr(x), _ptr(z), n, _stream(stream)))
         return z
 
@@ -294,7 +300,7 @@ class Simnet:
 
     def train_forward(self, x, stream=None):
         import torch
-        z = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+        z = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
         self._check(lib().simnet_train_forward(self._h, _ptr(x), _ptr(z), x.shape[0], _stream(stream)))
         return z
 

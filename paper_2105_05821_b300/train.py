@@ -59,6 +59,20 @@ def mse_softplus(z: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
     return (torch.nn.functional.softplus(z) - labels.float().clamp(0, 255)).pow(2).mean()
 
 
+def hybrid_loss(z: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
+    """Hybrid head (Sec. 2.3) loss on z [n, 22]: mean over the 2n latencies of the
+    cross-entropy of the ten class logits against class min(label, 9) plus the
+    squared error of softplus(regression output) against the label."""
+    y = labels.float().clamp(0, 255)
+    total = z.new_zeros(())
+    for t in range(2):
+        cls = y[:, t].clamp(max=9).long()
+        ce = torch.nn.functional.cross_entropy(z[:, 11 * t:11 * t + 10], cls, reduction="sum")
+        se = (torch.nn.functional.softplus(z[:, 11 * t + 10]) - y[:, t]).pow(2).sum()
+        total = total + ce + se
+    return total / (2 * z.shape[0])
+
+
 def train(sim: Simnet, w: Windows, steps: int, batch: int, lr: float = 1e-3, seed: int = 0,
           log_every: int = 0):
     """Fused library training steps on random windows; returns the loss per step."""

@@ -157,3 +157,23 @@ def test_hybrid_with_class_nine_always_winning_is_the_regression_model():
     np.testing.assert_array_equal(a.lat, b.lat)
     np.testing.assert_array_equal(a.cycles, b.cycles)
     np.testing.assert_array_equal(a.pre, b.pre)
+
+
+def test_head_decision_on_given_outputs():
+    """oracle.head on hand-set FC2 outputs: direct classes, the "more than 8"
+    class through softplus of the regression output, FP32 ties, and the
+    regression head's plain rounding."""
+    cfg = oracle.Config.of(hybrid(I.Arch(16, 2, 4, 8)))
+    z = np.zeros((3, 22))
+    z[0, 4] = 1.0                                  # fetch: class 4
+    z[0, 11 + 9], z[0, 21] = 2.0, 30.0             # execution: class 9, softplus(30) = 30
+    z[1, 0] = z[1, 7] = 0.5                        # exact tie: lowest index
+    z[1, 11 + 2], z[1, 11 + 3] = 0.25, 0.25 + 1e-12    # equal in FP32: class 2
+    z[2, 9], z[2, 10] = 1.0, -50.0                 # class 9 with a value that rounds to 0
+    z[2, 11 + 8] = 3.0
+    lat, pre = oracle.head(cfg, z)
+    np.testing.assert_array_equal(lat, [[4, 30], [0, 2], [0, 8]])
+    np.testing.assert_allclose(pre[:, 1], oracle.softplus(z[:, 21]), rtol=1e-15)
+    reg = oracle.Config.of(I.Arch(16, 2, 4, 8))
+    lat, pre = oracle.head(reg, np.array([[0.0, 3.4], [-60.0, 300.0]]))
+    np.testing.assert_array_equal(lat, [[1, 3], [0, 255]])   # softplus(0) = 0.693 -> 1
