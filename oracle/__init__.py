@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class _Cfg(C.Structure):
     _fields_ = [("window", C.c_int32), ("n_conv", C.c_int32), ("channels", C.c_int32),
                 ("hidden", C.c_int32), ("retire_width", C.c_int32), ("retire_strict", C.c_int32),
-                ("hybrid", C.c_int32)]
+                ("hybrid", C.c_int32), ("store_queue", C.c_int32)]
 
 
 _lib = None
@@ -52,7 +52,7 @@ def _L():
         _lib.oracle_blob_size.argtypes = [P]
         _lib.oracle_simulate.restype = C.c_int
         _lib.oracle_simulate.argtypes = [P, P, P, P, C.c_int32, P, C.c_int32, P, P, P,
-                                         P, P, P, P, P, C.c_int32]
+                                         P, P, P, P, P, P, C.c_int32]
         _lib.oracle_cnn_forward.restype = C.c_int
         _lib.oracle_cnn_forward.argtypes = [P, P, P, C.c_int64, P, C.c_int32]
         _lib.oracle_head.restype = C.c_int
@@ -80,20 +80,26 @@ class Config:
     hidden: int
     retire_width: int = 8
     retire_strict: bool = False
-    hybrid: bool = False          # hybrid head (22 FC2 outputs) instead of regression (2)
+    hybrid: bool = False          # hybrid head (11 FC2 outputs per latency) instead of regression (1)
+    store_queue: bool = False     # store latency + memory write queue (3 latencies instead of 2)
+
+    @property
+    def n_lat(self) -> int:
+        return 3 if self.store_queue else 2
 
     @property
     def n_out(self) -> int:
-        return 22 if self.hybrid else 2
+        return (11 if self.hybrid else 1) * self.n_lat
 
     def c(self) -> _Cfg:
         return _Cfg(self.window, self.n_conv, self.channels, self.hidden, self.retire_width,
-                    int(self.retire_strict), int(self.hybrid))
+                    int(self.retire_strict), int(self.hybrid), int(self.store_queue))
 
     @staticmethod
     def of(arch, retire_width: int = 8, retire_strict: bool = False) -> "Config":
         return Config(arch.window, arch.n_conv, arch.channels, arch.hidden, retire_width,
-                      retire_strict, getattr(arch, "head", "regression") == "hybrid")
+                      retire_strict, getattr(arch, "head", "regression") == "hybrid",
+                      bool(getattr(arch, "store_queue", False)))
 
 
 def blob_size(cfg: Config) -> int:
@@ -109,11 +115,12 @@ def num_threads() -> int:
 class SimResult:
     cycles: np.ndarray                 # int64 [n_subset]: final curTick of each sub-trace
     evictions: np.ndarray              # int64 [n_subset]
-    lat: Optional[np.ndarray] = None   # uint8 [N, 2] F, E used (global positions)
-    pre: Optional[np.ndarray] = None   # float64 [N, 2] softplus outputs before rounding
+    lat: Optional[np.ndarray] = None   # uint8 [N, n_lat] F, E (, S) used (global positions)
+    pre: Optional[np.ndarray] = None   # float64 [N, n_lat] softplus outputs before rounding
     tick: Optional[np.ndarray] = None  # int64 [N] curTick after each step
-    qlen: Optional[np.ndarray] = None  # int32 [N] queue length after each step
+    qlen: Optional[np.ndarray] = None  # int32 [N] processor-queue length after each step
     feat: Optional[np.ndarray] = None  # float64 [N, W, 50]
+    mlen: Optional[np.ndarray] = None  # int32 [N] memory-write-queue length after each step
 
 
 def simulate(cfg: Config, records: np.ndarray, offsets: np.ndarray,
@@ -130,21 +137,23 @@ def simulate(cfg: Config, records: np.ndarray, offsets: np.ndarray,
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
     if w is not None and len(w) != blob_size(cfg):
         raise ValueError(f"weight blob has {len(w)} values, config needs {blob_size(cfg)}")
-    rp = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8).reshape(N, 2)
+    NL = cfg.n_lat
+    rp = None if replay is None else np.ascontiguousarray(replay, dtype=np.uint8).reshape(N, NL)
     cyc = np.zeros(m, np.int64)
     ev = np.zeros(m, np.int64)
-    lat = np.zeros((N, 2), np.uint8) if logs else None
-    pre = np.full((N, 2), np.nan) if (logs and w is not None) else None
+    lat = np.zeros((N, NL), np.uint8) if logs else None
+    pre = np.full((N, NL), np.nan) if (logs and w is not None) else None
     tick = np.zeros(N, np.int64) if logs else None
     qlen = np.zeros(N, np.int32) if logs else None
+    mlen = np.zeros(N, np.int32) if logs else None
     feat = np.zeros((N, cfg.window, NF)) if features else None
     c = cfg.c()
     rc = _L().oracle_simulate(C.byref(c), _p(w), _p(records), _p(offsets), n_sub, _p(sub), m,
                               _p(rp), _p(cyc), _p(ev), _p(lat), _p(pre), _p(tick), _p(qlen),
-                              _p(feat), int(n_threads))
+                              _p(mlen), _p(feat), int(n_threads))
     if rc != 0:
         raise ValueError("oracle_simulate rejected its arguments")
-    return SimResult(cyc, ev, lat, pre, tick, qlen, feat)
+    return SimResult(cyc, ev, lat, pre, tick, qlen, feat, mlen)
 
 
 def cnn_forward(cfg: Config, weights: np.ndarray, x: np.ndarray, n_threads: int = 0) -> np.ndarray:
@@ -162,13 +171,13 @@ def cnn_forward(cfg: Config, weights: np.ndarray, x: np.ndarray, n_threads: int 
 
 
 def head(cfg: Config, z: np.ndarray):
-    """The head's latency decision on FC2 outputs z [n, n_out]: (lat [n, 2]
-    uint8, pre [n, 2] softplus of the regression output)."""
+    """The head's latency decision on FC2 outputs z [n, n_out]: (lat [n, n_lat]
+    uint8, pre [n, n_lat] softplus of the regression output)."""
     z = np.ascontiguousarray(z, dtype=np.float64)
     n = z.shape[0]
     assert z.shape[1:] == (cfg.n_out,)
-    lat = np.zeros((n, 2), np.uint8)
-    pre = np.zeros((n, 2))
+    lat = np.zeros((n, cfg.n_lat), np.uint8)
+    pre = np.zeros((n, cfg.n_lat))
     c = cfg.c()
     if _L().oracle_head(C.byref(c), _p(z), n, _p(lat), _p(pre)) != 0:
         raise ValueError("bad config")
@@ -196,11 +205,11 @@ def window_features(cfg: Config, records, fetch, e_label, ctx_begin, idx) -> np.
 
 
 def loss_grad(cfg: Config, weights: np.ndarray, x: np.ndarray, y: np.ndarray):
-    """(loss, grad) for labels y [n, 2]: mean squared error of softplus(z), plus the
+    """(loss, grad) for labels y [n, n_lat]: mean squared error of softplus(z), plus the
     cross-entropy of the class logits for a hybrid head (oracle.c states the loss)."""
     w = np.ascontiguousarray(weights, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64)
-    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 2)
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, cfg.n_lat)
     g = np.zeros_like(w)
     loss = C.c_double(0.0)
     c = cfg.c()

@@ -20,6 +20,10 @@
  *     bandwidth, eviction at capacity, append with residence 0, and the drain
  *     after the last instruction (Sec. 3.2), so that the final curTick equals
  *     the sum of fetch latencies plus Delta (Sec. 3.1, Eq. 1);
+ *   - optionally a third latency, the store latency, and the memory write
+ *     queue: a store that retires from the processor queue enters it and
+ *     leaves, in order and with no bandwidth limit, once its residence reaches
+ *     the store latency (Sec. 3.2);
  *   - sub-traces simulated independently, each from an empty queue and
  *     curTick = 0 (Sec. 3.3);
  *   - the MSE training loss (hybrid head: cross-entropy of the class logits
@@ -36,7 +40,8 @@
  * Feature encoding of one row (channel: meaning):
  *   0-31 opcode one-hot | 32,33,34 src0/32, src1/32, dst/32 |
  *   35,36,37 is_load, is_store, is_branch | 38-40 cache level one-hot |
- *   41 mispredict | 42 min(residence, 4095)/64 | 43 E/64 | 44 store latency (0) |
+ *   41 mispredict | 42 min(residence, 4095)/64 | 43 E/64 |
+ *   44 S/64 for a store when the memory write queue is modelled, else 0 |
  *   45,46,47 ctx.dst == cur.src0 / cur.src1 / cur.dst |
  *   48 both are memory ops at the same cache level | 49 zero.
  * The current instruction's row keeps channels 42-49 at zero (the paper pads
@@ -63,12 +68,16 @@ typedef struct {
     int32_t hidden;        /* FC1 width */
     int32_t retire_width;  /* processor-queue retire bandwidth per cycle */
     int32_t retire_strict; /* 0: ready at residence >= E; 1: residence > E */
-    int32_t hybrid;        /* 0: regression head (2 outputs); 1: hybrid head (22 outputs) */
+    int32_t hybrid;        /* 0: regression head; 1: hybrid head (11 outputs per latency) */
+    int32_t store_queue;   /* 1: a third latency (store) and the memory write queue (Sec. 3.2) */
 } oracle_cfg;
 
-/* FC2 outputs: regression [fetch, execution]; hybrid, per latency t in {fetch,
- * execution}: 10 class logits (0..8 cycles, "more than 8") then one value. */
-static int n_out(const oracle_cfg *c) { return c->hybrid ? 22 : 2; }
+/* Latencies predicted per instruction: fetch, execution (and store). */
+static int n_lat(const oracle_cfg *c) { return c->store_queue ? 3 : 2; }
+/* FC2 outputs: regression, one per latency [fetch, execution(, store)]; hybrid,
+ * per latency t: 10 class logits (0..8 cycles, "more than 8") then one value. */
+static int n_out(const oracle_cfg *c) { return (c->hybrid ? 11 : 1) * n_lat(c); }
+#define MAXOUT 33
 
 /* ------------------------------------------------------------------ records */
 typedef struct { int op, s0, s1, dst, ld, st, br, lvl, mp; } inst_t;
@@ -102,9 +111,10 @@ static void encode_static(const inst_t *a, double *row)
     row[41] = a->mp;
 }
 
-/* One context row: static features, residence and execution latency, and the
+/* One context row: static features, residence, execution latency and (for a
+ * store, with the memory write queue modelled) store latency, and the
  * dependency flags against the current instruction. */
-static void encode_context(const inst_t *cur, uint32_t ctx_rec, int64_t residence, int e,
+static void encode_context(const inst_t *cur, uint32_t ctx_rec, int64_t residence, int e, int s,
                            double *row)
 {
     inst_t c = decode(ctx_rec);
@@ -112,7 +122,7 @@ static void encode_context(const inst_t *cur, uint32_t ctx_rec, int64_t residenc
     if (residence > 4095) residence = 4095;
     row[42] = (double)residence / 64.0;
     row[43] = e / 64.0;
-    row[44] = 0.0;
+    row[44] = c.st ? s / 64.0 : 0.0;
     row[45] = (c.dst == cur->s0);
     row[46] = (c.dst == cur->s1);
     row[47] = (c.dst == cur->dst);
@@ -160,7 +170,7 @@ static net_t net_view(const oracle_cfg *c, const double *blob)
 typedef struct {
     double *act[MAXCONV + 1];  /* act[0] = input [W][NF]; act[k+1] = conv k out [W>>(k+1)][C] */
     double *hid;               /* FC1 output after ReLU [H] */
-    double z[22];              /* FC2 outputs (before softplus / class decision) */
+    double z[MAXOUT];          /* FC2 outputs (before softplus / class decision) */
 } fwd_t;
 
 static size_t fwd_doubles(const oracle_cfg *c)
@@ -233,7 +243,7 @@ static int to_cycles(double y)
     return (int)nearbyint(y);
 }
 
-/* Latency t (0 fetch, 1 execution) from the FC2 outputs z; *pre gets the
+/* Latency t (0 fetch, 1 execution, 2 store) from the FC2 outputs z; *pre gets the
  * regression output after softplus.  Regression head: that value, clamped and
  * rounded.  Hybrid head (Sec. 2.3): the class with the largest logit of
  * z[11t .. 11t+9], compared after rounding to FP32 as the kernels compute
@@ -257,91 +267,132 @@ static int head_latency(const oracle_cfg *c, const double *z, int t, double *pre
 typedef struct {
     uint32_t rec;
     int e;              /* predicted execution latency */
-    int64_t fetch_tick; /* curTick when it entered the queue (residence 0) */
+    int s;              /* predicted store latency (used for stores, memory write queue only) */
+    int64_t fetch_tick; /* curTick when it entered the processor queue (residence 0) */
 } qent_t;
 
-static int ready(const oracle_cfg *c, const qent_t *q, int64_t tick)
+/* Ready to leave the processor queue (lat = E) or the memory write queue (lat = S). */
+static int ready(const oracle_cfg *c, const qent_t *q, int lat, int64_t tick)
 {
     int64_t res = tick - q->fetch_tick;
-    return c->retire_strict ? (res > q->e) : (res >= q->e);
+    return c->retire_strict ? (res > lat) : (res >= lat);
 }
 
-/* retire up to `budget` ready entries from the oldest end, in order; returns how many */
-static int retire(const oracle_cfg *c, qent_t *q, int *len, int64_t tick, int64_t budget)
+/* Processor queue: retire up to `budget` ready entries from the oldest end, in
+ * order.  With the memory write queue modelled, a retired store moves to its
+ * tail (keeping fetch order); other instructions leave.  Returns how many. */
+static int retire_pq(const oracle_cfg *c, qent_t *q, int *len, qent_t *mq, int *mlen, int64_t tick,
+                     int64_t budget)
 {
     int k = 0;
-    while (k < *len && k < budget && ready(c, &q[k], tick)) k++;
+    while (k < *len && k < budget && ready(c, &q[k], q[k].e, tick)) {
+        if (c->store_queue && decode(q[k].rec).st) mq[(*mlen)++] = q[k];
+        k++;
+    }
     memmove(q, q + k, (size_t)(*len - k) * sizeof(qent_t));
     *len -= k;
     return k;
 }
 
+/* Memory write queue: retire every ready entry from the oldest end, in order,
+ * with no bandwidth limit (Sec. 3.2).  Returns how many. */
+static int retire_mq(const oracle_cfg *c, qent_t *mq, int *mlen, int64_t tick)
+{
+    int k = 0;
+    while (k < *mlen && ready(c, &mq[k], mq[k].s, tick)) k++;
+    memmove(mq, mq + k, (size_t)(*mlen - k) * sizeof(qent_t));
+    *mlen -= k;
+    return k;
+}
+
 typedef struct {
-    const uint8_t *replay;   /* [n][2] integer F,E to use instead of the CNN's, or NULL */
-    uint8_t *lat_log;        /* [n][2] F,E used */
-    double *pre_log;         /* [n][2] softplus outputs before clamp/round */
+    const uint8_t *replay;   /* [n][n_lat] integer latencies to use instead of the CNN's, or NULL */
+    uint8_t *lat_log;        /* [n][n_lat] latencies used */
+    double *pre_log;         /* [n][n_lat] softplus outputs before clamp/round */
     int64_t *tick_log;       /* [n] curTick after the instruction's step */
-    int32_t *len_log;        /* [n] queue length after the step */
+    int32_t *len_log;        /* [n] processor-queue length after the step */
+    int32_t *mlen_log;       /* [n] memory-write-queue length after the step */
     double *feat_log;        /* [n][W][NF] feature matrices (tiny cases only) */
     int64_t evictions, retired;
 } sublog_t;
 
-/* Simulate one sub-trace from an empty queue and curTick = 0 (Sec. 3.3).
- * Returns the final curTick = sum of F + Delta (Eq. 1). */
+/* Simulate one sub-trace from empty queues and curTick = 0 (Sec. 3.3).
+ * Returns the final curTick = sum of F + Delta (Eq. 1).
+ *
+ * The context of the next prediction is every instruction still in the
+ * simulator, newest first: the processor queue, then the memory write queue
+ * (whose stores all retired from the processor queue, so they are older).
+ * Both queues together hold at most W-1 entries; appending to a full simulator
+ * evicts the oldest instruction, the memory write queue's head if it has one. */
 static int64_t simulate_one(const oracle_cfg *c, const net_t *net, const uint32_t *rec, int64_t n,
                             sublog_t *lg)
 {
-    const int W = c->window, cap = W - 1;
+    const int W = c->window, cap = W - 1, NL = n_lat(c);
     qent_t *q = (qent_t *)malloc(sizeof(qent_t) * (size_t)(cap > 0 ? cap : 1));
+    qent_t *mq = (qent_t *)malloc(sizeof(qent_t) * (size_t)(cap > 0 ? cap : 1));
     double *X = (double *)malloc(sizeof(double) * (size_t)W * NF);
     double *mem = net ? (double *)malloc(sizeof(double) * fwd_doubles(c)) : NULL;
     fwd_t f;
-    int len = 0;
+    int len = 0, mlen = 0;
     int64_t tick = 0;
     lg->evictions = lg->retired = 0;
 
     for (int64_t i = 0; i < n; i++) {
         const inst_t cur = decode(rec[i]);
-        /* build the input: current instruction, then context newest first */
+        /* build the input: current instruction, then the context newest first */
         memset(X, 0, sizeof(double) * (size_t)W * NF);
         encode_static(&cur, X);
-        for (int j = 1; j <= len; j++) {
-            const qent_t *e = &q[len - j];
-            encode_context(&cur, e->rec, tick - e->fetch_tick, e->e, X + (size_t)j * NF);
+        for (int j = 1; j <= len + mlen; j++) {
+            const qent_t *e = j <= len ? &q[len - j] : &mq[mlen - (j - len)];
+            encode_context(&cur, e->rec, tick - e->fetch_tick, e->e, e->s, X + (size_t)j * NF);
         }
         if (lg->feat_log) memcpy(lg->feat_log + (size_t)i * W * NF, X, sizeof(double) * (size_t)W * NF);
 
-        int F, E;
+        int L[3] = {0, 0, 0};
         if (net) {
             fwd_bind(c, mem, X, &f);
             cnn_forward(c, net, &f);
-            double yf, ye;
-            F = head_latency(c, f.z, 0, &yf);
-            E = head_latency(c, f.z, 1, &ye);
-            if (lg->pre_log) { lg->pre_log[2 * i] = yf; lg->pre_log[2 * i + 1] = ye; }
+            for (int t = 0; t < NL; t++) {
+                double y;
+                L[t] = head_latency(c, f.z, t, &y);
+                if (lg->pre_log) lg->pre_log[NL * i + t] = y;
+            }
         }
-        if (lg->replay) { F = lg->replay[2 * i]; E = lg->replay[2 * i + 1]; }
-        if (lg->lat_log) { lg->lat_log[2 * i] = (uint8_t)F; lg->lat_log[2 * i + 1] = (uint8_t)E; }
+        if (lg->replay)
+            for (int t = 0; t < NL; t++) L[t] = lg->replay[NL * i + t];
+        if (lg->lat_log)
+            for (int t = 0; t < NL; t++) lg->lat_log[NL * i + t] = (uint8_t)L[t];
+        const int F = L[0], E = L[1], S = L[2];
 
         tick += F;                                                   /* curTick += F */
-        lg->retired += retire(c, q, &len, tick, (int64_t)c->retire_width * F);
-        if (len == cap) {                                            /* full: drop the oldest */
-            memmove(q, q + 1, (size_t)(len - 1) * sizeof(qent_t));
-            len--;
+        lg->retired += retire_pq(c, q, &len, mq, &mlen, tick, (int64_t)c->retire_width * F);
+        if (c->store_queue) retire_mq(c, mq, &mlen, tick);
+        if (len + mlen == cap) {                                     /* full: drop the oldest */
+            if (mlen > 0) {
+                memmove(mq, mq + 1, (size_t)(mlen - 1) * sizeof(qent_t));
+                mlen--;
+            } else {
+                memmove(q, q + 1, (size_t)(len - 1) * sizeof(qent_t));
+                len--;
+            }
             lg->evictions++;
         }
         q[len].rec = rec[i];                                         /* enter with residence 0 */
         q[len].e = E;
+        q[len].s = S;
         q[len].fetch_tick = tick;
         len++;
         if (lg->tick_log) lg->tick_log[i] = tick;
         if (lg->len_log) lg->len_log[i] = len;
+        if (lg->mlen_log) lg->mlen_log[i] = mlen;
     }
-    while (len > 0) {                                                /* drain: Delta */
+    while (len + mlen > 0) {                                         /* drain: Delta */
         tick += 1;
-        lg->retired += retire(c, q, &len, tick, c->retire_width);
+        lg->retired += retire_pq(c, q, &len, mq, &mlen, tick, c->retire_width);
+        if (c->store_queue) retire_mq(c, mq, &mlen, tick);
     }
     free(q);
+    free(mq);
     free(X);
     free(mem);
     return tick;
@@ -367,7 +418,7 @@ int oracle_simulate(const oracle_cfg *c, const double *weights, const uint32_t *
                     const int64_t *offsets, int32_t n_sub, const int32_t *subset, int32_t n_subset,
                     const uint8_t *replay, int64_t *cycles_out, int64_t *evictions_out,
                     uint8_t *lat_log, double *pre_log, int64_t *tick_log, int32_t *len_log,
-                    double *feat_log, int32_t n_threads)
+                    int32_t *mlen_log, double *feat_log, int32_t n_threads)
 {
     if (!cfg_ok(c) || (!weights && !replay)) return -1;
     int32_t m = subset ? n_subset : n_sub;
@@ -386,11 +437,13 @@ int oracle_simulate(const oracle_cfg *c, const double *weights, const uint32_t *
         int64_t o = offsets[b], n = offsets[b + 1] - o;
         sublog_t lg;
         memset(&lg, 0, sizeof lg);
-        lg.replay = replay ? replay + 2 * o : NULL;
-        lg.lat_log = lat_log ? lat_log + 2 * o : NULL;
-        lg.pre_log = pre_log ? pre_log + 2 * o : NULL;
+        const int NL = n_lat(c);
+        lg.replay = replay ? replay + NL * o : NULL;
+        lg.lat_log = lat_log ? lat_log + NL * o : NULL;
+        lg.pre_log = pre_log ? pre_log + NL * o : NULL;
         lg.tick_log = tick_log ? tick_log + o : NULL;
         lg.len_log = len_log ? len_log + o : NULL;
+        lg.mlen_log = mlen_log ? mlen_log + o : NULL;
         lg.feat_log = feat_log ? feat_log + o * (int64_t)c->window * NF : NULL;
         cycles_out[s] = simulate_one(c, weights ? &net : NULL, records + o, n, &lg);
         if (evictions_out) evictions_out[s] = lg.evictions;
@@ -424,14 +477,14 @@ int oracle_cnn_forward(const oracle_cfg *c, const double *weights, const double 
     return 0;
 }
 
-/* The latency decision of the head on given FC2 outputs z [n][n_out]: lat [n][2]
- * (the integer latencies) and pre [n][2] (softplus of the regression output). */
+/* The latency decision of the head on given FC2 outputs z [n][n_out]: lat [n][n_lat]
+ * (the integer latencies) and pre [n][n_lat] (softplus of the regression output). */
 int oracle_head(const oracle_cfg *c, const double *z, int64_t n, uint8_t *lat, double *pre)
 {
     if (!cfg_ok(c)) return -1;
     for (int64_t i = 0; i < n; i++)
-        for (int t = 0; t < 2; t++)
-            lat[2 * i + t] = (uint8_t)head_latency(c, z + (int64_t)n_out(c) * i, t, &pre[2 * i + t]);
+        for (int t = 0; t < n_lat(c); t++)
+            lat[n_lat(c) * i + t] = (uint8_t)head_latency(c, z + (int64_t)n_out(c) * i, t, &pre[n_lat(c) * i + t]);
     return 0;
 }
 
@@ -458,15 +511,15 @@ int oracle_window_features(const oracle_cfg *c, const uint32_t *records, int64_t
         encode_static(&cur, X);
         int64_t now = i > 0 ? fetch[i - 1] : 0;
         for (int j = 1; j < W && i - j >= ctx_begin[i]; j++)
-            encode_context(&cur, records[i - j], now - fetch[i - j], e_label[i - j],
-                           X + (size_t)j * NF);
+            encode_context(&cur, records[i - j], now - fetch[i - j], e_label[i - j], 0,
+                           X + (size_t)j * NF);   /* the timing model has no write queue: S = 0 */
     }
     return 0;
 }
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */
 /*
- * Loss J = mean over the n*2 latencies of (softplus(z) - y)^2 with y the label
+ * Loss J = mean over the n*n_lat latencies (y [n][n_lat]) of (softplus(z) - y)^2 with y the label
  * clamped to [0, 255] (squared-error loss, Sec. 2.4).  Hybrid head: the same
  * mean over the latencies of the cross-entropy of the 10 class logits against
  * class min(y, 9) plus the squared error of softplus(regression output) (the
@@ -495,9 +548,10 @@ int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x
         fwd_t f;
         fwd_bind(c, mem, x + i * (int64_t)W * NF, &f);
         cnn_forward(c, &net, &f);
-        double dz[22];
-        for (int k = 0; k < 2; k++) {
-            double t = y[2 * i + k];
+        double dz[MAXOUT];
+        const int NL = n_lat(c);
+        for (int k = 0; k < NL; k++) {
+            double t = y[NL * i + k];
             t = t < 0 ? 0 : (t > 255 ? 255 : t);
             const int reg = c->hybrid ? 11 * k + 10 : k;   /* the regression output */
             double yhat = softplus(f.z[reg]);
@@ -505,7 +559,7 @@ int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x
             loss += r * r;
             /* d/dz softplus(z) = sigmoid(z), and 1 above the threshold */
             double ds = f.z[reg] > 20.0 ? 1.0 : sigmoid(f.z[reg]);
-            dz[reg] = 2.0 * r / (2.0 * (double)n) * ds;
+            dz[reg] = 2.0 * r / ((double)NL * (double)n) * ds;
             if (c->hybrid) {
                 /* cross-entropy: log-sum-exp of the logits minus the target class's */
                 const double *lg = f.z + 11 * k;
@@ -516,7 +570,7 @@ int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x
                 for (int j = 0; j < 10; j++) se += exp(lg[j] - mx);
                 loss += mx + log(se) - lg[cls];
                 for (int j = 0; j < 10; j++)
-                    dz[11 * k + j] = (exp(lg[j] - mx) / se - (j == cls ? 1.0 : 0.0)) / (2.0 * (double)n);
+                    dz[11 * k + j] = (exp(lg[j] - mx) / se - (j == cls ? 1.0 : 0.0)) / ((double)NL * (double)n);
             }
         }
         /* FC2 */
@@ -567,7 +621,7 @@ int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x
             da = dx;
         }
     }
-    *loss_out = loss / (2.0 * (double)n);
+    *loss_out = loss / ((double)n_lat(c) * (double)n);
     free(mem);
     free(dcur);
     free(dnext);

@@ -52,16 +52,22 @@ class Arch:
     execution); "hybrid" (Sec. 2.3's hybrid scheme): per latency 10 class
     logits (0..8 cycles and "more than 8") and one regression value, in the
     order [fetch classes 0-9, fetch value, execution classes 0-9, execution
-    value]."""
+    value].  ``store_queue``: a third latency, the store latency (Sec. 2.2),
+    after the other two, for the simulator's memory write queue (Sec. 3.2)."""
     window: int
     n_conv: int
     channels: int
     hidden: int
     head: str = "regression"
+    store_queue: bool = False
+
+    @property
+    def n_lat(self) -> int:
+        return 3 if self.store_queue else 2
 
     @property
     def n_out(self) -> int:
-        return 22 if self.head == "hybrid" else 2
+        return (11 if self.head == "hybrid" else 1) * self.n_lat
 
     @property
     def rows_out(self) -> int:
@@ -277,8 +283,8 @@ def unflatten_weights(arch: Arch, blob: np.ndarray) -> List[Tuple[str, np.ndarra
     return out
 
 
-FC2_GAIN = (8.0, 25.0)    # scale of the fetch / execution rows of FC2
-FC2_BIAS = (0.3, 12.0)    # FC2 bias (fetch, execution)
+FC2_GAIN = (8.0, 25.0, 25.0)    # scale of the fetch / execution / store rows of FC2
+FC2_BIAS = (0.3, 12.0, 20.0)    # FC2 bias (fetch, execution, store)
 
 
 # Hybrid head: class-logit rows are scaled by HYB_CLASS_GAIN and biased
@@ -289,12 +295,13 @@ FC2_BIAS = (0.3, 12.0)    # FC2 bias (fetch, execution)
 # classes and the regression output (11-15 cycles).
 HYB_CLASS_GAIN = 3.0
 HYB_CLASS_BIAS = ((1.5, 3.5, 2.5, 1.0, -0.5, -1.0, -1.5, -2.0, -2.5, -3.0),
-                  (-2.0, -0.5, 0.5, 1.0, 1.5, 1.5, 1.5, 1.5, 1.5, 2.5))
+                  (-2.0, -0.5, 0.5, 1.0, 1.5, 1.5, 1.5, 1.5, 1.5, 2.5),
+                  (-3.0, -2.0, -1.0, -0.5, 0.0, 0.0, 0.0, 0.5, 0.5, 3.0))   # store: mostly "more than 8"
 
 
 def workload_weights(w: Workload) -> np.ndarray:
     """FP64 master blob for a workload: He-normal from PCG64(seed), zero
-    biases, except that FC2's regression rows (fetch, execution) are scaled by
+    biases, except that FC2's regression rows (fetch, execution, store) are scaled by
     ``FC2_GAIN`` and biased by ``FC2_BIAS``.  Plain He-init gives near-constant
     outputs (every F = 1, E = 0, a queue of length one); this recipe gives the
     mixed trajectory a trained predictor would (F mostly 0-1, E spread over
@@ -305,15 +312,15 @@ def workload_weights(w: Workload) -> np.ndarray:
     w2 = ws[-2][1].copy()
     b2 = np.zeros(w.arch.n_out)
     if w.arch.head == "hybrid":
-        for t in range(2):
+        for t in range(w.arch.n_lat):
             w2[11 * t:11 * t + 10] *= HYB_CLASS_GAIN
             b2[11 * t:11 * t + 10] = HYB_CLASS_BIAS[t]
             w2[11 * t + 10] *= FC2_GAIN[t]
             b2[11 * t + 10] = FC2_BIAS[t]
     else:
-        w2[0] *= FC2_GAIN[0]
-        w2[1] *= FC2_GAIN[1]
-        b2[:] = FC2_BIAS
+        for t in range(w.arch.n_lat):
+            w2[t] *= FC2_GAIN[t]
+            b2[t] = FC2_BIAS[t]
     ws[-2] = ("fc2.weight", w2)
     ws[-1] = ("fc2.bias", b2)
     return flatten_weights(ws)
