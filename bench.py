@@ -134,11 +134,14 @@ def cpu_sample_ids(w, trace, blob, target_s=15.0):
 
 
 def workload_of(args) -> I.Workload:
-    """The named workload, with the hybrid latency head (Sec. 2.3) on request."""
+    """The named workload, with the hybrid latency head (Sec. 2.3) and the store
+    latency with the memory write queue (Sec. 3.2) on request."""
     w = I.WORKLOADS[args.workload]
-    if getattr(args, "head", "regression") == "hybrid":
+    head = getattr(args, "head", "regression")
+    store = bool(getattr(args, "store_queue", False))
+    if head != "regression" or store:
         a = w.arch
-        w = dataclasses.replace(w, arch=I.Arch(a.window, a.n_conv, a.channels, a.hidden, "hybrid"))
+        w = dataclasses.replace(w, arch=I.Arch(a.window, a.n_conv, a.channels, a.hidden, head, store))
     return w
 
 
@@ -177,7 +180,7 @@ def workload_config(w, args, note=""):
     c = {"workload": f"{w.name}: {w.description}", "n_subtraces": w.n_subtraces,
          "instructions_per_step": None, "window": w.arch.window, "n_conv": w.arch.n_conv,
          "channels": w.arch.channels, "fc_hidden": w.arch.hidden, "retire_width": w.retire_width,
-         "precision": args.precision, "head": w.arch.head,
+         "precision": args.precision, "head": w.arch.head, "store_queue": w.arch.store_queue,
          "l2": "flushed (512 MB write) before every timed step"}
     if note:
         c["note"] = note
@@ -273,7 +276,7 @@ def run_ours(args, rank, world):
         trace = truncate(trace, args.subtrace_len)
     blob32 = I.workload_weights(w).astype(np.float32)
     train_info = None
-    if args.workload == "c4" and not args.untrained:
+    if args.workload == "c4" and not args.untrained and not w.arch.store_queue:   # no store labels to train on
         blob32, train_info = train_predictor(w, args.train_steps)
     N, B = trace.n_instructions, trace.n_subtraces
 
@@ -570,6 +573,8 @@ def main():
                     help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
     ap.add_argument("--head", default="regression", choices=["regression", "hybrid"],
                     help="latency head: regression (2 FC2 outputs) or the hybrid classes + regression (22)")
+    ap.add_argument("--store-queue", action="store_true",
+                    help="store latency and memory write queue (three latencies per instruction)")
     ap.add_argument("--untrained", action="store_true", help="c4: keep the seeded weights")
     ap.add_argument("--train-steps", type=int, default=300, help="c4: training steps before simulating")
     ap.add_argument("--sweep", action="store_true",

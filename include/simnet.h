@@ -84,6 +84,17 @@ typedef enum {
                                           round(clamp(softplus(z[11t+10]), 0, 255)) for class 9
                                           ("more than 8").  Without it FC2 has 2 outputs and
                                           latency t is round(clamp(softplus(z[t]), 0, 255)). */
+#define SIMNET_FLAG_STORE_QUEUE 0x80u  /* store latency and memory write queue (Sec. 3.2): a third
+                                          latency S per instruction (FC2 outputs 3, or 33 with the
+                                          hybrid head, latency order F, E, S).  A store that retires
+                                          from the processor queue enters the write queue, which
+                                          retires in order, with no bandwidth limit, once a
+                                          residence reaches S.  The context is every instruction in
+                                          the simulator, newest first (processor queue, then write
+                                          queue), at most window-1; appending to a full simulator
+                                          evicts the oldest (the write queue's head first).  Context
+                                          rows of stores carry S/64 in feature 44.  lat_log,
+                                          pre_log and lat_replay hold 3 values per instruction. */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -195,12 +206,13 @@ simnet_status simnet_load_weights(simnet_ctx *ctx, const float *blob, int64_t n_
  * Simulate every sub-trace of `trace` to completion from an empty queue and
  * curTick = 0 (Sec. 3.2-3.3).
  *   cycles_out  device int64 [n_subtraces]: final curTick of each sub-trace.
- *   lat_log     device uint8 [n_instructions][2] or NULL: the integer (F, E)
- *               each instruction received.
- *   pre_log     device float [n_instructions][2] or NULL: softplus outputs
+ *   lat_log     device uint8 [n_instructions][n_lat] or NULL: the integer
+ *               latencies (F, E, and S with SIMNET_FLAG_STORE_QUEUE; n_lat = 2
+ *               or 3) each instruction received.
+ *   pre_log     device float [n_instructions][n_lat] or NULL: softplus outputs
  *               before clamping and rounding (NaN where `lat_replay` skipped
  *               nothing: always written when non-NULL).
- *   lat_replay  device uint8 [n_instructions][2] or NULL: teacher forcing; the
+ *   lat_replay  device uint8 [n_instructions][n_lat] or NULL: teacher forcing; the
  *               CNN still runs (and pre_log records it) but the clock and
  *               queue use these latencies.
  *   stats       host, or NULL.  When given the call synchronises `stream`.

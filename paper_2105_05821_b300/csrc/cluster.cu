@@ -589,13 +589,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     if (s_al[s] && r <= ql) {
                         const uint32_t cur = recb[s * 4 + (s_p[s] & 3)];
                         if (r == 0) {
-                            row_chunks_bf16(cur, cur, false, 0, 0u, ch);
+                            row_chunks_bf16(cur, cur, false, 0, 0u, 0u, ch);
                         } else {
                             int idx = s_qs[s] + ql - r;
                             if (idx >= cap) idx -= cap;
                             const uint64_t ent = qring[s * cap + idx];
-                            row_chunks_bf16(entry_rec(ent), cur, true, s_tick[s] - (int32_t)entry_tick(ent),
-                                            entry_e(ent), ch);
+                            row_chunks_bf16(entry_rec(ent), cur, true, entry_res(ent, s_tick[s]), entry_e(ent),
+                                            entry_s(ent), ch);
                         }
                     } else {
 #pragma unroll
@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         }
                     }
                     float yf, ye;
-                    uint32_t F = head_latency<NO>(z, 0, yf), E = head_latency<NO>(z, 1, ye);
+                    uint32_t F = head_latency<NO, 0>(z, yf), E = head_latency<NO, 1>(z, ye);
                     const int64_t gi = o + p;
                     if (As.replay) {
                         F = As.replay[2 * gi];
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             int idx = qs + k;
                             if (idx >= cap) idx -= cap;
                             const uint64_t v = qr[idx];
-                            const int32_t res = tick - (int32_t)entry_tick(v), e = (int32_t)entry_e(v);
+                            const int32_t res = entry_res(v, tick), e = (int32_t)entry_e(v);
                             if (strict ? res <= e : res < e) break;
                             k++;
                         }
@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     {
                         int idx = qs + ql;
                         if (idx >= cap) idx -= cap;
-                        qr[idx] = pack_entry(recb[s * 4 + (p & 3)], E, (uint32_t)tick);
+                        qr[idx] = pack_entry(recb[s * 4 + (p & 3)], E, 0u, (uint32_t)tick);
                     }
                     ql++;
                     p++;
@@ -935,10 +935,11 @@ static int cluster_size(const simnet_config &k, int B) {
 }
 
 // Shapes this kernel handles: BF16; 2 or 3 conv layers of 64 or 128 channels;
-// FC1 width 256 or 512; queue capacity below 256.
+// FC1 width 256 or 512; queue capacity below 256; no memory write queue.
 bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     const simnet_config &k = c->cfg;
     if (k.precision != SIMNET_BF16) { why = "not BF16"; return false; }
+    if (c->store_queue) { why = "memory write queue"; return false; }
     if (k.n_conv < 2 || k.n_conv > 3) { why = "conv depth"; return false; }
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
     if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }

@@ -17,13 +17,25 @@ constexpr int kOutHybrid = 22;          // FC2 outputs of the hybrid head: per l
 // Device status word values (written by kernels, read by the host after a call).
 enum : int32_t { kStatusOk = 0, kStatusTimeout = 1, kStatusBadTrace = 2 };
 
-// Ring entry of the processor queue: record (26 bits) | E (8 bits) << 26 | fetch tick (30 bits) << 34.
-__host__ __device__ __forceinline__ uint64_t pack_entry(uint32_t rec, uint32_t e, uint32_t tick) {
-    return (uint64_t)(rec & 0x3ffffffu) | ((uint64_t)(e & 0xffu) << 26) | ((uint64_t)tick << 34);
+// Ring entry of the processor queue and the memory write queue: record (26 bits)
+// | E (8 bits) << 26 | S (8 bits) << 34 | fetch tick mod 2^22 << 42.  A
+// residence never comes near 2^22 cycles (an entry is at most 255 cycles from
+// its fetch to its latency, and then leaves within cap / retire_width further
+// cycles of retire bandwidth and one more jump of at most 255), so
+// (curTick - stored tick) mod 2^22 is the residence exactly.
+constexpr uint32_t kTickMask = (1u << 22) - 1u;
+__host__ __device__ __forceinline__ uint64_t pack_entry(uint32_t rec, uint32_t e, uint32_t s, uint32_t tick) {
+    return (uint64_t)(rec & 0x3ffffffu) | ((uint64_t)(e & 0xffu) << 26) | ((uint64_t)(s & 0xffu) << 34) |
+           ((uint64_t)(tick & kTickMask) << 42);
 }
 __host__ __device__ __forceinline__ uint32_t entry_rec(uint64_t v) { return (uint32_t)(v & 0x3ffffffu); }
 __host__ __device__ __forceinline__ uint32_t entry_e(uint64_t v) { return (uint32_t)((v >> 26) & 0xffu); }
-__host__ __device__ __forceinline__ uint32_t entry_tick(uint64_t v) { return (uint32_t)(v >> 34); }
+__host__ __device__ __forceinline__ uint32_t entry_s(uint64_t v) { return (uint32_t)((v >> 34) & 0xffu); }
+// residence of an entry at curTick `tick`
+__host__ __device__ __forceinline__ int32_t entry_res(uint64_t v, int32_t tick) {
+    return (int32_t)(((uint32_t)tick - (uint32_t)(v >> 42)) & kTickMask);
+}
+__host__ __device__ __forceinline__ bool rec_is_store(uint32_t rec) { return (rec >> 21) & 1u; }
 
 // Everything a step's simulation kernels need; lives in device memory so that a
 // captured CUDA graph stays valid when the caller passes new trace buffers.
@@ -53,6 +65,12 @@ struct StepArgs {
     int32_t retire_width;
     int32_t strict;
     int32_t hidden;
+    // memory write queue (Sec. 3.2), with the store latency as a third latency;
+    // null when it is not modelled
+    int32_t *mstart;  // [B]
+    int32_t *mlen;    // [B]
+    uint64_t *mring;  // [B][cap]
+    int32_t n_lat;    // latencies per instruction: 2 (F, E) or 3 (F, E, S)
 };
 
 // A GEMM layer C[M, N] = act(A[M, K] * B[N, K]^T * scale + bias), M = n_active * m_mult.
@@ -69,13 +87,14 @@ struct GemmLayer {
 
 // ------------------------------------------------------------------ feature encoding (Sec. 2.2)
 // Channel c of a row.  `rec` is the row's instruction; for a context row (ctx)
-// `cur` is the instruction being predicted, `res` its residence and `e` its
-// execution latency.  Layout: 0-31 opcode one-hot; 32-34 src0/src1/dst / 32;
-// 35-37 load/store/branch; 38-40 cache-level one-hot; 41 mispredict;
-// 42 min(res,4095)/64; 43 E/64; 44 store latency (0); 45-47 rec.dst equals
+// `cur` is the instruction being predicted, `res` its residence, `e` its
+// execution and `s` its store latency.  Layout: 0-31 opcode one-hot; 32-34
+// src0/src1/dst / 32; 35-37 load/store/branch; 38-40 cache-level one-hot;
+// 41 mispredict; 42 min(res,4095)/64; 43 E/64; 44 S/64 for a store (0 without
+// the memory write queue, whose entries carry S = 0); 45-47 rec.dst equals
 // cur.src0/src1/dst; 48 both memory ops at one cache level; 49-63 zero.
 __device__ __forceinline__ float feature(int c, uint32_t rec, uint32_t cur, bool ctx, int32_t res,
-                                         uint32_t e) {
+                                         uint32_t e, uint32_t s) {
     if (c < 32) return (rec & 31u) == (uint32_t)c ? 1.f : 0.f;
     const uint32_t dst = (rec >> 15) & 31u;
     switch (c) {
@@ -89,6 +108,7 @@ __device__ __forceinline__ float feature(int c, uint32_t rec, uint32_t cur, bool
         case 41: return (float)((rec >> 25) & 1u);
         case 42: return ctx ? (float)min(res, 4095) * 0.015625f : 0.f;
         case 43: return ctx ? (float)e * 0.015625f : 0.f;
+        case 44: return (ctx && rec_is_store(rec)) ? (float)s * 0.015625f : 0.f;
         case 45: return (ctx && dst == ((cur >> 5) & 31u)) ? 1.f : 0.f;
         case 46: return (ctx && dst == ((cur >> 10) & 31u)) ? 1.f : 0.f;
         case 47: return (ctx && dst == ((cur >> 15) & 31u)) ? 1.f : 0.f;

@@ -33,7 +33,9 @@ struct TrainState {
 struct simnet_ctx {
     simnet_config cfg{};
     int cap = 0, rows_n = 0, fc1_in = 0, n_layers = 0;
-    int n_out = 2;   // FC2 outputs: 2 (regression head) or 22 (hybrid head)
+    int n_lat = 2;   // latencies per instruction: fetch, execution (and store, with the write queue)
+    bool hybrid = false, store_queue = false;
+    int n_out = 2;   // FC2 outputs: n_lat (regression head) or 11 * n_lat (hybrid head)
     int64_t n_weights = 0;
     std::string err;
     bool has_weights = false;
@@ -58,6 +60,8 @@ struct simnet_ctx {
     int32_t *tick = nullptr, *pos = nullptr, *qstart = nullptr, *qlen = nullptr, *evict = nullptr;
     int32_t *active = nullptr, *n_active = nullptr, *status = nullptr, *cnt = nullptr;
     uint64_t *ring = nullptr;
+    int32_t *mstart = nullptr, *mlen = nullptr;   // memory write queue (store-queue contexts)
+    uint64_t *mring = nullptr;
     unsigned long long *totals = nullptr;
     StepArgs *d_args = nullptr, *h_args = nullptr;
     int64_t *h_offsets = nullptr;

@@ -9,7 +9,7 @@ namespace simnet {
 
 // 128 x BN tile, BK = 8, 256 threads; each thread owns an 8 x (BN/16) block of C.
 // Shared tiles are stored K-major so the inner loop reads float4 runs of M and N.
-// NO > 0: instead of storing C, fold FC2 (w2 [NO][N]) into the epilogue and write
+// NO > 0: instead of storing C, fold FC2 (w2 [NO][N], NO in {2, 3, 22, 33}) into the epilogue and write
 // per-column-block partial dot products C_part[blockIdx.y][row][0..NO).
 template <int BN, int NO>
 __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A, const float *__restrict__ B,
@@ -156,10 +156,12 @@ static void launch_part_no(const float *A, const float *B, const float *bias, co
 void launch_gemm_f32_part(const float *A, const float *B, const float *bias, const float *w2, float *part,
                           int part_stride, const int32_t *n_active, int m_mult, int m_cap, int N, int K, int relu,
                           int n_out, cudaStream_t s, bool pdl) {
-    if (n_out == kOutHybrid)
-        launch_part_no<kOutHybrid>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl);
-    else
-        launch_part_no<2>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl);
+    switch (n_out) {
+        case 3: launch_part_no<3>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl); break;
+        case 22: launch_part_no<22>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl); break;
+        case 33: launch_part_no<33>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl); break;
+        default: launch_part_no<2>(A, B, bias, w2, part, part_stride, n_active, m_mult, m_cap, N, K, relu, s, pdl); break;
+    }
 }
 
 }  // namespace simnet

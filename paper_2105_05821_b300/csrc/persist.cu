@@ -496,9 +496,13 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         return false;
     }
     const size_t smem = (size_t)a.stages * a.stage_bytes + fixed;
-    const bool hyb = c->n_out == kOutHybrid;
-    auto k = fp8 ? (hyb ? persist_kernel<true, kOutHybrid> : persist_kernel<true, 2>)
-                 : (hyb ? persist_kernel<false, kOutHybrid> : persist_kernel<false, 2>);
+    void (*k)(PArgs) = nullptr;
+    switch (c->n_out) {
+        case 3: k = fp8 ? persist_kernel<true, 3> : persist_kernel<false, 3>; break;
+        case 22: k = fp8 ? persist_kernel<true, 22> : persist_kernel<false, 22>; break;
+        case 33: k = fp8 ? persist_kernel<true, 33> : persist_kernel<false, 33>; break;
+        default: k = fp8 ? persist_kernel<true, 2> : persist_kernel<false, 2>; break;
+    }
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, smem);

@@ -42,7 +42,7 @@ template <> __device__ __forceinline__ void store16<__nv_fp8_e4m3>(__nv_fp8_e4m3
 // ------------------------------------------------------------------ whole-row feature writer
 // Channels 32..63 of a row (the part after the opcode one-hot), as floats.
 __device__ __forceinline__ void row_tail(uint32_t rec, uint32_t cur, bool ctx, int32_t res, uint32_t e,
-                                         float (&t)[32]) {
+                                         uint32_t s, float (&t)[32]) {
 #pragma unroll
     for (int j = 0; j < 32; j++) t[j] = 0.f;
     const uint32_t dst = (rec >> 15) & 31u, lvl = (rec >> 23) & 3u;
@@ -59,6 +59,7 @@ __device__ __forceinline__ void row_tail(uint32_t rec, uint32_t cur, bool ctx, i
     if (ctx) {
         t[10] = (float)min(res, 4095) * 0.015625f;
         t[11] = (float)e * 0.015625f;
+        t[12] = rec_is_store(rec) ? (float)s * 0.015625f : 0.f;
         t[13] = dst == ((cur >> 5) & 31u) ? 1.f : 0.f;
         t[14] = dst == ((cur >> 10) & 31u) ? 1.f : 0.f;
         t[15] = dst == ((cur >> 15) & 31u) ? 1.f : 0.f;
@@ -69,11 +70,11 @@ __device__ __forceinline__ void row_tail(uint32_t rec, uint32_t cur, bool ctx, i
 
 // Write one whole 64-channel row (same values as `feature` channel by channel).
 template <typename T> __device__ __forceinline__ void write_row(T *dst, uint32_t rec, uint32_t cur, bool ctx,
-                                                               int32_t res, uint32_t e);
+                                                               int32_t res, uint32_t e, uint32_t s);
 
 // A BF16 row as its eight 16-byte chunks (channels 8j .. 8j+7 in chunk j).
 __device__ __forceinline__ void row_chunks_bf16(uint32_t rec, uint32_t cur, bool ctx, int32_t res, uint32_t e,
-                                                uint4 (&o)[8]) {
+                                                uint32_t s, uint4 (&o)[8]) {
     const uint32_t op = rec & 31u;
     uint32_t w[16];
 #pragma unroll
@@ -81,7 +82,7 @@ __device__ __forceinline__ void row_chunks_bf16(uint32_t rec, uint32_t cur, bool
 #pragma unroll
     for (int i = 0; i < 4; i++) o[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
     float t[32];
-    row_tail(rec, cur, ctx, res, e, t);
+    row_tail(rec, cur, ctx, res, e, s, t);
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         __nv_bfloat162 b = __floats2bfloat162_rn(t[2 * i], t[2 * i + 1]);
@@ -92,16 +93,16 @@ __device__ __forceinline__ void row_chunks_bf16(uint32_t rec, uint32_t cur, bool
 }
 
 template <> __device__ __forceinline__ void write_row<__nv_bfloat16>(__nv_bfloat16 *dst, uint32_t rec, uint32_t cur,
-                                                                     bool ctx, int32_t res, uint32_t e) {
+                                                                     bool ctx, int32_t res, uint32_t e, uint32_t s) {
     uint4 o[8];
-    row_chunks_bf16(rec, cur, ctx, res, e, o);
+    row_chunks_bf16(rec, cur, ctx, res, e, s, o);
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
     for (int i = 0; i < 8; i++) d4[i] = o[i];
 }
 
 template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4m3 *dst, uint32_t rec, uint32_t cur,
-                                                                     bool ctx, int32_t res, uint32_t e) {
+                                                                     bool ctx, int32_t res, uint32_t e, uint32_t s) {
     const uint32_t op = rec & 31u;
     uint32_t w[8];
 #pragma unroll
@@ -110,7 +111,7 @@ template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4
     d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
     d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
     float t[32];
-    row_tail(rec, cur, ctx, res, e, t);
+    row_tail(rec, cur, ctx, res, e, s, t);
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(t[4 * i], t[4 * i + 1]), __NV_SATFINITE, __NV_E4M3);
@@ -122,7 +123,7 @@ template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4
 }
 
 template <> __device__ __forceinline__ void write_row<float>(float *dst, uint32_t rec, uint32_t cur, bool ctx,
-                                                             int32_t res, uint32_t e) {
+                                                             int32_t res, uint32_t e, uint32_t s) {
     const uint32_t op = rec & 31u;
     float4 *d4 = reinterpret_cast<float4 *>(dst);
 #pragma unroll
@@ -133,7 +134,7 @@ template <> __device__ __forceinline__ void write_row<float>(float *dst, uint32_
         d4[i] = make_float4(v[0], v[1], v[2], v[3]);
     }
     float t[32];
-    row_tail(rec, cur, ctx, res, e, t);
+    row_tail(rec, cur, ctx, res, e, s, t);
 #pragma unroll
     for (int i = 0; i < 8; i++) d4[8 + i] = make_float4(t[4 * i], t[4 * i + 1], t[4 * i + 2], t[4 * i + 3]);
 }
@@ -159,21 +160,26 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Latency t (0 fetch, 1 execution) from the FC2 outputs z[0..NO) (bias
+// FC2 outputs per window: a regression head has one per latency (2, or 3 with
+// the store latency); a hybrid head has eleven per latency (22 or 33).
+template <int NO> constexpr bool out_hybrid() { return NO % 11 == 0; }
+template <int NO> constexpr int out_lat() { return out_hybrid<NO>() ? NO / 11 : NO; }
+
+// Latency T (0 fetch, 1 execution, 2 store) from the FC2 outputs z[0..NO) (bias
 // included); `pre` receives the softplus value before clamping and rounding.
-// NO = 2, regression head: round(clamp(softplus(z[t]))).  NO = 22, hybrid head
-// (Sec. 2.3): the class k with the largest of the ten logits z[11t..11t+9],
-// compared in FP32 with the lowest index winning ties; classes 0..8 are the
-// latency itself, class 9 ("more than 8") takes the regression output z[11t+10].
-template <int NO>
-__device__ __forceinline__ uint32_t head_latency(const float (&z)[NO], int t, float &pre) {
-    if constexpr (NO == 2) {
-        pre = softplus_f(t ? z[1] : z[0]);
+// Regression head: round(clamp(softplus(z[T]))).  Hybrid head (Sec. 2.3): the
+// class k with the largest of the ten logits z[11T..11T+9], compared in FP32
+// with the lowest index winning ties; classes 0..8 are the latency itself,
+// class 9 ("more than 8") takes the regression output z[11T+10].
+template <int NO, int T>
+__device__ __forceinline__ uint32_t head_latency(const float (&z)[NO], float &pre) {
+    if constexpr (!out_hybrid<NO>()) {
+        pre = softplus_f(z[T]);
         return to_cycles(pre);
     } else {
         float lg[11];
 #pragma unroll
-        for (int j = 0; j < 11; j++) lg[j] = t ? z[11 + j] : z[j];
+        for (int j = 0; j < 11; j++) lg[j] = z[11 * T + j];
         float best = lg[0];
         int k = 0;
 #pragma unroll
@@ -199,19 +205,28 @@ __device__ __forceinline__ void head_sum_warp(const float *__restrict__ part, in
         z[0] = warp_sum(zf) + b2[0];
         z[1] = warp_sum(ze) + b2[1];
     } else {
-        // lane o < NO adds output o over the partials, then every lane gets all NO
-        float acc = 0.f;
-        if (lane < NO) {
-            acc = b2[lane];
-            for (int i = 0; i < P; i++) acc += part[((size_t)i * part_stride + slot) * NO + lane];
+        // lane l adds outputs l and l + 32 over the partials, then every lane gets all NO
+        constexpr int NA = (NO + 31) / 32;
+        float acc[NA];
+#pragma unroll
+        for (int a = 0; a < NA; a++) {
+            const int o = a * 32 + lane;
+            acc[a] = 0.f;
+            if (o < NO) {
+                acc[a] = b2[o];
+                for (int i = 0; i < P; i++) acc[a] += part[((size_t)i * part_stride + slot) * NO + o];
+            }
         }
 #pragma unroll
-        for (int o = 0; o < NO; o++) z[o] = __shfl_sync(0xffffffffu, acc, o);
+        for (int o = 0; o < NO; o++) z[o] = __shfl_sync(0xffffffffu, acc[o / 32], o % 32);
     }
 }
 
 // Length of the run of ready entries from the oldest, at most `lim`; in-order
-// retire means the first not-ready entry stops it.  Whole warp participates.
+// retire means the first not-ready entry stops it.  Ready: residence reaches E
+// (processor queue) or, with STORE_LAT, S (memory write queue).  Whole warp
+// participates.
+template <bool STORE_LAT = false>
 __device__ __forceinline__ int retire_run(const uint64_t *__restrict__ ring, int cap, int qs, int lim,
                                           int32_t tick, int strict, int lane) {
     int k = 0;
@@ -222,8 +237,8 @@ __device__ __forceinline__ int retire_run(const uint64_t *__restrict__ ring, int
             int idx = qs + i;
             if (idx >= cap) idx -= cap;
             const uint64_t v = ring[idx];
-            const int32_t res = tick - (int32_t)entry_tick(v);
-            const int32_t e = (int32_t)entry_e(v);
+            const int32_t res = entry_res(v, tick);
+            const int32_t e = (int32_t)(STORE_LAT ? entry_s(v) : entry_e(v));
             rd = strict ? (res > e) : (res >= e);
         }
         const unsigned m = __ballot_sync(0xffffffffu, rd);
@@ -232,6 +247,26 @@ __device__ __forceinline__ int retire_run(const uint64_t *__restrict__ ring, int
         if (run < 32) break;
     }
     return min(k, lim);
+}
+
+// Context of sub-trace b: every instruction still in the simulator, newest
+// first: the processor queue, then the memory write queue (whose stores all
+// retired from the processor queue, so they are older).
+__device__ __forceinline__ int ctx_len(const StepArgs *__restrict__ A, int b) {
+    return A->qlen[b] + (A->mlen ? A->mlen[b] : 0);
+}
+// Entry of context row r (1 <= r <= ctx_len).
+__device__ __forceinline__ uint64_t ctx_entry(const StepArgs *__restrict__ A, int b, int r) {
+    const int cap = A->cap, ql = A->qlen[b];
+    if (r <= ql) {
+        int idx = A->qstart[b] + ql - r;
+        if (idx >= cap) idx -= cap;
+        return A->ring[(size_t)b * cap + idx];
+    }
+    const int ml = A->mlen[b];
+    int idx = A->mstart[b] + ml - (r - ql);
+    if (idx >= cap) idx -= cap;
+    return A->mring[(size_t)b * cap + idx];
 }
 
 // One element of the context gather: thread `gid` of (slot, row, 16-byte chunk).
@@ -256,16 +291,13 @@ __device__ __forceinline__ void gather_elem(const StepArgs *__restrict__ A, T *_
             const uint32_t cur = A->records[o + p];
             if (r == 0) {
 #pragma unroll
-                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, cur, cur, false, 0, 0);
-            } else if (r <= A->qlen[b]) {
-                const int cap = A->cap;
-                int idx = A->qstart[b] + A->qlen[b] - r;
-                if (idx >= cap) idx -= cap;
-                const uint64_t ent = A->ring[(size_t)b * cap + idx];
-                const int32_t res = A->tick[b] - (int32_t)entry_tick(ent);
-                const uint32_t rec = entry_rec(ent), e = entry_e(ent);
+                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, cur, cur, false, 0, 0, 0);
+            } else if (r <= ctx_len(A, b)) {
+                const uint64_t ent = ctx_entry(A, b, r);
+                const int32_t res = entry_res(ent, A->tick[b]);
+                const uint32_t rec = entry_rec(ent), e = entry_e(ent), sl = entry_s(ent);
 #pragma unroll
-                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, rec, cur, true, res, e);
+                for (int j = 0; j < V; j++) v[j] = feature(chunk * V + j, rec, cur, true, res, e, sl);
             }
         }
     }
@@ -306,15 +338,12 @@ __device__ __forceinline__ void gather_row_into(const StepArgs *__restrict__ A, 
         if (p < n) {
             const uint32_t cur = A->records[o + p];
             if (r == 0) {
-                write_row<T>(dst, cur, cur, false, 0, 0);
+                write_row<T>(dst, cur, cur, false, 0, 0, 0);
                 return;
             }
-            if (r <= A->qlen[b]) {
-                const int cap = A->cap;
-                int idx = A->qstart[b] + A->qlen[b] - r;
-                if (idx >= cap) idx -= cap;
-                const uint64_t ent = A->ring[(size_t)b * cap + idx];
-                write_row<T>(dst, entry_rec(ent), cur, true, A->tick[b] - (int32_t)entry_tick(ent), entry_e(ent));
+            if (r <= ctx_len(A, b)) {
+                const uint64_t ent = ctx_entry(A, b, r);
+                write_row<T>(dst, entry_rec(ent), cur, true, entry_res(ent, A->tick[b]), entry_e(ent), entry_s(ent));
                 return;
             }
         }
@@ -373,7 +402,7 @@ __device__ __forceinline__ void gather_rows_warp_pm(const StepArgs *__restrict__
         const int slot = (int)(id / W);
         if (id % W == 0 && slot < *A->n_active) {
             const int b = A->active[slot];
-            if (A->pos[b] < (int)(A->offsets[b + 1] - A->offsets[b])) atomicMax(ext, A->qlen[b] + 1);
+            if (A->pos[b] < (int)(A->offsets[b + 1] - A->offsets[b])) atomicMax(ext, ctx_len(A, b) + 1);
         }
     }
     __syncwarp();
@@ -381,95 +410,165 @@ __device__ __forceinline__ void gather_rows_warp_pm(const StepArgs *__restrict__
     __syncwarp();
 }
 
+// Move the stores among the k entries at the processor queue's head (ring,
+// start qs) to the memory write queue's tail (mring, start ms, length ml), in
+// order; non-stores leave.  Whole warp participates; returns the new ml.
+__device__ __forceinline__ int stores_to_write_queue(const uint64_t *__restrict__ ring, int qs, int k,
+                                                     uint64_t *__restrict__ mring, int ms, int ml, int cap,
+                                                     int lane) {
+    for (int i0 = 0; i0 < k; i0 += 32) {
+        const int i = i0 + lane;
+        uint64_t v = 0;
+        bool st = false;
+        if (i < k) {
+            int idx = qs + i;
+            if (idx >= cap) idx -= cap;
+            v = ring[idx];
+            st = rec_is_store(entry_rec(v));
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, st);
+        if (st) {
+            int idx = ms + ml + __popc(m & ((1u << lane) - 1u));
+            if (idx >= cap) idx -= cap;
+            mring[idx] = v;
+        }
+        ml += __popc(m);
+    }
+    __syncwarp();
+    return ml;
+}
+
 // One warp, one active slot.  FC2 arrives as P partial dot products per output
 // (one per FC1 column block) which are summed with the bias; the latencies
 // follow by head_latency (softplus, clamp, round; or the hybrid class rule);
 // then curTick += F, retire (budget RW*F), evict at capacity, append with
 // residence 0; after the last instruction, drain one cycle at a time (budget
-// RW) and write the sub-trace's cycle count.  Otherwise the warp writes the
-// slot's feature rows for the next step (the gather, fused here); `sq` is this
-// warp's shared-memory scratch of 256 queue entries.
+// RW) and write the sub-trace's cycle count.  With the store latency (NO = 3
+// or 33) retired stores move to the memory write queue, which retires in order
+// with no bandwidth limit once a residence reaches S; both queues together hold
+// at most cap entries and a full simulator evicts its oldest instruction (the
+// write queue's head first).  Otherwise the warp writes the slot's feature
+// rows for the next step (the gather, fused here); `sq` is this warp's
+// shared-memory scratch of 256 queue entries.
 // With `pm_slots` > 0 the feature tile is pair-major over that many slots:
-// only rows 0 .. max(old, new queue length) are written (rows past a queue are
-// kept zero) and the next step's batch extent `ext` is raised to the new queue
-// length + 1.
+// only rows 0 .. max(old, new context length) are written (rows past the
+// context are kept zero) and the next step's batch extent `ext` is raised to
+// the new context length + 1.
 template <typename T, int NO = 2>
 __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A, int slot, int lane,
                                                  const float *__restrict__ part, int P, int part_stride,
                                                  const float *__restrict__ b2, T *__restrict__ X,
                                                  uint64_t *__restrict__ sq, uint8_t *__restrict__ stg,
                                                  int pm_slots = 0, int *ext = nullptr) {
+    constexpr int NL = out_lat<NO>();
+    constexpr bool SQ = NL == 3;
     const int b = A->active[slot];
     const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
     int p = A->pos[b];
     if (p >= n) return;
     float z[NO];
     head_sum_warp<NO>(part, P, part_stride, slot, b2, lane, z);
-    float yf, ye;
-    uint32_t F = head_latency<NO>(z, 0, yf), E = head_latency<NO>(z, 1, ye);
+    float pre[3];
+    uint32_t lat[3];
+    lat[0] = head_latency<NO, 0>(z, pre[0]);
+    lat[1] = head_latency<NO, 1>(z, pre[1]);
+    pre[2] = 0.f;
+    lat[2] = 0;
+    if constexpr (SQ) lat[2] = head_latency<NO, 2>(z, pre[2]);
     const int64_t gi = o + p;
-    if (A->replay) {
-        F = A->replay[2 * gi];
-        E = A->replay[2 * gi + 1];
-    }
+    if (A->replay)
+#pragma unroll
+        for (int t = 0; t < NL; t++) lat[t] = A->replay[NL * gi + t];
     if (lane == 0) {
-        if (A->pre_log) { A->pre_log[2 * gi] = yf; A->pre_log[2 * gi + 1] = ye; }
-        if (A->lat_log) { A->lat_log[2 * gi] = (uint8_t)F; A->lat_log[2 * gi + 1] = (uint8_t)E; }
+#pragma unroll
+        for (int t = 0; t < NL; t++) {
+            if (A->pre_log) A->pre_log[NL * gi + t] = pre[t];
+            if (A->lat_log) A->lat_log[NL * gi + t] = (uint8_t)lat[t];
+        }
     }
+    const uint32_t F = lat[0], E = lat[1], S = lat[2];
     const int cap = A->cap, RW = A->retire_width, strict = A->strict;
     uint64_t *ring = A->ring + (size_t)b * cap;
+    uint64_t *mring = SQ ? A->mring + (size_t)b * cap : nullptr;
     int qs = A->qstart[b], ql = A->qlen[b], ev = 0;
-    const int ql_old = ql;
+    int ms = 0, ml = 0;
+    if constexpr (SQ) {
+        ms = A->mstart[b];
+        ml = A->mlen[b];
+    }
+    const int ctx_old = ql + ml;
     int32_t tick = A->tick[b] + (int32_t)F;
-    const int k = retire_run(ring, cap, qs, min(ql, RW * (int)F), tick, strict, lane);
-    qs += k;
-    if (qs >= cap) qs -= cap;
-    ql -= k;
-    if (ql == cap) {  // full: drop the oldest
-        qs = (qs + 1 == cap) ? 0 : qs + 1;
-        ql--;
+    // processor queue, then (stores) the memory write queue
+    auto retire_both = [&](int budget) {
+        const int k = retire_run(ring, cap, qs, min(ql, budget), tick, strict, lane);
+        if constexpr (SQ) ml = stores_to_write_queue(ring, qs, k, mring, ms, ml, cap, lane);
+        qs += k;
+        if (qs >= cap) qs -= cap;
+        ql -= k;
+        if constexpr (SQ) {
+            const int km = retire_run<true>(mring, cap, ms, ml, tick, strict, lane);
+            ms += km;
+            if (ms >= cap) ms -= cap;
+            ml -= km;
+        }
+    };
+    retire_both(RW * (int)F);
+    if (ql + ml == cap) {  // full: drop the oldest instruction
+        if (ml > 0) {
+            ms = (ms + 1 == cap) ? 0 : ms + 1;
+            ml--;
+        } else {
+            qs = (qs + 1 == cap) ? 0 : qs + 1;
+            ql--;
+        }
         ev = 1;
     }
     if (lane == 0) {
         int idx = qs + ql;
         if (idx >= cap) idx -= cap;
-        ring[idx] = pack_entry(A->records[gi], E, (uint32_t)tick);
+        ring[idx] = pack_entry(A->records[gi], E, S, (uint32_t)tick);
     }
     ql++;
     p++;
     __syncwarp();
     if (p == n) {  // drain: Delta of Eq. 1
-        while (ql > 0) {
+        while (ql + ml > 0) {
             tick += 1;
-            const int kk = retire_run(ring, cap, qs, min(ql, RW), tick, strict, lane);
-            qs += kk;
-            if (qs >= cap) qs -= cap;
-            ql -= kk;
+            retire_both(RW);
         }
         if (lane == 0) A->cycles_out[b] = tick;
     } else if (X) {
-        // next step's input rows of this slot: row 0 = instruction p, row r = r-th newest entry.
-        // The queue is copied newest-first into shared memory with independent loads first.
-        for (int r = lane + 1; r <= ql; r += 32) {
-            int idx = qs + ql - r;
-            if (idx >= cap) idx -= cap;
-            sq[r] = ring[idx];
+        // next step's input rows of this slot: row 0 = instruction p, row r = r-th newest
+        // context entry.  The context is copied newest-first into shared memory with
+        // independent loads first.
+        for (int r = lane + 1; r <= ql + ml; r += 32) {
+            int idx;
+            if (r <= ql) {
+                idx = qs + ql - r;
+                if (idx >= cap) idx -= cap;
+                sq[r] = ring[idx];
+            } else {
+                idx = ms + ml - (r - ql);
+                if (idx >= cap) idx -= cap;
+                sq[r] = mring[idx];
+            }
         }
         __syncwarp();
         const int W = A->window;
         const uint32_t cur = A->records[o + p];
         constexpr int SR = stage_row_bytes<T>();
-        const int rows = pm_slots > 0 ? min(W, max(ql_old, ql) + 1) : W;
-        if (pm_slots > 0 && lane == 0) atomicMax(ext, ql + 1);
+        const int ctx_new = ql + ml;
+        const int rows = pm_slots > 0 ? min(W, max(ctx_old, ctx_new) + 1) : W;
+        if (pm_slots > 0 && lane == 0) atomicMax(ext, ctx_new + 1);
         for (int r0 = 0; r0 < rows; r0 += 32) {   // a lane builds a row, the warp stores rows whole
             const int r = r0 + lane;
             T *row = reinterpret_cast<T *>(stg + lane * SR);
             if (r < rows) {
                 if (r == 0) {
-                    write_row<T>(row, cur, cur, false, 0, 0);
-                } else if (r <= ql) {
+                    write_row<T>(row, cur, cur, false, 0, 0, 0);
+                } else if (r <= ctx_new) {
                     const uint64_t ent = sq[r];
-                    write_row<T>(row, entry_rec(ent), cur, true, tick - (int32_t)entry_tick(ent), entry_e(ent));
+                    write_row<T>(row, entry_rec(ent), cur, true, entry_res(ent, tick), entry_e(ent), entry_s(ent));
                 } else {
                     zero_row_bytes(row, kNFP * (int)sizeof(T));
                 }
@@ -488,6 +587,10 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
         A->qstart[b] = qs;
         A->qlen[b] = ql;
         A->evict[b] += ev;
+        if constexpr (SQ) {
+            A->mstart[b] = ms;
+            A->mlen[b] = ml;
+        }
     }
 }
 

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) head_part_z_kernel(const float *__restric
     head_sum_warp<NO>(part, P, part_stride, row, b2, lane, zr);
 #pragma unroll
     for (int o = 0; o < NO; o++)
-        if (lane == (o & 31)) z[(size_t)row * NO + o] = zr[o];
+        if (lane == o % 32) z[(size_t)row * NO + o] = zr[o];
 }
 
 // FC2 only (pre-softplus outputs, w2 [n_out][H]) for the CNN-only entry points:
@@ -102,6 +102,10 @@ __global__ void init_state_kernel(const StepArgs *__restrict__ A) {
     A->pos[b] = 0;
     A->qstart[b] = 0;
     A->qlen[b] = 0;
+    if (A->mlen) {
+        A->mstart[b] = 0;
+        A->mlen[b] = 0;
+    }
     A->evict[b] = 0;
     A->active[b] = b;
     A->cycles_out[b] = 0;
@@ -181,10 +185,12 @@ static void launch_head_update_no(const StepArgs *A, const float *part, int P, i
 template <typename T>
 void launch_head_update(const StepArgs *A, const float *part, int P, int part_stride, const float *b2, T *X,
                         int n_slots, int n_out, cudaStream_t s, bool pdl) {
-    if (n_out == kOutHybrid)
-        launch_head_update_no<T, kOutHybrid>(A, part, P, part_stride, b2, X, n_slots, s, pdl);
-    else
-        launch_head_update_no<T, 2>(A, part, P, part_stride, b2, X, n_slots, s, pdl);
+    switch (n_out) {
+        case 3: launch_head_update_no<T, 3>(A, part, P, part_stride, b2, X, n_slots, s, pdl); break;
+        case 22: launch_head_update_no<T, 22>(A, part, P, part_stride, b2, X, n_slots, s, pdl); break;
+        case 33: launch_head_update_no<T, 33>(A, part, P, part_stride, b2, X, n_slots, s, pdl); break;
+        default: launch_head_update_no<T, 2>(A, part, P, part_stride, b2, X, n_slots, s, pdl); break;
+    }
 }
 template void launch_head_update<float>(const StepArgs *, const float *, int, int, const float *, float *, int, int,
                                         cudaStream_t, bool);
@@ -204,10 +210,12 @@ void launch_head_part_z(const float *part, int P, int part_stride, const float *
     const int64_t threads = (int64_t)n * 32;
     if (n <= 0) return;
     const unsigned g = (unsigned)((threads + 255) / 256);
-    if (n_out == kOutHybrid)
-        head_part_z_kernel<kOutHybrid><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n);
-    else
-        head_part_z_kernel<2><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n);
+    switch (n_out) {
+        case 3: head_part_z_kernel<3><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n); break;
+        case 22: head_part_z_kernel<22><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n); break;
+        case 33: head_part_z_kernel<33><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n); break;
+        default: head_part_z_kernel<2><<<g, 256, 0, s>>>(part, P, part_stride, b2, z, n); break;
+    }
 }
 
 void launch_init_state(const StepArgs *A, int n_sub, cudaStream_t s) {

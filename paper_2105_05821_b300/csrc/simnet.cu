@@ -67,7 +67,10 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
     c->rows_n = k.window >> k.n_conv;
     c->fc1_in = c->rows_n * k.conv_channels;
     c->n_layers = k.n_conv + 1;
-    c->n_out = (k.flags & SIMNET_FLAG_HYBRID_HEAD) ? kOutHybrid : 2;
+    c->hybrid = (k.flags & SIMNET_FLAG_HYBRID_HEAD) != 0;
+    c->store_queue = (k.flags & SIMNET_FLAG_STORE_QUEUE) != 0;
+    c->n_lat = c->store_queue ? 3 : 2;
+    c->n_out = (c->hybrid ? 11 : 1) * c->n_lat;
     int64_t n = 0, cin = kNF;
     for (int l = 0; l < k.n_conv; l++) {
         n += (int64_t)k.conv_channels * cin * 2 + k.conv_channels;
@@ -94,13 +97,16 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
 
 static void free_workspace(simnet_ctx *c) {
     void *bufs[] = {c->X, c->act[0], c->act[1], c->h1, c->tick, c->pos, c->qstart, c->qlen, c->evict,
-                    c->active, c->n_active, c->status, c->cnt, c->ring, c->totals, c->d_args, c->cyc};
+                    c->active, c->n_active, c->status, c->cnt, c->ring, c->totals, c->d_args, c->cyc,
+                    c->mstart, c->mlen, c->mring};
     for (void *p : bufs)
         if (p) cudaFree(p);
     c->X = c->act[0] = c->act[1] = nullptr;
     c->h1 = nullptr;
     c->tick = c->pos = c->qstart = c->qlen = c->evict = c->active = c->n_active = c->status = c->cnt = nullptr;
     c->ring = nullptr;
+    c->mstart = c->mlen = nullptr;
+    c->mring = nullptr;
     c->cyc = nullptr;
     c->totals = nullptr;
     c->d_args = nullptr;
@@ -469,6 +475,11 @@ simnet_status ensure_workspace(simnet_ctx *c, int B) {
     CK(cudaMalloc(&c->status, 4));
     CK(cudaMalloc(&c->cnt, 4));
     CK(cudaMalloc(&c->ring, (size_t)B * c->cap * sizeof(uint64_t)));
+    if (c->store_queue) {
+        CK(cudaMalloc(&c->mstart, (size_t)B * 4));
+        CK(cudaMalloc(&c->mlen, (size_t)B * 4));
+        CK(cudaMalloc(&c->mring, (size_t)B * c->cap * sizeof(uint64_t)));
+    }
     CK(cudaMalloc(&c->cyc, (size_t)B * sizeof(int64_t)));
     CK(cudaMalloc(&c->totals, 2 * sizeof(unsigned long long)));
     CK(cudaMalloc(&c->d_args, sizeof(StepArgs)));
@@ -578,7 +589,10 @@ static simnet_status prepare_plans(simnet_ctx *c, int B, bool pdl) {
         const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
         void *out = last ? (void *)c->h1 : c->act[l & 1];
         std::string why;
-        const int ok_kind = !last ? TC_OUT_ACT : c->n_out == kOutHybrid ? TC_OUT_PART_HYBRID : TC_OUT_PART;
+        const int ok_kind = !last ? TC_OUT_ACT
+                            : c->n_out == 3 ? TC_OUT_PART3
+                            : c->n_out == 22 ? TC_OUT_PART_HYBRID
+                            : c->n_out == 33 ? TC_OUT_PART33 : TC_OUT_PART;
         if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, ok_kind, B * g.m_mult,
                           c->cfg.spin_limit_ns, c->status, pdl, why))
             return fail(c, SIMNET_ECUDA, "tensor-core plan for layer %d: %s", l, why.c_str());
@@ -689,6 +703,10 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
     a.retire_width = c->cfg.retire_width;
     a.strict = (c->cfg.flags & SIMNET_FLAG_RETIRE_STRICT) ? 1 : 0;
     a.hidden = c->cfg.fc_hidden;
+    a.mstart = c->mstart;
+    a.mlen = c->mlen;
+    a.mring = c->mring;
+    a.n_lat = c->n_lat;
     CK(cudaEventRecord(c->ev0, s));
     CK(cudaMemcpyAsync(c->d_args, c->h_args, sizeof(StepArgs), cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(c->args_ev, s));

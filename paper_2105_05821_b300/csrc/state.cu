@@ -14,14 +14,14 @@
 namespace {
 
 constexpr char kMagic[8] = {'S', 'I', 'M', 'N', 'E', 'T', 'S', '1'};
-constexpr int32_t kVersion = 1;
+constexpr int32_t kVersion = 2;   // 2: ring entries carry S and a 22-bit fetch tick
 
 struct StateHeader {
     char magic[8];
     int32_t version, kind;
     int32_t window, n_conv, conv_channels, fc_hidden;
     int32_t retire_width, strict, precision, n_sub;
-    int32_t cap, head;   // head: 0 regression FC2 (2 outputs), 1 hybrid (22)
+    int32_t cap, head;   // head: bit 0 hybrid FC2, bit 1 store latency + memory write queue
     int64_t steps_done, max_len, n_instructions;
     uint64_t trace_fp, weights_fp;
     int64_t payload_bytes;
@@ -29,9 +29,10 @@ struct StateHeader {
 static_assert(sizeof(StateHeader) == 104, "state header layout");
 
 // SIM payload: tick, pos, qstart, qlen, evict, active (int32 [B] each),
-// n_active (int64), finished cycles (int64 [B]), ring (uint64 [B][cap]).
-size_t sim_payload(int B, int cap) {
-    return (size_t)B * 6 * 4 + 8 + (size_t)B * 8 + (size_t)B * cap * 8;
+// n_active (int64), finished cycles (int64 [B]), ring (uint64 [B][cap]); with
+// the memory write queue then mstart, mlen (int32 [B]) and its ring (uint64 [B][cap]).
+size_t sim_payload(int B, int cap, bool sq) {
+    return (size_t)B * 6 * 4 + 8 + (size_t)B * 8 + (size_t)B * cap * 8 + (sq ? (size_t)B * 8 + (size_t)B * cap * 8 : 0);
 }
 
 // TRAIN payload: canonical FP32 weights [n_weights], step (int64), then per
@@ -56,7 +57,7 @@ void fill_header(const simnet_ctx *c, int kind, StateHeader &h) {
     h.strict = (c->cfg.flags & SIMNET_FLAG_RETIRE_STRICT) ? 1 : 0;
     h.precision = c->cfg.precision;
     h.cap = c->cap;
-    h.head = c->n_out == 22 ? 1 : 0;
+    h.head = (c->hybrid ? 1 : 0) | (c->store_queue ? 2 : 0);
 }
 
 }  // namespace
@@ -68,7 +69,7 @@ extern "C" simnet_status simnet_state_save(simnet_ctx *c, int32_t kind, void *ho
         return fail(c, SIMNET_EINVAL, "state_save: bad kind or NULL size");
     if (kind == SIMNET_STATE_SIM && !c->sim_valid) return fail(c, SIMNET_ESTATE, "state_save: no simulation state");
     if (kind == SIMNET_STATE_TRAIN && !c->has_weights) return fail(c, SIMNET_ESTATE, "state_save: no weights loaded");
-    const size_t payload = kind == SIMNET_STATE_SIM ? sim_payload(c->sim_B, c->cap) : train_payload(c);
+    const size_t payload = kind == SIMNET_STATE_SIM ? sim_payload(c->sim_B, c->cap, c->store_queue) : train_payload(c);
     const size_t need = sizeof(StateHeader) + payload;
     if (!host_buf) {
         *bytes = need;
@@ -104,6 +105,11 @@ extern "C" simnet_status simnet_state_save(simnet_ctx *c, int32_t kind, void *ho
         off += 8;
         CK(get(c->cyc, (size_t)B * 8));
         CK(get(c->ring, (size_t)B * c->cap * 8));
+        if (c->store_queue) {
+            CK(get(c->mstart, (size_t)B * 4));
+            CK(get(c->mlen, (size_t)B * 4));
+            CK(get(c->mring, (size_t)B * c->cap * 8));
+        }
     } else {
         h.weights_fp = weights_fingerprint(c);
         simnet_status st = simnet_get_weights(c, (float *)(out + off));
@@ -154,8 +160,9 @@ extern "C" simnet_status simnet_state_load(simnet_ctx *c, int32_t kind, const vo
     fill_header(c, kind, mine);
     if (h.window != mine.window || h.n_conv != mine.n_conv || h.conv_channels != mine.conv_channels ||
         h.fc_hidden != mine.fc_hidden || h.head != mine.head)
-        return fail(c, SIMNET_EINVAL, "state_load: state of another CNN shape (W=%d, %d x conv%d, FC%d, %s head)",
-                    h.window, h.n_conv, h.conv_channels, h.fc_hidden, h.head ? "hybrid" : "regression");
+        return fail(c, SIMNET_EINVAL, "state_load: state of another CNN shape (W=%d, %d x conv%d, FC%d, %s head%s)",
+                    h.window, h.n_conv, h.conv_channels, h.fc_hidden, (h.head & 1) ? "hybrid" : "regression",
+                    (h.head & 2) ? ", write queue" : "");
     const uint8_t *in = (const uint8_t *)host_buf;
     size_t off = sizeof h;
     CK(cudaSetDevice(c->device));
@@ -169,8 +176,9 @@ extern "C" simnet_status simnet_state_load(simnet_ctx *c, int32_t kind, const vo
         if (h.retire_width != mine.retire_width || h.strict != mine.strict || h.cap != mine.cap)
             return fail(c, SIMNET_EINVAL, "state_load: state of another retire width, retire rule or queue capacity");
         const int B = h.n_sub;
-        if (B < 1 || h.steps_done < 0 || h.steps_done > h.max_len || h.payload_bytes != (int64_t)sim_payload(B, h.cap) ||
-            bytes != sizeof h + sim_payload(B, h.cap))
+        const size_t pl = sim_payload(B, h.cap, c->store_queue);
+        if (B < 1 || h.steps_done < 0 || h.steps_done > h.max_len || h.payload_bytes != (int64_t)pl ||
+            bytes != sizeof h + pl)
             return fail(c, SIMNET_EINVAL, "state_load: inconsistent simulation state header or size");
         simnet_status st = ensure_workspace(c, B);
         if (st != SIMNET_OK) return st;
@@ -184,6 +192,11 @@ extern "C" simnet_status simnet_state_load(simnet_ctx *c, int32_t kind, const vo
         CK(cudaMemcpy(c->n_active, &na, 4, cudaMemcpyHostToDevice));
         CK(put(c->cyc, (size_t)B * 8));
         CK(put(c->ring, (size_t)B * c->cap * 8));
+        if (c->store_queue) {
+            CK(put(c->mstart, (size_t)B * 4));
+            CK(put(c->mlen, (size_t)B * 4));
+            CK(put(c->mring, (size_t)B * c->cap * 8));
+        }
         c->sim_valid = true;
         c->sim_B = B;
         c->sim_steps = h.steps_done;

@@ -31,7 +31,11 @@ namespace {
 
 using namespace tcx;
 
-enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_FP8 = 2, OUT_FC2PART = 3, OUT_FC2HYB = 4 };
+enum OutKind { OUT_BF16 = 0, OUT_F32 = 1, OUT_FP8 = 2, OUT_FC2PART = 3, OUT_FC2HYB = 4, OUT_FC2P3 = 5, OUT_FC2P33 = 6 };
+// FC2 outputs folded by the generic (L1-read) epilogue of an output kind, 0 if none
+template <int OUT> constexpr int fc2_outs() {
+    return OUT == OUT_FC2HYB ? 22 : OUT == OUT_FC2P3 ? 3 : OUT == OUT_FC2P33 ? 33 : 0;
+}
 
 struct TcArgs {
     const float *bias, *scale, *oscale, *w2;
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(320, 1)
             const int row = m0 + q * 32 + lane;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + half * (BN / 2));
             float pf = 0.f, pe = 0.f;
-            constexpr int NH = OUT == OUT_FC2HYB ? kOutHybrid : 1;
+            constexpr int NH = fc2_outs<OUT>() > 0 ? fc2_outs<OUT>() : 1;
             float ph[NH];
 #pragma unroll
             for (int o = 0; o < NH; o++) ph[o] = 0.f;
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(320, 1)
                         pe = fmaf(v[4 * j4], we.x, pe); pe = fmaf(v[4 * j4 + 1], we.y, pe);
                         pe = fmaf(v[4 * j4 + 2], we.z, pe); pe = fmaf(v[4 * j4 + 3], we.w, pe);
                     }
-                } else if constexpr (OUT == OUT_FC2HYB) {
+                } else if constexpr (fc2_outs<OUT>() > 0) {
                     // every lane reads the same FC2 row segment: L1 broadcasts
 #pragma unroll
                     for (int o = 0; o < NH; o++) {
@@ -303,7 +307,7 @@ __global__ void __launch_bounds__(320, 1)
                     reinterpret_cast<float2 *>(args.out)[(size_t)(2 * nt + half) * args.part_stride + row] =
                         make_float2(pf, pe);
             }
-            if constexpr (OUT == OUT_FC2HYB) {
+            if constexpr (fc2_outs<OUT>() > 0) {
                 if (row < M) {
                     float *dst = reinterpret_cast<float *>(args.out) +
                                  ((size_t)(2 * nt + half) * args.part_stride + row) * NH;
@@ -497,6 +501,14 @@ void launch_tc_gemm(const TcPlan &p, const GemmLayer &g, const int32_t *count, c
         case TC_OUT_PART_HYBRID:
             if (fp8) dispatch<true, OUT_FC2HYB>(p, a, s);
             else dispatch<false, OUT_FC2HYB>(p, a, s);
+            break;
+        case TC_OUT_PART3:
+            if (fp8) dispatch<true, OUT_FC2P3>(p, a, s);
+            else dispatch<false, OUT_FC2P3>(p, a, s);
+            break;
+        case TC_OUT_PART33:
+            if (fp8) dispatch<true, OUT_FC2P33>(p, a, s);
+            else dispatch<false, OUT_FC2P33>(p, a, s);
             break;
         default:
             if (fp8) dispatch<true, OUT_FP8>(p, a, s);

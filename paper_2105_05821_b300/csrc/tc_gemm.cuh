@@ -14,6 +14,8 @@ enum TcOut : int {
     TC_OUT_F32 = 1,   // FP32 [M][N]
     TC_OUT_PART = 3,  // FC2 partial dot products [2*N/BN][m_cap][2] float (fetch, execution)
     TC_OUT_PART_HYBRID = 4,  // the same for the hybrid head's 22 FC2 outputs: [2*N/BN][m_cap][22]
+    TC_OUT_PART3 = 5,        // ... three regression outputs (fetch, execution, store)
+    TC_OUT_PART33 = 6,       // ... the hybrid head with the store latency (33 outputs)
 };
 
 // Everything one layer's tensor-core launch needs; built once per

@@ -33,13 +33,13 @@ __global__ void window_gather_kernel(const uint32_t *__restrict__ rec, const int
     const uint32_t cur = rec[i];
     float v[4] = {0.f, 0.f, 0.f, 0.f};
     if (r == 0) {
-        for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, cur, cur, false, 0, 0);
+        for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, cur, cur, false, 0, 0, 0);
     } else if (i - r >= ctx_begin[i]) {
         const int64_t jj = i - r;
         const int64_t now = i > 0 ? fetch[i - 1] : 0;
         const int64_t res = now - fetch[jj];
         const int32_t res32 = (int32_t)(res > 4095 ? 4095 : res);
-        for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, rec[jj], cur, true, res32, e_label[jj]);
+        for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, rec[jj], cur, true, res32, e_label[jj], 0);
     }
     *reinterpret_cast<float4 *>(X + rowid * kNFP + chunk * 4) = make_float4(v[0], v[1], v[2], v[3]);
     if (x50)
@@ -162,8 +162,8 @@ __global__ void hybrid_loss_kernel(const float *__restrict__ z, const uint8_t *_
     double l = 0.0;
     if (i < 2 * n) {
         const int r = i >> 1, k = i & 1;
-        const float *lg = z + (size_t)r * kOutHybrid + 11 * k;
-        float *dl = dz + (size_t)r * kOutHybrid + 11 * k;
+        const float *lg = z + (size_t)r * 22 + 11 * k;
+        float *dl = dz + (size_t)r * 22 + 11 * k;
         const int t = labels[2 * idx[r] + k];
         const int cls = t > 8 ? 9 : t;
         float mx = lg[0];
@@ -451,6 +451,8 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
         return fail(c, SIMNET_EINVAL, "train_step: bad arguments");
     if (!c->has_weights) return fail(c, SIMNET_ESTATE, "train_step: no weights loaded");
     if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context");
+    if (c->store_queue)
+        return fail(c, SIMNET_EUNSUPPORTED, "train_step: the training windows carry no store latency labels");
     CK(cudaSetDevice(c->device));
     simnet_status st = ensure_train(c, batch);
     if (st != SIMNET_OK) return st;
@@ -460,7 +462,7 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
         w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X, nullptr);
     train_forward_enqueue(c, batch, s);
     CK(cudaMemsetAsync(t.loss, 0, sizeof(double), s));
-    if (c->n_out == kOutHybrid)
+    if (c->hybrid)
         hybrid_loss_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
     else
         mse_softplus_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);

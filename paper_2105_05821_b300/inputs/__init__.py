@@ -284,7 +284,7 @@ def unflatten_weights(arch: Arch, blob: np.ndarray) -> List[Tuple[str, np.ndarra
 
 
 FC2_GAIN = (8.0, 25.0, 25.0)    # scale of the fetch / execution / store rows of FC2
-FC2_BIAS = (0.3, 12.0, 20.0)    # FC2 bias (fetch, execution, store)
+FC2_BIAS = (0.3, 12.0, 40.0)    # FC2 bias (fetch, execution, store)
 
 
 # Hybrid head: class-logit rows are scaled by HYB_CLASS_GAIN and biased

@@ -26,6 +26,7 @@ FLAG_NO_PDL = 0x8
 FLAG_LAYERWISE = 0x10
 FLAG_NO_CLUSTER = 0x20
 FLAG_HYBRID_HEAD = 0x40
+FLAG_STORE_QUEUE = 0x80
 PATHS = {0: "none", 1: "layerwise", 2: "persistent", 3: "cluster"}
 KERNEL_KINDS = 12
 KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
@@ -158,19 +159,21 @@ class Simnet:
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
                  pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0,
-                 cluster: bool = True, hybrid: bool = False):
+                 cluster: bool = True, hybrid: bool = False, store_queue: bool = False):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
                  | (0 if persistent else FLAG_LAYERWISE) | (0 if cluster else FLAG_NO_CLUSTER)
-                 | (FLAG_HYBRID_HEAD if hybrid else 0))
+                 | (FLAG_HYBRID_HEAD if hybrid else 0) | (FLAG_STORE_QUEUE if store_queue else 0))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, barrier_limit_us,
                             spin_limit_ns)
         self.window = window
         self.precision = prec
         self.hybrid = bool(hybrid)
-        self.n_out = 22 if hybrid else 2      # FC2 outputs per window
+        self.store_queue = bool(store_queue)
+        self.n_lat = 3 if store_queue else 2                      # latencies per instruction
+        self.n_out = (11 if hybrid else 1) * self.n_lat          # FC2 outputs per window
         h = C.c_void_p()
         st = L.simnet_init(C.byref(self._cfg), C.byref(h))
         if st != 0:
@@ -180,6 +183,7 @@ class Simnet:
     @classmethod
     def for_arch(cls, arch, **kw) -> "Simnet":
         kw.setdefault("hybrid", getattr(arch, "head", "regression") == "hybrid")
+        kw.setdefault("store_queue", bool(getattr(arch, "store_queue", False)))
         return cls(arch.window, arch.n_conv, arch.channels, arch.hidden, **kw)
 
     def close(self):

@@ -25,8 +25,9 @@ def to_dev(trace: I.Trace):
 def run_gpu(sim: Simnet, trace: I.Trace, replay=None, logs=True):
     rec, off = to_dev(trace)
     N = trace.n_instructions
-    lat = torch.zeros((max(N, 1), 2), dtype=torch.uint8, device="cuda") if logs else None
-    pre = torch.full((max(N, 1), 2), float("nan"), dtype=torch.float32, device="cuda") if logs else None
+    NL = sim.n_lat
+    lat = torch.zeros((max(N, 1), NL), dtype=torch.uint8, device="cuda") if logs else None
+    pre = torch.full((max(N, 1), NL), float("nan"), dtype=torch.float32, device="cuda") if logs else None
     rp = None
     if replay is not None:
         rp = torch.from_numpy(np.ascontiguousarray(replay, dtype=np.uint8)).cuda()

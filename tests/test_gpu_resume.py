@@ -35,8 +35,8 @@ def sim_for(arch, precision, mode, **kw):
 def run(sim, rec, off, N, chunks=None, state_via=None):
     """Simulate to the end, in one call or in bounded calls of chunks[i] steps;
     state_via(sim) -> sim swaps contexts between calls through state bytes."""
-    lat = torch.zeros((N, 2), dtype=torch.uint8, device="cuda")
-    pre = torch.full((N, 2), float("nan"), dtype=torch.float32, device="cuda")
+    lat = torch.zeros((N, sim.n_lat), dtype=torch.uint8, device="cuda")
+    pre = torch.full((N, sim.n_lat), float("nan"), dtype=torch.float32, device="cuda")
     cyc = torch.empty(off.numel() - 1, dtype=torch.int64, device="cuda")
     if chunks is None:
         st = sim.simulate(rec, off, cycles_out=cyc, lat_log=lat, pre_log=pre)
