@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import dataclasses
+import faulthandler
 import json
 import os
 import subprocess
@@ -141,7 +142,7 @@ def workload_of(args) -> I.Workload:
     store = bool(getattr(args, "store_queue", False))
     if head != "regression" or store:
         a = w.arch
-        w = dataclasses.replace(w, arch=I.Arch(a.window, a.n_conv, a.channels, a.hidden, head, store))
+        w = dataclasses.replace(w, arch=I.Arch(a.window, a.n_conv, a.channels, a.hidden, head, store, a.block))
     return w
 
 
@@ -181,6 +182,7 @@ def workload_config(w, args, note=""):
          "instructions_per_step": None, "window": w.arch.window, "n_conv": w.arch.n_conv,
          "channels": w.arch.channels, "fc_hidden": w.arch.hidden, "retire_width": w.retire_width,
          "precision": args.precision, "head": w.arch.head, "store_queue": w.arch.store_queue,
+         "block": w.arch.block,
          "l2": "flushed (512 MB write) before every timed step"}
     if note:
         c["note"] = note
@@ -198,6 +200,9 @@ def algorithmic_units(w: I.Workload, kind: int, n_active: float, prec: str):
             rows = a.window >> (l + 1)
             cin = I.N_FEATURES if l == 0 else a.channels
             macs = rows * a.channels * cin * 2
+            if a.block == "residual":   # the block's three GEMMs (conv, projection, pointwise),
+                # three launches of this kind a step: the per-launch average
+                macs = (2 * rows * a.channels * cin * 2 + rows * a.channels * a.channels) / 3.0
         else:
             macs = a.fc1_in * a.hidden
         return 2.0 * macs * n_active, "flop", ("alu" if prec == "fp32" else "tensor")
@@ -206,7 +211,7 @@ def algorithmic_units(w: I.Workload, kind: int, n_active: float, prec: str):
         return per * n_active, "byte", "hbm"
     if kind == 10:  # head + update + next gather: FC2 partials, ring, append, scalars, next tile rows
         parts = a.hidden // 64
-        per = parts * 8 + (a.window - 1) * 8 + 8 + 4 + 32 + a.window * 64 * es
+        per = parts * 4 * a.n_out + (a.window - 1) * 8 + 8 + 4 + 32 + a.window * 64 * es
         return per * n_active, "byte", "hbm"
     return 0.0, "byte", "hbm"
 
@@ -218,7 +223,9 @@ def kind_name(w, k):
     if k in KIND_NAMES:
         return KIND_NAMES[k]
     l = k - 1
-    return f"conv{l + 1}_gemm" if l < w.arch.n_conv else "fc1_gemm"
+    if l < w.arch.n_conv:
+        return f"rb{l + 1}_gemms" if w.arch.block == "residual" else f"conv{l + 1}_gemm"
+    return "fc1_gemm"
 
 
 def aggregate(ms_total: float, steps: int, inst_per_step: int, world: int, device):
@@ -344,7 +351,7 @@ def run_ours(args, rank, world):
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * N + 8 * (B + 1)),
                    "d2h_bytes_per_step": int(8 * B)},
            "wall_s_timed": wall,
-           "tile_widths": tiles[:w.arch.n_conv + 1],
+           "tile_widths": tiles[:(3 if w.arch.block == "residual" else 1) * w.arch.n_conv + 1],
            "kernel_mode": {"layerwise": "per-layer kernels", "persistent": "persistent",
                            "cluster": "cluster"}.get(path, path)}
     out["config"]["instructions_per_step"] = N
@@ -557,12 +564,13 @@ def run_training(args):
 
 
 def main():
+    faulthandler.enable()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "rb7"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-breakdown", action="store_true")

@@ -95,6 +95,16 @@ typedef enum {
                                           evicts the oldest (the write queue's head first).  Context
                                           rows of stores carry S/64 in feature 44.  lat_log,
                                           pre_log and lat_replay hold 3 values per instruction. */
+#define SIMNET_FLAG_RESIDUAL 0x100u    /* the n_conv layers are residual blocks (the RB models of
+                                          Sec. 2.3): block k computes a = ReLU(conv(x)) and
+                                          y = ReLU(pw(a) + proj(x)), conv and proj k=2 / stride-2
+                                          convolutions (proj without bias), pw a pointwise
+                                          convolution with bias.  Blob per block: conv.weight
+                                          [C][C_in][2], conv.bias [C], pw.weight [C][C][1],
+                                          pw.bias [C], proj.weight [C][C_in][2].  FP32 or BF16
+                                          only (EUNSUPPORTED for FP8); runs as per-layer kernels;
+                                          no device training (train_* and set_weights_device
+                                          return EUNSUPPORTED) and no cnn_forward_noalloc. */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -160,7 +170,8 @@ typedef struct {
  * (64, 128, 256 output columns) of every tensor-core layer, one layer after
  * another, on a synthetic trace of `steps` instructions per sub-trace, and keep
  * the fastest whole simnet_simulate call.  Later calls with the same batch size
- * use the choice.  bn_out (host, n_conv + 1 entries) or NULL receives the
+ * use the choice.  bn_out (host, one entry per GEMM: n_conv + 1, or
+ * 3 * n_conv + 1 with SIMNET_FLAG_RESIDUAL; 25 always suffice) or NULL receives the
  * widths.  FP32 contexts have nothing to tune (returns OK).  Synchronises.
  * Errors: EINVAL, ESTATE (no weights), ENOMEM.
  */

@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class _Cfg(C.Structure):
     _fields_ = [("window", C.c_int32), ("n_conv", C.c_int32), ("channels", C.c_int32),
                 ("hidden", C.c_int32), ("retire_width", C.c_int32), ("retire_strict", C.c_int32),
-                ("hybrid", C.c_int32), ("store_queue", C.c_int32)]
+                ("hybrid", C.c_int32), ("store_queue", C.c_int32), ("residual", C.c_int32)]
 
 
 _lib = None
@@ -82,6 +82,7 @@ class Config:
     retire_strict: bool = False
     hybrid: bool = False          # hybrid head (11 FC2 outputs per latency) instead of regression (1)
     store_queue: bool = False     # store latency + memory write queue (3 latencies instead of 2)
+    residual: bool = False        # residual blocks (RB models) instead of plain conv layers
 
     @property
     def n_lat(self) -> int:
@@ -93,13 +94,13 @@ class Config:
 
     def c(self) -> _Cfg:
         return _Cfg(self.window, self.n_conv, self.channels, self.hidden, self.retire_width,
-                    int(self.retire_strict), int(self.hybrid), int(self.store_queue))
+                    int(self.retire_strict), int(self.hybrid), int(self.store_queue), int(self.residual))
 
     @staticmethod
     def of(arch, retire_width: int = 8, retire_strict: bool = False) -> "Config":
         return Config(arch.window, arch.n_conv, arch.channels, arch.hidden, retire_width,
                       retire_strict, getattr(arch, "head", "regression") == "hybrid",
-                      bool(getattr(arch, "store_queue", False)))
+                      bool(getattr(arch, "store_queue", False)), getattr(arch, "block", "conv") == "residual")
 
 
 def blob_size(cfg: Config) -> int:

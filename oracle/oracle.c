@@ -9,8 +9,9 @@
  * What it computes (SimNet, arXiv 2105.05821):
  *   - the 50-feature rows of the current instruction and its context
  *     instructions (Sec. 2.2, Table 1, in the synthetic encoding below);
- *   - the CNN latency predictor: k=2 / stride-2 convolutions with ReLU,
- *     flatten, FC + ReLU, FC to (fetch, execution) (Sec. 2.3, Fig. 2);
+ *   - the CNN latency predictor: k=2 / stride-2 convolutions with ReLU, or
+ *     residual blocks (the RB models), flatten, FC + ReLU, FC to the
+ *     latencies (Sec. 2.3, Fig. 2);
  *   - latency = softplus(output), clamped to [0, 255] and rounded half-to-even;
  *     or, with the hybrid head (Sec. 2.3), per latency the class with the
  *     largest of 10 logits (0..8 cycles, or "more than 8", which takes the
@@ -70,6 +71,7 @@ typedef struct {
     int32_t retire_strict; /* 0: ready at residence >= E; 1: residence > E */
     int32_t hybrid;        /* 0: regression head; 1: hybrid head (11 outputs per latency) */
     int32_t store_queue;   /* 1: a third latency (store) and the memory write queue (Sec. 3.2) */
+    int32_t residual;      /* 1: the n_conv layers are residual blocks (RB models, Sec. 2.3) */
 } oracle_cfg;
 
 /* Latencies predicted per instruction: fetch, execution (and store). */
@@ -131,8 +133,18 @@ static void encode_context(const inst_t *cur, uint32_t ctx_rec, int64_t residenc
 }
 
 /* ------------------------------------------------------------------ CNN (Sec. 2.3) */
+/* Layer k of a residual network is a residual block (the paper draws it only
+ * in a figure; this build's reading, in the spirit of the EfficientNet-style
+ * blocks it cites, with the kernel-2 / stride-2 rule kept):
+ *   a = ReLU(conv_k(x)), k = 2, stride 2, with bias (cw, cb);
+ *   y = ReLU(pw_k(a) + proj_k(x)), pw a pointwise (k = 1) conv with bias (pw,
+ *   pwb) and proj a k = 2 / stride-2 conv without bias (pj), the shortcut that
+ *   matches the halved length and the channel count.
+ * Blob order per block: conv.weight [C][Cin][2], conv.bias [C], pw.weight
+ * [C][C][1], pw.bias [C], proj.weight [C][Cin][2]. */
 typedef struct {
     const double *cw[MAXCONV], *cb[MAXCONV];
+    const double *pw[MAXCONV], *pwb[MAXCONV], *pj[MAXCONV];   /* residual blocks only */
     const double *w1, *b1, *w2, *b2;
 } net_t;
 
@@ -141,6 +153,7 @@ static int64_t blob_size(const oracle_cfg *c)
     int64_t n = 0, cin = NF;
     for (int k = 0; k < c->n_conv; k++) {
         n += (int64_t)c->channels * cin * 2 + c->channels;
+        if (c->residual) n += (int64_t)c->channels * c->channels + c->channels + (int64_t)c->channels * cin * 2;
         cin = c->channels;
     }
     int64_t fin = (int64_t)c->channels * (c->window >> c->n_conv);
@@ -156,6 +169,11 @@ static net_t net_view(const oracle_cfg *c, const double *blob)
     for (int k = 0; k < c->n_conv; k++) {
         n.cw[k] = p; p += (int64_t)c->channels * cin * 2;
         n.cb[k] = p; p += c->channels;
+        if (c->residual) {
+            n.pw[k] = p; p += (int64_t)c->channels * c->channels;
+            n.pwb[k] = p; p += c->channels;
+            n.pj[k] = p; p += (int64_t)c->channels * cin * 2;
+        }
         cin = c->channels;
     }
     int64_t fin = (int64_t)c->channels * (c->window >> c->n_conv);
@@ -169,6 +187,7 @@ static net_t net_view(const oracle_cfg *c, const double *blob)
 /* Work area holding every layer's output, kept for the backward pass. */
 typedef struct {
     double *act[MAXCONV + 1];  /* act[0] = input [W][NF]; act[k+1] = conv k out [W>>(k+1)][C] */
+    double *ra, *rs;           /* residual blocks: branch and shortcut [W/2][C] (reused per block) */
     double *hid;               /* FC1 output after ReLU [H] */
     double z[MAXOUT];          /* FC2 outputs (before softplus / class decision) */
 } fwd_t;
@@ -177,6 +196,7 @@ static size_t fwd_doubles(const oracle_cfg *c)
 {
     size_t n = (size_t)c->window * NF;
     for (int k = 0; k < c->n_conv; k++) n += (size_t)(c->window >> (k + 1)) * c->channels;
+    if (c->residual) n += 2 * (size_t)(c->window >> 1) * c->channels;
     return n + c->hidden;
 }
 
@@ -187,6 +207,13 @@ static void fwd_bind(const oracle_cfg *c, double *mem, const double *x, fwd_t *f
     for (int k = 0; k < c->n_conv; k++) {
         f->act[k + 1] = p;
         p += (size_t)(c->window >> (k + 1)) * c->channels;
+    }
+    f->ra = f->rs = NULL;
+    if (c->residual) {
+        f->ra = p;
+        p += (size_t)(c->window >> 1) * c->channels;
+        f->rs = p;
+        p += (size_t)(c->window >> 1) * c->channels;
     }
     f->hid = p;
 }
@@ -205,11 +232,35 @@ static void conv_forward(const double *w, const double *b, const double *x, int 
         }
 }
 
+/* Residual block k: a = ReLU(conv(x)); s = proj(x); y = ReLU(pw(a) + pw bias + s). */
+static void residual_forward(const net_t *n, int k, const double *x, int rows_in, int cin, int C,
+                             double *a, double *s, double *y)
+{
+    conv_forward(n->cw[k], n->cb[k], x, rows_in, cin, C, a);
+    for (int l = 0; l < rows_in / 2; l++)
+        for (int co = 0; co < C; co++) {
+            double t = 0.0;
+            for (int ci = 0; ci < cin; ci++)
+                for (int tap = 0; tap < 2; tap++)
+                    t += n->pj[k][((int64_t)co * cin + ci) * 2 + tap] * x[(int64_t)(2 * l + tap) * cin + ci];
+            s[(int64_t)l * C + co] = t;
+        }
+    for (int l = 0; l < rows_in / 2; l++)
+        for (int co = 0; co < C; co++) {
+            double t = n->pwb[k][co] + s[(int64_t)l * C + co];
+            for (int ci = 0; ci < C; ci++) t += n->pw[k][(int64_t)co * C + ci] * a[(int64_t)l * C + ci];
+            y[(int64_t)l * C + co] = t > 0.0 ? t : 0.0;
+        }
+}
+
 static void cnn_forward(const oracle_cfg *c, const net_t *n, fwd_t *f)
 {
     int rows = c->window, cin = NF;
     for (int k = 0; k < c->n_conv; k++) {
-        conv_forward(n->cw[k], n->cb[k], f->act[k], rows, cin, c->channels, f->act[k + 1]);
+        if (c->residual)
+            residual_forward(n, k, f->act[k], rows, cin, c->channels, f->ra, f->rs, f->act[k + 1]);
+        else
+            conv_forward(n->cw[k], n->cb[k], f->act[k], rows, cin, c->channels, f->act[k + 1]);
         rows /= 2;
         cin = c->channels;
     }
@@ -529,7 +580,7 @@ int oracle_window_features(const oracle_cfg *c, const uint32_t *records, int64_t
 int oracle_loss_grad(const oracle_cfg *c, const double *weights, const double *x,
                      const double *y, int64_t n, double *loss_out, double *grad_out)
 {
-    if (!cfg_ok(c) || n <= 0) return -1;
+    if (!cfg_ok(c) || n <= 0 || c->residual) return -1;   /* training: plain conv layers only */
     const int W = c->window, C = c->channels, H = c->hidden, NC = c->n_conv;
     net_t net = net_view(c, weights);
     int64_t P = blob_size(c);

@@ -12,6 +12,7 @@ namespace simnet {
 constexpr int kNF = SIMNET_N_FEATURES;  // real features per row (Sec. 2.2)
 constexpr int kNFP = 64;                // features per row in device layout (zero padded)
 constexpr int kMaxConv = 8;
+constexpr int kMaxGemm = 3 * kMaxConv + 1;  // GEMMs of the deepest CNN: 3 per residual block + FC1
 constexpr int kOutHybrid = 22;          // FC2 outputs of the hybrid head: per latency 10 class logits + 1 value
 
 // Device status word values (written by kernels, read by the host after a call).
@@ -73,12 +74,18 @@ struct StepArgs {
     int32_t n_lat;    // latencies per instruction: 2 (F, E) or 3 (F, E, S)
 };
 
-// A GEMM layer C[M, N] = act(A[M, K] * B[N, K]^T * scale + bias), M = n_active * m_mult.
+// Workspace buffers a GEMM of the CNN reads or writes (see GemmLayer).
+enum GemmBuf : int { kBufNone = -1, kBufX = 0, kBufAct0 = 1, kBufAct1 = 2, kBufTmpA = 3, kBufTmpS = 4, kBufH1 = 5 };
+
+// A GEMM layer C[M, N] = act(A[M, K] * B[N, K]^T * scale + bias [+ R]), M = n_active * m_mult.
 struct GemmLayer {
     int m_mult;    // output rows per sub-trace
     int K;         // reduction length (padded)
     int N;         // output columns
     int relu;
+    int in_buf = kBufX, out_buf = kBufH1;  // A and C
+    int res_buf = kBufNone;  // R [M][N] in the layer precision, added before the activation
+    int kind = 0;            // timing kind offset (conv layer / residual block index; FC1 last)
     const void *B; // weights [N][K] in the layer's precision
     const float *bias;   // [N]
     const float *scale;  // [N] per-output-channel dequant scale (FP8) or nullptr

@@ -17,13 +17,13 @@ struct TrainState {
     bool ready = false;
     int n_cap = 0;                     // windows the buffers hold
     int64_t step = 0;                  // Adam step counter
-    float *gW[kMaxConv + 1] = {}, *gb[kMaxConv + 1] = {};    // gradients
-    float *mW[kMaxConv + 1] = {}, *vW[kMaxConv + 1] = {};    // Adam moments (weights)
-    float *mb[kMaxConv + 1] = {}, *vb[kMaxConv + 1] = {};    // Adam moments (biases)
+    float *gW[kMaxGemm] = {}, *gb[kMaxGemm] = {};    // gradients
+    float *mW[kMaxGemm] = {}, *vW[kMaxGemm] = {};    // Adam moments (weights)
+    float *mb[kMaxGemm] = {}, *vb[kMaxGemm] = {};    // Adam moments (biases)
     float *gw2 = nullptr, *gb2 = nullptr;
     float *mw2 = nullptr, *vw2 = nullptr, *mb2 = nullptr, *vb2 = nullptr;
     float *X = nullptr;                // packed input [n][W][64]
-    float *Y[kMaxConv + 1] = {};       // outputs of every layer (post-ReLU); Y[L] = FC1 [n][H]
+    float *Y[kMaxGemm] = {};           // outputs of every layer (post-ReLU); Y[L] = FC1 [n][H]
     float *dA = nullptr, *dB = nullptr;  // gradient ping-pong buffers (largest activation)
     float *z = nullptr, *dz = nullptr; // [n][n_out]
     double *loss = nullptr;            // device scalar
@@ -42,18 +42,25 @@ struct simnet_ctx {
     int device = 0;
 
     // weights in GEMM layout ([N][K], layer precision) + FP32 biases; FC2 in FP32
-    void *Wl[kMaxConv + 1] = {};
-    float *bias[kMaxConv + 1] = {};
-    float *wscale[kMaxConv + 1] = {};  // FP8: per-output-channel dequant scale
-    float *oscale[kMaxConv + 1] = {};  // FP8: per-output-channel requant multiplier (1/next act scale)
-    float *W32[kMaxConv + 1] = {};     // FP32 GEMM-layout weights (aliases Wl for FP32 contexts)
+    void *Wl[kMaxGemm] = {};
+    float *bias[kMaxGemm] = {};
+    float *wscale[kMaxGemm] = {};  // FP8: per-output-channel dequant scale
+    float *oscale[kMaxGemm] = {};  // FP8: per-output-channel requant multiplier (1/next act scale)
+    float *W32[kMaxGemm] = {};     // FP32 GEMM-layout weights (aliases Wl for FP32 contexts)
     float *w2 = nullptr, *b2 = nullptr;
-    GemmLayer layer[kMaxConv + 1];
-    TcPlan plan[kMaxConv + 1];
+    GemmLayer layer[kMaxGemm];
+    TcPlan plan[kMaxGemm];
+    // residual blocks (SIMNET_FLAG_RESIDUAL): GEMMs 3b, 3b+1, 3b+2 are block b's
+    // conv, projection shortcut and pointwise conv (+ shortcut); the canonical
+    // blob is kept on the host (these contexts do not train on the device)
+    bool residual = false;
+    int n_blocks = 0;
+    std::vector<float> blob_host;
 
     // workspace, sized for ws_B sub-traces
     int ws_B = 0;
     void *X = nullptr, *act[2] = {nullptr, nullptr};
+    void *tmpA = nullptr, *tmpS = nullptr;   // residual blocks: branch and shortcut [B][W/2][C]
     float *h1 = nullptr;  // FC2 partial sums [n_part][B][n_out] float
     int n_part = 0;
     bool pdl = true;
@@ -98,7 +105,7 @@ struct simnet_ctx {
 
     // autotuned tile widths: tuned_bn[l] applies to batches of tuned_B sub-traces
     int tuned_B = -1;
-    int tuned_bn[kMaxConv + 1] = {};
+    int tuned_bn[kMaxGemm] = {};
 
     // resumable simulation state: the workspace arrays tick/pos/qstart/qlen/
     // evict/ring/active/n_active plus the finished cycle counts `cyc`

@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
                                                     const float *__restrict__ bias, float *__restrict__ C,
                                                     const int32_t *__restrict__ n_active, int m_mult,
                                                     int m_cap, int N, int K, int relu,
-                                                    const float *__restrict__ w2, int part_stride) {
+                                                    const float *__restrict__ w2, int part_stride,
+                                                    const float *__restrict__ R) {
     constexpr int BM = 128, BK = 8, TM = 8, TN = BN / 16;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -119,6 +120,10 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
             v.y = acc[i][j + 1] + bias[col + 1];
             v.z = acc[i][j + 2] + bias[col + 2];
             v.w = acc[i][j + 3] + bias[col + 3];
+            if (R) {   // residual block: the shortcut, before the activation
+                const float4 r = *reinterpret_cast<const float4 *>(R + (size_t)row * N + col);
+                v.x += r.x; v.y += r.y; v.z += r.z; v.w += r.w;
+            }
             if (relu) { v.x = fmaxf(v.x, 0.f); v.y = fmaxf(v.y, 0.f); v.z = fmaxf(v.z, 0.f); v.w = fmaxf(v.w, 0.f); }
             *reinterpret_cast<float4 *>(C + (size_t)row * N + col) = v;
         }
@@ -126,15 +131,15 @@ __global__ void __launch_bounds__(256) sgemm_kernel(const float *__restrict__ A,
 }
 
 void launch_gemm_f32(const float *A, const float *B, const float *bias, float *C, const int32_t *n_active,
-                     int m_mult, int m_cap, int N, int K, int relu, cudaStream_t s, bool pdl) {
+                     int m_mult, int m_cap, int N, int K, int relu, cudaStream_t s, bool pdl, const float *R) {
     const unsigned gm = (unsigned)((m_cap + 127) / 128);
     if (gm == 0) return;
     if (N % 128 == 0)
         launch_k(pdl, sgemm_kernel<128, 0>, dim3(gm, N / 128), dim3(256), 0, s, A, B, bias, C, n_active, m_mult,
-                 m_cap, N, K, relu, (const float *)nullptr, 0);
+                 m_cap, N, K, relu, (const float *)nullptr, 0, R);
     else
         launch_k(pdl, sgemm_kernel<64, 0>, dim3(gm, (N + 63) / 64), dim3(256), 0, s, A, B, bias, C, n_active,
-                 m_mult, m_cap, N, K, relu, (const float *)nullptr, 0);
+                 m_mult, m_cap, N, K, relu, (const float *)nullptr, 0, R);
 }
 
 int gemm_f32_part_blocks(int N) { return N % 128 == 0 ? N / 128 : (N + 63) / 64; }
@@ -147,10 +152,10 @@ static void launch_part_no(const float *A, const float *B, const float *bias, co
     if (gm == 0) return;
     if (N % 128 == 0)
         launch_k(pdl, sgemm_kernel<128, NO>, dim3(gm, N / 128), dim3(256), 0, s, A, B, bias, part, n_active, m_mult,
-                 m_cap, N, K, relu, w2, part_stride);
+                 m_cap, N, K, relu, w2, part_stride, (const float *)nullptr);
     else
         launch_k(pdl, sgemm_kernel<64, NO>, dim3(gm, (N + 63) / 64), dim3(256), 0, s, A, B, bias, part, n_active,
-                 m_mult, m_cap, N, K, relu, w2, part_stride);
+                 m_mult, m_cap, N, K, relu, w2, part_stride, (const float *)nullptr);
 }
 
 void launch_gemm_f32_part(const float *A, const float *B, const float *bias, const float *w2, float *part,

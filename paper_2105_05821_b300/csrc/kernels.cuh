@@ -22,9 +22,11 @@ void launch_compact(const StepArgs *A, cudaStream_t s, bool pdl = false);
 void launch_totals(const StepArgs *A, unsigned long long *out, int n_sub, cudaStream_t s);
 void launch_channel_amax(const float *y, int64_t rows, int C, unsigned *out, cudaStream_t s);
 
-// FP32 CUDA-core GEMM: C[M,N] = act(A[M,K] * B[N,K]^T + bias), M = min(*n_active * m_mult, m_cap).
+// FP32 CUDA-core GEMM: C[M,N] = act(A[M,K] * B[N,K]^T + bias [+ R]), M = min(*n_active * m_mult, m_cap);
+// R [M][N] (the shortcut of a residual block) or null.
 void launch_gemm_f32(const float *A, const float *B, const float *bias, float *C, const int32_t *n_active,
-                     int m_mult, int m_cap, int N, int K, int relu, cudaStream_t s, bool pdl = false);
+                     int m_mult, int m_cap, int N, int K, int relu, cudaStream_t s, bool pdl = false,
+                     const float *R = nullptr);
 // The same with FC2 (w2 [n_out][N], n_out 2 or 22) folded into the epilogue:
 // part [gemm_f32_part_blocks(N)][part_stride][n_out] float.
 int gemm_f32_part_blocks(int N);
@@ -35,7 +37,7 @@ void launch_gemm_f32_part(const float *A, const float *B, const float *bias, con
 // FP32 weights of a context, for entry points defined outside simnet.cu.
 struct CtxFp32View {
     int window = 0, hidden = 0, n_layers = 0, device = 0, n_out = 2;
-    GemmLayer layer[kMaxConv + 1];
+    GemmLayer layer[kMaxGemm];
     const float *w2 = nullptr, *b2 = nullptr;
 };
 bool ctx_fp32_view(const simnet_ctx *c, CtxFp32View &v);

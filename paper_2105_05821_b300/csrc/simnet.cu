@@ -22,7 +22,7 @@ static constexpr int kGraphSteps = 16;
 // Read-only view of a context's FP32 weights for entry points in other files.
 namespace simnet {
 bool ctx_fp32_view(const simnet_ctx *c, CtxFp32View &v) {
-    if (!c || !c->has_weights || c->cfg.precision != SIMNET_FP32) return false;
+    if (!c || !c->has_weights || c->cfg.precision != SIMNET_FP32 || c->residual) return false;
     v.window = c->cfg.window;
     v.hidden = c->cfg.fc_hidden;
     v.n_layers = c->n_layers;
@@ -66,30 +66,56 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
     c->cap = k.window - 1;
     c->rows_n = k.window >> k.n_conv;
     c->fc1_in = c->rows_n * k.conv_channels;
-    c->n_layers = k.n_conv + 1;
     c->hybrid = (k.flags & SIMNET_FLAG_HYBRID_HEAD) != 0;
     c->store_queue = (k.flags & SIMNET_FLAG_STORE_QUEUE) != 0;
     c->n_lat = c->store_queue ? 3 : 2;
     c->n_out = (c->hybrid ? 11 : 1) * c->n_lat;
+    c->residual = (k.flags & SIMNET_FLAG_RESIDUAL) != 0;
+    c->n_blocks = c->residual ? k.n_conv : 0;
+    c->n_layers = c->residual ? 3 * k.n_conv + 1 : k.n_conv + 1;   // GEMMs: 3 per residual block, + FC1
+    if (c->residual && k.precision == SIMNET_FP8_E4M3) {
+        delete c;
+        return SIMNET_EUNSUPPORTED;
+    }
     int64_t n = 0, cin = kNF;
     for (int l = 0; l < k.n_conv; l++) {
         n += (int64_t)k.conv_channels * cin * 2 + k.conv_channels;
+        if (c->residual)   // pointwise conv + bias, projection shortcut
+            n += (int64_t)k.conv_channels * k.conv_channels + k.conv_channels + (int64_t)k.conv_channels * cin * 2;
         cin = k.conv_channels;
     }
     n += (int64_t)c->fc1_in * k.fc_hidden + k.fc_hidden + (int64_t)c->n_out * k.fc_hidden + c->n_out;
     c->n_weights = n;
     for (int l = 0; l < c->n_layers; l++) {
         GemmLayer &g = c->layer[l];
-        if (l < k.n_conv) {
-            g.m_mult = k.window >> (l + 1);
-            g.K = l == 0 ? 2 * kNFP : 2 * k.conv_channels;
-            g.N = k.conv_channels;
-        } else {
+        const bool fc1 = l == c->n_layers - 1;
+        const int blk = c->residual ? l / 3 : l, part = c->residual ? l % 3 : 0;
+        g.relu = 1;
+        if (fc1) {
             g.m_mult = 1;
             g.K = c->fc1_in;
             g.N = k.fc_hidden;
+            g.in_buf = k.n_conv == 0 ? kBufX : ((k.n_conv - 1) & 1) ? kBufAct1 : kBufAct0;
+            g.out_buf = kBufH1;
+            g.kind = k.n_conv;
+            continue;
         }
-        g.relu = 1;
+        const int in = blk == 0 ? kBufX : ((blk - 1) & 1) ? kBufAct1 : kBufAct0;
+        const int out = (blk & 1) ? kBufAct1 : kBufAct0;
+        g.m_mult = k.window >> (blk + 1);
+        g.N = k.conv_channels;
+        g.kind = blk;
+        if (part == 2) {   // residual block: pointwise conv of the branch, plus the shortcut
+            g.K = k.conv_channels;
+            g.in_buf = kBufTmpA;
+            g.out_buf = out;
+            g.res_buf = kBufTmpS;
+        } else {           // conv layer, or a block's conv (branch) / projection (shortcut)
+            g.K = blk == 0 ? 2 * kNFP : 2 * k.conv_channels;
+            g.in_buf = in;
+            g.out_buf = !c->residual ? out : part == 0 ? kBufTmpA : kBufTmpS;
+            g.relu = part == 1 ? 0 : 1;
+        }
     }
     *out = c;
     return SIMNET_OK;
@@ -98,10 +124,10 @@ extern "C" simnet_status simnet_init(const simnet_config *cfg, simnet_ctx **out)
 static void free_workspace(simnet_ctx *c) {
     void *bufs[] = {c->X, c->act[0], c->act[1], c->h1, c->tick, c->pos, c->qstart, c->qlen, c->evict,
                     c->active, c->n_active, c->status, c->cnt, c->ring, c->totals, c->d_args, c->cyc,
-                    c->mstart, c->mlen, c->mring};
+                    c->mstart, c->mlen, c->mring, c->tmpA, c->tmpS};
     for (void *p : bufs)
         if (p) cudaFree(p);
-    c->X = c->act[0] = c->act[1] = nullptr;
+    c->X = c->act[0] = c->act[1] = c->tmpA = c->tmpS = nullptr;
     c->h1 = nullptr;
     c->tick = c->pos = c->qstart = c->qlen = c->evict = c->active = c->n_active = c->status = c->cnt = nullptr;
     c->ring = nullptr;
@@ -121,7 +147,7 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     cudaDeviceSynchronize();
     free_workspace(c);
     TrainState &t = c->tr;
-    for (int l = 0; l <= kMaxConv; l++) {
+    for (int l = 0; l < kMaxGemm; l++) {
         void *tb[] = {t.gW[l], t.gb[l], t.mW[l], t.vW[l], t.mb[l], t.vb[l], t.Y[l]};
         for (void *q : tb)
             if (q) cudaFree(q);
@@ -132,7 +158,7 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
         for (void *q : tb)
             if (q) cudaFree(q);
     }
-    for (int l = 0; l <= kMaxConv; l++) {
+    for (int l = 0; l < kMaxGemm; l++) {
         if (c->Wl[l]) cudaFree(c->Wl[l]);
         if (c->bias[l]) cudaFree(c->bias[l]);
         if (c->wscale[l]) cudaFree(c->wscale[l]);
@@ -339,19 +365,33 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     std::vector<std::vector<float>> Wg(c->n_layers), Bg(c->n_layers);
     const float *p = blob;
     int cin = kNF;
-    for (int l = 0; l < k.n_conv; l++) {
-        const int cin_pad = l == 0 ? kNFP : C, K = 2 * cin_pad;
-        Wg[l].assign((size_t)C * K, 0.f);
+    // a k=2 / stride-2 conv [C][cin][2] as a GEMM [C][2 * cin_pad] (K = tap * cin_pad + channel)
+    auto conv_gemm = [&](std::vector<float> &dst, int cin_pad) {
+        const int K = 2 * cin_pad;
+        dst.assign((size_t)C * K, 0.f);
         for (int co = 0; co < C; co++)
             for (int ci = 0; ci < cin; ci++)
-                for (int t = 0; t < 2; t++) Wg[l][(size_t)co * K + t * cin_pad + ci] = p[((size_t)co * cin + ci) * 2 + t];
+                for (int t = 0; t < 2; t++) dst[(size_t)co * K + t * cin_pad + ci] = p[((size_t)co * cin + ci) * 2 + t];
         p += (size_t)C * cin * 2;
+    };
+    for (int b = 0; b < k.n_conv; b++) {
+        const int cin_pad = b == 0 ? kNFP : C;
+        const int l = c->residual ? 3 * b : b;
+        conv_gemm(Wg[l], cin_pad);
         Bg[l].assign(p, p + C);
         p += C;
+        if (c->residual) {   // pointwise conv [C][C][1] = GEMM [C][C]; then the bias-free projection
+            Wg[l + 2].assign(p, p + (size_t)C * C);
+            p += (size_t)C * C;
+            Bg[l + 2].assign(p, p + C);
+            p += C;
+            conv_gemm(Wg[l + 1], cin_pad);
+            Bg[l + 1].assign(C, 0.f);
+        }
         cin = C;
     }
     {
-        const int l = k.n_conv, K = c->fc1_in;
+        const int l = c->n_layers - 1, K = c->fc1_in;
         Wg[l].assign((size_t)H * K, 0.f);
         for (int h = 0; h < H; h++)
             for (int ch = 0; ch < C; ch++)
@@ -424,7 +464,9 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     }
     if ((st = upload(c, (void **)&c->w2, w2)) != SIMNET_OK) return st;
     if ((st = upload(c, (void **)&c->b2, b2)) != SIMNET_OK) return st;
-    if (k.precision != SIMNET_FP32 && (st = build_fc1_const(c, Bg, Wdeq, osc)) != SIMNET_OK) return st;
+    if (k.precision != SIMNET_FP32 && !c->residual && (st = build_fc1_const(c, Bg, Wdeq, osc)) != SIMNET_OK)
+        return st;
+    if (c->residual) c->blob_host.assign(blob, blob + n_values);
     c->weights_fp = fnv1a(blob, (size_t)n_values * sizeof(float));
     c->weights_fp_dirty = false;
     c->const_stale = false;
@@ -462,6 +504,10 @@ simnet_status ensure_workspace(simnet_ctx *c, int B) {
     CK(cudaMalloc(&c->X, xb));
     CK(cudaMalloc(&c->act[0], ab));
     CK(cudaMalloc(&c->act[1], ab));
+    if (c->residual) {
+        CK(cudaMalloc(&c->tmpA, ab));
+        CK(cudaMalloc(&c->tmpS, ab));
+    }
     // FC2 partials: at most fc_hidden / 32 column blocks (64-wide tiles, two halves) x n_out per row
     const size_t h1n = std::max((size_t)k.fc_hidden, (size_t)(k.fc_hidden / 32) * c->n_out);
     CK(cudaMalloc(&c->h1, (size_t)B * h1n * sizeof(float)));
@@ -507,15 +553,28 @@ simnet_status ensure_workspace(simnet_ctx *c, int B) {
 // `count` is a device int of active rows-groups (sub-traces or windows).
 // The CNN on the batch already in c->X: conv GEMMs, then FC1 with FC2 folded
 // into its epilogue, leaving c->n_part partial sums per row in c->h1.
+// Workspace buffer of a GemmBuf id.
+static void *wsbuf(simnet_ctx *c, int id) {
+    switch (id) {
+        case kBufX: return c->X;
+        case kBufAct0: return c->act[0];
+        case kBufAct1: return c->act[1];
+        case kBufTmpA: return c->tmpA;
+        case kBufTmpS: return c->tmpS;
+        case kBufH1: return c->h1;
+        default: return nullptr;
+    }
+}
+
 static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t s, bool pdl,
                         KTimer *kt = nullptr) {
     const simnet_config &k = c->cfg;
-    const void *in = c->X;
     for (int l = 0; l < c->n_layers; l++) {
-        if (kt) kt->begin(SIMNET_KERNEL_LAYER0 + l);
         const GemmLayer &g = c->layer[l];
+        if (kt) kt->begin(SIMNET_KERNEL_LAYER0 + g.kind);
         const bool last = l == c->n_layers - 1;
-        void *out = last ? (void *)c->h1 : c->act[l & 1];
+        const void *in = wsbuf(c, g.in_buf);
+        void *out = wsbuf(c, g.out_buf);
         const int m_cap = B * g.m_mult;
         if (k.precision == SIMNET_FP32) {
             if (last)
@@ -523,12 +582,11 @@ static void enqueue_cnn(simnet_ctx *c, const int32_t *count, int B, cudaStream_t
                                      g.m_mult, m_cap, g.N, g.K, g.relu, c->n_out, s, pdl);
             else
                 launch_gemm_f32((const float *)in, (const float *)g.B, g.bias, (float *)out, count, g.m_mult, m_cap,
-                                g.N, g.K, g.relu, s, pdl);
+                                g.N, g.K, g.relu, s, pdl, (const float *)wsbuf(c, g.res_buf));
         } else {
             launch_tc_gemm(c->plan[l], g, count, c->w2, s);
         }
         if (kt) kt->end();
-        in = out;
     }
 }
 
@@ -586,15 +644,15 @@ static simnet_status prepare_plans(simnet_ctx *c, int B, bool pdl) {
     for (int l = 0; l < c->n_layers; l++) {
         const GemmLayer &g = c->layer[l];
         const bool last = l == c->n_layers - 1;
-        const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
-        void *out = last ? (void *)c->h1 : c->act[l & 1];
+        const void *in = wsbuf(c, g.in_buf);
+        void *out = wsbuf(c, g.out_buf);
         std::string why;
         const int ok_kind = !last ? TC_OUT_ACT
                             : c->n_out == 3 ? TC_OUT_PART3
                             : c->n_out == 22 ? TC_OUT_PART_HYBRID
                             : c->n_out == 33 ? TC_OUT_PART33 : TC_OUT_PART;
         if (!make_tc_plan(c->plan[l], c->cfg.precision, in, g, out, ok_kind, B * g.m_mult,
-                          c->cfg.spin_limit_ns, c->status, pdl, why))
+                          c->cfg.spin_limit_ns, c->status, pdl, why, wsbuf(c, g.res_buf)))
             return fail(c, SIMNET_ECUDA, "tensor-core plan for layer %d: %s", l, why.c_str());
         if (c->tuned_B == B && c->tuned_bn[l] && c->tuned_bn[l] != c->plan[l].BN &&
             !retune_tc_plan(c->plan[l], g, c->tuned_bn[l], why))
@@ -738,7 +796,8 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
         c->kt_valid = false;
     }
     c->phase_valid = false;
-    const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE);
+    // residual blocks run as per-layer kernels (the single-launch kernels hold plain conv layers)
+    const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE) && !c->residual;
     std::string why_not_cluster;
     if (n_steps <= 0) {
         launches = resume ? 0 : 1;
@@ -962,7 +1021,7 @@ extern "C" simnet_status simnet_autotune(simnet_ctx *c, int32_t n_sub, int32_t s
     c->tuned_B = -1;
     simnet_status r = prepare_plans(c, n_sub, c->pdl);
     if (r != SIMNET_OK) { cleanup(); return r; }
-    int cur[kMaxConv + 1];
+    int cur[kMaxGemm];
     for (int l = 0; l < c->n_layers; l++) cur[l] = c->plan[l].BN;
     c->tuned_B = n_sub;
     for (int l = 0; l < c->n_layers; l++) c->tuned_bn[l] = cur[l];

@@ -216,7 +216,8 @@ extern "C" simnet_status simnet_state_load(simnet_ctx *c, int32_t kind, const vo
     int64_t step = 0;
     memcpy(&step, in + off, 8);
     off += 8;
-    if (c->cfg.precision != SIMNET_FP32 && c->cfg.precision != SIMNET_BF16) return SIMNET_OK;  // FP8: weights only
+    if ((c->cfg.precision != SIMNET_FP32 && c->cfg.precision != SIMNET_BF16) || c->residual)
+        return SIMNET_OK;  // FP8 and residual contexts do not train: weights only
     if ((st = ensure_train(c, 0)) != SIMNET_OK) return st;
     TrainState &t = c->tr;
     for (int l = 0; l < c->n_layers; l++) {

@@ -39,6 +39,7 @@ template <int OUT> constexpr int fc2_outs() {
 
 struct TcArgs {
     const float *bias, *scale, *oscale, *w2;
+    const void *resid;         // [M][N] in the output precision, added before the activation, or null
     void *out;                 // [M][N] activations, or FC2 partials [2 * n_tiles_n][part_stride][2 or 22] float
     const int32_t *count;
     int m_mult, m_cap, N, K, relu, n_tiles_n, part_stride, prm_floats;
@@ -212,6 +213,40 @@ __global__ void __launch_bounds__(320, 1)
                 tmem_ld32(tbase + (uint32_t)(c * 32), r);
                 const int col0 = n0 + half * (BN / 2) + c * 32;
                 float v[32];
+                // residual block: the shortcut rows (same layout as the output)
+                float rs[32];
+#pragma unroll
+                for (int j = 0; j < 32; j++) rs[j] = 0.f;
+                if constexpr (OUT == OUT_BF16) {
+                    if (args.resid && row < M) {
+                        const uint4 *rp = reinterpret_cast<const uint4 *>(
+                            reinterpret_cast<const __nv_bfloat16 *>(args.resid) + (size_t)row * N + col0);
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; q4++) {
+                            const uint4 u = rp[q4];
+                            const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w4[h]));
+                                rs[8 * q4 + 2 * h] = f.x;
+                                rs[8 * q4 + 2 * h + 1] = f.y;
+                            }
+                        }
+                    }
+                } else if constexpr (OUT == OUT_F32) {
+                    if (args.resid && row < M) {
+                        const float4 *rp =
+                            reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(args.resid) + (size_t)row * N + col0);
+#pragma unroll
+                        for (int q4 = 0; q4 < 8; q4++) {
+                            const float4 f = rp[q4];
+                            rs[4 * q4] = f.x;
+                            rs[4 * q4 + 1] = f.y;
+                            rs[4 * q4 + 2] = f.z;
+                            rs[4 * q4 + 3] = f.w;
+                        }
+                    }
+                }
 #pragma unroll
                 for (int j4 = 0; j4 < 8; j4++) {
                     const float4 bb = *reinterpret_cast<const float4 *>(s_bias + col0 + 4 * j4);
@@ -226,7 +261,7 @@ __global__ void __launch_bounds__(320, 1)
                     for (int e = 0; e < 4; e++) {
                         float x = __uint_as_float(r[4 * j4 + e]);
                         if constexpr (FP8) x *= s4[e];
-                        x += b4[e];
+                        x += b4[e] + rs[4 * j4 + e];
                         if (args.relu) x = fmaxf(x, 0.f);
                         if constexpr (FP8) x *= o4[e];
                         v[4 * j4 + e] = x;
@@ -429,10 +464,15 @@ static void finish_plan(TcPlan &p) {
 }
 
 bool make_tc_plan(TcPlan &p, int prec, const void *in, const GemmLayer &g, void *out, int out_kind, int m_cap,
-                  int64_t spin_ns, int32_t *status, bool pdl, std::string &why) {
+                  int64_t spin_ns, int32_t *status, bool pdl, std::string &why, const void *resid) {
     if (p.ready && p.prec == prec && p.in == in && p.out == out && p.m_cap == m_cap && p.K == g.K && p.N == g.N &&
-        p.out_kind == out_kind && p.status == status && p.pdl == pdl && p.wB == g.B)
+        p.out_kind == out_kind && p.status == status && p.pdl == pdl && p.wB == g.B && p.resid == resid)
         return true;
+    if (resid && !(out_kind == TC_OUT_ACT && prec == SIMNET_BF16) && out_kind != TC_OUT_F32) {
+        why = "a shortcut is added only to BF16 or FP32 outputs";
+        return false;
+    }
+    p.resid = resid;
     const int BK = prec == SIMNET_BF16 ? 64 : 128;
     if (g.K % BK != 0 || g.N % 64 != 0) { why = "K or N not a multiple of the tile"; return false; }
     p.prec = prec;
@@ -472,6 +512,7 @@ bool retune_tc_plan(TcPlan &p, const GemmLayer &g, int BN, std::string &why) {
 
 void launch_tc_gemm(const TcPlan &p, const GemmLayer &g, const int32_t *count, const float *w2, cudaStream_t s) {
     TcArgs a;
+    a.resid = p.resid;
     a.bias = g.bias;
     a.scale = g.scale;
     a.oscale = g.oscale;

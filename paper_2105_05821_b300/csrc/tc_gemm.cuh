@@ -31,6 +31,7 @@ struct TcPlan {
     const void *in = nullptr;
     const void *wB = nullptr;
     void *out = nullptr;
+    const void *resid = nullptr;   // residual block: [m_cap][N] added before the activation
     size_t smem = 0;
     int64_t spin_ns = 0;
     int32_t *status = nullptr;
@@ -40,7 +41,7 @@ struct TcPlan {
 // Choose tile shape and encode the TMA descriptors.  Returns false (and a
 // reason) for shapes this kernel does not handle.
 bool make_tc_plan(TcPlan &p, int prec, const void *in, const GemmLayer &g, void *out, int out_kind, int m_cap,
-                  int64_t spin_ns, int32_t *status, bool pdl, std::string &why);
+                  int64_t spin_ns, int32_t *status, bool pdl, std::string &why, const void *resid = nullptr);
 
 // Force a tile width (the autotuner's knob); re-encodes B's map.
 bool retune_tc_plan(TcPlan &p, const GemmLayer &g, int BN, std::string &why);

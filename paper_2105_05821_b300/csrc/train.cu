@@ -305,8 +305,10 @@ simnet_status ensure_train(simnet_ctx *c, int n) {
     return SIMNET_OK;
 }
 
+// Device training: FP32 or BF16 contexts of plain conv layers (residual blocks
+// have no backward pass in this library).
 static bool train_precision_ok(const simnet_ctx *c) {
-    return c->cfg.precision == SIMNET_FP32 || c->cfg.precision == SIMNET_BF16;
+    return (c->cfg.precision == SIMNET_FP32 || c->cfg.precision == SIMNET_BF16) && !c->residual;
 }
 
 // Forward over t.X (already packed): every layer's output kept; z = FC2.
@@ -419,7 +421,7 @@ extern "C" simnet_status simnet_train_forward(simnet_ctx *c, const float *x, flo
     if (!c) return SIMNET_EINVAL;
     if (!x || !z || n <= 0) return fail(c, SIMNET_EINVAL, "train_forward: bad arguments");
     if (!c->has_weights) return fail(c, SIMNET_ESTATE, "train_forward: no weights loaded");
-    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context");
+    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context of plain conv layers");
     CK(cudaSetDevice(c->device));
     simnet_status st = ensure_train(c, n);
     if (st != SIMNET_OK) return st;
@@ -450,7 +452,7 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
     if (!w || !idx || batch <= 0 || !w->labels || !(lr >= 0.f))
         return fail(c, SIMNET_EINVAL, "train_step: bad arguments");
     if (!c->has_weights) return fail(c, SIMNET_ESTATE, "train_step: no weights loaded");
-    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context");
+    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "training needs an FP32 or BF16 context of plain conv layers");
     if (c->store_queue)
         return fail(c, SIMNET_EUNSUPPORTED, "train_step: the training windows carry no store latency labels");
     CK(cudaSetDevice(c->device));
@@ -497,7 +499,7 @@ extern "C" simnet_status simnet_set_weights_device(simnet_ctx *c, const float *b
     if (!c) return SIMNET_EINVAL;
     if (!blob) return fail(c, SIMNET_EINVAL, "set_weights_device: blob is NULL");
     if (!c->has_weights) return fail(c, SIMNET_ESTATE, "set_weights_device: load weights once first");
-    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "needs an FP32 or BF16 context");
+    if (!train_precision_ok(c)) return fail(c, SIMNET_EUNSUPPORTED, "needs an FP32 or BF16 context of plain conv layers");
     CK(cudaSetDevice(c->device));
     cudaStream_t s = (cudaStream_t)stream;
     const simnet_config &k = c->cfg;
@@ -533,6 +535,10 @@ extern "C" simnet_status simnet_get_weights(simnet_ctx *c, float *blob) {
     if (!c) return SIMNET_EINVAL;
     if (!blob) return fail(c, SIMNET_EINVAL, "get_weights: blob is NULL");
     if (!c->has_weights) return fail(c, SIMNET_ESTATE, "get_weights: no weights loaded");
+    if (c->residual) {   // weights only change by load_weights: the loaded blob
+        memcpy(blob, c->blob_host.data(), c->blob_host.size() * sizeof(float));
+        return SIMNET_OK;
+    }
     CK(cudaSetDevice(c->device));
     const simnet_config &k = c->cfg;
     const int C = k.conv_channels, H = k.fc_hidden, Ln = c->rows_n;

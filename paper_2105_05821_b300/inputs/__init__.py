@@ -53,13 +53,18 @@ class Arch:
     logits (0..8 cycles and "more than 8") and one regression value, in the
     order [fetch classes 0-9, fetch value, execution classes 0-9, execution
     value].  ``store_queue``: a third latency, the store latency (Sec. 2.2),
-    after the other two, for the simulator's memory write queue (Sec. 3.2)."""
+    after the other two, for the simulator's memory write queue (Sec. 3.2).
+    ``block`` = "residual": the ``n_conv`` layers are residual blocks (the RB
+    models of Sec. 2.3), each y = ReLU(pw(ReLU(conv(x))) + proj(x)) with conv
+    and proj k=2 / stride-2 convolutions (proj without bias) and pw a
+    pointwise (k=1) convolution."""
     window: int
     n_conv: int
     channels: int
     hidden: int
     head: str = "regression"
     store_queue: bool = False
+    block: str = "conv"
 
     @property
     def n_lat(self) -> int:
@@ -80,11 +85,18 @@ class Arch:
     def shapes(self) -> List[Tuple[str, Tuple[int, ...]]]:
         """Parameter names and PyTorch shapes, in blob order."""
         out: List[Tuple[str, Tuple[int, ...]]] = []
-        cin = N_FEATURES
+        cin, C = N_FEATURES, self.channels
         for k in range(self.n_conv):
-            out.append((f"conv{k + 1}.weight", (self.channels, cin, 2)))
-            out.append((f"conv{k + 1}.bias", (self.channels,)))
-            cin = self.channels
+            if self.block == "residual":
+                out.append((f"rb{k + 1}.conv.weight", (C, cin, 2)))
+                out.append((f"rb{k + 1}.conv.bias", (C,)))
+                out.append((f"rb{k + 1}.pw.weight", (C, C, 1)))
+                out.append((f"rb{k + 1}.pw.bias", (C,)))
+                out.append((f"rb{k + 1}.proj.weight", (C, cin, 2)))
+            else:
+                out.append((f"conv{k + 1}.weight", (C, cin, 2)))
+                out.append((f"conv{k + 1}.bias", (C,)))
+            cin = C
         out.append(("fc1.weight", (self.hidden, self.fc1_in)))
         out.append(("fc1.bias", (self.hidden,)))
         out.append(("fc2.weight", (self.n_out, self.hidden)))
@@ -100,6 +112,8 @@ class Arch:
         for _ in range(self.n_conv):
             rows //= 2
             macs += rows * self.channels * cin * 2
+            if self.block == "residual":      # projection shortcut and pointwise conv
+                macs += rows * self.channels * cin * 2 + rows * self.channels * self.channels
             cin = self.channels
         macs += self.fc1_in * self.hidden + self.hidden * self.n_out
         return macs
@@ -123,6 +137,7 @@ class Workload:
 ARCH_SMALL = lambda w: Arch(window=w, n_conv=2, channels=64, hidden=256)   # noqa: E731
 ARCH_MID = Arch(window=96, n_conv=3, channels=128, hidden=512)
 ARCH_WIDE = Arch(window=128, n_conv=5, channels=256, hidden=1024)
+ARCH_RB7 = Arch(window=128, n_conv=7, channels=256, hidden=1024, head="hybrid", block="residual")
 
 WORKLOADS: Dict[str, Workload] = {
     "c1": Workload("c1", ARCH_SMALL(32), 8, 20_000, seed=1,
@@ -135,6 +150,10 @@ WORKLOADS: Dict[str, Workload] = {
                    description="4,096 sub-traces, log-normal lengths (median 8k, clip 1k-64k), W=96"),
     "c5": Workload("c5", ARCH_WIDE, 65_536, 100_000_000, seed=5,
                    description="65,536 sub-traces x ~1,526 inst (100M), W=128, 5xConv256, FC1024"),
+    # the paper's most accurate model family: residual blocks with the hybrid head
+    "rb7": Workload("rb7", ARCH_RB7, 1024, 1_024_000, seed=6,
+                    description="1,024 sub-traces x 1,000 inst, W=128, 7 residual blocks of 256 channels, "
+                                "FC1024, hybrid head"),
 }
 
 
@@ -309,6 +328,11 @@ def workload_weights(w: Workload) -> np.ndarray:
     head the class-logit rows are scaled by ``HYB_CLASS_GAIN`` and biased by
     ``HYB_CLASS_BIAS`` (a mix of direct classes and the regression output)."""
     ws = he_weights(w.arch, w.seed)
+    if w.arch.block == "residual":
+        # the two branches of a block add: scale each by 1/sqrt(2) so that the
+        # activations keep their size through the blocks
+        ws = [(n, a / np.sqrt(2.0) if (n.endswith("pw.weight") or n.endswith("proj.weight")) else a)
+              for n, a in ws]
     w2 = ws[-2][1].copy()
     b2 = np.zeros(w.arch.n_out)
     if w.arch.head == "hybrid":

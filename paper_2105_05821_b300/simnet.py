@@ -27,6 +27,8 @@ FLAG_LAYERWISE = 0x10
 FLAG_NO_CLUSTER = 0x20
 FLAG_HYBRID_HEAD = 0x40
 FLAG_STORE_QUEUE = 0x80
+FLAG_RESIDUAL = 0x100
+MAX_GEMMS = 25          # GEMMs of the deepest CNN: 3 per residual block (up to 8) + FC1
 PATHS = {0: "none", 1: "layerwise", 2: "persistent", 3: "cluster"}
 KERNEL_KINDS = 12
 KERNEL_GATHER, KERNEL_LAYER0, KERNEL_HEAD_UPDATE, KERNEL_COMPACT = 0, 1, 10, 11
@@ -159,13 +161,15 @@ class Simnet:
                  precision: str | int = "fp32", retire_width: int = 8, strict: bool = False,
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
                  pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0,
-                 cluster: bool = True, hybrid: bool = False, store_queue: bool = False):
+                 cluster: bool = True, hybrid: bool = False, store_queue: bool = False,
+                 residual: bool = False):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
                  | (0 if persistent else FLAG_LAYERWISE) | (0 if cluster else FLAG_NO_CLUSTER)
-                 | (FLAG_HYBRID_HEAD if hybrid else 0) | (FLAG_STORE_QUEUE if store_queue else 0))
+                 | (FLAG_HYBRID_HEAD if hybrid else 0) | (FLAG_STORE_QUEUE if store_queue else 0)
+                 | (FLAG_RESIDUAL if residual else 0))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, barrier_limit_us,
                             spin_limit_ns)
         self.window = window
@@ -184,6 +188,7 @@ class Simnet:
     def for_arch(cls, arch, **kw) -> "Simnet":
         kw.setdefault("hybrid", getattr(arch, "head", "regression") == "hybrid")
         kw.setdefault("store_queue", bool(getattr(arch, "store_queue", False)))
+        kw.setdefault("residual", getattr(arch, "block", "conv") == "residual")
         return cls(arch.window, arch.n_conv, arch.channels, arch.hidden, **kw)
 
     def close(self):
@@ -259,7 +264,7 @@ class Simnet:
 
     def autotune(self, n_subtraces: int, steps: int = 24, stream=None):
         """Pick per-layer tile widths for this batch size by timing; returns them."""
-        out = (C.c_int32 * 16)()
+        out = (C.c_int32 * MAX_GEMMS)()    # one tile width per GEMM of the CNN
         self._check(lib().simnet_autotune(self._h, n_subtraces, steps, out, _stream(stream)))
         return list(out)
 
