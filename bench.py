@@ -122,6 +122,16 @@ def host_cores():
     return n
 
 
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_sample_ids(w, trace, blob, target_s=15.0):
     """A bounded sample of whole sub-traces sized for ~target_s of oracle work,
     calibrated on one wave of sub-traces (one per thread)."""
@@ -413,9 +423,13 @@ def run_ours(args, rank, world):
         else:
             ids, threads = cpu_sample_ids(w, trace, blob64)
         rate, n, dt, r = oracle_rate(w, trace, blob64, ids, threads=threads)
+        rate1, n1, dt1, _ = oracle_rate(w, trace, blob64, ids[:1], threads=1)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                "sample": f"{len(ids)} whole sub-traces ({n} instructions) of the same "
-                                         f"workload, {dt:.1f} s, FP64"}
+                                         f"workload, {dt:.1f} s, FP64",
+                               "value_1_thread": rate1,
+                               "sample_1_thread": f"1 whole sub-trace ({n1} instructions), {dt1:.1f} s",
+                               "cpu_model": cpu_model(), "nproc": os.cpu_count()}
         gcyc = cyc.cpu().numpy()[ids]
         out["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids),
                                       "cpi_error": abs(float(gcyc.sum()) / float(r.cycles.sum()) - 1.0)}

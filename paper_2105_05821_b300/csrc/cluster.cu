@@ -940,6 +940,7 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     const simnet_config &k = c->cfg;
     if (k.precision != SIMNET_BF16) { why = "not BF16"; return false; }
     if (c->store_queue) { why = "memory write queue"; return false; }
+    if (c->residual) { why = "residual blocks"; return false; }
     if (k.n_conv < 2 || k.n_conv > 3) { why = "conv depth"; return false; }
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
     if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }

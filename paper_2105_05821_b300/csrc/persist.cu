@@ -44,10 +44,19 @@ struct PLayer {
     int K, N, BN, out_part, n_tiles_n;
     int cin;             // input row width in elements (FC1: channels of one input row)
     int pos_shift;       // conv: output positions computed = e << pos_shift
+    int relu;            // activation after bias (and shortcut)
+    // Pointwise GEMM of a residual block: its rows are output positions.  The
+    // pair-major [pairs * B][2N] tile is read and written as [2 * pairs * B][N]
+    // (row 2 * (pair * B + slot) + half), which is the pair-major layout of the
+    // block output again; `resid` (the block's shortcut, same view) is added
+    // before the activation.  Tiles take one pair of 64 slots (128 rows).
+    int rows_plain;
+    const void *resid;
+    int kind;            // timing kind offset: conv layer or residual block index, FC1 last
 };
 
 struct PArgs {
-    PLayer layer[kMaxConv + 1];
+    PLayer layer[kMaxGemm];
     const StepArgs *A;
     void *X;
     const float *part;
@@ -65,6 +74,7 @@ struct PArgs {
     int64_t spin_ns;
     int64_t bar_spin_ns;          // grid-barrier wait bound
     int n_layers, B, P, compact_every, stages, stage_bytes, prm_floats;
+    int n_conv;                   // conv layers or residual blocks (the pair-major extent's halvings)
     int rows_n, e_round;          // last conv rows; FC1 k-block rows (extent granularity)
 };
 
@@ -117,6 +127,9 @@ __device__ void gather_phase(const PArgs &a, uint8_t *ring, int *ext) {
         gather_rows_warp_pm<T>(a.A, reinterpret_cast<T *>(a.X), a.B, row0, total, stg, lane, ext);
 }
 
+// kernel parameters (__grid_constant__) stay under the 32 KB parameter limit
+static_assert(sizeof(PArgs) <= 32000, "persistent kernel arguments too large");
+
 struct Pipe {  // pipeline counters that carry over between GEMM phases
     int prod_it = 0, mma_it = 0, mma_tc = 0, epi_tc = 0;
 };
@@ -148,8 +161,9 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
     auto tfull = [&](int x) { return smem_u32(&bars[2 * S + x]); };
     auto tempty = [&](int x) { return smem_u32(&bars[2 * S + 2 + x]); };
     const int M = min(*a.A->n_active, a.B);                 // slots
-    const int n_sb = (M + BM - 1) / BM;
-    const int n_pos = L.out_part ? 1 : (e << L.pos_shift);  // output row positions computed
+    const int n_sb = L.rows_plain ? (M + BM / 2 - 1) / (BM / 2) : (M + BM - 1) / BM;   // slot blocks per tile
+    int n_pos = L.out_part ? 1 : (e << L.pos_shift);        // output row positions computed
+    if (L.rows_plain) n_pos = (n_pos + 1) >> 1;             // ... as pairs of positions
     const int n_tiles = n_pos * n_sb * L.n_tiles_n;
     const int KB = L.out_part ? e * L.cin / BK : L.K / BK;
     auto tile_of = [&](int t, int &pos, int &sb, int &nt) {
@@ -181,6 +195,9 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
                         const int kk = kb * BK, row = kk / L.cin;
                         ax = (row & 1) * L.cin + kk % L.cin;
                         ay = (row >> 1) * a.B + sb * BM;
+                    } else if (L.rows_plain) {   // pair `pos`, slots sb * 64 ..: 128 consecutive view rows
+                        ax = kb * BK;
+                        ay = 2 * (pos * a.B + sb * (BM / 2));
                     } else {
                         ax = kb * BK;
                         ay = pos * a.B + sb * BM;
@@ -228,7 +245,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, pp.epi_tc++) {
             int pos, sb, nt;
             tile_of(t, pos, sb, nt);
-            const int m0 = sb * BM, n0 = nt * BN;
+            const int m0 = L.rows_plain ? 2 * (pos * a.B + sb * (BM / 2)) : sb * BM, n0 = nt * BN;
             const int acc = pp.epi_tc & 1;
             const uint32_t aph = (uint32_t)(pp.epi_tc >> 1) & 1u;
             if (!mbar_wait(tfull(acc), aph, lim, cta_abort, a.status)) break;
@@ -245,12 +262,32 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
                 tmem_ld32(tbase + (uint32_t)(c * 32), r);
                 const int col0 = n0 + half * (BN / 2) + c * 32;
                 float v[32];
+                uint32_t rs[16];   // residual block: the shortcut of this row (BF16 pairs, same view)
+#pragma unroll
+                for (int j = 0; j < 16; j++) rs[j] = 0u;
+                if constexpr (!FP8) {
+                    if (L.resid && (sb * (BM / 2) + ((q * 32 + lane) >> 1)) < M) {
+                        const uint4 *rp = reinterpret_cast<const uint4 *>(
+                            reinterpret_cast<const __nv_bfloat16 *>(L.resid) + (size_t)row * N + col0);
+#pragma unroll
+                        for (int q4 = 0; q4 < 4; q4++) {
+                            const uint4 u = rp[q4];
+                            rs[4 * q4] = u.x;
+                            rs[4 * q4 + 1] = u.y;
+                            rs[4 * q4 + 2] = u.z;
+                            rs[4 * q4 + 3] = u.w;
+                        }
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 32; j++) {
                     float x = __uint_as_float(r[j]);
                     if (FP8) x *= s_scale[col0 + j];
                     if (L.out_part) x += s_cst[col0 + j];   // FC1: the constant rows past the extent
-                    x = fmaxf(x + s_bias[col0 + j], 0.f);
+                    // BF16 bits to FP32: the value's 16 bits as the high half of an FP32 word
+                    const float rv = __uint_as_float((j & 1) ? (rs[j >> 1] & 0xffff0000u) : (rs[j >> 1] << 16));
+                    x += s_bias[col0 + j] + rv;
+                    if (L.relu) x = fmaxf(x, 0.f);
                     if (FP8 && !L.out_part) x *= s_oscale[col0 + j];
                     v[j] = x;
                 }
@@ -303,15 +340,26 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
                     __syncwarp();
                     constexpr int U = CB / 16, RPP = 32 / U;
                     const int rr = lane / U, u = lane % U;
-                    // pair-major destination of output position `pos` of each slot
-                    uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) +
-                                     ((size_t)(pos >> 1) * a.B * 2 * N + (size_t)(pos & 1) * N + col0) * OES + u * 16;
+                    if (L.rows_plain) {   // view rows m0 + i, slot sb * 64 + i / 2
+                        uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) + ((size_t)m0 * N + col0) * OES + u * 16;
 #pragma unroll
-                    for (int pass = 0; pass < U; pass++) {
-                        const int r_in = pass * RPP + rr;
-                        const int slot = m0 + q * 32 + r_in;
-                        const uint4 val = *reinterpret_cast<const uint4 *>(stg + r_in * SROW + u * 16);
-                        if (slot < M) *reinterpret_cast<uint4 *>(gbase + (size_t)slot * 2 * N * OES) = val;
+                        for (int pass = 0; pass < U; pass++) {
+                            const int r_in = pass * RPP + rr, i = q * 32 + r_in;
+                            const uint4 val = *reinterpret_cast<const uint4 *>(stg + r_in * SROW + u * 16);
+                            if (sb * (BM / 2) + (i >> 1) < M)
+                                *reinterpret_cast<uint4 *>(gbase + (size_t)i * N * OES) = val;
+                        }
+                    } else {
+                        // pair-major destination of output position `pos` of each slot
+                        uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) +
+                                         ((size_t)(pos >> 1) * a.B * 2 * N + (size_t)(pos & 1) * N + col0) * OES + u * 16;
+#pragma unroll
+                        for (int pass = 0; pass < U; pass++) {
+                            const int r_in = pass * RPP + rr;
+                            const int slot = m0 + q * 32 + r_in;
+                            const uint4 val = *reinterpret_cast<const uint4 *>(stg + r_in * SROW + u * 16);
+                            if (slot < M) *reinterpret_cast<uint4 *>(gbase + (size_t)slot * 2 * N * OES) = val;
+                        }
                     }
                     __syncwarp();
                 }
@@ -385,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
     mark(SIMNET_KERNEL_GATHER);
     for (int64_t step = 0; step < a.n_steps && ok; step++) {
         int *ext_now = a.ext + (step & 1), *ext_next = a.ext + ((step + 1) & 1);
-        int e = (*(volatile int *)ext_now + (1 << (a.n_layers - 1)) - 1) >> (a.n_layers - 1);  // conv-output rows
+        int e = (*(volatile int *)ext_now + (1 << a.n_conv) - 1) >> a.n_conv;  // last conv-output rows
         e = (e + a.e_round - 1) / a.e_round * a.e_round;
         e = max(1, min(e, a.rows_n));
         if (blockIdx.x == 0 && threadIdx.x == 0) *ext_next = 0;   // the head phase raises it
@@ -393,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             const uint64_t tp = gemm_phase<FP8, NO>(a, l, e, smem, bars, prm, staging, tmem_base, cta_abort, pp);
             ok = grid_sync(a, target, cta_abort);
             if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
-            mark(SIMNET_KERNEL_LAYER0 + l);
+            mark(SIMNET_KERNEL_LAYER0 + a.layer[l].kind);
         }
         if (!ok) break;
         {   // head phase: every warp of the grid takes slots; the stage ring is its scratch
@@ -434,33 +482,49 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     int bn_max = 64, n_max = 0;
     const int BK = fp8 ? 128 : 64;
     const int C = c->cfg.conv_channels, W = c->cfg.window;
+    void *bufs[6] = {c->X, c->act[0], c->act[1], c->tmpA, c->tmpS, c->h1};
     for (int l = 0; l < c->n_layers; l++) {
         const TcPlan &p = c->plan[l];
         const GemmLayer &g = c->layer[l];
         PLayer &L = a.layer[l];
         const bool fc1 = l == c->n_layers - 1;
-        // input rows of this layer and its pair-major view [pairs * B][2 * row width]
-        const int in_rows = W >> l;
-        const int row_w = l == 0 ? kNFP : C;
-        const void *in = l == 0 ? c->X : c->act[(l - 1) & 1];
-        if (!encode_map_2d(L.tA, c->cfg.precision, in, (uint64_t)2 * row_w, (uint64_t)((in_rows + 1) / 2) * B, BK,
-                           BM, why))
-            return false;
+        const int blk = fc1 ? c->cfg.n_conv : c->residual ? l / 3 : l;   // conv layer / residual block
+        const bool pw = c->residual && !fc1 && l % 3 == 2;
+        const void *in = bufs[g.in_buf];
+        if (pw) {
+            // positions of the block output viewed as [2 * pairs * B][C]
+            const int rows_out = W >> (blk + 1);
+            if (!encode_map_2d(L.tA, c->cfg.precision, in, (uint64_t)C, (uint64_t)2 * ((rows_out + 1) / 2) * B, BK,
+                               BM, why))
+                return false;
+        } else {
+            // input rows of this layer and its pair-major view [pairs * B][2 * row width]
+            const int in_rows = W >> blk;
+            const int row_w = blk == 0 ? kNFP : C;
+            if (!encode_map_2d(L.tA, c->cfg.precision, in, (uint64_t)2 * row_w, (uint64_t)((in_rows + 1) / 2) * B, BK,
+                               BM, why))
+                return false;
+        }
         L.tB = p.tB;
         L.bias = g.bias;
         L.scale = g.scale;
         L.oscale = g.oscale;
-        L.out = fc1 ? (void *)c->h1 : c->act[l & 1];
+        L.out = bufs[g.out_buf];
         L.K = g.K;
         L.N = g.N;
         L.BN = p.BN;
         L.out_part = fc1;
         L.n_tiles_n = g.N / p.BN;
-        L.cin = row_w;
-        L.pos_shift = fc1 ? 0 : c->cfg.n_conv - 1 - l;
+        L.cin = blk == 0 ? kNFP : C;
+        L.pos_shift = fc1 ? 0 : c->cfg.n_conv - 1 - blk;
+        L.relu = g.relu;
+        L.rows_plain = pw;
+        L.resid = g.res_buf >= 0 ? bufs[g.res_buf] : nullptr;
+        L.kind = g.kind;
         bn_max = std::max(bn_max, p.BN);
         n_max = std::max(n_max, g.N);
     }
+    a.n_conv = c->cfg.n_conv;
     a.fc1_const = c->fc1_const;
     a.ext = c->ext;
     a.rows_n = c->rows_n;
@@ -475,7 +539,8 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.status = c->status;
     a.phase_ns = c->phase_on ? c->phase_ns : nullptr;
     a.phase_n = c->phase_on ? c->phase_n : nullptr;
-    a.detail = c->phase_on ? c->phase_ns + 16 : nullptr;
+    // per-GEMM detail has room for the layers of a plain CNN (4 counters each)
+    a.detail = c->phase_on && c->n_layers <= kMaxConv + 1 ? c->phase_ns + 16 : nullptr;
     a.n_steps = n_steps;
     a.spin_ns = c->cfg.spin_limit_ns;
     a.bar_spin_ns = c->cfg.barrier_limit_us > 0 ? (int64_t)c->cfg.barrier_limit_us * 1000 : c->cfg.spin_limit_ns;

@@ -300,18 +300,34 @@ simnet_status build_fc1_const(simnet_ctx *c, const std::vector<std::vector<float
     };
     std::vector<double> cst(kNFP, 0.0);
     int cin_pad = kNFP;
-    for (int l = 0; l < k.n_conv; l++) {
+    // a k=2 / stride-2 GEMM layer on a pair of constant rows (bias, optional ReLU, stored rounding)
+    auto pair_layer = [&](int l, int cp, bool relu) {
         const int K = c->layer[l].K;
         std::vector<double> nxt(C);
         for (int n = 0; n < C; n++) {
             double acc = Bg[l][n];
-            for (int kk = 0; kk < K; kk++) acc += (double)Wdeq[l][(size_t)n * K + kk] * cst[kk % cin_pad];
-            nxt[n] = quant(l, n, acc > 0.0 ? acc : 0.0);
+            for (int kk = 0; kk < K; kk++) acc += (double)Wdeq[l][(size_t)n * K + kk] * cst[kk % cp];
+            nxt[n] = quant(l, n, relu && acc < 0.0 ? 0.0 : acc);
         }
-        cst = nxt;
+        return nxt;
+    };
+    for (int b = 0; b < k.n_conv; b++) {
+        if (!c->residual) {
+            cst = pair_layer(b, cin_pad, true);
+        } else {   // residual block: branch a, shortcut s, then ReLU(pw(a) + s)
+            const std::vector<double> a_c = pair_layer(3 * b, cin_pad, true), s_c = pair_layer(3 * b + 1, cin_pad, false);
+            const int l = 3 * b + 2;
+            std::vector<double> nxt(C);
+            for (int n = 0; n < C; n++) {
+                double acc = Bg[l][n] + s_c[n];
+                for (int j = 0; j < C; j++) acc += (double)Wdeq[l][(size_t)n * C + j] * a_c[j];
+                nxt[n] = quant(l, n, acc > 0.0 ? acc : 0.0);
+            }
+            cst = nxt;
+        }
         cin_pad = C;
     }
-    const int L = k.n_conv, K1 = c->fc1_in;
+    const int L = c->n_layers - 1, K1 = c->fc1_in;
     std::vector<float> S((size_t)(Ln + 1) * H, 0.f);
     for (int n = 0; n < H; n++) {
         double run = 0.0;
@@ -464,8 +480,7 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     }
     if ((st = upload(c, (void **)&c->w2, w2)) != SIMNET_OK) return st;
     if ((st = upload(c, (void **)&c->b2, b2)) != SIMNET_OK) return st;
-    if (k.precision != SIMNET_FP32 && !c->residual && (st = build_fc1_const(c, Bg, Wdeq, osc)) != SIMNET_OK)
-        return st;
+    if (k.precision != SIMNET_FP32 && (st = build_fc1_const(c, Bg, Wdeq, osc)) != SIMNET_OK) return st;
     if (c->residual) c->blob_host.assign(blob, blob + n_values);
     c->weights_fp = fnv1a(blob, (size_t)n_values * sizeof(float));
     c->weights_fp_dirty = false;
@@ -796,8 +811,7 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
         c->kt_valid = false;
     }
     c->phase_valid = false;
-    // residual blocks run as per-layer kernels (the single-launch kernels hold plain conv layers)
-    const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE) && !c->residual;
+    const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE);
     std::string why_not_cluster;
     if (n_steps <= 0) {
         launches = resume ? 0 : 1;
