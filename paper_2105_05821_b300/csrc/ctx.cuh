@@ -102,6 +102,12 @@ struct simnet_ctx {
     // and the batch extent per step parity
     float *fc1_const = nullptr;
     int *ext = nullptr;
+    // per-layer extent: each conv-stack layer's constant output row in storage
+    // units ([n_layers - 1][C]) and the layers' private output tiles (pair-major,
+    // sized for pbuf_B sub-traces) that keep those constants past the extent
+    float *layer_const = nullptr;
+    void *pbuf[kMaxGemm] = {};
+    int pbuf_B = 0;
 
     // autotuned tile widths: tuned_bn[l] applies to batches of tuned_B sub-traces
     int tuned_B = -1;

@@ -53,6 +53,11 @@ struct PLayer {
     int rows_plain;
     const void *resid;
     int kind;            // timing kind offset: conv layer or residual block index, FC1 last
+    // per-layer extent: output position p covers input rows [p << pos_log, (p + 1) << pos_log)
+    // of the window; positions at or past ceil(extent / 2^pos_log) see only padding rows and
+    // hold the constant row `cst` (storage units [N]); rows_out = the layer's positions
+    int pos_log, rows_out;
+    const float *cst;
 };
 
 struct PArgs {
@@ -134,9 +139,31 @@ struct Pipe {  // pipeline counters that carry over between GEMM phases
     int prod_it = 0, mma_it = 0, mma_tc = 0, epi_tc = 0;
 };
 
+// Positions [lo, hi) of every slot below M in a layer's pair-major output tile
+// get the layer's constant row; the epilogue warps of the grid share the work.
+template <typename T>
+__device__ void fill_const(const PArgs &a, const PLayer &L, int lo, int hi, int M) {
+    if (lo >= hi) return;
+    constexpr int V = Vec<T>::N;
+    const int N = L.N, chunks = N / V;
+    const int64_t total = (int64_t)(hi - lo) * M * chunks;
+    const int64_t nth = (int64_t)gridDim.x * 32 * kEpiWarps;
+    for (int64_t i = (int64_t)blockIdx.x * 32 * kEpiWarps + (threadIdx.x - 64); i < total; i += nth) {
+        const int ch = (int)(i % chunks);
+        const int64_t r = i / chunks;
+        const int slot = (int)(r % M), pos = lo + (int)(r / M);
+        float v[V];
+#pragma unroll
+        for (int j = 0; j < V; j++) v[j] = L.cst[ch * V + j];
+        T *dst = reinterpret_cast<T *>(L.out) + ((size_t)(pos >> 1) * a.B + slot) * 2 * N + (size_t)(pos & 1) * N +
+                 ch * V;
+        store16<T>(dst, v);
+    }
+}
+
 template <bool FP8, int NO>
-__device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint64_t *bars, float *prm,
-                               uint8_t *staging, uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
+__device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_prev, uint8_t *smem, uint64_t *bars,
+                               float *prm, uint8_t *staging, uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
     const PLayer &L = a.layer[l];
     constexpr int BK = FP8 ? 128 : 64;
     const int S = a.stages, N = L.N, BN = L.BN;
@@ -162,7 +189,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
     auto tempty = [&](int x) { return smem_u32(&bars[2 * S + 2 + x]); };
     const int M = min(*a.A->n_active, a.B);                 // slots
     const int n_sb = L.rows_plain ? (M + BM / 2 - 1) / (BM / 2) : (M + BM - 1) / BM;   // slot blocks per tile
-    int n_pos = L.out_part ? 1 : (e << L.pos_shift);        // output row positions computed
+    int n_pos = L.out_part ? 1 : n_now;                     // output row positions computed
     if (L.rows_plain) n_pos = (n_pos + 1) >> 1;             // ... as pairs of positions
     const int n_tiles = n_pos * n_sb * L.n_tiles_n;
     const int KB = L.out_part ? e * L.cin / BK : L.K / BK;
@@ -237,6 +264,12 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, uint8_t *smem, uint
         }
         __syncwarp();
     } else {
+        // positions this step no longer computes get the constant row first (the
+        // pointwise phase computes whole pairs)
+        if (!L.out_part) {
+            using T = typename std::conditional<FP8, __nv_fp8_e4m3, __nv_bfloat16>::type;
+            fill_const<T>(a, L, L.rows_plain ? (n_now + 1) & ~1 : n_now, n_prev, M);
+        }
         const int q = warp & 3, half = (warp - 2) >> 2;
         const int CPW = BN / 64;
         constexpr int OES = FP8 ? 1 : 2;
@@ -431,19 +464,29 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
     gather_phase<T>(a, smem, a.ext);
     bool ok = grid_sync(a, target, cta_abort);
     mark(SIMNET_KERNEL_GATHER);
+    // positions per layer for a batch extent x (rows in use: the longest context + 1)
+    auto layer_pos = [&](const PLayer &L, int x) {
+        return max(1, min(L.rows_out, (x + (1 << L.pos_log) - 1) >> L.pos_log));
+    };
+    int ext_prev = a.A->window;   // tiles hold stale rows at the start: fill every position
     for (int64_t step = 0; step < a.n_steps && ok; step++) {
         int *ext_now = a.ext + (step & 1), *ext_next = a.ext + ((step + 1) & 1);
-        int e = (*(volatile int *)ext_now + (1 << a.n_conv) - 1) >> a.n_conv;  // last conv-output rows
+        const int ext = *(volatile int *)ext_now;
+        int e = (ext + (1 << a.n_conv) - 1) >> a.n_conv;  // last conv-output rows
         e = (e + a.e_round - 1) / a.e_round * a.e_round;
         e = max(1, min(e, a.rows_n));
         if (blockIdx.x == 0 && threadIdx.x == 0) *ext_next = 0;   // the head phase raises it
         for (int l = 0; l < a.n_layers && ok; l++) {
-            const uint64_t tp = gemm_phase<FP8, NO>(a, l, e, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+            const PLayer &L = a.layer[l];
+            const int n_now = L.out_part ? 1 : layer_pos(L, ext), n_prev = L.out_part ? 1 : layer_pos(L, ext_prev);
+            const uint64_t tp =
+                gemm_phase<FP8, NO>(a, l, e, n_now, n_prev, smem, bars, prm, staging, tmem_base, cta_abort, pp);
             ok = grid_sync(a, target, cta_abort);
             if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
             mark(SIMNET_KERNEL_LAYER0 + a.layer[l].kind);
         }
         if (!ok) break;
+        ext_prev = ext;
         {   // head phase: every warp of the grid takes slots; the stage ring is its scratch
             constexpr int PER = 256 * 8 + 32 * stage_row_bytes<T>();
             uint8_t *mine = smem + warp * PER;
@@ -462,6 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             gather_phase<T>(a, smem, ext_next);
             ok = grid_sync(a, target, cta_abort);
             mark(SIMNET_KERNEL_GATHER);
+            ext_prev = a.A->window;   // slots moved: every tile position is stale
         }
     }
     tc_fence_before();
@@ -482,7 +526,22 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     int bn_max = 64, n_max = 0;
     const int BK = fp8 ? 128 : 64;
     const int C = c->cfg.conv_channels, W = c->cfg.window;
-    void *bufs[6] = {c->X, c->act[0], c->act[1], c->tmpA, c->tmpS, c->h1};
+    // every conv-stack layer writes its own pair-major tile (the per-layer extent keeps
+    // constant rows in it past the extent, so tiles cannot be shared between layers)
+    const size_t es = fp8 ? 1 : 2;
+    if (c->pbuf_B < B) {
+        for (auto &q : c->pbuf)
+            if (q) { cudaFree(q); q = nullptr; }
+        c->pbuf_B = 0;
+        for (int l = 0; l + 1 < c->n_layers; l++) {
+            const int blk = c->residual ? l / 3 : l, rows_out = W >> (blk + 1);
+            const size_t bytes = (size_t)B * (2 * ((rows_out + 1) / 2)) * C * es;
+            if (cudaMalloc(&c->pbuf[l], bytes) != cudaSuccess) { why = "out of memory for layer tiles"; return false; }
+        }
+        c->pbuf_B = B;
+    }
+    // the layer that last wrote each workspace buffer id (inputs follow the producers)
+    int writer[6] = {-1, -1, -1, -1, -1, -1};
     for (int l = 0; l < c->n_layers; l++) {
         const TcPlan &p = c->plan[l];
         const GemmLayer &g = c->layer[l];
@@ -490,7 +549,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         const bool fc1 = l == c->n_layers - 1;
         const int blk = fc1 ? c->cfg.n_conv : c->residual ? l / 3 : l;   // conv layer / residual block
         const bool pw = c->residual && !fc1 && l % 3 == 2;
-        const void *in = bufs[g.in_buf];
+        const void *in = g.in_buf == kBufX ? c->X : c->pbuf[writer[g.in_buf]];
         if (pw) {
             // positions of the block output viewed as [2 * pairs * B][C]
             const int rows_out = W >> (blk + 1);
@@ -509,7 +568,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         L.bias = g.bias;
         L.scale = g.scale;
         L.oscale = g.oscale;
-        L.out = bufs[g.out_buf];
+        L.out = fc1 ? (void *)c->h1 : c->pbuf[l];
         L.K = g.K;
         L.N = g.N;
         L.BN = p.BN;
@@ -519,8 +578,12 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         L.pos_shift = fc1 ? 0 : c->cfg.n_conv - 1 - blk;
         L.relu = g.relu;
         L.rows_plain = pw;
-        L.resid = g.res_buf >= 0 ? bufs[g.res_buf] : nullptr;
+        L.resid = g.res_buf >= 0 ? c->pbuf[writer[g.res_buf]] : nullptr;
         L.kind = g.kind;
+        L.pos_log = blk + 1;
+        L.rows_out = fc1 ? 1 : W >> (blk + 1);
+        L.cst = fc1 ? nullptr : c->layer_const + (size_t)l * C;
+        if (!fc1) writer[g.out_buf] = l;
         bn_max = std::max(bn_max, p.BN);
         n_max = std::max(n_max, g.N);
     }

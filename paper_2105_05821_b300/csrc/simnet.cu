@@ -137,6 +137,9 @@ static void free_workspace(simnet_ctx *c) {
     c->totals = nullptr;
     c->d_args = nullptr;
     c->ws_B = 0;
+    for (auto &q : c->pbuf)
+        if (q) { cudaFree(q); q = nullptr; }
+    c->pbuf_B = 0;
     for (auto &g : c->gexec)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     c->g_B = -1;
@@ -166,6 +169,7 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     }
     if (c->w2) cudaFree(c->w2);
     if (c->b2) cudaFree(c->b2);
+    if (c->layer_const) cudaFree(c->layer_const);
     if (c->h_args) cudaFreeHost(c->h_args);
     if (c->h_offsets) cudaFreeHost(c->h_offsets);
     if (c->h_totals) cudaFreeHost(c->h_totals);
@@ -298,6 +302,13 @@ simnet_status build_fc1_const(simnet_ctx *c, const std::vector<std::vector<float
         const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8((float)x * o, __NV_SATFINITE, __NV_E4M3);
         return (double)__half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3))) / o;
     };
+    // each layer's constant output row as the kernels store it (BF16, or the FP8 byte
+    // of value * requant multiplier), for the persistent kernel's per-layer extent
+    std::vector<float> lc((size_t)(c->n_layers - 1) * C, 0.f);
+    auto keep = [&](int l, const std::vector<double> &v) {
+        for (int n = 0; n < C; n++)
+            lc[(size_t)l * C + n] = k.precision == SIMNET_BF16 ? (float)v[n] : (float)(v[n] * osc[l][n]);
+    };
     std::vector<double> cst(kNFP, 0.0);
     int cin_pad = kNFP;
     // a k=2 / stride-2 GEMM layer on a pair of constant rows (bias, optional ReLU, stored rounding)
@@ -309,6 +320,7 @@ simnet_status build_fc1_const(simnet_ctx *c, const std::vector<std::vector<float
             for (int kk = 0; kk < K; kk++) acc += (double)Wdeq[l][(size_t)n * K + kk] * cst[kk % cp];
             nxt[n] = quant(l, n, relu && acc < 0.0 ? 0.0 : acc);
         }
+        keep(l, nxt);
         return nxt;
     };
     for (int b = 0; b < k.n_conv; b++) {
@@ -323,10 +335,13 @@ simnet_status build_fc1_const(simnet_ctx *c, const std::vector<std::vector<float
                 for (int j = 0; j < C; j++) acc += (double)Wdeq[l][(size_t)n * C + j] * a_c[j];
                 nxt[n] = quant(l, n, acc > 0.0 ? acc : 0.0);
             }
+            keep(l, nxt);
             cst = nxt;
         }
         cin_pad = C;
     }
+    simnet_status st0 = upload(c, (void **)&c->layer_const, lc);
+    if (st0 != SIMNET_OK) return st0;
     const int L = c->n_layers - 1, K1 = c->fc1_in;
     std::vector<float> S((size_t)(Ln + 1) * H, 0.f);
     for (int n = 0; n < H; n++) {
