@@ -201,7 +201,8 @@ def workload_config(w, args, note=""):
 
 # ----------------------------------------------------------------------------- our arm
 def algorithmic_units(w: I.Workload, kind: int, n_active: float, prec: str):
-    """(amount, unit, bound) per launch of kernel `kind` for n_active sub-traces."""
+    """(amount, unit, bound) per step of kernel kind `kind` for n_active
+    sub-traces (a residual block's kind covers its three GEMMs)."""
     a = w.arch
     es = {"fp32": 4, "bf16": 2, "fp8": 1}[prec]
     if 1 <= kind <= a.n_conv + 1:
@@ -210,9 +211,8 @@ def algorithmic_units(w: I.Workload, kind: int, n_active: float, prec: str):
             rows = a.window >> (l + 1)
             cin = I.N_FEATURES if l == 0 else a.channels
             macs = rows * a.channels * cin * 2
-            if a.block == "residual":   # the block's three GEMMs (conv, projection, pointwise),
-                # three launches of this kind a step: the per-launch average
-                macs = (2 * rows * a.channels * cin * 2 + rows * a.channels * a.channels) / 3.0
+            if a.block == "residual":   # the block's three GEMMs: conv, projection, pointwise
+                macs = 2 * rows * a.channels * cin * 2 + rows * a.channels * a.channels
         else:
             macs = a.fc1_in * a.hidden
         return 2.0 * macs * n_active, "flop", ("alu" if prec == "fp32" else "tensor")
@@ -476,7 +476,7 @@ def roofline(w, args, blob32, rec, off, cyc, B):
     ms, n = sim.kernel_times()
     sim.close()
     total = sum(ms)
-    steps = max(n[0], 1)
+    steps = max(n[10], 1)   # head/update: one launch (or phase) a step
     kernels = {}
     for k in range(len(ms)):
         if n[k] == 0:
@@ -486,6 +486,8 @@ def roofline(w, args, blob32, rec, off, cyc, B):
                                     "avg_us": 1e3 * ms[k] / n[k], "bound": bound}
     dom = max(range(len(ms)), key=lambda k: ms[k])
     amt, unit, bound = algorithmic_units(w, dom, B, args.precision)
+    # per launch: the kind's per-step work over its launches (or phases) a step
+    amt = amt * steps / n[dom]
     avg_s = ms[dom] / n[dom] / 1e3
     if unit == "flop":
         achieved = amt / avg_s / 1e12

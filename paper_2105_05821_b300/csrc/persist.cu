@@ -58,6 +58,7 @@ struct PLayer {
     // hold the constant row `cst` (storage units [N]); rows_out = the layer's positions
     int pos_log, rows_out;
     const float *cst;
+    int pair_next;       // layer l + 1 (same input, K and N) runs in this layer's phase
 };
 
 struct PArgs {
@@ -161,12 +162,16 @@ __device__ void fill_const(const PArgs &a, const PLayer &L, int lo, int hi, int 
     }
 }
 
+// One GEMM phase: the tiles of layer l, or of layers l and l2 together (a residual
+// block's conv and projection: same input and shape, independent outputs, so one
+// phase and one grid barrier serve both; tiles [0, T0) are layer l's).
 template <bool FP8, int NO>
-__device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_prev, uint8_t *smem, uint64_t *bars,
-                               float *prm, uint8_t *staging, uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
+__device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, int n_prev, uint8_t *smem,
+                               uint64_t *bars, float *prm, uint8_t *staging, uint32_t tmem_base,
+                               volatile int *cta_abort, Pipe &pp) {
     const PLayer &L = a.layer[l];
     constexpr int BK = FP8 ? 128 : 64;
-    const int S = a.stages, N = L.N, BN = L.BN;
+    const int S = a.stages, N = L.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *s_bias = prm, *s_scale = prm + N, *s_oscale = prm + 2 * N, *s_w2 = prm + 3 * N, *s_cst = prm + 5 * N;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -180,6 +185,14 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
             s_w2[i] = a.w2[i];
             s_w2[N + i] = a.w2[N + i];
         }
+        if (l2 >= 0) {   // the second layer's parameters (conv-stack layers use no FC2 / padding table)
+            const PLayer &L2 = a.layer[l2];
+            prm[3 * N + i] = L2.bias[i];
+            if (FP8) {
+                prm[4 * N + i] = L2.scale[i];
+                prm[5 * N + i] = L2.oscale ? L2.oscale[i] : 1.f;
+            }
+        }
     }
     __syncthreads();
     const uint32_t smem_base = smem_u32(smem);
@@ -191,16 +204,20 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
     const int n_sb = L.rows_plain ? (M + BM / 2 - 1) / (BM / 2) : (M + BM - 1) / BM;   // slot blocks per tile
     int n_pos = L.out_part ? 1 : n_now;                     // output row positions computed
     if (L.rows_plain) n_pos = (n_pos + 1) >> 1;             // ... as pairs of positions
-    const int n_tiles = n_pos * n_sb * L.n_tiles_n;
-    const int KB = L.out_part ? e * L.cin / BK : L.K / BK;
-    auto tile_of = [&](int t, int &pos, int &sb, int &nt) {
-        nt = t % L.n_tiles_n;
-        const int r = t / L.n_tiles_n;
+    const int T0 = n_pos * n_sb * L.n_tiles_n;
+    const int n_tiles = T0 + (l2 >= 0 ? n_pos * n_sb * a.layer[l2].n_tiles_n : 0);
+    const int KB = L.out_part ? e * L.cin / BK : L.K / BK;   // the paired layer has the same K
+    // tile t -> its layer (0: l, 1: l2), input position (pair), slot block, column block
+    auto tile_of = [&](int t, int &which, int &pos, int &sb, int &nt) {
+        which = (!FP8 && t >= T0) ? 1 : 0;   // residual blocks (the only pairs) are BF16
+        if (which) t -= T0;
+        const int ntn = which ? a.layer[l2].n_tiles_n : L.n_tiles_n;
+        nt = t % ntn;
+        const int r = t / ntn;
         sb = r % n_sb;
         pos = r / n_sb;
     };
     const int64_t lim = a.spin_ns;
-    const uint32_t stage_tx = (uint32_t)(A_BYTES + BN * ROW_BYTES);
     const bool det = a.detail && blockIdx.x == 0;
     const uint64_t t_phase = det ? gtimer() : 0;
     if (warp == 0) {
@@ -208,9 +225,11 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
             asm volatile("fence.proxy.async.global;" ::: "memory");
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-                int pos, sb, nt;
-                tile_of(t, pos, sb, nt);
-                const int n0 = nt * BN;
+                int which, pos, sb, nt;
+                tile_of(t, which, pos, sb, nt);
+                const PLayer &Lt = which ? a.layer[l2] : L;
+                const int n0 = nt * Lt.BN;
+                const uint32_t stage_tx = (uint32_t)(A_BYTES + Lt.BN * ROW_BYTES);
                 for (int kb = 0; kb < KB; kb++, pp.prod_it++) {
                     const int s = pp.prod_it % S;
                     const uint32_t ph = (uint32_t)(pp.prod_it / S) & 1u;
@@ -231,15 +250,15 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
                     }
                     mbar_expect_tx(full(s), stage_tx);
                     tma_load_2d(sa, &L.tA, full(s), ax, ay);
-                    tma_load_2d(sa + A_BYTES, &L.tB, full(s), kb * BK, n0);
+                    tma_load_2d(sa + A_BYTES, &Lt.tB, full(s), kb * BK, n0);
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t ID = idesc_rt(BN, FP8);
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, pp.mma_tc++) {
+                const uint32_t ID = idesc_rt((!FP8 && t >= T0) ? a.layer[l2].BN : L.BN, FP8);
                 const int acc = pp.mma_tc & 1;
                 const uint32_t aph = (uint32_t)(pp.mma_tc >> 1) & 1u;
                 if (!mbar_wait(tempty(acc), aph ^ 1u, lim, cta_abort, a.status)) break;
@@ -269,15 +288,20 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
         if (!L.out_part) {
             using T = typename std::conditional<FP8, __nv_fp8_e4m3, __nv_bfloat16>::type;
             fill_const<T>(a, L, L.rows_plain ? (n_now + 1) & ~1 : n_now, n_prev, M);
+            if (l2 >= 0) fill_const<T>(a, a.layer[l2], n_now, n_prev, M);
         }
         const int q = warp & 3, half = (warp - 2) >> 2;
-        const int CPW = BN / 64;
         constexpr int OES = FP8 ? 1 : 2;
         constexpr int CB = 32 * OES, SROW = CB + 16;
         uint8_t *stg = staging + (warp - 2) * 32 * SROW;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, pp.epi_tc++) {
-            int pos, sb, nt;
-            tile_of(t, pos, sb, nt);
+            int which, pos, sb, nt;
+            tile_of(t, which, pos, sb, nt);
+            const PLayer &Lt = which ? a.layer[l2] : L;
+            const int BN = Lt.BN, CPW = BN / 64;
+            // this tile's layer parameters: the paired layer's sit 3N floats further
+            const float *t_bias = s_bias + (which ? 3 * N : 0), *t_scale = s_scale + (which ? 3 * N : 0),
+                        *t_oscale = s_oscale + (which ? 3 * N : 0);
             const int m0 = L.rows_plain ? 2 * (pos * a.B + sb * (BM / 2)) : sb * BM, n0 = nt * BN;
             const int acc = pp.epi_tc & 1;
             const uint32_t aph = (uint32_t)(pp.epi_tc >> 1) & 1u;
@@ -315,13 +339,13 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
 #pragma unroll
                 for (int j = 0; j < 32; j++) {
                     float x = __uint_as_float(r[j]);
-                    if (FP8) x *= s_scale[col0 + j];
+                    if (FP8) x *= t_scale[col0 + j];
                     if (L.out_part) x += s_cst[col0 + j];   // FC1: the constant rows past the extent
                     // BF16 bits to FP32: the value's 16 bits as the high half of an FP32 word
                     const float rv = __uint_as_float((j & 1) ? (rs[j >> 1] & 0xffff0000u) : (rs[j >> 1] << 16));
-                    x += s_bias[col0 + j] + rv;
-                    if (L.relu) x = fmaxf(x, 0.f);
-                    if (FP8 && !L.out_part) x *= s_oscale[col0 + j];
+                    x += t_bias[col0 + j] + rv;
+                    if (Lt.relu) x = fmaxf(x, 0.f);
+                    if (FP8 && !L.out_part) x *= t_oscale[col0 + j];
                     v[j] = x;
                 }
                 if (L.out_part) {
@@ -374,7 +398,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
                     constexpr int U = CB / 16, RPP = 32 / U;
                     const int rr = lane / U, u = lane % U;
                     if (L.rows_plain) {   // view rows m0 + i, slot sb * 64 + i / 2
-                        uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) + ((size_t)m0 * N + col0) * OES + u * 16;
+                        uint8_t *gbase = reinterpret_cast<uint8_t *>(Lt.out) + ((size_t)m0 * N + col0) * OES + u * 16;
 #pragma unroll
                         for (int pass = 0; pass < U; pass++) {
                             const int r_in = pass * RPP + rr, i = q * 32 + r_in;
@@ -384,7 +408,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int e, int n_now, int n_pr
                         }
                     } else {
                         // pair-major destination of output position `pos` of each slot
-                        uint8_t *gbase = reinterpret_cast<uint8_t *>(L.out) +
+                        uint8_t *gbase = reinterpret_cast<uint8_t *>(Lt.out) +
                                          ((size_t)(pos >> 1) * a.B * 2 * N + (size_t)(pos & 1) * N + col0) * OES + u * 16;
 #pragma unroll
                         for (int pass = 0; pass < U; pass++) {
@@ -479,8 +503,10 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         for (int l = 0; l < a.n_layers && ok; l++) {
             const PLayer &L = a.layer[l];
             const int n_now = L.out_part ? 1 : layer_pos(L, ext), n_prev = L.out_part ? 1 : layer_pos(L, ext_prev);
+            const int l2 = L.pair_next ? l + 1 : -1;   // a residual block's conv takes its projection along
             const uint64_t tp =
-                gemm_phase<FP8, NO>(a, l, e, n_now, n_prev, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+                gemm_phase<FP8, NO>(a, l, l2, e, n_now, n_prev, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+            if (l2 >= 0) l++;
             ok = grid_sync(a, target, cta_abort);
             if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
             mark(SIMNET_KERNEL_LAYER0 + a.layer[l].kind);
@@ -581,6 +607,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         L.resid = g.res_buf >= 0 ? c->pbuf[writer[g.res_buf]] : nullptr;
         L.kind = g.kind;
         L.pos_log = blk + 1;
+        L.pair_next = c->residual && !fc1 && l % 3 == 0;
         L.rows_out = fc1 ? 1 : W >> (blk + 1);
         L.cst = fc1 ? nullptr : c->layer_const + (size_t)l * C;
         if (!fc1) writer[g.out_buf] = l;
