@@ -59,6 +59,8 @@ struct PLayer {
     int pos_log, rows_out;
     const float *cst;
     int pair_next;       // layer l + 1 (same input, K and N) runs in this layer's phase
+    int prm_off;         // this layer's parameters in shared memory (staged once per call):
+                         // bias [N], FP8 scale [N] and requant [N], FC1 with 2 outputs: FC2 rows [2N]
 };
 
 struct PArgs {
@@ -81,6 +83,8 @@ struct PArgs {
     int64_t bar_spin_ns;          // grid-barrier wait bound
     int n_layers, B, P, compact_every, stages, stage_bytes, prm_floats;
     int n_conv;                   // conv layers or residual blocks (the pair-major extent's halvings)
+    int w2h_off;                  // hybrid / store heads: per-epilogue-warp FC2 row slices at prm + w2h_off
+    int cst_off;                  // FC1's padding row S[e] of the current step at prm + cst_off
     int rows_n, e_round;          // last conv rows; FC1 k-block rows (extent granularity)
 };
 
@@ -173,28 +177,13 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
     constexpr int BK = FP8 ? 128 : 64;
     const int S = a.stages, N = L.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *s_bias = prm, *s_scale = prm + N, *s_oscale = prm + 2 * N, *s_w2 = prm + 3 * N, *s_cst = prm + 5 * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        s_bias[i] = L.bias[i];
-        if (L.out_part) s_cst[i] = a.fc1_const[(size_t)e * N + i];
-        if (FP8) {
-            s_scale[i] = L.scale[i];
-            s_oscale[i] = L.oscale ? L.oscale[i] : 1.f;
-        }
-        if (NO == 2 && L.out_part) {   // the hybrid head's 22 FC2 rows are read through L1
-            s_w2[i] = a.w2[i];
-            s_w2[N + i] = a.w2[N + i];
-        }
-        if (l2 >= 0) {   // the second layer's parameters (conv-stack layers use no FC2 / padding table)
-            const PLayer &L2 = a.layer[l2];
-            prm[3 * N + i] = L2.bias[i];
-            if (FP8) {
-                prm[4 * N + i] = L2.scale[i];
-                prm[5 * N + i] = L2.oscale ? L2.oscale[i] : 1.f;
-            }
-        }
+    // parameters were staged at the start of the call; only FC1's padding row changes per step
+    float *s_bias = prm + L.prm_off, *s_scale = s_bias + N, *s_oscale = s_bias + 2 * N;
+    float *s_w2 = s_bias + (FP8 ? 3 * N : N), *s_cst = prm + a.cst_off;
+    if (L.out_part) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) s_cst[i] = a.fc1_const[(size_t)e * N + i];
+        __syncthreads();
     }
-    __syncthreads();
     const uint32_t smem_base = smem_u32(smem);
     auto full = [&](int s) { return smem_u32(&bars[s]); };
     auto empty = [&](int s) { return smem_u32(&bars[S + s]); };
@@ -299,9 +288,8 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
             tile_of(t, which, pos, sb, nt);
             const PLayer &Lt = which ? a.layer[l2] : L;
             const int BN = Lt.BN, CPW = BN / 64;
-            // this tile's layer parameters: the paired layer's sit 3N floats further
-            const float *t_bias = s_bias + (which ? 3 * N : 0), *t_scale = s_scale + (which ? 3 * N : 0),
-                        *t_oscale = s_oscale + (which ? 3 * N : 0);
+            // this tile's layer parameters
+            const float *t_bias = prm + Lt.prm_off, *t_scale = t_bias + N, *t_oscale = t_bias + 2 * N;
             const int m0 = L.rows_plain ? 2 * (pos * a.B + sb * (BM / 2)) : sb * BM, n0 = nt * BN;
             const int acc = pp.epi_tc & 1;
             const uint32_t aph = (uint32_t)(pp.epi_tc >> 1) & 1u;
@@ -356,16 +344,23 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                             pe = fmaf(v[j], s_w2[N + col0 + j], pe);
                         }
                     } else {
+                        // this warp's 32 columns of the NH FC2 rows, staged in its own shared
+                        // slice (coalesced loads, no cross-warp wait), then read as broadcasts
+                        float *myw = prm + a.w2h_off + (warp - 2) * NH * 32;
+#pragma unroll
+                        for (int o = 0; o < NH; o++) myw[o * 32 + lane] = __ldg(a.w2 + (size_t)o * N + col0 + lane);
+                        __syncwarp();
 #pragma unroll
                         for (int o = 0; o < NH; o++) {
-                            const float4 *wr = reinterpret_cast<const float4 *>(a.w2 + (size_t)o * N + col0);
+                            const float4 *wr = reinterpret_cast<const float4 *>(myw + o * 32);
 #pragma unroll
                             for (int j4 = 0; j4 < 8; j4++) {
-                                const float4 w = __ldg(wr + j4);
+                                const float4 w = wr[j4];
                                 ph[o] = fmaf(v[4 * j4], w.x, ph[o]); ph[o] = fmaf(v[4 * j4 + 1], w.y, ph[o]);
                                 ph[o] = fmaf(v[4 * j4 + 2], w.z, ph[o]); ph[o] = fmaf(v[4 * j4 + 3], w.w, ph[o]);
                             }
                         }
+                        __syncwarp();   // read before the next chunk overwrites
                     }
                 } else {
                     uint4 *dst = reinterpret_cast<uint4 *>(stg + lane * SROW);
@@ -485,6 +480,25 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             t_prev = t;
         }
     };
+    // every layer's parameters, once for the call
+    for (int l = 0; l < a.n_layers; l++) {
+        const PLayer &L = a.layer[l];
+        float *pb = prm + L.prm_off;
+        const int N = L.N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            pb[i] = L.bias[i];
+            if (FP8) {
+                pb[N + i] = L.scale[i];
+                pb[2 * N + i] = L.oscale ? L.oscale[i] : 1.f;
+            }
+            if (NO == 2 && L.out_part) {   // the hybrid / store heads stage their FC2 rows per warp
+                float *w = pb + (FP8 ? 3 * N : N);
+                w[i] = a.w2[i];
+                w[N + i] = a.w2[N + i];
+            }
+        }
+    }
+    __syncthreads();
     gather_phase<T>(a, smem, a.ext);
     bool ok = grid_sync(a, target, cta_abort);
     mark(SIMNET_KERNEL_GATHER);
@@ -639,7 +653,19 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.P = c->n_part;
     a.compact_every = uneven ? 16 : 0;
     a.stage_bytes = A_BYTES + bn_max * ROW_BYTES;
-    a.prm_floats = 6 * n_max;
+    // shared parameter table: per layer bias (+ FP8 scale, requant) (+ FC1's FC2 rows),
+    // then FC1's per-step padding row, then the per-warp FC2 row slices of wider heads
+    int off = 0;
+    for (int l = 0; l < c->n_layers; l++) {
+        a.layer[l].prm_off = off;
+        const int N = a.layer[l].N;
+        off += N * (fp8 ? 3 : 1) + (a.layer[l].out_part && c->n_out == 2 ? 2 * N : 0);
+        off = (off + 3) & ~3;   // 16-byte aligned blocks
+    }
+    a.cst_off = off;
+    off += a.layer[c->n_layers - 1].N;
+    a.w2h_off = (off + 3) & ~3;
+    a.prm_floats = a.w2h_off + (c->n_out == 2 ? 0 : kEpiWarps * c->n_out * 32);
     const size_t staging = (size_t)kEpiWarps * 32 * (32 * (fp8 ? 1 : 2) + 16);
     const size_t fixed = 1024 + 256 + (size_t)a.prm_floats * 4 + staging;
     const size_t budget = 232448 - 1024;   // minus the static shared memory of the compaction
