@@ -35,9 +35,11 @@ FP32_FMA_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # SMs x FP32 lanes x 2 f
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
 # keyed by (workload, precision, kernel); from the capture summarised in profiles/.
 TRAFFIC = {
-    # persist_kernel, c2 BF16: 1.32 MB of DRAM traffic over 20 steps in the capture of
+    # persist_kernel, c2 BF16: 1.53 MB of DRAM traffic over 20 steps in the capture of
     # profiles/persist_kernel_c2_bf16.md, scaled by steps to the 1,000-step launch
-    ("c2", "bf16", "persist_kernel"): 1.317e6 * 1000 / 20,
+    ("c2", "bf16", "persist_kernel"): 1.526e6 * 1000 / 20,
+    # cluster_kernel, c2 BF16: 1.49 MB over 20 steps (profiles/cluster_kernel_c2_bf16.md)
+    ("c2", "bf16", "cluster_kernel"): 1.494e6 * 1000 / 20,
 }
 
 
