@@ -186,3 +186,27 @@ def test_bf16_padding_table_follows_device_weight_updates(trace, mode):
     np.testing.assert_array_equal(ca, cb)
     np.testing.assert_array_equal(la, lb)
     np.testing.assert_array_equal(pa.view(np.uint32), pb.view(np.uint32))
+
+
+@pytest.mark.parametrize("variant", ["hybrid", "residual", "residual-hybrid"])
+def test_split_run_equals_unsplit_other_networks(trace, variant):
+    """Split runs on the grid-persistent kernel for the hybrid head and the
+    residual network: every resumed launch starts from stale per-layer tiles and
+    refills their constant rows, so the split run must still equal the unsplit
+    one bit for bit."""
+    base = I.ARCH_SMALL(32)
+    head = "hybrid" if "hybrid" in variant else "regression"
+    block = "residual" if "residual" in variant else "conv"
+    arch = I.Arch(base.window, 3 if block == "residual" else base.n_conv, base.channels, base.hidden, head,
+                  block=block)
+    sim, blob = make_sim(arch, "bf16", seed=3, cluster=False)
+    rec, off = to_dev(trace)
+    N = trace.n_instructions
+    c0, l0, p0, _ = run(sim, rec, off, N)
+    c1, l1, p1, st1 = run(sim, rec, off, N, chunks=[1, 17, 64, 5])
+    assert sim.kernel_path == "persistent"
+    np.testing.assert_array_equal(c1, c0)
+    np.testing.assert_array_equal(l1, l0)
+    np.testing.assert_array_equal(p1.view(np.uint32), p0.view(np.uint32))
+    back = oracle.simulate(oracle.Config.of(arch), trace.records, trace.offsets, replay=l1, logs=False)
+    np.testing.assert_array_equal(back.cycles, c1)
