@@ -384,7 +384,7 @@ def run_ours(args, rank, world):
                            "algorithmic_unit": "flop", "share_of_step": 1.0}
         out["phases_us_per_step"] = cluster_phases(w, args, blob32, rec, off, cyc, clocks.get("sm_mhz") or 2032.0)
     elif rank == 0 and not args.no_breakdown:
-        out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B)
+        out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B, path)
         if out["kernel_mode"] == "persistent":
             # one launch does every step: its roofline is the whole call's algorithmic
             # work over its device time; the per-phase table above explains the split
@@ -464,15 +464,16 @@ def cluster_phases(w, args, blob32, rec, off, cyc, sm_mhz):
     return out
 
 
-def roofline(w, args, blob32, rec, off, cyc, B):
+def roofline(w, args, blob32, rec, off, cyc, B, path):
     """Per-kernel CUDA-event times from one extra full step with an event pair
     around every launch; roofline of the kernel with the largest share."""
     from paper_2105_05821_b300.simnet import Simnet
     hbm, bf16_burst, bf16_sus, src = peaks()
-    # the per-layer or grid-persistent path (a cluster call that hands its long
-    # queues to the grid kernel is measured here as the grid kernel)
+    # the per-layer or grid-persistent path the timed call finished on (a cluster
+    # call that hands its long queues on is measured here as the path it moved to)
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          kernel_events=True, persistent=not args.layerwise, cluster=False)
+                          kernel_events=True, persistent=not args.layerwise and path != "layerwise",
+                          cluster=False)
     sim.load_weights(blob32)
     if args.precision != "fp32" and not args.no_autotune:
         sim.autotune(B)

@@ -105,6 +105,17 @@ typedef enum {
                                           only (EUNSUPPORTED for FP8); runs as per-layer kernels;
                                           no device training (train_* and set_weights_device
                                           return EUNSUPPORTED) and no cnn_forward_noalloc. */
+#define SIMNET_FLAG_FIXED_PATH 0x200u  /* run a whole simulate call on the path the other flags
+                                          select.  Without it a long untimed BF16/FP8 call picks its
+                                          path as it goes: the cluster kernel measures its padding
+                                          extent over its first 128 steps and hands a batch whose
+                                          queues stay long to the grid-wide kernels, and the grid-wide
+                                          choice times 32 steps of the persistent kernel against 32
+                                          of the per-layer kernels from the same state and runs the
+                                          rest on the faster; the context keeps that pick for later
+                                          calls with the same batch size, compaction and weights.
+                                          Paths differ only in FP32 summation order;
+                                          simulate_stats.path reports the last one used. */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -344,11 +355,12 @@ simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
                                     whole call, no grid-wide synchronisation (BF16; 2-3 conv
                                     layers of 64 or 128 channels; FC1 width 256 or 512) */
 
-/* Path the last simnet_simulate call took (SIMNET_PATH_*), or -1 for a NULL context.  A
- * BF16 call where the cluster kernel applies starts on it; if the call is longer than 512
- * steps and steps 64-127 needed more than two passes of last-conv positions per step (long
- * queues), the rest of the call runs on the grid-wide kernel and the call reports
- * SIMNET_PATH_PERSISTENT. */
+/* Path that ran the last steps of the last simnet_simulate call (SIMNET_PATH_*), or -1 for
+ * a NULL context.  A BF16 call where the cluster kernel applies starts on it; if the call is
+ * longer than 512 steps and steps 64-127 needed more than two passes of last-conv positions
+ * per step (long queues), the rest of the call runs on the grid-wide path.  The grid-wide
+ * path of a long call is the persistent kernel or the per-layer kernels, whichever a timed
+ * comparison picked (SIMNET_FLAG_FIXED_PATH: always the persistent kernel). */
 int32_t simnet_kernel_path(const simnet_ctx *ctx);
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */

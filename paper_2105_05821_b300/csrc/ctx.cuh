@@ -128,6 +128,10 @@ struct simnet_ctx {
     // on-device weight updates; rebuilt before the next persistent run)
     bool const_stale = false;
     int path = SIMNET_PATH_NONE;   // kernel path of the last simulate call
+    // the grid-wide path picked by the last timed comparison (SIMNET_PATH_PERSISTENT or
+    // SIMNET_PATH_LAYERWISE) and what it was measured for: batch size, compaction, weights
+    int pick = SIMNET_PATH_NONE, pick_B = -1, pick_uneven = -1;
+    uint64_t pick_wfp = 0;
 };
 
 namespace simnet {

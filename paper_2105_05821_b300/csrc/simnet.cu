@@ -817,7 +817,7 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
     const bool timed = (c->cfg.flags & SIMNET_FLAG_KERNEL_EVENTS) != 0;
     const bool pdl = c->pdl && !timed;
     if ((st = prepare_plans(c, B, pdl)) != SIMNET_OK) return st;
-    int64_t launches = (resume ? 1 : 2) + n_steps * launches_per_step(c);
+    int64_t launches = 0;
     KTimer kt;
     kt.c = timed ? c : nullptr;
     kt.s = s;
@@ -827,61 +827,15 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
     }
     c->phase_valid = false;
     const bool persistent = c->cfg.precision != SIMNET_FP32 && !(c->cfg.flags & SIMNET_FLAG_LAYERWISE);
+    const bool fixed = (c->cfg.flags & SIMNET_FLAG_FIXED_PATH) != 0;
     std::string why_not_cluster;
-    if (n_steps <= 0) {
-        launches = resume ? 0 : 1;
-    } else if (persistent && !(c->cfg.flags & SIMNET_FLAG_NO_CLUSTER) && cluster_eligible(c, why_not_cluster)) {
-        // Clusters own their sub-traces for the whole call: no grid-wide barriers.  Each
-        // cluster runs the last-conv positions below its padding extent in passes of a few
-        // positions, so when queues stay long the grid-wide kernel, which spreads the
-        // positions over every SM, is faster: the first kProbe steps (queues fill by at most
-        // one entry a step) measure the extent over their second half, and the rest of a
-        // long call continues on the grid kernel if that needed more than two passes a step
-        // (the state lives in the same device arrays either way).
-        constexpr int64_t kProbe = 128;
-        c->phase_on = timed;
-        if (timed) CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
-        CK(cudaMemsetAsync(c->phase_ns + 56, 0, 2 * sizeof(unsigned long long), s));
-        c->phase_valid = timed;
-        std::string why;
-        const bool probe = !timed && n_steps > 4 * kProbe;
-        const int64_t first = probe ? kProbe : n_steps;
-        if (!launch_cluster(c, B, first, s, why)) return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
-        launches = resume ? 1 : 2;
-        c->path = SIMNET_PATH_CLUSTER;
-        if (probe) {
-            unsigned long long ps[2] = {0, 0};
-            CK(cudaMemcpyAsync(ps, c->phase_ns + 56, sizeof ps, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            const int pm = 8 >> (c->cfg.n_conv - 1);   // positions per pass
-            const bool long_queues = ps[1] > 0 && (double)ps[0] / (double)ps[1] > 2.0 * pm;
-            if (long_queues) {
-                if (!launch_persistent(c, B, n_steps - first, uneven, s, why))
-                    return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
-                c->path = SIMNET_PATH_PERSISTENT;
-            } else if (!launch_cluster(c, B, n_steps - first, s, why)) {
-                return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
-            }
-            launches += 1;
-        }
-    } else if (persistent) {
-        // one cooperative kernel runs every step; its phases are timed by CTA 0 on request
-        c->phase_on = timed;
-        if (timed) {
-            CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
-            CK(cudaMemsetAsync(c->phase_n, 0, SIMNET_KERNEL_KINDS * sizeof(unsigned long long), s));
-        }
-        std::string why;
-        if (!launch_persistent(c, B, n_steps, uneven, s, why))
-            return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
-        launches = resume ? 1 : 2;
-        c->phase_valid = timed;
-        c->path = SIMNET_PATH_PERSISTENT;
-    } else {
-        c->path = SIMNET_PATH_LAYERWISE;
+    // the per-layer kernels from the current device state (a gather first: their
+    // feature tile is slot-major); CUDA graphs of whole steps unless timed
+    auto run_layerwise = [&](int64_t steps) -> simnet_status {
         enqueue_gather(c, B, s, false, timed ? &kt : nullptr);
+        launches += 1 + steps * launches_per_step(c);
         if (timed || (c->cfg.flags & SIMNET_FLAG_NO_GRAPH)) {
-            for (int64_t i = 0; i < n_steps; i++) {
+            for (int64_t i = 0; i < steps; i++) {
                 enqueue_step(c, B, s, pdl, timed ? &kt : nullptr);
                 if (uneven && (i % kGraphSteps) == kGraphSteps - 1) {
                     enqueue_compact(c, B, s, pdl, timed ? &kt : nullptr);
@@ -891,13 +845,109 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
             if (timed && !kt.ok) return fail(c, SIMNET_ENOMEM, "kernel timing: event pool exhausted");
             c->kt_valid = timed;
         } else {
+            simnet_status st2;
             if (c->g_B != B || c->g_compact != (int)uneven || !c->gexec[0])
-                if ((st = capture_graphs(c, B, uneven)) != SIMNET_OK) return st;
-            const int64_t full = n_steps / kGraphSteps, rest = n_steps % kGraphSteps;
+                if ((st2 = capture_graphs(c, B, uneven)) != SIMNET_OK) return st2;
+            const int64_t full = steps / kGraphSteps, rest = steps % kGraphSteps;
             for (int64_t i = 0; i < full; i++) CK(cudaGraphLaunch(c->gexec[0], s));
             for (int64_t i = 0; i < rest; i++) CK(cudaGraphLaunch(c->gexec[1], s));
             if (uneven) launches += 2 * (full + rest);
         }
+        c->path = SIMNET_PATH_LAYERWISE;
+        return SIMNET_OK;
+    };
+    auto run_persistent = [&](int64_t steps) -> simnet_status {
+        std::string why;
+        if (!launch_persistent(c, B, steps, uneven, s, why))
+            return fail(c, SIMNET_ECUDA, "persistent kernel: %s", why.c_str());
+        launches += 1;
+        c->path = SIMNET_PATH_PERSISTENT;
+        return SIMNET_OK;
+    };
+    // Grid-persistent kernel or per-layer kernels for `steps` steps.  The persistent
+    // kernel skips the padding rows past the batch's longest queue but pays a grid
+    // barrier per phase; per-layer kernels compute every row with cheaper boundaries.
+    // Which wins depends on the queue lengths the predictor produces and the batch,
+    // so a long untimed call measures both: (after `warm` steps that let the queues
+    // fill) kCmp steps on each from the same state, then the faster runs the rest.
+    // The pick holds for later calls with the same batch size, compaction and weights.
+    auto run_grid_or_layers = [&](int64_t steps, int64_t warm) -> simnet_status {
+        constexpr int64_t kCmp = 32;
+        simnet_status st2;
+        if (timed || fixed || steps < warm + 2 * kCmp + 512) return run_persistent(steps);
+        const uint64_t wfp = weights_fingerprint(c);
+        if (c->pick != SIMNET_PATH_NONE && c->pick_B == B && c->pick_uneven == (int)uneven && c->pick_wfp == wfp)
+            return c->pick == SIMNET_PATH_LAYERWISE ? run_layerwise(steps) : run_persistent(steps);
+        if (warm > 0 && (st2 = run_persistent(warm)) != SIMNET_OK) return st2;
+        if (c->g_B != B || c->g_compact != (int)uneven || !c->gexec[0])   // capture outside the timing
+            if ((st2 = capture_graphs(c, B, uneven)) != SIMNET_OK) return st2;
+        cudaEvent_t e[3];
+        for (auto &x : e) CK(cudaEventCreate(&x));
+        CK(cudaEventRecord(e[0], s));
+        if ((st2 = run_persistent(kCmp)) != SIMNET_OK) return st2;
+        CK(cudaEventRecord(e[1], s));
+        if ((st2 = run_layerwise(kCmp)) != SIMNET_OK) return st2;
+        CK(cudaEventRecord(e[2], s));
+        CK(cudaEventSynchronize(e[2]));
+        float t_grid = 0.f, t_layers = 0.f;
+        cudaEventElapsedTime(&t_grid, e[0], e[1]);
+        cudaEventElapsedTime(&t_layers, e[1], e[2]);
+        for (auto &x : e) cudaEventDestroy(x);
+        const int64_t rest = steps - warm - 2 * kCmp;
+        c->pick = t_layers < t_grid ? SIMNET_PATH_LAYERWISE : SIMNET_PATH_PERSISTENT;
+        c->pick_B = B;
+        c->pick_uneven = (int)uneven;
+        c->pick_wfp = wfp;
+        return c->pick == SIMNET_PATH_LAYERWISE ? run_layerwise(rest) : run_persistent(rest);
+    };
+    launches = resume ? 0 : 1;   // init_state
+    if (n_steps <= 0) {
+        // nothing to run
+    } else if (persistent && !(c->cfg.flags & SIMNET_FLAG_NO_CLUSTER) && cluster_eligible(c, why_not_cluster)) {
+        // Clusters own their sub-traces for the whole call: no grid-wide barriers.  Each
+        // cluster runs the last-conv positions below its padding extent in passes of a few
+        // positions, so when queues stay long the grid-wide or per-layer kernels, which
+        // spread the positions over every SM, are faster: the first kProbe steps (queues
+        // fill by at most one entry a step) measure the extent over their second half, and
+        // the rest of a long call moves on (the state lives in the same device arrays
+        // either way).
+        constexpr int64_t kProbe = 128;
+        c->phase_on = timed;
+        if (timed) CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(c->phase_ns + 56, 0, 2 * sizeof(unsigned long long), s));
+        c->phase_valid = timed;
+        std::string why;
+        const bool probe = !timed && !fixed && n_steps > 4 * kProbe;
+        const int64_t first = probe ? kProbe : n_steps;
+        if (!launch_cluster(c, B, first, s, why)) return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
+        launches += 1;
+        c->path = SIMNET_PATH_CLUSTER;
+        if (probe) {
+            unsigned long long ps[2] = {0, 0};
+            CK(cudaMemcpyAsync(ps, c->phase_ns + 56, sizeof ps, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const int pm = 8 >> (c->cfg.n_conv - 1);   // positions per pass
+            const bool long_queues = ps[1] > 0 && (double)ps[0] / (double)ps[1] > 2.0 * pm;
+            if (long_queues) {
+                c->phase_on = false;
+                if ((st = run_grid_or_layers(n_steps - first, 0)) != SIMNET_OK) return st;
+            } else {
+                if (!launch_cluster(c, B, n_steps - first, s, why))
+                    return fail(c, SIMNET_ECUDA, "cluster kernel: %s", why.c_str());
+                launches += 1;
+            }
+        }
+    } else if (persistent) {
+        // one cooperative kernel runs the steps; its phases are timed by CTA 0 on request
+        c->phase_on = timed;
+        if (timed) {
+            CK(cudaMemsetAsync(c->phase_ns, 0, 64 * sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(c->phase_n, 0, SIMNET_KERNEL_KINDS * sizeof(unsigned long long), s));
+        }
+        if ((st = run_grid_or_layers(n_steps, 128)) != SIMNET_OK) return st;
+        c->phase_valid = timed && c->path == SIMNET_PATH_PERSISTENT;
+    } else {
+        if ((st = run_layerwise(n_steps)) != SIMNET_OK) return st;
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(cycles_out, c->cyc, (size_t)B * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));

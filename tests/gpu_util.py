@@ -41,6 +41,7 @@ def run_gpu(sim: Simnet, trace: I.Trace, replay=None, logs=True):
 
 
 def make_sim(arch, precision="fp32", blob=None, seed=None, **kw):
+    kw.setdefault("auto_path", False)   # a test pins its path unless it tests the choice
     sim = Simnet.for_arch(arch, precision=precision, **kw)
     if blob is None:
         blob = I.workload_weights(I.Workload("x", arch, 1, 1, seed=seed or 1))

@@ -173,19 +173,47 @@ def test_cluster_done_before_the_call_ends():
 def test_long_queues_move_to_the_grid_kernel():
     """Replayed latencies F = 1, E = 200 fill every queue to capacity, so the
     cluster kernel's probe (steps 64-127) sees more than two passes of
-    positions a step and the call continues on the grid-wide kernel from the
-    same device state; cycle counts and evictions stay bit-exact."""
+    positions a step and the call continues on the grid-wide kernels from the
+    same device state (the persistent or the per-layer kernels, whichever its
+    timed comparison picks); cycle counts and evictions stay bit-exact.  With
+    the path pinned the cluster kernel runs the whole call."""
     w = I.WORKLOADS["c2"]
     trace = I.small_trace([600] * 128, seed=27)
     replay = np.zeros((trace.n_instructions, 2), np.uint8)
     replay[:, 0], replay[:, 1] = 1, 200
     cfg = oracle.Config.of(w.arch)
     ref = oracle.simulate(cfg, trace.records, trace.offsets, replay=replay)
-    sim, _ = make_sim(w.arch, "bf16", blob=I.workload_weights(w))
+    for auto, paths in ((True, ("persistent", "layerwise")), (False, ("cluster",))):
+        sim, _ = make_sim(w.arch, "bf16", blob=I.workload_weights(w), auto_path=auto)
+        g = run_gpu(sim, trace, replay=replay)
+        assert sim.kernel_path in paths
+        np.testing.assert_array_equal(g["cycles"], ref.cycles)
+        assert g["stats"].evictions == int(ref.evictions.sum()) > 0
+
+
+@pytest.mark.parametrize("arch,precision", [(I.ARCH_MID, "fp8"), (I.ARCH_WIDE, "bf16")])
+def test_grid_path_choice_keeps_the_state(arch, precision):
+    """A long untimed call on the grid-wide path runs 128 steps on the
+    persistent kernel, then 64 on it and 64 on the per-layer kernels from the
+    same state, timed, and finishes on the faster, so the state passes between
+    the two paths at least twice, with compactions on both (sub-traces of
+    1,000 and 300 instructions).  Under replayed latencies that fill the queues
+    every cycle count and eviction is bit-exact; free-running, the oracle
+    replaying the GPU's own latencies reproduces its cycle counts."""
+    trace = I.small_trace([1000] * 48 + [300] * 80, seed=29)
+    replay = np.zeros((trace.n_instructions, 2), np.uint8)
+    replay[:, 0], replay[:, 1] = 1, 200
+    cfg = oracle.Config.of(arch)
+    ref = oracle.simulate(cfg, trace.records, trace.offsets, replay=replay)
+    blob = I.workload_weights(I.Workload("g", arch, 1, 1, seed=29))
+    sim, _ = make_sim(arch, precision, blob=blob, auto_path=True)
     g = run_gpu(sim, trace, replay=replay)
-    assert sim.kernel_path == "persistent"
+    assert sim.kernel_path in ("persistent", "layerwise")
     np.testing.assert_array_equal(g["cycles"], ref.cycles)
     assert g["stats"].evictions == int(ref.evictions.sum()) > 0
+    f = run_gpu(sim, trace)
+    back = oracle.simulate(cfg, trace.records, trace.offsets, replay=f["lat"])
+    np.testing.assert_array_equal(back.cycles, f["cycles"])
 
 
 def test_single_long_subtrace_free_running_fp32():
