@@ -268,8 +268,13 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_cluster() {
-    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from this CTA's
+// shared memory into CTA r's, counted (complete_tx) on a barrier in CTA r.
+__device__ __forceinline__ void cl_bulk_copy(uint32_t dst_cluster, uint32_t src, uint32_t bytes, uint32_t bar_cluster) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_cluster),
+                 "r"(src), "r"(bytes), "r"(bar_cluster)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             mbar_init(bar(S + s), kMulticastWeights ? CS : 1);   // free once every reader has read it
         }
         mbar_init(bar(B_D), 1);
-        mbar_init(bar(B_FULL), CS * 8);
+        mbar_init(bar(B_FULL), 1);   // thread 0's expect_tx; the peers' row copies complete it
         mbar_init(bar(B_EMPTY), CS);
         mbar_init(bar(B_DFC), 1);
         mbar_init(bar(B_PART), CS * 2);
@@ -435,13 +440,18 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            int it = 0;
+            int it = 0, ps = 0;     // panels issued; stage of the next one
+            uint32_t pph = 0;       // and its phase parity (no division on the issue path)
+            auto adv = [&] {
+                it++;
+                if (++ps == S) { ps = 0; pph ^= 1u; }
+            };
             bool ok = true;
             // conv panels: this CTA loads rows [rank C/CS, (rank+1) C/CS) of each into every CTA
             // of the cluster (all need the same weights); FC1 panels are its own
             auto load = [&](const CUtensorMap *m, int x, int yy, uint32_t bytes, bool shared_panel) {
-                const int s = it % S;
-                if (!note(cl_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
+                const int s = ps;
+                if (!note(cl_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
                     ok = false;
                     return;
                 }
@@ -450,7 +460,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     tma_load_2d_mc(ring0 + s * kStage + rank * (uint32_t)(C / CS) * 128u, m, bar(s), x, yy, kAll);
                 else
                     tma_load_2d(ring0 + s * kStage, m, bar(s), x, yy);
-                it++;
+                adv();
             };
             // conv panel i of a pass (all layers' weights in consumption order), i in [from, to)
             int n_conv_panels = 0;
@@ -462,14 +472,14 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         if (i < from || i >= to) continue;
                         if (kMulticastWeights) load(&a.tW[l], pi * 64, (int)rank * (C / CS), (uint32_t)C * 128u, true);
                         else for (int r = 0; r < CS && ok; r++) {   // the whole panel, slice by slice, locally
-                            const int s = it % S;
+                            const int s = ps;
                             if (r == 0) {
-                                if (!note(cl_wait(bar(S + s), ((uint32_t)(it / S) & 1u) ^ 1u, lim, abort_f, a.status), 1, -1, it)) { ok = false; break; }
+                                if (!note(cl_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) { ok = false; break; }
                                 mbar_expect_tx(bar(s), (uint32_t)C * 128u);
                             }
                             tma_load_2d(ring0 + s * kStage + (uint32_t)r * (uint32_t)(C / CS) * 128u, &a.tW[l], bar(s),
                                         pi * 64, r * (C / CS));
-                            if (r == CS - 1) it++;
+                            if (r == CS - 1) adv();
                         }
                     }
             };
@@ -498,6 +508,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // ---------------------------------------------------------------- workers (thread 0 also issues the MMAs)
         const int wi = warp - 2, qd = warp & 3, half = wi >> 2, tid = threadIdx.x - 64;
         int d_uses = 0, it = 0;    // it: weight panels consumed (thread 0)
+        int cs = 0;                // stage of panel `it` and its phase parity
+        uint32_t cph = 0;
+        auto adv = [&] {
+            it++;
+            if (++cs == S) { cs = 0; cph ^= 1u; }
+        };
         int64_t R = 0;             // passes exchanged
         bool mma_ok = true;        // thread 0: false after a bounded wait gave up
         const StepArgs &As = *A;
@@ -512,9 +528,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             }
         };
         auto take = [&](int &s, int who) -> bool {   // thread 0: next weight panel (who: layer, L = FC1)
-            s = it % S;
+            s = cs;
             const uint64_t tw = prof ? (uint64_t)clock64() : 0;
-            if (!note(mbar_wait(bar(s), (uint32_t)(it / S) & 1u, lim, abort_f, a.status), 3, -1, it)) return false;
+            if (!note(mbar_wait(bar(s), cph, lim, abort_f, a.status), 3, -1, it)) return false;
             if (prof) pacc[26 + who] += (uint64_t)clock64() - tw;
             tc_fence_after();
             return true;
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 }
                 if (kMulticastWeights) commit_mc(bar(S + s), kAll);   // stage read here: tell every CTA
                 else umma_commit(bar(S + s));
-                it++;
+                adv();
             }
             if (mma_ok) umma_commit(bar(B_D));
         };
@@ -676,20 +692,28 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         workers_sync();
                     } else {
                         if (tid >= 128 && tid < 128 + HN) cp_wait<0>();   // S[e] landed (read after the barrier)
+                        if (prof) pacc[17] += (uint64_t)clock64() - tp;   // last conv epilogue (thread 0's share)
                         workers_sync();   // this CTA's rows of the pass are all in its own buffer
-                        constexpr int CPP = SPC * 8;        // 16-byte chunks of this CTA's rows per panel
-                        const int n16 = P * C / 64 * CPP;
-                        for (int i = tid; i < n16; i += kWk) {
-                            const uint32_t off = (uint32_t)(i / CPP) * 16384u + rank * (SPC * 128) + (uint32_t)(i % CPP) * 16u;
-                            const uint4 v = *reinterpret_cast<const uint4 *>(sm + y.fc1a + off);
-                            for (int r = 1; r < CS; r++) cl_st_v4(cl_map(fc0 + off, (rank + r) % CS), v);
+                        const uint64_t tx0 = prof ? (uint64_t)clock64() : 0;
+                        // this CTA's rows (written and fenced to the async proxy above) to every
+                        // peer: one bulk copy per 64-column panel and peer, counted on the peer's
+                        // B_FULL; a peer overwrites its copy only after B_EMPTY, i.e. after every
+                        // CTA's FC1 of this pass, which waited for all of its copies
+                        constexpr uint32_t kRowBytes = SPC * 128;   // this CTA's rows of one panel
+                        const int np = P * C / 64;
+                        if (ok && lane == 0 && wi < CS - 1) {   // one warp per peer: the issues overlap
+                            const uint32_t peer = (rank + 1u + (uint32_t)wi) % CS;
+                            const uint32_t rb = cl_map(bar(B_FULL), peer);
+                            for (int i = 0; i < np; i++) {
+                                const uint32_t src = fc0 + (uint32_t)i * 16384u + rank * kRowBytes;
+                                cl_bulk_copy(cl_map(src, peer), src, kRowBytes, rb);
+                            }
                         }
-                        fence_async_cluster();
-                        __syncwarp();
-                        if (lane < CS) cl_arrive(cl_map(bar(B_FULL), (uint32_t)lane));
                         // FC1 over this pass's positions, once every CTA's rows are in (thread 0)
                         if (tid == 0 && mma_ok) {
+                            mbar_expect_tx(bar(B_FULL), (uint32_t)((CS - 1) * np) * kRowBytes);
                             const uint64_t tw = prof ? (uint64_t)clock64() : 0;
+                            if (prof) pacc[16] += tw - tx0;   // own rows to every peer (issue)
                             if (!note(cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status), 7, t, R)) mma_ok = false;
                             if (prof) pacc[18] += (uint64_t)clock64() - tw;
                             fence_async_smem();
@@ -705,9 +729,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                                 (q0 | pi | k) != 0 ? 1u : 0u);
                                 if (kMulticastWeights) commit_mc(bar(S + s), kAll);
                                 else umma_commit(bar(S + s));
-                                it++;
+                                adv();
                             }
                             if (mma_ok) commit_mc(bar(B_EMPTY), kAll);
+                            if (prof) pacc[19] += (uint64_t)clock64() - tw;   // FC1 wait + issue
                         }
                         __syncwarp();
                         R++;
@@ -915,7 +940,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         for (int it = cnt[1]; it < cnt[0]; it++) drain_wait(bar(it % S), (uint32_t)(it / S) & 1u, drain_ns);
     }
     __syncthreads();
-    cluster_sync_all();   // no peer writes into this CTA's shared memory any more
+    cluster_sync_all();   // no peer starts a write into this CTA's shared memory any more
+    if (*abort_f) {
+        // after a wait gave up, a peer may have started a row copy into this CTA that no
+        // barrier here waits for; copies already issued land within microseconds
+        const uint64_t t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) __nanosleep(1000);
+    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
