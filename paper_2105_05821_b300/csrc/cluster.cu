@@ -101,7 +101,7 @@ __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, i
     y.slot = al_up(y.prm + (uint32_t)prm_floats(L, C, HN, no) * 4, 16);
     y.misc = y.slot + SPC * 8 + 8 * SPC * 4;
     y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8, 8);   // + 32 phase counters (profiling)
-    y.total = y.bars + (2 * stages + 12) * 8;
+    y.total = y.bars + (2 * stages + 16) * 8;
     return y;
 }
 
@@ -330,8 +330,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + y.bars);
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
     // 0..S-1 weight panel full, S..2S-1 empty; then:
-    const int B_D = 2 * S, B_FULL = 2 * S + 1, B_EMPTY = 2 * S + 2, B_DFC = 2 * S + 3, B_PART = 2 * S + 4,
-              B_EXT = 2 * S + 5, B_FIN = 2 * S + 7;
+    // B_FULL + i: the peers' rows of FC1 operand panel i (at most 8 panels a pass)
+    const int B_D = 2 * S, B_EMPTY = 2 * S + 1, B_DFC = 2 * S + 2, B_PART = 2 * S + 3, B_EXT = 2 * S + 4,
+              B_FIN = 2 * S + 6, B_FULL = 2 * S + 7;
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
     float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
     float *s_Se = s_fb + HN;                                 // [HN] S[e] of the current step
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             mbar_init(bar(S + s), kMulticastWeights ? CS : 1);   // free once every reader has read it
         }
         mbar_init(bar(B_D), 1);
-        mbar_init(bar(B_FULL), 1);   // thread 0's expect_tx; the peers' row copies complete it
+        for (int i = 0; i < 8; i++) mbar_init(bar(B_FULL + i), 1);   // thread 0's expect_tx; the peers' copies
         mbar_init(bar(B_EMPTY), CS);
         mbar_init(bar(B_DFC), 1);
         mbar_init(bar(B_PART), CS * 2);
@@ -516,6 +517,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         };
         int64_t R = 0;             // passes exchanged
         bool mma_ok = true;        // thread 0: false after a bounded wait gave up
+        uint32_t fph = 0;          // thread 0: phase parity of each B_FULL + i
         const StepArgs &As = *A;
         const int RW = As.retire_width, strict = As.strict;
         const bool prof = a.prof && blockIdx.x == 0 && tid == 0;
@@ -627,7 +629,14 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 for (int l = 0; l < L; l++) {
                     const bool last = l == L - 1;
                     uint64_t ti0 = prof ? (uint64_t)clock64() : 0;
-                    if (tid == 0 && mma_ok) issue_conv(l, P);
+                    if (tid == 0 && mma_ok) {
+                        issue_conv(l, P);
+                        // the peers' rows of this pass, expected while the first layer's MMAs run
+                        // (every phase of the previous pass completed before its FC1 MMAs)
+                        if (l == 0)
+                            for (int i = 0; i < P * C / 64; i++)
+                                mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * (uint32_t)(SPC * 128));
+                    }
                     __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
                     uint64_t ti1 = prof ? (uint64_t)clock64() : 0;
                     bool ok = note(sleep_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status, false), 5, t, R);
@@ -697,29 +706,34 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         const uint64_t tx0 = prof ? (uint64_t)clock64() : 0;
                         // this CTA's rows (written and fenced to the async proxy above) to every
                         // peer: one bulk copy per 64-column panel and peer, counted on the peer's
-                        // B_FULL; a peer overwrites its copy only after B_EMPTY, i.e. after every
-                        // CTA's FC1 of this pass, which waited for all of its copies
+                        // B_FULL + panel; a peer overwrites its copy only after B_EMPTY, i.e. after
+                        // every CTA's FC1 of this pass, which waited for all of its copies
                         constexpr uint32_t kRowBytes = SPC * 128;   // this CTA's rows of one panel
                         const int np = P * C / 64;
-                        if (ok && lane == 0 && wi < CS - 1) {   // one warp per peer: the issues overlap
-                            const uint32_t peer = (rank + 1u + (uint32_t)wi) % CS;
-                            const uint32_t rb = cl_map(bar(B_FULL), peer);
+                        // one warp per peer (warps 1..CS-1: the copies take ~1 us to issue, which
+                        // warp 0's MMA thread spends on FC1 instead)
+                        if (ok && lane == 0 && wi >= 1 && wi < CS) {
+                            const uint32_t peer = (rank + (uint32_t)wi) % CS;
                             for (int i = 0; i < np; i++) {
                                 const uint32_t src = fc0 + (uint32_t)i * 16384u + rank * kRowBytes;
-                                cl_bulk_copy(cl_map(src, peer), src, kRowBytes, rb);
+                                cl_bulk_copy(cl_map(src, peer), src, kRowBytes, cl_map(bar(B_FULL + i), peer));
                             }
                         }
-                        // FC1 over this pass's positions, once every CTA's rows are in (thread 0)
+                        // FC1 over this pass's positions, each panel once every CTA's rows of it
+                        // are in (thread 0): the MMAs of the first panels overlap later copies
                         if (tid == 0 && mma_ok) {
-                            mbar_expect_tx(bar(B_FULL), (uint32_t)((CS - 1) * np) * kRowBytes);
                             const uint64_t tw = prof ? (uint64_t)clock64() : 0;
                             if (prof) pacc[16] += tw - tx0;   // own rows to every peer (issue)
-                            if (!note(cl_wait(bar(B_FULL), (uint32_t)(R & 1), lim, abort_f, a.status), 7, t, R)) mma_ok = false;
-                            if (prof) pacc[18] += (uint64_t)clock64() - tw;
                             fence_async_smem();
-                            tc_fence_after();
                             const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
-                            for (int pi = 0; pi < P * C / 64 && mma_ok; pi++) {
+                            for (int pi = 0; pi < np && mma_ok; pi++) {
+                                const uint64_t tf = prof ? (uint64_t)clock64() : 0;
+                                if (!note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R)) {
+                                    mma_ok = false;
+                                    break;
+                                }
+                                fph ^= 1u << pi;
+                                if (prof) pacc[18] += (uint64_t)clock64() - tf;
                                 int s;
                                 if (!take(s, L)) { mma_ok = false; break; }
                                 const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u), bd = sdesc(ring0 + s * kStage);
