@@ -49,7 +49,7 @@ struct CArgs {
     unsigned long long *tinfo;  // [4] first expired wait: site, CTA, step, pass (zero at launch)
     unsigned long long *pos_sum;  // [2] positions computed and cluster-steps run (accumulated)
     int64_t n_steps, spin_ns;
-    int L, C, H, cap, rows_n, stages;
+    int L, C, H, cap, rows_n, stages, stage_bytes;
 };
 
 namespace {
@@ -57,9 +57,12 @@ using namespace tcx;
 
 // A cluster of CS CTAs (4 or 8) owns 128 batch slots, 128 / CS per CTA.
 constexpr int kCThreads = 320;
-constexpr bool kMulticastWeights = true;   // conv weight panels shared by TMA multicast, or loaded per CTA    // warp 0 TMA, warp 1 MMA, warps 2-9 workers
 constexpr int kWk = 256;          // worker threads
-constexpr int kStage = 16384;     // one weight panel: 128 rows x 64 BF16
+// One weight stage: consecutive panels (N rows x 64 K-columns BF16, at most 16 KB) of
+// one layer, as many as fit in 16 or 32 KB (the larger where three such stages fit);
+// one full and one empty barrier per stage, so the MMA thread waits and commits once
+// per stage, not once per panel.
+constexpr int kPanelMax = 16384;
 constexpr int kTmemCols = 512;
 
 __host__ __device__ inline uint32_t al_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -82,7 +85,7 @@ __host__ __device__ inline int prm_floats(int L, int C, int HN, int no) {
     return L * C + 2 * HN + 24 + (no == 2 ? 2 * HN : 24 * HN);
 }
 
-__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages, int no) {
+__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages, int no, int stage_bytes) {
     CLay y;
     const int HN = H / CS, SPC = 128 / CS, PM = pass_positions(L);
     // operand of layer l: its rows (pass positions x pairs x slots) x K, in 64-column panels
@@ -92,7 +95,7 @@ __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, i
         actb = b > actb ? b : actb;
     }
     y.ring = 0;
-    y.act = (uint32_t)stages * kStage;
+    y.act = (uint32_t)stages * (uint32_t)stage_bytes;
     y.fc1a = al_up(y.act + actb, 1024);
     y.qring = y.fc1a + 256u * (uint32_t)(pass_positions(L) * C);           // 128 slots x positions x C BF16
     y.rec = y.qring + (uint32_t)SPC * cap * 8;
@@ -191,7 +194,9 @@ __device__ __noinline__ bool cl_wait_slow(uint32_t bar, uint32_t parity, int64_t
     if (cl_try(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (true) {
-        if (cl_try(bar, parity)) return true;
+        // suspended until the phase completes (or the hint runs out): no polling that
+        // competes with the MMA thread's barrier operations
+        if (try_sleep(bar, parity, 20000u, true)) return true;
         if (*abort_flag) return false;
         if ((int64_t)(gtimer() - t0) > limit) {
             *abort_flag = 1;
@@ -306,8 +311,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int L = a.L, C = a.C, HN = a.H / CS, S = a.stages, cap = a.cap, PM = pass_positions(L);
+    const uint32_t kStage = (uint32_t)a.stage_bytes;
     constexpr int PF = NO == 2 ? 2 : 24;   // part_floats(NO)
-    const CLay y = c_layout(CS, L, C, a.H, cap, S, NO);
+    const CLay y = c_layout(CS, L, C, a.H, cap, S, NO, a.stage_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cl_rank();
     const int slot0 = (int)(blockIdx.x / CS) * 128 + (int)rank * SPC;
@@ -357,7 +363,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; s++) {
             mbar_init(bar(s), 1);
-            mbar_init(bar(S + s), kMulticastWeights ? CS : 1);   // free once every reader has read it
+            mbar_init(bar(S + s), CS);   // free once every CTA's MMAs have read it
         }
         mbar_init(bar(B_D), 1);
         for (int i = 0; i < 8; i++) mbar_init(bar(B_FULL + i), 1);   // thread 0's expect_tx; the peers' copies
@@ -438,6 +444,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // pass's rows; an MMA tile past them reads neighbouring shared memory into rows it ignores
     auto pstride_of = [&](int l, int P) { return (uint32_t)rows_of(l, P) * 128u; };
     auto panels_of = [&](int l) { return l == 0 ? 2 : C / 32; };                   // K / 64
+    // panels a stage holds: conv panels are C x 64, FC1 panels HN x 64 (BF16)
+    const int kConvPer = (int)kStage / (C * 128), kFcPer = min((int)kStage / (HN * 128), 8);
+    auto conv_stages = [&](int l) { return (panels_of(l) + kConvPer - 1) / kConvPer; };
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
@@ -448,47 +457,42 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 if (++ps == S) { ps = 0; pph ^= 1u; }
             };
             bool ok = true;
-            // conv panels: this CTA loads rows [rank C/CS, (rank+1) C/CS) of each into every CTA
-            // of the cluster (all need the same weights); FC1 panels are its own
-            auto load = [&](const CUtensorMap *m, int x, int yy, uint32_t bytes, bool shared_panel) {
+            // n panels of pb bytes (K-columns x0, x0 + 64, ...) into the next stage.  Conv
+            // panels: this CTA loads rows [rank C/CS, (rank+1) C/CS) of each into every CTA of
+            // the cluster (all need the same weights); FC1 panels are its own.
+            auto load = [&](const CUtensorMap *m, int x0, int yy, uint32_t pb, int n, bool shared_panel) {
                 const int s = ps;
                 if (!note(cl_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
                     ok = false;
                     return;
                 }
-                mbar_expect_tx(bar(s), bytes);
-                if (shared_panel)
-                    tma_load_2d_mc(ring0 + s * kStage + rank * (uint32_t)(C / CS) * 128u, m, bar(s), x, yy, kAll);
-                else
-                    tma_load_2d(ring0 + s * kStage, m, bar(s), x, yy);
+                mbar_expect_tx(bar(s), (uint32_t)n * pb);
+                for (int j = 0; j < n; j++) {
+                    const uint32_t dst = ring0 + (uint32_t)s * kStage + (uint32_t)j * pb;
+                    if (shared_panel)
+                        tma_load_2d_mc(dst + rank * (uint32_t)(C / CS) * 128u, m, bar(s), x0 + 64 * j, yy, kAll);
+                    else
+                        tma_load_2d(dst, m, bar(s), x0 + 64 * j, yy);
+                }
                 adv();
             };
-            // conv panel i of a pass (all layers' weights in consumption order), i in [from, to)
-            int n_conv_panels = 0;
-            for (int l = 0; l < L; l++) n_conv_panels += panels_of(l);
-            auto conv_panels = [&](int from, int to) {
+            // conv stage i of a pass (all layers' weights in consumption order), i in [from, to)
+            int n_conv_stages = 0;
+            for (int l = 0; l < L; l++) n_conv_stages += conv_stages(l);
+            auto conv_loads = [&](int from, int to) {
                 int i = 0;
                 for (int l = 0; l < L && ok; l++)
-                    for (int pi = 0; pi < panels_of(l) && ok; pi++, i++) {
+                    for (int g = 0; g < conv_stages(l) && ok; g++, i++) {
                         if (i < from || i >= to) continue;
-                        if (kMulticastWeights) load(&a.tW[l], pi * 64, (int)rank * (C / CS), (uint32_t)C * 128u, true);
-                        else for (int r = 0; r < CS && ok; r++) {   // the whole panel, slice by slice, locally
-                            const int s = ps;
-                            if (r == 0) {
-                                if (!note(cl_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) { ok = false; break; }
-                                mbar_expect_tx(bar(s), (uint32_t)C * 128u);
-                            }
-                            tma_load_2d(ring0 + s * kStage + (uint32_t)r * (uint32_t)(C / CS) * 128u, &a.tW[l], bar(s),
-                                        pi * 64, r * (C / CS));
-                            if (r == CS - 1) adv();
-                        }
+                        const int p0 = g * kConvPer, n = min(kConvPer, panels_of(l) - p0);
+                        load(&a.tW[l], p0 * 64, (int)rank * (C / CS), (uint32_t)C * 128u, n, true);
                     }
             };
-            // Before a step's extent is known only its first S panels are loaded: their stages
-            // are freed by the current step, which every CTA finishes; a stage holding one of
+            // Before a step's extent is known only its first S stages are loaded: they are
+            // freed by the current step, which every CTA finishes; a stage holding one of
             // those panels is freed only if the step runs (the cluster may be done by then).
-            const int pre = min(n_conv_panels, S);
-            if (a.n_steps > 0) conv_panels(0, pre);
+            const int pre = min(n_conv_stages, S);
+            if (a.n_steps > 0) conv_loads(0, pre);
             for (int64_t t = 0; t < a.n_steps && ok; t++) {
                 if (!note(cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status), 2, t, 0)) break;
                 int E, AL;
@@ -497,11 +501,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 const int eL = positions_of(E, L, a.rows_n);
                 for (int q0 = 0; q0 < eL && ok; q0 += PM) {
                     const int P = min(PM, eL - q0);
-                    conv_panels(q0 > 0 ? 0 : pre, n_conv_panels);
-                    for (int pi = 0; pi < P * C / 64 && ok; pi++)
-                        load(&a.tF, q0 * C + pi * 64, (int)rank * HN, (uint32_t)HN * 128u, false);
+                    conv_loads(q0 > 0 ? 0 : pre, n_conv_stages);
+                    const int np = P * C / 64;
+                    for (int p0 = 0; p0 < np && ok; p0 += kFcPer)
+                        load(&a.tF, q0 * C + p0 * 64, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0), false);
                 }
-                if (t + 1 < a.n_steps) conv_panels(0, pre);   // the next step's first panels
+                if (t + 1 < a.n_steps) conv_loads(0, pre);   // the next step's first stages
             }
             cnt[0] = it;
         }
@@ -543,19 +548,23 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             tc_fence_after();
             fence_async_smem();
             const uint32_t ID = idesc_rt(C, false);
-            for (int pi = 0; pi < panels_of(l) && mma_ok; pi++) {
+            const uint32_t pstride = pstride_of(l, P);
+            for (int p0 = 0; p0 < panels_of(l) && mma_ok; p0 += kConvPer) {
                 int s;
                 if (!take(s, l)) { mma_ok = false; break; }
-                const uint64_t bd = sdesc(ring0 + s * kStage);
-                for (int tt = 0; tt < T; tt++) {
-                    const uint64_t ad = sdesc(act0 + (uint32_t)pi * pstride_of(l, P) + (uint32_t)tt * 16384u);
-                    const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
+                const int n = min(kConvPer, panels_of(l) - p0);
+                for (int j = 0; j < n; j++) {
+                    const int pi = p0 + j;
+                    const uint64_t bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(C * 128));
+                    for (int tt = 0; tt < T; tt++) {
+                        const uint64_t ad = sdesc(act0 + (uint32_t)pi * pstride + (uint32_t)tt * 16384u);
+                        const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
 #pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
+                        for (int k = 0; k < 4; k++)
+                            umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
+                    }
                 }
-                if (kMulticastWeights) commit_mc(bar(S + s), kAll);   // stage read here: tell every CTA
-                else umma_commit(bar(S + s));
+                commit_mc(bar(S + s), kAll);   // stage read here: tell every CTA
                 adv();
             }
             if (mma_ok) umma_commit(bar(B_D));
@@ -726,23 +735,28 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             if (prof) pacc[16] += tw - tx0;   // own rows to every peer (issue)
                             fence_async_smem();
                             const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
-                            for (int pi = 0; pi < np && mma_ok; pi++) {
-                                const uint64_t tf = prof ? (uint64_t)clock64() : 0;
-                                if (!note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R)) {
-                                    mma_ok = false;
-                                    break;
-                                }
-                                fph ^= 1u << pi;
-                                if (prof) pacc[18] += (uint64_t)clock64() - tf;
+                            for (int p0 = 0; p0 < np && mma_ok; p0 += kFcPer) {
                                 int s;
                                 if (!take(s, L)) { mma_ok = false; break; }
-                                const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u), bd = sdesc(ring0 + s * kStage);
+                                const int n = min(kFcPer, np - p0);
+                                for (int j = 0; j < n; j++) {
+                                    const int pi = p0 + j;
+                                    const uint64_t tf = prof ? (uint64_t)clock64() : 0;
+                                    if (!note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R)) {
+                                        mma_ok = false;
+                                        break;
+                                    }
+                                    fph ^= 1u << pi;
+                                    if (prof) pacc[18] += (uint64_t)clock64() - tf;
+                                    const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u),
+                                                   bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(HN * 128));
 #pragma unroll
-                                for (int k = 0; k < 4; k++)
-                                    umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
-                                                (q0 | pi | k) != 0 ? 1u : 0u);
-                                if (kMulticastWeights) commit_mc(bar(S + s), kAll);
-                                else umma_commit(bar(S + s));
+                                    for (int k = 0; k < 4; k++)
+                                        umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
+                                                    (q0 | pi | k) != 0 ? 1u : 0u);
+                                }
+                                if (!mma_ok) break;
+                                commit_mc(bar(S + s), kAll);
                                 adv();
                             }
                             if (mma_ok) commit_mc(bar(B_EMPTY), kAll);
@@ -990,7 +1004,7 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
     if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }
     if (c->cap > 255 || c->rows_n < 1) { why = "window"; return false; }
-    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2, c->n_out);   // the larger layout
+    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2, c->n_out, kPanelMax);   // the larger layout
     if (y.total + 1024 > 232448) { why = "shared memory"; return false; }
     return true;
 }
@@ -1028,9 +1042,11 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.spin_ns = c->cfg.spin_limit_ns;
     int stages = 8;
     const int no = c->n_out;
-    while (stages > 2 && c_layout(CS, a.L, a.C, a.H, a.cap, stages, no).total + 1024 > 232448) stages--;
+    auto fits = [&](int st, int sb) { return c_layout(CS, a.L, a.C, a.H, a.cap, st, no, sb).total + 1024 <= 232448; };
+    a.stage_bytes = fits(3, 2 * kPanelMax) ? 2 * kPanelMax : kPanelMax;
+    while (stages > 2 && !fits(stages, a.stage_bytes)) stages--;
     a.stages = stages;
-    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no).total + 1024;
+    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no, a.stage_bytes).total + 1024;
     auto kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid> : cluster_kernel<4, kOutHybrid>)
                                  : (CS == 8 ? cluster_kernel<8, 2> : cluster_kernel<4, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
