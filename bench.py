@@ -338,7 +338,8 @@ def run_ours(args, rank, world):
         return ms, wall
 
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          persistent=not args.layerwise, cluster=not args.no_cluster)
+                          persistent=not args.layerwise, cluster=not args.no_cluster,
+                          auto_path=not args.fixed_path)
     sim.load_weights(blob32)
     st = sim.simulate(rec, off, cycles_out=cyc, stats=True)          # compile graphs, count launches
     path = sim.kernel_path
@@ -368,6 +369,9 @@ def run_ours(args, rank, world):
            "tile_widths": tiles[:(3 if w.arch.block == "residual" else 1) * w.arch.n_conv + 1],
            "kernel_mode": {"layerwise": "per-layer kernels", "persistent": "persistent",
                            "cluster": "cluster"}.get(path, path)}
+    pc = sim.path_choice
+    if pc["steps"]:
+        out["path_choice"] = pc   # the timed persistent / per-layer comparison behind kernel_mode
     out["config"]["instructions_per_step"] = N
     out["total_cycles"] = int(st.total_cycles)
     out["cpi"] = st.total_cycles / N
@@ -598,6 +602,8 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cluster", action="store_true", help="BF16: the grid-wide persistent kernel")
+    ap.add_argument("--fixed-path", action="store_true",
+                    help="no timed persistent / per-layer choice and no cluster probe: the path the flags select")
     ap.add_argument("--layerwise", action="store_true",
                     help="BF16/FP8: one kernel per layer and step instead of the persistent kernel")
     ap.add_argument("--head", default="regression", choices=["regression", "hybrid"],

@@ -110,9 +110,10 @@ typedef enum {
                                           path as it goes: the cluster kernel measures its padding
                                           extent over its first 128 steps and hands a batch whose
                                           queues stay long to the grid-wide kernels, and the grid-wide
-                                          choice times 32 steps of the persistent kernel against 32
-                                          of the per-layer kernels from the same state and runs the
-                                          rest on the faster; the context keeps that pick for later
+                                          choice times the persistent kernel (launches of 16 and 48
+                                          steps: the difference is its cost per step) and 32 steps of
+                                          the per-layer kernels from the same state and runs the
+                                          rest on the cheaper; the context keeps that pick for later
                                           calls with the same batch size, compaction and weights.
                                           Paths differ only in FP32 summation order;
                                           simulate_stats.path reports the last one used. */
@@ -362,6 +363,13 @@ simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
  * path of a long call is the persistent kernel or the per-layer kernels, whichever a timed
  * comparison picked (SIMNET_FLAG_FIXED_PATH: always the persistent kernel). */
 int32_t simnet_kernel_path(const simnet_ctx *ctx);
+
+/* The last timed choice between the persistent kernel and the per-layer kernels (see
+ * SIMNET_FLAG_FIXED_PATH): ms_out[0] = the persistent kernel's device time for *steps_out
+ * steps without its once-per-launch start, ms_out[1] = the per-layer kernels' for as many steps
+ * from the same state (with their gather).  The pick also counts the persistent kernel's start.
+ * All zero when no comparison has run on the context.  SIMNET_EINVAL for NULL pointers. */
+simnet_status simnet_path_choice(const simnet_ctx *ctx, float *ms_out, int32_t *steps_out);
 
 /* ------------------------------------------------------------------ training (Sec. 2.4) */
 

@@ -132,6 +132,8 @@ struct simnet_ctx {
     // SIMNET_PATH_LAYERWISE) and what it was measured for: batch size, compaction, weights
     int pick = SIMNET_PATH_NONE, pick_B = -1, pick_uneven = -1;
     uint64_t pick_wfp = 0;
+    float pick_ms[2] = {0.f, 0.f};   // the comparison's persistent / per-layer times
+    int pick_steps = 0;
 };
 
 namespace simnet {

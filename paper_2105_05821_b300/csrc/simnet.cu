@@ -868,36 +868,49 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
     // kernel skips the padding rows past the batch's longest queue but pays a grid
     // barrier per phase; per-layer kernels compute every row with cheaper boundaries.
     // Which wins depends on the queue lengths the predictor produces and the batch,
-    // so a long untimed call measures both: (after `warm` steps that let the queues
-    // fill) kCmp steps on each from the same state, then the faster runs the rest.
-    // The pick holds for later calls with the same batch size, compaction and weights.
+    // so a long untimed call measures both after `warm` steps that let the queues fill:
+    // the persistent kernel as two launches (kA and kA + kCmp steps: their difference is
+    // its cost per step without the once-per-launch start) and kCmp steps of the
+    // per-layer kernels, all from the same state in turn; the path with the smaller
+    // estimated cost for the remaining steps runs them.  The pick holds for later calls
+    // with the same batch size, compaction and weights.
     auto run_grid_or_layers = [&](int64_t steps, int64_t warm) -> simnet_status {
-        constexpr int64_t kCmp = 32;
+        constexpr int64_t kA = 16, kCmp = 32, kSpent = 2 * kA + 2 * kCmp;
         simnet_status st2;
-        if (timed || fixed || steps < warm + 2 * kCmp + 512) return run_persistent(steps);
+        if (timed || fixed || steps < warm + kSpent + 512) return run_persistent(steps);
         const uint64_t wfp = weights_fingerprint(c);
         if (c->pick != SIMNET_PATH_NONE && c->pick_B == B && c->pick_uneven == (int)uneven && c->pick_wfp == wfp)
             return c->pick == SIMNET_PATH_LAYERWISE ? run_layerwise(steps) : run_persistent(steps);
         if (warm > 0 && (st2 = run_persistent(warm)) != SIMNET_OK) return st2;
         if (c->g_B != B || c->g_compact != (int)uneven || !c->gexec[0])   // capture outside the timing
             if ((st2 = capture_graphs(c, B, uneven)) != SIMNET_OK) return st2;
-        cudaEvent_t e[3];
+        cudaEvent_t e[4];
         for (auto &x : e) CK(cudaEventCreate(&x));
         CK(cudaEventRecord(e[0], s));
-        if ((st2 = run_persistent(kCmp)) != SIMNET_OK) return st2;
+        if ((st2 = run_persistent(kA)) != SIMNET_OK) return st2;
         CK(cudaEventRecord(e[1], s));
-        if ((st2 = run_layerwise(kCmp)) != SIMNET_OK) return st2;
+        if ((st2 = run_persistent(kA + kCmp)) != SIMNET_OK) return st2;
         CK(cudaEventRecord(e[2], s));
-        CK(cudaEventSynchronize(e[2]));
-        float t_grid = 0.f, t_layers = 0.f;
-        cudaEventElapsedTime(&t_grid, e[0], e[1]);
-        cudaEventElapsedTime(&t_layers, e[1], e[2]);
+        if ((st2 = run_layerwise(kCmp)) != SIMNET_OK) return st2;
+        CK(cudaEventRecord(e[3], s));
+        CK(cudaEventSynchronize(e[3]));
+        float t_a = 0.f, t_b = 0.f, t_layers = 0.f;
+        cudaEventElapsedTime(&t_a, e[0], e[1]);
+        cudaEventElapsedTime(&t_b, e[1], e[2]);
+        cudaEventElapsedTime(&t_layers, e[2], e[3]);
         for (auto &x : e) cudaEventDestroy(x);
-        const int64_t rest = steps - warm - 2 * kCmp;
-        c->pick = t_layers < t_grid ? SIMNET_PATH_LAYERWISE : SIMNET_PATH_PERSISTENT;
+        const int64_t rest = steps - warm - kSpent;
+        const double per_grid = std::max(0.0, (double)(t_b - t_a) / kCmp);
+        const double start_grid = std::max(0.0, (double)t_a - kA * per_grid);
+        const double cost_grid = start_grid + per_grid * (double)rest, cost_layers = (double)t_layers / kCmp * (double)rest;
+        // within 3% the persistent kernel stays: its later steps tend to run shorter extents
+        c->pick = cost_layers < 0.97 * cost_grid ? SIMNET_PATH_LAYERWISE : SIMNET_PATH_PERSISTENT;
         c->pick_B = B;
         c->pick_uneven = (int)uneven;
         c->pick_wfp = wfp;
+        c->pick_ms[0] = (float)(per_grid * kCmp);
+        c->pick_ms[1] = t_layers;
+        c->pick_steps = (int)kCmp;
         return c->pick == SIMNET_PATH_LAYERWISE ? run_layerwise(rest) : run_persistent(rest);
     };
     launches = resume ? 0 : 1;   // init_state
@@ -1043,6 +1056,14 @@ extern "C" simnet_status simnet_kernel_times(simnet_ctx *c, float *ms_out, int64
 }
 
 extern "C" int32_t simnet_kernel_path(const simnet_ctx *c) { return c ? c->path : -1; }
+
+extern "C" simnet_status simnet_path_choice(const simnet_ctx *c, float *ms_out, int32_t *steps_out) {
+    if (!c || !ms_out || !steps_out) return SIMNET_EINVAL;
+    ms_out[0] = c->pick_ms[0];
+    ms_out[1] = c->pick_ms[1];
+    *steps_out = c->pick_steps;
+    return SIMNET_OK;
+}
 
 extern "C" simnet_status simnet_phase_detail(simnet_ctx *c, uint64_t *out, int32_t n) {
     if (!c) return SIMNET_EINVAL;

@@ -40,7 +40,8 @@ EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_e
            "simnet_kernel_times", "simnet_cnn_forward_noalloc", "simnet_noalloc_scratch_bytes",
            "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
            "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune",
-           "simnet_simulate_steps", "simnet_state_save", "simnet_state_load", "simnet_kernel_path"]
+           "simnet_simulate_steps", "simnet_state_save", "simnet_state_load", "simnet_kernel_path",
+           "simnet_path_choice"]
 STATE_KINDS = {"sim": 0, "train": 1}
 
 
@@ -129,6 +130,8 @@ def lib() -> C.CDLL:
         L.simnet_state_load.argtypes = [P, C.c_int32, P, C.c_size_t, P]
         L.simnet_kernel_path.restype = C.c_int32
         L.simnet_kernel_path.argtypes = [P]
+        L.simnet_path_choice.restype = C.c_int
+        L.simnet_path_choice.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -256,6 +259,15 @@ class Simnet:
     def kernel_path(self) -> str:
         """Kernel path of the last simulate call: layerwise, persistent or cluster."""
         return PATHS.get(int(lib().simnet_kernel_path(self._h)), "none")
+
+    @property
+    def path_choice(self) -> dict:
+        """The last timed persistent / per-layer comparison: device ms of each over the
+        same number of steps from the same state (zeros if none ran)."""
+        ms = (C.c_float * 2)()
+        n = C.c_int32()
+        self._check(lib().simnet_path_choice(self._h, ms, C.byref(n)))
+        return {"persistent_ms": float(ms[0]), "layerwise_ms": float(ms[1]), "steps": int(n.value)}
 
     def phase_detail(self, n_layers):
         """Per GEMM layer: summed ns to first data, last MMA, epilogue done, barrier passed (CTA 0)."""
