@@ -120,18 +120,17 @@ __device__ __forceinline__ uint32_t cl_map(uint32_t a, uint32_t r) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(o) : "r"(a), "r"(r));
     return o;
 }
-__device__ __forceinline__ void cl_st_v4(uint32_t a, uint4 v) {
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+// Asynchronous stores into CTA r's shared memory (a and bar from mapa): the bytes are
+// counted (complete_tx) on the barrier `bar` there; the storing thread does not wait.
+__device__ __forceinline__ void cl_st_async_v4(uint32_t a, uint4 v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1,%2,%3,%4}, [%5];" ::"r"(a),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ void cl_st_v2f(uint32_t a, float x, float y) {
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1,%2};" ::"r"(a), "f"(x), "f"(y) : "memory");
-}
-__device__ __forceinline__ void cl_st_v2i(uint32_t a, int x, int y) {
-    asm volatile("st.shared::cluster.v2.u32 [%0], {%1,%2};" ::"r"(a), "r"(x), "r"(y) : "memory");
-}
-__device__ __forceinline__ void cl_arrive(uint32_t remote_bar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote_bar) : "memory");
+__device__ __forceinline__ void cl_st_async_v2(uint32_t a, uint32_t x, uint32_t y, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1,%2}, [%3];" ::"r"(a), "r"(x),
+                 "r"(y), "r"(bar)
+                 : "memory");
 }
 __device__ __forceinline__ bool cl_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -263,6 +262,16 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[2][32]) 
         : "r"(taddr), "r"(taddr + 32u)
         : "memory");
 }
+// 16 consecutive TMEM columns of this warp's 32 lanes, waited for.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
 // 32 or 64 columns from taddr into r[0] (and r[1]).
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int cols, uint32_t (&r)[2][32]) {
     if (cols > 32) tmem_ld64(taddr, r);
@@ -337,6 +346,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     auto bar = [&](int i) { return smem_u32(&bars[i]); };
     // 0..S-1 weight panel full, S..2S-1 empty; then:
     // B_FULL + i: the peers' rows of FC1 operand panel i (at most 8 panels a pass)
+    // bytes a phase of B_PART / B_EXT receives: every CTA's FC2 partials (two column halves)
+    // for this CTA's slots; every CTA's (extent, live count)
+    constexpr uint32_t kPartBytes = 2u * CS * SPC * PF * 4u, kExtBytes = CS * 8u;
     const int B_D = 2 * S, B_EMPTY = 2 * S + 1, B_DFC = 2 * S + 2, B_PART = 2 * S + 3, B_EXT = 2 * S + 4,
               B_FIN = 2 * S + 6, B_FULL = 2 * S + 7;
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
@@ -369,9 +381,14 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         for (int i = 0; i < 8; i++) mbar_init(bar(B_FULL + i), 1);   // thread 0's expect_tx; the peers' copies
         mbar_init(bar(B_EMPTY), CS);
         mbar_init(bar(B_DFC), 1);
-        mbar_init(bar(B_PART), CS * 2);
-        mbar_init(bar(B_EXT), CS);
-        mbar_init(bar(B_EXT + 1), CS);
+        // partial sums and extents arrive by st.async, counted in bytes: one local
+        // arrival (with the byte count) per phase, made here for the first phases
+        mbar_init(bar(B_PART), 1);
+        mbar_init(bar(B_EXT), 1);
+        mbar_init(bar(B_EXT + 1), 1);
+        mbar_expect_tx(bar(B_PART), kPartBytes);
+        mbar_expect_tx(bar(B_EXT), kExtBytes);
+        mbar_expect_tx(bar(B_EXT + 1), kExtBytes);
         mbar_init(bar(B_FIN), 1);
         *abort_f = 0;
         cnt[0] = cnt[1] = 0;
@@ -579,14 +596,15 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 al += __shfl_xor_sync(0xffffffffu, al, o);
             }
             if (lane < CS) {   // one lane per destination CTA: the release arrives overlap
-                cl_st_v2i(cl_map(smem_u32(&ext_in[nb * CS + rank]), (uint32_t)lane), mx, al);
-                cl_arrive(cl_map(bar(B_EXT + nb), (uint32_t)lane));
+                cl_st_async_v2(cl_map(smem_u32(&ext_in[nb * CS + rank]), (uint32_t)lane), (uint32_t)mx, (uint32_t)al,
+                               cl_map(bar(B_EXT + nb), (uint32_t)lane));
             }
         };
         if (wi == 0) send_ext(0);
         for (int64_t t = 0; t < a.n_steps; t++) {
             if (tid == 0) {
                 const bool ok = note(sleep_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status, true), 4, t, 0);
+                if (ok) mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
                 int E, AL;
                 read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 ctl[0] = positions_of(E, L, a.rows_n);
@@ -798,15 +816,15 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             }
                         }
                     } else {
-                        // 22 outputs per neuron: 32 TMEM columns at a time keeps the
-                        // accumulators and one chunk in registers
+                        // 22 outputs per neuron: 16 TMEM columns at a time keeps the
+                        // accumulators and one chunk in registers (no spills)
 #pragma unroll 1
-                        for (int bi = 0; bi < cols / 32; bi++) {
-                            uint32_t r32[32];
-                            tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)(j0 + bi * 32), r32);
+                        for (int bi = 0; bi < cols / 16; bi++) {
+                            uint32_t r32[16];
+                            tmem_ld16(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)(j0 + bi * 16), r32);
 #pragma unroll
-                            for (int jj = 0; jj < 32; jj++) {
-                                const int j = j0 + bi * 32 + jj;
+                            for (int jj = 0; jj < 16; jj++) {
+                                const int j = j0 + bi * 16 + jj;
                                 const float v = fmaxf(__uint_as_float(r32[jj]) + s_fb[j] + s_Se[j], 0.f);
                                 const float4 *wv = reinterpret_cast<const float4 *>(s_w2 + j * 24);
 #pragma unroll
@@ -823,25 +841,29 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 }
                 tc_fence_before();
                 // cluster slot g = qd * 32 + lane belongs to CTA g / SPC, where it is slot g % SPC
+                const uint64_t te0 = prof ? (uint64_t)clock64() : 0;
+                if (prof) pacc[30] += te0 - tp;   // FC1 epilogue arithmetic (thread 0)
                 const int g = qd * 32 + lane, owner = g / SPC;
                 const uint32_t dst =
                     cl_map(smem_u32(&part[(((int)rank * 2 + half) * SPC + g % SPC) * PF]), (uint32_t)owner);
+                const uint32_t pb = cl_map(bar(B_PART), (uint32_t)owner);
                 if constexpr (NO == 2) {
-                    cl_st_v2f(dst, pf, pe);
+                    cl_st_async_v2(dst, __float_as_uint(pf), __float_as_uint(pe), pb);
                 } else {
 #pragma unroll
                     for (int q4 = 0; q4 < 6; q4++)
-                        cl_st_v4(dst + 16u * q4, make_uint4(__float_as_uint(ph[4 * q4]), __float_as_uint(ph[4 * q4 + 1]),
-                                                            __float_as_uint(ph[4 * q4 + 2]),
-                                                            __float_as_uint(ph[4 * q4 + 3])));
+                        cl_st_async_v4(dst + 16u * q4,
+                                       make_uint4(__float_as_uint(ph[4 * q4]), __float_as_uint(ph[4 * q4 + 1]),
+                                                  __float_as_uint(ph[4 * q4 + 2]), __float_as_uint(ph[4 * q4 + 3])),
+                                       pb);
                 }
-                __syncwarp();
-                if (g % SPC == 0) cl_arrive(cl_map(bar(B_PART), (uint32_t)owner));
+                if (prof) pacc[31] += (uint64_t)clock64() - te0;   // partial sums to their owners
                 mark(9);
             }
             // head, clock and queue update, drain: one thread per slot (warp 2)
             if (wi == 0) {
                 bool ok = note(sleep_wait(bar(B_PART), (uint32_t)(t & 1), lim, abort_f, a.status, true), 9, t, R);
+                if (ok && lane == 0) mbar_expect_tx(bar(B_PART), kPartBytes);   // the next step's phase
                 ok = __all_sync(0xffffffffu, ok);
                 mark(10);
                 const int s = lane;
