@@ -685,8 +685,6 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         const bool valid = m < Rl;
                         const int p = m / SPC, s = m % SPC;
                         const int c0 = half * (C / 2), nb = C / 64;   // this warp's channels: nb blocks of 32
-                        uint32_t r32[2][32];
-                        tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0), C / 2, r32);
                         int row;
                         uint32_t base, pstride;
                         if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
@@ -699,15 +697,20 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             pstride = 16384u;
                         }
                         const int kb = last ? p * C + c0 : (p & 1) * C + c0;
-#pragma unroll
-                        for (int bi = 0; bi < 2; bi++) {
-                            if (bi >= nb) break;
+                        // one block of 32 columns at a time (a TMEM load costs ~80 cycles; holding
+                        // both blocks' registers at once spilled)
+#pragma unroll 1
+                        for (int bi = 0; bi < nb; bi++) {
+                            uint32_t r32[32];
+                            tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0 + bi * 32),
+                                      r32);
+                            const float2 *cb = reinterpret_cast<const float2 *>(s_cb + l * C + c0 + bi * 32);
                             uint32_t w[16];
 #pragma unroll
                             for (int j = 0; j < 16; j++) {
-                                const int ch = c0 + bi * 32 + 2 * j;
-                                const float v0 = fmaxf(__uint_as_float(r32[bi][2 * j]) + s_cb[l * C + ch], 0.f);
-                                const float v1 = fmaxf(__uint_as_float(r32[bi][2 * j + 1]) + s_cb[l * C + ch + 1], 0.f);
+                                const float2 b = cb[j];
+                                const float v0 = fmaxf(__uint_as_float(r32[2 * j]) + b.x, 0.f);
+                                const float v1 = fmaxf(__uint_as_float(r32[2 * j + 1]) + b.y, 0.f);
                                 __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
                                 w[j] = *reinterpret_cast<uint32_t *>(&b2);
                             }
