@@ -704,15 +704,22 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             uint32_t r32[32];
                             tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0 + bi * 32),
                                       r32);
-                            const float2 *cb = reinterpret_cast<const float2 *>(s_cb + l * C + c0 + bi * 32);
+                            // bias four channels to a load; ReLU on the rounded pairs (rounding to
+                            // nearest keeps the sign, so this equals rounding the ReLU output)
+                            const float4 *cb = reinterpret_cast<const float4 *>(s_cb + l * C + c0 + bi * 32);
+                            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
                             uint32_t w[16];
 #pragma unroll
-                            for (int j = 0; j < 16; j++) {
-                                const float2 b = cb[j];
-                                const float v0 = fmaxf(__uint_as_float(r32[2 * j]) + b.x, 0.f);
-                                const float v1 = fmaxf(__uint_as_float(r32[2 * j + 1]) + b.y, 0.f);
-                                __nv_bfloat162 b2 = __floats2bfloat162_rn(v0, v1);
-                                w[j] = *reinterpret_cast<uint32_t *>(&b2);
+                            for (int j = 0; j < 8; j++) {
+                                const float4 b = cb[j];
+                                __nv_bfloat162 p0 = __floats2bfloat162_rn(__uint_as_float(r32[4 * j]) + b.x,
+                                                                          __uint_as_float(r32[4 * j + 1]) + b.y);
+                                __nv_bfloat162 p1 = __floats2bfloat162_rn(__uint_as_float(r32[4 * j + 2]) + b.z,
+                                                                          __uint_as_float(r32[4 * j + 3]) + b.w);
+                                p0 = __hmax2(p0, zero2);
+                                p1 = __hmax2(p1, zero2);
+                                w[2 * j] = *reinterpret_cast<uint32_t *>(&p0);
+                                w[2 * j + 1] = *reinterpret_cast<uint32_t *>(&p1);
                             }
 #pragma unroll
                             for (int j = 0; j < 4; j++) {
