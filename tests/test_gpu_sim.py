@@ -207,8 +207,11 @@ def test_grid_path_choice_keeps_the_state(arch, precision):
     ref = oracle.simulate(cfg, trace.records, trace.offsets, replay=replay)
     blob = I.workload_weights(I.Workload("g", arch, 1, 1, seed=29))
     sim, _ = make_sim(arch, precision, blob=blob, auto_path=True)
+    assert sim.path_choice == {"persistent_ms": 0.0, "layerwise_ms": 0.0, "steps": 0}
     g = run_gpu(sim, trace, replay=replay)
     assert sim.kernel_path in ("persistent", "layerwise")
+    pc = sim.path_choice                     # the comparison that ran: both times measured
+    assert pc["steps"] == 32 and pc["persistent_ms"] > 0 and pc["layerwise_ms"] > 0
     np.testing.assert_array_equal(g["cycles"], ref.cycles)
     assert g["stats"].evictions == int(ref.evictions.sum()) > 0
     f = run_gpu(sim, trace)
