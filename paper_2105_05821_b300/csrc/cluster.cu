@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 int E, AL;
                 read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 if (AL == 0) break;
-                const int eL = positions_of(E, L, a.rows_n);
+                const int eL = max(positions_of(E, L, a.rows_n), min(PM, a.rows_n));   // as the workers
                 for (int q0 = 0; q0 < eL && ok; q0 += PM) {
                     const int P = min(PM, eL - q0);
                     conv_loads(q0 > 0 ? 0 : pre, n_conv_stages);
@@ -601,13 +601,48 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             }
         };
         if (wi == 0) send_ext(0);
+        // feature rows of positions q0 .. q0 + P - 1 into the first layer's operand
+        auto build_rows = [&](int q0, int P) {
+            // layer-0 A row (pair, slot), K = the pair's two rows
+            for (int f = tid; f < P * (1 << L) * SPC; f += kWk) {
+                const int s = f % SPC, rr = f / SPC, r = q0 * (1 << L) + rr;
+                const int m = (rr >> 1) * SPC + s;
+                uint4 ch[8];
+                const int ql = s_ql[s];
+                if (s_al[s] && r <= ql) {
+                    const uint32_t cur = recb[s * 4 + (s_p[s] & 3)];
+                    if (r == 0) {
+                        row_chunks_bf16(cur, cur, false, 0, 0u, 0u, ch);
+                    } else {
+                        int idx = s_qs[s] + ql - r;
+                        if (idx >= cap) idx -= cap;
+                        const uint64_t ent = qring[s * cap + idx];
+                        row_chunks_bf16(entry_rec(ent), cur, true, entry_res(ent, s_tick[s]), entry_e(ent),
+                                        entry_s(ent), ch);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; j++) ch[j] = make_uint4(0, 0, 0, 0);
+                }
+                uint8_t *dst = sm + y.act + (uint32_t)(rr & 1) * pstride_of(0, P) + (uint32_t)m * 128u;
+#pragma unroll
+                for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(dst + ((j ^ (m & 7)) << 4)) = ch[j];
+            }
+            fence_async_smem();
+        };
+        // The first pass always covers P0 positions: its rows need no cluster-wide extent, so
+        // they are built while the extents are exchanged (positions of the pass past the
+        // extent are padding rows, computed rather than taken from S[e]: the same result).
+        const int P0 = min(PM, a.rows_n);
         for (int64_t t = 0; t < a.n_steps; t++) {
+            workers_sync();   // the previous step's head (warp 2) is visible
+            build_rows(0, P0);
             if (tid == 0) {
                 const bool ok = note(sleep_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status, true), 4, t, 0);
                 if (ok) mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
                 int E, AL;
                 read_ext<CS>(ext_in, (int)(t & 1), E, AL);
-                ctl[0] = positions_of(E, L, a.rows_n);
+                ctl[0] = max(positions_of(E, L, a.rows_n), P0);
                 ctl[1] = (!ok || AL == 0 || *abort_f) ? 1 : 0;
             }
             workers_sync();
@@ -624,34 +659,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 cp_commit();
             }
             for (int q0 = 0; q0 < eL; q0 += PM) {
-                const int P = min(PM, eL - q0);
-                // feature rows of the pass: layer-0 A row (pair, slot), K = the pair's two rows
-                for (int f = tid; f < P * (1 << L) * SPC; f += kWk) {
-                    const int s = f % SPC, rr = f / SPC, r = q0 * (1 << L) + rr;
-                    const int m = (rr >> 1) * SPC + s;
-                    uint4 ch[8];
-                    const int ql = s_ql[s];
-                    if (s_al[s] && r <= ql) {
-                        const uint32_t cur = recb[s * 4 + (s_p[s] & 3)];
-                        if (r == 0) {
-                            row_chunks_bf16(cur, cur, false, 0, 0u, 0u, ch);
-                        } else {
-                            int idx = s_qs[s] + ql - r;
-                            if (idx >= cap) idx -= cap;
-                            const uint64_t ent = qring[s * cap + idx];
-                            row_chunks_bf16(entry_rec(ent), cur, true, entry_res(ent, s_tick[s]), entry_e(ent),
-                                            entry_s(ent), ch);
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 8; j++) ch[j] = make_uint4(0, 0, 0, 0);
-                    }
-                    uint8_t *dst = sm + y.act + (uint32_t)(rr & 1) * pstride_of(0, P) + (uint32_t)m * 128u;
-#pragma unroll
-                    for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(dst + ((j ^ (m & 7)) << 4)) = ch[j];
+                const int P = min(PM, eL - q0);   // P0 for the first pass
+                if (q0 > 0) {
+                    build_rows(q0, P);
+                    workers_sync();
                 }
-                fence_async_smem();
-                workers_sync();
                 mark(1);
                 for (int l = 0; l < L; l++) {
                     const bool last = l == L - 1;
