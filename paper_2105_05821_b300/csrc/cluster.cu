@@ -2,8 +2,8 @@
 // independent thread-block clusters (BF16 CNNs with 2 or 3 conv layers of 64
 // or 128 channels).
 //
-// Sub-traces never interact (Sec. 3.3), so a cluster of 4 CTAs takes 128
-// batch slots for the whole call, 32 per CTA, and needs no grid-wide
+// Sub-traces never interact (Sec. 3.3), so a cluster of CS = 4 or 8 CTAs takes
+// 128 batch slots for the whole call, 128 / CS per CTA, and needs no grid-wide
 // synchronisation at all:
 //   * each CTA keeps its slots' state in shared memory: position, curTick, the
 //     processor-queue ring and its counters (Sec. 3.2), and the instruction
@@ -13,21 +13,21 @@
 //     writes the feature rows (Sec. 2.2) of its slots that those positions
 //     depend on straight into shared memory and runs the k=2 / stride-2 conv
 //     pyramid on them (Sec. 2.3), one tcgen05 MMA per 128-row tile and layer
-//     (rows as A, the layer's weights streamed by TMA as B); layer l's
-//     epilogue writes layer l+1's operand in place, rows 2j and 2j+1 of a slot
-//     side by side along K;
+//     (rows as A, the layer's weights streamed by TMA multicast as B, several
+//     panels to a pipeline stage); layer l's epilogue writes layer l+1's
+//     operand in place, rows 2j and 2j+1 of a slot side by side along K;
 //   * the last conv layer's rows of all 128 slots are exchanged through
-//     distributed shared memory and every CTA accumulates FC1 for its quarter
-//     of the hidden neurons in TMEM over the passes; positions at or past the
-//     extent are constant rows whose FC1 contribution S[e] was tabulated when
-//     the weights were loaded;
+//     distributed shared memory by bulk copies, and every CTA accumulates FC1
+//     for its 1 / CS of the hidden neurons in TMEM over the passes; positions
+//     at or past the extent are constant rows whose FC1 contribution S[e] was
+//     tabulated when the weights were loaded;
 //   * the FC1 epilogue folds FC2 into per-slot partial sums that go to each
-//     slot's owner CTA, where one thread per slot runs the head, the clock and
-//     queue update and the drain (Eq. 1); the CTA then shares its new extent
-//     with the cluster.
+//     slot's owner CTA (st.async), where one thread per slot runs the head,
+//     the clock and queue update and the drain (Eq. 1); the CTA then shares its
+//     new extent with the cluster (st.async).
 // Every wait is bounded (globaltimer); an expired wait records a timeout and
 // the CTA leaves at the next step boundary; a final cluster barrier keeps each
-// CTA's shared memory alive until its peers no longer write to it.
+// CTA's shared memory alive until its peers no longer start writes into it.
 #include <algorithm>
 #include <cstring>
 #include <string>
