@@ -1,0 +1,64 @@
+"""Randomised parity of the integer state machine on every GPU kernel path.
+
+Each case draws a CNN shape, a retire width and rule, ragged sub-trace lengths
+(empty, single-instruction and long ones mixed), a precision and a kernel path,
+and replays seeded random latencies F, E (Sec. 3.2): the CNN's outputs are
+then irrelevant, so the per-sub-trace cycle counts, the evictions and the
+logged latencies must equal the oracle's bit for bit on the cluster kernel,
+the grid-persistent kernel, the per-layer kernels and the FP32 form alike.
+The latency mixes cover an empty retire budget (F = 0), queues that overflow
+(long E) and queues that stay short.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2105_05821_b300 import inputs as I
+
+from gpu_util import make_sim, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [I.ARCH_SMALL(32), I.ARCH_MID]
+# (precision, Simnet keyword arguments, kernel path the call must report)
+PATHS = [
+    ("bf16", {}, "cluster"),
+    ("bf16", {"cluster": False}, "persistent"),
+    ("bf16", {"persistent": False}, "layerwise"),
+    ("fp8", {}, "persistent"),
+    ("fp8", {"persistent": False}, "layerwise"),
+    ("fp32", {}, "layerwise"),
+]
+
+
+def latencies(rng, n, mix):
+    if mix == "short":      # queues stay short: everything retires within a few steps
+        f, e = rng.integers(1, 4, n), rng.integers(0, 6, n)
+    elif mix == "overflow":  # F = 1, long E: queues fill to capacity and evict
+        f, e = np.ones(n, np.int64), rng.integers(100, 256, n)
+    else:                   # F = 0 in a third of the steps (no retire budget), wide E
+        f, e = rng.integers(0, 3, n), rng.integers(0, 60, n)
+    return np.stack([f, e], 1).astype(np.uint8)
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_replay_bit_exact(case):
+    rng = np.random.default_rng(1000 + case)
+    arch = SHAPES[case // len(PATHS)]
+    precision, kw, path = PATHS[case % len(PATHS)]
+    rw, strict = int(rng.integers(1, 9)), bool(rng.integers(0, 2))
+    n_sub = int(rng.choice([3, 40, 200]))
+    lengths = rng.integers(0, 400, n_sub)
+    lengths[rng.random(n_sub) < 0.1] = 0
+    lengths[rng.random(n_sub) < 0.1] = 1
+    trace = I.small_trace(lengths.tolist(), seed=2000 + case)
+    replay = latencies(rng, trace.n_instructions, ["short", "overflow", "mixed"][case % 3])
+    cfg = oracle.Config.of(arch, retire_width=rw, retire_strict=strict)
+    ref = oracle.simulate(cfg, trace.records, trace.offsets, replay=replay, logs=True)
+    sim, _ = make_sim(arch, precision, retire_width=rw, strict=strict, **kw)
+    g = run_gpu(sim, trace, replay=replay)
+    assert sim.kernel_path == path
+    np.testing.assert_array_equal(g["cycles"], ref.cycles)
+    np.testing.assert_array_equal(g["lat"], ref.lat)
+    assert g["stats"].evictions == int(ref.evictions.sum())
+    assert g["stats"].total_cycles == int(ref.cycles.sum())
