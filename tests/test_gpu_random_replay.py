@@ -5,7 +5,9 @@ Each case draws a CNN shape, a retire width and rule, ragged sub-trace lengths
 and replays seeded random latencies F, E (Sec. 3.2): the CNN's outputs are
 then irrelevant, so the per-sub-trace cycle counts, the evictions and the
 logged latencies must equal the oracle's bit for bit on the cluster kernel,
-the grid-persistent kernel, the per-layer kernels and the FP32 form alike.
+the grid-persistent kernel, the per-layer kernels and the FP32 form alike, for
+the regression and hybrid heads and (with a third, store latency) the memory
+write queue.
 The latency mixes cover an empty retire budget (F = 0), queues that overflow
 (long E) and queues that stay short.
 """
@@ -41,18 +43,29 @@ def latencies(rng, n, mix):
     return np.stack([f, e], 1).astype(np.uint8)
 
 
-@pytest.mark.parametrize("case", range(12))
+HYBRID = I.Arch(96, 3, 128, 512, "hybrid")               # 22 FC2 outputs: other kernel instances
+STORE = I.Arch(32, 2, 64, 256, store_queue=True)          # three latencies, memory write queue
+CASES = ([(a, p) for a in SHAPES for p in PATHS] + [(HYBRID, p) for p in PATHS]
+         + [(STORE, p) for p in PATHS if p[2] != "cluster"])   # the cluster kernel does not take stores
+
+
+def latencies3(rng, n, mix):
+    s = rng.integers(0, 80, n) if mix != "short" else rng.integers(0, 6, n)
+    return np.concatenate([latencies(rng, n, mix), s[:, None].astype(np.uint8)], 1)
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
 def test_random_replay_bit_exact(case):
     rng = np.random.default_rng(1000 + case)
-    arch = SHAPES[case // len(PATHS)]
-    precision, kw, path = PATHS[case % len(PATHS)]
+    arch, (precision, kw, path) = CASES[case]
     rw, strict = int(rng.integers(1, 9)), bool(rng.integers(0, 2))
     n_sub = int(rng.choice([3, 40, 200]))
     lengths = rng.integers(0, 400, n_sub)
     lengths[rng.random(n_sub) < 0.1] = 0
     lengths[rng.random(n_sub) < 0.1] = 1
     trace = I.small_trace(lengths.tolist(), seed=2000 + case)
-    replay = latencies(rng, trace.n_instructions, ["short", "overflow", "mixed"][case % 3])
+    mix = ["short", "overflow", "mixed"][case % 3]
+    replay = (latencies3 if arch.store_queue else latencies)(rng, trace.n_instructions, mix)
     cfg = oracle.Config.of(arch, retire_width=rw, retire_strict=strict)
     ref = oracle.simulate(cfg, trace.records, trace.offsets, replay=replay, logs=True)
     sim, _ = make_sim(arch, precision, retire_width=rw, strict=strict, **kw)
