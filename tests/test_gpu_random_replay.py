@@ -6,8 +6,8 @@ and replays seeded random latencies F, E (Sec. 3.2): the CNN's outputs are
 then irrelevant, so the per-sub-trace cycle counts, the evictions and the
 logged latencies must equal the oracle's bit for bit on the cluster kernel,
 the grid-persistent kernel, the per-layer kernels and the FP32 form alike, for
-the regression and hybrid heads and (with a third, store latency) the memory
-write queue.
+the regression and hybrid heads, residual blocks and (with a third, store
+latency) the memory write queue.
 The latency mixes cover an empty retire budget (F = 0), queues that overflow
 (long E) and queues that stay short.
 """
@@ -45,8 +45,10 @@ def latencies(rng, n, mix):
 
 HYBRID = I.Arch(96, 3, 128, 512, "hybrid")               # 22 FC2 outputs: other kernel instances
 STORE = I.Arch(32, 2, 64, 256, store_queue=True)          # three latencies, memory write queue
+RESID = I.Arch(32, 2, 64, 256, block="residual")          # residual blocks: BF16 and FP32 only
 CASES = ([(a, p) for a in SHAPES for p in PATHS] + [(HYBRID, p) for p in PATHS]
-         + [(STORE, p) for p in PATHS if p[2] != "cluster"])   # the cluster kernel does not take stores
+         + [(STORE, p) for p in PATHS if p[2] != "cluster"]    # the cluster kernel does not take stores
+         + [(RESID, p) for p in PATHS if p[0] != "fp8" and p[2] != "cluster"])
 
 
 def latencies3(rng, n, mix):
