@@ -73,16 +73,17 @@ __host__ __device__ inline int pass_positions(int L) { return 8 >> (L - 1); }
 
 // Shared-memory layout, offsets from the 1024-byte aligned base.
 struct CLay {
-    uint32_t ring, act, fc1a, qring, rec, part, prm, slot, misc, bars, total;
+    uint32_t ring, act, fc1a, qring, mring, rec, part, prm, slot, misc, bars, total;
 };
 
 // FC2 partial sums per (source CTA, column half, slot): 2 floats (regression
-// head), or the hybrid head's 22 padded to 24 (16-byte stores).
-__host__ __device__ inline int part_floats(int no) { return no == 2 ? 2 : 24; }
+// head), 3 padded to 4 (regression head with the store latency), or the hybrid
+// head's 22 padded to 24 (16-byte stores).
+__host__ __device__ inline int part_floats(int no) { return no == 2 ? 2 : no == 3 ? 4 : 24; }
 // prm: conv biases [L*C] | FC1 bias [HN] | S[e] [HN] | b2 [24] | FC2 rows of this
-// CTA's neurons: [2][HN] (regression) or [HN][24] (hybrid, padded).
+// CTA's neurons: [2][HN] or [3][HN] (regression) or [HN][24] (hybrid, padded).
 __host__ __device__ inline int prm_floats(int L, int C, int HN, int no) {
-    return L * C + 2 * HN + 24 + (no == 2 ? 2 * HN : 24 * HN);
+    return L * C + 2 * HN + 24 + (no == 2 ? 2 * HN : no == 3 ? 3 * HN : 24 * HN);
 }
 
 __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages, int no, int stage_bytes) {
@@ -98,11 +99,12 @@ __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, i
     y.act = (uint32_t)stages * (uint32_t)stage_bytes;
     y.fc1a = al_up(y.act + actb, 1024);
     y.qring = y.fc1a + 256u * (uint32_t)(pass_positions(L) * C);           // 128 slots x positions x C BF16
-    y.rec = y.qring + (uint32_t)SPC * cap * 8;
+    y.mring = y.qring + (uint32_t)SPC * cap * 8;                            // memory write queues (n_out 3)
+    y.rec = y.mring + (no == 3 ? (uint32_t)SPC * cap * 8 : 0u);
     y.part = al_up(y.rec + SPC * 4 * 4, 16);
     y.prm = y.part + 2 * CS * SPC * 4 * part_floats(no);
     y.slot = al_up(y.prm + (uint32_t)prm_floats(L, C, HN, no) * 4, 16);
-    y.misc = y.slot + SPC * 8 + 8 * SPC * 4;
+    y.misc = y.slot + SPC * 8 + 10 * SPC * 4;
     y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8, 8);   // + 32 phase counters (profiling)
     y.total = y.bars + (2 * stages + 16) * 8;
     return y;
@@ -321,7 +323,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int L = a.L, C = a.C, HN = a.H / CS, S = a.stages, cap = a.cap, PM = pass_positions(L);
     const uint32_t kStage = (uint32_t)a.stage_bytes;
-    constexpr int PF = NO == 2 ? 2 : 24;   // part_floats(NO)
+    constexpr bool SQ = NO == 3;            // store latency and memory write queue (Sec. 3.2)
+    constexpr int NL = SQ ? 3 : 2;          // latencies per instruction
+    constexpr int PF = NO == 2 ? 2 : NO == 3 ? 4 : 24;   // part_floats(NO)
     const CLay y = c_layout(CS, L, C, a.H, cap, S, NO, a.stage_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cl_rank();
@@ -360,8 +364,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     int64_t *s_o = reinterpret_cast<int64_t *>(sm + y.slot);
     int32_t *s_b = reinterpret_cast<int32_t *>(s_o + SPC), *s_n = s_b + SPC, *s_p = s_n + SPC,
             *s_tick = s_p + SPC, *s_qs = s_tick + SPC, *s_ql = s_qs + SPC, *s_ev = s_ql + SPC,
-            *s_al = s_ev + SPC;
+            *s_al = s_ev + SPC, *s_ms = s_al + SPC, *s_ml = s_ms + SPC;   // s_ms/s_ml: write queue
     uint64_t *qring = reinterpret_cast<uint64_t *>(sm + y.qring);
+    uint64_t *mring = reinterpret_cast<uint64_t *>(sm + y.mring);   // used with SQ only
     uint32_t *recb = reinterpret_cast<uint32_t *>(sm + y.rec);   // [slot][position & 3]
     float *part = reinterpret_cast<float *>(sm + y.part);       // [source CTA * 2 + half][slot][PF]
     int2 *ext_in = reinterpret_cast<int2 *>(sm + y.misc);       // [step parity][source CTA]
@@ -406,12 +411,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     for (int j = threadIdx.x; j < HN; j += blockDim.x) {
         const int nn = (int)rank * HN + j;
         s_fb[j] = a.fbias[nn];
-        if constexpr (NO == 2) {
+        if constexpr (NO == 2 || NO == 3) {
             s_w2f[j] = a.w2[nn];
             s_w2e[j] = a.w2[a.H + nn];
+            if constexpr (SQ) s_w2f[2 * HN + j] = a.w2[2 * a.H + nn];
         }
     }
-    if constexpr (NO != 2)
+    if constexpr (NO != 2 && NO != 3)
         for (int i = threadIdx.x; i < HN * 24; i += blockDim.x) {
             const int j = i / 24, o = i % 24;
             s_w2[i] = o < NO ? a.w2[(size_t)o * a.H + (int)rank * HN + j] : 0.f;
@@ -431,6 +437,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 n = (int)(A->offsets[b + 1] - o);
                 p = A->pos[b];
                 for (int i = lane; i < cap; i += 32) qring[s * cap + i] = A->ring[(size_t)b * cap + i];
+                if constexpr (SQ)
+                    for (int i = lane; i < cap; i += 32) mring[s * cap + i] = A->mring[(size_t)b * cap + i];
             }
             if (lane == 0) {
                 s_b[s] = b;
@@ -442,6 +450,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 s_ql[s] = b >= 0 ? A->qlen[b] : 0;
                 s_ev[s] = b >= 0 ? A->evict[b] : 0;
                 s_al[s] = (b >= 0 && p < n) ? 1 : 0;
+                s_ms[s] = (SQ && b >= 0) ? A->mstart[b] : 0;
+                s_ml[s] = (SQ && b >= 0) ? A->mlen[b] : 0;
                 if (p < n) recb[s * 4 + (p & 3)] = A->records[o + p];
                 if (p + 1 < n) recb[s * 4 + ((p + 1) & 3)] = A->records[o + p + 1];
             }
@@ -589,7 +599,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // extent of this CTA's slots (longest queue + 1) and live count, to every CTA of the cluster
         auto send_ext = [&](int nb) {   // warp 2 only
             int mx = 0, al = 0;
-            if (lane < SPC && s_al[lane]) { mx = s_ql[lane] + 1; al = 1; }
+            if (lane < SPC && s_al[lane]) { mx = s_ql[lane] + s_ml[lane] + 1; al = 1; }   // whole context
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -609,14 +619,22 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 const int m = (rr >> 1) * SPC + s;
                 uint4 ch[8];
                 const int ql = s_ql[s];
-                if (s_al[s] && r <= ql) {
+                // context row r: the processor queue newest first, then the write queue
+                if (s_al[s] && r <= ql + s_ml[s]) {
                     const uint32_t cur = recb[s * 4 + (s_p[s] & 3)];
                     if (r == 0) {
                         row_chunks_bf16(cur, cur, false, 0, 0u, 0u, ch);
                     } else {
-                        int idx = s_qs[s] + ql - r;
-                        if (idx >= cap) idx -= cap;
-                        const uint64_t ent = qring[s * cap + idx];
+                        uint64_t ent;
+                        if (r <= ql) {
+                            int idx = s_qs[s] + ql - r;
+                            if (idx >= cap) idx -= cap;
+                            ent = qring[s * cap + idx];
+                        } else {
+                            int idx = s_ms[s] + s_ml[s] - (r - ql);
+                            if (idx >= cap) idx -= cap;
+                            ent = mring[s * cap + idx];
+                        }
                         row_chunks_bf16(entry_rec(ent), cur, true, entry_res(ent, s_tick[s]), entry_e(ent),
                                         entry_s(ent), ch);
                     }
@@ -816,14 +834,14 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 ok = __all_sync(0xffffffffu, ok);
                 tc_fence_after();
                 mark(8);
-                float pf = 0.f, pe = 0.f;
-                constexpr int NH = NO == 2 ? 1 : 24;
+                float pf = 0.f, pe = 0.f, ps = 0.f;
+                constexpr int NH = NO <= 3 ? 1 : 24;
                 float ph[NH];
 #pragma unroll
                 for (int o = 0; o < NH; o++) ph[o] = 0.f;
                 if (ok) {
                     const int cols = HN / 2, j0 = half * cols;
-                    if constexpr (NO == 2) {
+                    if constexpr (NO <= 3) {
                         uint32_t r32[2][32];
                         tmem_ld_cols(tmem_base + ((uint32_t)(qd * 32) << 16) + 384u + (uint32_t)j0, cols, r32);
 #pragma unroll
@@ -835,6 +853,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                 const float v = fmaxf(__uint_as_float(r32[bi][jj]) + s_fb[j] + s_Se[j], 0.f);
                                 pf = fmaf(v, s_w2f[j], pf);
                                 pe = fmaf(v, s_w2e[j], pe);
+                                if constexpr (SQ) ps = fmaf(v, s_w2f[2 * HN + j], ps);
                             }
                         }
                     } else {
@@ -871,6 +890,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 const uint32_t pb = cl_map(bar(B_PART), (uint32_t)owner);
                 if constexpr (NO == 2) {
                     cl_st_async_v2(dst, __float_as_uint(pf), __float_as_uint(pe), pb);
+                } else if constexpr (SQ) {
+                    cl_st_async_v4(dst, make_uint4(__float_as_uint(pf), __float_as_uint(pe), __float_as_uint(ps), 0u), pb);
                 } else {
 #pragma unroll
                     for (int q4 = 0; q4 < 6; q4++)
@@ -904,6 +925,16 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         }
                         z[0] = zf;
                         z[1] = ze;
+                    } else if constexpr (SQ) {
+#pragma unroll
+                        for (int o2 = 0; o2 < NO; o2++) z[o2] = s_b2[o2];
+#pragma unroll
+                        for (int i = 0; i < 2 * CS; i++) {
+                            const float4 v = reinterpret_cast<const float4 *>(part)[i * SPC + s];
+                            z[0] += v.x;
+                            z[1] += v.y;
+                            z[min(2, NO - 1)] += v.z;
+                        }
                     } else {
 #pragma unroll
                         for (int o2 = 0; o2 < NO; o2++) z[o2] = s_b2[o2];
@@ -920,19 +951,34 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             }
                         }
                     }
-                    float yf, ye;
-                    uint32_t F = head_latency<NO, 0>(z, yf), E = head_latency<NO, 1>(z, ye);
+                    float yf, ye, ys = 0.f;
+                    uint32_t F = head_latency<NO, 0>(z, yf), E = head_latency<NO, 1>(z, ye), Sl = 0;
+                    if constexpr (SQ) Sl = head_latency<NO, 2>(z, ys);
                     const int64_t gi = o + p;
                     if (As.replay) {
-                        F = As.replay[2 * gi];
-                        E = As.replay[2 * gi + 1];
+                        F = As.replay[NL * gi];
+                        E = As.replay[NL * gi + 1];
+                        if constexpr (SQ) Sl = As.replay[NL * gi + 2];
                     }
-                    if (As.pre_log) { As.pre_log[2 * gi] = yf; As.pre_log[2 * gi + 1] = ye; }
-                    if (As.lat_log) { As.lat_log[2 * gi] = (uint8_t)F; As.lat_log[2 * gi + 1] = (uint8_t)E; }
+                    if (As.pre_log) {
+                        As.pre_log[NL * gi] = yf;
+                        As.pre_log[NL * gi + 1] = ye;
+                        if constexpr (SQ) As.pre_log[NL * gi + 2] = ys;
+                    }
+                    if (As.lat_log) {
+                        As.lat_log[NL * gi] = (uint8_t)F;
+                        As.lat_log[NL * gi + 1] = (uint8_t)E;
+                        if constexpr (SQ) As.lat_log[NL * gi + 2] = (uint8_t)Sl;
+                    }
                     uint64_t *qr = qring + s * cap;
+                    uint64_t *mr = mring + s * cap;   // SQ only
                     int qs = s_qs[s], ql = s_ql[s], ev = 0;
+                    int ms = SQ ? s_ms[s] : 0, ml = SQ ? s_ml[s] : 0;
                     int32_t tick = s_tick[s] + (int32_t)F;
-                    // in-order retire from the oldest, at most lim_n entries
+                    // in-order retire from the oldest, at most lim_n entries; with the store
+                    // latency the retired stores move to the write queue's tail, and the write
+                    // queue then retires in order, with no limit, every store whose residence
+                    // has reached its S
                     auto retire = [&](int lim_n) {
                         int k = 0;
                         while (k < lim_n) {
@@ -941,27 +987,54 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             const uint64_t v = qr[idx];
                             const int32_t res = entry_res(v, tick), e = (int32_t)entry_e(v);
                             if (strict ? res <= e : res < e) break;
+                            if constexpr (SQ) {
+                                if (rec_is_store(entry_rec(v))) {
+                                    int mi = ms + ml;
+                                    if (mi >= cap) mi -= cap;
+                                    mr[mi] = v;
+                                    ml++;
+                                }
+                            }
                             k++;
                         }
                         qs += k;
                         if (qs >= cap) qs -= cap;
                         ql -= k;
+                        if constexpr (SQ) {
+                            int km = 0;
+                            while (km < ml) {
+                                int idx = ms + km;
+                                if (idx >= cap) idx -= cap;
+                                const uint64_t v = mr[idx];
+                                const int32_t res = entry_res(v, tick), sl = (int32_t)entry_s(v);
+                                if (strict ? res <= sl : res < sl) break;
+                                km++;
+                            }
+                            ms += km;
+                            if (ms >= cap) ms -= cap;
+                            ml -= km;
+                        }
                     };
                     retire(min(ql, RW * (int)F));
-                    if (ql == cap) {   // full: drop the oldest
-                        qs = (qs + 1 == cap) ? 0 : qs + 1;
-                        ql--;
+                    if (ql + ml == cap) {   // full: drop the oldest instruction (the write queue's head first)
+                        if (SQ && ml > 0) {
+                            ms = (ms + 1 == cap) ? 0 : ms + 1;
+                            ml--;
+                        } else {
+                            qs = (qs + 1 == cap) ? 0 : qs + 1;
+                            ql--;
+                        }
                         ev = 1;
                     }
                     {
                         int idx = qs + ql;
                         if (idx >= cap) idx -= cap;
-                        qr[idx] = pack_entry(recb[s * 4 + (p & 3)], E, 0u, (uint32_t)tick);
+                        qr[idx] = pack_entry(recb[s * 4 + (p & 3)], E, SQ ? Sl : 0u, (uint32_t)tick);
                     }
                     ql++;
                     p++;
                     if (p == n) {   // drain: Delta of Eq. 1
-                        while (ql > 0) {
+                        while (ql + ml > 0) {
                             tick += 1;
                             retire(min(ql, RW));
                         }
@@ -971,6 +1044,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     s_p[s] = p;
                     s_qs[s] = qs;
                     s_ql[s] = ql;
+                    if constexpr (SQ) {
+                        s_ms[s] = ms;
+                        s_ml[s] = ml;
+                    }
                     s_ev[s] += ev;
                     s_al[s] = p < n ? 1 : 0;
                     if (p + 1 < n)   // record of the position two steps ahead
@@ -997,11 +1074,17 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             const int s = wi + 8 * j, b = s_b[s];
             if (b < 0) continue;
             for (int i = lane; i < cap; i += 32) A->ring[(size_t)b * cap + i] = qring[s * cap + i];
+            if constexpr (SQ)
+                for (int i = lane; i < cap; i += 32) A->mring[(size_t)b * cap + i] = mring[s * cap + i];
             if (lane == 0) {
                 A->tick[b] = s_tick[s];
                 A->pos[b] = s_p[s];
                 A->qstart[b] = s_qs[s];
                 A->qlen[b] = s_ql[s];
+                if constexpr (SQ) {
+                    A->mstart[b] = s_ms[s];
+                    A->mlen[b] = s_ml[s];
+                }
                 A->evict[b] = s_ev[s];
             }
         }
@@ -1042,7 +1125,7 @@ static int cluster_size(const simnet_config &k, int B) {
 bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     const simnet_config &k = c->cfg;
     if (k.precision != SIMNET_BF16) { why = "not BF16"; return false; }
-    if (c->store_queue) { why = "memory write queue"; return false; }
+    if (c->store_queue && c->hybrid) { why = "memory write queue with the hybrid head"; return false; }
     if (c->residual) { why = "residual blocks"; return false; }
     if (k.n_conv < 2 || k.n_conv > 3) { why = "conv depth"; return false; }
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
@@ -1092,6 +1175,7 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.stages = stages;
     const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no, a.stage_bytes).total + 1024;
     auto kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid> : cluster_kernel<4, kOutHybrid>)
+                : no == 3        ? (CS == 8 ? cluster_kernel<8, 3> : cluster_kernel<4, 3>)
                                  : (CS == 8 ? cluster_kernel<8, 2> : cluster_kernel<4, 2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }

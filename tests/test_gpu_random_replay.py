@@ -47,7 +47,7 @@ HYBRID = I.Arch(96, 3, 128, 512, "hybrid")               # 22 FC2 outputs: other
 STORE = I.Arch(32, 2, 64, 256, store_queue=True)          # three latencies, memory write queue
 RESID = I.Arch(32, 2, 64, 256, block="residual")          # residual blocks: BF16 and FP32 only
 CASES = ([(a, p) for a in SHAPES for p in PATHS] + [(HYBRID, p) for p in PATHS]
-         + [(STORE, p) for p in PATHS if p[2] != "cluster"]    # the cluster kernel does not take stores
+         + [(STORE, p) for p in PATHS]
          + [(RESID, p) for p in PATHS if p[0] != "fp8" and p[2] != "cluster"])
 
 

@@ -7,8 +7,9 @@ CNN's context is every instruction still in the simulator.
   the GPU give their hand-computed cycle counts and evictions.
 * Real networks: integer state bit-exact under teacher forcing both ways and
   the three regression outputs within the precision's bound, on every kernel
-  path that takes the write queue (per-layer FP32 / BF16 / FP8, grid-persistent
-  BF16 / FP8; the cluster kernel hands these calls to the grid kernel).
+  path (per-layer FP32 / BF16 / FP8, grid-persistent BF16 / FP8, the cluster
+  kernel for BF16 with the regression head; with the hybrid head the cluster
+  kernel hands these calls to the grid kernel).
 * FC2 reduced to its bias: every decision known (F = 1, E = 2, S = 7).
 * Split runs and saved states resume bit for bit; the CNN entry point returns
   three outputs.
@@ -41,7 +42,8 @@ ARCH = sq(I.ARCH_SMALL(32))
 PATHS = {
     "fp32": ("fp32", {}, "layerwise"),
     "bf16-layerwise": ("bf16", {"persistent": False}, "layerwise"),
-    "bf16-default": ("bf16", {}, "persistent"),          # the cluster kernel does not take the write queue
+    "bf16-default": ("bf16", {}, "cluster"),
+    "bf16-persistent": ("bf16", {"cluster": False}, "persistent"),
     "fp8-layerwise": ("fp8", {"persistent": False}, "layerwise"),
     "fp8-persistent": ("fp8", {}, "persistent"),
 }
@@ -94,14 +96,16 @@ def test_teacher_forced_and_free_running(path, case):
     assert (r.mlen > 0).any() and ref.lat.shape[1] == 3   # the write queue is in use
 
 
-def test_c2_architecture():
+@pytest.mark.parametrize("path", ["bf16-default", "bf16-persistent"])
+def test_c2_architecture(path):
+    precision, kw, kind = PATHS[path]
     arch = sq(I.ARCH_MID)
     blob = I.workload_weights(I.Workload("s", arch, 1, 1, seed=2))
     trace = I.small_trace([400, 37, 250, 0, 128], seed=21)
-    teacher_forced_check(arch, trace, "bf16", blob, 5e-2, path="persistent")
+    teacher_forced_check(arch, trace, precision, blob, 5e-2, path=kind, **kw)
 
 
-@pytest.mark.parametrize("path", ["fp32", "bf16-default"])
+@pytest.mark.parametrize("path", ["fp32", "bf16-persistent"])
 def test_hybrid_head_with_store_latency(path):
     """33 FC2 outputs: the hybrid head's class rule for all three latencies."""
     precision, kw, kind = PATHS[path]
@@ -109,6 +113,10 @@ def test_hybrid_head_with_store_latency(path):
     blob = I.workload_weights(I.Workload("s", arch, 1, 1, seed=7))
     trace = I.small_trace([300, 130, 77, 0, 1, 45], seed=5)
     teacher_forced_check(arch, trace, precision, blob, TOL[precision][0], path=kind, **kw)
+    if precision == "bf16":   # the default BF16 path hands the hybrid head with stores to the grid kernel
+        d, _ = make_sim(arch, "bf16", blob=blob)
+        run_gpu(d, trace, logs=False)
+        assert d.kernel_path == "persistent"
 
 
 @pytest.mark.parametrize("path", list(PATHS))
@@ -127,12 +135,14 @@ def test_bias_only_latencies_exact(path):
     np.testing.assert_array_equal(g["cycles"], ref.cycles)
 
 
-@pytest.mark.parametrize("precision,mode", [("fp32", "layerwise"), ("bf16", "persistent"), ("fp8", "persistent")])
+@pytest.mark.parametrize("precision,mode", [("fp32", "layerwise"), ("bf16", "cluster"), ("bf16", "persistent"),
+                                            ("fp8", "persistent")])
 def test_split_and_saved_runs_resume_bit_for_bit(precision, mode):
     lengths = [0, 1, 37, 300, 41, 512, 90, 5, 260, 128, 64, 7, 1000, 3, 222, 99]
     trace = I.small_trace(lengths, seed=11)
     rec, off = to_dev(trace)
-    sim, blob = make_sim(ARCH, precision, persistent=mode != "layerwise", seed=3)
+    kw = {"persistent": mode != "layerwise", "cluster": mode == "cluster"}
+    sim, blob = make_sim(ARCH, precision, seed=3, **kw)
     c0, l0, p0, st0 = run_chunks(sim, rec, off, trace.n_instructions)
     c1, l1, p1, st1 = run_chunks(sim, rec, off, trace.n_instructions, chunks=[1, 17, 64, 5])
     np.testing.assert_array_equal(c1, c0)
@@ -141,14 +151,14 @@ def test_split_and_saved_runs_resume_bit_for_bit(precision, mode):
 
     def swap(s):
         data = s.state_save("sim")
-        fresh, _ = make_sim(ARCH, precision, blob=blob, persistent=mode != "layerwise")
+        fresh, _ = make_sim(ARCH, precision, blob=blob, **kw)
         fresh.state_load(data, "sim")
         return fresh
     c2, l2, p2, _ = run_chunks(sim, rec, off, trace.n_instructions, chunks=[50, 200], state_via=swap)
     np.testing.assert_array_equal(c2, c0)
     np.testing.assert_array_equal(l2, l0)
     # a state without the write queue does not load into a context with it, and back
-    plain, _ = make_sim(I.ARCH_SMALL(32), precision, persistent=mode != "layerwise", seed=3)
+    plain, _ = make_sim(I.ARCH_SMALL(32), precision, seed=3, **kw)
     with pytest.raises(SimnetError):
         plain.state_load(sim.state_save("sim"), "sim")
 
