@@ -353,8 +353,9 @@ simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
 #define SIMNET_PATH_LAYERWISE 1  /* one kernel per layer and step (CUDA graphs) */
 #define SIMNET_PATH_PERSISTENT 2 /* one cooperative kernel, grid-wide barriers between phases */
 #define SIMNET_PATH_CLUSTER 3    /* clusters of 4 or 8 CTAs each owning 128 sub-traces for the
-                                    whole call, no grid-wide synchronisation (BF16; 2-3 conv
-                                    layers of 64 or 128 channels; FC1 width 256 or 512) */
+                                    whole call, no grid-wide synchronisation (BF16; 2-3 plain
+                                    conv layers of 64 or 128 channels; FC1 width 256 or 512;
+                                    either head, or the write queue with the regression head) */
 
 /* Path that ran the last steps of the last simnet_simulate call (SIMNET_PATH_*), or -1 for
  * a NULL context.  A BF16 call where the cluster kernel applies starts on it; if the call is
