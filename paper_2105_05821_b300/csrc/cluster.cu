@@ -847,13 +847,28 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 #pragma unroll
                         for (int bi = 0; bi < 2; bi++) {
                             if (bi >= cols / 32) break;
+                            // bias, S[e] and FC2 rows four neurons to a load
+                            const int jb = j0 + bi * 32;
+                            const float4 *fb4 = reinterpret_cast<const float4 *>(s_fb + jb);
+                            const float4 *se4 = reinterpret_cast<const float4 *>(s_Se + jb);
+                            const float4 *wf4 = reinterpret_cast<const float4 *>(s_w2f + jb);
+                            const float4 *we4 = reinterpret_cast<const float4 *>(s_w2e + jb);
+                            const float4 *ws4 = reinterpret_cast<const float4 *>(s_w2f + 2 * HN + jb);   // SQ only
 #pragma unroll
-                            for (int jj = 0; jj < 32; jj++) {
-                                const int j = j0 + bi * 32 + jj;
-                                const float v = fmaxf(__uint_as_float(r32[bi][jj]) + s_fb[j] + s_Se[j], 0.f);
-                                pf = fmaf(v, s_w2f[j], pf);
-                                pe = fmaf(v, s_w2e[j], pe);
-                                if constexpr (SQ) ps = fmaf(v, s_w2f[2 * HN + j], ps);
+                            for (int q = 0; q < 8; q++) {
+                                const float4 fb = fb4[q], se = se4[q], wf = wf4[q], we = we4[q];
+                                float4 wsv = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if constexpr (SQ) wsv = ws4[q];
+                                const float bb[4] = {fb.x + se.x, fb.y + se.y, fb.z + se.z, fb.w + se.w};
+                                const float wfa[4] = {wf.x, wf.y, wf.z, wf.w}, wea[4] = {we.x, we.y, we.z, we.w};
+                                const float wsa[4] = {wsv.x, wsv.y, wsv.z, wsv.w};
+#pragma unroll
+                                for (int u = 0; u < 4; u++) {
+                                    const float v = fmaxf(__uint_as_float(r32[bi][4 * q + u]) + bb[u], 0.f);
+                                    pf = fmaf(v, wfa[u], pf);
+                                    pe = fmaf(v, wea[u], pe);
+                                    if constexpr (SQ) ps = fmaf(v, wsa[u], ps);
+                                }
                             }
                         }
                     } else {
