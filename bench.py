@@ -39,9 +39,9 @@ TRAFFIC = {
     # profiles/persist_kernel_c2_bf16.md, scaled by steps to the 1,000-step launch
     ("c2", "bf16", "persist_kernel"): 1.526e6 * 1000 / 20,
     # cluster_kernel, c2 BF16: one 1,000-step call is two launches (the 128-step probe and the
-    # rest), 2.14 + 5.59 MB read and nothing written, measured on the full workload
+    # rest), 2.14 + 5.54 MB read and nothing written, measured on the full workload
     # (profiles/cluster_kernel_c2_bf16_traffic.md); the working set stays on chip and in L2
-    ("c2", "bf16", "cluster_kernel"): 2.138e6 + 5.586e6,
+    ("c2", "bf16", "cluster_kernel"): 2.138e6 + 5.543e6,
 }
 
 
