@@ -113,6 +113,117 @@ __global__ void __launch_bounds__(256) gemm_strided_kernel(const float *__restri
     }
 }
 
+// The same product on 128 x TN tiles (TN = 64 or 128), each thread 8 x TN/16
+// outputs, the next K slice loaded into registers while the current one is
+// multiplied (for products with enough 128-row tiles to fill the GPU).
+template <bool ROUND, int TN>
+__global__ void __launch_bounds__(256) gemm_strided_tile_kernel(const float *__restrict__ A, int64_t sam, int64_t sak,
+                                                                const float *__restrict__ B, int64_t sbk,
+                                                                int64_t sbn, float *__restrict__ C, int64_t ldc, int M,
+                                                                int N, int K, int k_chunk,
+                                                                const float *__restrict__ bias, int relu,
+                                                                int accumulate) {
+    constexpr int TM = 128, BK = 16, NA = TM * BK / 256, NB = TN * BK / 256, CN = TN / 16;
+    __shared__ __align__(16) float As[BK][TM + 4];
+    __shared__ __align__(16) float Bs[BK][TN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int k_lo = blockIdx.z * k_chunk, k_hi = min(K, k_lo + k_chunk);
+    const bool a_kfast = sak == 1, b_nfast = sbn == 1;
+    float ra[NA], rb[NB];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < NA; q++) {
+            const int e = tid + 256 * q;
+            int mm, kk;
+            if (a_kfast) { kk = e & (BK - 1); mm = e / BK; } else { mm = e & (TM - 1); kk = e / TM; }
+            const int gm = m0 + mm, gk = k0 + kk;
+            float v = (gm < M && gk < k_hi) ? A[(int64_t)gm * sam + (int64_t)gk * sak] : 0.f;
+            if (ROUND) v = __bfloat162float(__float2bfloat16_rn(v));
+            ra[q] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int e = tid + 256 * q;
+            int nn, kb;
+            if (b_nfast) { nn = e & (TN - 1); kb = e / TN; } else { kb = e & (BK - 1); nn = e / BK; }
+            const int gn = n0 + nn, gk = k0 + kb;
+            float v = (gn < N && gk < k_hi) ? B[(int64_t)gk * sbk + (int64_t)gn * sbn] : 0.f;
+            if (ROUND) v = __bfloat162float(__float2bfloat16_rn(v));
+            rb[q] = v;
+        }
+    };
+    auto store = [&]() {
+#pragma unroll
+        for (int q = 0; q < NA; q++) {
+            const int e = tid + 256 * q;
+            if (a_kfast) As[e & (BK - 1)][e / BK] = ra[q];
+            else As[e / TM][e & (TM - 1)] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int e = tid + 256 * q;
+            if (b_nfast) Bs[e / TN][e & (TN - 1)] = rb[q];
+            else Bs[e & (BK - 1)][e / BK] = rb[q];
+        }
+    };
+    float acc[8][CN] = {};
+    if (k_lo < k_hi) load(k_lo);
+    for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
+        store();
+        __syncthreads();
+        if (k0 + BK < k_hi) load(k0 + BK);   // the next slice's global loads overlap this slice's FMAs
+#pragma unroll
+        for (int k = 0; k < BK; k++) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[k][ty * 8 + 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[CN];
+#pragma unroll
+            for (int j4 = 0; j4 < CN / 4; j4++) {
+                const float4 b4 = *reinterpret_cast<const float4 *>(&Bs[k][tx * CN + 4 * j4]);
+                b[4 * j4] = b4.x;
+                b[4 * j4 + 1] = b4.y;
+                b[4 * j4 + 2] = b4.z;
+                b[4 * j4 + 3] = b4.w;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++)
+#pragma unroll
+                for (int j = 0; j < CN; j++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int m = m0 + ty * 8 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < CN; j++) {
+            const int n = n0 + tx * CN + j;
+            if (n >= N) continue;
+            if (accumulate) {
+                atomicAdd(C + (int64_t)m * ldc + n, acc[i][j]);
+            } else {
+                float v = acc[i][j] + (bias ? bias[n] : 0.f);
+                if (relu) v = fmaxf(v, 0.f);
+                C[(int64_t)m * ldc + n] = v;
+            }
+        }
+    }
+}
+
+// C(m, n) = (relu) (C(m, n) + bias[n]): the epilogue of a product whose K was split
+__global__ void bias_relu_kernel(float *__restrict__ C, int64_t ldc, int M, int N, const float *__restrict__ bias,
+                                 int relu) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)M * N) return;
+    const int m = (int)(i / N), n = (int)(i % N);
+    float v = C[(int64_t)m * ldc + n] + (bias ? bias[n] : 0.f);
+    if (relu) v = fmaxf(v, 0.f);
+    C[(int64_t)m * ldc + n] = v;
+}
+
 // ------------------------------------------------------------------ elementwise
 __global__ void relu_mask_kernel(float *__restrict__ d, const float *__restrict__ y, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -228,9 +339,52 @@ unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 using namespace simnet;
 
+template <int TN>
+static void gemm_tile(bool round, const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn,
+                      float *C, int64_t ldc, int M, int N, int K, const float *bias, int relu, bool accumulate,
+                      cudaStream_t s) {
+    int splits = 1, chunk = K;
+    if (accumulate) {
+        const int tiles = ((M + 127) / 128) * ((N + TN - 1) / TN);
+        splits = std::max(1, std::min((K + 255) / 256, 4 * 148 / std::max(tiles, 1)));
+        chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+        splits = (K + chunk - 1) / chunk;
+    }
+    dim3 g((N + TN - 1) / TN, (M + 127) / 128, splits);
+    if (round)
+        gemm_strided_tile_kernel<true, TN><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, chunk, bias,
+                                                             relu, accumulate);
+    else
+        gemm_strided_tile_kernel<false, TN><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, chunk, bias,
+                                                              relu, accumulate);
+}
+
 static void gemm(bool round, const float *A, int64_t sam, int64_t sak, const float *B, int64_t sbk, int64_t sbn,
                  float *C, int64_t ldc, int M, int N, int K, const float *bias, int relu, bool accumulate,
                  cudaStream_t s) {
+    // 128-row tiles when they alone fill the GPU twice over (the products over the
+    // windows' rows); a product with few output tiles and a long K splits K
+    // instead (atomically summed into C, then bias and ReLU)
+    const int TN = N >= 128 ? 128 : 64;
+    const int tiles128 = ((M + 127) / 128) * ((N + TN - 1) / TN), tiles64 = ((M + 63) / 64) * ((N + 63) / 64);
+    if (M >= 128 && N >= 64 && (accumulate || tiles128 >= 2 * 148)) {
+        if (TN == 128) gemm_tile<128>(round, A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, bias, relu, accumulate, s);
+        else gemm_tile<64>(round, A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, bias, relu, accumulate, s);
+        return;
+    }
+    if (!accumulate && tiles64 < 2 * 148 && K >= 512) {
+        const int splits = std::min(K / 256, (4 * 148 + tiles64 - 1) / tiles64);
+        const int chunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+        cudaMemset2DAsync(C, (size_t)ldc * sizeof(float), 0, (size_t)N * sizeof(float), (size_t)M, s);
+        dim3 g((N + 63) / 64, (M + 63) / 64, (K + chunk - 1) / chunk);
+        if (round)
+            gemm_strided_kernel<true><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, chunk, nullptr, 0, 1);
+        else
+            gemm_strided_kernel<false><<<g, 256, 0, s>>>(A, sam, sak, B, sbk, sbn, C, ldc, M, N, K, chunk, nullptr, 0, 1);
+        if (bias || relu)
+            bias_relu_kernel<<<(int)(((int64_t)M * N + 255) / 256), 256, 0, s>>>(C, ldc, M, N, bias, relu);
+        return;
+    }
     int splits = 1, chunk = K;
     if (accumulate) {  // long reductions (weight gradients): split the rows over blocks
         const int tiles = ((M + 63) / 64) * ((N + 63) / 64);
