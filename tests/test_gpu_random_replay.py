@@ -9,15 +9,18 @@ the grid-persistent kernel, the per-layer kernels and the FP32 form alike, for
 the regression and hybrid heads, residual blocks and (with a third, store
 latency) the memory write queue.
 The latency mixes cover an empty retire budget (F = 0), queues that overflow
-(long E) and queues that stay short.
+(long E) and queues that stay short.  Each case is run again in bounded calls
+of random lengths (the resumable state carried between them) and must give
+the same run.
 """
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2105_05821_b300 import inputs as I
 
-from gpu_util import make_sim, run_gpu
+from gpu_util import make_sim, run_gpu, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -77,3 +80,17 @@ def test_random_replay_bit_exact(case):
     np.testing.assert_array_equal(g["lat"], ref.lat)
     assert g["stats"].evictions == int(ref.evictions.sum())
     assert g["stats"].total_cycles == int(ref.cycles.sum())
+    # the same call in bounded pieces of random lengths (resumable state) gives the same run
+    rec_d, off_d = to_dev(trace)
+    rp = torch.from_numpy(np.ascontiguousarray(replay)).cuda()
+    n = max(trace.n_instructions, 1)
+    lat = torch.zeros((n, sim.n_lat), dtype=torch.uint8, device="cuda")
+    cyc = torch.empty(trace.n_subtraces, dtype=torch.int64, device="cuda")
+    resume, pending, calls = False, None, 0
+    while pending != 0 and calls < 10000:
+        st = sim.simulate(rec_d, off_d, cycles_out=cyc, lat_log=lat, replay=rp,
+                          max_steps=int(rng.integers(1, 200)), resume=resume)
+        pending, resume, calls = st.pending, True, calls + 1
+    assert pending == 0
+    np.testing.assert_array_equal(cyc.cpu().numpy(), ref.cycles)
+    np.testing.assert_array_equal(lat.cpu().numpy()[:trace.n_instructions], ref.lat)
