@@ -296,10 +296,10 @@ static int to_cycles(double y)
 
 /* Latency t (0 fetch, 1 execution, 2 store) from the FC2 outputs z; *pre gets the
  * regression output after softplus.  Regression head: that value, clamped and
- * rounded.  Hybrid head (Sec. 2.3): the class with the largest logit of
- * z[11t .. 11t+9], compared after rounding to FP32 as the kernels compute
- * them (lowest class on ties); classes 0..8 are that many cycles, class 9
- * ("more than 8") takes the regression output. */
+ * rounded.  Hybrid head (Sec. 2.3): the class with the largest probability,
+ * i.e. the largest of the logits z[11t .. 11t+9] (softmax is monotone),
+ * compared in FP64 (lowest class on exact ties); classes 0..8 are that many
+ * cycles, class 9 ("more than 8") takes the regression output. */
 static int head_latency(const oracle_cfg *c, const double *z, int t, double *pre)
 {
     if (!c->hybrid) {
@@ -309,7 +309,7 @@ static int head_latency(const oracle_cfg *c, const double *z, int t, double *pre
     const double *lg = z + 11 * t;
     int k = 0;
     for (int j = 1; j < 10; j++)
-        if ((float)lg[j] > (float)lg[k]) k = j;
+        if (lg[j] > lg[k]) k = j;
     *pre = softplus(lg[10]);
     return k <= 8 ? k : to_cycles(*pre);
 }

@@ -122,15 +122,18 @@ def test_hybrid_decisions_drive_the_simulation(fetch_class, exec_value, expect_f
     np.testing.assert_array_equal(r.cycles, s.cycles)
 
 
-def test_hybrid_ties_take_the_lowest_class_after_fp32_rounding():
+def test_hybrid_largest_logit_lowest_class_on_exact_ties():
+    """The class with the largest probability (Sec. 2.3) is the largest logit,
+    compared in FP64: an exact tie takes the lower class, a gap of 1e-12 is
+    enough to decide."""
     arch = hybrid(I.Arch(16, 2, 4, 8))
     trace = I.small_trace([5], seed=4)
     lf = np.zeros(10)
     lf[2] = lf[6] = 1.5                           # an exact tie: class 2
     le = np.zeros(10)
-    le[4], le[5] = 1.0, 1.0 + 1e-12               # equal in FP32, not in FP64: class 4
+    le[4], le[5] = 1.0, 1.0 + 1e-12               # larger in FP64 (equal once rounded to FP32): class 5
     r = run(arch, bias_only_blob(arch, lf, 0.0, le, 0.0), trace)
-    assert (r.lat[:, 0] == 2).all() and (r.lat[:, 1] == 4).all()
+    assert (r.lat[:, 0] == 2).all() and (r.lat[:, 1] == 5).all()
 
 
 def test_hybrid_with_class_nine_always_winning_is_the_regression_model():
@@ -161,18 +164,18 @@ def test_hybrid_with_class_nine_always_winning_is_the_regression_model():
 
 def test_head_decision_on_given_outputs():
     """oracle.head on hand-set FC2 outputs: direct classes, the "more than 8"
-    class through softplus of the regression output, FP32 ties, and the
-    regression head's plain rounding."""
+    class through softplus of the regression output, exact ties, a gap of
+    1e-12 decided in FP64, and the regression head's plain rounding."""
     cfg = oracle.Config.of(hybrid(I.Arch(16, 2, 4, 8)))
     z = np.zeros((3, 22))
     z[0, 4] = 1.0                                  # fetch: class 4
     z[0, 11 + 9], z[0, 21] = 2.0, 30.0             # execution: class 9, softplus(30) = 30
     z[1, 0] = z[1, 7] = 0.5                        # exact tie: lowest index
-    z[1, 11 + 2], z[1, 11 + 3] = 0.25, 0.25 + 1e-12    # equal in FP32: class 2
+    z[1, 11 + 2], z[1, 11 + 3] = 0.25, 0.25 + 1e-12    # decided in FP64: class 3
     z[2, 9], z[2, 10] = 1.0, -50.0                 # class 9 with a value that rounds to 0
     z[2, 11 + 8] = 3.0
     lat, pre = oracle.head(cfg, z)
-    np.testing.assert_array_equal(lat, [[4, 30], [0, 2], [0, 8]])
+    np.testing.assert_array_equal(lat, [[4, 30], [0, 3], [0, 8]])
     np.testing.assert_allclose(pre[:, 1], oracle.softplus(z[:, 21]), rtol=1e-15)
     reg = oracle.Config.of(I.Arch(16, 2, 4, 8))
     lat, pre = oracle.head(reg, np.array([[0.0, 3.4], [-60.0, 300.0]]))
