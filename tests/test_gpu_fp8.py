@@ -3,8 +3,8 @@
 Integer state stays bit-exact under teacher forcing.  Predicted latencies carry
 e4m3 rounding (3 mantissa bits) of features, weights and activations, with
 per-output-channel weight scales and calibrated per-channel activation scales
-folded into the next layer's weights; the asserted bounds are the stated FP8
-bounds of the design notes.
+folded into the next layer's weights; the asserted bounds are the FP8 row of
+tests/tolerances.py.
 """
 import numpy as np
 import pytest
@@ -16,11 +16,10 @@ from paper_2105_05821_b300 import inputs as I
 from gpu_util import latency_error, make_sim, run_gpu
 from test_gpu_sim import teacher_forced_check
 from test_gpu_tc import real_windows
+from tolerances import check, check_cpi
 
 pytestmark = pytest.mark.gpu
 
-FP8_LAT_TOL = 0.6        # max |f - y| / (y + 1) over every predicted latency
-FP8_P99_TOL = 0.2
 
 
 @pytest.mark.parametrize("arch", [I.ARCH_SMALL(32), I.ARCH_MID, I.ARCH_WIDE, I.ARCH_SMALL(96)])
@@ -29,23 +28,17 @@ def test_cnn_forward_fp8(arch):
     sim, _ = make_sim(arch, "fp8", blob=blob)
     z = sim.cnn_forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
     zr = oracle.cnn_forward(oracle.Config.of(arch), blob, x)
-    err = latency_error(oracle.softplus(z), oracle.softplus(zr))
-    print(f"\nfp8 cnn {arch}: vs fp64 oracle p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} "
-          f"max {err.max():.2e}")
     assert np.isfinite(z).all()
-    assert np.percentile(err, 99) <= FP8_P99_TOL and err.max() <= FP8_LAT_TOL
+    check(latency_error(oracle.softplus(z), oracle.softplus(zr)), "fp8", f"latencies {arch}")
+    check(latency_error(z, zr), "fp8", f"CNN outputs {arch}")
 
 
 def test_c1_fp8_teacher_forced():
     w = I.WORKLOADS["c1"]
     trace = I.make_trace(w)
     blob = I.workload_weights(w)
-    ref, free, err = teacher_forced_check(w.arch, trace, "fp8", blob, FP8_LAT_TOL)
-    cpi = abs(free["cycles"].sum() / ref.cycles.sum() - 1.0)
-    print(f"\nfp8 c1: lat p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} "
-          f"max {err.max():.2e}; free-running CPI error {cpi:.2e}")
-    assert np.percentile(err, 99) <= FP8_P99_TOL
-    assert cpi <= 0.05
+    ref, free, err = teacher_forced_check(w.arch, trace, "fp8", blob)
+    check_cpi(abs(free["cycles"].sum() / ref.cycles.sum() - 1.0), "fp8", "c1 free-running")
 
 
 def test_c2_full_size_sampled_fp8():
@@ -59,9 +52,6 @@ def test_c2_full_size_sampled_fp8():
     ref = oracle.simulate(cfg, trace.records, trace.offsets, blob, subset=ids, replay=g["lat"], logs=True)
     np.testing.assert_array_equal(ref.cycles, g["cycles"][ids])
     sel = np.concatenate([np.arange(trace.offsets[i], trace.offsets[i + 1]) for i in ids])
-    err = latency_error(g["pre"][sel], ref.pre[sel])
+    check(latency_error(g["pre"][sel], ref.pre[sel]), "fp8", "c2 full size, 5 sampled sub-traces")
     free = oracle.simulate(cfg, trace.records, trace.offsets, blob, subset=ids)
-    cpi = abs(g["cycles"][ids].sum() / free.cycles.sum() - 1.0)
-    print(f"\nfp8 c2 sampled: p50 {np.median(err):.2e} p99 {np.percentile(err, 99):.2e} max {err.max():.2e}; "
-          f"CPI error on {len(ids)} sub-traces {cpi:.2e}")
-    assert np.percentile(err, 99) <= FP8_P99_TOL and err.max() <= FP8_LAT_TOL
+    check_cpi(abs(g["cycles"][ids].sum() / free.cycles.sum() - 1.0), "fp8", "c2, 5 sampled sub-traces")

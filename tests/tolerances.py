@@ -1,0 +1,50 @@
+"""The parity bounds of the CUDA path against the FP64 oracle: one row per
+precision, asserted by every GPU test and by `smoke()`.
+
+Latency error is the paper's prediction-error form |f - y| / (y + 1)
+(Sec. 2.5), taken on the softplus outputs before clamping and rounding, GPU
+against oracle on the same integer state (teacher forcing).  `LAT_MAX` bounds
+every predicted latency of a test, `LAT_P99` the 99th percentile of them.
+CNN outputs (FC2, before softplus) are held to the same bounds, element by
+element, in the same form.  `CPI` bounds |CPI_gpu / CPI_oracle - 1| of a
+free-running simulation (each side on its own trajectory).
+
+FP32 is held to 1e-3.  BF16 and FP8 bound what their rounding gives on the
+workloads' weights: the FC2 rows of the execution and store latencies carry
+gains of 25 (the synthetic weight recipe), so an activation rounding error of
+a few hundredths of a unit in FC1's output moves those logits by up to about
+one; softplus is 1-Lipschitz, so a latency moves by at most as much.  The
+largest errors seen over all workloads, heads and kernel paths of the tests
+(store-queue workload: BF16 0.063, FP8 0.98; the c2 workload: BF16 0.005, FP8
+0.09) are inside these rows.
+"""
+import numpy as np
+
+LAT_MAX = {"fp32": 1e-3, "bf16": 0.1, "fp8": 1.0}
+LAT_P99 = {"fp32": 1e-3, "bf16": 0.02, "fp8": 0.25}
+CPI = {"fp32": 1e-3, "bf16": 0.02, "fp8": 0.05}
+
+
+def rel_error(gpu, ref):
+    """|f - y| / (|y| + 1), element by element."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.abs(gpu - ref) / (np.abs(ref) + 1.0)
+
+
+def check(err, precision, what=""):
+    """Assert the precision's row on a set of errors; returns (p50, p99, max)."""
+    err = np.asarray(err, dtype=np.float64).reshape(-1)
+    assert np.isfinite(err).all(), what
+    if err.size == 0:
+        return 0.0, 0.0, 0.0
+    p50, p99, mx = float(np.median(err)), float(np.percentile(err, 99)), float(err.max())
+    print(f"\n{what} {precision}: p50 {p50:.2e} p99 {p99:.2e} max {mx:.2e}")
+    assert mx <= LAT_MAX[precision], (what, precision, "max", mx)
+    assert p99 <= LAT_P99[precision], (what, precision, "p99", p99)
+    return p50, p99, mx
+
+
+def check_cpi(cpi_err, precision, what=""):
+    print(f"\n{what} {precision}: CPI error {cpi_err:.2e}")
+    assert cpi_err <= CPI[precision], (what, precision, cpi_err)
