@@ -1,5 +1,5 @@
 """Benchmark: simulated instructions per second of SimNet's lock-step sub-trace
-simulation on one B300 (or N independent replicas under torchrun).
+simulation on one B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--precision bf16]
     python bench.py --impl reference ...      # the FP64 CPU oracle on the host cores
@@ -192,7 +192,7 @@ def run_reference(args, rank, world):
 
 
 def workload_config(w, args, note=""):
-    c = {"workload": f"{w.name}: {w.description}", "n_subtraces": w.n_subtraces,
+    c = {"workload": f"{w.name}: {w.description}; weights: {I.weight_recipe(w)}", "n_subtraces": w.n_subtraces,
          "instructions_per_step": None, "window": w.arch.window, "n_conv": w.arch.n_conv,
          "channels": w.arch.channels, "fc_hidden": w.arch.hidden, "retire_width": w.retire_width,
          "precision": args.precision, "head": w.arch.head, "store_queue": w.arch.store_queue,
@@ -242,19 +242,6 @@ def kind_name(w, k):
     return "fc1_gemm"
 
 
-def aggregate(ms_total: float, steps: int, inst_per_step: int, world: int, device):
-    """Whole-job throughput of `world` replicas, each timing `steps` steps of
-    `inst_per_step` instructions: the slowest rank's time (max over ranks)
-    divides all ranks' instructions.  Returns (ms per step, inst/s)."""
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([ms_total], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_per_step = float(t.item()) / steps
-    return ms_per_step, world * inst_per_step / (ms_per_step / 1e3)
-
-
 def train_predictor(w: I.Workload, steps: int):
     """The uneven-batching workload uses a trained CNN: train its architecture
     (window 96) with the library's fused steps on toy-pipeline labels of the
@@ -284,13 +271,113 @@ def truncate(trace: I.Trace, n: int) -> I.Trace:
     return I.Trace(np.concatenate(parts).astype(np.uint32), offs)
 
 
-def run_ours(args, rank, world):
-    import torch
-    import torch.distributed as dist
-    from paper_2105_05821_b300.simnet import Simnet
+class Timer:
+    """CUDA-event timing of whole simnet_simulate calls on one device: L2
+    flushed (512 MB write) before every timed call, outside its event pair."""
 
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    def __init__(self, dev):
+        import torch
+        self.torch = torch
+        self.dev = dev
+        self.flush = torch.empty(128 * 1024 * 1024, dtype=torch.int32, device=dev)   # 512 MB > L2
+
+    def run(self, sim, rec, off, cyc, steps, warmup, e2e=None):
+        """Device ms of each of `steps` calls after `warmup` untimed ones.  With
+        e2e = (rec_h, off_h, cyc_h) every timed call also copies the trace from
+        pinned host memory and the cycle counts back inside its event pair."""
+        torch = self.torch
+        for _ in range(warmup):
+            sim.simulate(rec, off, cycles_out=cyc, stats=False)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            self.flush.zero_()
+            evs[i][0].record()
+            if e2e:
+                rec.copy_(e2e[0], non_blocking=True)
+                off.copy_(e2e[1], non_blocking=True)
+            sim.simulate(rec, off, cycles_out=cyc, stats=False)
+            if e2e:
+                e2e[2].copy_(cyc, non_blocking=True)
+            evs[i][1].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return [a.elapsed_time(b) for a, b in evs], wall
+
+
+def tensor_peak(prec: str, call_ms: float):
+    """The tensor roofline's denominator: the measured BF16 burst peak for a call
+    shorter than 0.2 s (one call timed alone between L2 flushes), the sustained
+    one for a longer call; FP8 takes twice the BF16 figure (nominal ratio)."""
+    hbm, burst, sus, src = peaks()
+    base, which = (burst, "burst") if call_ms < 200.0 else (sus, "sustained")
+    scale = 2.0 if prec == "fp8" else 1.0
+    return base * scale, f"{src} bf16 {which}" + (" x2 (fp8 nominal ratio)" if scale > 1 else "")
+
+
+def whole_call_roofline(w, prec, N, ms_per_step, kernel, traffic=None):
+    """One launch (or one kernel path) does the whole call: its algorithmic
+    FLOPs (dense count of the scope table) over the call's device time."""
+    flops = 2.0 * w.arch.macs_per_inference() * N
+    ach = flops / (ms_per_step / 1e3) / 1e12
+    peak, note = tensor_peak(prec, ms_per_step)
+    return {"kernel": kernel, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "peak_source": note, "traffic": traffic, "avg_launch_us": ms_per_step * 1e3,
+            "algorithmic_per_launch": flops, "algorithmic_unit": "flop", "share_of_step": 1.0}
+
+
+PATH_KERNEL = {"cluster": "cluster_kernel", "persistent": "persist_kernel", "layerwise": "per-layer kernels"}
+
+
+def measure(timer, w, trace, blob32, prec, steps, warmup, rec, off, autotune=False, **kw):
+    """One context of workload `w` at precision `prec`: its first (untimed)
+    call runs any path choice, then `steps` timed calls.  Returns the record
+    and the per-sub-trace cycles of the last call."""
+    import torch
+    from paper_2105_05821_b300.simnet import Simnet
+    N, B = trace.n_instructions, trace.n_subtraces
+    cyc = torch.empty(B, dtype=torch.int64, device=rec.device)
+    sim = Simnet.for_arch(w.arch, precision=prec, retire_width=w.retire_width, **kw)
+    sim.load_weights(blob32)
+    st = sim.simulate(rec, off, cycles_out=cyc, stats=True)
+    tiles = []
+    if autotune and prec != "fp32" and sim.kernel_path != "cluster":
+        tiles = sim.autotune(B)
+        st = sim.simulate(rec, off, cycles_out=cyc, stats=True)
+    ms, wall = timer.run(sim, rec, off, cyc, steps, warmup)
+    ms_per_step = sum(ms) / len(ms)
+    rec_out = {"value": N / (ms_per_step / 1e3), "unit": UNIT, "ms_per_step": ms_per_step,
+               "ms_range": [min(ms), max(ms)], "steps": steps, "warmup": warmup, "dtype": prec,
+               "kernel_mode": sim.kernel_path, "gpu_launches_per_step": int(st.kernel_launches),
+               "total_cycles": int(st.total_cycles), "cpi": st.total_cycles / N, "wall_s_timed": wall}
+    if tiles:
+        rec_out["tile_widths"] = tiles[:w.arch.n_conv + 1]
+    pc = sim.path_choice
+    if pc["steps"]:
+        rec_out["path_choice"] = pc
+    cycles = cyc.cpu().numpy()
+    return sim, rec_out, cycles
+
+
+def device_trace(trace, dev):
+    import torch
+    rec_h = torch.from_numpy(trace.records.view(np.int32).copy()).pin_memory()
+    off_h = torch.from_numpy(trace.offsets.copy()).pin_memory()
+    return rec_h, off_h, rec_h.to(dev), off_h.to(dev)
+
+
+def cpi_error(gpu_cycles, ids, oracle_cycles):
+    return abs(float(np.asarray(gpu_cycles)[ids].sum()) / float(np.asarray(oracle_cycles).sum()) - 1.0)
+
+
+def run_ours(args):
+    import torch
+    dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    timer = Timer(dev)
     w = workload_of(args)
     trace = I.make_trace(w)
     if args.subtrace_len:
@@ -300,130 +387,92 @@ def run_ours(args, rank, world):
     if args.workload == "c4" and not args.untrained and not w.arch.store_queue:   # no store labels to train on
         blob32, train_info = train_predictor(w, args.train_steps)
     N, B = trace.n_instructions, trace.n_subtraces
-
-    rec_h = torch.from_numpy(trace.records.view(np.int32).copy()).pin_memory()
-    off_h = torch.from_numpy(trace.offsets.copy()).pin_memory()
-    rec = rec_h.to(dev)
-    off = off_h.to(dev)
-    cyc = torch.empty(B, dtype=torch.int64, device=dev)
+    rec_h, off_h, rec, off = device_trace(trace, dev)
     cyc_h = torch.empty(B, dtype=torch.int64).pin_memory()
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.int32, device=dev)   # 512 MB > L2
-
-    def sync_all():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def timed_run(sim, steps, warmup, e2e=False):
-        for _ in range(warmup):
-            sim.simulate(rec, off, cycles_out=cyc, stats=False)
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(steps)]
-        sync_all()
-        t0 = time.perf_counter()
-        for i in range(steps):
-            flush.zero_()
-            evs[i][0].record()
-            if e2e:
-                rec.copy_(rec_h, non_blocking=True)
-                off.copy_(off_h, non_blocking=True)
-            sim.simulate(rec, off, cycles_out=cyc, stats=False)
-            if e2e:
-                cyc_h.copy_(cyc, non_blocking=True)
-            evs[i][1].record()
-        sync_all()
-        wall = time.perf_counter() - t0
-        ms = sum(a.elapsed_time(b) for a, b in evs)
-        return ms, wall
-
-    sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width,
-                          persistent=not args.layerwise, cluster=not args.no_cluster,
-                          auto_path=not args.fixed_path)
-    sim.load_weights(blob32)
-    st = sim.simulate(rec, off, cycles_out=cyc, stats=True)          # compile graphs, count launches
-    path = sim.kernel_path
-    tiles = []
-    if args.precision != "fp32" and not args.no_autotune and path != "cluster":
-        tiles = sim.autotune(B)                                      # tile widths of the tcgen05 GEMM phases
-        st = sim.simulate(rec, off, cycles_out=cyc, stats=True)
-    launches_per_step = st.kernel_launches
+    kw = dict(persistent=not args.layerwise, cluster=not args.no_cluster, auto_path=not args.fixed_path)
 
     with ClockSampler(dev.index) as clk:
-        ms, wall = timed_run(sim, args.steps, args.warmup)
+        sim, main, cycles = measure(timer, w, trace, blob32, args.precision, args.steps, args.warmup, rec, off,
+                                    autotune=not args.no_autotune, **kw)
     clocks = clk.summary()
-    ms_per_step, value = aggregate(ms, args.steps, N, world, dev)
-
+    path = main["kernel_mode"]
     # end to end through host buffers (pinned H2D of the trace, D2H of the cycle counts)
-    ms_e2e, _ = timed_run(sim, max(2, args.steps // 2), 1, e2e=True)
-    _, e2e_value = aggregate(ms_e2e, max(2, args.steps // 2), N, world, dev)
+    cyc = torch.empty(B, dtype=torch.int64, device=dev)
+    ms_e2e, _ = timer.run(sim, rec, off, cyc, max(2, args.steps // 2), 1, e2e=(rec_h, off_h, cyc_h))
+    e2e_value = N / (sum(ms_e2e) / len(ms_e2e) / 1e3)
+    sim.close()
 
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+    out = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
            "config": workload_config(w, args), "clocks": clocks,
-           "gpu_launches": int(launches_per_step * args.steps),
+           "gpu_launches": int(main["gpu_launches_per_step"] * args.steps),
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(4 * N + 8 * (B + 1)),
                    "d2h_bytes_per_step": int(8 * B)},
-           "wall_s_timed": wall,
-           "tile_widths": tiles[:(3 if w.arch.block == "residual" else 1) * w.arch.n_conv + 1],
+           "wall_s_timed": main["wall_s_timed"], "ms_range": main["ms_range"],
+           "tile_widths": main.get("tile_widths", []),
            "kernel_mode": {"layerwise": "per-layer kernels", "persistent": "persistent",
                            "cluster": "cluster"}.get(path, path)}
-    pc = sim.path_choice
-    if pc["steps"]:
-        out["path_choice"] = pc   # the timed persistent / per-layer comparison behind kernel_mode
+    if "path_choice" in main:
+        out["path_choice"] = main["path_choice"]   # the timed persistent / per-layer comparison behind kernel_mode
     out["config"]["instructions_per_step"] = N
-    out["total_cycles"] = int(st.total_cycles)
-    out["cpi"] = st.total_cycles / N
+    out["total_cycles"] = main["total_cycles"]
+    out["cpi"] = main["cpi"]
 
-    if rank == 0 and not args.no_breakdown and path == "cluster":
+    if not args.no_breakdown and path == "cluster":
         # one launch does every step: the whole call's algorithmic work over its device time
-        hbm, bf16_burst, bf16_sus, src = peaks()
-        flops = 2.0 * w.arch.macs_per_inference() * N
-        ach = flops / (ms_per_step / 1e3) / 1e12
-        out["roofline"] = {"kernel": "cluster_kernel", "bound": "tensor", "achieved": ach, "peak": bf16_sus,
-                           "unit": "TFLOP/s", "frac": ach / bf16_sus, "peak_source": f"{src} bf16 sustained",
-                           "traffic": TRAFFIC.get((w.name, args.precision, "cluster_kernel")),
-                           "avg_launch_us": ms_per_step * 1e3, "algorithmic_per_launch": flops,
-                           "algorithmic_unit": "flop", "share_of_step": 1.0}
-        out["phases_us_per_step"] = cluster_phases(w, args, blob32, rec, off, cyc, clocks.get("sm_mhz") or 2032.0)
-    elif rank == 0 and not args.no_breakdown:
-        out["roofline"], out["kernels"] = roofline(w, args, blob32, rec, off, cyc, B, path)
-        if out["kernel_mode"] == "persistent":
-            # one launch does every step: its roofline is the whole call's algorithmic
-            # work over its device time; the per-phase table above explains the split
-            hbm, bf16_burst, bf16_sus, src = peaks()
-            flops = 2.0 * w.arch.macs_per_inference() * N
-            scale = 2.0 if args.precision == "fp8" else 1.0
-            ach = flops / (ms_per_step / 1e3) / 1e12
-            peak = bf16_sus * scale
-            phase = out["roofline"]
-            out["roofline"] = {"kernel": "persist_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
-                               "unit": "TFLOP/s", "frac": ach / peak,
-                               "peak_source": f"{src} bf16 sustained" + (" x2 (fp8 nominal ratio)" if scale > 1 else ""),
-                               "traffic": TRAFFIC.get((w.name, args.precision, "persist_kernel")),
-                               "avg_launch_us": ms_per_step * 1e3, "algorithmic_per_launch": flops,
-                               "algorithmic_unit": "flop", "share_of_step": 1.0,
-                               "dominant_phase": phase}
-    if rank == 0 and args.precision != "fp32" and not args.no_fp32:
-        s32 = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
-        s32.load_weights(blob32)
-        m32, _ = timed_run(s32, max(2, args.steps // 3), 1)
-        out["fp32_form"] = {"value": N / (m32 / max(2, args.steps // 3) / 1e3), "unit": UNIT,
-                            "note": "FFMA CUDA-core GEMMs, per-layer kernels, same workload and timing"}
+        out["roofline"] = whole_call_roofline(w, args.precision, N, main["ms_per_step"], "cluster_kernel",
+                                              TRAFFIC.get((w.name, args.precision, "cluster_kernel")))
+        ph = cluster_phases(w, args, blob32, rec, off, clocks.get("sm_mhz") or 2032.0)
+        out["phases_us_per_step"] = ph
+        # the padding extent: the kernel computes only the last-conv positions below
+        # the longest queue, so it executes a fraction of the dense FLOPs
+        frac_pos = ph["positions_per_step"] / w.arch.rows_out
+        exe = 2.0 * (frac_pos * (w.arch.macs_per_inference() - w.arch.n_out * w.arch.hidden)
+                     + w.arch.n_out * w.arch.hidden) * N
+        out["roofline"]["executed_flop"] = exe
+        out["roofline"]["executed_tflops"] = exe / (main["ms_per_step"] / 1e3) / 1e12
+        out["roofline"]["executed_note"] = (f"positions computed per step {ph['positions_per_step']:.2f} of "
+                                            f"{w.arch.rows_out} (CTA 0's counter); conv and FC1 scale with "
+                                            "them, FC2 does not")
+    elif not args.no_breakdown:
+        roof, kernels = roofline(w, args, blob32, rec, off, B, path)
+        out["kernels"] = kernels
+        out["roofline"] = roof
+        if path == "persistent":
+            # one launch does every step: its roofline is the whole call's work over its
+            # device time; the per-phase table explains the split
+            out["roofline"] = whole_call_roofline(w, args.precision, N, main["ms_per_step"], "persist_kernel",
+                                                  TRAFFIC.get((w.name, args.precision, "persist_kernel")))
+            out["roofline"]["dominant_phase"] = roof
+
+    forms = {}
+    if args.precision != "fp32" and not args.no_fp32:
+        s32, r32, c32 = measure(timer, w, trace, blob32, "fp32", max(2, args.steps // 3), 1, rec, off)
         s32.close()
-    if rank == 0 and args.precision == "bf16" and not args.no_fp32:
-        s8 = Simnet.for_arch(w.arch, precision="fp8", retire_width=w.retire_width, persistent=not args.layerwise)
-        s8.load_weights(blob32)
-        if not args.no_autotune:
-            s8.autotune(B)
-        m8, _ = timed_run(s8, args.steps, args.warmup)
-        out["fp8_form"] = {"value": N / (m8 / args.steps / 1e3), "unit": UNIT,
-                           "note": "FP8 e4m3 tcgen05 path, same workload and timing"}
+        r32["note"] = "FFMA CUDA-core GEMMs, per-layer kernels, same workload and timing"
+        out["fp32_form"] = r32
+        forms["fp32_form"] = c32
+    if args.precision == "bf16" and not args.no_fp32:
+        s8, r8, c8 = measure(timer, w, trace, blob32, "fp8", args.steps, args.warmup, rec, off,
+                             autotune=not args.no_autotune, persistent=not args.layerwise)
         s8.close()
+        r8["note"] = "FP8 e4m3 tcgen05 path, same workload and timing"
+        out["fp8_form"] = r8
+        forms["fp8_form"] = c8
     if train_info:
         out["trained_predictor"] = train_info
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    del rec, off
+
+    # the larger configurations, each in its own record (the main line stays the
+    # c2 workload): c5 at BF16 and FP8, c4 (trained predictor) at FP8 and BF16
+    extra = {}
+    if args.workload == "c2" and not args.no_extra and not args.subtrace_len:
+        extra = run_extra(args, timer)
+        out.update({k: v["record"] for k, v in extra.items()})
+
+    # CPU side last (nothing on the GPU is timed while the oracle runs)
+    if not args.no_cpu_baseline:
         blob64 = blob32.astype(np.float64) if train_info else I.workload_weights(w)
         if args.workload == "c4":   # the configuration's own check: 64 sampled sub-traces
             ids = sorted(np.random.default_rng(w.seed).choice(trace.n_subtraces, 64, replace=False).tolist())
@@ -438,22 +487,70 @@ def run_ours(args, rank, world):
                                "value_1_thread": rate1,
                                "sample_1_thread": f"1 whole sub-trace ({n1} instructions), {dt1:.1f} s",
                                "cpu_model": cpu_model(), "nproc": os.cpu_count()}
-        gcyc = cyc.cpu().numpy()[ids]
-        out["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids),
-                                      "cpi_error": abs(float(gcyc.sum()) / float(r.cycles.sum()) - 1.0)}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+        out["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids), "cpi_error": cpi_error(cycles, ids, r.cycles)}
+        for k, c in forms.items():
+            out[k]["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids), "cpi_error": cpi_error(c, ids, r.cycles)}
+        for k, v in extra.items():
+            ew, etrace, eblob, eids = v["check"]
+            _, en, edt, er = oracle_rate(ew, etrace, eblob, eids, threads=host_cores())
+            out[k]["cpi_error_vs_oracle"] = {"sampled_subtraces": len(eids), "instructions": en,
+                                             "oracle_s": edt, "cpi_error": cpi_error(v["cycles"], eids, er.cycles)}
+    print(json.dumps(out), flush=True)
+
+
+def run_extra(args, timer):
+    """c5 (65,536 sub-traces, 100M instructions, W=128, 5 x Conv256, FC1024) at
+    BF16 and FP8, and c4 (4,096 log-normal sub-traces, about 40M instructions,
+    the trained c2 architecture) at FP8 and BF16.  Each record: inst/s, ms per
+    call, the roofline of the whole call, and (filled in later) the CPI error
+    of the sampled sub-traces against the FP64 oracle."""
+    import torch
+    res = {}
+    steps, warmup = max(2, args.extra_steps), 1
+    w5 = I.WORKLOADS["c5"]
+    t5 = I.make_trace(w5)
+    b5 = I.workload_weights(w5)
+    ids5 = sorted(np.random.default_rng(w5.seed).choice(t5.n_subtraces, args.c5_sample, replace=False).tolist())
+    _, _, rec, off = device_trace(t5, timer.dev)
+    for prec in ("bf16", "fp8"):
+        sim, r, c = measure(timer, w5, t5, b5.astype(np.float32), prec, steps, warmup, rec, off)
+        sim.close()
+        r["workload"] = f"c5: {w5.description}; weights: {I.weight_recipe(w5)}"
+        r["roofline"] = whole_call_roofline(w5, prec, t5.n_instructions, r["ms_per_step"],
+                                            PATH_KERNEL.get(r["kernel_mode"], r["kernel_mode"]),
+                                            TRAFFIC.get(("c5", prec, PATH_KERNEL.get(r["kernel_mode"]))))
+        res[f"c5_{prec}"] = {"record": r, "cycles": c, "check": (w5, t5, b5, ids5)}
+    del rec, off
+    torch.cuda.empty_cache()
+    w4 = I.WORKLOADS["c4"]
+    t4 = I.make_trace(w4)
+    b4, info = train_predictor(w4, args.train_steps)
+    ids4 = sorted(np.random.default_rng(w4.seed).choice(t4.n_subtraces, 64, replace=False).tolist())
+    _, _, rec, off = device_trace(t4, timer.dev)
+    for prec in ("fp8", "bf16"):
+        sim, r, c = measure(timer, w4, t4, b4, prec, steps, warmup, rec, off, autotune=not args.no_autotune)
+        sim.close()
+        r["workload"] = f"c4: {w4.description}; {t4.n_instructions} instructions; trained predictor"
+        r["trained_predictor"] = info
+        r["roofline"] = whole_call_roofline(w4, prec, t4.n_instructions, r["ms_per_step"],
+                                            PATH_KERNEL.get(r["kernel_mode"], r["kernel_mode"]))
+        res[f"c4_{prec}"] = {"record": r, "cycles": c, "check": (w4, t4, b4.astype(np.float64), ids4)}
+    del rec, off
+    torch.cuda.empty_cache()
+    return res
 
 
 CLUSTER_PHASES = ["step start", "feature rows", "wait conv1", "epilogue conv1", "wait conv2", "epilogue conv2",
                   "wait conv3", "epilogue conv3", "wait FC1", "FC1 epilogue", "wait partials", "head", "extent"]
 
 
-def cluster_phases(w, args, blob32, rec, off, cyc, sm_mhz):
+def cluster_phases(w, args, blob32, rec, off, sm_mhz):
     """CTA 0's time per phase of the cluster kernel (SM clock cycles of one
     extra timed call, converted at the sampled SM clock), in microseconds per
     lock-step."""
+    import torch
     from paper_2105_05821_b300.simnet import Simnet
+    cyc = torch.empty(off.numel() - 1, dtype=torch.int64, device=off.device)
     sim = Simnet.for_arch(w.arch, precision=args.precision, retire_width=w.retire_width, kernel_events=True)
     sim.load_weights(blob32)
     sim.simulate(rec, off, cycles_out=cyc, stats=True)
@@ -478,10 +575,12 @@ def cluster_phases(w, args, blob32, rec, off, cyc, sm_mhz):
     return out
 
 
-def roofline(w, args, blob32, rec, off, cyc, B, path):
+def roofline(w, args, blob32, rec, off, B, path):
     """Per-kernel CUDA-event times from one extra full step with an event pair
     around every launch; roofline of the kernel with the largest share."""
+    import torch
     from paper_2105_05821_b300.simnet import Simnet
+    cyc = torch.empty(B, dtype=torch.int64, device=off.device)
     hbm, bf16_burst, bf16_sus, src = peaks()
     # the per-layer or grid-persistent path the timed call finished on (a cluster
     # call that hands its long queues on is measured here as the path it moved to)
@@ -626,6 +725,10 @@ def main():
                     help="CPI error against sub-trace length (one trace split into more and more parts)")
     ap.add_argument("--sweep-n", type=int, default=65536, help="--sweep: trace length")
     ap.add_argument("--sweep-min", type=int, default=64, help="--sweep: shortest sub-trace")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="c2: skip the c5 / c4 records (profiling runs)")
+    ap.add_argument("--extra-steps", type=int, default=2, help="timed calls of each c5 / c4 record")
+    ap.add_argument("--c5-sample", type=int, default=8, help="c5 sub-traces re-simulated by the oracle")
     ap.add_argument("--subtrace-len", type=int, default=0,
                     help="keep only the first N instructions of every sub-trace (profiling runs)")
     args = ap.parse_args()
@@ -641,14 +744,15 @@ def main():
         run_sweep(args)
         return
     if world > 1:
-        import torch
-        import torch.distributed as dist
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-        dist.init_process_group("nccl")
-    run_ours(args, rank, world)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        # The simulation runs on one GPU: its default kernel loads weights with
+        # cluster-multicast TMA, which stays in single-GPU processes.  Rank 0
+        # says so; every rank exits without GPU work.
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": world,
+                              "unavailable": "one GPU only: the simulation path is built and measured "
+                                             "on a single B300 (run without torchrun)"}), flush=True)
+        return
+    run_ours(args)
 
 
 if __name__ == "__main__":

@@ -350,6 +350,19 @@ def workload_weights(w: Workload) -> np.ndarray:
     return flatten_weights(ws)
 
 
+def weight_recipe(w: Workload) -> str:
+    """One line naming the weight recipe of ``workload_weights``."""
+    a = w.arch
+    names = ("fetch", "execution", "store")[:a.n_lat]
+    rows = ", ".join(f"{n} x{FC2_GAIN[t]:g} bias {FC2_BIAS[t]:g}" for t, n in enumerate(names))
+    s = f"He-normal from PCG64(seed {w.seed}), zero biases; FC2 regression rows {rows}"
+    if a.head == "hybrid":
+        s += f"; class-logit rows x{HYB_CLASS_GAIN:g} with per-class biases"
+    if a.block == "residual":
+        s += "; residual branches scaled by 1/sqrt(2)"
+    return s
+
+
 # ----------------------------------------------------------------------------- random inputs
 def random_windows(n: int, arch: Arch, seed: int) -> np.ndarray:
     """Feature matrices [n, W, 50] with the encoding's value set (one-hots,
