@@ -17,7 +17,10 @@
 // capture that includes this entry point.  All calls share the array and it
 // keeps the last call's contents; calls whose GPU work overlaps (other streams,
 // other threads) race on it.  Nothing in it needs clearing: every call writes
-// each byte it later reads (row count, features, activations).
+// each byte it later reads (row count, features, activations).  The row count
+// is written by a one-thread kernel that takes it by value, so no host memory
+// is read while the call's work runs.  The caller's current device is restored
+// before every return.
 #include <cstdio>
 #include <mutex>
 
@@ -33,6 +36,21 @@ unsigned char *g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+__global__ void set_count_kernel(int32_t *count, int32_t n) { *count = n; }
+
+// Makes `dev` current for the scope and puts the caller's device back after.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -66,7 +84,12 @@ extern "C" simnet_status simnet_cnn_forward_noalloc(simnet_ctx *c, const float *
         return SIMNET_EINVAL;
     }
     if (n == 0) return SIMNET_OK;
-    if (v.device < 0 || v.device >= kMaxDevices || cudaSetDevice(v.device) != cudaSuccess) {
+    if (v.device < 0 || v.device >= kMaxDevices) {
+        ctx_set_error(c, "cnn_forward_noalloc: cannot select the context's device");
+        return SIMNET_ECUDA;
+    }
+    DeviceGuard guard(v.device);
+    if (!guard.ok) {
         ctx_set_error(c, "cnn_forward_noalloc: cannot select the context's device");
         return SIMNET_ECUDA;
     }
@@ -92,12 +115,8 @@ extern "C" simnet_status simnet_cnn_forward_noalloc(simnet_ctx *c, const float *
     float *X = (float *)(base + 256);
     float *act[2] = {(float *)(base + 256 + xb), (float *)(base + 256 + xb + ab)};
     float *h1 = (float *)(base + 256 + xb + 2 * ab);
-    // the row count the GEMMs read; the source is a stack value, which a
-    // pageable-memory cudaMemcpyAsync has staged by the time it returns
-    if (cudaMemcpyAsync(count, &n, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        ctx_set_error(c, "cnn_forward_noalloc: count upload failed");
-        return SIMNET_ECUDA;
-    }
+    // the row count the GEMMs read, passed by value to a one-thread kernel
+    set_count_kernel<<<1, 1, 0, s>>>(count, n);
     launch_pack_x<float>(x, X, (int64_t)n * v.window, s);
     const float *in = X;
     for (int l = 0; l < v.n_layers; l++) {
