@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define SIMNET_ABI_VERSION 3
+#define SIMNET_ABI_VERSION 4
 #define SIMNET_N_FEATURES 50 /* features per instruction row (Sec. 2.2) */
 
 typedef struct simnet_ctx simnet_ctx;
@@ -405,8 +405,10 @@ simnet_status simnet_gather_windows(simnet_ctx *ctx, const simnet_windows *w, co
  * CNN forward for training: x device float [n][window][50], z device float
  * [n][n_out] (FC2 outputs before softplus).  Keeps every layer's output for the next
  * simnet_train_backward (one forward is kept per context).  FP32 contexts
- * compute in FP32; BF16 contexts round GEMM operands to BF16 and accumulate
- * in FP32 (autocast numerics).  Errors: EINVAL, ESTATE, EUNSUPPORTED (FP8).
+ * compute in FP32 on the CUDA cores; BF16 contexts use autocast numerics on the
+ * tcgen05 tensor cores: the windows, the conv layers' outputs and their
+ * gradients are BF16, sums FP32, FC1's output, FC2 and the loss FP32.
+ * Errors: EINVAL, ESTATE, EUNSUPPORTED (FP8).
  */
 simnet_status simnet_train_forward(simnet_ctx *ctx, const float *x, float *z, int32_t n, void *stream);
 
@@ -417,6 +419,24 @@ simnet_status simnet_train_forward(simnet_ctx *ctx, const float *x, float *z, in
  * Errors: EINVAL, ESTATE (no forward yet).
  */
 simnet_status simnet_train_backward(simnet_ctx *ctx, const float *dz, float *grad, void *stream);
+
+/*
+ * The training loss of Sec. 2.4 on FC2 outputs, and its gradient.
+ *   z           device float [n][n_out] (FC2 outputs before softplus).
+ *   labels      device uint8 [n][2]: the (fetch, execution) latency labels of row r.
+ *   grad_scale  device float [1] or NULL (= 1): multiplies dz (the incoming
+ *               gradient of an autograd graph).
+ *   loss        device float [1] or NULL: the mean over the 2n latencies of
+ *               (softplus(z) - label)^2; with SIMNET_FLAG_HYBRID_HEAD plus the
+ *               cross-entropy of each latency's ten class logits against class
+ *               min(label, 9).
+ *   dz          device float [n][n_out] or NULL: grad_scale * dloss/dz.
+ * The same arithmetic as simnet_train_step's loss.  Errors: EINVAL (null z or
+ * labels, n <= 0, or neither output), EUNSUPPORTED (SIMNET_FLAG_STORE_QUEUE:
+ * no store-latency labels).
+ */
+simnet_status simnet_train_loss(simnet_ctx *ctx, const float *z, const uint8_t *labels, int32_t n,
+                                const float *grad_scale, float *loss, float *dz, void *stream);
 
 /*
  * One training step on the windows idx[0..batch) (device int64): gather, forward,

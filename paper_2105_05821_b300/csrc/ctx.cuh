@@ -8,6 +8,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tc_gemm.cuh"
+#include "train_tc.cuh"
 
 using namespace simnet;
 
@@ -28,6 +29,13 @@ struct TrainState {
     float *z = nullptr, *dz = nullptr; // [n][n_out]
     double *loss = nullptr;            // device scalar
     int n_last = 0;                    // windows of the last forward
+    // BF16 contexts train on the tensor cores: BF16 operands and saved activations
+    __nv_bfloat16 *Xb = nullptr;           // packed input [n][W][64]
+    __nv_bfloat16 *Yb[kMaxGemm] = {};      // conv outputs [n * m_mult][N] (post-ReLU)
+    __nv_bfloat16 *dHb = nullptr;          // dLoss / d(FC1 output) [n][H] (ReLU applied)
+    __nv_bfloat16 *dYb[2] = {};            // conv-output gradients, ping-pong (largest activation)
+    TgPlan fwd[kMaxGemm], wgrad[kMaxGemm], dgrad[kMaxGemm];
+    int plan_n = -1;                       // windows the plans were built for
 };
 
 struct simnet_ctx {

@@ -151,13 +151,14 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     free_workspace(c);
     TrainState &t = c->tr;
     for (int l = 0; l < kMaxGemm; l++) {
-        void *tb[] = {t.gW[l], t.gb[l], t.mW[l], t.vW[l], t.mb[l], t.vb[l], t.Y[l]};
+        void *tb[] = {t.gW[l], t.gb[l], t.mW[l], t.vW[l], t.mb[l], t.vb[l], t.Y[l], t.Yb[l]};
         for (void *q : tb)
             if (q) cudaFree(q);
         if (c->W32[l] && (void *)c->W32[l] != c->Wl[l]) cudaFree(c->W32[l]);
     }
     {
-        void *tb[] = {t.gw2, t.gb2, t.mw2, t.vw2, t.mb2, t.vb2, t.X, t.dA, t.dB, t.z, t.dz, t.loss};
+        void *tb[] = {t.gw2, t.gb2, t.mw2, t.vw2, t.mb2, t.vb2, t.X, t.dA, t.dB, t.z, t.dz, t.loss,
+                      t.Xb, t.dHb, t.dYb[0], t.dYb[1]};
         for (void *q : tb)
             if (q) cudaFree(q);
     }
@@ -501,6 +502,7 @@ extern "C" simnet_status simnet_load_weights(simnet_ctx *c, const float *blob, i
     c->weights_fp_dirty = false;
     c->const_stale = false;
     c->has_weights = true;
+    c->tr.plan_n = -1;   // the training GEMMs hold the old weight buffers
     if (c->tr.ready) {  // new weights: restart the optimiser
         TrainState &t = c->tr;
         t.step = 0;

@@ -2,11 +2,15 @@
 // timing model, the CNN forward with saved activations, hand-written backward
 // kernels for the loss, FC and k=2/stride-2 conv layers, and Adam.
 //
-// All GEMMs here are one strided FP32 kernel (CUDA cores) covering the three
-// forms a layer needs: Y = A W^T (forward), dA = dY W (input gradient) and
-// dW = dY^T A (weight gradient, split over rows with atomic accumulation).
-// With a BF16 context the operands are rounded to BF16 on load and the sums
-// stay FP32 (autocast numerics); master weights, moments and gradients are FP32.
+// FP32 contexts run every GEMM on one strided FP32 kernel (CUDA cores) covering
+// the three forms a layer needs: Y = A W^T (forward), dA = dY W (input
+// gradient) and dW = dY^T A (weight gradient, split over rows with atomic
+// accumulation).  BF16 contexts (autocast numerics: BF16 operands, FP32 sums)
+// run the same three forms on the tcgen05 tensor cores (train_tc.cu), with the
+// windows, saved activations and gradients of the conv outputs in BF16; FC2, the
+// loss and the FC1 output stay FP32.  Master weights, moments and weight
+// gradients are FP32 in both; one Adam kernel updates every parameter and
+// refreshes a BF16 context's BF16 weight copies.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -17,11 +21,13 @@ namespace simnet {
 namespace {
 
 // ------------------------------------------------------------------ windows
-// X [n][W][64] (and optionally x50 [n][W][50]): row 0 = instruction i, row r =
-// instruction i-r while i-r >= ctx_begin[i], residence fetch[i-1] - fetch[i-r].
+// X [n][W][64] (FP32 or BF16; optionally also x50 [n][W][50] FP32): row 0 =
+// instruction i, row r = instruction i-r while i-r >= ctx_begin[i], residence
+// fetch[i-1] - fetch[i-r].  Every value is k / 2^m with few bits: exact in BF16.
+template <typename T>
 __global__ void window_gather_kernel(const uint32_t *__restrict__ rec, const int64_t *__restrict__ fetch,
                                      const uint8_t *__restrict__ e_label, const int64_t *__restrict__ ctx_begin,
-                                     const int64_t *__restrict__ idx, int n, int W, float *__restrict__ X,
+                                     const int64_t *__restrict__ idx, int n, int W, T *__restrict__ X,
                                      float *__restrict__ x50) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)n * W * 16) return;
@@ -41,7 +47,13 @@ __global__ void window_gather_kernel(const uint32_t *__restrict__ rec, const int
         const int32_t res32 = (int32_t)(res > 4095 ? 4095 : res);
         for (int j = 0; j < 4; j++) v[j] = feature(chunk * 4 + j, rec[jj], cur, true, res32, e_label[jj], 0);
     }
-    *reinterpret_cast<float4 *>(X + rowid * kNFP + chunk * 4) = make_float4(v[0], v[1], v[2], v[3]);
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(X + rowid * kNFP + chunk * 4) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+        *reinterpret_cast<uint2 *>(X + rowid * kNFP + chunk * 4) =
+            make_uint2(*reinterpret_cast<uint32_t *>(&p0), *reinterpret_cast<uint32_t *>(&p1));
+    }
     if (x50)
         for (int j = 0; j < 4; j++)
             if (chunk * 4 + j < kNF) x50[rowid * kNF + chunk * 4 + j] = v[j];
@@ -240,20 +252,22 @@ __global__ void colsum_kernel(const float *__restrict__ d, int64_t rows, int C, 
 }
 
 // z -> softplus; loss += (y - t)^2 / (2n) with t the label clamped to [0, 255];
-// dz = (y - t) / n * sigmoid(z) (1 above the softplus threshold).
+// dz = (y - t) / n * sigmoid(z) (1 above the softplus threshold), times *gs when
+// given.  The label of row r is labels[2 idx[r] + k] (labels[2 r + k] without
+// idx); dz may be null (loss only).
 __global__ void mse_softplus_kernel(const float *__restrict__ z, const uint8_t *__restrict__ labels,
                                     const int64_t *__restrict__ idx, int n, float *__restrict__ dz,
-                                    double *__restrict__ loss) {
+                                    double *__restrict__ loss, const float *__restrict__ gs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (i < 2 * n) {
         const int r = i >> 1, k = i & 1;
         const float x = z[i];
         const float y = x > 20.f ? x : log1pf(expf(x));
-        const float t = (float)labels[2 * idx[r] + k];
+        const float t = (float)labels[2 * (idx ? idx[r] : (int64_t)r) + k];
         const float diff = y - t;
         const float sg = x > 20.f ? 1.f : 1.f / (1.f + expf(-x));
-        dz[i] = diff / (float)n * sg;
+        if (dz) dz[i] = diff / (float)n * sg * (gs ? *gs : 1.f);
         l = (double)diff * diff / (2.0 * n);
     }
 #pragma unroll
@@ -265,29 +279,32 @@ __global__ void mse_softplus_kernel(const float *__restrict__ z, const uint8_t *
 // outputs per window, the ten class logits of latency k at 11k..11k+9 and its
 // regression output at 11k+10.  loss += (CE + (softplus(z_v) - t)^2) / (2n) with
 // CE = logsumexp(logits) - logit[min(t, 9)]; dz of the logits = (softmax - onehot)
-// / (2n), of the value (softplus(z_v) - t) / n * sigmoid(z_v).
+// / (2n), of the value (softplus(z_v) - t) / n * sigmoid(z_v); labels, idx, gs and a
+// null dz as for mse_softplus_kernel.
 __global__ void hybrid_loss_kernel(const float *__restrict__ z, const uint8_t *__restrict__ labels,
                                    const int64_t *__restrict__ idx, int n, float *__restrict__ dz,
-                                   double *__restrict__ loss) {
+                                   double *__restrict__ loss, const float *__restrict__ gs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (i < 2 * n) {
         const int r = i >> 1, k = i & 1;
         const float *lg = z + (size_t)r * 22 + 11 * k;
-        float *dl = dz + (size_t)r * 22 + 11 * k;
-        const int t = labels[2 * idx[r] + k];
+        const int t = labels[2 * (idx ? idx[r] : (int64_t)r) + k];
         const int cls = t > 8 ? 9 : t;
         float mx = lg[0];
         for (int j = 1; j < 10; j++) mx = fmaxf(mx, lg[j]);
         float se = 0.f;
         for (int j = 0; j < 10; j++) se += expf(lg[j] - mx);
-        const float inv2n = 1.f / (2.f * (float)n);
-        for (int j = 0; j < 10; j++) dl[j] = (expf(lg[j] - mx) / se - (j == cls ? 1.f : 0.f)) * inv2n;
         const float x = lg[10];
         const float y = x > 20.f ? x : log1pf(expf(x));
         const float diff = y - (float)t;
         const float sg = x > 20.f ? 1.f : 1.f / (1.f + expf(-x));
-        dl[10] = diff / (float)n * sg;
+        if (dz) {
+            float *dl = dz + (size_t)r * 22 + 11 * k;
+            const float g = gs ? *gs : 1.f, inv2n = 1.f / (2.f * (float)n);
+            for (int j = 0; j < 10; j++) dl[j] = (expf(lg[j] - mx) / se - (j == cls ? 1.f : 0.f)) * inv2n * g;
+            dl[10] = diff / (float)n * sg * g;
+        }
         const double ce = (double)mx + log((double)se) - (double)lg[cls];
         l = (ce + (double)diff * diff) / (2.0 * n);
     }
@@ -296,18 +313,104 @@ __global__ void hybrid_loss_kernel(const float *__restrict__ z, const uint8_t *_
     if ((threadIdx.x & 31) == 0 && l != 0.0) atomicAdd(loss, l);
 }
 
-__global__ void adam_kernel(float *__restrict__ th, float *__restrict__ m, float *__restrict__ v,
-                            const float *__restrict__ g, int64_t n, float lr, float b1, float b2, float eps,
-                            float c1, float c2) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+// Adam over every parameter array of the CNN in one launch: segment k holds
+// parameters [start[k], start[k+1]) of the concatenation; a BF16 context's
+// weight segments also rewrite their BF16 copy.
+struct AdamSeg {
+    float *th, *m, *v;
+    const float *g;
+    __nv_bfloat16 *shadow;   // or null
+};
+constexpr int kAdamSegs = 2 * kMaxGemm + 2;
+struct AdamTable {
+    AdamSeg seg[kAdamSegs];
+    int64_t start[kAdamSegs + 1];
+    int nseg;
+};
+
+__global__ void adam_multi_kernel(const __grid_constant__ AdamTable T, float lr, float b1, float b2, float eps,
+                                  float c1, float c2) {
+    const int64_t total = T.start[T.nseg];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (i >= T.start[k + 1]) k++;
+        const AdamSeg &S = T.seg[k];
+        const int64_t j = i - T.start[k];
+        const float gi = S.g[j];
+        const float mi = b1 * S.m[j] + (1.f - b1) * gi;
+        const float vi = b2 * S.v[j] + (1.f - b2) * gi * gi;
+        S.m[j] = mi;
+        S.v[j] = vi;
+        const float th = S.th[j] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        S.th[j] = th;
+        if (S.shadow) S.shadow[j] = __float2bfloat16_rn(th);
+    }
 }
+
+// ------------------------------------------------------------------ BF16 training (tensor cores)
+// FC2 backward for a block of 32 windows, one thread per FC1 neuron h:
+// gw2[o][h] += sum_r dz[r][o] H[r][h], gb2[o] += sum_r dz[r][o], and
+// dH[r][h] = (sum_o dz[r][o] w2[o][h]) where H[r][h] > 0 (BF16, the next
+// GEMM's operand), whose FP32 column sums are FC1's bias gradient gb1[h].
+template <int NO>
+__global__ void __launch_bounds__(256) head_bwd_kernel(const float *__restrict__ Hh, const float *__restrict__ dz,
+                                                       const float *__restrict__ w2, int n, int H,
+                                                       __nv_bfloat16 *__restrict__ dH, float *__restrict__ gw2,
+                                                       float *__restrict__ gb2, float *__restrict__ gb1) {
+    constexpr int RB = 32;
+    __shared__ float s_dz[RB][NO];
+    const int r0 = blockIdx.x * RB, rn = min(RB, n - r0);
+    for (int i = threadIdx.x; i < RB * NO; i += blockDim.x) {
+        const int r = i / NO, o = i % NO;
+        s_dz[r][o] = r < rn ? dz[(size_t)(r0 + r) * NO + o] : 0.f;
+    }
+    __syncthreads();
+    if (threadIdx.x < NO) {
+        float sum = 0.f;
+        for (int r = 0; r < rn; r++) sum += s_dz[r][threadIdx.x];
+        atomicAdd(&gb2[threadIdx.x], sum);
+    }
+    for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        float w[NO], g[NO];
+#pragma unroll
+        for (int o = 0; o < NO; o++) {
+            w[o] = w2[(size_t)o * H + h];
+            g[o] = 0.f;
+        }
+        float gb = 0.f;
+        for (int r = 0; r < rn; r++) {
+            const float hv = Hh[(size_t)(r0 + r) * H + h];
+            float d = 0.f;
+#pragma unroll
+            for (int o = 0; o < NO; o++) {
+                g[o] = fmaf(s_dz[r][o], hv, g[o]);
+                d = fmaf(s_dz[r][o], w[o], d);
+            }
+            d = hv > 0.f ? d : 0.f;
+            dH[(size_t)(r0 + r) * H + h] = __float2bfloat16_rn(d);
+            gb += d;
+        }
+#pragma unroll
+        for (int o = 0; o < NO; o++) atomicAdd(&gw2[(size_t)o * H + h], g[o]);
+        atomicAdd(&gb1[h], gb);
+    }
+}
+
+// out[c] += sum over rows of d[r][c] (BF16 input, C even and at most 512): a thread
+// takes one column pair, blockDim / (C / 2) rows at a time.
+__global__ void colsum_bf16_kernel(const __nv_bfloat16 *__restrict__ d, int64_t rows, int C, float *__restrict__ out) {
+    const int CP = C / 2, cp = threadIdx.x % CP, rl = threadIdx.x / CP, rpb = blockDim.x / CP;
+    float a0 = 0.f, a1 = 0.f;
+    for (int64_t r = (int64_t)blockIdx.x * rpb + rl; r < rows; r += (int64_t)gridDim.x * rpb) {
+        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(d + r * C)[cp];
+        a0 += __bfloat162float(v.x);
+        a1 += __bfloat162float(v.y);
+    }
+    atomicAdd(&out[2 * cp], a0);
+    atomicAdd(&out[2 * cp + 1], a1);
+}
+
+__global__ void loss_to_float_kernel(const double *__restrict__ l, float *__restrict__ out) { *out = (float)*l; }
 
 __global__ void to_bf16_kernel(const float *__restrict__ src, __nv_bfloat16 *__restrict__ dst, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -403,6 +506,9 @@ static void gemm(bool round, const float *A, int64_t sam, int64_t sak, const flo
 
 static int64_t layer_rows(const simnet_ctx *c, int l, int n) { return (int64_t)n * c->layer[l].m_mult; }
 
+// Tensor-core training: BF16 contexts.
+static bool train_on_tc(const simnet_ctx *c) { return c->cfg.precision == SIMNET_BF16; }
+
 // Allocate training buffers for n windows (and master-weight bookkeeping once).
 simnet_status ensure_train(simnet_ctx *c, int n) {
     TrainState &t = c->tr;
@@ -438,21 +544,39 @@ simnet_status ensure_train(simnet_ctx *c, int n) {
     }
     if (n <= t.n_cap) return SIMNET_OK;
     CK(cudaDeviceSynchronize());
-    cudaFree(t.X);
-    cudaFree(t.dA);
-    cudaFree(t.dB);
-    cudaFree(t.z);
-    cudaFree(t.dz);
-    for (int l = 0; l < c->n_layers; l++) cudaFree(t.Y[l]);
-    CK(cudaMalloc(&t.X, (size_t)n * k.window * kNFP * 4));
-    size_t big = (size_t)n * k.window * kNFP;
+    void *old[] = {t.X, t.dA, t.dB, t.z, t.dz, t.Xb, t.dHb, t.dYb[0], t.dYb[1]};
+    for (void *q : old)
+        if (q) cudaFree(q);
+    t.X = t.dA = t.dB = t.z = t.dz = nullptr;
+    t.Xb = t.dHb = t.dYb[0] = t.dYb[1] = nullptr;
     for (int l = 0; l < c->n_layers; l++) {
-        const size_t e = (size_t)layer_rows(c, l, n) * c->layer[l].N;
-        CK(cudaMalloc(&t.Y[l], e * 4));
-        big = std::max(big, e);
+        if (t.Y[l]) cudaFree(t.Y[l]);
+        if (t.Yb[l]) cudaFree(t.Yb[l]);
+        t.Y[l] = nullptr;
+        t.Yb[l] = nullptr;
     }
-    CK(cudaMalloc(&t.dA, big * 4));
-    CK(cudaMalloc(&t.dB, big * 4));
+    t.plan_n = -1;
+    const int L = c->n_layers - 1;   // conv layers; layer L is FC1
+    size_t big = 0;
+    for (int l = 0; l < L; l++) big = std::max(big, (size_t)layer_rows(c, l, n) * c->layer[l].N);
+    if (train_on_tc(c)) {
+        CK(cudaMalloc(&t.Xb, (size_t)n * k.window * kNFP * 2));
+        for (int l = 0; l < L; l++) CK(cudaMalloc(&t.Yb[l], (size_t)layer_rows(c, l, n) * c->layer[l].N * 2));
+        CK(cudaMalloc(&t.Y[L], (size_t)n * k.fc_hidden * 4));   // FC1 output, FP32
+        CK(cudaMalloc(&t.dHb, (size_t)n * k.fc_hidden * 2));
+        CK(cudaMalloc(&t.dYb[0], std::max(big, (size_t)1) * 2));
+        CK(cudaMalloc(&t.dYb[1], std::max(big, (size_t)1) * 2));
+    } else {
+        CK(cudaMalloc(&t.X, (size_t)n * k.window * kNFP * 4));
+        size_t bigf = (size_t)n * k.window * kNFP;
+        for (int l = 0; l < c->n_layers; l++) {
+            const size_t e = (size_t)layer_rows(c, l, n) * c->layer[l].N;
+            CK(cudaMalloc(&t.Y[l], e * 4));
+            bigf = std::max(bigf, e);
+        }
+        CK(cudaMalloc(&t.dA, bigf * 4));
+        CK(cudaMalloc(&t.dB, bigf * 4));
+    }
     CK(cudaMalloc(&t.z, (size_t)n * c->n_out * 4));
     CK(cudaMalloc(&t.dz, (size_t)n * c->n_out * 4));
     t.n_cap = n;
@@ -465,34 +589,96 @@ static bool train_precision_ok(const simnet_ctx *c) {
     return (c->cfg.precision == SIMNET_FP32 || c->cfg.precision == SIMNET_BF16) && !c->residual;
 }
 
-// Forward over t.X (already packed): every layer's output kept; z = FC2.
-static void train_forward_enqueue(simnet_ctx *c, int n, cudaStream_t s) {
+// The tensor-core GEMMs of a step over n windows (built when n changes).  Layer l
+// reads A_l = the packed windows (l = 0) or layer l-1's output, viewed as
+// [n * m_mult_l][K_l] (row pairs of a conv layer, the flatten for FC1).
+static simnet_status tc_plans(simnet_ctx *c, int n) {
     TrainState &t = c->tr;
-    const bool round = c->cfg.precision == SIMNET_BF16;
-    const float *in = t.X;
-    for (int l = 0; l < c->n_layers; l++) {
+    if (t.plan_n == n) return SIMNET_OK;
+    const int L = c->n_layers - 1, H = c->cfg.fc_hidden;
+    std::string why;
+    for (int l = 0; l <= L; l++) {
         const GemmLayer &g = c->layer[l];
-        const int R = (int)layer_rows(c, l, n);
-        gemm(round, in, g.K, 1, c->W32[l], 1, g.K, t.Y[l], g.N, R, g.N, g.K, c->bias[l], 1, false, s);
-        in = t.Y[l];
+        const int M = (int)layer_rows(c, l, n);
+        const void *A = l == 0 ? (const void *)t.Xb : (const void *)t.Yb[l - 1];
+        const void *dY = l == L ? (const void *)t.dHb : (const void *)t.dYb[l & 1];
+        bool ok = make_tg_plan(t.fwd[l], l == L ? TG_FWD_F32 : TG_FWD_BF16, A, false, c->Wl[l], false, M, g.N, g.K,
+                               l == L ? (void *)t.Y[L] : (void *)t.Yb[l], g.N, c->bias[l], nullptr, why);
+        // weight gradient, stored transposed by the epilogue: rows = K (A's columns), columns = N
+        ok = ok && make_tg_plan(t.wgrad[l], TG_WGRAD, A, true, dY, true, g.K, g.N, M, t.gW[l], g.K, nullptr, nullptr,
+                                why);
+        if (ok && l > 0)   // input gradient into layer l-1's output, masked by its ReLU
+            ok = make_tg_plan(t.dgrad[l], TG_DGRAD, dY, false, c->Wl[l], true, M, g.K, g.N,
+                              (void *)t.dYb[(l - 1) & 1], 0, nullptr, (const void *)t.Yb[l - 1], why);
+        if (!ok) return fail(c, SIMNET_EUNSUPPORTED, "tensor-core training, layer %d: %s", l, why.c_str());
+    }
+    (void)H;
+    t.plan_n = n;
+    return SIMNET_OK;
+}
+
+// Forward over the packed windows: every layer's output kept; z = FC2.
+static simnet_status train_forward_enqueue(simnet_ctx *c, int n, cudaStream_t s) {
+    TrainState &t = c->tr;
+    if (train_on_tc(c)) {
+        simnet_status st = tc_plans(c, n);
+        if (st != SIMNET_OK) return st;
+        for (int l = 0; l < c->n_layers; l++) launch_tg(t.fwd[l], c->cfg.spin_limit_ns, c->status, s);
+    } else {
+        const float *in = t.X;
+        for (int l = 0; l < c->n_layers; l++) {
+            const GemmLayer &g = c->layer[l];
+            const int R = (int)layer_rows(c, l, n);
+            gemm(false, in, g.K, 1, c->W32[l], 1, g.K, t.Y[l], g.N, R, g.N, g.K, c->bias[l], 1, false, s);
+            in = t.Y[l];
+        }
     }
     launch_head_z(t.Y[c->n_layers - 1], c->w2, c->b2, t.z, n, c->cfg.fc_hidden, c->n_out, s);
     t.n_last = n;
+    return SIMNET_OK;
+}
+
+static void launch_head_bwd(const float *Hh, const float *dz, const float *w2, int n, int H, int no,
+                            __nv_bfloat16 *dH, float *gw2, float *gb2, float *gb1, cudaStream_t s) {
+    const unsigned g = (unsigned)((n + 31) / 32);
+    switch (no) {
+        case 3: head_bwd_kernel<3><<<g, 256, 0, s>>>(Hh, dz, w2, n, H, dH, gw2, gb2, gb1); break;
+        case 22: head_bwd_kernel<22><<<g, 256, 0, s>>>(Hh, dz, w2, n, H, dH, gw2, gb2, gb1); break;
+        case 33: head_bwd_kernel<33><<<g, 256, 0, s>>>(Hh, dz, w2, n, H, dH, gw2, gb2, gb1); break;
+        default: head_bwd_kernel<2><<<g, 256, 0, s>>>(Hh, dz, w2, n, H, dH, gw2, gb2, gb1); break;
+    }
+}
+
+static void launch_colsum_bf16(const __nv_bfloat16 *d, int64_t rows, int C, float *out, cudaStream_t s) {
+    const int rpb = 256 / (C / 2);
+    const int64_t want = (rows + rpb - 1) / rpb;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 4 * 148));
+    colsum_bf16_kernel<<<g, 256, 0, s>>>(d, rows, C, out);
 }
 
 // Backward from t.dz through the saved activations; gradients (GEMM layout) in t.g*.
 static void train_backward_enqueue(simnet_ctx *c, cudaStream_t s) {
     TrainState &t = c->tr;
     const int n = t.n_last, H = c->cfg.fc_hidden, L = c->n_layers, NO = c->n_out;
-    const bool round = c->cfg.precision == SIMNET_BF16;
     for (int l = 0; l < L; l++) {
         cudaMemsetAsync(t.gW[l], 0, (size_t)c->layer[l].N * c->layer[l].K * 4, s);
         cudaMemsetAsync(t.gb[l], 0, (size_t)c->layer[l].N * 4, s);
     }
     cudaMemsetAsync(t.gw2, 0, (size_t)NO * H * 4, s);
     cudaMemsetAsync(t.gb2, 0, (size_t)NO * 4, s);
-    // FC2: dW2 = dz^T H, db2 = sum dz, dH = dz W2 (masked by ReLU of FC1)
     const float *Hh = t.Y[L - 1];
+    if (train_on_tc(c)) {
+        // FC2 and FC1's ReLU on the CUDA cores (2 or 22 outputs), then per layer, last
+        // to first: dW = dY^T A and dA = (dY W) * [A > 0] on the tensor cores
+        launch_head_bwd(Hh, t.dz, c->w2, n, H, NO, t.dHb, t.gw2, t.gb2, t.gb[L - 1], s);
+        for (int l = L - 1; l >= 0; l--) {
+            launch_tg(t.wgrad[l], c->cfg.spin_limit_ns, c->status, s);
+            if (l < L - 1) launch_colsum_bf16(t.dYb[l & 1], layer_rows(c, l, n), c->layer[l].N, t.gb[l], s);
+            if (l > 0) launch_tg(t.dgrad[l], c->cfg.spin_limit_ns, c->status, s);
+        }
+        return;
+    }
+    // FC2: dW2 = dz^T H, db2 = sum dz, dH = dz W2 (masked by ReLU of FC1)
     gemm(false, t.dz, 1, NO, Hh, H, 1, t.gw2, H, NO, H, n, nullptr, 0, true, s);
     colsum_kernel<<<dim3(64, 1), 32, 0, s>>>(t.dz, n, NO, t.gb2);
     float *d = t.dA, *d2 = t.dB;
@@ -503,10 +689,10 @@ static void train_backward_enqueue(simnet_ctx *c, cudaStream_t s) {
         const GemmLayer &g = c->layer[l];
         const int R = (int)layer_rows(c, l, n);
         const float *A = l == 0 ? t.X : t.Y[l - 1];
-        gemm(round, d, 1, g.N, A, g.K, 1, t.gW[l], g.K, g.N, g.K, R, nullptr, 0, true, s);
+        gemm(false, d, 1, g.N, A, g.K, 1, t.gW[l], g.K, g.N, g.K, R, nullptr, 0, true, s);
         colsum_kernel<<<dim3(std::min(R, 512), (g.N + 127) / 128), 128, 0, s>>>(d, R, g.N, t.gb[l]);
         if (l > 0) {
-            gemm(round, d, g.N, 1, c->W32[l], g.K, 1, d2, g.K, R, g.K, g.N, nullptr, 0, false, s);
+            gemm(false, d, g.N, 1, c->W32[l], g.K, 1, d2, g.K, R, g.K, g.N, nullptr, 0, false, s);
             const int64_t e = layer_rows(c, l - 1, n) * c->layer[l - 1].N;
             relu_mask_kernel<<<blocks(e), 256, 0, s>>>(d2, t.Y[l - 1], e);
             std::swap(d, d2);
@@ -548,6 +734,37 @@ static void refresh_shadow(simnet_ctx *c, cudaStream_t s) {
     }
 }
 
+// One Adam step (beta 0.9 / 0.999, eps 1e-8, no weight decay) on every parameter,
+// in one launch; a BF16 context's BF16 weight copies are rewritten by it.
+static void adam_all(simnet_ctx *c, float lr, cudaStream_t s) {
+    TrainState &t = c->tr;
+    t.step++;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)t.step), c2 = 1.f - powf(b2, (float)t.step);
+    const bool bf16 = c->cfg.precision == SIMNET_BF16;
+    AdamTable T;
+    memset(&T, 0, sizeof T);
+    int k = 0;
+    int64_t at = 0;
+    auto add = [&](float *th, float *m, float *v, const float *g, __nv_bfloat16 *sh, int64_t n) {
+        T.seg[k] = AdamSeg{th, m, v, g, sh};
+        T.start[k] = at;
+        at += n;
+        k++;
+    };
+    for (int l = 0; l < c->n_layers; l++) {
+        const int64_t e = (int64_t)c->layer[l].N * c->layer[l].K;
+        add(c->W32[l], t.mW[l], t.vW[l], t.gW[l], bf16 ? (__nv_bfloat16 *)c->Wl[l] : nullptr, e);
+        add(c->bias[l], t.mb[l], t.vb[l], t.gb[l], nullptr, c->layer[l].N);
+    }
+    add(c->w2, t.mw2, t.vw2, t.gw2, nullptr, (int64_t)c->n_out * c->cfg.fc_hidden);
+    add(c->b2, t.mb2, t.vb2, t.gb2, nullptr, c->n_out);
+    T.nseg = k;
+    T.start[k] = at;
+    const unsigned g = (unsigned)std::min<int64_t>((at + 255) / 256, 8 * 148);
+    adam_multi_kernel<<<g, 256, 0, s>>>(T, lr, b1, b2, eps, c1, c2);
+}
+
 static void invalidate_plans(simnet_ctx *c) {
     for (auto &g : c->gexec)
         if (g) { cudaGraphExecDestroy(g); g = nullptr; }
@@ -565,8 +782,12 @@ extern "C" simnet_status simnet_gather_windows(simnet_ctx *c, const simnet_windo
     simnet_status st = ensure_train(c, n);
     if (st != SIMNET_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    window_gather_kernel<<<blocks((int64_t)n * c->cfg.window * 16), 256, 0, s>>>(
-        w->records, w->fetch, w->e_label, w->ctx_begin, idx, n, c->cfg.window, c->tr.X, x_out);
+    if (train_on_tc(c))
+        window_gather_kernel<__nv_bfloat16><<<blocks((int64_t)n * c->cfg.window * 16), 256, 0, s>>>(
+            w->records, w->fetch, w->e_label, w->ctx_begin, idx, n, c->cfg.window, c->tr.Xb, x_out);
+    else
+        window_gather_kernel<float><<<blocks((int64_t)n * c->cfg.window * 16), 256, 0, s>>>(
+            w->records, w->fetch, w->e_label, w->ctx_begin, idx, n, c->cfg.window, c->tr.X, x_out);
     CK(cudaGetLastError());
     return SIMNET_OK;
 }
@@ -580,8 +801,10 @@ extern "C" simnet_status simnet_train_forward(simnet_ctx *c, const float *x, flo
     simnet_status st = ensure_train(c, n);
     if (st != SIMNET_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    launch_pack_x<float>(x, c->tr.X, (int64_t)n * c->cfg.window, s);
-    train_forward_enqueue(c, n, s);
+    if (train_on_tc(c)) launch_pack_x<__nv_bfloat16>(x, c->tr.Xb, (int64_t)n * c->cfg.window, s);
+    else launch_pack_x<float>(x, c->tr.X, (int64_t)n * c->cfg.window, s);
+    st = train_forward_enqueue(c, n, s);
+    if (st != SIMNET_OK) return st;
     CK(cudaMemcpyAsync(z, c->tr.z, (size_t)n * c->n_out * 4, cudaMemcpyDeviceToDevice, s));
     CK(cudaGetLastError());
     return SIMNET_OK;
@@ -600,6 +823,27 @@ extern "C" simnet_status simnet_train_backward(simnet_ctx *c, const float *dz, f
     return SIMNET_OK;
 }
 
+extern "C" simnet_status simnet_train_loss(simnet_ctx *c, const float *z, const uint8_t *labels, int32_t n,
+                                           const float *grad_scale, float *loss, float *dz, void *stream) {
+    if (!c) return SIMNET_EINVAL;
+    if (!z || !labels || n <= 0 || (!loss && !dz)) return fail(c, SIMNET_EINVAL, "train_loss: bad arguments");
+    if (c->store_queue)
+        return fail(c, SIMNET_EUNSUPPORTED, "train_loss: the latency labels carry no store latency");
+    CK(cudaSetDevice(c->device));
+    simnet_status st = ensure_train(c, 0);   // the loss accumulator
+    if (st != SIMNET_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *acc = c->tr.loss;
+    CK(cudaMemsetAsync(acc, 0, sizeof(double), s));
+    if (c->hybrid)
+        hybrid_loss_kernel<<<blocks(2 * (int64_t)n), 256, 0, s>>>(z, labels, nullptr, n, dz, acc, grad_scale);
+    else
+        mse_softplus_kernel<<<blocks(2 * (int64_t)n), 256, 0, s>>>(z, labels, nullptr, n, dz, acc, grad_scale);
+    if (loss) loss_to_float_kernel<<<1, 1, 0, s>>>(acc, loss);
+    CK(cudaGetLastError());
+    return SIMNET_OK;
+}
+
 extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *w, const int64_t *idx, int32_t batch,
                                            float lr, float *loss_out, void *stream) {
     if (!c) return SIMNET_EINVAL;
@@ -614,28 +858,23 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
     if (st != SIMNET_OK) return st;
     TrainState &t = c->tr;
     cudaStream_t s = (cudaStream_t)stream;
-    window_gather_kernel<<<blocks((int64_t)batch * c->cfg.window * 16), 256, 0, s>>>(
-        w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X, nullptr);
-    train_forward_enqueue(c, batch, s);
+    if (train_on_tc(c))
+        window_gather_kernel<__nv_bfloat16><<<blocks((int64_t)batch * c->cfg.window * 16), 256, 0, s>>>(
+            w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.Xb, nullptr);
+    else
+        window_gather_kernel<float><<<blocks((int64_t)batch * c->cfg.window * 16), 256, 0, s>>>(
+            w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X, nullptr);
+    st = train_forward_enqueue(c, batch, s);
+    if (st != SIMNET_OK) return st;
     CK(cudaMemsetAsync(t.loss, 0, sizeof(double), s));
     if (c->hybrid)
-        hybrid_loss_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
+        hybrid_loss_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss,
+                                                                      nullptr);
     else
-        mse_softplus_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss);
+        mse_softplus_kernel<<<blocks(2 * (int64_t)batch), 256, 0, s>>>(t.z, w->labels, idx, batch, t.dz, t.loss,
+                                                                       nullptr);
     train_backward_enqueue(c, s);
-    // Adam (beta 0.9 / 0.999, eps 1e-8, no weight decay) on every parameter
-    t.step++;
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    const float c1 = 1.f - powf(b1, (float)t.step), c2 = 1.f - powf(b2, (float)t.step);
-    for (int l = 0; l < c->n_layers; l++) {
-        const int64_t e = (int64_t)c->layer[l].N * c->layer[l].K, nb = c->layer[l].N;
-        adam_kernel<<<blocks(e), 256, 0, s>>>(c->W32[l], t.mW[l], t.vW[l], t.gW[l], e, lr, b1, b2, eps, c1, c2);
-        adam_kernel<<<blocks(nb), 256, 0, s>>>(c->bias[l], t.mb[l], t.vb[l], t.gb[l], nb, lr, b1, b2, eps, c1, c2);
-    }
-    const int64_t h2 = (int64_t)c->n_out * c->cfg.fc_hidden;
-    adam_kernel<<<blocks(h2), 256, 0, s>>>(c->w2, t.mw2, t.vw2, t.gw2, h2, lr, b1, b2, eps, c1, c2);
-    adam_kernel<<<1, 32, 0, s>>>(c->b2, t.mb2, t.vb2, t.gb2, c->n_out, lr, b1, b2, eps, c1, c2);
-    refresh_shadow(c, s);
+    adam_all(c, lr, s);
     invalidate_plans(c);
     c->weights_fp_dirty = true;
     c->const_stale = true;

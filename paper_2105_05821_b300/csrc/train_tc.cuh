@@ -1,0 +1,43 @@
+// train_tc.cuh -- tcgen05 GEMMs of the BF16 training step (host interface).
+#pragma once
+#include <cuda.h>
+
+#include <string>
+
+#include "common.cuh"
+
+namespace simnet {
+
+// What a training GEMM's epilogue does with C[m][n] = sum_r A(m, r) B(n, r).
+enum TgEpi : int {
+    TG_FWD_BF16 = 0,  // out bf16 [M][N] = ReLU(C + bias[n])
+    TG_FWD_F32 = 1,   // out f32 [M][N] = ReLU(C + bias[n])
+    TG_DGRAD = 2,     // out bf16 [M][N] = C where mask[m][n] > 0, else 0 (ReLU derivative)
+    TG_WGRAD = 3,     // out f32 [N][ldo]: out[n][m] += C (split reductions add atomically)
+};
+
+// One training GEMM, built once per (buffers, sizes) and launched every step.
+//   A(m, r): K-major, stored [M][R] (a_mn = false), or MN-major, stored [R][M] (a_mn = true)
+//   B(n, r): K-major, stored [N][R] (b_mn = false), or MN-major, stored [R][N] (b_mn = true)
+// All operands BF16; R is padded to a multiple of 64 by zero fill (TMA out-of-bounds reads).
+struct TgPlan {
+    bool ready = false;
+    int epi = 0, BN = 0, stages = 0, grid = 0;
+    bool a_mn = false, b_mn = false;
+    int M = 0, N = 0, R = 0, ldo = 0;
+    int n_tiles_n = 0, m_tiles = 0, splits = 1, kb_per_split = 0;
+    size_t smem = 0;
+    const float *bias = nullptr;
+    const void *mask = nullptr;
+    void *out = nullptr;
+    CUtensorMap tA, tB;
+};
+
+// Describe C = A * B^T for the given storage; returns false (and why) for
+// shapes the kernel does not take (N not a multiple of 64, or of BN).
+bool make_tg_plan(TgPlan &p, int epi, const void *A, bool a_mn, const void *B, bool b_mn, int M, int N, int R,
+                  void *out, int ldo, const float *bias, const void *mask, std::string &why);
+
+void launch_tg(const TgPlan &p, int64_t spin_ns, int32_t *status, cudaStream_t s);
+
+}  // namespace simnet

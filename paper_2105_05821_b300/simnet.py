@@ -41,7 +41,7 @@ EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_e
            "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
            "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune",
            "simnet_simulate_steps", "simnet_state_save", "simnet_state_load", "simnet_kernel_path",
-           "simnet_path_choice"]
+           "simnet_path_choice", "simnet_train_loss"]
 STATE_KINDS = {"sim": 0, "train": 1}
 
 
@@ -111,6 +111,8 @@ def lib() -> C.CDLL:
         L.simnet_train_forward.argtypes = [P, P, P, C.c_int32, P]
         L.simnet_train_backward.restype = C.c_int
         L.simnet_train_backward.argtypes = [P, P, P, P]
+        L.simnet_train_loss.restype = C.c_int
+        L.simnet_train_loss.argtypes = [P, P, P, C.c_int32, P, P, P, P]
         L.simnet_train_step.restype = C.c_int
         L.simnet_train_step.argtypes = [P, C.POINTER(_Windows), P, C.c_int32, C.c_float, P, P]
         L.simnet_set_weights_device.restype = C.c_int
@@ -333,12 +335,22 @@ class Simnet:
         self._check(lib().simnet_train_backward(self._h, _ptr(dz), _ptr(grad), _stream(stream)))
         return grad
 
-    def train_step(self, w, idx, lr=1e-3, stream=None) -> float:
+    def train_loss(self, z, labels, grad_scale=None, loss=None, dz=None, stream=None):
+        """The training loss on FC2 outputs z [n, n_out] against uint8 labels [n, 2]
+        (device): fills `loss` (float [1]) and/or `dz` (float [n, n_out]),
+        dz scaled by the device scalar `grad_scale` when given."""
+        self._check(lib().simnet_train_loss(self._h, _ptr(z), _ptr(labels), z.shape[0], _ptr(grad_scale),
+                                            _ptr(loss), _ptr(dz), _stream(stream)))
+        return loss, dz
+
+    def train_step(self, w, idx, lr=1e-3, stream=None, loss: bool = True) -> Optional[float]:
+        """One fused step; returns the loss (the call then synchronises), or
+        None with loss=False (asynchronous)."""
         win = self._win(w)
-        loss = C.c_float(0.0)
+        out = C.c_float(0.0)
         self._check(lib().simnet_train_step(self._h, C.byref(win), _ptr(idx), idx.numel(), float(lr),
-                                            C.byref(loss), _stream(stream)))
-        return float(loss.value)
+                                            C.byref(out) if loss else None, _stream(stream)))
+        return float(out.value) if loss else None
 
     def set_weights_device(self, blob, stream=None):
         self._check(lib().simnet_set_weights_device(self._h, _ptr(blob), _stream(stream)))

@@ -7,7 +7,10 @@ backward kernels.
 * `CNNFunction`: a torch.autograd.Function whose forward and backward are
   simnet_train_forward / simnet_train_backward; the parameters are one flat
   FP32 tensor in the canonical blob layout, so any torch optimiser can drive it.
-* `train`: the library's own fused step (gather, forward, MSE, backward, Adam).
+* `LossFunction`: the training loss (squared error of softplus, plus the class
+  cross-entropy with the hybrid head) as a torch.autograd.Function over
+  simnet_train_loss: the library's loss kernels compute the loss and dz.
+* `train`: the library's own fused step (gather, forward, loss, backward, Adam).
 """
 from __future__ import annotations
 
@@ -54,23 +57,28 @@ class CNNFunction(torch.autograd.Function):
         return None, g, None
 
 
-def mse_softplus(z: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
-    """Mean over all outputs of (softplus(z) - clamp(label, 0, 255))^2."""
-    return (torch.nn.functional.softplus(z) - labels.float().clamp(0, 255)).pow(2).mean()
+class LossFunction(torch.autograd.Function):
+    """loss = the library's training loss of FC2 outputs z [n, n_out] against
+    uint8 latency labels [n, 2] (Sec. 2.4; with the hybrid head Sec. 2.3's
+    cross-entropy is added).  Forward and backward are simnet_train_loss."""
 
+    @staticmethod
+    def forward(ctx, z, labels, sim: Simnet):
+        z = z.detach().contiguous().float()
+        labels = labels.contiguous()
+        loss = torch.empty((), dtype=torch.float32, device=z.device)
+        sim.train_loss(z, labels, loss=loss)
+        ctx.save_for_backward(z, labels)
+        ctx.sim = sim
+        return loss
 
-def hybrid_loss(z: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
-    """Hybrid head (Sec. 2.3) loss on z [n, 22]: mean over the 2n latencies of the
-    cross-entropy of the ten class logits against class min(label, 9) plus the
-    squared error of softplus(regression output) against the label."""
-    y = labels.float().clamp(0, 255)
-    total = z.new_zeros(())
-    for t in range(2):
-        cls = y[:, t].clamp(max=9).long()
-        ce = torch.nn.functional.cross_entropy(z[:, 11 * t:11 * t + 10], cls, reduction="sum")
-        se = (torch.nn.functional.softplus(z[:, 11 * t + 10]) - y[:, t]).pow(2).sum()
-        total = total + ce + se
-    return total / (2 * z.shape[0])
+    @staticmethod
+    def backward(ctx, g):
+        z, labels = ctx.saved_tensors
+        dz = torch.empty_like(z)
+        gs = g.detach().reshape(1).contiguous().float()
+        ctx.sim.train_loss(z, labels, grad_scale=gs, dz=dz)
+        return dz, None, None
 
 
 def train(sim: Simnet, w: Windows, steps: int, batch: int, lr: float = 1e-3, seed: int = 0,

@@ -40,6 +40,29 @@ def run_gpu(sim: Simnet, trace: I.Trace, replay=None, logs=True):
     return out
 
 
+# Plain PyTorch statements of the training losses (Sec. 2.4; the hybrid head's
+# cross-entropy of Sec. 2.3), the references the library's loss kernels are
+# checked against.
+def mse_softplus(z: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
+    """Mean over all outputs of (softplus(z) - clamp(label, 0, 255))^2."""
+    return (torch.nn.functional.softplus(z) - labels.float().clamp(0, 255)).pow(2).mean()
+
+
+def hybrid_loss(z: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
+    """Hybrid head (Sec. 2.3) loss on z [n, 22]: mean over the 2n latencies of the
+    cross-entropy of the ten class logits against class min(label, 9) plus the
+    squared error of softplus(regression output) against the label."""
+    y = labels.float().clamp(0, 255)
+    total = z.new_zeros(())
+    for t in range(2):
+        cls = y[:, t].clamp(max=9).long()
+        ce = torch.nn.functional.cross_entropy(z[:, 11 * t:11 * t + 10], cls, reduction="sum")
+        se = (torch.nn.functional.softplus(z[:, 11 * t + 10]) - y[:, t]).pow(2).sum()
+        total = total + ce + se
+    return total / (2 * z.shape[0])
+
+
+
 def make_sim(arch, precision="fp32", blob=None, seed=None, **kw):
     kw.setdefault("auto_path", False)   # a test pins its path unless it tests the choice
     sim = Simnet.for_arch(arch, precision=precision, **kw)

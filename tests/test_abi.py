@@ -39,7 +39,7 @@ def test_exports_every_declared_symbol(libpath):
 
 def test_loads_and_reports_version(libpath):
     L = ctypes.CDLL(libpath)
-    assert L.simnet_abi_version() == 3
+    assert L.simnet_abi_version() == 4
 
 
 def test_sm103a_only(libpath):

@@ -18,12 +18,19 @@ import torch
 import oracle
 from paper_2105_05821_b300 import inputs as I
 from paper_2105_05821_b300.simnet import SimnetError
-from paper_2105_05821_b300.train import CNNFunction, Windows, hybrid_loss
+from paper_2105_05821_b300.train import CNNFunction, LossFunction, Windows
 
-from gpu_util import latency_error, make_sim, run_gpu
+from gpu_util import hybrid_loss, latency_error, make_sim, run_gpu
 from test_gpu_sim import teacher_forced_check
 from test_oracle_hybrid import bias_only_blob
 from tolerances import check
+
+
+def sim_windows(arch, blob, n, seed):
+    """n feature matrices the simulator builds: the oracle's per-step inputs on
+    a short synthetic trace with these weights."""
+    trace = I.small_trace([n // 3, n // 3, n - 2 * (n // 3)], seed=seed)
+    return oracle.simulate(oracle.Config.of(arch), trace.records, trace.offsets, blob, features=True).feat
 
 pytestmark = pytest.mark.gpu
 
@@ -127,9 +134,11 @@ def test_c2_architecture_hybrid_cluster():
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_cnn_forward_outputs(precision):
+    """FC2 outputs, element by element, on the feature rows the simulator
+    builds (the oracle's per-step inputs of a short trace)."""
     cfg = oracle.Config.of(ARCH)
     blob = I.workload_weights(I.Workload("h", ARCH, 1, 1, seed=7))
-    x = I.random_windows(300, ARCH, 12)
+    x = sim_windows(ARCH, blob, 300, seed=12)
     sim, _ = make_sim(ARCH, precision, blob=blob)
     z = sim.cnn_forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
     zr = oracle.cnn_forward(cfg, blob, x)
@@ -162,8 +171,10 @@ def test_training_gradient_and_adam_match_oracle(data):
     wt = torch.from_numpy(blob.astype(np.float32)).cuda().requires_grad_(True)
     z = CNNFunction.apply(torch.from_numpy(x.astype(np.float32)).cuda(), wt, sim)
     assert tuple(z.shape) == (256, 22)
-    loss = hybrid_loss(z, torch.from_numpy(y).cuda())
+    loss = LossFunction.apply(z, torch.from_numpy(y.astype(np.uint8)).cuda(), sim)   # the library's loss kernel
     loss.backward()
+    assert loss.item() == pytest.approx(hybrid_loss(z.detach().double(), torch.from_numpy(y).cuda()).item(),
+                                        rel=1e-5)
     assert loss.item() == pytest.approx(loss_o, rel=1e-4)
     g = wt.grad.cpu().numpy().astype(np.float64)
     k = 0
