@@ -490,9 +490,12 @@ def run_ours(args):
         out["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids), "cpi_error": cpi_error(cycles, ids, r.cycles)}
         for k, c in forms.items():
             out[k]["cpi_error_vs_oracle"] = {"sampled_subtraces": len(ids), "cpi_error": cpi_error(c, ids, r.cycles)}
+        runs = {}   # one oracle run per workload (the precisions share its sample and weights)
         for k, v in extra.items():
             ew, etrace, eblob, eids = v["check"]
-            _, en, edt, er = oracle_rate(ew, etrace, eblob, eids, threads=host_cores())
+            if ew.name not in runs:
+                runs[ew.name] = oracle_rate(ew, etrace, eblob, eids, threads=host_cores())
+            _, en, edt, er = runs[ew.name]
             out[k]["cpi_error_vs_oracle"] = {"sampled_subtraces": len(eids), "instructions": en,
                                              "oracle_s": edt, "cpi_error": cpi_error(v["cycles"], eids, er.cycles)}
     print(json.dumps(out), flush=True)
@@ -629,72 +632,120 @@ def roofline(w, args, blob32, rec, off, B, path):
 def run_sweep(args):
     """Sub-trace length against simulation error, the trade-off behind splitting
     a trace for parallel simulation (Sec. 3.3): one synthetic trace of N
-    instructions with the c2 workload's record mix and CNN, simulated unsplit
-    (one sub-trace, FP32 form: the reference) and split into equal contiguous
-    sub-traces (BF16, default kernel path).  Each split sub-trace starts from
-    an empty queue and ends with its own drain, so its CPI drifts from the
-    unsplit CPI as sub-traces get shorter; prints one JSON line."""
+    instructions with the c2 workload's record mix and CNN, simulated by the
+    FP64 oracle as one sub-trace (the reference: no split), and split into
+    equal contiguous sub-traces, both by the oracle (the method's own error
+    from splitting: every sub-trace starts from an empty queue and ends with
+    its own drain) and on the GPU's default BF16 path (that error plus the
+    precision's).  The GPU FP32 form of the unsplit trace is reported beside
+    the oracle's.  Prints one JSON line."""
     import torch
     from paper_2105_05821_b300.simnet import Simnet
+    import oracle
     w = I.WORKLOADS["c2"]
     N = args.sweep_n
     records = I.make_records(N, 7)
-    blob = I.workload_weights(w).astype(np.float32)
+    blob64 = I.workload_weights(w)
+    blob = blob64.astype(np.float32)
+    cfg = oracle.Config.of(w.arch, retire_width=w.retire_width)
     rec = torch.from_numpy(records.view(np.int32).copy()).cuda()
 
-    def run(sim, n_sub):
+    def gpu(sim, n_sub):
         off = torch.from_numpy(I.equal_offsets(N, n_sub)).cuda()
         sim.simulate(rec, off, stats=False)   # warm
         torch.cuda.synchronize()
         st = sim.simulate(rec, off)
         return st.total_cycles / N, st.ms_total, sim.kernel_path
 
-    ref = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
-    ref.load_weights(blob)
-    cpi_ref, ms_ref, _ = run(ref, 1)
+    def orc(n_sub):
+        t0 = time.perf_counter()
+        r = oracle.simulate(cfg, records, I.equal_offsets(N, n_sub), blob64, n_threads=host_cores())
+        return float(r.cycles.sum()) / N, time.perf_counter() - t0
+
+    cpi_ref, s_ref = orc(1)
+    ref32 = Simnet.for_arch(w.arch, precision="fp32", retire_width=w.retire_width)
+    ref32.load_weights(blob)
+    cpi32, ms32, _ = gpu(ref32, 1)
     sim = Simnet.for_arch(w.arch, precision="bf16", retire_width=w.retire_width)
     sim.load_weights(blob)
     rows = []
     length = N
     while length >= args.sweep_min:
         n_sub = N // length
-        cpi, ms, path = run(sim, n_sub)
-        rows.append({"subtrace_len": length, "n_subtraces": n_sub, "cpi": cpi, "cpi_error": cpi / cpi_ref - 1.0,
+        cpi, ms, path = gpu(sim, n_sub)
+        cpi_o, s_o = (cpi_ref, s_ref) if n_sub == 1 else orc(n_sub)
+        rows.append({"subtrace_len": length, "n_subtraces": n_sub, "cpi_gpu_bf16": cpi,
+                     "cpi_oracle_split": cpi_o, "split_error_oracle": cpi_o / cpi_ref - 1.0,
+                     "gpu_error_vs_oracle_unsplit": cpi / cpi_ref - 1.0,
+                     "gpu_error_vs_oracle_split": cpi / cpi_o - 1.0, "oracle_s": s_o,
                      "ms": ms, "inst_per_s": N / (ms / 1e3), "kernel_mode": path})
         length //= 4
     print(json.dumps({"metric": "CPI error of split simulation vs sub-trace length", "unit": "relative",
-                      "instructions": N, "reference": {"form": "FP32, one sub-trace", "cpi": cpi_ref, "ms": ms_ref},
-                      "data": "synthetic", "rows": rows}))
+                      "instructions": N, "data": "synthetic",
+                      "reference": {"form": "FP64 oracle, one sub-trace", "cpi": cpi_ref, "oracle_s": s_ref},
+                      "gpu_fp32_unsplit": {"cpi": cpi32, "error_vs_oracle": cpi32 / cpi_ref - 1.0, "ms": ms32},
+                      "rows": rows}))
 
 
 def run_training(args):
     """Training throughput on the training workload (windows/s of fused library
-    steps: gather, forward, MSE, hand-written backward, Adam); a side measurement,
+    steps: gather, forward, loss, hand-written backward, Adam; BF16 on the
+    tensor cores, with the FP32 CUDA-core form beside it); a side measurement,
     not the simulation metric."""
     import torch
     from paper_2105_05821_b300.simnet import Simnet
     from paper_2105_05821_b300.train import Windows
     w = I.WORKLOADS["c3"]
     rec = I.make_records(w.n_instructions, w.seed)
-    win = Windows.from_labels(rec, I.toy_labels(rec))
-    sim = Simnet.for_arch(w.arch, precision=args.precision if args.precision != "fp8" else "bf16")
-    sim.load_weights(I.workload_weights(w).astype(np.float32))
+    labels = I.toy_labels(rec)
+    win = Windows.from_labels(rec, labels)
+    blob = I.workload_weights(w)
     batch = 4096
     g = torch.Generator(device="cuda").manual_seed(0)
     idx = [torch.randint(0, len(win), (batch,), device="cuda", generator=g) for _ in range(args.warmup + args.steps)]
-    for i in range(args.warmup):
-        sim.train_step(win, idx[i], 1e-3)
-    torch.cuda.synchronize()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    ev[0].record()
-    losses = [sim.train_step(win, idx[args.warmup + i], 1e-3) for i in range(args.steps)]
-    ev[1].record()
-    torch.cuda.synchronize()
-    ms = ev[0].elapsed_time(ev[1]) / args.steps
-    print(json.dumps({"metric": "training windows/s (fused gather, forward, backward, Adam)",
-                      "value": batch / (ms / 1e3), "unit": "windows/s", "ms_per_step": ms, "batch": batch,
-                      "dtype": sim.precision, "loss_first": losses[0], "loss_last": losses[-1],
-                      "config": {"workload": f"c3: {w.description}"}}), flush=True)
+
+    def one(prec):
+        sim = Simnet.for_arch(w.arch, precision=prec)
+        sim.load_weights(blob.astype(np.float32))
+        for i in range(args.warmup):
+            sim.train_step(win, idx[i], 1e-3)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for i in range(args.steps - 1):
+            sim.train_step(win, idx[args.warmup + i], 1e-3, loss=False)
+        last = sim.train_step(win, idx[args.warmup + args.steps - 1], 1e-3)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        sim.close()
+        return {"value": batch / (ms / 1e3), "unit": "windows/s", "ms_per_step": ms, "loss_last": last,
+                "dtype": prec}
+
+    main = one(args.precision if args.precision != "fp8" else "bf16")
+    out = {"metric": "training windows/s (fused gather, forward, loss, backward, Adam)", **main, "batch": batch,
+           "steps": args.steps, "warmup": args.warmup,
+           "config": {"workload": f"c3: {w.description}; weights: {I.weight_recipe(w)}"}}
+    if main["dtype"] != "fp32":
+        out["fp32_form"] = one("fp32")
+        flop = 2.0 * 3.0 * w.arch.macs_per_inference() * batch     # forward, input and weight gradients
+        hbm, burst, sus, src = peaks()
+        out["roofline"] = {"bound": "tensor", "achieved": flop / (main["ms_per_step"] / 1e3) / 1e12,
+                           "peak": sus, "unit": "TFLOP/s", "peak_source": f"{src} bf16 sustained",
+                           "note": "3 x forward MACs per window (forward, input and weight gradients)"}
+        out["roofline"]["frac"] = out["roofline"]["achieved"] / sus
+    if not args.no_cpu_baseline:
+        import oracle
+        cfg = oracle.Config.of(w.arch)
+        ids = np.random.default_rng(3).integers(0, len(rec), 64)
+        x = oracle.window_features(cfg, rec, labels.fetch, labels.E, labels.ctx_begin, ids)
+        y = np.stack([labels.F[ids], labels.E[ids]], 1).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.loss_grad(cfg, blob, x, y)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(ids) / dt, "unit": "windows/s", "cores": 1, "kind": "oracle",
+                               "sample": f"FP64 forward + backward of {len(ids)} windows, {dt:.2f} s"}
+    print(json.dumps(out), flush=True)
 
 
 def main():

@@ -23,6 +23,7 @@ from paper_2105_05821_b300.simnet import Simnet, SimnetError
 
 from gpu_util import latency_error, make_sim, run_gpu
 from test_gpu_sim import teacher_forced_check
+from test_gpu_hybrid import sim_windows
 from tolerances import LAT_MAX, check
 
 pytestmark = pytest.mark.gpu
@@ -81,7 +82,7 @@ def test_persistent_matches_per_layer_on_identical_states(arch):
 def test_cnn_forward_outputs(precision):
     arch = rb(I.Arch(32, 3, 64, 256), "hybrid")
     blob = I.workload_weights(I.Workload("r", arch, 1, 1, seed=5))
-    x = I.random_windows(200, arch, 4)
+    x = sim_windows(arch, blob, 200, seed=4)   # the feature rows the simulator builds
     sim, _ = make_sim(arch, precision, blob=blob)
     z = sim.cnn_forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
     zr = oracle.cnn_forward(oracle.Config.of(arch), blob, x)
