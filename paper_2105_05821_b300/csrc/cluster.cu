@@ -13,9 +13,10 @@
 //     writes the feature rows (Sec. 2.2) of its slots that those positions
 //     depend on straight into shared memory and runs the k=2 / stride-2 conv
 //     pyramid on them (Sec. 2.3), one tcgen05 MMA per 128-row tile and layer
-//     (rows as A, the layer's weights streamed by TMA multicast as B, several
-//     panels to a pipeline stage); layer l's epilogue writes layer l+1's
-//     operand in place, rows 2j and 2j+1 of a slot side by side along K;
+//     (rows as A, the layer's weights streamed by TMA as B, each CTA loading
+//     its own copy, several panels to a pipeline stage); layer l's epilogue
+//     writes layer l+1's operand in place, rows 2j and 2j+1 of a slot side by
+//     side along K;
 //   * the last conv layer's rows of all 128 slots are exchanged through
 //     distributed shared memory by bulk copies, and every CTA accumulates FC1
 //     for its 1 / CS of the hidden neurons in TMEM over the passes; positions
@@ -26,8 +27,12 @@
 //     the clock and queue update and the drain (Eq. 1); the CTA then shares its
 //     new extent with the cluster (st.async).
 // Every wait is bounded (globaltimer); an expired wait records a timeout and
-// the CTA leaves at the next step boundary; a final cluster barrier keeps each
-// CTA's shared memory alive until its peers no longer start writes into it.
+// the CTA leaves at the next step boundary.  Leaving is deterministic: each CTA
+// counts what it sent every peer (extents, partial sums, row copies), tells
+// the peers at the end, and every CTA then waits, on the very barriers those
+// writes complete on, until each write sent to it has landed (the bytes no
+// peer will send are completed locally); a last cluster barrier then keeps
+// every CTA's shared memory alive until no copy reads or writes it any more.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -39,7 +44,7 @@
 namespace simnet {
 
 struct CArgs {
-    CUtensorMap tW[3];   // conv weights [C][K_l] (BF16, GEMM layout), box C/4 rows x 64 columns
+    CUtensorMap tW[3];   // conv weights [C][K_l] (BF16, GEMM layout), box C rows x 64 columns
     CUtensorMap tF;      // FC1 weights [H][K1], box H/4 rows x 64 columns
     const float *cbias[3];
     const float *fbias, *w2, *b2, *fc1_const;
@@ -105,8 +110,10 @@ __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, i
     y.prm = y.part + 2 * CS * SPC * 4 * part_floats(no);
     y.slot = al_up(y.prm + (uint32_t)prm_floats(L, C, HN, no) * 4, 16);
     y.misc = y.slot + SPC * 8 + 10 * SPC * 4;
-    y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8, 8);   // + 32 phase counters (profiling)
-    y.total = y.bars + (2 * stages + 16) * 8;
+    // misc: extents in | control words | 32 phase counters (profiling) | exit counters
+    // (64 ints) | what every peer sent this CTA (one uint4 per peer)
+    y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8 + 256 + 128, 8);
+    y.total = y.bars + (2 * stages + 17) * 8;
     return y;
 }
 
@@ -223,23 +230,21 @@ __device__ __noinline__ void drain_wait(uint32_t bar, uint32_t parity, int64_t l
     while (!cl_try(bar, parity) && (int64_t)(gtimer() - t0) < limit) {
     }
 }
-// Arrive (once) on the barrier at this offset in every CTA of `mask` when this
-// thread's earlier tcgen05 operations have completed.
-__device__ __forceinline__ void commit_mc(uint32_t bar, uint16_t mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                     bar),
-                 "h"(mask)
-                 : "memory");
+// Arrive on a barrier of another CTA of the cluster (shared::cluster address
+// from mapa); the release orders this thread's earlier writes before it.
+__device__ __forceinline__ void cl_arrive_remote(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
-// 2D TMA load of one box into the same shared-memory offset of every CTA in
-// `mask`, each CTA's barrier at `bar`'s offset receiving the bytes.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-        : "memory");
+// Complete `bytes` of a local barrier's transaction count: stands in for bytes
+// that were expected but that no peer will send.
+__device__ __forceinline__ void mbar_complete_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Plain 16-byte store into another CTA's shared memory (made visible by the next
+// cluster barrier).
+__device__ __forceinline__ void cl_st_v4(uint32_t a, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
 }
 // 64 consecutive TMEM columns of this warp's 32 lanes (two 32x32b loads, one
 // wait, in one statement so that no use of the registers precedes the wait).
@@ -318,7 +323,6 @@ __device__ __forceinline__ int positions_of(int E, int L, int rows_n) {
 template <int CS, int NO>
 __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_constant__ CArgs a) {
     constexpr int SPC = 128 / CS;   // batch slots per CTA
-    constexpr uint16_t kAll = (uint16_t)((1u << CS) - 1u);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int L = a.L, C = a.C, HN = a.H / CS, S = a.stages, cap = a.cap, PM = pass_positions(L);
@@ -335,7 +339,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     const int64_t drain_ns = lim > 200000000 ? lim : 200000000;   // 0.2 s at least
     // Record where the first expired wait of the launch was (sites: 1 weight stage free,
     // 2 extent (producer), 3 weight panel, 4 extent (workers), 5 conv layer done, 6 exchange
-    // buffer free, 7 exchanged rows in, 8 FC1 done, 9 FC2 partial sums in).
+    // buffer free, 7 exchanged rows in, 8 FC1 done, 9 FC2 partial sums in, 10 FC1 done
+    // (warp 1's signal to the cluster)).
     auto note = [&](bool ok, int site, int64_t step, int64_t pass) -> bool {
         if (!ok && *(volatile int32_t *)a.status == kStatusTimeout &&
             atomicCAS(&a.tinfo[0], 0ull, (unsigned long long)site) == 0ull) {
@@ -353,8 +358,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // bytes a phase of B_PART / B_EXT receives: every CTA's FC2 partials (two column halves)
     // for this CTA's slots; every CTA's (extent, live count)
     constexpr uint32_t kPartBytes = 2u * CS * SPC * PF * 4u, kExtBytes = CS * 8u;
-    const int B_D = 2 * S, B_EMPTY = 2 * S + 1, B_DFC = 2 * S + 2, B_PART = 2 * S + 3, B_EXT = 2 * S + 4,
-              B_FIN = 2 * S + 6, B_FULL = 2 * S + 7;
+    const int B_D = 2 * S, B_DFC = 2 * S + 2, B_PART = 2 * S + 3, B_EXT = 2 * S + 4,
+              B_FIN = 2 * S + 6, B_FULL = 2 * S + 7, B_F1D = 2 * S + 15;
+    // the exchanged rows of pass R may be overwritten once every CTA's FC1 of pass R is
+    // done: CS arrivals on B_EMPTY + (R & 1) (two barriers, so that an arrival for the
+    // next pass can never complete the phase of this one)
+    auto b_empty = [&](int64_t r) { return bar((r & 1) ? 2 * S + 16 : 2 * S + 1); };
+    constexpr uint32_t kRowBytes = SPC * 128;   // one CTA's rows of one exchanged 64-column panel
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
     float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
     float *s_Se = s_fb + HN;                                 // [HN] S[e] of the current step
@@ -376,15 +386,21 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     int *cnt = reinterpret_cast<int *>(sm + y.misc + 16 * CS + 24);   // weight panels issued, consumed
     // phase counters (CTA 0, on request): shared-memory accumulators, written out at the end
     unsigned long long *pacc = reinterpret_cast<unsigned long long *>(sm + y.misc + 16 * CS + 32);
+    // exit counters: what this CTA sent (X_*_SENT), consumed (X_*_CONS, X_ROWS_DONE) and armed
+    volatile int *xs = reinterpret_cast<volatile int *>(sm + y.misc + 16 * CS + 32 + 256);
+    enum { X_EXT_SENT = 0, X_PART_SENT, X_EXT_CONS, X_PART_CONS, X_ROWS_DONE, X_FC1_WAITED, X_ARMED_R, X_ARMED_NP,
+           X_FPH, X_DONE, X_F1C, X_ROWS_SENT = 16, X_ROWS_NP = 24 };
+    uint4 *inbox = reinterpret_cast<uint4 *>(sm + y.misc + 16 * CS + 32 + 512);   // [source CTA]
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; s++) {
             mbar_init(bar(s), 1);
-            mbar_init(bar(S + s), CS);   // free once every CTA's MMAs have read it
+            mbar_init(bar(S + s), 1);    // free once this CTA's MMAs have read it
         }
         mbar_init(bar(B_D), 1);
         for (int i = 0; i < 8; i++) mbar_init(bar(B_FULL + i), 1);   // thread 0's expect_tx; the peers' copies
-        mbar_init(bar(B_EMPTY), CS);
+        mbar_init(b_empty(0), CS);
+        mbar_init(b_empty(1), CS);
         mbar_init(bar(B_DFC), 1);
         // partial sums and extents arrive by st.async, counted in bytes: one local
         // arrival (with the byte count) per phase, made here for the first phases
@@ -395,9 +411,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         mbar_expect_tx(bar(B_EXT), kExtBytes);
         mbar_expect_tx(bar(B_EXT + 1), kExtBytes);
         mbar_init(bar(B_FIN), 1);
+        mbar_init(bar(B_F1D), 1);
         *abort_f = 0;
         cnt[0] = cnt[1] = 0;
         for (int k = 0; k < 32; k++) pacc[k] = 0;
+        for (int k = 0; k < 64; k++) xs[k] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -484,23 +502,17 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 if (++ps == S) { ps = 0; pph ^= 1u; }
             };
             bool ok = true;
-            // n panels of pb bytes (K-columns x0, x0 + 64, ...) into the next stage.  Conv
-            // panels: this CTA loads rows [rank C/CS, (rank+1) C/CS) of each into every CTA of
-            // the cluster (all need the same weights); FC1 panels are its own.
-            auto load = [&](const CUtensorMap *m, int x0, int yy, uint32_t pb, int n, bool shared_panel) {
+            // n panels of pb bytes (K-columns x0, x0 + 64, ...) into the next stage: whole
+            // conv panels (all C rows) or this CTA's rows of FC1 panels
+            auto load = [&](const CUtensorMap *m, int x0, int yy, uint32_t pb, int n) {
                 const int s = ps;
-                if (!note(cl_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
+                if (!note(mbar_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
                     ok = false;
                     return;
                 }
                 mbar_expect_tx(bar(s), (uint32_t)n * pb);
-                for (int j = 0; j < n; j++) {
-                    const uint32_t dst = ring0 + (uint32_t)s * kStage + (uint32_t)j * pb;
-                    if (shared_panel)
-                        tma_load_2d_mc(dst + rank * (uint32_t)(C / CS) * 128u, m, bar(s), x0 + 64 * j, yy, kAll);
-                    else
-                        tma_load_2d(dst, m, bar(s), x0 + 64 * j, yy);
-                }
+                for (int j = 0; j < n; j++)
+                    tma_load_2d(ring0 + (uint32_t)s * kStage + (uint32_t)j * pb, m, bar(s), x0 + 64 * j, yy);
                 adv();
             };
             // conv stage i of a pass (all layers' weights in consumption order), i in [from, to)
@@ -512,7 +524,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     for (int g = 0; g < conv_stages(l) && ok; g++, i++) {
                         if (i < from || i >= to) continue;
                         const int p0 = g * kConvPer, n = min(kConvPer, panels_of(l) - p0);
-                        load(&a.tW[l], p0 * 64, (int)rank * (C / CS), (uint32_t)C * 128u, n, true);
+                        load(&a.tW[l], p0 * 64, 0, (uint32_t)C * 128u, n);
                     }
             };
             // Before a step's extent is known only its first S stages are loaded: they are
@@ -531,7 +543,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     conv_loads(q0 > 0 ? 0 : pre, n_conv_stages);
                     const int np = P * C / 64;
                     for (int p0 = 0; p0 < np && ok; p0 += kFcPer)
-                        load(&a.tF, q0 * C + p0 * 64, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0), false);
+                        load(&a.tF, q0 * C + p0 * 64, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0));
                 }
                 if (t + 1 < a.n_steps) conv_loads(0, pre);   // the next step's first stages
             }
@@ -591,7 +603,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
                     }
                 }
-                commit_mc(bar(S + s), kAll);   // stage read here: tell every CTA
+                umma_commit(bar(S + s));   // the stage is free once these MMAs have read it
                 adv();
             }
             if (mma_ok) umma_commit(bar(B_D));
@@ -609,6 +621,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 cl_st_async_v2(cl_map(smem_u32(&ext_in[nb * CS + rank]), (uint32_t)lane), (uint32_t)mx, (uint32_t)al,
                                cl_map(bar(B_EXT + nb), (uint32_t)lane));
             }
+            __syncwarp();
+            if (lane == 0) xs[X_EXT_SENT] = xs[X_EXT_SENT] + 1;
         };
         if (wi == 0) send_ext(0);
         // feature rows of positions q0 .. q0 + P - 1 into the first layer's operand
@@ -657,7 +671,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             build_rows(0, P0);
             if (tid == 0) {
                 const bool ok = note(sleep_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status, true), 4, t, 0);
-                if (ok) mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
+                if (ok) {
+                    mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
+                    xs[X_EXT_CONS] = xs[X_EXT_CONS] + 1;
+                }
                 int E, AL;
                 read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 ctl[0] = max(positions_of(E, L, a.rows_n), P0);
@@ -690,9 +707,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         issue_conv(l, P);
                         // the peers' rows of this pass, expected while the first layer's MMAs run
                         // (every phase of the previous pass completed before its FC1 MMAs)
-                        if (l == 0)
+                        if (l == 0) {
                             for (int i = 0; i < P * C / 64; i++)
-                                mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * (uint32_t)(SPC * 128));
+                                mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * kRowBytes);
+                            xs[X_ARMED_R] = (int)R + 1;
+                            xs[X_ARMED_NP] = P * C / 64;
+                        }
                     }
                     __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
                     uint64_t ti1 = prof ? (uint64_t)clock64() : 0;
@@ -704,7 +724,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     }
                     d_uses++;
                     if (last && R >= 1 && ok)   // every CTA has consumed the previous pass's exchanged rows
-                        ok = note(cl_wait(bar(B_EMPTY), (uint32_t)((R - 1) & 1), lim, abort_f, a.status), 6, t, R);
+                        ok = note(cl_wait(b_empty(R - 1), (uint32_t)(((R - 1) >> 1) & 1), lim, abort_f, a.status),
+                                  6, t, R);
                     ok = __all_sync(0xffffffffu, ok);
                     tc_fence_after();
                     mark(2 + 2 * l);
@@ -775,7 +796,6 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         // peer: one bulk copy per 64-column panel and peer, counted on the peer's
                         // B_FULL + panel; a peer overwrites its copy only after B_EMPTY, i.e. after
                         // every CTA's FC1 of this pass, which waited for all of its copies
-                        constexpr uint32_t kRowBytes = SPC * 128;   // this CTA's rows of one panel
                         const int np = P * C / 64;
                         // one warp per peer (warps 1..CS-1: the copies take ~1 us to issue, which
                         // warp 0's MMA thread spends on FC1 instead)
@@ -785,6 +805,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                 const uint32_t src = fc0 + (uint32_t)i * 16384u + rank * kRowBytes;
                                 cl_bulk_copy(cl_map(src, peer), src, kRowBytes, cl_map(bar(B_FULL + i), peer));
                             }
+                            xs[X_ROWS_SENT + wi] = (int)R + 1;   // what this warp sent its peer
+                            xs[X_ROWS_NP + wi] = np;
                         }
                         // FC1 over this pass's positions, each panel once every CTA's rows of it
                         // are in (thread 0): the MMAs of the first panels overlap later copies
@@ -805,6 +827,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                         break;
                                     }
                                     fph ^= 1u << pi;
+                                    xs[X_FPH] = (int)fph;
+                                    xs[X_FC1_WAITED] = pi + 1;
                                     if (prof) pacc[18] += (uint64_t)clock64() - tf;
                                     const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u),
                                                    bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(HN * 128));
@@ -814,10 +838,15 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                                     (q0 | pi | k) != 0 ? 1u : 0u);
                                 }
                                 if (!mma_ok) break;
-                                commit_mc(bar(S + s), kAll);
+                                umma_commit(bar(S + s));
                                 adv();
                             }
-                            if (mma_ok) commit_mc(bar(B_EMPTY), kAll);
+                            if (mma_ok) {   // warp 1 tells every CTA once these MMAs are done
+                                umma_commit(bar(B_F1D));
+                                xs[X_F1C] = xs[X_F1C] + 1;
+                                xs[X_ROWS_DONE] = (int)R + 1;
+                                xs[X_FC1_WAITED] = 0;
+                            }
                             if (prof) pacc[19] += (uint64_t)clock64() - tw;   // FC1 wait + issue
                         }
                         __syncwarp();
@@ -915,13 +944,17 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                                   __float_as_uint(ph[4 * q4 + 2]), __float_as_uint(ph[4 * q4 + 3])),
                                        pb);
                 }
+                if (tid == 0) xs[X_PART_SENT] = xs[X_PART_SENT] + 1;   // every worker sent its share
                 if (prof) pacc[31] += (uint64_t)clock64() - te0;   // partial sums to their owners
                 mark(9);
             }
             // head, clock and queue update, drain: one thread per slot (warp 2)
             if (wi == 0) {
                 bool ok = note(sleep_wait(bar(B_PART), (uint32_t)(t & 1), lim, abort_f, a.status, true), 9, t, R);
-                if (ok && lane == 0) mbar_expect_tx(bar(B_PART), kPartBytes);   // the next step's phase
+                if (ok && lane == 0) {
+                    mbar_expect_tx(bar(B_PART), kPartBytes);   // the next step's phase
+                    xs[X_PART_CONS] = xs[X_PART_CONS] + 1;
+                }
                 ok = __all_sync(0xffffffffu, ok);
                 mark(10);
                 const int s = lane;
@@ -1078,6 +1111,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         }
         if (tid == 0) {   // every MMA done before TMEM is released
             cnt[1] = it;
+            __threadfence_block();
+            xs[X_DONE] = 1;   // no more FC1 commits: warp 1 stops once it has signalled them all
             umma_commit(bar(B_FIN));
             drain_wait(bar(B_FIN), 0u, drain_ns);
         }
@@ -1103,6 +1138,27 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 A->evict[b] = s_ev[s];
             }
         }
+    } else if (lane == 0) {
+        // ---------------------------------------------------------------- warp 1: FC1 done
+        // Once this CTA's FC1 MMAs of a pass have completed, its copy of the pass's rows
+        // may be overwritten: one arrive on every CTA's B_EMPTY + (pass & 1).
+        int rh = 0;
+        uint64_t t0 = gtimer();
+        while (true) {
+            if (try_sleep(bar(B_F1D), (uint32_t)(rh & 1), 20000u, false)) {
+                for (int r = 0; r < CS; r++) cl_arrive_remote(cl_map(b_empty(rh), (uint32_t)r));
+                rh++;
+                t0 = gtimer();
+                continue;
+            }
+            if (xs[X_DONE] && rh >= xs[X_F1C]) break;
+            if ((int64_t)(gtimer() - t0) > lim) {
+                *abort_f = 1;
+                atomicExch(a.status, kStatusTimeout);
+                note(false, 10, -1, rh);
+                break;
+            }
+        }
     }
     __syncthreads();
     if (a.prof && blockIdx.x == 0 && threadIdx.x < 32) a.prof[threadIdx.x] = pacc[threadIdx.x];
@@ -1110,13 +1166,63 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         for (int it = cnt[1]; it < cnt[0]; it++) drain_wait(bar(it % S), (uint32_t)(it / S) & 1u, drain_ns);
     }
     __syncthreads();
-    cluster_sync_all();   // no peer starts a write into this CTA's shared memory any more
-    if (*abort_f) {
-        // after a wait gave up, a peer may have started a row copy into this CTA that no
-        // barrier here waits for; copies already issued land within microseconds
-        const uint64_t t0 = gtimer();
-        while (gtimer() - t0 < 200000ull) __nanosleep(1000);
+    // Leaving.  Every peer learns what this CTA sent it: extents and partial-sum
+    // steps, and the passes (and their panel count) of row copies.
+    if (threadIdx.x < CS) {
+        const int d = (int)threadIdx.x, wd = (d - (int)rank + CS) % CS;   // the warp that sends to d
+        const uint4 v = make_uint4((uint32_t)xs[X_EXT_SENT], (uint32_t)xs[X_PART_SENT],
+                                   wd ? (uint32_t)xs[X_ROWS_SENT + wd] : 0u, wd ? (uint32_t)xs[X_ROWS_NP + wd] : 0u);
+        cl_st_v4(cl_map(smem_u32(&inbox[rank]), (uint32_t)d), v);
     }
+    cluster_sync_all();   // the counts are in, and no CTA starts another write into a peer
+    if (threadIdx.x == 0) {
+        // Wait, on the barriers they complete on, until every write sent to this CTA
+        // has landed.  A phase that was armed for bytes no peer sent gets them
+        // completed here; one that was not armed is armed for what was sent.
+        // Extents: phases of the steps after the last one consumed (armed two ahead);
+        // partial sums: the step after the last one consumed; rows: the pass after the
+        // last one whose FC1 read them all (peers send a pass only after every CTA's
+        // FC1 of the previous one), from the first panel not yet read.
+        const int tc = xs[X_EXT_CONS];
+        for (int st = tc; st < tc + 2; st++) {
+            uint32_t got = 0;
+            for (int q = 0; q < CS; q++)
+                if ((int)inbox[q].x > st) got += 8u;
+            const uint32_t b = bar(B_EXT + (st & 1));
+            if (got < kExtBytes) mbar_complete_tx(b, kExtBytes - got);
+            drain_wait(b, (uint32_t)(st >> 1) & 1u, drain_ns);
+        }
+        const int pc = xs[X_PART_CONS];
+        uint32_t got = 0;
+        for (int q = 0; q < CS; q++)
+            if ((int)inbox[q].y > pc) got += kPartBytes / CS;
+        if (got < kPartBytes) mbar_complete_tx(bar(B_PART), kPartBytes - got);
+        drain_wait(bar(B_PART), (uint32_t)pc & 1u, drain_ns);
+        const int rc = xs[X_ROWS_DONE];
+        int senders = 0, np = 0;
+        for (int q = 0; q < CS; q++)
+            if (q != (int)rank && (int)inbox[q].z > rc) {
+                senders++;
+                np = (int)inbox[q].w;
+            }
+        const bool armed = xs[X_ARMED_R] > rc;
+        if (armed) np = xs[X_ARMED_NP];
+        const uint32_t fph_now = (uint32_t)xs[X_FPH];
+        for (int i = armed ? xs[X_FC1_WAITED] : 0; i < np; i++) {
+            const uint32_t b = bar(B_FULL + i);
+            if (armed) {
+                const uint32_t missing = (uint32_t)(CS - 1 - senders) * kRowBytes;
+                if (missing) mbar_complete_tx(b, missing);
+            } else if (senders > 0) {
+                mbar_expect_tx(b, (uint32_t)senders * kRowBytes);
+            } else {
+                continue;
+            }
+            drain_wait(b, (fph_now >> i) & 1u, drain_ns);
+        }
+    }
+    __syncthreads();
+    cluster_sync_all();   // every copy into any CTA of the cluster has landed: none reads or writes here any more
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
@@ -1151,10 +1257,29 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     return true;
 }
 
+// Largest stage count for a cluster size and stage size (0 if none fits).
+static int cluster_stages_max(const simnet_ctx *c, int CS, int stage_bytes) {
+    const simnet_config &k = c->cfg;
+    int st = 8;
+    while (st >= 2 && c_layout(CS, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, st, c->n_out, stage_bytes).total +
+                              1024 > 232448)
+        st--;
+    return st >= 2 ? st : 0;
+}
+
+bool cluster_size_ok(const simnet_ctx *c, int CS, int B) {
+    if (CS == 4) return true;
+    return CS == 8 && c->cfg.fc_hidden / 8 >= 64 && (B + 127) / 128 * 8 <= num_sms();
+}
+
+int cluster_stage_limit(const simnet_ctx *c, int CS, int stage_bytes) { return cluster_stages_max(c, CS, stage_bytes); }
+
 bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::string &why) {
     if (!cluster_eligible(c, why)) return false;
     const simnet_config &k = c->cfg;
-    const int CS = cluster_size(k, B);
+    const bool tuned = c->tuned_B == B;
+    const int CS = tuned && c->tuned_cluster_size && cluster_size_ok(c, c->tuned_cluster_size, B)
+                       ? c->tuned_cluster_size : cluster_size(k, B);
     CArgs a;
     memset(&a, 0, sizeof a);
     a.L = k.n_conv;
@@ -1164,7 +1289,7 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.rows_n = c->rows_n;
     for (int l = 0; l < a.L; l++) {
         if (!encode_map_2d(a.tW[l], SIMNET_BF16, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, 64,
-                           (uint32_t)(a.C / CS), why))
+                           (uint32_t)a.C, why))
             return false;
         a.cbias[l] = c->bias[l];
     }
@@ -1186,7 +1311,11 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     const int no = c->n_out;
     auto fits = [&](int st, int sb) { return c_layout(CS, a.L, a.C, a.H, a.cap, st, no, sb).total + 1024 <= 232448; };
     a.stage_bytes = fits(3, 2 * kPanelMax) ? 2 * kPanelMax : kPanelMax;
+    if (tuned && (c->tuned_cluster_stage_bytes == kPanelMax || c->tuned_cluster_stage_bytes == 2 * kPanelMax) &&
+        fits(2, c->tuned_cluster_stage_bytes))
+        a.stage_bytes = c->tuned_cluster_stage_bytes;   // the autotuner's pick
     while (stages > 2 && !fits(stages, a.stage_bytes)) stages--;
+    if (tuned && c->tuned_cluster_stages >= 2 && c->tuned_cluster_stages < stages) stages = c->tuned_cluster_stages;
     a.stages = stages;
     const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no, a.stage_bytes).total + 1024;
     auto kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid> : cluster_kernel<4, kOutHybrid>)
