@@ -74,7 +74,7 @@ typedef enum {
 #define SIMNET_FLAG_LAYERWISE 0x10u    /* BF16/FP8: one kernel per layer and step (CUDA graphs,
                                           PDL, dense padding rows) instead of the default single
                                           persistent kernel that skips the padding */
-#define SIMNET_FLAG_NO_CLUSTER 0x20u   /* BF16: the grid-wide persistent kernel even where the
+#define SIMNET_FLAG_NO_CLUSTER 0x20u   /* BF16/FP8: the grid-wide persistent kernel even where the
                                           cluster kernel (SIMNET_PATH_CLUSTER) applies */
 #define SIMNET_FLAG_HYBRID_HEAD 0x40u  /* hybrid latency head (Sec. 2.3): FC2 has 22 outputs, for
                                           each latency t (0 fetch, 1 execution) ten class logits
@@ -178,17 +178,35 @@ typedef struct {
 #define SIMNET_KERNEL_COMPACT 11        /* active-set compaction */
 
 /*
- * Autotuner: for batches of n_subtraces sub-traces, time every tile width
- * (64, 128, 256 output columns) of every tensor-core layer, one layer after
- * another, on a synthetic trace of `steps` instructions per sub-trace, and keep
- * the fastest whole simnet_simulate call.  Later calls with the same batch size
- * use the choice.  bn_out (host, one entry per GEMM: n_conv + 1, or
- * 3 * n_conv + 1 with SIMNET_FLAG_RESIDUAL; 25 always suffice) or NULL receives the
- * widths.  FP32 contexts have nothing to tune (returns OK).  Synchronises.
- * Errors: EINVAL, ESTATE (no weights), ENOMEM.
+ * Autotuner: for batches of n_subtraces sub-traces, time the launch shapes of
+ * the kernel path such a call takes, on a synthetic trace of `steps`
+ * instructions per sub-trace, one knob after another, keeping the fastest
+ * whole simnet_simulate call (the faster of two timed calls per candidate):
+ *   cluster kernel:     cluster size (4 or 8 CTAs), weight-stage size (16 or
+ *                       32 KB), number of weight stages (2 up to what fits);
+ *   persistent kernel:  tile width (64, 128, 256 output columns) of every
+ *                       tensor-core GEMM phase, then its pipeline stages (2-6);
+ *   per-layer kernels:  the tile width of every tensor-core GEMM.
+ * Later calls with the same batch size use the choice (simnet_autotune_plan
+ * reports it).  Launch shapes change no per-element arithmetic except the
+ * split of FC1's FC2 partial sums (cluster size, FC1 tile width), which moves
+ * FP32 rounding only.  bn_out (host, one entry per GEMM: n_conv + 1, or
+ * 3 * n_conv + 1 with SIMNET_FLAG_RESIDUAL; 25 always suffice) or NULL receives
+ * the tile widths.  FP32 contexts have nothing to tune (returns OK).
+ * Synchronises.  Errors: EINVAL, ESTATE (no weights), ENOMEM.
  */
 simnet_status simnet_autotune(simnet_ctx *ctx, int32_t n_subtraces, int32_t steps, int32_t *bn_out,
                               void *stream);
+
+/*
+ * The last autotuner choice, into out (host, n >= 6 entries): out[0] the batch
+ * size it applies to (-1: none), out[1] the kernel path it was tuned on
+ * (SIMNET_PATH_*), out[2] cluster size, out[3] weight-stage bytes, out[4] weight
+ * stages (cluster kernel; 0 when not tuned), out[5] pipeline stages of the
+ * persistent kernel (6: as many as fit), out[6 + l] the tile width of GEMM l.
+ * Errors: EINVAL (NULL pointers or n < 6).
+ */
+simnet_status simnet_autotune_plan(const simnet_ctx *ctx, int32_t *out, int32_t n);
 
 /* ABI version of the loaded library (SIMNET_ABI_VERSION of its build). */
 int32_t simnet_abi_version(void);
@@ -353,12 +371,12 @@ simnet_status simnet_phase_detail(simnet_ctx *ctx, uint64_t *out, int32_t n);
 #define SIMNET_PATH_LAYERWISE 1  /* one kernel per layer and step (CUDA graphs) */
 #define SIMNET_PATH_PERSISTENT 2 /* one cooperative kernel, grid-wide barriers between phases */
 #define SIMNET_PATH_CLUSTER 3    /* clusters of 4 or 8 CTAs each owning 128 sub-traces for the
-                                    whole call, no grid-wide synchronisation (BF16; 2-3 plain
+                                    whole call, no grid-wide synchronisation (BF16 or FP8; 2-3 plain
                                     conv layers of 64 or 128 channels; FC1 width 256 or 512;
                                     either head, or the write queue with the regression head) */
 
 /* Path that ran the last steps of the last simnet_simulate call (SIMNET_PATH_*), or -1 for
- * a NULL context.  A BF16 call where the cluster kernel applies starts on it; if the call is
+ * a NULL context.  A BF16/FP8 call where the cluster kernel applies starts on it; if the call is
  * longer than 512 steps and steps 64-127 needed more than two passes of last-conv positions
  * per step (long queues), the rest of the call runs on the grid-wide path.  The grid-wide
  * path of a long call is the persistent kernel or the per-layer kernels, whichever a timed

@@ -1,6 +1,6 @@
 // cluster.cu -- the whole lock-step simulation of one simnet_simulate call as
-// independent thread-block clusters (BF16 CNNs with 2 or 3 conv layers of 64
-// or 128 channels).
+// independent thread-block clusters (BF16 or FP8 e4m3 CNNs with 2 or 3 conv
+// layers of 64 or 128 channels).
 //
 // Sub-traces never interact (Sec. 3.3), so a cluster of CS = 4 or 8 CTAs takes
 // 128 batch slots for the whole call, 128 / CS per CTA, and needs no grid-wide
@@ -44,9 +44,12 @@
 namespace simnet {
 
 struct CArgs {
-    CUtensorMap tW[3];   // conv weights [C][K_l] (BF16, GEMM layout), box C rows x 64 columns
-    CUtensorMap tF;      // FC1 weights [H][K1], box H/4 rows x 64 columns
+    CUtensorMap tW[3];   // conv weights [C][K_l] (GEMM layout), box C rows x 128 bytes
+    CUtensorMap tF;      // FC1 weights [H][K1], box H/CS rows x 128 bytes
     const float *cbias[3];
+    // FP8: per-output-channel weight scales of the conv layers and FC1, and the conv
+    // layers' requantisation multipliers (1 / the next layer's input scale)
+    const float *cws[3], *cos[3], *fws;
     const float *fbias, *w2, *b2, *fc1_const;
     const StepArgs *A;
     int32_t *status;
@@ -86,29 +89,33 @@ struct CLay {
 // head's 22 padded to 24 (16-byte stores).
 __host__ __device__ inline int part_floats(int no) { return no == 2 ? 2 : no == 3 ? 4 : 24; }
 // prm: conv biases [L*C] | FC1 bias [HN] | S[e] [HN] | b2 [24] | FC2 rows of this
-// CTA's neurons: [2][HN] or [3][HN] (regression) or [HN][24] (hybrid, padded).
-__host__ __device__ inline int prm_floats(int L, int C, int HN, int no) {
-    return L * C + 2 * HN + 24 + (no == 2 ? 2 * HN : no == 3 ? 3 * HN : 24 * HN);
+// CTA's neurons: [2][HN] or [3][HN] (regression) or [HN][24] (hybrid, padded) |
+// FP8 only: conv weight scales [L*C], conv requantisation [L*C], FC1 weight scales [HN].
+__host__ __device__ inline int prm_floats(int L, int C, int HN, int no, int es) {
+    return L * C + 2 * HN + 24 + (no == 2 ? 2 * HN : no == 3 ? 3 * HN : 24 * HN) + (es == 1 ? 2 * L * C + HN : 0);
 }
 
-__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages, int no, int stage_bytes) {
+// es: bytes per operand element (2 BF16, 1 FP8).  Every operand row is a 128-byte
+// swizzled row of 128 / es elements.
+__host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, int stages, int no, int stage_bytes,
+                                         int es) {
     CLay y;
     const int HN = H / CS, SPC = 128 / CS, PM = pass_positions(L);
-    // operand of layer l: its rows (pass positions x pairs x slots) x K, in 64-column panels
-    uint32_t actb = (uint32_t)(PM * (1 << (L - 1)) * SPC) * 256u;
+    // operand of layer l: its rows (pass positions x pairs x slots) x K, in 128-byte panels
+    uint32_t actb = (uint32_t)(PM * (1 << (L - 1)) * SPC) * 128u * (uint32_t)es;
     for (int l = 1; l < L; l++) {
-        const uint32_t b = (uint32_t)(PM * (1 << (L - 1 - l)) * SPC) * 4u * (uint32_t)C;
+        const uint32_t b = (uint32_t)(PM * (1 << (L - 1 - l)) * SPC) * 2u * (uint32_t)(es * C);
         actb = b > actb ? b : actb;
     }
     y.ring = 0;
     y.act = (uint32_t)stages * (uint32_t)stage_bytes;
     y.fc1a = al_up(y.act + actb, 1024);
-    y.qring = y.fc1a + 256u * (uint32_t)(pass_positions(L) * C);           // 128 slots x positions x C BF16
+    y.qring = y.fc1a + 128u * (uint32_t)(pass_positions(L) * C * es);      // 128 slots x positions x C
     y.mring = y.qring + (uint32_t)SPC * cap * 8;                            // memory write queues (n_out 3)
     y.rec = y.mring + (no == 3 ? (uint32_t)SPC * cap * 8 : 0u);
     y.part = al_up(y.rec + SPC * 4 * 4, 16);
     y.prm = y.part + 2 * CS * SPC * 4 * part_floats(no);
-    y.slot = al_up(y.prm + (uint32_t)prm_floats(L, C, HN, no) * 4, 16);
+    y.slot = al_up(y.prm + (uint32_t)prm_floats(L, C, HN, no, es) * 4, 16);
     y.misc = y.slot + SPC * 8 + 10 * SPC * 4;
     // misc: extents in | control words | 32 phase counters (profiling) | exit counters
     // (64 ints) | what every peer sent this CTA (one uint4 per peer)
@@ -319,18 +326,30 @@ __device__ __forceinline__ int positions_of(int E, int L, int rows_n) {
     const int span = 1 << L;
     return max(1, min((E + span - 1) / span, rows_n));
 }
+// The positions a step computes: at least the first pass, and whole 128-byte FC1
+// operand panels (FP8 with 64 channels: positions in pairs; rows_n is then even).
+__device__ __forceinline__ int step_positions(int E, int L, int rows_n, int first, int e_round) {
+    const int e = max(positions_of(E, L, rows_n), first);
+    return min(rows_n, (e + e_round - 1) / e_round * e_round);
+}
 
-template <int CS, int NO>
+template <int CS, int NO, bool F8>
 __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_constant__ CArgs a) {
     constexpr int SPC = 128 / CS;   // batch slots per CTA
+    // operand elements: BF16, or FP8 e4m3 (kind::f8f6f4 MMAs, per-channel scales); a
+    // 128-byte swizzled operand row holds EPP of them, one MMA consumes 32 bytes of K
+    constexpr int ES = F8 ? 1 : 2, EPP = 128 / ES;
+    // positions per 128-byte FC1 operand panel (2 for FP8 with 64 channels): a step
+    // computes whole panels, so its extent is rounded up to a multiple of this
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int L = a.L, C = a.C, HN = a.H / CS, S = a.stages, cap = a.cap, PM = pass_positions(L);
+    const int kERound = max(1, EPP / C);
     const uint32_t kStage = (uint32_t)a.stage_bytes;
     constexpr bool SQ = NO == 3;            // store latency and memory write queue (Sec. 3.2)
     constexpr int NL = SQ ? 3 : 2;          // latencies per instruction
     constexpr int PF = NO == 2 ? 2 : NO == 3 ? 4 : 24;   // part_floats(NO)
-    const CLay y = c_layout(CS, L, C, a.H, cap, S, NO, a.stage_bytes);
+    const CLay y = c_layout(CS, L, C, a.H, cap, S, NO, a.stage_bytes, ES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cl_rank();
     const int slot0 = (int)(blockIdx.x / CS) * 128 + (int)rank * SPC;
@@ -371,6 +390,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     float *s_b2 = s_Se + HN;                                 // [24] FC2 bias
     float *s_w2 = s_b2 + 24;                                 // FC2 rows for this CTA's neurons
     float *s_w2f = s_w2, *s_w2e = s_w2 + HN;                 // regression: [2][HN]; hybrid: [HN][24]
+    float *s_ws = s_w2 + (NO == 2 ? 2 * HN : NO == 3 ? 3 * HN : 24 * HN);   // FP8: [L][C] weight scales
+    float *s_os = s_ws + L * C;                                  // FP8: [L][C] requantisation
+    float *s_fws = s_os + L * C;                                 // FP8: [HN] FC1 weight scales
     int64_t *s_o = reinterpret_cast<int64_t *>(sm + y.slot);
     int32_t *s_b = reinterpret_cast<int32_t *>(s_o + SPC), *s_n = s_b + SPC, *s_p = s_n + SPC,
             *s_tick = s_p + SPC, *s_qs = s_tick + SPC, *s_ql = s_qs + SPC, *s_ev = s_ql + SPC,
@@ -425,10 +447,17 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // constants of this CTA's share
-    for (int i = threadIdx.x; i < L * C; i += blockDim.x) s_cb[i] = a.cbias[i / C][i % C];
+    for (int i = threadIdx.x; i < L * C; i += blockDim.x) {
+        s_cb[i] = a.cbias[i / C][i % C];
+        if constexpr (F8) {
+            s_ws[i] = a.cws[i / C][i % C];
+            s_os[i] = a.cos[i / C][i % C];
+        }
+    }
     for (int j = threadIdx.x; j < HN; j += blockDim.x) {
         const int nn = (int)rank * HN + j;
         s_fb[j] = a.fbias[nn];
+        if constexpr (F8) s_fws[j] = a.fws[nn];
         if constexpr (NO == 2 || NO == 3) {
             s_w2f[j] = a.w2[nn];
             s_w2e[j] = a.w2[a.H + nn];
@@ -488,7 +517,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // bytes between the 64-column K panels of layer l's operand: the panels hold just the
     // pass's rows; an MMA tile past them reads neighbouring shared memory into rows it ignores
     auto pstride_of = [&](int l, int P) { return (uint32_t)rows_of(l, P) * 128u; };
-    auto panels_of = [&](int l) { return l == 0 ? 2 : C / 32; };                   // K / 64
+    auto panels_of = [&](int l) { return l == 0 ? 128 / EPP : 2 * C / EPP; };   // K / EPP
     // panels a stage holds: conv panels are C x 64, FC1 panels HN x 64 (BF16)
     const int kConvPer = (int)kStage / (C * 128), kFcPer = min((int)kStage / (HN * 128), 8);
     auto conv_stages = [&](int l) { return (panels_of(l) + kConvPer - 1) / kConvPer; };
@@ -512,7 +541,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 }
                 mbar_expect_tx(bar(s), (uint32_t)n * pb);
                 for (int j = 0; j < n; j++)
-                    tma_load_2d(ring0 + (uint32_t)s * kStage + (uint32_t)j * pb, m, bar(s), x0 + 64 * j, yy);
+                    tma_load_2d(ring0 + (uint32_t)s * kStage + (uint32_t)j * pb, m, bar(s), x0 + EPP * j, yy);
                 adv();
             };
             // conv stage i of a pass (all layers' weights in consumption order), i in [from, to)
@@ -524,7 +553,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     for (int g = 0; g < conv_stages(l) && ok; g++, i++) {
                         if (i < from || i >= to) continue;
                         const int p0 = g * kConvPer, n = min(kConvPer, panels_of(l) - p0);
-                        load(&a.tW[l], p0 * 64, 0, (uint32_t)C * 128u, n);
+                        load(&a.tW[l], p0 * EPP, 0, (uint32_t)C * 128u, n);
                     }
             };
             // Before a step's extent is known only its first S stages are loaded: they are
@@ -537,13 +566,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 int E, AL;
                 read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 if (AL == 0) break;
-                const int eL = max(positions_of(E, L, a.rows_n), min(PM, a.rows_n));   // as the workers
+                const int eL = step_positions(E, L, a.rows_n, min(PM, a.rows_n), kERound);   // as the workers
                 for (int q0 = 0; q0 < eL && ok; q0 += PM) {
                     const int P = min(PM, eL - q0);
                     conv_loads(q0 > 0 ? 0 : pre, n_conv_stages);
-                    const int np = P * C / 64;
+                    const int np = P * C / EPP;
                     for (int p0 = 0; p0 < np && ok; p0 += kFcPer)
-                        load(&a.tF, q0 * C + p0 * 64, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0));
+                        load(&a.tF, q0 * C + p0 * EPP, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0));
                 }
                 if (t + 1 < a.n_steps) conv_loads(0, pre);   // the next step's first stages
             }
@@ -586,7 +615,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             const int T = tiles_of(l, P);
             tc_fence_after();
             fence_async_smem();
-            const uint32_t ID = idesc_rt(C, false);
+            const uint32_t ID = idesc_rt(C, F8);
             const uint32_t pstride = pstride_of(l, P);
             for (int p0 = 0; p0 < panels_of(l) && mma_ok; p0 += kConvPer) {
                 int s;
@@ -600,7 +629,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
 #pragma unroll
                         for (int k = 0; k < 4; k++)
-                            umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
+                            umma<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
                     }
                 }
                 umma_commit(bar(S + s));   // the stage is free once these MMAs have read it
@@ -626,18 +655,24 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         };
         if (wi == 0) send_ext(0);
         // feature rows of positions q0 .. q0 + P - 1 into the first layer's operand
+        constexpr int NCH = F8 ? 4 : 8;   // 16-byte chunks of one 64-feature row
+        auto chunks = [&](uint32_t rec, uint32_t cur, bool ctx, int32_t res, uint32_t e, uint32_t sl, uint4 (&o)[NCH]) {
+            if constexpr (F8) row_chunks_fp8(rec, cur, ctx, res, e, sl, o);
+            else row_chunks_bf16(rec, cur, ctx, res, e, sl, o);
+        };
         auto build_rows = [&](int q0, int P) {
-            // layer-0 A row (pair, slot), K = the pair's two rows
+            // layer-0 A row (pair, slot), K = the pair's two rows: two 128-byte panels
+            // (BF16) or the two halves of one (FP8)
             for (int f = tid; f < P * (1 << L) * SPC; f += kWk) {
                 const int s = f % SPC, rr = f / SPC, r = q0 * (1 << L) + rr;
                 const int m = (rr >> 1) * SPC + s;
-                uint4 ch[8];
+                uint4 ch[NCH];
                 const int ql = s_ql[s];
                 // context row r: the processor queue newest first, then the write queue
                 if (s_al[s] && r <= ql + s_ml[s]) {
                     const uint32_t cur = recb[s * 4 + (s_p[s] & 3)];
                     if (r == 0) {
-                        row_chunks_bf16(cur, cur, false, 0, 0u, 0u, ch);
+                        chunks(cur, cur, false, 0, 0u, 0u, ch);
                     } else {
                         uint64_t ent;
                         if (r <= ql) {
@@ -649,16 +684,16 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             if (idx >= cap) idx -= cap;
                             ent = mring[s * cap + idx];
                         }
-                        row_chunks_bf16(entry_rec(ent), cur, true, entry_res(ent, s_tick[s]), entry_e(ent),
-                                        entry_s(ent), ch);
+                        chunks(entry_rec(ent), cur, true, entry_res(ent, s_tick[s]), entry_e(ent), entry_s(ent), ch);
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 8; j++) ch[j] = make_uint4(0, 0, 0, 0);
+                    for (int j = 0; j < NCH; j++) ch[j] = make_uint4(0, 0, 0, 0);
                 }
-                uint8_t *dst = sm + y.act + (uint32_t)(rr & 1) * pstride_of(0, P) + (uint32_t)m * 128u;
+                const int c0 = F8 ? 4 * (rr & 1) : 0;   // first chunk of this row in its operand row
+                uint8_t *dst = sm + y.act + (uint32_t)(F8 ? 0 : (rr & 1)) * pstride_of(0, P) + (uint32_t)m * 128u;
 #pragma unroll
-                for (int j = 0; j < 8; j++) *reinterpret_cast<uint4 *>(dst + ((j ^ (m & 7)) << 4)) = ch[j];
+                for (int j = 0; j < NCH; j++) *reinterpret_cast<uint4 *>(dst + (((c0 + j) ^ (m & 7)) << 4)) = ch[j];
             }
             fence_async_smem();
         };
@@ -666,6 +701,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // they are built while the extents are exchanged (positions of the pass past the
         // extent are padding rows, computed rather than taken from S[e]: the same result).
         const int P0 = min(PM, a.rows_n);
+        auto arm_rows = [&](int P) {   // thread 0: the peers' rows of pass R, all panels
+            for (int i = 0; i < P * C / EPP; i++) mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * kRowBytes);
+            xs[X_ARMED_R] = (int)R + 1;
+            xs[X_ARMED_NP] = P * C / EPP;
+        };
         for (int64_t t = 0; t < a.n_steps; t++) {
             workers_sync();   // the previous step's head (warp 2) is visible
             build_rows(0, P0);
@@ -677,7 +717,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 }
                 int E, AL;
                 read_ext<CS>(ext_in, (int)(t & 1), E, AL);
-                ctl[0] = max(positions_of(E, L, a.rows_n), P0);
+                ctl[0] = step_positions(E, L, a.rows_n, P0, kERound);
                 ctl[1] = (!ok || AL == 0 || *abort_f) ? 1 : 0;
             }
             workers_sync();
@@ -707,12 +747,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         issue_conv(l, P);
                         // the peers' rows of this pass, expected while the first layer's MMAs run
                         // (every phase of the previous pass completed before its FC1 MMAs)
-                        if (l == 0) {
-                            for (int i = 0; i < P * C / 64; i++)
-                                mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * kRowBytes);
-                            xs[X_ARMED_R] = (int)R + 1;
-                            xs[X_ARMED_NP] = P * C / 64;
-                        }
+                        if (l == 0) arm_rows(P);
                     }
                     __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
                     uint64_t ti1 = prof ? (uint64_t)clock64() : 0;
@@ -755,6 +790,36 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             uint32_t r32[32];
                             tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0 + bi * 32),
                                       r32);
+                            if constexpr (F8) {
+                                // dequantise (weight scale), bias, ReLU, requantise to the next
+                                // layer's input scale, e4m3 with saturation: 16 channels a chunk
+                                const int cc = l * C + c0 + bi * 32;
+                                const float4 *cb = reinterpret_cast<const float4 *>(s_cb + cc);
+                                const float4 *cw = reinterpret_cast<const float4 *>(s_ws + cc);
+                                const float4 *co = reinterpret_cast<const float4 *>(s_os + cc);
+                                uint32_t w[8];
+#pragma unroll
+                                for (int j = 0; j < 8; j++) {
+                                    const float4 b = cb[j], sw = cw[j], so = co[j];
+                                    const float v0 = fmaxf(__uint_as_float(r32[4 * j]) * sw.x + b.x, 0.f) * so.x;
+                                    const float v1 = fmaxf(__uint_as_float(r32[4 * j + 1]) * sw.y + b.y, 0.f) * so.y;
+                                    const float v2 = fmaxf(__uint_as_float(r32[4 * j + 2]) * sw.z + b.z, 0.f) * so.z;
+                                    const float v3 = fmaxf(__uint_as_float(r32[4 * j + 3]) * sw.w + b.w, 0.f) * so.w;
+                                    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
+                                    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
+                                    w[j] = (lo & 0xffffu) | (hi << 16);
+                                }
+#pragma unroll
+                                for (int j = 0; j < 2; j++) {
+                                    const int k = kb + bi * 32 + 16 * j;
+                                    const uint32_t off = base + (uint32_t)(k >> 7) * pstride + (uint32_t)row * 128u +
+                                                         ((uint32_t)(((k >> 4) & 7) ^ (row & 7)) << 4);
+                                    if (valid)
+                                        *reinterpret_cast<uint4 *>(sm + off) =
+                                            make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                                }
+                                continue;
+                            }
                             // bias four channels to a load; ReLU on the rounded pairs (rounding to
                             // nearest keeps the sign, so this equals rounding the ReLU output)
                             const float4 *cb = reinterpret_cast<const float4 *>(s_cb + l * C + c0 + bi * 32);
@@ -796,7 +861,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         // peer: one bulk copy per 64-column panel and peer, counted on the peer's
                         // B_FULL + panel; a peer overwrites its copy only after B_EMPTY, i.e. after
                         // every CTA's FC1 of this pass, which waited for all of its copies
-                        const int np = P * C / 64;
+                        const int np = P * C / EPP;
                         // one warp per peer (warps 1..CS-1: the copies take ~1 us to issue, which
                         // warp 0's MMA thread spends on FC1 instead)
                         if (ok && lane == 0 && wi >= 1 && wi < CS) {
@@ -814,7 +879,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             const uint64_t tw = prof ? (uint64_t)clock64() : 0;
                             if (prof) pacc[16] += tw - tx0;   // own rows to every peer (issue)
                             fence_async_smem();
-                            const uint32_t ID = idesc_rt(HN, false), d = tmem_base + 384u;
+                            const uint32_t ID = idesc_rt(HN, F8), d = tmem_base + 384u;
                             for (int p0 = 0; p0 < np && mma_ok; p0 += kFcPer) {
                                 int s;
                                 if (!take(s, L)) { mma_ok = false; break; }
@@ -834,7 +899,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                                    bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(HN * 128));
 #pragma unroll
                                     for (int k = 0; k < 4; k++)
-                                        umma<false>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
+                                        umma<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
                                                     (q0 | pi | k) != 0 ? 1u : 0u);
                                 }
                                 if (!mma_ok) break;
@@ -883,17 +948,20 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             const float4 *wf4 = reinterpret_cast<const float4 *>(s_w2f + jb);
                             const float4 *we4 = reinterpret_cast<const float4 *>(s_w2e + jb);
                             const float4 *ws4 = reinterpret_cast<const float4 *>(s_w2f + 2 * HN + jb);   // SQ only
+                            const float4 *fw4 = reinterpret_cast<const float4 *>(s_fws + jb);            // FP8 only
 #pragma unroll
                             for (int q = 0; q < 8; q++) {
                                 const float4 fb = fb4[q], se = se4[q], wf = wf4[q], we = we4[q];
-                                float4 wsv = make_float4(0.f, 0.f, 0.f, 0.f);
+                                float4 wsv = make_float4(0.f, 0.f, 0.f, 0.f), fsc = make_float4(1.f, 1.f, 1.f, 1.f);
                                 if constexpr (SQ) wsv = ws4[q];
+                                if constexpr (F8) fsc = fw4[q];
                                 const float bb[4] = {fb.x + se.x, fb.y + se.y, fb.z + se.z, fb.w + se.w};
                                 const float wfa[4] = {wf.x, wf.y, wf.z, wf.w}, wea[4] = {we.x, we.y, we.z, we.w};
-                                const float wsa[4] = {wsv.x, wsv.y, wsv.z, wsv.w};
+                                const float wsa[4] = {wsv.x, wsv.y, wsv.z, wsv.w}, fsa[4] = {fsc.x, fsc.y, fsc.z, fsc.w};
 #pragma unroll
                                 for (int u = 0; u < 4; u++) {
-                                    const float v = fmaxf(__uint_as_float(r32[bi][4 * q + u]) + bb[u], 0.f);
+                                    const float acc = __uint_as_float(r32[bi][4 * q + u]);
+                                    const float v = fmaxf((F8 ? acc * fsa[u] : acc) + bb[u], 0.f);
                                     pf = fmaf(v, wfa[u], pf);
                                     pe = fmaf(v, wea[u], pe);
                                     if constexpr (SQ) ps = fmaf(v, wsa[u], ps);
@@ -910,7 +978,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 #pragma unroll
                             for (int jj = 0; jj < 16; jj++) {
                                 const int j = j0 + bi * 16 + jj;
-                                const float v = fmaxf(__uint_as_float(r32[jj]) + s_fb[j] + s_Se[j], 0.f);
+                                const float acc = __uint_as_float(r32[jj]) * (F8 ? s_fws[j] : 1.f);
+                                const float v = fmaxf(acc + s_fb[j] + s_Se[j], 0.f);
                                 const float4 *wv = reinterpret_cast<const float4 *>(s_w2 + j * 24);
 #pragma unroll
                                 for (int q4 = 0; q4 < 6; q4++) {
@@ -1241,18 +1310,23 @@ static int cluster_size(const simnet_config &k, int B) {
     return n_clusters * 8 <= num_sms() ? 8 : 4;
 }
 
-// Shapes this kernel handles: BF16; 2 or 3 conv layers of 64 or 128 channels;
-// FC1 width 256 or 512; queue capacity below 256; no memory write queue.
+static int elem_bytes(const simnet_ctx *c) { return c->cfg.precision == SIMNET_FP8_E4M3 ? 1 : 2; }
+
+// Shapes this kernel handles: BF16 or FP8 e4m3; 2 or 3 conv layers of 64 or 128
+// channels; FC1 width 256 or 512; queue capacity below 256; the memory write
+// queue only with the regression head.
 bool cluster_eligible(const simnet_ctx *c, std::string &why) {
     const simnet_config &k = c->cfg;
-    if (k.precision != SIMNET_BF16) { why = "not BF16"; return false; }
+    if (k.precision != SIMNET_BF16 && k.precision != SIMNET_FP8_E4M3) { why = "not BF16 or FP8"; return false; }
     if (c->store_queue && c->hybrid) { why = "memory write queue with the hybrid head"; return false; }
     if (c->residual) { why = "residual blocks"; return false; }
     if (k.n_conv < 2 || k.n_conv > 3) { why = "conv depth"; return false; }
     if (k.conv_channels != 64 && k.conv_channels != 128) { why = "conv width"; return false; }
     if (k.fc_hidden != 256 && k.fc_hidden != 512) { why = "FC1 width"; return false; }
     if (c->cap > 255 || c->rows_n < 1) { why = "window"; return false; }
-    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2, c->n_out, kPanelMax);   // the larger layout
+    if ((c->rows_n * k.conv_channels * elem_bytes(c)) % 128 != 0) { why = "FC1 input not whole 128-byte panels"; return false; }
+    const CLay y = c_layout(4, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, 2, c->n_out, kPanelMax,
+                            elem_bytes(c));   // the larger layout
     if (y.total + 1024 > 232448) { why = "shared memory"; return false; }
     return true;
 }
@@ -1261,8 +1335,8 @@ bool cluster_eligible(const simnet_ctx *c, std::string &why) {
 static int cluster_stages_max(const simnet_ctx *c, int CS, int stage_bytes) {
     const simnet_config &k = c->cfg;
     int st = 8;
-    while (st >= 2 && c_layout(CS, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, st, c->n_out, stage_bytes).total +
-                              1024 > 232448)
+    while (st >= 2 && c_layout(CS, k.n_conv, k.conv_channels, k.fc_hidden, c->cap, st, c->n_out, stage_bytes,
+                               elem_bytes(c)).total + 1024 > 232448)
         st--;
     return st >= 2 ? st : 0;
 }
@@ -1287,14 +1361,20 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.H = k.fc_hidden;
     a.cap = c->cap;
     a.rows_n = c->rows_n;
+    const int prec = k.precision, es = elem_bytes(c), epp = 128 / es;   // elements per 128-byte row
+    const bool f8 = prec == SIMNET_FP8_E4M3;
     for (int l = 0; l < a.L; l++) {
-        if (!encode_map_2d(a.tW[l], SIMNET_BF16, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, 64,
+        if (!encode_map_2d(a.tW[l], prec, c->Wl[l], (uint64_t)c->layer[l].K, (uint64_t)a.C, (uint32_t)epp,
                            (uint32_t)a.C, why))
             return false;
         a.cbias[l] = c->bias[l];
+        a.cws[l] = f8 ? c->wscale[l] : nullptr;
+        a.cos[l] = f8 ? c->oscale[l] : nullptr;
     }
-    if (!encode_map_2d(a.tF, SIMNET_BF16, c->Wl[a.L], (uint64_t)c->fc1_in, (uint64_t)a.H, 64, (uint32_t)(a.H / CS), why))
+    if (!encode_map_2d(a.tF, prec, c->Wl[a.L], (uint64_t)c->fc1_in, (uint64_t)a.H, (uint32_t)epp, (uint32_t)(a.H / CS),
+                       why))
         return false;
+    a.fws = f8 ? c->wscale[a.L] : nullptr;
     a.fbias = c->bias[a.L];
     a.w2 = c->w2;
     a.b2 = c->b2;
@@ -1309,7 +1389,7 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     a.spin_ns = c->cfg.spin_limit_ns;
     int stages = 8;
     const int no = c->n_out;
-    auto fits = [&](int st, int sb) { return c_layout(CS, a.L, a.C, a.H, a.cap, st, no, sb).total + 1024 <= 232448; };
+    auto fits = [&](int st, int sb) { return c_layout(CS, a.L, a.C, a.H, a.cap, st, no, sb, es).total + 1024 <= 232448; };
     a.stage_bytes = fits(3, 2 * kPanelMax) ? 2 * kPanelMax : kPanelMax;
     if (tuned && (c->tuned_cluster_stage_bytes == kPanelMax || c->tuned_cluster_stage_bytes == 2 * kPanelMax) &&
         fits(2, c->tuned_cluster_stage_bytes))
@@ -1317,10 +1397,16 @@ bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::
     while (stages > 2 && !fits(stages, a.stage_bytes)) stages--;
     if (tuned && c->tuned_cluster_stages >= 2 && c->tuned_cluster_stages < stages) stages = c->tuned_cluster_stages;
     a.stages = stages;
-    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no, a.stage_bytes).total + 1024;
-    auto kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid> : cluster_kernel<4, kOutHybrid>)
-                : no == 3        ? (CS == 8 ? cluster_kernel<8, 3> : cluster_kernel<4, 3>)
-                                 : (CS == 8 ? cluster_kernel<8, 2> : cluster_kernel<4, 2>);
+    const size_t smem = c_layout(CS, a.L, a.C, a.H, a.cap, stages, no, a.stage_bytes, es).total + 1024;
+    void (*kern)(CArgs);
+    if (f8)
+        kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid, true> : cluster_kernel<4, kOutHybrid, true>)
+               : no == 3        ? (CS == 8 ? cluster_kernel<8, 3, true> : cluster_kernel<4, 3, true>)
+                                : (CS == 8 ? cluster_kernel<8, 2, true> : cluster_kernel<4, 2, true>);
+    else
+        kern = no == kOutHybrid ? (CS == 8 ? cluster_kernel<8, kOutHybrid, false> : cluster_kernel<4, kOutHybrid, false>)
+               : no == 3        ? (CS == 8 ? cluster_kernel<8, 3, false> : cluster_kernel<4, 3, false>)
+                                : (CS == 8 ? cluster_kernel<8, 2, false> : cluster_kernel<4, 2, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { why = cudaGetErrorString(e); return false; }
     const int n_clusters = (B + 127) / 128;

@@ -101,15 +101,15 @@ template <> __device__ __forceinline__ void write_row<__nv_bfloat16>(__nv_bfloat
     for (int i = 0; i < 8; i++) d4[i] = o[i];
 }
 
-template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4m3 *dst, uint32_t rec, uint32_t cur,
-                                                                     bool ctx, int32_t res, uint32_t e, uint32_t s) {
+// An FP8 e4m3 row as its four 16-byte chunks (channels 16j .. 16j+15 in chunk j).
+__device__ __forceinline__ void row_chunks_fp8(uint32_t rec, uint32_t cur, bool ctx, int32_t res, uint32_t e,
+                                               uint32_t s, uint4 (&o)[4]) {
     const uint32_t op = rec & 31u;
     uint32_t w[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) w[i] = (op >> 2) == (uint32_t)i ? (0x38u << (8 * (op & 3u))) : 0u;  // e4m3 1.0
-    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-    d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    o[1] = make_uint4(w[4], w[5], w[6], w[7]);
     float t[32];
     row_tail(rec, cur, ctx, res, e, s, t);
 #pragma unroll
@@ -118,8 +118,17 @@ template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4
         const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(t[4 * i + 2], t[4 * i + 3]), __NV_SATFINITE, __NV_E4M3);
         w[i] = (lo & 0xffffu) | (hi << 16);
     }
-    d4[2] = make_uint4(w[0], w[1], w[2], w[3]);
-    d4[3] = make_uint4(w[4], w[5], w[6], w[7]);
+    o[2] = make_uint4(w[0], w[1], w[2], w[3]);
+    o[3] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+template <> __device__ __forceinline__ void write_row<__nv_fp8_e4m3>(__nv_fp8_e4m3 *dst, uint32_t rec, uint32_t cur,
+                                                                     bool ctx, int32_t res, uint32_t e, uint32_t s) {
+    uint4 o[4];
+    row_chunks_fp8(rec, cur, ctx, res, e, s, o);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; i++) d4[i] = o[i];
 }
 
 template <> __device__ __forceinline__ void write_row<float>(float *dst, uint32_t rec, uint32_t cur, bool ctx,

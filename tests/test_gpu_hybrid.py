@@ -48,7 +48,8 @@ PATHS = {
     "bf16-persistent": ("bf16", {"cluster": False}, "persistent"),
     "bf16-cluster": ("bf16", {}, "cluster"),
     "fp8-layerwise": ("fp8", {"persistent": False}, "layerwise"),
-    "fp8-persistent": ("fp8", {}, "persistent"),
+    "fp8-persistent": ("fp8", {"cluster": False}, "persistent"),
+    "fp8-cluster": ("fp8", {}, "cluster"),
 }
 # precision -> smallest share of decisions whose margin exceeds the GPU's error
 # (the latency bounds are the precision rows of tests/tolerances.py)

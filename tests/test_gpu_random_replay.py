@@ -30,7 +30,8 @@ PATHS = [
     ("bf16", {}, "cluster"),
     ("bf16", {"cluster": False}, "persistent"),
     ("bf16", {"persistent": False}, "layerwise"),
-    ("fp8", {}, "persistent"),
+    ("fp8", {}, "cluster"),
+    ("fp8", {"cluster": False}, "persistent"),
     ("fp8", {"persistent": False}, "layerwise"),
     ("fp32", {}, "layerwise"),
 ]

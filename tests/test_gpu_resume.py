@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 # uneven lengths (compaction runs mid-trace), an empty and a one-instruction sub-trace
 LENGTHS = [0, 1, 37, 300, 41, 512, 90, 5, 260, 128, 64, 7, 1000, 3, 222, 99]
 MODES = [("fp32", "layerwise"), ("bf16", "cluster"), ("bf16", "persistent"), ("bf16", "layerwise"),
-         ("fp8", "persistent")]
+         ("fp8", "cluster"), ("fp8", "persistent")]
 
 
 def sim_for(arch, precision, mode, **kw):

@@ -110,7 +110,8 @@ def test_launch_modes_identical(precision):
         np.testing.assert_array_equal(r["cycles"], runs[0]["cycles"])
 
 
-@pytest.mark.parametrize("precision,kernel", [("bf16", "cluster"), ("bf16", "persistent"), ("fp8", "persistent")])
+@pytest.mark.parametrize("precision,kernel", [("bf16", "cluster"), ("bf16", "persistent"), ("fp8", "cluster"),
+                                              ("fp8", "persistent")])
 @pytest.mark.parametrize("case", ["c1", "ragged", "uneven", "c2arch"])
 def test_persistent_kernel_teacher_forced(precision, kernel, case):
     """The single-launch kernels against the oracle: the cluster kernel (slots

@@ -46,7 +46,8 @@ PATHS = {
     "bf16-default": ("bf16", {}, "cluster"),
     "bf16-persistent": ("bf16", {"cluster": False}, "persistent"),
     "fp8-layerwise": ("fp8", {"persistent": False}, "layerwise"),
-    "fp8-persistent": ("fp8", {}, "persistent"),
+    "fp8-persistent": ("fp8", {"cluster": False}, "persistent"),
+    "fp8-cluster": ("fp8", {}, "cluster"),
 }
 # The bounds are the precision rows of tests/tolerances.py.  With three outputs
 # and the uneven trace's 26,502 x 3 samples the largest BF16 / FP8 errors reach
@@ -135,7 +136,7 @@ def test_bias_only_latencies_exact(path):
 
 
 @pytest.mark.parametrize("precision,mode", [("fp32", "layerwise"), ("bf16", "cluster"), ("bf16", "persistent"),
-                                            ("fp8", "persistent")])
+                                            ("fp8", "cluster"), ("fp8", "persistent")])
 def test_split_and_saved_runs_resume_bit_for_bit(precision, mode):
     lengths = [0, 1, 37, 300, 41, 512, 90, 5, 260, 128, 64, 7, 1000, 3, 222, 99]
     trace = I.small_trace(lengths, seed=11)
