@@ -36,6 +36,9 @@ struct TrainState {
     __nv_bfloat16 *dYb[2] = {};            // conv-output gradients, ping-pong (largest activation)
     TgPlan fwd[kMaxGemm], wgrad[kMaxGemm], dgrad[kMaxGemm];
     int plan_n = -1;                       // windows the plans were built for
+    float *colpart = nullptr;              // per-block column sums of the bias gradients
+    float *wpart = nullptr;                // split partial tiles of the weight gradients
+    size_t wpart_cap = 0;                  // floats
 };
 
 struct simnet_ctx {
@@ -117,9 +120,15 @@ struct simnet_ctx {
     void *pbuf[kMaxGemm] = {};
     int pbuf_B = 0;
 
-    // autotuned tile widths: tuned_bn[l] applies to batches of tuned_B sub-traces
+    // autotuned launch shapes, for batches of tuned_B sub-traces (0 = the built-in
+    // rule): tile widths of the tensor-core GEMMs (per-layer and persistent kernels),
+    // the persistent kernel's pipeline stages, the cluster kernel's cluster size,
+    // weight-stage bytes and stage count
     int tuned_B = -1;
     int tuned_bn[kMaxGemm] = {};
+    int tuned_persist_stages = 0;
+    int tuned_cluster_size = 0, tuned_cluster_stage_bytes = 0, tuned_cluster_stages = 0;
+    int tuned_path = SIMNET_PATH_NONE;   // the path the tuning ran on
 
     // resumable simulation state: the workspace arrays tick/pos/qstart/qlen/
     // evict/ring/active/n_active plus the finished cycle counts `cyc`
@@ -150,6 +159,10 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
 // for the shapes cluster_eligible accepts.
 bool cluster_eligible(const simnet_ctx *c, std::string &why);
 bool launch_cluster(simnet_ctx *c, int B, int64_t n_steps, cudaStream_t s, std::string &why);
+// Autotuner support: whether clusters of CS CTAs can run a batch of B, and the most
+// weight stages of stage_bytes that fit with them (0 if none).
+bool cluster_size_ok(const simnet_ctx *c, int CS, int B);
+int cluster_stage_limit(const simnet_ctx *c, int CS, int stage_bytes);
 }
 
 // Training buffers for n windows (and the optimiser state, once); train.cu.

@@ -670,9 +670,13 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     const size_t fixed = 1024 + 256 + (size_t)a.prm_floats * 4 + staging;
     const size_t budget = 232448 - 1024;   // minus the static shared memory of the compaction
     a.stages = (int)std::min<size_t>(6, (budget - fixed) / a.stage_bytes);
+    // the head phase reuses the stage ring as 10 x 256 queue entries: fewest stages that hold them
+    const size_t head_scratch = (size_t)kWarps * (256 * 8 + 32 * (kNFP * 4 + 16));
+    const int min_stages = std::max<int>(2, (int)((head_scratch + a.stage_bytes - 1) / a.stage_bytes));
+    if (c->tuned_B == B && c->tuned_persist_stages >= 2 && c->tuned_persist_stages < a.stages)
+        a.stages = std::max(c->tuned_persist_stages, min_stages);   // the autotuner's pick
     if (a.stages < 2) { why = "shared memory budget"; return false; }
-    // the head phase reuses the stage ring as 10 x 256 queue entries
-    if ((size_t)a.stages * a.stage_bytes < (size_t)kWarps * (256 * 8 + 32 * (kNFP * 4 + 16))) {
+    if ((size_t)a.stages * a.stage_bytes < head_scratch) {
         why = "ring too small for the head and gather scratch";
         return false;
     }

@@ -158,7 +158,7 @@ extern "C" void simnet_destroy(simnet_ctx *c) {
     }
     {
         void *tb[] = {t.gw2, t.gb2, t.mw2, t.vw2, t.mb2, t.vb2, t.X, t.dA, t.dB, t.z, t.dz, t.loss,
-                      t.Xb, t.dHb, t.dYb[0], t.dYb[1]};
+                      t.Xb, t.dHb, t.dYb[0], t.dYb[1], t.wpart, t.colpart};
         for (void *q : tb)
             if (q) cudaFree(q);
     }
@@ -1111,36 +1111,86 @@ extern "C" simnet_status simnet_autotune(simnet_ctx *c, int32_t n_sub, int32_t s
     cudaMemcpy(d_rec, rec.data(), N * 4, cudaMemcpyHostToDevice);
     cudaMemcpy(d_off, off.data(), (n_sub + 1) * 8, cudaMemcpyHostToDevice);
     simnet_trace tr{d_rec, d_off, n_sub, 0, N};
+    // one untimed call, then the faster of two timed ones
     auto run = [&](float &ms) -> simnet_status {
         simnet_stats sts;
         simnet_status r = simnet_simulate(c, &tr, d_cyc, nullptr, nullptr, nullptr, &sts, s);
-        if (r != SIMNET_OK) return r;
-        r = simnet_simulate(c, &tr, d_cyc, nullptr, nullptr, nullptr, &sts, s);
-        ms = sts.ms_total;
+        ms = 1e30f;
+        for (int k = 0; r == SIMNET_OK && k < 2; k++) {
+            r = simnet_simulate(c, &tr, d_cyc, nullptr, nullptr, nullptr, &sts, s);
+            ms = std::min(ms, sts.ms_total);
+        }
         return r;
     };
-    // start from the heuristic plans
+    // coordinate search over one knob at a time, keeping the fastest whole call
+    float best = 1e30f;
+    auto try_knob = [&](int &knob, std::initializer_list<int> vals, auto ok) -> simnet_status {
+        int keep = knob;
+        for (int v : vals) {
+            if (v == keep || !ok(v)) continue;
+            knob = v;
+            float ms = 0.f;
+            simnet_status r = run(ms);
+            if (r != SIMNET_OK) return r;
+            if (ms < best) { best = ms; keep = v; }
+        }
+        knob = keep;
+        return SIMNET_OK;
+    };
+    // start from the built-in rules
     c->tuned_B = -1;
+    c->tuned_persist_stages = c->tuned_cluster_size = c->tuned_cluster_stage_bytes = c->tuned_cluster_stages = 0;
     simnet_status r = prepare_plans(c, n_sub, c->pdl);
     if (r != SIMNET_OK) { cleanup(); return r; }
     int cur[kMaxGemm];
     for (int l = 0; l < c->n_layers; l++) cur[l] = c->plan[l].BN;
     c->tuned_B = n_sub;
     for (int l = 0; l < c->n_layers; l++) c->tuned_bn[l] = cur[l];
-    float best = 1e30f;
     if ((r = run(best)) != SIMNET_OK) { cleanup(); return r; }
-    for (int l = 0; l < c->n_layers; l++) {
-        for (int bn : {64, 128, 256}) {
-            if (bn == cur[l] || c->layer[l].N % bn) continue;
-            c->tuned_bn[l] = bn;
-            float ms = 0.f;
-            if ((r = run(ms)) != SIMNET_OK) { cleanup(); return r; }
-            if (ms < best) { best = ms; cur[l] = bn; }
+    c->tuned_path = c->path;
+    if (c->path == SIMNET_PATH_CLUSTER) {
+        // cluster size, then weight-stage size, then stage count
+        const int cs0 = cluster_size_ok(c, 8, n_sub) && c->cfg.fc_hidden / 8 >= 64 ? 8 : 4;
+        c->tuned_cluster_size = cs0;
+        if ((r = try_knob(c->tuned_cluster_size, {4, 8}, [&](int v) { return cluster_size_ok(c, v, n_sub); })) !=
+            SIMNET_OK) { cleanup(); return r; }
+        const int CS = c->tuned_cluster_size;
+        c->tuned_cluster_stage_bytes = cluster_stage_limit(c, CS, 32768) >= 3 ? 32768 : 16384;
+        if ((r = try_knob(c->tuned_cluster_stage_bytes, {16384, 32768},
+                          [&](int v) { return cluster_stage_limit(c, CS, v) >= 2; })) != SIMNET_OK) { cleanup(); return r; }
+        const int smax = cluster_stage_limit(c, CS, c->tuned_cluster_stage_bytes);
+        c->tuned_cluster_stages = smax;
+        if ((r = try_knob(c->tuned_cluster_stages, {2, 3, 4, 5, 6, 7, 8}, [&](int v) { return v <= smax; })) !=
+            SIMNET_OK) { cleanup(); return r; }
+    } else {
+        // tile width of every tensor-core GEMM (the persistent kernel's phases and the
+        // per-layer kernels take the same plans), then the persistent kernel's stages
+        for (int l = 0; l < c->n_layers; l++) {
+            const int N = c->layer[l].N;
+            if ((r = try_knob(c->tuned_bn[l], {64, 128, 256}, [&](int v) { return N % v == 0; })) != SIMNET_OK) {
+                cleanup();
+                return r;
+            }
+            cur[l] = c->tuned_bn[l];
         }
-        c->tuned_bn[l] = cur[l];
+        if (c->path == SIMNET_PATH_PERSISTENT) {
+            c->tuned_persist_stages = 6;
+            if ((r = try_knob(c->tuned_persist_stages, {2, 3, 4, 5}, [](int) { return true; })) != SIMNET_OK) {
+                cleanup();
+                return r;
+            }
+        }
     }
     cleanup();
     if (bn_out)
-        for (int l = 0; l < c->n_layers; l++) bn_out[l] = cur[l];
+        for (int l = 0; l < c->n_layers; l++) bn_out[l] = c->tuned_bn[l];
+    return SIMNET_OK;
+}
+
+extern "C" simnet_status simnet_autotune_plan(const simnet_ctx *c, int32_t *out, int32_t n) {
+    if (!c || !out || n < 6) return SIMNET_EINVAL;
+    const int32_t head[6] = {c->tuned_B, c->tuned_path, c->tuned_cluster_size, c->tuned_cluster_stage_bytes,
+                             c->tuned_cluster_stages, c->tuned_persist_stages};
+    for (int i = 0; i < n; i++) out[i] = i < 6 ? head[i] : (i - 6 < c->n_layers ? c->tuned_bn[i - 6] : 0);
     return SIMNET_OK;
 }

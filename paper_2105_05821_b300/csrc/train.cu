@@ -16,6 +16,7 @@
 #include <cstring>
 
 #include "ctx.cuh"
+#include "sim_device.cuh"
 
 namespace simnet {
 namespace {
@@ -57,6 +58,31 @@ __global__ void window_gather_kernel(const uint32_t *__restrict__ rec, const int
     if (x50)
         for (int j = 0; j < 4; j++)
             if (chunk * 4 + j < kNF) x50[rowid * kNF + chunk * 4 + j] = v[j];
+}
+
+// The same rows for the training step, one thread per row: the row's 64 channels
+// built whole by the simulator's row writer (the values `feature` gives).
+template <typename T>
+__global__ void window_rows_kernel(const uint32_t *__restrict__ rec, const int64_t *__restrict__ fetch,
+                                   const uint8_t *__restrict__ e_label, const int64_t *__restrict__ ctx_begin,
+                                   const int64_t *__restrict__ idx, int n, int W, T *__restrict__ X) {
+    const int64_t rowid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rowid >= (int64_t)n * W) return;
+    const int r = (int)(rowid % W);
+    const int64_t i = idx[rowid / W];
+    const uint32_t cur = rec[i];
+    T *dst = X + rowid * kNFP;
+    if (r == 0) {
+        write_row<T>(dst, cur, cur, false, 0, 0u, 0u);
+    } else if (i - r >= ctx_begin[i]) {
+        const int64_t jj = i - r;
+        const int64_t res = (i > 0 ? fetch[i - 1] : 0) - fetch[jj];
+        write_row<T>(dst, rec[jj], cur, true, (int32_t)(res > 4095 ? 4095 : res), e_label[jj], 0u);
+    } else {
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+        for (int k = 0; k < kNFP * (int)sizeof(T) / 16; k++) d4[k] = make_uint4(0, 0, 0, 0);
+    }
 }
 
 // ------------------------------------------------------------------ strided GEMM
@@ -396,18 +422,44 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const float *__restrict__
     }
 }
 
-// out[c] += sum over rows of d[r][c] (BF16 input, C even and at most 512): a thread
-// takes one column pair, blockDim / (C / 2) rows at a time.
-__global__ void colsum_bf16_kernel(const __nv_bfloat16 *__restrict__ d, int64_t rows, int C, float *__restrict__ out) {
+// Column sums out[c] = sum over rows of d[r][c] in two passes with no atomics:
+// block g sums its share of the rows into part[g][c] (a thread takes one column
+// pair, 256 / (C / 2) rows at a time, then the block adds its row lanes), and
+// one thread per column adds the blocks' sums.  C even, at most 512.
+constexpr int kColBlocks = 2 * 148;
+template <typename T>
+__global__ void __launch_bounds__(256) colsum_part_kernel(const T *__restrict__ d, int64_t rows, int C,
+                                                          float *__restrict__ part) {
+    __shared__ float sh[512];
     const int CP = C / 2, cp = threadIdx.x % CP, rl = threadIdx.x / CP, rpb = blockDim.x / CP;
-    float a0 = 0.f, a1 = 0.f;
-    for (int64_t r = (int64_t)blockIdx.x * rpb + rl; r < rows; r += (int64_t)gridDim.x * rpb) {
-        const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(d + r * C)[cp];
-        a0 += __bfloat162float(v.x);
-        a1 += __bfloat162float(v.y);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) sh[c] = 0.f;
+    __syncthreads();
+    if (rl < rpb) {
+        float a0 = 0.f, a1 = 0.f;
+        for (int64_t r = (int64_t)blockIdx.x * rpb + rl; r < rows; r += (int64_t)gridDim.x * rpb) {
+            if constexpr (sizeof(T) == 4) {
+                const float2 v = reinterpret_cast<const float2 *>(d + r * C)[cp];
+                a0 += v.x;
+                a1 += v.y;
+            } else {
+                const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(d + r * C)[cp];
+                a0 += __bfloat162float(v.x);
+                a1 += __bfloat162float(v.y);
+            }
+        }
+        atomicAdd(&sh[2 * cp], a0);   // shared-memory sums of the block's row lanes
+        atomicAdd(&sh[2 * cp + 1], a1);
     }
-    atomicAdd(&out[2 * cp], a0);
-    atomicAdd(&out[2 * cp + 1], a1);
+    __syncthreads();
+    for (int c = threadIdx.x; c < C; c += blockDim.x) part[(size_t)blockIdx.x * C + c] = sh[c];
+}
+
+__global__ void colsum_final_kernel(const float *__restrict__ part, int G, int C, float *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int g = 0; g < G; g++) s += part[(size_t)g * C + c];
+    out[c] = s;
 }
 
 __global__ void loss_to_float_kernel(const double *__restrict__ l, float *__restrict__ out) { *out = (float)*l; }
@@ -540,6 +592,7 @@ simnet_status ensure_train(simnet_ctx *c, int n) {
         CK(cudaMemset(t.mb2, 0, b2n));
         CK(cudaMemset(t.vb2, 0, b2n));
         CK(cudaMalloc(&t.loss, sizeof(double)));
+        CK(cudaMalloc(&t.colpart, (size_t)kColBlocks * 512 * sizeof(float)));
         t.ready = true;
     }
     if (n <= t.n_cap) return SIMNET_OK;
@@ -613,6 +666,18 @@ static simnet_status tc_plans(simnet_ctx *c, int n) {
         if (!ok) return fail(c, SIMNET_EUNSUPPORTED, "tensor-core training, layer %d: %s", l, why.c_str());
     }
     (void)H;
+    // split scratch of the weight gradients and of FC1's forward (one GEMM at a time: one buffer)
+    size_t need = 0;
+    for (int l = 0; l <= L; l++) need = std::max({need, tg_part_floats(t.wgrad[l]), tg_part_floats(t.fwd[l])});
+    if (need > t.wpart_cap) {
+        CK(cudaDeviceSynchronize());
+        if (t.wpart) cudaFree(t.wpart);
+        t.wpart = nullptr;
+        t.wpart_cap = 0;
+        CK(cudaMalloc(&t.wpart, need * sizeof(float)));
+        t.wpart_cap = need;
+    }
+    for (int l = 0; l <= L; l++) t.wgrad[l].part = t.fwd[l].part = t.wpart;
     t.plan_n = n;
     return SIMNET_OK;
 }
@@ -649,11 +714,13 @@ static void launch_head_bwd(const float *Hh, const float *dz, const float *w2, i
     }
 }
 
-static void launch_colsum_bf16(const __nv_bfloat16 *d, int64_t rows, int C, float *out, cudaStream_t s) {
+// out[c] = column sums of d [rows][C] (overwritten); part: kColBlocks * C floats.
+template <typename T>
+static void launch_colsum(const T *d, int64_t rows, int C, float *part, float *out, cudaStream_t s) {
     const int rpb = 256 / (C / 2);
-    const int64_t want = (rows + rpb - 1) / rpb;
-    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 4 * 148));
-    colsum_bf16_kernel<<<g, 256, 0, s>>>(d, rows, C, out);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpb - 1) / rpb, kColBlocks));
+    colsum_part_kernel<T><<<g, 256, 0, s>>>(d, rows, C, part);
+    colsum_final_kernel<<<(C + 127) / 128, 128, 0, s>>>(part, g, C, out);
 }
 
 // Backward from t.dz through the saved activations; gradients (GEMM layout) in t.g*.
@@ -661,19 +728,19 @@ static void train_backward_enqueue(simnet_ctx *c, cudaStream_t s) {
     TrainState &t = c->tr;
     const int n = t.n_last, H = c->cfg.fc_hidden, L = c->n_layers, NO = c->n_out;
     for (int l = 0; l < L; l++) {
-        cudaMemsetAsync(t.gW[l], 0, (size_t)c->layer[l].N * c->layer[l].K * 4, s);
+        if (!train_on_tc(c)) cudaMemsetAsync(t.gW[l], 0, (size_t)c->layer[l].N * c->layer[l].K * 4, s);
         cudaMemsetAsync(t.gb[l], 0, (size_t)c->layer[l].N * 4, s);
     }
     cudaMemsetAsync(t.gw2, 0, (size_t)NO * H * 4, s);
     cudaMemsetAsync(t.gb2, 0, (size_t)NO * 4, s);
     const float *Hh = t.Y[L - 1];
-    if (train_on_tc(c)) {
+    if (train_on_tc(c)) {   // (the weight-gradient GEMMs overwrite gW)
         // FC2 and FC1's ReLU on the CUDA cores (2 or 22 outputs), then per layer, last
         // to first: dW = dY^T A and dA = (dY W) * [A > 0] on the tensor cores
         launch_head_bwd(Hh, t.dz, c->w2, n, H, NO, t.dHb, t.gw2, t.gb2, t.gb[L - 1], s);
         for (int l = L - 1; l >= 0; l--) {
             launch_tg(t.wgrad[l], c->cfg.spin_limit_ns, c->status, s);
-            if (l < L - 1) launch_colsum_bf16(t.dYb[l & 1], layer_rows(c, l, n), c->layer[l].N, t.gb[l], s);
+            if (l < L - 1) launch_colsum(t.dYb[l & 1], layer_rows(c, l, n), c->layer[l].N, t.colpart, t.gb[l], s);
             if (l > 0) launch_tg(t.dgrad[l], c->cfg.spin_limit_ns, c->status, s);
         }
         return;
@@ -690,7 +757,7 @@ static void train_backward_enqueue(simnet_ctx *c, cudaStream_t s) {
         const int R = (int)layer_rows(c, l, n);
         const float *A = l == 0 ? t.X : t.Y[l - 1];
         gemm(false, d, 1, g.N, A, g.K, 1, t.gW[l], g.K, g.N, g.K, R, nullptr, 0, true, s);
-        colsum_kernel<<<dim3(std::min(R, 512), (g.N + 127) / 128), 128, 0, s>>>(d, R, g.N, t.gb[l]);
+        launch_colsum(d, R, g.N, t.colpart, t.gb[l], s);
         if (l > 0) {
             gemm(false, d, g.N, 1, c->W32[l], g.K, 1, d2, g.K, R, g.K, g.N, nullptr, 0, false, s);
             const int64_t e = layer_rows(c, l - 1, n) * c->layer[l - 1].N;
@@ -859,11 +926,11 @@ extern "C" simnet_status simnet_train_step(simnet_ctx *c, const simnet_windows *
     TrainState &t = c->tr;
     cudaStream_t s = (cudaStream_t)stream;
     if (train_on_tc(c))
-        window_gather_kernel<__nv_bfloat16><<<blocks((int64_t)batch * c->cfg.window * 16), 256, 0, s>>>(
-            w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.Xb, nullptr);
+        window_rows_kernel<__nv_bfloat16><<<blocks((int64_t)batch * c->cfg.window, 128), 128, 0, s>>>(
+            w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.Xb);
     else
-        window_gather_kernel<float><<<blocks((int64_t)batch * c->cfg.window * 16), 256, 0, s>>>(
-            w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X, nullptr);
+        window_rows_kernel<float><<<blocks((int64_t)batch * c->cfg.window, 128), 128, 0, s>>>(
+            w->records, w->fetch, w->e_label, w->ctx_begin, idx, batch, c->cfg.window, t.X);
     st = train_forward_enqueue(c, batch, s);
     if (st != SIMNET_OK) return st;
     CK(cudaMemsetAsync(t.loss, 0, sizeof(double), s));

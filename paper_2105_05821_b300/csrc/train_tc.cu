@@ -40,6 +40,7 @@ struct TgArgs {
     const float *bias;
     const __nv_bfloat16 *mask;
     void *out;
+    float *part;   // split partial tiles [splits][N][ldo], or null
     int M, N, R, ldo;
     int n_tiles_n, m_tiles, splits, kb_per_split;
     int64_t spin_ns;
@@ -79,9 +80,11 @@ struct TgLayout {
 
 // Work item t: (reduction split, row tile, column tile) -> first row, column
 // tile index and the range of 64-wide reduction blocks.
-__device__ __forceinline__ void tg_decode(const TgArgs &a, int t, int &m0, int &nt, int &kb0, int &kb1) {
+__device__ __forceinline__ void tg_decode(const TgArgs &a, int t, int &m0, int &nt, int &kb0, int &kb1,
+                                          int *split_out = nullptr) {
     const int per_split = a.m_tiles * a.n_tiles_n;
     const int split = t / per_split, rem = t % per_split;
+    if (split_out) *split_out = split;
     m0 = (rem / a.n_tiles_n) * BM;
     nt = rem % a.n_tiles_n;
     kb0 = split * a.kb_per_split;
@@ -217,21 +220,53 @@ __global__ void __launch_bounds__(320, 1)
         const int q = warp & 3, half = (warp - 2) >> 2;
         int tc = 0;
         for (int t = blockIdx.x; t < items; t += gridDim.x, tc++) {
-            int m0, nt, kb0, kb1;
-            tg_decode(a, t, m0, nt, kb0, kb1);
+            int m0, nt, kb0, kb1, split;
+            tg_decode(a, t, m0, nt, kb0, kb1, &split);
             const int n0 = nt * BN;
             const int acc = tc & 1;
             const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
-            if (!mbar_wait(tfull(acc), aph, lim, abort_flag, a.status)) break;
-            tc_fence_after();
             const int m = m0 + q * 32 + lane;
             const bool valid = m < a.M;
+            // DGRAD: this row's mask one chunk ahead; the first chunk's is loaded while
+            // the tile's MMAs still run
+            uint4 mk_next[4];
+            if constexpr (EPI == TG_DGRAD) {
+                if (valid) {
+                    const uint4 *mk = reinterpret_cast<const uint4 *>(a.mask + (size_t)m * a.N + n0 + half * (BN / 2));
+#pragma unroll
+                    for (int j = 0; j < 4; j++) mk_next[j] = mk[j];
+                }
+            }
+            if (!mbar_wait(tfull(acc), aph, lim, abort_flag, a.status)) break;
+            tc_fence_after();
 #pragma unroll 1
             for (int ch = 0; ch < BN / 64; ch++) {
                 const int c = half * (BN / 2) + ch * 32;   // tile column of this chunk
+                uint4 mkv[4];
+                if constexpr (EPI == TG_DGRAD) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) mkv[j] = mk_next[j];
+                    if (valid && ch + 1 < BN / 64) {
+                        const uint4 *mk = reinterpret_cast<const uint4 *>(a.mask + (size_t)m * a.N + n0 + c + 32);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) mk_next[j] = mk[j];
+                    }
+                }
                 uint32_t r[32];
                 tmem_ld32(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + c), r);
                 const int n = n0 + c;
+                if constexpr (EPI == TG_FWD_F32) {
+                    if (a.part) {   // a split reduction: this split's raw sums (bias, ReLU after the sum)
+                        if (valid) {
+                            float4 *o = reinterpret_cast<float4 *>(a.part + ((size_t)split * a.M + m) * a.N + n);
+#pragma unroll
+                            for (int j = 0; j < 8; j++)
+                                o[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                                   __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                        }
+                        continue;
+                    }
+                }
                 if constexpr (EPI == TG_FWD_BF16 || EPI == TG_FWD_F32) {
                     float v[32];
                     const float4 *b4 = reinterpret_cast<const float4 *>(a.bias + n);
@@ -265,11 +300,10 @@ __global__ void __launch_bounds__(320, 1)
                     }
                 } else if constexpr (EPI == TG_DGRAD) {
                     if (valid) {
-                        const uint4 *mk = reinterpret_cast<const uint4 *>(a.mask + (size_t)m * a.N + n);
                         uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(a.out) + (size_t)m * a.N + n);
 #pragma unroll
                         for (int j = 0; j < 4; j++) {
-                            const uint4 mv = mk[j];
+                            const uint4 mv = mkv[j];
                             const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
                             uint32_t w[4];
 #pragma unroll
@@ -283,11 +317,12 @@ __global__ void __launch_bounds__(320, 1)
                             o[j] = make_uint4(w[0], w[1], w[2], w[3]);
                         }
                     }
-                } else {   // TG_WGRAD: out[n][m] += C[m][n]; a warp's 32 rows are consecutive in memory
+                } else {   // TG_WGRAD: out[n][m] = C[m][n]; a warp's 32 rows are consecutive in memory
                     if (valid) {
-                        float *o = reinterpret_cast<float *>(a.out) + (size_t)n * a.ldo + m;
+                        float *dst = a.part ? a.part + (size_t)split * a.N * a.ldo : reinterpret_cast<float *>(a.out);
+                        float *o = dst + (size_t)n * a.ldo + m;
 #pragma unroll
-                        for (int j = 0; j < 32; j++) atomicAdd(o + (size_t)j * a.ldo, __uint_as_float(r[j]));
+                        for (int j = 0; j < 32; j++) o[(size_t)j * a.ldo] = __uint_as_float(r[j]);
                     }
                 }
             }
@@ -303,6 +338,30 @@ __global__ void __launch_bounds__(320, 1)
 }
 
 template <int BN> constexpr int tg_stages() { return BN == 256 ? 4 : BN == 128 ? 6 : 8; }
+
+// out[i] = sum over s of part[s][i], then (forward) + bias[i % N] and ReLU: the
+// splits of a reduction, summed in a fixed order.  A block takes 32 consecutive
+// elements; its 8 warps sum every 8th split each, then one warp adds the 8.
+__global__ void __launch_bounds__(256) tg_reduce_kernel(const float *__restrict__ part, int splits, int64_t count,
+                                                        float *__restrict__ out, const float *__restrict__ bias, int N,
+                                                        int relu) {
+    __shared__ float sh[8][33];
+    const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + e;
+    float s = 0.f;
+    if (i < count)
+        for (int k = g; k < splits; k += 8) s += part[(size_t)k * count + i];
+    sh[g][e] = s;
+    __syncthreads();
+    if (g == 0 && i < count) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; q++) t += sh[q][e];
+        if (bias) t += bias[i % N];
+        if (relu) t = fmaxf(t, 0.f);
+        out[i] = t;
+    }
+}
 
 template <int BN, bool AMN, bool BMN, int EPI>
 void tg_launch_one(const TgPlan &p, const TgArgs &a, cudaStream_t s) {
@@ -367,7 +426,7 @@ bool make_tg_plan(TgPlan &p, int epi, const void *A, bool a_mn, const void *B, b
     const int KB = (R + 63) / 64, base = p.m_tiles * p.n_tiles_n, sms = num_sms();
     p.splits = 1;
     p.kb_per_split = KB;
-    if (epi == TG_WGRAD && base < sms) {   // split the reduction until the tiles fill the GPU
+    if ((epi == TG_WGRAD || epi == TG_FWD_F32) && base < sms) {   // split the reduction until the tiles fill the GPU
         int splits = std::min(KB, (sms + base - 1) / base);
         p.kb_per_split = (KB + splits - 1) / splits;
         p.splits = (KB + p.kb_per_split - 1) / p.kb_per_split;
@@ -384,6 +443,7 @@ void launch_tg(const TgPlan &p, int64_t spin_ns, int32_t *status, cudaStream_t s
     a.bias = p.bias;
     a.mask = reinterpret_cast<const __nv_bfloat16 *>(p.mask);
     a.out = p.out;
+    a.part = tg_part_floats(p) ? p.part : nullptr;
     a.M = p.M;
     a.N = p.N;
     a.R = p.R;
@@ -399,6 +459,13 @@ void launch_tg(const TgPlan &p, int64_t spin_ns, int32_t *status, cudaStream_t s
         case TG_FWD_F32: tg_launch_epi<TG_FWD_F32>(p, a, s); break;
         case TG_DGRAD: tg_launch_epi<TG_DGRAD>(p, a, s); break;
         default: tg_launch_epi<TG_WGRAD>(p, a, s); break;
+    }
+    if (a.part) {
+        const bool fwd = p.epi == TG_FWD_F32;
+        const int64_t count = fwd ? (int64_t)p.M * p.N : (int64_t)p.N * p.ldo;
+        tg_reduce_kernel<<<(unsigned)((count + 31) / 32), 256, 0, s>>>(a.part, p.splits, count,
+                                                                       reinterpret_cast<float *>(p.out),
+                                                                       fwd ? p.bias : nullptr, p.N, fwd ? 1 : 0);
     }
 }
 

@@ -41,7 +41,7 @@ EXPORTS = ["simnet_abi_version", "simnet_init", "simnet_destroy", "simnet_last_e
            "simnet_gather_windows", "simnet_train_forward", "simnet_train_backward", "simnet_train_step",
            "simnet_set_weights_device", "simnet_get_weights", "simnet_phase_detail", "simnet_autotune",
            "simnet_simulate_steps", "simnet_state_save", "simnet_state_load", "simnet_kernel_path",
-           "simnet_path_choice", "simnet_train_loss"]
+           "simnet_path_choice", "simnet_train_loss", "simnet_autotune_plan"]
 STATE_KINDS = {"sim": 0, "train": 1}
 
 
@@ -119,6 +119,8 @@ def lib() -> C.CDLL:
         L.simnet_set_weights_device.argtypes = [P, P, P]
         L.simnet_get_weights.restype = C.c_int
         L.simnet_get_weights.argtypes = [P, P]
+        L.simnet_autotune_plan.restype = C.c_int
+        L.simnet_autotune_plan.argtypes = [P, P, C.c_int32]
         L.simnet_autotune.restype = C.c_int
         L.simnet_autotune.argtypes = [P, C.c_int32, C.c_int32, P, P]
         L.simnet_phase_detail.restype = C.c_int
@@ -282,6 +284,14 @@ class Simnet:
         out = (C.c_int32 * MAX_GEMMS)()    # one tile width per GEMM of the CNN
         self._check(lib().simnet_autotune(self._h, n_subtraces, steps, out, _stream(stream)))
         return list(out)
+
+    def autotune_plan(self) -> dict:
+        """The autotuner's last choice: batch size, path and launch shapes."""
+        out = (C.c_int32 * (6 + MAX_GEMMS))()
+        self._check(lib().simnet_autotune_plan(self._h, out, 6 + MAX_GEMMS))
+        v = list(out)
+        return {"batch": v[0], "path": PATHS.get(v[1], "none"), "cluster_size": v[2], "cluster_stage_bytes": v[3],
+                "cluster_stages": v[4], "persist_stages": v[5], "tile_widths": [x for x in v[6:] if x]}
 
     def kernel_times(self):
         """(ms, launches) per kernel kind of the last simulate with kernel_events=True."""
