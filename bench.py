@@ -38,10 +38,11 @@ TRAFFIC = {
     # persist_kernel, c2 BF16: 1.53 MB of DRAM traffic over 20 steps in the capture of
     # profiles/persist_kernel_c2_bf16.md, scaled by steps to the 1,000-step launch
     ("c2", "bf16", "persist_kernel"): 1.526e6 * 1000 / 20,
-    # cluster_kernel, c2 BF16: one 1,000-step call is two launches (the 128-step probe and the
-    # rest), 2.14 + 5.54 MB read and nothing written, measured on the full workload
-    # (profiles/cluster_kernel_c2_bf16_traffic.md); the working set stays on chip and in L2
-    ("c2", "bf16", "cluster_kernel"): 2.138e6 + 5.543e6,
+    # cluster_kernel, c2: one 1,000-step call is two launches (the 128-step probe and the
+    # rest), measured on the full workload; nothing is written, the working set stays on
+    # chip and in L2 (profiles/cluster_kernel_c2_bf16_traffic.md, ..._fp8_traffic.md)
+    ("c2", "bf16", "cluster_kernel"): 2.191872e6 + 5.452544e6,
+    ("c2", "fp8", "cluster_kernel"): 1.805824e6 + 5.395456e6,
 }
 
 
@@ -458,6 +459,8 @@ def run_ours(args):
                              autotune=not args.no_autotune, persistent=not args.layerwise)
         s8.close()
         r8["note"] = "FP8 e4m3 tcgen05 path, same workload and timing"
+        k8 = PATH_KERNEL.get(r8["kernel_mode"], r8["kernel_mode"])
+        r8["roofline"] = whole_call_roofline(w, "fp8", N, r8["ms_per_step"], k8, TRAFFIC.get((w.name, "fp8", k8)))
         out["fp8_form"] = r8
         forms["fp8_form"] = c8
     if train_info:
