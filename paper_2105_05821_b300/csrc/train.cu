@@ -435,31 +435,61 @@ __global__ void __launch_bounds__(256) colsum_part_kernel(const T *__restrict__ 
     for (int c = threadIdx.x; c < C; c += blockDim.x) sh[c] = 0.f;
     __syncthreads();
     if (rl < rpb) {
-        float a0 = 0.f, a1 = 0.f;
-        for (int64_t r = (int64_t)blockIdx.x * rpb + rl; r < rows; r += (int64_t)gridDim.x * rpb) {
+        auto ld = [&](int64_t r) -> float2 {
             if constexpr (sizeof(T) == 4) {
-                const float2 v = reinterpret_cast<const float2 *>(d + r * C)[cp];
-                a0 += v.x;
-                a1 += v.y;
+                return reinterpret_cast<const float2 *>(d + r * C)[cp];
             } else {
                 const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(d + r * C)[cp];
-                a0 += __bfloat162float(v.x);
-                a1 += __bfloat162float(v.y);
+                return make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
             }
+        };
+        float2 a = make_float2(0.f, 0.f), b = a;   // two rows in flight per iteration
+        const int64_t step = (int64_t)gridDim.x * rpb;
+        int64_t r = (int64_t)blockIdx.x * rpb + rl;
+        for (; r + step < rows; r += 2 * step) {
+            const float2 u = ld(r), v = ld(r + step);
+            a.x += u.x;
+            a.y += u.y;
+            b.x += v.x;
+            b.y += v.y;
         }
-        atomicAdd(&sh[2 * cp], a0);   // shared-memory sums of the block's row lanes
-        atomicAdd(&sh[2 * cp + 1], a1);
+        if (r < rows) {
+            const float2 u = ld(r);
+            a.x += u.x;
+            a.y += u.y;
+        }
+        atomicAdd(&sh[2 * cp], a.x + b.x);   // shared-memory sums of the block's row lanes
+        atomicAdd(&sh[2 * cp + 1], a.y + b.y);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += blockDim.x) part[(size_t)blockIdx.x * C + c] = sh[c];
 }
 
-__global__ void colsum_final_kernel(const float *__restrict__ part, int G, int C, float *__restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    float s = 0.f;
-    for (int g = 0; g < G; g++) s += part[(size_t)g * C + c];
-    out[c] = s;
+// A block takes 32 columns; its 8 warps sum every 8th block's sums (four loads in
+// flight each), then one warp adds the 8.
+__global__ void __launch_bounds__(256) colsum_final_kernel(const float *__restrict__ part, int G, int C,
+                                                           float *__restrict__ out) {
+    __shared__ float sh[8][33];
+    const int e = threadIdx.x & 31, w = threadIdx.x >> 5, c = blockIdx.x * 32 + e;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    if (c < C) {
+        int g = w;
+        for (; g + 24 < G; g += 32) {
+            s0 += part[(size_t)g * C + c];
+            s1 += part[(size_t)(g + 8) * C + c];
+            s2 += part[(size_t)(g + 16) * C + c];
+            s3 += part[(size_t)(g + 24) * C + c];
+        }
+        for (; g < G; g += 8) s0 += part[(size_t)g * C + c];
+    }
+    sh[w][e] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (w == 0 && c < C) {
+        float t = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; q++) t += sh[q][e];
+        out[c] = t;
+    }
 }
 
 __global__ void loss_to_float_kernel(const double *__restrict__ l, float *__restrict__ out) { *out = (float)*l; }
@@ -720,7 +750,7 @@ static void launch_colsum(const T *d, int64_t rows, int C, float *part, float *o
     const int rpb = 256 / (C / 2);
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpb - 1) / rpb, kColBlocks));
     colsum_part_kernel<T><<<g, 256, 0, s>>>(d, rows, C, part);
-    colsum_final_kernel<<<(C + 127) / 128, 128, 0, s>>>(part, g, C, out);
+    colsum_final_kernel<<<(C + 31) / 32, 256, 0, s>>>(part, g, C, out);
 }
 
 // Backward from t.dz through the saved activations; gradients (GEMM layout) in t.g*.

@@ -349,8 +349,18 @@ __global__ void __launch_bounds__(256) tg_reduce_kernel(const float *__restrict_
     const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * 32 + e;
     float s = 0.f;
-    if (i < count)
-        for (int k = g; k < splits; k += 8) s += part[(size_t)k * count + i];
+    if (i < count) {   // four independent loads in flight per thread
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int k = g;
+        for (; k + 24 < splits; k += 32) {
+            s0 += part[(size_t)k * count + i];
+            s1 += part[(size_t)(k + 8) * count + i];
+            s2 += part[(size_t)(k + 16) * count + i];
+            s3 += part[(size_t)(k + 24) * count + i];
+        }
+        for (; k < splits; k += 8) s0 += part[(size_t)k * count + i];
+        s = (s0 + s1) + (s2 + s3);
+    }
     sh[g][e] = s;
     __syncthreads();
     if (g == 0 && i < count) {
