@@ -589,10 +589,19 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             if (++cs == S) { cs = 0; cph ^= 1u; }
         };
         int64_t R = 0;             // passes exchanged
-        bool mma_ok = true;        // thread 0: false after a bounded wait gave up
-        uint32_t fph = 0;          // thread 0: phase parity of each B_FULL + i
+        // The MMAs are issued by warp 2 as a whole (converged, one elected lane issues; the
+        // operands are then warp-uniform values, which issue faster than from a lone thread).
+        bool mma_ok = true;        // warp 2: false after a bounded wait gave up
+        uint32_t fph = 0;          // warp 2: phase parity of each B_FULL + i
         const StepArgs &As = *A;
         const int RW = As.retire_width, strict = As.strict;
+        // the call's pointers, read once (the head's stores could alias the argument block,
+        // so the compiler would otherwise reload them from device memory every step)
+        const uint8_t *const replay = As.replay;
+        float *const pre_log = As.pre_log;
+        uint8_t *const lat_log = As.lat_log;
+        int64_t *const cycles_out = As.cycles_out;
+        const uint32_t *const records = As.records;
         const bool prof = a.prof && blockIdx.x == 0 && tid == 0;
         uint64_t tp = prof ? (uint64_t)clock64() : 0;
         auto mark = [&](int k) {
@@ -602,15 +611,16 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 tp = tn;
             }
         };
-        auto take = [&](int &s, int who) -> bool {   // thread 0: next weight panel (who: layer, L = FC1)
+        auto take = [&](int &s, int who) -> bool {   // warp 2: next weight panel (who: layer, L = FC1)
             s = cs;
             const uint64_t tw = prof ? (uint64_t)clock64() : 0;
-            if (!note(mbar_wait(bar(s), cph, lim, abort_f, a.status), 3, -1, it)) return false;
+            const bool ok = note(mbar_wait(bar(s), cph, lim, abort_f, a.status), 3, -1, it);
+            if (!__all_sync(0xffffffffu, ok)) return false;
             if (prof) pacc[26 + who] += (uint64_t)clock64() - tw;
             tc_fence_after();
             return true;
         };
-        // thread 0: the conv MMAs of layer l over the pass's row tiles (P positions), committed to B_D
+        // warp 2: the conv MMAs of layer l over the pass's row tiles (P positions), committed to B_D
         auto issue_conv = [&](int l, int P) {
             const int T = tiles_of(l, P);
             tc_fence_after();
@@ -629,13 +639,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
 #pragma unroll
                         for (int k = 0; k < 4; k++)
-                            umma<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
+                            umma_warp<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
                     }
                 }
-                umma_commit(bar(S + s));   // the stage is free once these MMAs have read it
+                umma_commit_warp(bar(S + s));   // the stage is free once these MMAs have read it
                 adv();
             }
-            if (mma_ok) umma_commit(bar(B_D));
+            if (mma_ok) umma_commit_warp(bar(B_D));
         };
         // extent of this CTA's slots (longest queue + 1) and live count, to every CTA of the cluster
         auto send_ext = [&](int nb) {   // warp 2 only
@@ -743,11 +753,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 for (int l = 0; l < L; l++) {
                     const bool last = l == L - 1;
                     uint64_t ti0 = prof ? (uint64_t)clock64() : 0;
-                    if (tid == 0 && mma_ok) {
+                    if (wi == 0 && mma_ok) {
                         issue_conv(l, P);
                         // the peers' rows of this pass, expected while the first layer's MMAs run
                         // (every phase of the previous pass completed before its FC1 MMAs)
-                        if (l == 0) arm_rows(P);
+                        if (l == 0 && lane == 0) arm_rows(P);
                     }
                     __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
                     uint64_t ti1 = prof ? (uint64_t)clock64() : 0;
@@ -874,8 +884,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             xs[X_ROWS_NP + wi] = np;
                         }
                         // FC1 over this pass's positions, each panel once every CTA's rows of it
-                        // are in (thread 0): the MMAs of the first panels overlap later copies
-                        if (tid == 0 && mma_ok) {
+                        // are in (warp 2): the MMAs of the first panels overlap later copies
+                        if (wi == 0 && mma_ok) {
                             const uint64_t tw = prof ? (uint64_t)clock64() : 0;
                             if (prof) pacc[16] += tw - tx0;   // own rows to every peer (issue)
                             fence_async_smem();
@@ -887,30 +897,35 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                                 for (int j = 0; j < n; j++) {
                                     const int pi = p0 + j;
                                     const uint64_t tf = prof ? (uint64_t)clock64() : 0;
-                                    if (!note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R)) {
+                                    const bool in = note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R);
+                                    if (!__all_sync(0xffffffffu, in)) {
                                         mma_ok = false;
                                         break;
                                     }
                                     fph ^= 1u << pi;
-                                    xs[X_FPH] = (int)fph;
-                                    xs[X_FC1_WAITED] = pi + 1;
+                                    if (lane == 0) {
+                                        xs[X_FPH] = (int)fph;
+                                        xs[X_FC1_WAITED] = pi + 1;
+                                    }
                                     if (prof) pacc[18] += (uint64_t)clock64() - tf;
                                     const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u),
                                                    bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(HN * 128));
 #pragma unroll
                                     for (int k = 0; k < 4; k++)
-                                        umma<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
-                                                    (q0 | pi | k) != 0 ? 1u : 0u);
+                                        umma_warp<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
+                                                      (q0 | pi | k) != 0 ? 1u : 0u);
                                 }
                                 if (!mma_ok) break;
-                                umma_commit(bar(S + s));
+                                umma_commit_warp(bar(S + s));
                                 adv();
                             }
                             if (mma_ok) {   // warp 1 tells every CTA once these MMAs are done
-                                umma_commit(bar(B_F1D));
-                                xs[X_F1C] = xs[X_F1C] + 1;
-                                xs[X_ROWS_DONE] = (int)R + 1;
-                                xs[X_FC1_WAITED] = 0;
+                                umma_commit_warp(bar(B_F1D));
+                                if (lane == 0) {
+                                    xs[X_F1C] = xs[X_F1C] + 1;
+                                    xs[X_ROWS_DONE] = (int)R + 1;
+                                    xs[X_FC1_WAITED] = 0;
+                                }
                             }
                             if (prof) pacc[19] += (uint64_t)clock64() - tw;   // FC1 wait + issue
                         }
@@ -920,7 +935,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     mark(3 + 2 * l);
                 }
             }
-            if (tid == 0 && mma_ok) umma_commit(bar(B_DFC));
+            if (wi == 0 && mma_ok) umma_commit_warp(bar(B_DFC));
             __syncwarp();
             // FC1 epilogue: ReLU(FC1 + bias + S[e]) folded into FC2 partials per slot
             {
@@ -1072,20 +1087,20 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     uint32_t F = head_latency<NO, 0>(z, yf), E = head_latency<NO, 1>(z, ye), Sl = 0;
                     if constexpr (SQ) Sl = head_latency<NO, 2>(z, ys);
                     const int64_t gi = o + p;
-                    if (As.replay) {
-                        F = As.replay[NL * gi];
-                        E = As.replay[NL * gi + 1];
-                        if constexpr (SQ) Sl = As.replay[NL * gi + 2];
+                    if (replay) {
+                        F = replay[NL * gi];
+                        E = replay[NL * gi + 1];
+                        if constexpr (SQ) Sl = replay[NL * gi + 2];
                     }
-                    if (As.pre_log) {
-                        As.pre_log[NL * gi] = yf;
-                        As.pre_log[NL * gi + 1] = ye;
-                        if constexpr (SQ) As.pre_log[NL * gi + 2] = ys;
+                    if (pre_log) {
+                        pre_log[NL * gi] = yf;
+                        pre_log[NL * gi + 1] = ye;
+                        if constexpr (SQ) pre_log[NL * gi + 2] = ys;
                     }
-                    if (As.lat_log) {
-                        As.lat_log[NL * gi] = (uint8_t)F;
-                        As.lat_log[NL * gi + 1] = (uint8_t)E;
-                        if constexpr (SQ) As.lat_log[NL * gi + 2] = (uint8_t)Sl;
+                    if (lat_log) {
+                        lat_log[NL * gi] = (uint8_t)F;
+                        lat_log[NL * gi + 1] = (uint8_t)E;
+                        if constexpr (SQ) lat_log[NL * gi + 2] = (uint8_t)Sl;
                     }
                     uint64_t *qr = qring + s * cap;
                     uint64_t *mr = mring + s * cap;   // SQ only
@@ -1155,7 +1170,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             tick += 1;
                             retire(min(ql, RW));
                         }
-                        As.cycles_out[s_b[s]] = tick;
+                        cycles_out[s_b[s]] = tick;
                     }
                     s_tick[s] = tick;
                     s_p[s] = p;
@@ -1168,7 +1183,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     s_ev[s] += ev;
                     s_al[s] = p < n ? 1 : 0;
                     if (p + 1 < n)   // record of the position two steps ahead
-                        cp_async4(smem_u32(&recb[s * 4 + ((p + 1) & 3)]), As.records + o + p + 1);
+                        cp_async4(smem_u32(&recb[s * 4 + ((p + 1) & 3)]), records + o + p + 1);
                 }
                 cp_commit();      // one group per step, empty or not
                 cp_wait<1>();     // the record fetched one step ago has landed

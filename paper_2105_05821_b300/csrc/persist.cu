@@ -244,31 +244,32 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        {   // the whole warp runs the issue loop, one elected lane issues (umma_warp)
             bool ok = true;
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, pp.mma_tc++) {
                 const uint32_t ID = idesc_rt((!FP8 && t >= T0) ? a.layer[l2].BN : L.BN, FP8);
                 const int acc = pp.mma_tc & 1;
                 const uint32_t aph = (uint32_t)(pp.mma_tc >> 1) & 1u;
-                if (!mbar_wait(tempty(acc), aph ^ 1u, lim, cta_abort, a.status)) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(tempty(acc), aph ^ 1u, lim, cta_abort, a.status))) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * 256);
                 for (int kb = 0; kb < KB; kb++, pp.mma_it++) {
                     const int s = pp.mma_it % S;
                     const uint32_t ph = (uint32_t)(pp.mma_it / S) & 1u;
-                    if (!mbar_wait(full(s), ph, lim, cta_abort, a.status)) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(full(s), ph, lim, cta_abort, a.status))) { ok = false; break; }
                     tc_fence_after();
-                    if (det && t == (int)blockIdx.x && kb == 0) atomicAdd(&a.detail[4 * l + 0], gtimer() - t_phase);
+                    if (det && lane == 0 && t == (int)blockIdx.x && kb == 0)
+                        atomicAdd(&a.detail[4 * l + 0], gtimer() - t_phase);
                     const uint32_t sa = smem_base + s * a.stage_bytes;
                     const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
 #pragma unroll
                     for (int k = 0; k < 4; k++)
-                        umma<FP8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (kb | k) != 0 ? 1u : 0u);
-                    umma_commit(empty(s));
+                        umma_warp<FP8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (kb | k) != 0 ? 1u : 0u);
+                    umma_commit_warp(empty(s));
                 }
-                if (ok) umma_commit(tfull(acc));
+                if (ok) umma_commit_warp(tfull(acc));
             }
-            if (det) atomicAdd(&a.detail[4 * l + 1], gtimer() - t_phase);
+            if (det && lane == 0) atomicAdd(&a.detail[4 * l + 1], gtimer() - t_phase);
         }
         __syncwarp();
     } else {

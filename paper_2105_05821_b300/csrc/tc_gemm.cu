@@ -158,30 +158,30 @@ __global__ void __launch_bounds__(320, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        {   // the whole warp runs the issue loop, one elected lane issues (umma_warp)
             int it = 0, tc = 0;
             bool ok = true;
             constexpr uint32_t ID = idesc<BN, FP8>();
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, tc++) {
                 const int acc = tc & 1;
                 const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
-                if (!mbar_wait(tempty(acc), aph ^ 1u, lim, abort_flag, args.status)) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(tempty(acc), aph ^ 1u, lim, abort_flag, args.status))) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < KB; kb++, it++) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!mbar_wait(full(s), ph, lim, abort_flag, args.status)) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(full(s), ph, lim, abort_flag, args.status))) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_base + s * L::STAGE_BYTES;
                     const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
 #pragma unroll
                     for (int k = 0; k < 4; k++)
-                        umma<FP8>(d, ad + (uint64_t)(k * KSTEP_DESC), bd + (uint64_t)(k * KSTEP_DESC), ID,
-                                  (kb | k) != 0 ? 1u : 0u);
-                    umma_commit(empty(s));
+                        umma_warp<FP8>(d, ad + (uint64_t)(k * KSTEP_DESC), bd + (uint64_t)(k * KSTEP_DESC), ID,
+                                       (kb | k) != 0 ? 1u : 0u);
+                    umma_commit_warp(empty(s));
                 }
-                if (ok) umma_commit(tfull(acc));
+                if (ok) umma_commit_warp(tfull(acc));
             }
         }
         __syncwarp();

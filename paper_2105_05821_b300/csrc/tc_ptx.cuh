@@ -116,6 +116,31 @@ __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, ui
     }
 }
 
+// The same MMA from a converged warp: every lane runs the issue loop (so the
+// operands are warp-uniform values) and one elected lane issues.  A lone
+// thread in a divergent branch issued an MMA every ~95 cycles on this GPU,
+// a whole warp every ~64.
+template <bool FP8>
+__device__ __forceinline__ void umma_warp(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t id, uint32_t accum) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(id), "r"(accum));
+    } else {
+        asm volatile(
+            "{\n .reg .pred e, p;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(id), "r"(accum));
+    }
+}
+// Commit from a converged warp (one elected lane).
+__device__ __forceinline__ void umma_commit_warp(uint32_t bar) {
+    asm volatile(
+        "{\n .reg .pred e;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(bar)
+        : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }

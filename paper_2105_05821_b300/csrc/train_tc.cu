@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(320, 1)
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        {   // the whole warp runs the issue loop, one elected lane issues (umma_warp)
             int it = 0, tc = 0;
             bool ok = true;
             constexpr uint32_t ID = tg_idesc<BN, AMN, BMN>();
@@ -185,13 +185,13 @@ __global__ void __launch_bounds__(320, 1)
                 tg_decode(a, t, m0, nt, kb0, kb1);
                 const int acc = tc & 1;
                 const uint32_t aph = (uint32_t)(tc >> 1) & 1u;
-                if (!mbar_wait(tempty(acc), aph ^ 1u, lim, abort_flag, a.status)) break;
+                if (!__all_sync(0xffffffffu, mbar_wait(tempty(acc), aph ^ 1u, lim, abort_flag, a.status))) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
                 for (int kb = kb0; kb < kb1; kb++, it++) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!mbar_wait(full(s), ph, lim, abort_flag, a.status)) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, mbar_wait(full(s), ph, lim, abort_flag, a.status))) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_base + s * L::STAGE_BYTES, sb = sa + A_BYTES;
                     const uint64_t ad = AMN ? sdesc_mn(sa) : sdesc(sa);
@@ -202,14 +202,14 @@ __global__ void __launch_bounds__(320, 1)
                         // MN-major piece
                         const uint64_t ak = ad + (uint64_t)(AMN ? k * 128 : k * 2);
                         const uint64_t bk = bd + (uint64_t)(BMN ? k * 128 : k * 2);
-                        umma<false>(d, ak, bk, ID, (kb != kb0 || k != 0) ? 1u : 0u);
+                        umma_warp<false>(d, ak, bk, ID, (kb != kb0 || k != 0) ? 1u : 0u);
                     }
-                    umma_commit(empty(s));
+                    umma_commit_warp(empty(s));
                 }
-                if (ok) umma_commit(tfull(acc));
+                if (ok) umma_commit_warp(tfull(acc));
             }
             // MMAs still in flight after an abort finish before TMEM is released
-            umma_commit(fin);
+            umma_commit_warp(fin);
             volatile int never = 0;
             mbar_wait(fin, 0u, lim > 200000000 ? lim : 200000000, &never, a.status);
         }
