@@ -568,16 +568,18 @@ def cluster_phases(w, args, blob32, rec, off, sm_mhz):
         names = names[:6] + ["-", "-"] + names[8:]
     out = {n: float(d[k]) / steps / sm_mhz for k, n in enumerate(names) if n != "-"}
     out["positions_per_step"] = float(d[15]) / steps
-    # the MMA thread's view of the same steps (counters 16-31 of the kernel)
+    # the MMA warp's view of the same steps (counters 16-29 of the kernel; 30-31 are the
+    # workers' FC1 epilogue)
     L = w.arch.n_conv
-    detail = {"exchange issue": 16, "last conv epilogue": 17, "wait peer rows": 18, "FC1 waits and issue": 19,
-              "FC1 epilogue arithmetic": 30, "partial sums sent": 31}
+    detail = {"wait feature rows": 16, "wait extent": 17, "wait peer rows": 18, "FC1 issue": 19,
+              "wait FC1 operand halves": 20, "FC1 epilogue arithmetic": 30, "partial sums sent": 31}
     for l in range(L):
-        detail[f"conv{l + 1} issue"] = 20 + 2 * l
-        detail[f"conv{l + 1} last commit to done"] = 21 + 2 * l
+        if l > 0:
+            detail[f"wait conv{l + 1} operand halves"] = 20 + l
+        detail[f"conv{l + 1} issue"] = 23 + l
         detail[f"conv{l + 1} weight waits"] = 26 + l
     detail["FC1 weight waits"] = 26 + L
-    out["mma_thread"] = {n: float(d[k]) / steps / sm_mhz for n, k in detail.items()}
+    out["mma_warp"] = {n: float(d[k]) / steps / sm_mhz for n, k in detail.items()}
     return out
 
 

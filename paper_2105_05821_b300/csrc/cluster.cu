@@ -64,7 +64,8 @@ namespace {
 using namespace tcx;
 
 // A cluster of CS CTAs (4 or 8) owns 128 batch slots, 128 / CS per CTA.
-constexpr int kCThreads = 320;
+// Roles: warp 0 TMA producer, warp 1 FC1-done signal, warp 2 MMAs, warps 3-10 workers.
+constexpr int kCThreads = 352;
 constexpr int kWk = 256;          // worker threads
 // One weight stage: consecutive panels (N rows x 64 K-columns BF16, at most 16 KB) of
 // one layer, as many as fit in 16 or 32 KB (the larger where three such stages fit);
@@ -120,7 +121,7 @@ __host__ __device__ inline CLay c_layout(int CS, int L, int C, int H, int cap, i
     // misc: extents in | control words | 32 phase counters (profiling) | exit counters
     // (64 ints) | what every peer sent this CTA (one uint4 per peer)
     y.bars = al_up(y.misc + 16 * CS + 32 + 32 * 8 + 256 + 128, 8);
-    y.total = y.bars + (2 * stages + 17) * 8;
+    y.total = y.bars + (2 * stages + 21) * 8;
     return y;
 }
 
@@ -359,7 +360,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // Record where the first expired wait of the launch was (sites: 1 weight stage free,
     // 2 extent (producer), 3 weight panel, 4 extent (workers), 5 conv layer done, 6 exchange
     // buffer free, 7 exchanged rows in, 8 FC1 done, 9 FC2 partial sums in, 10 FC1 done
-    // (warp 1's signal to the cluster)).
+    // (warp 1's signal to the cluster), 11 feature rows in, 12 / 13 first / second channel
+    // half of a layer's output in, 14 the step's extent (the MMA warp's waits)).
     auto note = [&](bool ok, int site, int64_t step, int64_t pass) -> bool {
         if (!ok && *(volatile int32_t *)a.status == kStatusTimeout &&
             atomicCAS(&a.tinfo[0], 0ull, (unsigned long long)site) == 0ull) {
@@ -379,6 +381,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     constexpr uint32_t kPartBytes = 2u * CS * SPC * PF * 4u, kExtBytes = CS * 8u;
     const int B_D = 2 * S, B_DFC = 2 * S + 2, B_PART = 2 * S + 3, B_EXT = 2 * S + 4,
               B_FIN = 2 * S + 6, B_FULL = 2 * S + 7, B_F1D = 2 * S + 15;
+    // the workers' signals to the MMA warp (one arrival per worker warp, after its writes):
+    // a pass's feature rows, the first and the second channel half of a layer's output; and
+    // the step's extent (worker thread 0)
+    const int B_ROWS = 2 * S + 17, B_HA = 2 * S + 18, B_HB = 2 * S + 19, B_CTL = 2 * S + 20;
     // the exchanged rows of pass R may be overwritten once every CTA's FC1 of pass R is
     // done: CS arrivals on B_EMPTY + (R & 1) (two barriers, so that an arrival for the
     // next pass can never complete the phase of this one)
@@ -434,6 +440,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         mbar_expect_tx(bar(B_EXT + 1), kExtBytes);
         mbar_init(bar(B_FIN), 1);
         mbar_init(bar(B_F1D), 1);
+        mbar_init(bar(B_ROWS), 8);
+        mbar_init(bar(B_HA), 8);
+        mbar_init(bar(B_HB), 8);
+        mbar_init(bar(B_CTL), 1);
         *abort_f = 0;
         cnt[0] = cnt[1] = 0;
         for (int k = 0; k < 32; k++) pacc[k] = 0;
@@ -470,11 +480,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             s_w2[i] = o < NO ? a.w2[(size_t)o * a.H + (int)rank * HN + j] : 0.f;
         }
     if (threadIdx.x < 24) s_b2[threadIdx.x] = threadIdx.x < NO ? a.b2[threadIdx.x] : 0.f;
-    // slot state (workers: warp w takes slots w-2, w+6, ...)
-    if (warp >= 2) {
+    // slot state (workers: warp w takes slots w-3, w+5, ...)
+    if (warp >= 3) {
         const int n_act = min(*A->n_active, A->n_sub);
         for (int j = 0; j < SPC / 8; j++) {
-            const int s = (warp - 2) + 8 * j, g = slot0 + s;
+            const int s = (warp - 3) + 8 * j, g = slot0 + s;
             int b = -1;
             int64_t o = 0;
             int n = 0, p = 0;
@@ -521,6 +531,19 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // panels a stage holds: conv panels are C x 64, FC1 panels HN x 64 (BF16)
     const int kConvPer = (int)kStage / (C * 128), kFcPer = min((int)kStage / (HN * 128), 8);
     auto conv_stages = [&](int l) { return (panels_of(l) + kConvPer - 1) / kConvPer; };
+    // Channel halves of an operand whose K runs over blocks of C channels (a conv layer's two
+    // input rows, or FC1's positions).  With panels of EPP <= C elements the K-steps of half h
+    // in a panel are one contiguous run: all or none of a panel half a row wide (BF16,
+    // C = 128: the even panels hold the first half), else its first or its last two of four.
+    // FP8 with 64 channels (two rows to a panel) is not split.
+    const bool kSplit = EPP <= C;
+    // load order of layer l's weight panels (l >= 1): the first channel half's panels first
+    // where a panel is narrower than a row
+    auto conv_perm = [&](int l, int i) -> int {
+        if (l == 0 || !(EPP < C)) return i;
+        const int hp = panels_of(l) / 2;
+        return i < hp ? 2 * i : 2 * (i - hp) + 1;
+    };
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
@@ -531,9 +554,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 if (++ps == S) { ps = 0; pph ^= 1u; }
             };
             bool ok = true;
-            // n panels of pb bytes (K-columns x0, x0 + 64, ...) into the next stage: whole
+            // n panels of pb bytes (K-columns x0, x0 + xs, ...) into the next stage: whole
             // conv panels (all C rows) or this CTA's rows of FC1 panels
-            auto load = [&](const CUtensorMap *m, int x0, int yy, uint32_t pb, int n) {
+            auto load = [&](const CUtensorMap *m, int x0, int xs, int yy, uint32_t pb, int n) {
                 const int s = ps;
                 if (!note(mbar_wait(bar(S + s), pph ^ 1u, lim, abort_f, a.status), 1, -1, it)) {
                     ok = false;
@@ -541,7 +564,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 }
                 mbar_expect_tx(bar(s), (uint32_t)n * pb);
                 for (int j = 0; j < n; j++)
-                    tma_load_2d(ring0 + (uint32_t)s * kStage + (uint32_t)j * pb, m, bar(s), x0 + EPP * j, yy);
+                    tma_load_2d(ring0 + (uint32_t)s * kStage + (uint32_t)j * pb, m, bar(s), x0 + xs * j, yy);
                 adv();
             };
             // conv stage i of a pass (all layers' weights in consumption order), i in [from, to)
@@ -553,7 +576,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     for (int g = 0; g < conv_stages(l) && ok; g++, i++) {
                         if (i < from || i >= to) continue;
                         const int p0 = g * kConvPer, n = min(kConvPer, panels_of(l) - p0);
-                        load(&a.tW[l], p0 * EPP, 0, (uint32_t)C * 128u, n);
+                        // panels in the MMA warp's order (a stage's panels are evenly spaced)
+                        const int x0 = conv_perm(l, p0) * EPP, xs = n > 1 ? (conv_perm(l, p0 + 1) - conv_perm(l, p0)) * EPP : 0;
+                        load(&a.tW[l], x0, xs, 0, (uint32_t)C * 128u, n);
                     }
             };
             // Before a step's extent is known only its first S stages are loaded: they are
@@ -572,27 +597,260 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     conv_loads(q0 > 0 ? 0 : pre, n_conv_stages);
                     const int np = P * C / EPP;
                     for (int p0 = 0; p0 < np && ok; p0 += kFcPer)
-                        load(&a.tF, q0 * C + p0 * EPP, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0));
+                        load(&a.tF, q0 * C + p0 * EPP, EPP, (int)rank * HN, (uint32_t)HN * 128u, min(kFcPer, np - p0));
                 }
                 if (t + 1 < a.n_steps) conv_loads(0, pre);   // the next step's first stages
             }
             cnt[0] = it;
         }
-    } else if (warp >= 2) {
-        // ---------------------------------------------------------------- workers (thread 0 also issues the MMAs)
-        const int wi = warp - 2, qd = warp & 3, half = wi >> 2, tid = threadIdx.x - 64;
-        int d_uses = 0, it = 0;    // it: weight panels consumed (thread 0)
-        int cs = 0;                // stage of panel `it` and its phase parity
+    } else if (warp == 2) {
+        // ---------------------------------------------------------------- MMA warp
+        // The whole warp runs the issue loops (warp-uniform operands, one elected lane issues
+        // each MMA) and follows the workers through the step: the first layer's MMAs as soon
+        // as the pass's feature rows are in (the first pass's before the cluster's extent is
+        // known), then per layer the K-steps of the first channel half of the operand while
+        // the workers still write the second half.
+        int it = 0, cs = 0;        // weight stages consumed; ring slot of the next one and its phase
         uint32_t cph = 0;
-        auto adv = [&] {
+        uint32_t fph = 0;          // phase parity of each B_FULL + i
+        uint32_t ph_rows = 0, ph_ha = 0, ph_hb = 0, ph_ctl = 0;   // phases of the workers' signals
+        int64_t R = 0;             // passes exchanged
+        bool ok = true;
+        const bool prof = a.prof && blockIdx.x == 0 && lane == 0;
+        // a worker signal (B_ROWS, B_HA, B_HB, B_CTL); the wait's time goes to counter pc
+        auto wait_sig = [&](int b, uint32_t &ph, int site, int64_t t, int pc) -> bool {
+            const uint64_t t0 = prof ? (uint64_t)clock64() : 0;
+            const bool w = note(sleep_wait(bar(b), ph, lim, abort_f, a.status, false), site, t, R);
+            ph ^= 1u;
+            if (prof) pacc[pc] += (uint64_t)clock64() - t0;
+            const bool all = __all_sync(0xffffffffu, w);
+            tc_fence_after();
+            return all;
+        };
+        auto take = [&](int &s, int who) -> bool {   // the next weight stage (who: layer, L = FC1)
+            s = cs;
+            const uint64_t tw = prof ? (uint64_t)clock64() : 0;
+            const bool w = note(mbar_wait(bar(s), cph, lim, abort_f, a.status), 3, -1, it);
+            if (!__all_sync(0xffffffffu, w)) return false;
+            if (prof) pacc[26 + who] += (uint64_t)clock64() - tw;
+            tc_fence_after();
             it++;
             if (++cs == S) { cs = 0; cph ^= 1u; }
+            return true;
         };
+        // K-steps k0 .. k0 + nk - 1 (nk 2 or 4) of one 128-byte operand panel; the layer's
+        // first MMA (fresh) overwrites the accumulator
+        auto mma_ks = [&](uint32_t d, uint32_t alo, uint32_t blo, uint32_t ID, int k0, int nk, bool &fresh) {
+            alo += 2u * (uint32_t)k0;
+            blo += 2u * (uint32_t)k0;
+            umma_lo<F8>(d, alo, blo, ID, fresh ? 0u : 1u);
+            fresh = false;
+            umma_lo<F8>(d, alo + 2u, blo + 2u, ID, 1u);
+            if (nk == 4) {
+                umma_lo<F8>(d, alo + 4u, blo + 4u, ID, 1u);
+                umma_lo<F8>(d, alo + 6u, blo + 6u, ID, 1u);
+            }
+        };
+        const uint32_t act_lo = sdesc_lo(act0), ring_lo = sdesc_lo(ring0), fc_lo = sdesc_lo(fc0);
+        const uint32_t cstep = (uint32_t)(C * 128) >> 4, hstep = (uint32_t)(HN * 128) >> 4;
+        // the first layer over a pass's rows (all K-steps: the rows are built whole)
+        auto conv_first = [&](int P) -> bool {
+            const int T = tiles_of(0, P), np = panels_of(0), G = conv_stages(0);
+            const uint32_t ID = idesc_rt(C, F8), astep = pstride_of(0, P) >> 4;
+            bool f0 = true, f1 = true;
+            for (int g = 0; g < G; g++) {
+                int s;
+                if (!take(s, 0)) return false;
+                const int n = min(kConvPer, np - g * kConvPer);
+                for (int j = 0; j < n; j++) {
+                    const int pi = g * kConvPer + j;
+                    const uint32_t a0 = act_lo + (uint32_t)pi * astep, b0 = ring_lo + ((uint32_t)s * kStage >> 4) + (uint32_t)j * cstep;
+                    mma_ks(tmem_base, a0, b0, ID, 0, 4, f0);
+                    if (T == 2) mma_ks(tmem_base + (uint32_t)C, a0 + 1024u, b0, ID, 0, 4, f1);
+                }
+                umma_commit_warp(bar(S + s));   // the stage is free once these MMAs have read it
+            }
+            umma_commit_warp(bar(B_D));
+            return true;
+        };
+        // Layer l >= 1 (one 128-row tile): its operand's channel halves as the workers finish
+        // them.  The issue path carries as little arithmetic as possible (the MMA warp shares
+        // its scheduler with two busy worker warps while it issues the first half).
+        auto conv_next = [&](int l, int P, int64_t t) -> bool {
+            const int np = panels_of(l), G = conv_stages(l);
+            const uint32_t ID = idesc_rt(C, F8), astep = pstride_of(l, P) >> 4, d = tmem_base + dcol(l);
+            bool fresh = true;
+            if (!kSplit) {   // FP8 with 64 channels: everything once both halves are in
+                if (!wait_sig(B_HA, ph_ha, 12, t, 20 + l) || !wait_sig(B_HB, ph_hb, 13, t, 20 + l)) return false;
+                const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                for (int g = 0; g < G; g++) {
+                    int s;
+                    if (!take(s, l)) return false;
+                    const int n = min(kConvPer, np - g * kConvPer);
+                    const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4);
+                    for (int j = 0; j < n; j++)
+                        mma_ks(d, act_lo + (uint32_t)(g * kConvPer + j) * astep, b0 + (uint32_t)j * cstep, ID, 0, 4, fresh);
+                    umma_commit_warp(bar(S + s));
+                }
+                if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
+            } else if (EPP < C) {
+                // panels half a row wide (BF16, 128 channels): the stages of the first half hold
+                // the even panels (rows 2j, 2j+1, channels 0-63), those of the second the odd ones
+                const int hp = np / 2, Gh = G / 2;
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20 + l)) return false;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    for (int g = 0; g < Gh; g++) {
+                        int s;
+                        if (!take(s, l)) return false;
+                        const int i0 = g * kConvPer, n = min(kConvPer, hp - i0);
+                        const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4);
+                        uint32_t a = act_lo + (uint32_t)(2 * i0 + h) * astep;
+                        for (int j = 0; j < n; j++, a += 2u * astep) mma_ks(d, a, b0 + (uint32_t)j * cstep, ID, 0, 4, fresh);
+                        umma_commit_warp(bar(S + s));
+                    }
+                    if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
+                }
+            } else {
+                // panels a row wide (BF16 with 64 channels, FP8 with 128): K-steps 0-1 of every
+                // panel are the first half, 2-3 the second; the layer's stages (at most two)
+                // stay held until the second half is issued
+                int s0 = 0, s1 = 0;
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20 + l)) return false;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    for (int g = 0; g < G; g++) {
+                        if (h == 0) {
+                            int s;
+                            if (!take(s, l)) return false;
+                            if (g == 0) s0 = s; else s1 = s;
+                        }
+                        const uint32_t s = g == 0 ? (uint32_t)s0 : (uint32_t)s1;
+                        const int n = min(kConvPer, np - g * kConvPer);
+                        const uint32_t b0 = ring_lo + (s * kStage >> 4);
+                        for (int j = 0; j < n; j++)
+                            mma_ks(d, act_lo + (uint32_t)(g * kConvPer + j) * astep, b0 + (uint32_t)j * cstep, ID, 2 * h, 2, fresh);
+                        if (h == 1) umma_commit_warp(bar(S + (int)s));
+                    }
+                    if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
+                }
+            }
+            umma_commit_warp(bar(B_D));
+            return true;
+        };
+        // FC1 over a pass's positions: per panel once every CTA's rows of it are in; with the
+        // split (every FC1 stage of the pass held at once) the first channel half's K-steps first
+        auto fc1 = [&](int q0, int P, int64_t t) -> bool {
+            const int np = P * C / EPP, G = (np + kFcPer - 1) / kFcPer;
+            const bool split = kSplit && G <= S;
+            const int fmask = kFcPer - 1, fshift = __ffs(kFcPer) - 1;   // kFcPer is a power of two
+            const uint32_t ID = idesc_rt(HN, F8), d = tmem_base + 384u;
+            bool fresh = q0 == 0;   // FC1 accumulates over the passes
+            uint64_t slots = 0;     // ring slot of each stage taken (up to eight)
+            int taken = 0;
+            // panel pi: its stage (taken at first use), the peers' rows (waited at first use)
+            auto panel = [&](int pi, int k0, int nk) -> bool {
+                const int g = pi >> fshift, j = pi & fmask;
+                while (taken <= g) {
+                    int s;
+                    if (!take(s, L)) return false;
+                    slots |= (uint64_t)s << (8 * taken);
+                    taken++;
+                }
+                if (k0 == 0) {   // first use of the panel
+                    const uint64_t tf = prof ? (uint64_t)clock64() : 0;
+                    const bool in = note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R);
+                    if (!__all_sync(0xffffffffu, in)) return false;
+                    fph ^= 1u << pi;
+                    if (lane == 0) {
+                        xs[X_FPH] = (int)fph;
+                        xs[X_FC1_WAITED] = xs[X_FC1_WAITED] | (1 << pi);
+                    }
+                    if (prof) pacc[18] += (uint64_t)clock64() - tf;
+                }
+                const uint32_t s = (uint32_t)(slots >> (8 * g)) & 0xffu;
+                mma_ks(d, fc_lo + (uint32_t)pi * 1024u, ring_lo + (s * kStage >> 4) + (uint32_t)j * hstep, ID, k0, nk,
+                       fresh);
+                return true;
+            };
+            if (!split) {
+                if (!wait_sig(B_HA, ph_ha, 12, t, 20) || !wait_sig(B_HB, ph_hb, 13, t, 20)) return false;
+                const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                for (int pi = 0; pi < np; pi++) {
+                    if (!panel(pi, 0, 4)) return false;
+                    if (pi + 1 == np || ((pi + 1) & fmask) == 0)   // the stage's last panel
+                        umma_commit_warp(bar(S + (int)((slots >> (8 * (pi >> fshift))) & 0xffu)));
+                }
+                if (prof) pacc[19] += (uint64_t)clock64() - ti;
+            } else {
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20)) return false;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    if (EPP < C) {   // the even panels are the first half, the odd ones the second
+                        for (int pi = h; pi < np; pi += 2)
+                            if (!panel(pi, 0, 4)) return false;
+                    } else {         // K-steps 0-1 of every panel, then 2-3
+                        for (int pi = 0; pi < np; pi++)
+                            if (!panel(pi, 2 * h, 2)) return false;
+                    }
+                    if (prof) pacc[19] += (uint64_t)clock64() - ti;
+                }
+                for (int g = 0; g < taken; g++) umma_commit_warp(bar(S + (int)((slots >> (8 * g)) & 0xffu)));
+            }
+            umma_commit_warp(bar(B_F1D));   // warp 1 tells every CTA once these MMAs are done
+            if (lane == 0) {
+                xs[X_F1C] = xs[X_F1C] + 1;
+                xs[X_ROWS_DONE] = (int)R + 1;
+                xs[X_FC1_WAITED] = 0;
+            }
+            R++;
+            return true;
+        };
+        auto arm_rows = [&](int P) {   // lane 0: the peers' rows of pass R, all panels
+            for (int i = 0; i < P * C / EPP; i++) mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * kRowBytes);
+            xs[X_ARMED_R] = (int)R + 1;
+            xs[X_ARMED_NP] = P * C / EPP;
+        };
+        const int P0 = min(PM, a.rows_n);
+        for (int64_t t = 0; t < a.n_steps && ok; t++) {
+            int eL = P0;
+            for (int q0 = 0; q0 < eL && ok; q0 += PM) {
+                const int P = min(PM, eL - q0);   // P0 for the first pass
+                ok = wait_sig(B_ROWS, ph_rows, 11, t, 16);
+                if (ok) {
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    tc_fence_after();
+                    ok = conv_first(P);
+                    if (prof) pacc[23] += (uint64_t)clock64() - ti;
+                }
+                // the peers' rows of this pass, expected while its MMAs run (every phase of
+                // the previous pass completed before that pass's FC1 MMAs)
+                if (ok && lane == 0) arm_rows(P);
+                __syncwarp();
+                if (ok && q0 == 0) {   // the step's extent: positions, or the cluster is done
+                    ok = wait_sig(B_CTL, ph_ctl, 14, t, 17);
+                    if (!ok || ctl[1]) { ok = false; break; }
+                    eL = ctl[0];
+                }
+                for (int l = 1; l < L && ok; l++) ok = conv_next(l, P, t);
+                if (ok) ok = fc1(q0, P, t);
+            }
+            if (ok) umma_commit_warp(bar(B_DFC));
+        }
+        // every MMA done before TMEM is released
+        if (lane == 0) {
+            cnt[1] = it;
+            __threadfence_block();
+            xs[X_DONE] = 1;   // no more FC1 commits: warp 1 stops once it has signalled them all
+        }
+        umma_commit_warp(bar(B_FIN));
+        if (lane == 0) drain_wait(bar(B_FIN), 0u, drain_ns);
+        __syncwarp();
+    } else if (warp >= 3) {
+        // ---------------------------------------------------------------- workers
+        const int wi = warp - 3, qd = warp & 3, half = wi >> 2, tid = threadIdx.x - 96;
+        int d_uses = 0;
         int64_t R = 0;             // passes exchanged
-        // The MMAs are issued by warp 2 as a whole (converged, one elected lane issues; the
-        // operands are then warp-uniform values, which issue faster than from a lone thread).
-        bool mma_ok = true;        // warp 2: false after a bounded wait gave up
-        uint32_t fph = 0;          // warp 2: phase parity of each B_FULL + i
         const StepArgs &As = *A;
         const int RW = As.retire_width, strict = As.strict;
         // the call's pointers, read once (the head's stores could alias the argument block,
@@ -611,44 +869,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 tp = tn;
             }
         };
-        auto take = [&](int &s, int who) -> bool {   // warp 2: next weight panel (who: layer, L = FC1)
-            s = cs;
-            const uint64_t tw = prof ? (uint64_t)clock64() : 0;
-            const bool ok = note(mbar_wait(bar(s), cph, lim, abort_f, a.status), 3, -1, it);
-            if (!__all_sync(0xffffffffu, ok)) return false;
-            if (prof) pacc[26 + who] += (uint64_t)clock64() - tw;
-            tc_fence_after();
-            return true;
-        };
-        // warp 2: the conv MMAs of layer l over the pass's row tiles (P positions), committed to B_D
-        auto issue_conv = [&](int l, int P) {
-            const int T = tiles_of(l, P);
-            tc_fence_after();
+        auto signal = [&](int b) {   // this warp's share of a signal to the MMA warp (after its writes)
             fence_async_smem();
-            const uint32_t ID = idesc_rt(C, F8);
-            const uint32_t pstride = pstride_of(l, P);
-            for (int p0 = 0; p0 < panels_of(l) && mma_ok; p0 += kConvPer) {
-                int s;
-                if (!take(s, l)) { mma_ok = false; break; }
-                const int n = min(kConvPer, panels_of(l) - p0);
-                for (int j = 0; j < n; j++) {
-                    const int pi = p0 + j;
-                    const uint64_t bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(C * 128));
-                    for (int tt = 0; tt < T; tt++) {
-                        const uint64_t ad = sdesc(act0 + (uint32_t)pi * pstride + (uint32_t)tt * 16384u);
-                        const uint32_t d = tmem_base + dcol(l) + (uint32_t)(tt * C);
-#pragma unroll
-                        for (int k = 0; k < 4; k++)
-                            umma_warp<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (pi | k) != 0 ? 1u : 0u);
-                    }
-                }
-                umma_commit_warp(bar(S + s));   // the stage is free once these MMAs have read it
-                adv();
-            }
-            if (mma_ok) umma_commit_warp(bar(B_D));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(b));
         };
         // extent of this CTA's slots (longest queue + 1) and live count, to every CTA of the cluster
-        auto send_ext = [&](int nb) {   // warp 2 only
+        auto send_ext = [&](int nb) {   // worker warp 0 only
             int mx = 0, al = 0;
             if (lane < SPC && s_al[lane]) { mx = s_ql[lane] + s_ml[lane] + 1; al = 1; }   // whole context
 #pragma unroll
@@ -705,30 +932,136 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 #pragma unroll
                 for (int j = 0; j < NCH; j++) *reinterpret_cast<uint4 *>(dst + (((c0 + j) ^ (m & 7)) << 4)) = ch[j];
             }
-            fence_async_smem();
+        };
+        // Epilogue of layer l, channel half h, for this warp's TMEM lanes (quadrant qd) and its
+        // quarter of the channels: bias, ReLU, rounding (FP8: dequantise and requantise), written
+        // as the next layer's operand (rows 2j, 2j+1 of a slot side by side along K) or, after
+        // the last conv layer, as this CTA's rows of the FC1 operand.
+        auto epilogue = [&](auto CWc, int l, int P, int h) {
+            constexpr int CW = decltype(CWc)::value;   // channels a warp converts (C / 4)
+            const bool last = l == L - 1;
+            const int T = tiles_of(l, P), Rl = rows_of(l, P);
+            const int cb = h * (C / 2) + half * CW;   // this warp's first channel
+            for (int tt = 0; tt < T; tt++) {
+                const int m = tt * 128 + qd * 32 + lane;   // this lane's row of the tile
+                if (tt * 128 + qd * 32 >= Rl) continue;    // warp-uniform: rows past the pass
+                const bool valid = m < Rl;
+                const int p = m / SPC, s = m % SPC;
+                int row;
+                uint32_t base, pstride;
+                if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
+                    row = (p >> 1) * SPC + s;
+                    base = y.act;
+                    pstride = pstride_of(l + 1, P);
+                } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
+                    row = (int)rank * SPC + s;
+                    base = y.fc1a;
+                    pstride = 16384u;
+                }
+                const int kb = (last ? p * C : (p & 1) * C) + cb;
+                uint32_t r[CW];
+                const uint32_t ta = tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + cb);
+                if constexpr (CW == 32) tmem_ld32(ta, r);
+                else tmem_ld16(ta, r);
+                if constexpr (F8) {
+                    // dequantise (weight scale), bias, ReLU, requantise to the next layer's
+                    // input scale, e4m3 with saturation: 16 channels a chunk
+                    const int cc = l * C + cb;
+                    const float4 *cbv = reinterpret_cast<const float4 *>(s_cb + cc);
+                    const float4 *cw = reinterpret_cast<const float4 *>(s_ws + cc);
+                    const float4 *co = reinterpret_cast<const float4 *>(s_os + cc);
+                    uint32_t w[CW / 4];
+#pragma unroll
+                    for (int j = 0; j < CW / 4; j++) {
+                        const float4 b = cbv[j], sw = cw[j], so = co[j];
+                        const float v0 = fmaxf(__uint_as_float(r[4 * j]) * sw.x + b.x, 0.f) * so.x;
+                        const float v1 = fmaxf(__uint_as_float(r[4 * j + 1]) * sw.y + b.y, 0.f) * so.y;
+                        const float v2 = fmaxf(__uint_as_float(r[4 * j + 2]) * sw.z + b.z, 0.f) * so.z;
+                        const float v3 = fmaxf(__uint_as_float(r[4 * j + 3]) * sw.w + b.w, 0.f) * so.w;
+                        const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
+                        const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
+                        w[j] = (lo & 0xffffu) | (hi << 16);
+                    }
+#pragma unroll
+                    for (int j = 0; j < CW / 16; j++) {
+                        const int k = kb + 16 * j;
+                        const uint32_t off = base + (uint32_t)(k >> 7) * pstride + (uint32_t)row * 128u +
+                                             ((uint32_t)(((k >> 4) & 7) ^ (row & 7)) << 4);
+                        if (valid)
+                            *reinterpret_cast<uint4 *>(sm + off) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                    }
+                } else {
+                    // bias four channels to a load; ReLU on the rounded pairs (rounding to
+                    // nearest keeps the sign, so this equals rounding the ReLU output)
+                    const float4 *cbv = reinterpret_cast<const float4 *>(s_cb + l * C + cb);
+                    const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
+                    uint32_t w[CW / 2];
+#pragma unroll
+                    for (int j = 0; j < CW / 4; j++) {
+                        const float4 b = cbv[j];
+                        __nv_bfloat162 p0 = __floats2bfloat162_rn(__uint_as_float(r[4 * j]) + b.x,
+                                                                  __uint_as_float(r[4 * j + 1]) + b.y);
+                        __nv_bfloat162 p1 = __floats2bfloat162_rn(__uint_as_float(r[4 * j + 2]) + b.z,
+                                                                  __uint_as_float(r[4 * j + 3]) + b.w);
+                        p0 = __hmax2(p0, zero2);
+                        p1 = __hmax2(p1, zero2);
+                        w[2 * j] = *reinterpret_cast<uint32_t *>(&p0);
+                        w[2 * j + 1] = *reinterpret_cast<uint32_t *>(&p1);
+                    }
+#pragma unroll
+                    for (int j = 0; j < CW / 8; j++) {
+                        const int k = kb + 8 * j;
+                        const uint32_t off = base + (uint32_t)(k >> 6) * pstride + (uint32_t)row * 128u +
+                                             ((uint32_t)(((k >> 3) & 7) ^ (row & 7)) << 4);
+                        if (valid)
+                            *reinterpret_cast<uint4 *>(sm + off) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+                    }
+                }
+            }
+        };
+        auto epi = [&](int l, int P, int h) {
+            if (C == 128) epilogue(std::integral_constant<int, 32>{}, l, P, h);
+            else epilogue(std::integral_constant<int, 16>{}, l, P, h);
+        };
+        // this CTA's rows of the pass's FC1 panels of channel half h (all panels when a panel
+        // spans both halves: h = 1 only) to every peer, one warp per peer: one bulk copy per
+        // panel, counted on the peer's B_FULL + panel; a peer overwrites its copy only after
+        // B_EMPTY, i.e. after every CTA's FC1 of this pass, which waited for all of its copies
+        auto send_rows = [&](int P, int h) {
+            if (lane != 0 || wi < 1 || wi >= CS) return;
+            const uint32_t peer = (rank + (uint32_t)wi) % CS;
+            const int np = P * C / EPP;
+            for (int i = 0; i < np; i++) {
+                // panels half a row wide: the even ones are complete after the first half
+                if (kSplit && EPP < C ? (i & 1) != h : h == 0) continue;
+                const uint32_t src = fc0 + (uint32_t)i * 16384u + rank * kRowBytes;
+                cl_bulk_copy(cl_map(src, peer), src, kRowBytes, cl_map(bar(B_FULL + i), peer));
+            }
+            if (h == 1) {
+                xs[X_ROWS_SENT + wi] = (int)R + 1;   // what this warp sent its peer
+                xs[X_ROWS_NP + wi] = np;
+            }
         };
         // The first pass always covers P0 positions: its rows need no cluster-wide extent, so
-        // they are built while the extents are exchanged (positions of the pass past the
-        // extent are padding rows, computed rather than taken from S[e]: the same result).
+        // they are built (and the first layer's MMAs issued) while the extents are exchanged
+        // (positions of the pass past the extent are padding rows, computed rather than taken
+        // from S[e]: the same result).
         const int P0 = min(PM, a.rows_n);
-        auto arm_rows = [&](int P) {   // thread 0: the peers' rows of pass R, all panels
-            for (int i = 0; i < P * C / EPP; i++) mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * kRowBytes);
-            xs[X_ARMED_R] = (int)R + 1;
-            xs[X_ARMED_NP] = P * C / EPP;
-        };
         for (int64_t t = 0; t < a.n_steps; t++) {
-            workers_sync();   // the previous step's head (warp 2) is visible
+            workers_sync();   // the previous step's head (worker warp 0) is visible
             build_rows(0, P0);
+            signal(B_ROWS);   // the MMA warp starts the first layer while the extent is awaited
             if (tid == 0) {
                 const bool ok = note(sleep_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status, true), 4, t, 0);
+                int E, AL;
+                read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 if (ok) {
                     mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
                     xs[X_EXT_CONS] = xs[X_EXT_CONS] + 1;
                 }
-                int E, AL;
-                read_ext<CS>(ext_in, (int)(t & 1), E, AL);
                 ctl[0] = step_positions(E, L, a.rows_n, P0, kERound);
                 ctl[1] = (!ok || AL == 0 || *abort_f) ? 1 : 0;
+                mbar_arrive(bar(B_CTL));   // the MMA warp reads ctl
             }
             workers_sync();
             const int eL = ctl[0];
@@ -747,26 +1080,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 const int P = min(PM, eL - q0);   // P0 for the first pass
                 if (q0 > 0) {
                     build_rows(q0, P);
-                    workers_sync();
+                    signal(B_ROWS);
                 }
                 mark(1);
                 for (int l = 0; l < L; l++) {
                     const bool last = l == L - 1;
-                    uint64_t ti0 = prof ? (uint64_t)clock64() : 0;
-                    if (wi == 0 && mma_ok) {
-                        issue_conv(l, P);
-                        // the peers' rows of this pass, expected while the first layer's MMAs run
-                        // (every phase of the previous pass completed before its FC1 MMAs)
-                        if (l == 0 && lane == 0) arm_rows(P);
-                    }
-                    __syncwarp();   // the rest of warp 2 waits here, not in the spin loop beside the issuing lane
-                    uint64_t ti1 = prof ? (uint64_t)clock64() : 0;
                     bool ok = note(sleep_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status, false), 5, t, R);
-                    if (prof) {
-                        const uint64_t ti2 = (uint64_t)clock64();
-                        pacc[20 + 2 * l] += ti1 - ti0;   // issue (incl. weight waits)
-                        pacc[21 + 2 * l] += ti2 - ti1;   // last commit -> layer done seen
-                    }
                     d_uses++;
                     if (last && R >= 1 && ok)   // every CTA has consumed the previous pass's exchanged rows
                         ok = note(cl_wait(b_empty(R - 1), (uint32_t)(((R - 1) >> 1) & 1), lim, abort_f, a.status),
@@ -774,169 +1093,28 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     ok = __all_sync(0xffffffffu, ok);
                     tc_fence_after();
                     mark(2 + 2 * l);
-                    const int T = tiles_of(l, P), Rl = rows_of(l, P);
-                    for (int tt = 0; tt < T && ok; tt++) {
-                        const int m = tt * 128 + qd * 32 + lane;   // this lane's row of the tile
-                        if (tt * 128 + qd * 32 >= Rl) continue;    // warp-uniform: rows past the pass
-                        const bool valid = m < Rl;
-                        const int p = m / SPC, s = m % SPC;
-                        const int c0 = half * (C / 2), nb = C / 64;   // this warp's channels: nb blocks of 32
-                        int row;
-                        uint32_t base, pstride;
-                        if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
-                            row = (p >> 1) * SPC + s;
-                            base = y.act;
-                            pstride = pstride_of(l + 1, P);
-                        } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
-                            row = (int)rank * SPC + s;
-                            base = y.fc1a;
-                            pstride = 16384u;
-                        }
-                        const int kb = last ? p * C + c0 : (p & 1) * C + c0;
-                        // one block of 32 columns at a time (a TMEM load costs ~80 cycles; holding
-                        // both blocks' registers at once spilled)
-#pragma unroll 1
-                        for (int bi = 0; bi < nb; bi++) {
-                            uint32_t r32[32];
-                            tmem_ld32(tmem_base + ((uint32_t)(qd * 32) << 16) + dcol(l) + (uint32_t)(tt * C + c0 + bi * 32),
-                                      r32);
-                            if constexpr (F8) {
-                                // dequantise (weight scale), bias, ReLU, requantise to the next
-                                // layer's input scale, e4m3 with saturation: 16 channels a chunk
-                                const int cc = l * C + c0 + bi * 32;
-                                const float4 *cb = reinterpret_cast<const float4 *>(s_cb + cc);
-                                const float4 *cw = reinterpret_cast<const float4 *>(s_ws + cc);
-                                const float4 *co = reinterpret_cast<const float4 *>(s_os + cc);
-                                uint32_t w[8];
-#pragma unroll
-                                for (int j = 0; j < 8; j++) {
-                                    const float4 b = cb[j], sw = cw[j], so = co[j];
-                                    const float v0 = fmaxf(__uint_as_float(r32[4 * j]) * sw.x + b.x, 0.f) * so.x;
-                                    const float v1 = fmaxf(__uint_as_float(r32[4 * j + 1]) * sw.y + b.y, 0.f) * so.y;
-                                    const float v2 = fmaxf(__uint_as_float(r32[4 * j + 2]) * sw.z + b.z, 0.f) * so.z;
-                                    const float v3 = fmaxf(__uint_as_float(r32[4 * j + 3]) * sw.w + b.w, 0.f) * so.w;
-                                    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
-                                    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
-                                    w[j] = (lo & 0xffffu) | (hi << 16);
-                                }
-#pragma unroll
-                                for (int j = 0; j < 2; j++) {
-                                    const int k = kb + bi * 32 + 16 * j;
-                                    const uint32_t off = base + (uint32_t)(k >> 7) * pstride + (uint32_t)row * 128u +
-                                                         ((uint32_t)(((k >> 4) & 7) ^ (row & 7)) << 4);
-                                    if (valid)
-                                        *reinterpret_cast<uint4 *>(sm + off) =
-                                            make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-                                }
-                                continue;
-                            }
-                            // bias four channels to a load; ReLU on the rounded pairs (rounding to
-                            // nearest keeps the sign, so this equals rounding the ReLU output)
-                            const float4 *cb = reinterpret_cast<const float4 *>(s_cb + l * C + c0 + bi * 32);
-                            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
-                            uint32_t w[16];
-#pragma unroll
-                            for (int j = 0; j < 8; j++) {
-                                const float4 b = cb[j];
-                                __nv_bfloat162 p0 = __floats2bfloat162_rn(__uint_as_float(r32[4 * j]) + b.x,
-                                                                          __uint_as_float(r32[4 * j + 1]) + b.y);
-                                __nv_bfloat162 p1 = __floats2bfloat162_rn(__uint_as_float(r32[4 * j + 2]) + b.z,
-                                                                          __uint_as_float(r32[4 * j + 3]) + b.w);
-                                p0 = __hmax2(p0, zero2);
-                                p1 = __hmax2(p1, zero2);
-                                w[2 * j] = *reinterpret_cast<uint32_t *>(&p0);
-                                w[2 * j + 1] = *reinterpret_cast<uint32_t *>(&p1);
-                            }
-#pragma unroll
-                            for (int j = 0; j < 4; j++) {
-                                const int k = kb + bi * 32 + 8 * j;
-                                const uint32_t off = base + (uint32_t)(k >> 6) * pstride + (uint32_t)row * 128u +
-                                                     ((uint32_t)(((k >> 3) & 7) ^ (row & 7)) << 4);
-                                if (valid)
-                                    *reinterpret_cast<uint4 *>(sm + off) =
-                                        make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-                            }
-                        }
-                    }
-                    fence_async_smem();
+                    // the first channel half, handed to the MMA warp (and its complete FC1
+                    // panels to the peers) while the second is converted
+                    if (ok) epi(l, P, 0);
                     tc_fence_before();
-                    if (!last) {
+                    signal(B_HA);
+                    if (last) {
                         workers_sync();
-                    } else {
+                        if (ok && kSplit && EPP < C) send_rows(P, 0);
+                    }
+                    if (ok) epi(l, P, 1);
+                    tc_fence_before();
+                    signal(B_HB);
+                    if (last) {
                         if (tid >= 128 && tid < 128 + HN) cp_wait<0>();   // S[e] landed (read after the barrier)
-                        if (prof) pacc[17] += (uint64_t)clock64() - tp;   // last conv epilogue (thread 0's share)
                         workers_sync();   // this CTA's rows of the pass are all in its own buffer
-                        const uint64_t tx0 = prof ? (uint64_t)clock64() : 0;
-                        // this CTA's rows (written and fenced to the async proxy above) to every
-                        // peer: one bulk copy per 64-column panel and peer, counted on the peer's
-                        // B_FULL + panel; a peer overwrites its copy only after B_EMPTY, i.e. after
-                        // every CTA's FC1 of this pass, which waited for all of its copies
-                        const int np = P * C / EPP;
-                        // one warp per peer (warps 1..CS-1: the copies take ~1 us to issue, which
-                        // warp 0's MMA thread spends on FC1 instead)
-                        if (ok && lane == 0 && wi >= 1 && wi < CS) {
-                            const uint32_t peer = (rank + (uint32_t)wi) % CS;
-                            for (int i = 0; i < np; i++) {
-                                const uint32_t src = fc0 + (uint32_t)i * 16384u + rank * kRowBytes;
-                                cl_bulk_copy(cl_map(src, peer), src, kRowBytes, cl_map(bar(B_FULL + i), peer));
-                            }
-                            xs[X_ROWS_SENT + wi] = (int)R + 1;   // what this warp sent its peer
-                            xs[X_ROWS_NP + wi] = np;
-                        }
-                        // FC1 over this pass's positions, each panel once every CTA's rows of it
-                        // are in (warp 2): the MMAs of the first panels overlap later copies
-                        if (wi == 0 && mma_ok) {
-                            const uint64_t tw = prof ? (uint64_t)clock64() : 0;
-                            if (prof) pacc[16] += tw - tx0;   // own rows to every peer (issue)
-                            fence_async_smem();
-                            const uint32_t ID = idesc_rt(HN, F8), d = tmem_base + 384u;
-                            for (int p0 = 0; p0 < np && mma_ok; p0 += kFcPer) {
-                                int s;
-                                if (!take(s, L)) { mma_ok = false; break; }
-                                const int n = min(kFcPer, np - p0);
-                                for (int j = 0; j < n; j++) {
-                                    const int pi = p0 + j;
-                                    const uint64_t tf = prof ? (uint64_t)clock64() : 0;
-                                    const bool in = note(cl_wait(bar(B_FULL + pi), (fph >> pi) & 1u, lim, abort_f, a.status), 7, t, R);
-                                    if (!__all_sync(0xffffffffu, in)) {
-                                        mma_ok = false;
-                                        break;
-                                    }
-                                    fph ^= 1u << pi;
-                                    if (lane == 0) {
-                                        xs[X_FPH] = (int)fph;
-                                        xs[X_FC1_WAITED] = pi + 1;
-                                    }
-                                    if (prof) pacc[18] += (uint64_t)clock64() - tf;
-                                    const uint64_t ad = sdesc(fc0 + (uint32_t)pi * 16384u),
-                                                   bd = sdesc(ring0 + (uint32_t)s * kStage + (uint32_t)j * (uint32_t)(HN * 128));
-#pragma unroll
-                                    for (int k = 0; k < 4; k++)
-                                        umma_warp<F8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID,
-                                                      (q0 | pi | k) != 0 ? 1u : 0u);
-                                }
-                                if (!mma_ok) break;
-                                umma_commit_warp(bar(S + s));
-                                adv();
-                            }
-                            if (mma_ok) {   // warp 1 tells every CTA once these MMAs are done
-                                umma_commit_warp(bar(B_F1D));
-                                if (lane == 0) {
-                                    xs[X_F1C] = xs[X_F1C] + 1;
-                                    xs[X_ROWS_DONE] = (int)R + 1;
-                                    xs[X_FC1_WAITED] = 0;
-                                }
-                            }
-                            if (prof) pacc[19] += (uint64_t)clock64() - tw;   // FC1 wait + issue
-                        }
+                        if (ok) send_rows(P, 1);
                         __syncwarp();
                         R++;
                     }
                     mark(3 + 2 * l);
                 }
             }
-            if (wi == 0 && mma_ok) umma_commit_warp(bar(B_DFC));
-            __syncwarp();
             // FC1 epilogue: ReLU(FC1 + bias + S[e]) folded into FC2 partials per slot
             {
                 bool ok = note(sleep_wait(bar(B_DFC), (uint32_t)(t & 1), lim, abort_f, a.status, false), 8, t, R);
@@ -1193,13 +1371,6 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 mark(12);
             }
         }
-        if (tid == 0) {   // every MMA done before TMEM is released
-            cnt[1] = it;
-            __threadfence_block();
-            xs[X_DONE] = 1;   // no more FC1 commits: warp 1 stops once it has signalled them all
-            umma_commit(bar(B_FIN));
-            drain_wait(bar(B_FIN), 0u, drain_ns);
-        }
         // state back to device memory (resumable), outstanding record copies drained; the
         // barrier orders the last step's head (warp 2) before the other warps read its state
         cp_wait<0>();
@@ -1266,7 +1437,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // Extents: phases of the steps after the last one consumed (armed two ahead);
         // partial sums: the step after the last one consumed; rows: the pass after the
         // last one whose FC1 read them all (peers send a pass only after every CTA's
-        // FC1 of the previous one), from the first panel not yet read.
+        // FC1 of the previous one), every panel whose phase the FC1 MMAs did not wait for.
         const int tc = xs[X_EXT_CONS];
         for (int st = tc; st < tc + 2; st++) {
             uint32_t got = 0;
@@ -1291,8 +1462,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             }
         const bool armed = xs[X_ARMED_R] > rc;
         if (armed) np = xs[X_ARMED_NP];
-        const uint32_t fph_now = (uint32_t)xs[X_FPH];
-        for (int i = armed ? xs[X_FC1_WAITED] : 0; i < np; i++) {
+        const uint32_t fph_now = (uint32_t)xs[X_FPH], waited = armed ? (uint32_t)xs[X_FC1_WAITED] : 0u;
+        for (int i = 0; i < np; i++) {
+            if ((waited >> i) & 1u) continue;   // its phase completed in the FC1 MMAs
             const uint32_t b = bar(B_FULL + i);
             if (armed) {
                 const uint32_t missing = (uint32_t)(CS - 1 - senders) * kRowBytes;

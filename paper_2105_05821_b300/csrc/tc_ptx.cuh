@@ -134,6 +134,27 @@ __device__ __forceinline__ void umma_warp(uint32_t tmem_d, uint64_t a, uint64_t 
             "l"(a), "l"(b), "r"(id), "r"(accum));
     }
 }
+// Low word of sdesc(saddr); the high word (stride 1024, version, 128-byte swizzle) is
+// kSdescHi for every operand of these kernels.
+__device__ __forceinline__ uint32_t sdesc_lo(uint32_t saddr) { return ((saddr & 0x3FFFFu) >> 4) | (1u << 16); }
+constexpr uint32_t kSdescHi = (1024u >> 4) | (1u << 14) | (2u << 29);
+// umma_warp on descriptors given by their low words (32-bit arithmetic on the issue path).
+template <bool FP8>
+__device__ __forceinline__ void umma_lo(uint32_t tmem_d, uint32_t a_lo, uint32_t b_lo, uint32_t id, uint32_t accum) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n .reg .pred e, p;\n .reg .b64 da, db;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %5};\n"
+            " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+            "r"(a_lo), "r"(b_lo), "r"(id), "r"(accum), "n"(kSdescHi));
+    } else {
+        asm volatile(
+            "{\n .reg .pred e, p;\n .reg .b64 da, db;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %5};\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+            "r"(a_lo), "r"(b_lo), "r"(id), "r"(accum), "n"(kSdescHi));
+    }
+}
 // Commit from a converged warp (one elected lane).
 __device__ __forceinline__ void umma_commit_warp(uint32_t bar) {
     asm volatile(
