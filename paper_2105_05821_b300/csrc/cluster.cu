@@ -392,12 +392,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     constexpr uint32_t kRowBytes = SPC * 128;   // one CTA's rows of one exchanged 64-column panel
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
     float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
-    float *s_Se = s_fb + HN;                                 // [HN] S[e] of the current step
+    float *s_Se = s_fb + HN;                                 // [HN] S[e] of the current step (+ FC1 bias)
     float *s_b2 = s_Se + HN;                                 // [24] FC2 bias
     float *s_w2 = s_b2 + 24;                                 // FC2 rows for this CTA's neurons
     float *s_w2f = s_w2, *s_w2e = s_w2 + HN;                 // regression: [2][HN]; hybrid: [HN][24]
     float *s_ws = s_w2 + (NO == 2 ? 2 * HN : NO == 3 ? 3 * HN : 24 * HN);   // FP8: [L][C] weight scales
-    float *s_os = s_ws + L * C;                                  // FP8: [L][C] requantisation
+    float *s_os = s_ws + L * C;                                  // FP8: [L][C] requantisation (folded into s_ws, s_cb)
     float *s_fws = s_os + L * C;                                 // FP8: [HN] FC1 weight scales
     int64_t *s_o = reinterpret_cast<int64_t *>(sm + y.slot);
     int32_t *s_b = reinterpret_cast<int32_t *>(s_o + SPC), *s_n = s_b + SPC, *s_p = s_n + SPC,
@@ -460,8 +460,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     for (int i = threadIdx.x; i < L * C; i += blockDim.x) {
         s_cb[i] = a.cbias[i / C][i % C];
         if constexpr (F8) {
-            s_ws[i] = a.cws[i / C][i % C];
-            s_os[i] = a.cos[i / C][i % C];
+            // the requantisation multiplier (1 / the next layer's input scale, positive)
+            // folded in: ReLU(acc w + b) m = ReLU(acc (w m) + b m)
+            const float m = a.cos[i / C][i % C];
+            s_ws[i] = a.cws[i / C][i % C] * m;
+            s_cb[i] *= m;
+            s_os[i] = m;
         }
     }
     for (int j = threadIdx.x; j < HN; j += blockDim.x) {
@@ -964,20 +968,20 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 if constexpr (CW == 32) tmem_ld32(ta, r);
                 else tmem_ld16(ta, r);
                 if constexpr (F8) {
-                    // dequantise (weight scale), bias, ReLU, requantise to the next layer's
-                    // input scale, e4m3 with saturation: 16 channels a chunk
+                    // dequantise (weight scale), bias, ReLU and requantise to the next layer's
+                    // input scale in one FMA (the scale folded into the weight scale and the
+                    // bias at the start), e4m3 with saturation: 16 channels a chunk
                     const int cc = l * C + cb;
                     const float4 *cbv = reinterpret_cast<const float4 *>(s_cb + cc);
                     const float4 *cw = reinterpret_cast<const float4 *>(s_ws + cc);
-                    const float4 *co = reinterpret_cast<const float4 *>(s_os + cc);
                     uint32_t w[CW / 4];
 #pragma unroll
                     for (int j = 0; j < CW / 4; j++) {
-                        const float4 b = cbv[j], sw = cw[j], so = co[j];
-                        const float v0 = fmaxf(__uint_as_float(r[4 * j]) * sw.x + b.x, 0.f) * so.x;
-                        const float v1 = fmaxf(__uint_as_float(r[4 * j + 1]) * sw.y + b.y, 0.f) * so.y;
-                        const float v2 = fmaxf(__uint_as_float(r[4 * j + 2]) * sw.z + b.z, 0.f) * so.z;
-                        const float v3 = fmaxf(__uint_as_float(r[4 * j + 3]) * sw.w + b.w, 0.f) * so.w;
+                        const float4 b = cbv[j], sw = cw[j];
+                        const float v0 = fmaxf(__uint_as_float(r[4 * j]) * sw.x + b.x, 0.f);
+                        const float v1 = fmaxf(__uint_as_float(r[4 * j + 1]) * sw.y + b.y, 0.f);
+                        const float v2 = fmaxf(__uint_as_float(r[4 * j + 2]) * sw.z + b.z, 0.f);
+                        const float v3 = fmaxf(__uint_as_float(r[4 * j + 3]) * sw.w + b.w, 0.f);
                         const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v0, v1), __NV_SATFINITE, __NV_E4M3);
                         const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v2, v3), __NV_SATFINITE, __NV_E4M3);
                         w[j] = (lo & 0xffffu) | (hi << 16);
@@ -1106,7 +1110,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     tc_fence_before();
                     signal(B_HB);
                     if (last) {
-                        if (tid >= 128 && tid < 128 + HN) cp_wait<0>();   // S[e] landed (read after the barrier)
+                        if (tid >= 128 && tid < 128 + HN) {   // S[e] landed; FC1's bias added once a step
+                            cp_wait<0>();
+                            if (q0 == 0) s_Se[tid - 128] += s_fb[tid - 128];
+                        }
                         workers_sync();   // this CTA's rows of the pass are all in its own buffer
                         if (ok) send_rows(P, 1);
                         __syncwarp();
@@ -1134,9 +1141,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 #pragma unroll
                         for (int bi = 0; bi < 2; bi++) {
                             if (bi >= cols / 32) break;
-                            // bias, S[e] and FC2 rows four neurons to a load
+                            // bias + S[e] and FC2 rows four neurons to a load
                             const int jb = j0 + bi * 32;
-                            const float4 *fb4 = reinterpret_cast<const float4 *>(s_fb + jb);
                             const float4 *se4 = reinterpret_cast<const float4 *>(s_Se + jb);
                             const float4 *wf4 = reinterpret_cast<const float4 *>(s_w2f + jb);
                             const float4 *we4 = reinterpret_cast<const float4 *>(s_w2e + jb);
@@ -1144,11 +1150,11 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             const float4 *fw4 = reinterpret_cast<const float4 *>(s_fws + jb);            // FP8 only
 #pragma unroll
                             for (int q = 0; q < 8; q++) {
-                                const float4 fb = fb4[q], se = se4[q], wf = wf4[q], we = we4[q];
+                                const float4 se = se4[q], wf = wf4[q], we = we4[q];
                                 float4 wsv = make_float4(0.f, 0.f, 0.f, 0.f), fsc = make_float4(1.f, 1.f, 1.f, 1.f);
                                 if constexpr (SQ) wsv = ws4[q];
                                 if constexpr (F8) fsc = fw4[q];
-                                const float bb[4] = {fb.x + se.x, fb.y + se.y, fb.z + se.z, fb.w + se.w};
+                                const float bb[4] = {se.x, se.y, se.z, se.w};
                                 const float wfa[4] = {wf.x, wf.y, wf.z, wf.w}, wea[4] = {we.x, we.y, we.z, we.w};
                                 const float wsa[4] = {wsv.x, wsv.y, wsv.z, wsv.w}, fsa[4] = {fsc.x, fsc.y, fsc.z, fsc.w};
 #pragma unroll
@@ -1172,7 +1178,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                             for (int jj = 0; jj < 16; jj++) {
                                 const int j = j0 + bi * 16 + jj;
                                 const float acc = __uint_as_float(r32[jj]) * (F8 ? s_fws[j] : 1.f);
-                                const float v = fmaxf(acc + s_fb[j] + s_Se[j], 0.f);
+                                const float v = fmaxf(acc + s_Se[j], 0.f);
                                 const float4 *wv = reinterpret_cast<const float4 *>(s_w2 + j * 24);
 #pragma unroll
                                 for (int q4 = 0; q4 < 6; q4++) {
@@ -1290,22 +1296,37 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     // queue then retires in order, with no limit, every store whose residence
                     // has reached its S
                     auto retire = [&](int lim_n) {
+                        // four entries a round: their loads are independent and overlap, the
+                        // tests then run in order (a ring load costs ~30 cycles, a round of
+                        // one entry ~50)
                         int k = 0;
-                        while (k < lim_n) {
-                            int idx = qs + k;
-                            if (idx >= cap) idx -= cap;
-                            const uint64_t v = qr[idx];
-                            const int32_t res = entry_res(v, tick), e = (int32_t)entry_e(v);
-                            if (strict ? res <= e : res < e) break;
-                            if constexpr (SQ) {
-                                if (rec_is_store(entry_rec(v))) {
-                                    int mi = ms + ml;
-                                    if (mi >= cap) mi -= cap;
-                                    mr[mi] = v;
-                                    ml++;
-                                }
+                        bool blocked = false;
+                        while (k < lim_n && !blocked) {
+                            uint64_t v[4];
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                int idx = qs + k + u;   // below 2 cap for the entries tested
+                                if (idx >= cap) idx -= cap;
+                                v[u] = qr[min(idx, cap - 1)];
                             }
-                            k++;
+#pragma unroll
+                            for (int u = 0; u < 4; u++) {
+                                if (blocked || k >= lim_n) break;
+                                const int32_t res = entry_res(v[u], tick), e = (int32_t)entry_e(v[u]);
+                                if (strict ? res <= e : res < e) {
+                                    blocked = true;
+                                    break;
+                                }
+                                if constexpr (SQ) {
+                                    if (rec_is_store(entry_rec(v[u]))) {
+                                        int mi = ms + ml;
+                                        if (mi >= cap) mi -= cap;
+                                        mr[mi] = v[u];
+                                        ml++;
+                                    }
+                                }
+                                k++;
+                            }
                         }
                         qs += k;
                         if (qs >= cap) qs -= cap;
