@@ -389,7 +389,14 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // done: CS arrivals on B_EMPTY + (R & 1) (two barriers, so that an arrival for the
     // next pass can never complete the phase of this one)
     auto b_empty = [&](int64_t r) { return bar((r & 1) ? 2 * S + 16 : 2 * S + 1); };
-    constexpr uint32_t kRowBytes = SPC * 128;   // one CTA's rows of one exchanged 64-column panel
+    // The FC1 operand is exchanged in units: its 128-byte panels (one CTA's rows of one:
+    // SPC x 128 bytes), or, for FP8 with 128 channels (a panel is one position), half panels
+    // of 64-byte rows with 64-byte swizzle, one per position and channel half, so that the
+    // first channel half travels while the second is converted.
+    const bool hfc = F8 && C == 128;
+    const uint32_t xbytes = hfc ? (uint32_t)SPC * 64u : (uint32_t)SPC * 128u;   // one CTA's rows of a unit
+    const uint32_t xstride = hfc ? 8192u : 16384u;                             // between units
+    auto xunits = [&](int P) { return hfc ? 2 * P : P * C / EPP; };
     float *s_cb = reinterpret_cast<float *>(sm + y.prm);   // [L][C] conv biases
     float *s_fb = s_cb + L * C;                              // [HN] FC1 bias of this CTA's neurons
     float *s_Se = s_fb + HN;                                 // [HN] S[e] of the current step (+ FC1 bias)
@@ -745,7 +752,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // FC1 over a pass's positions: per panel once every CTA's rows of it are in; with the
         // split (every FC1 stage of the pass held at once) the first channel half's K-steps first
         auto fc1 = [&](int q0, int P, int64_t t) -> bool {
-            const int np = P * C / EPP, G = (np + kFcPer - 1) / kFcPer;
+            const int np = P * C / EPP, G = (np + kFcPer - 1) / kFcPer;   // weight panels (positions for FP8)
             const bool split = kSplit && G <= S;
             const int fmask = kFcPer - 1, fshift = __ffs(kFcPer) - 1;   // kFcPer is a power of two
             const uint32_t ID = idesc_rt(HN, F8), d = tmem_base + 384u;
@@ -777,7 +784,52 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                        fresh);
                 return true;
             };
-            if (!split) {
+            if (hfc) {
+                // FP8, 128 channels: half panel 2 pi + h (64-byte rows) against K-steps 2h, 2h + 1
+                // of weight panel pi
+                auto hpanel = [&](int pi, int h) -> bool {
+                    const int g = pi >> fshift, j = pi & fmask, u = 2 * pi + h;
+                    while (taken <= g) {
+                        int s;
+                        if (!take(s, L)) return false;
+                        slots |= (uint64_t)s << (8 * taken);
+                        taken++;
+                    }
+                    const uint64_t tf = prof ? (uint64_t)clock64() : 0;
+                    const bool in = note(cl_wait(bar(B_FULL + u), (fph >> u) & 1u, lim, abort_f, a.status), 7, t, R);
+                    if (!__all_sync(0xffffffffu, in)) return false;
+                    fph ^= 1u << u;
+                    if (lane == 0) {
+                        xs[X_FPH] = (int)fph;
+                        xs[X_FC1_WAITED] = xs[X_FC1_WAITED] | (1 << u);
+                    }
+                    if (prof) pacc[18] += (uint64_t)clock64() - tf;
+                    const uint32_t s = (uint32_t)(slots >> (8 * g)) & 0xffu;
+                    const uint32_t alo = fc_lo + (uint32_t)u * 512u, blo = ring_lo + (s * kStage >> 4) + (uint32_t)j * hstep + 4u * (uint32_t)h;
+                    umma_lo_a<F8>(d, alo, kSdescHi64, blo, ID, fresh ? 0u : 1u);
+                    fresh = false;
+                    umma_lo_a<F8>(d, alo + 2u, kSdescHi64, blo + 2u, ID, 1u);
+                    return true;
+                };
+                const bool hold = G <= S;   // every stage held until the second half, else both halves at once
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20)) return false;
+                    if (!hold && h == 0) continue;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    for (int pi = 0; pi < P; pi++) {
+                        if (hold) {
+                            if (!hpanel(pi, h)) return false;
+                        } else {
+                            if (!hpanel(pi, 0) || !hpanel(pi, 1)) return false;
+                            if (pi + 1 == P || ((pi + 1) & fmask) == 0)
+                                umma_commit_warp(bar(S + (int)((slots >> (8 * (pi >> fshift))) & 0xffu)));
+                        }
+                    }
+                    if (prof) pacc[19] += (uint64_t)clock64() - ti;
+                }
+                if (hold)
+                    for (int g = 0; g < taken; g++) umma_commit_warp(bar(S + (int)((slots >> (8 * g)) & 0xffu)));
+            } else if (!split) {
                 if (!wait_sig(B_HA, ph_ha, 12, t, 20) || !wait_sig(B_HB, ph_hb, 13, t, 20)) return false;
                 const uint64_t ti = prof ? (uint64_t)clock64() : 0;
                 for (int pi = 0; pi < np; pi++) {
@@ -811,9 +863,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             return true;
         };
         auto arm_rows = [&](int P) {   // lane 0: the peers' rows of pass R, all panels
-            for (int i = 0; i < P * C / EPP; i++) mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * kRowBytes);
+            for (int i = 0; i < xunits(P); i++) mbar_expect_tx(bar(B_FULL + i), (uint32_t)(CS - 1) * xbytes);
             xs[X_ARMED_R] = (int)R + 1;
-            xs[X_ARMED_NP] = P * C / EPP;
+            xs[X_ARMED_NP] = xunits(P);
         };
         const int P0 = min(PM, a.rows_n);
         for (int64_t t = 0; t < a.n_steps && ok; t++) {
@@ -989,8 +1041,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
 #pragma unroll
                     for (int j = 0; j < CW / 16; j++) {
                         const int k = kb + 16 * j;
-                        const uint32_t off = base + (uint32_t)(k >> 7) * pstride + (uint32_t)row * 128u +
-                                             ((uint32_t)(((k >> 4) & 7) ^ (row & 7)) << 4);
+                        // FC1 operand with 128 channels: half panels of 64-byte rows (64-byte swizzle)
+                        const uint32_t off = last && hfc
+                                                 ? base + (uint32_t)(k >> 6) * 8192u + (uint32_t)row * 64u +
+                                                       ((uint32_t)(((k >> 4) & 3) ^ ((row >> 1) & 3)) << 4)
+                                                 : base + (uint32_t)(k >> 7) * pstride + (uint32_t)row * 128u +
+                                                       ((uint32_t)(((k >> 4) & 7) ^ (row & 7)) << 4);
                         if (valid)
                             *reinterpret_cast<uint4 *>(sm + off) = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
                     }
@@ -1034,12 +1090,13 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         auto send_rows = [&](int P, int h) {
             if (lane != 0 || wi < 1 || wi >= CS) return;
             const uint32_t peer = (rank + (uint32_t)wi) % CS;
-            const int np = P * C / EPP;
+            const int np = xunits(P);
             for (int i = 0; i < np; i++) {
-                // panels half a row wide: the even ones are complete after the first half
-                if (kSplit && EPP < C ? (i & 1) != h : h == 0) continue;
-                const uint32_t src = fc0 + (uint32_t)i * 16384u + rank * kRowBytes;
-                cl_bulk_copy(cl_map(src, peer), src, kRowBytes, cl_map(bar(B_FULL + i), peer));
+                // units half a row wide (BF16 panels, FP8 half panels): the even ones are
+                // complete after the first half
+                if ((kSplit && EPP < C) || hfc ? (i & 1) != h : h == 0) continue;
+                const uint32_t src = fc0 + (uint32_t)i * xstride + rank * xbytes;
+                cl_bulk_copy(cl_map(src, peer), src, xbytes, cl_map(bar(B_FULL + i), peer));
             }
             if (h == 1) {
                 xs[X_ROWS_SENT + wi] = (int)R + 1;   // what this warp sent its peer
@@ -1104,7 +1161,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     signal(B_HA);
                     if (last) {
                         workers_sync();
-                        if (ok && kSplit && EPP < C) send_rows(P, 0);
+                        if (ok && ((kSplit && EPP < C) || hfc)) send_rows(P, 0);
                     }
                     if (ok) epi(l, P, 1);
                     tc_fence_before();
@@ -1488,10 +1545,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             if ((waited >> i) & 1u) continue;   // its phase completed in the FC1 MMAs
             const uint32_t b = bar(B_FULL + i);
             if (armed) {
-                const uint32_t missing = (uint32_t)(CS - 1 - senders) * kRowBytes;
+                const uint32_t missing = (uint32_t)(CS - 1 - senders) * xbytes;
                 if (missing) mbar_complete_tx(b, missing);
             } else if (senders > 0) {
-                mbar_expect_tx(b, (uint32_t)senders * kRowBytes);
+                mbar_expect_tx(b, (uint32_t)senders * xbytes);
             } else {
                 continue;
             }

@@ -155,6 +155,27 @@ __device__ __forceinline__ void umma_lo(uint32_t tmem_d, uint32_t a_lo, uint32_t
             "r"(a_lo), "r"(b_lo), "r"(id), "r"(accum), "n"(kSdescHi));
     }
 }
+// High word of a descriptor of a K-major operand with 64-byte rows, 64-byte swizzle
+// (8-row groups 512 bytes apart); its low word is sdesc_lo of the start address.
+constexpr uint32_t kSdescHi64 = (512u >> 4) | (1u << 14) | (4u << 29);
+// umma_lo with A's high word given (A with 64-byte swizzle, B with 128-byte swizzle).
+template <bool FP8>
+__device__ __forceinline__ void umma_lo_a(uint32_t tmem_d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t id,
+                                          uint32_t accum) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n .reg .pred e, p;\n .reg .b64 da, db;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %6};\n"
+            " @e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+            "r"(a_lo), "r"(b_lo), "r"(id), "r"(accum), "r"(a_hi), "n"(kSdescHi));
+    } else {
+        asm volatile(
+            "{\n .reg .pred e, p;\n .reg .b64 da, db;\n elect.sync _|e, 0xffffffff;\n setp.ne.b32 p, %4, 0;\n"
+            " mov.b64 da, {%1, %5};\n mov.b64 db, {%2, %6};\n"
+            " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %3, p;\n}\n" ::"r"(tmem_d),
+            "r"(a_lo), "r"(b_lo), "r"(id), "r"(accum), "r"(a_hi), "n"(kSdescHi));
+    }
+}
 // Commit from a converged warp (one elected lane).
 __device__ __forceinline__ void umma_commit_warp(uint32_t bar) {
     asm volatile(
