@@ -662,6 +662,16 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 umma_lo<F8>(d, alo + 6u, blo + 6u, ID, 1u);
             }
         };
+        // Straight-line issue of the K-steps of one or two panels: loops with run-time trip
+        // counts between the MMAs cost this warp more than the MMAs themselves take.
+        auto mma2 = [&](uint32_t d, uint32_t alo, uint32_t blo, uint32_t ID, uint32_t acc0) {
+            umma_lo<F8>(d, alo, blo, ID, acc0);
+            umma_lo<F8>(d, alo + 2u, blo + 2u, ID, 1u);
+        };
+        auto mma4 = [&](uint32_t d, uint32_t alo, uint32_t blo, uint32_t ID, uint32_t acc0) {
+            mma2(d, alo, blo, ID, acc0);
+            mma2(d, alo + 4u, blo + 4u, ID, 1u);
+        };
         const uint32_t act_lo = sdesc_lo(act0), ring_lo = sdesc_lo(ring0), fc_lo = sdesc_lo(fc0);
         const uint32_t cstep = (uint32_t)(C * 128) >> 4, hstep = (uint32_t)(HN * 128) >> 4;
         // the first layer over a pass's rows (all K-steps: the rows are built whole)
@@ -669,6 +679,16 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             const int T = tiles_of(0, P), np = panels_of(0), G = conv_stages(0);
             const uint32_t ID = idesc_rt(C, F8), astep = pstride_of(0, P) >> 4;
             bool f0 = true, f1 = true;
+            if (G == 1 && T == 1 && np <= 2) {   // one stage, one tile (c2's shapes): straight line
+                int s;
+                if (!take(s, 0)) return false;
+                const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4);
+                mma4(tmem_base, act_lo, b0, ID, 0u);
+                if (np == 2) mma4(tmem_base, act_lo + astep, b0 + cstep, ID, 1u);
+                umma_commit_warp(bar(S + s));
+                umma_commit_warp(bar(B_D));
+                return true;
+            }
             for (int g = 0; g < G; g++) {
                 int s;
                 if (!take(s, 0)) return false;
@@ -704,6 +724,33 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     umma_commit_warp(bar(S + s));
                 }
                 if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
+            } else if (EPP < C && kConvPer == 2 && np == 4) {
+                // BF16, 128 channels, 32 KB stages (c2): per half one stage of panels h, 2 + h
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20 + l)) return false;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    int s;
+                    if (!take(s, l)) return false;
+                    const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4), a0 = act_lo + (uint32_t)h * astep;
+                    mma4(d, a0, b0, ID, h ? 1u : 0u);
+                    mma4(d, a0 + 2u * astep, b0 + cstep, ID, 1u);
+                    umma_commit_warp(bar(S + s));
+                    if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
+                }
+            } else if (EPP == C && G == 1 && np == 2) {
+                // one stage of two row-wide panels (FP8 with 128 channels, BF16 with 64): K-steps
+                // 0-1 of both panels for the first half, 2-3 for the second
+                int s = 0;
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20 + l)) return false;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    if (h == 0 && !take(s, l)) return false;
+                    const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4) + 4u * (uint32_t)h, a0 = act_lo + 4u * (uint32_t)h;
+                    mma2(d, a0, b0, ID, h ? 1u : 0u);
+                    mma2(d, a0 + astep, b0 + cstep, ID, 1u);
+                    if (h == 1) umma_commit_warp(bar(S + s));
+                    if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
+                }
             } else if (EPP < C) {
                 // panels half a row wide (BF16, 128 channels): the stages of the first half hold
                 // the even panels (rows 2j, 2j+1, channels 0-63), those of the second the odd ones
