@@ -831,7 +831,48 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                        fresh);
                 return true;
             };
-            if (hfc) {
+            // exchange unit u: the peers' rows of it are in
+            auto unit_in = [&](int u) -> bool {
+                const uint64_t tf = prof ? (uint64_t)clock64() : 0;
+                const bool in = note(cl_wait(bar(B_FULL + u), (fph >> u) & 1u, lim, abort_f, a.status), 7, t, R);
+                if (!__all_sync(0xffffffffu, in)) return false;
+                fph ^= 1u << u;
+                if (lane == 0) {
+                    xs[X_FPH] = (int)fph;
+                    xs[X_FC1_WAITED] = xs[X_FC1_WAITED] | (1 << u);
+                }
+                if (prof) pacc[18] += (uint64_t)clock64() - tf;
+                return true;
+            };
+            if (G == 1 && P == 2 && (hfc || (split && EPP < C && np == 4))) {
+                // c2's shapes, one weight stage, straight line: per channel half the two units of
+                // that half (BF16: panels h and 2 + h; FP8: half panels h and 2 + h against
+                // K-steps 2h, 2h + 1 of weight panels 0 and 1)
+                int s = 0;
+                for (int h = 0; h < 2; h++) {
+                    if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20)) return false;
+                    const uint64_t ti = prof ? (uint64_t)clock64() : 0;
+                    if (h == 0 && !take(s, L)) return false;
+                    const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4);
+                    const uint32_t acc0 = (h == 0 && fresh) ? 0u : 1u;
+                    if (hfc) {
+                        if (!unit_in(h)) return false;
+                        umma_lo_a<F8>(d, fc_lo + 512u * (uint32_t)h, kSdescHi64, b0 + 4u * (uint32_t)h, ID, acc0);
+                        umma_lo_a<F8>(d, fc_lo + 512u * (uint32_t)h + 2u, kSdescHi64, b0 + 4u * (uint32_t)h + 2u, ID, 1u);
+                        if (!unit_in(2 + h)) return false;
+                        const uint32_t a1 = fc_lo + 512u * (uint32_t)(2 + h), b1 = b0 + hstep + 4u * (uint32_t)h;
+                        umma_lo_a<F8>(d, a1, kSdescHi64, b1, ID, 1u);
+                        umma_lo_a<F8>(d, a1 + 2u, kSdescHi64, b1 + 2u, ID, 1u);
+                    } else {
+                        if (!unit_in(h)) return false;
+                        mma4(d, fc_lo + 1024u * (uint32_t)h, b0 + (uint32_t)h * hstep, ID, acc0);
+                        if (!unit_in(2 + h)) return false;
+                        mma4(d, fc_lo + 1024u * (uint32_t)(2 + h), b0 + (uint32_t)(2 + h) * hstep, ID, 1u);
+                    }
+                    if (prof) pacc[19] += (uint64_t)clock64() - ti;
+                }
+                umma_commit_warp(bar(S + s));
+            } else if (hfc) {
                 // FP8, 128 channels: half panel 2 pi + h (64-byte rows) against K-steps 2h, 2h + 1
                 // of weight panel pi
                 auto hpanel = [&](int pi, int h) -> bool {
