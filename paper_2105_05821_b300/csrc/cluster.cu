@@ -1172,12 +1172,14 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             else epilogue(std::integral_constant<int, 16>{}, l, P, h);
         };
         // this CTA's rows of the pass's FC1 panels of channel half h (all panels when a panel
-        // spans both halves: h = 1 only) to every peer, one warp per peer: one bulk copy per
-        // panel, counted on the peer's B_FULL + panel; a peer overwrites its copy only after
-        // B_EMPTY, i.e. after every CTA's FC1 of this pass, which waited for all of its copies
+        // spans both halves: h = 1 only) to every peer: lane j of worker warp 0 (whose TMEM
+        // lanes hold no rows of a last layer with at most 96 rows) sends to peer rank + j, one
+        // bulk copy per unit, counted on the peer's B_FULL + unit; a peer overwrites its copy
+        // only after B_EMPTY, i.e. after every CTA's FC1 of this pass, which waited for all of
+        // its copies
         auto send_rows = [&](int P, int h) {
-            if (lane != 0 || wi < 1 || wi >= CS) return;
-            const uint32_t peer = (rank + (uint32_t)wi) % CS;
+            if (wi != 0 || lane < 1 || lane >= CS) return;
+            const uint32_t peer = (rank + (uint32_t)lane) % CS;
             const int np = xunits(P);
             for (int i = 0; i < np; i++) {
                 // units half a row wide (BF16 panels, FP8 half panels): the even ones are
@@ -1187,8 +1189,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 cl_bulk_copy(cl_map(src, peer), src, xbytes, cl_map(bar(B_FULL + i), peer));
             }
             if (h == 1) {
-                xs[X_ROWS_SENT + wi] = (int)R + 1;   // what this warp sent its peer
-                xs[X_ROWS_NP + wi] = np;
+                xs[X_ROWS_SENT + lane] = (int)R + 1;   // what this lane sent its peer
+                xs[X_ROWS_NP + lane] = np;
             }
         };
         // The first pass always covers P0 positions: its rows need no cluster-wide extent, so
@@ -1590,7 +1592,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     // Leaving.  Every peer learns what this CTA sent it: extents and partial-sum
     // steps, and the passes (and their panel count) of row copies.
     if (threadIdx.x < CS) {
-        const int d = (int)threadIdx.x, wd = (d - (int)rank + CS) % CS;   // the warp that sends to d
+        const int d = (int)threadIdx.x, wd = (d - (int)rank + CS) % CS;   // the lane that sends to d
         const uint4 v = make_uint4((uint32_t)xs[X_EXT_SENT], (uint32_t)xs[X_PART_SENT],
                                    wd ? (uint32_t)xs[X_ROWS_SENT + wd] : 0u, wd ? (uint32_t)xs[X_ROWS_NP + wd] : 0u);
         cl_st_v4(cl_map(smem_u32(&inbox[rank]), (uint32_t)d), v);
