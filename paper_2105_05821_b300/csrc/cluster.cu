@@ -293,6 +293,16 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int cols, uint32_t 
     else tmem_ld32(taddr, r[0]);
 }
 __device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// workers_sync that also returns whether p holds in any worker thread
+__device__ __forceinline__ bool workers_any(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, 1, 256, q;\n selp.u32 %0, 1, 0, o;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -358,10 +368,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
     const int64_t lim = a.spin_ns;
     const int64_t drain_ns = lim > 200000000 ? lim : 200000000;   // 0.2 s at least
     // Record where the first expired wait of the launch was (sites: 1 weight stage free,
-    // 2 extent (producer), 3 weight panel, 4 extent (workers), 5 conv layer done, 6 exchange
+    // 2 extent (producer), 3 weight panel, 4 (unused), 5 conv layer done, 6 exchange
     // buffer free, 7 exchanged rows in, 8 FC1 done, 9 FC2 partial sums in, 10 FC1 done
     // (warp 1's signal to the cluster), 11 feature rows in, 12 / 13 first / second channel
-    // half of a layer's output in, 14 the step's extent (the MMA warp's waits)).
+    // half of a layer's output in, 14 the step's extent published by the producer).
     auto note = [&](bool ok, int site, int64_t step, int64_t pass) -> bool {
         if (!ok && *(volatile int32_t *)a.status == kStatusTimeout &&
             atomicCAS(&a.tinfo[0], 0ull, (unsigned long long)site) == 0ull) {
@@ -598,11 +608,22 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             const int pre = min(n_conv_stages, S);
             if (a.n_steps > 0) conv_loads(0, pre);
             for (int64_t t = 0; t < a.n_steps && ok; t++) {
-                if (!note(cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status), 2, t, 0)) break;
-                int E, AL;
-                read_ext<CS>(ext_in, (int)(t & 1), E, AL);
-                if (AL == 0) break;
-                const int eL = step_positions(E, L, a.rows_n, min(PM, a.rows_n), kERound);   // as the workers
+                // The step's extent (the cluster's longest context + 1, and its live count),
+                // published to the MMA warp and the workers through ctl (double-buffered by
+                // step): neither waits for the cluster's slowest head before its first layer.
+                const bool w = note(cl_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status), 2, t, 0);
+                int E = 0, AL = 0;
+                if (w) {
+                    read_ext<CS>(ext_in, (int)(t & 1), E, AL);
+                    mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
+                    xs[X_EXT_CONS] = xs[X_EXT_CONS] + 1;
+                }
+                const int eL = step_positions(E, L, a.rows_n, min(PM, a.rows_n), kERound);
+                volatile int *c = ctl + 2 * (int)(t & 1);
+                c[0] = eL;
+                c[1] = (!w || AL == 0 || *abort_f) ? 1 : 0;
+                mbar_arrive(bar(B_CTL));
+                if (c[1]) break;
                 for (int q0 = 0; q0 < eL && ok; q0 += PM) {
                     const int P = min(PM, eL - q0);
                     conv_loads(q0 > 0 ? 0 : pre, n_conv_stages);
@@ -973,8 +994,9 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 __syncwarp();
                 if (ok && q0 == 0) {   // the step's extent: positions, or the cluster is done
                     ok = wait_sig(B_CTL, ph_ctl, 14, t, 17);
-                    if (!ok || ctl[1]) { ok = false; break; }
-                    eL = ctl[0];
+                    const volatile int *c = ctl + 2 * (int)(t & 1);
+                    if (!ok || c[1]) { ok = false; break; }
+                    eL = c[0];
                 }
                 for (int l = 1; l < L && ok; l++) ok = conv_next(l, P, t);
                 if (ok) ok = fc1(q0, P, t);
@@ -1198,36 +1220,15 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         // (positions of the pass past the extent are padding rows, computed rather than taken
         // from S[e]: the same result).
         const int P0 = min(PM, a.rows_n);
-        for (int64_t t = 0; t < a.n_steps; t++) {
+        uint32_t ph_ctl = 0;
+        bool stop = false;
+        for (int64_t t = 0; t < a.n_steps && !stop; t++) {
             workers_sync();   // the previous step's head (worker warp 0) is visible
             build_rows(0, P0);
-            signal(B_ROWS);   // the MMA warp starts the first layer while the extent is awaited
-            if (tid == 0) {
-                const bool ok = note(sleep_wait(bar(B_EXT + (int)(t & 1)), (uint32_t)(t >> 1) & 1u, lim, abort_f, a.status, true), 4, t, 0);
-                int E, AL;
-                read_ext<CS>(ext_in, (int)(t & 1), E, AL);
-                if (ok) {
-                    mbar_expect_tx(bar(B_EXT + (int)(t & 1)), kExtBytes);   // its phase two steps on
-                    xs[X_EXT_CONS] = xs[X_EXT_CONS] + 1;
-                }
-                ctl[0] = step_positions(E, L, a.rows_n, P0, kERound);
-                ctl[1] = (!ok || AL == 0 || *abort_f) ? 1 : 0;
-                mbar_arrive(bar(B_CTL));   // the MMA warp reads ctl
-            }
-            workers_sync();
-            const int eL = ctl[0];
-            if (ctl[1]) break;
+            signal(B_ROWS);   // the MMA warp starts the first layer; the extent is read after it
             mark(0);
-            if (prof) { pacc[14] += 1; pacc[15] += (unsigned long long)eL; }
-            if (tid == 0 && rank == 0 && 2 * t >= a.n_steps) {   // extent needed in the launch's second half
-                atomicAdd(&a.pos_sum[0], (unsigned long long)eL);
-                atomicAdd(&a.pos_sum[1], 1ull);
-            }
-            if (tid >= 128 && tid < 128 + HN) {   // S[e] for this CTA's neurons, needed by the FC1 epilogue
-                cp_async4(smem_u32(&s_Se[tid - 128]), a.fc1_const + (size_t)eL * a.H + (int)rank * HN + (tid - 128));
-                cp_commit();
-            }
-            for (int q0 = 0; q0 < eL; q0 += PM) {
+            int eL = P0;      // the first pass's positions, whatever the extent
+            for (int q0 = 0; q0 < eL && !stop; q0 += PM) {
                 const int P = min(PM, eL - q0);   // P0 for the first pass
                 if (q0 > 0) {
                     build_rows(q0, P);
@@ -1256,6 +1257,25 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     if (ok) epi(l, P, 1);
                     tc_fence_before();
                     signal(B_HB);
+                    if (q0 == 0 && l == 0) {
+                        // the step's extent, published by the producer: positions, or the
+                        // cluster is done (then the MMA warp stops before the second layer)
+                        const bool w = note(sleep_wait(bar(B_CTL), ph_ctl, lim, abort_f, a.status, false), 14, t, R);
+                        ph_ctl ^= 1u;
+                        const volatile int *c = ctl + 2 * (int)(t & 1);
+                        stop = workers_any(!w || c[1] != 0);   // the same decision in every worker
+                        if (stop) break;
+                        eL = c[0];
+                        if (prof) { pacc[14] += 1; pacc[15] += (unsigned long long)eL; }
+                        if (tid == 0 && rank == 0 && 2 * t >= a.n_steps) {   // extent in the launch's second half
+                            atomicAdd(&a.pos_sum[0], (unsigned long long)eL);
+                            atomicAdd(&a.pos_sum[1], 1ull);
+                        }
+                        if (tid >= 128 && tid < 128 + HN) {   // S[e] of this CTA's neurons, for the FC1 epilogue
+                            cp_async4(smem_u32(&s_Se[tid - 128]), a.fc1_const + (size_t)eL * a.H + (int)rank * HN + (tid - 128));
+                            cp_commit();
+                        }
+                    }
                     if (last) {
                         if (tid >= 128 && tid < 128 + HN) {   // S[e] landed; FC1's bias added once a step
                             cp_wait<0>();
@@ -1269,6 +1289,7 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     mark(3 + 2 * l);
                 }
             }
+            if (stop) break;
             // FC1 epilogue: ReLU(FC1 + bias + S[e]) folded into FC2 partials per slot
             {
                 bool ok = note(sleep_wait(bar(B_DFC), (uint32_t)(t & 1), lim, abort_f, a.status, false), 8, t, R);
