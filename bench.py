@@ -41,8 +41,8 @@ TRAFFIC = {
     # cluster_kernel, c2: one 1,000-step call is two launches (the 128-step probe and the
     # rest), measured on the full workload; nothing is written, the working set stays on
     # chip and in L2 (profiles/cluster_kernel_c2_bf16_traffic.md, ..._fp8_traffic.md)
-    ("c2", "bf16", "cluster_kernel"): 2.191872e6 + 5.452544e6,
-    ("c2", "fp8", "cluster_kernel"): 1.805824e6 + 5.395456e6,
+    ("c2", "bf16", "cluster_kernel"): 2.256896e6 + 5.301504e6,
+    ("c2", "fp8", "cluster_kernel"): 1.857792e6 + 5.340160e6,
 }
 
 
