@@ -568,6 +568,8 @@ def cluster_phases(w, args, blob32, rec, off, sm_mhz):
         names = names[:6] + ["-", "-"] + names[8:]
     out = {n: float(d[k]) / steps / sm_mhz for k, n in enumerate(names) if n != "-"}
     out["positions_per_step"] = float(d[15]) / steps
+    # part of the last layer's wait: every CTA done reading the previous pass's exchanged rows
+    out["wait exchange buffer free"] = float(d[13]) / steps / sm_mhz
     # the MMA warp's view of the same steps (counters 16-29 of the kernel; 30-31 are the
     # workers' FC1 epilogue)
     L = w.arch.n_conv

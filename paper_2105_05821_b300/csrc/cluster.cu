@@ -292,6 +292,24 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, int cols, uint32_t 
     if (cols > 32) tmem_ld64(taddr, r);
     else tmem_ld32(taddr, r[0]);
 }
+// 16 TMEM lanes from taddr's lane x 16 columns, waited for: thread t gets lanes t/4 and
+// t/4 + 8, columns 2(t%4), 2(t%4) + 1 (r[0..3]) and those columns + 8 (r[4..7]) -- the
+// fragment layout of an 8x8 16-bit matrix per register pair (16x256b shape, two repeats).
+__device__ __forceinline__ void tmem_ld16x256b_x2(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+}
+// Four 8x8 16-bit matrices (fragments f[0..3]) stored transposed: thread 8i + j gives the
+// shared-memory address of row j of transposed matrix i (16 contiguous bytes).
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, const uint32_t (&f)[4]) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(f[0]),
+                 "r"(f[1]), "r"(f[2]), "r"(f[3])
+                 : "memory");
+}
 __device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 // workers_sync that also returns whether p holds in any worker thread
 __device__ __forceinline__ bool workers_any(bool p) {
@@ -565,6 +583,12 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
         const int hp = panels_of(l) / 2;
         return i < hp ? 2 * i : 2 * (i - hp) + 1;
     };
+    // A layer after the first with at most 64 rows in the pass (BF16, 128 channels) runs with
+    // the operands swapped: the weights as the 128-row side (M = output channels), the pass's
+    // rows as N.  An MMA's time follows N (measured: N = 128, 64, 32 take ~73, ~57, ~48
+    // cycles; M = 64 saves nothing), and every worker warp then has output channels to
+    // convert (TMEM lanes = channels).
+    auto swapped = [&](int l, int P) { return !F8 && C == 128 && l >= 1 && rows_of(l, P) <= 64; };
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
@@ -747,14 +771,21 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
             } else if (EPP < C && kConvPer == 2 && np == 4) {
                 // BF16, 128 channels, 32 KB stages (c2): per half one stage of panels h, 2 + h
+                const bool sw = swapped(l, P);
+                const uint32_t IDs = sw ? idesc_rt(rows_of(l, P), false) : ID;
                 for (int h = 0; h < 2; h++) {
                     if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20 + l)) return false;
                     const uint64_t ti = prof ? (uint64_t)clock64() : 0;
                     int s;
                     if (!take(s, l)) return false;
                     const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4), a0 = act_lo + (uint32_t)h * astep;
-                    mma4(d, a0, b0, ID, h ? 1u : 0u);
-                    mma4(d, a0 + 2u * astep, b0 + cstep, ID, 1u);
+                    if (sw) {   // weights as A (M = channels), the pass's rows as B
+                        mma4(d, b0, a0, IDs, h ? 1u : 0u);
+                        mma4(d, b0 + cstep, a0 + 2u * astep, IDs, 1u);
+                    } else {
+                        mma4(d, a0, b0, ID, h ? 1u : 0u);
+                        mma4(d, a0 + 2u * astep, b0 + cstep, ID, 1u);
+                    }
                     umma_commit_warp(bar(S + s));
                     if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
                 }
@@ -776,6 +807,8 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                 // panels half a row wide (BF16, 128 channels): the stages of the first half hold
                 // the even panels (rows 2j, 2j+1, channels 0-63), those of the second the odd ones
                 const int hp = np / 2, Gh = G / 2;
+                const bool sw = swapped(l, P);
+                const uint32_t IDs = sw ? idesc_rt(rows_of(l, P), false) : ID;
                 for (int h = 0; h < 2; h++) {
                     if (!wait_sig(h ? B_HB : B_HA, h ? ph_hb : ph_ha, h ? 13 : 12, t, 20 + l)) return false;
                     const uint64_t ti = prof ? (uint64_t)clock64() : 0;
@@ -785,7 +818,10 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                         const int i0 = g * kConvPer, n = min(kConvPer, hp - i0);
                         const uint32_t b0 = ring_lo + ((uint32_t)s * kStage >> 4);
                         uint32_t a = act_lo + (uint32_t)(2 * i0 + h) * astep;
-                        for (int j = 0; j < n; j++, a += 2u * astep) mma_ks(d, a, b0 + (uint32_t)j * cstep, ID, 0, 4, fresh);
+                        for (int j = 0; j < n; j++, a += 2u * astep) {
+                            if (sw) mma_ks(d, b0 + (uint32_t)j * cstep, a, IDs, 0, 4, fresh);
+                            else mma_ks(d, a, b0 + (uint32_t)j * cstep, ID, 0, 4, fresh);
+                        }
                         umma_commit_warp(bar(S + s));
                     }
                     if (prof) pacc[23 + l] += (uint64_t)clock64() - ti;
@@ -1193,6 +1229,48 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
             if (C == 128) epilogue(std::integral_constant<int, 32>{}, l, P, h);
             else epilogue(std::integral_constant<int, 16>{}, l, P, h);
         };
+        // Epilogue of a swapped layer (TMEM lanes = output channels, columns = the pass's
+        // rows): this warp takes 16 channels (half of its quadrant's lanes) of every row, 16
+        // rows at a time: bias, ReLU and BF16 pairs in the 8x8 fragment layout the 16x256b
+        // load delivers, stored transposed by stmatrix, i.e. as 16-byte runs of 8 channels of
+        // one operand row (the same bytes the row-major epilogue writes).
+        auto epi_swapped = [&](int l, int P) {
+            const bool last = l == L - 1;
+            const int Rl = rows_of(l, P);
+            const int cob = qd * 32 + half * 16, g = lane >> 2;
+            const float b0 = s_cb[l * C + cob + g], b1 = s_cb[l * C + cob + 8 + g];
+            const uint32_t ta = tmem_base + ((uint32_t)cob << 16) + dcol(l);
+            const int mi = lane >> 3, mj = lane & 7;              // the matrix and row this thread addresses
+            const int cbi = cob + ((mi & 1) ? 8 : 0), rbo = (mi & 2) ? 8 : 0;
+            const __nv_bfloat162 zero2 = __floats2bfloat162_rn(0.f, 0.f);
+            auto pk = [&](uint32_t x, uint32_t y, float b) {
+                __nv_bfloat162 v = __floats2bfloat162_rn(__uint_as_float(x) + b, __uint_as_float(y) + b);
+                v = __hmax2(v, zero2);
+                return *reinterpret_cast<uint32_t *>(&v);
+            };
+            for (int r0 = 0; r0 < Rl; r0 += 16) {
+                uint32_t v[8];
+                tmem_ld16x256b_x2(ta + (uint32_t)r0, v);
+                const uint32_t f[4] = {pk(v[0], v[1], b0), pk(v[2], v[3], b1), pk(v[4], v[5], b0), pk(v[6], v[7], b1)};
+                const int m = r0 + rbo + mj, p = m / SPC, s = m % SPC;
+                int row, k;
+                uint32_t base, pstride;
+                if (!last) {   // next layer's row (pair p >> 1, slot s), K half p & 1
+                    row = (p >> 1) * SPC + s;
+                    k = (p & 1) * C + cbi;
+                    base = y.act;
+                    pstride = pstride_of(l + 1, P);
+                } else {       // FC1 operand: row = cluster slot, K = position in pass x C + channel
+                    row = (int)rank * SPC + s;
+                    k = p * C + cbi;
+                    base = y.fc1a;
+                    pstride = 16384u;
+                }
+                const uint32_t off = base + (uint32_t)(k >> 6) * pstride + (uint32_t)row * 128u +
+                                     ((uint32_t)(((k >> 3) & 7) ^ (row & 7)) << 4);
+                stmatrix_x4_trans(smem_u32(sm + off), f);
+            }
+        };
         // this CTA's rows of the pass's FC1 panels of channel half h (all panels when a panel
         // spans both halves: h = 1 only) to every peer: lane j of worker warp 0 (whose TMEM
         // lanes hold no rows of a last layer with at most 96 rows) sends to peer rank + j, one
@@ -1239,24 +1317,39 @@ __global__ void __launch_bounds__(kCThreads, 1) cluster_kernel(const __grid_cons
                     const bool last = l == L - 1;
                     bool ok = note(sleep_wait(bar(B_D), (uint32_t)d_uses & 1u, lim, abort_f, a.status, false), 5, t, R);
                     d_uses++;
-                    if (last && R >= 1 && ok)   // every CTA has consumed the previous pass's exchanged rows
+                    if (last && R >= 1 && ok) {   // every CTA has consumed the previous pass's exchanged rows
+                        const uint64_t tb = prof ? (uint64_t)clock64() : 0;
                         ok = note(cl_wait(b_empty(R - 1), (uint32_t)(((R - 1) >> 1) & 1), lim, abort_f, a.status),
                                   6, t, R);
+                        if (prof) pacc[13] += (uint64_t)clock64() - tb;
+                    }
                     ok = __all_sync(0xffffffffu, ok);
                     tc_fence_after();
                     mark(2 + 2 * l);
-                    // the first channel half, handed to the MMA warp (and its complete FC1
-                    // panels to the peers) while the second is converted
-                    if (ok) epi(l, P, 0);
-                    tc_fence_before();
-                    signal(B_HA);
-                    if (last) {
-                        workers_sync();
-                        if (ok && ((kSplit && EPP < C) || hfc)) send_rows(P, 0);
+                    if (swapped(l, P)) {
+                        // both channel halves at once (each warp converts its own channels)
+                        if (ok) epi_swapped(l, P);
+                        tc_fence_before();
+                        signal(B_HA);
+                        signal(B_HB);
+                        if (last) {
+                            workers_sync();
+                            if (ok) send_rows(P, 0);
+                        }
+                    } else {
+                        // the first channel half, handed to the MMA warp (and its complete FC1
+                        // panels to the peers) while the second is converted
+                        if (ok) epi(l, P, 0);
+                        tc_fence_before();
+                        signal(B_HA);
+                        if (last) {
+                            workers_sync();
+                            if (ok && ((kSplit && EPP < C) || hfc)) send_rows(P, 0);
+                        }
+                        if (ok) epi(l, P, 1);
+                        tc_fence_before();
+                        signal(B_HB);
                     }
-                    if (ok) epi(l, P, 1);
-                    tc_fence_before();
-                    signal(B_HB);
                     if (q0 == 0 && l == 0) {
                         // the step's extent, published by the producer: positions, or the
                         // cluster is done (then the MMA warp stops before the second layer)
