@@ -528,13 +528,27 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         }
         if (!ok) break;
         ext_prev = ext;
-        {   // head phase: every warp of the grid takes slots; the stage ring is its scratch
+        {   // head phase: every warp of the grid takes slots; the stage ring is its scratch.
+            // Software-pipelined over a warp's slots: the sub-trace of the slot two ahead and
+            // the state and FC2 partials of the next one are loaded before this one is
+            // processed, so their device-memory round trips overlap its work.
             constexpr int PER = 256 * 8 + 32 * stage_row_bytes<T>();
             uint8_t *mine = smem + warp * PER;
-            const int n_act = *a.A->n_active;
-            for (int slot = blockIdx.x * kWarps + warp; slot < n_act; slot += gridDim.x * kWarps)
-                head_update_warp<T, NO>(a.A, slot, lane, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
-                                    reinterpret_cast<uint64_t *>(mine), mine + 256 * 8, a.B, ext_next);
+            const int n_act = *a.A->n_active, stride = gridDim.x * kWarps;
+            int slot = blockIdx.x * kWarps + warp;
+            HeadState cur;
+            if (slot < n_act) head_load<NO>(a.A, slot, a.A->active[slot], lane, a.part, a.P, a.B, cur);
+            int b_next = slot + stride < n_act ? a.A->active[slot + stride] : 0;
+            for (; slot < n_act; slot += stride) {
+                const int s1 = slot + stride, s2 = slot + 2 * stride;
+                const int b_after = s2 < n_act ? a.A->active[s2] : 0;
+                HeadState nxt;
+                if (s1 < n_act) head_load<NO>(a.A, s1, b_next, lane, a.part, a.P, a.B, nxt);
+                head_update_state<T, NO>(a.A, slot, lane, cur, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
+                                         reinterpret_cast<uint64_t *>(mine), mine + 256 * 8, a.B, ext_next);
+                cur = nxt;
+                b_next = b_after;
+            }
         }
         ok = grid_sync(a, target, cta_abort);
         mark(SIMNET_KERNEL_HEAD_UPDATE);

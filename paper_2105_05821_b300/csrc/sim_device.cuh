@@ -463,20 +463,95 @@ __device__ __forceinline__ int stores_to_write_queue(const uint64_t *__restrict_
 // only rows 0 .. max(old, new context length) are written (rows past the
 // context are kept zero) and the next step's batch extent `ext` is raised to
 // the new context length + 1.
+// What the head of one slot reads before any arithmetic of its own: the
+// sub-trace, its state and (regression head) this lane's share of the FC2
+// partial sums.  Loaded one slot ahead by head phases that walk many slots, so
+// that the device-memory round trips overlap the previous slot's work.
+struct HeadState {
+    int b;
+    int64_t o, n;
+    int p, tick, qs, ql, ms, ml;
+    float zf, ze;   // NO = 2: this lane's sums of the partials i = lane, lane + 32, ...
+};
+template <int NO>
+__device__ __forceinline__ void head_load(const StepArgs *__restrict__ A, int slot, int b, int lane,
+                                          const float *__restrict__ part, int P, int part_stride, HeadState &h) {
+    h.b = b;
+    h.o = A->offsets[b];
+    h.n = A->offsets[b + 1] - h.o;
+    h.p = A->pos[b];
+    h.tick = A->tick[b];
+    h.qs = A->qstart[b];
+    h.ql = A->qlen[b];
+    h.ms = 0;
+    h.ml = 0;
+    if constexpr (out_lat<NO>() == 3) {
+        h.ms = A->mstart[b];
+        h.ml = A->mlen[b];
+    }
+    h.zf = 0.f;
+    h.ze = 0.f;
+    if constexpr (NO == 2) {
+        for (int i = lane; i < P; i += 32) {
+            const float2 v = reinterpret_cast<const float2 *>(part)[(size_t)i * part_stride + slot];
+            h.zf += v.x;
+            h.ze += v.y;
+        }
+    }
+}
+
+template <typename T, int NO = 2>
+__device__ __forceinline__ void head_update_state(const StepArgs *__restrict__ A, int slot, int lane, const HeadState &h,
+                                                  const float *__restrict__ part, int P, int part_stride,
+                                                  const float *__restrict__ b2, T *__restrict__ X,
+                                                  uint64_t *__restrict__ sq, uint8_t *__restrict__ stg,
+                                                  int pm_slots, int *ext);
+
 template <typename T, int NO = 2>
 __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A, int slot, int lane,
                                                  const float *__restrict__ part, int P, int part_stride,
                                                  const float *__restrict__ b2, T *__restrict__ X,
                                                  uint64_t *__restrict__ sq, uint8_t *__restrict__ stg,
                                                  int pm_slots = 0, int *ext = nullptr) {
+    HeadState h;
+    head_load<NO>(A, slot, A->active[slot], lane, part, P, part_stride, h);
+    head_update_state<T, NO>(A, slot, lane, h, part, P, part_stride, b2, X, sq, stg, pm_slots, ext);
+}
+
+template <typename T, int NO>
+__device__ __forceinline__ void head_update_state(const StepArgs *__restrict__ A, int slot, int lane, const HeadState &h,
+                                                  const float *__restrict__ part, int P, int part_stride,
+                                                  const float *__restrict__ b2, T *__restrict__ X,
+                                                  uint64_t *__restrict__ sq, uint8_t *__restrict__ stg,
+                                                  int pm_slots, int *ext) {
     constexpr int NL = out_lat<NO>();
     constexpr bool SQ = NL == 3;
-    const int b = A->active[slot];
-    const int64_t o = A->offsets[b], n = A->offsets[b + 1] - o;
-    int p = A->pos[b];
+    const int b = h.b;
+    const int64_t o = h.o, n = h.n;
+    int p = h.p;
     if (p >= n) return;
+    // the records of this step's append and of the next step's row 0, and (processor queue
+    // of at most 32 entries, no write queue) the whole queue, newest first in the lanes:
+    // the retire scan and the next step's rows both come from these registers, so the ring
+    // is read once, before the head's arithmetic
+    const uint32_t rec_cur = A->records[o + p];
+    const uint32_t rec_next = (p + 1 < n) ? A->records[o + p + 1] : 0u;
+    const int cap = A->cap, RW = A->retire_width, strict = A->strict;
+    uint64_t *ring = A->ring + (size_t)b * cap;
+    const bool small = !SQ && h.ql <= 32;
+    uint64_t qv = 0;
+    if (small && lane < h.ql) {
+        int idx = h.qs + h.ql - 1 - lane;
+        if (idx >= cap) idx -= cap;
+        qv = ring[idx];
+    }
     float z[NO];
-    head_sum_warp<NO>(part, P, part_stride, slot, b2, lane, z);
+    if constexpr (NO == 2) {
+        z[0] = warp_sum(h.zf) + b2[0];
+        z[1] = warp_sum(h.ze) + b2[1];
+    } else {
+        head_sum_warp<NO>(part, P, part_stride, slot, b2, lane, z);
+    }
     float pre[3];
     uint32_t lat[3];
     lat[0] = head_latency<NO, 0>(z, pre[0]);
@@ -496,17 +571,12 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
         }
     }
     const uint32_t F = lat[0], E = lat[1], S = lat[2];
-    const int cap = A->cap, RW = A->retire_width, strict = A->strict;
-    uint64_t *ring = A->ring + (size_t)b * cap;
     uint64_t *mring = SQ ? A->mring + (size_t)b * cap : nullptr;
-    int qs = A->qstart[b], ql = A->qlen[b], ev = 0;
-    int ms = 0, ml = 0;
-    if constexpr (SQ) {
-        ms = A->mstart[b];
-        ml = A->mlen[b];
-    }
+    int qs = h.qs, ql = h.ql, ev = 0;
+    int ms = h.ms, ml = h.ml;
     const int ctx_old = ql + ml;
-    int32_t tick = A->tick[b] + (int32_t)F;
+    const int ql_old = ql;
+    int32_t tick = h.tick + (int32_t)F;
     // processor queue, then (stores) the memory write queue
     auto retire_both = [&](int budget) {
         const int k = retire_run(ring, cap, qs, min(ql, budget), tick, strict, lane);
@@ -521,7 +591,24 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
             ml -= km;
         }
     };
-    retire_both(RW * (int)F);
+    if (small) {
+        // the oldest-first run of ready entries, from the registers (entry k of the queue
+        // is in lane ql - 1 - k)
+        const int lim = min(ql, RW * (int)F);
+        const uint64_t v = __shfl_sync(0xffffffffu, qv, max(ql - 1 - lane, 0));
+        bool rd = false;
+        if (lane < lim) {
+            const int32_t res = entry_res(v, tick), e = (int32_t)entry_e(v);
+            rd = strict ? (res > e) : (res >= e);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, rd);
+        const int k = min((m == 0xffffffffu) ? 32 : (__ffs(~m) - 1), lim);
+        qs += k;
+        if (qs >= cap) qs -= cap;
+        ql -= k;
+    } else {
+        retire_both(RW * (int)F);
+    }
     if (ql + ml == cap) {  // full: drop the oldest instruction
         if (ml > 0) {
             ms = (ms + 1 == cap) ? 0 : ms + 1;
@@ -532,10 +619,11 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
         }
         ev = 1;
     }
+    const uint64_t appended = pack_entry(rec_cur, E, S, (uint32_t)tick);
     if (lane == 0) {
         int idx = qs + ql;
         if (idx >= cap) idx -= cap;
-        ring[idx] = pack_entry(A->records[gi], E, S, (uint32_t)tick);
+        ring[idx] = appended;
     }
     ql++;
     p++;
@@ -549,22 +637,28 @@ __device__ __forceinline__ void head_update_warp(const StepArgs *__restrict__ A,
     } else if (X) {
         // next step's input rows of this slot: row 0 = instruction p, row r = r-th newest
         // context entry.  The context is copied newest-first into shared memory with
-        // independent loads first.
-        for (int r = lane + 1; r <= ql + ml; r += 32) {
-            int idx;
-            if (r <= ql) {
-                idx = qs + ql - r;
-                if (idx >= cap) idx -= cap;
-                sq[r] = ring[idx];
-            } else {
-                idx = ms + ml - (r - ql);
-                if (idx >= cap) idx -= cap;
-                sq[r] = mring[idx];
+        // independent loads first (or, for a small queue, from the registers read at the
+        // start: row 1 is the entry just appended, row r >= 2 the old (r - 2)-th newest).
+        if (small) {
+            if (lane == 0) sq[1] = appended;
+            if (lane + 2 <= ql && lane < ql_old) sq[lane + 2] = qv;
+        } else {
+            for (int r = lane + 1; r <= ql + ml; r += 32) {
+                int idx;
+                if (r <= ql) {
+                    idx = qs + ql - r;
+                    if (idx >= cap) idx -= cap;
+                    sq[r] = ring[idx];
+                } else {
+                    idx = ms + ml - (r - ql);
+                    if (idx >= cap) idx -= cap;
+                    sq[r] = mring[idx];
+                }
             }
         }
         __syncwarp();
         const int W = A->window;
-        const uint32_t cur = A->records[o + p];
+        const uint32_t cur = rec_next;
         constexpr int SR = stage_row_bytes<T>();
         const int ctx_new = ql + ml;
         const int rows = pm_slots > 0 ? min(W, max(ctx_old, ctx_new) + 1) : W;
