@@ -142,6 +142,7 @@ static_assert(sizeof(PArgs) <= 32000, "persistent kernel arguments too large");
 
 struct Pipe {  // pipeline counters that carry over between GEMM phases
     int prod_it = 0, mma_it = 0, mma_tc = 0, epi_tc = 0;
+    int res = 0;   // phases that loaded their weights once (resident), for that barrier's parity
 };
 
 // Positions [lo, hi) of every slot below M in a layer's pair-major output tile
@@ -209,21 +210,35 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
     const int64_t lim = a.spin_ns;
     const bool det = a.detail && blockIdx.x == 0;
     const uint64_t t_phase = det ? gtimer() : 0;
+    // A layer whose whole weight matrix (one column block of KB panels) fits beside S
+    // operand-only stages keeps it in shared memory for the phase, loaded once: the first
+    // conv layer (K = 128, two panels) would else reload its 64 KB for every 128-row tile.
+    const bool resident = !L.out_part && l2 < 0 && L.n_tiles_n == 1 && blockIdx.x < n_tiles &&
+                          (uint32_t)S * A_BYTES + (uint32_t)KB * L.BN * ROW_BYTES <= (uint32_t)S * a.stage_bytes;
+    const uint32_t res_base = smem_base + (uint32_t)S * A_BYTES, res_panel = (uint32_t)L.BN * ROW_BYTES;
+    const uint32_t bres = smem_u32(&bars[2 * S + 5]);
+    auto a_stage = [&](int s) {
+        return resident ? smem_base + (uint32_t)s * A_BYTES : smem_base + (uint32_t)s * a.stage_bytes;
+    };
     if (warp == 0) {
         if (lane == 0) {
             asm volatile("fence.proxy.async.global;" ::: "memory");
             bool ok = true;
+            if (resident) {   // the stages of the previous phase are all consumed (grid barrier)
+                mbar_expect_tx(bres, (uint32_t)KB * res_panel);
+                for (int kb = 0; kb < KB; kb++) tma_load_2d(res_base + (uint32_t)kb * res_panel, &L.tB, bres, kb * BK, 0);
+            }
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 int which, pos, sb, nt;
                 tile_of(t, which, pos, sb, nt);
                 const PLayer &Lt = which ? a.layer[l2] : L;
                 const int n0 = nt * Lt.BN;
-                const uint32_t stage_tx = (uint32_t)(A_BYTES + Lt.BN * ROW_BYTES);
+                const uint32_t stage_tx = (uint32_t)(A_BYTES + (resident ? 0 : Lt.BN * ROW_BYTES));
                 for (int kb = 0; kb < KB; kb++, pp.prod_it++) {
                     const int s = pp.prod_it % S;
                     const uint32_t ph = (uint32_t)(pp.prod_it / S) & 1u;
                     if (!mbar_wait(empty(s), ph ^ 1u, lim, cta_abort, a.status)) { ok = false; break; }
-                    const uint32_t sa = smem_base + s * a.stage_bytes;
+                    const uint32_t sa = a_stage(s);
                     // A: conv -> input pair `pos`; FC1 -> the input row holding this K slice
                     int ax, ay;
                     if (L.out_part) {
@@ -239,13 +254,18 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                     }
                     mbar_expect_tx(full(s), stage_tx);
                     tma_load_2d(sa, &L.tA, full(s), ax, ay);
-                    tma_load_2d(sa + A_BYTES, &Lt.tB, full(s), kb * BK, n0);
+                    if (!resident) tma_load_2d(sa + A_BYTES, &Lt.tB, full(s), kb * BK, n0);
                 }
             }
         }
     } else if (warp == 1) {
         {   // the whole warp runs the issue loop, one elected lane issues (umma_warp)
             bool ok = true;
+            if (resident) {
+                ok = __all_sync(0xffffffffu, mbar_wait(bres, (uint32_t)pp.res & 1u, lim, cta_abort, a.status));
+                pp.res++;
+                tc_fence_after();
+            }
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, pp.mma_tc++) {
                 const uint32_t ID = idesc_rt((!FP8 && t >= T0) ? a.layer[l2].BN : L.BN, FP8);
                 const int acc = pp.mma_tc & 1;
@@ -260,8 +280,8 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                     tc_fence_after();
                     if (det && lane == 0 && t == (int)blockIdx.x && kb == 0)
                         atomicAdd(&a.detail[4 * l + 0], gtimer() - t_phase);
-                    const uint32_t sa = smem_base + s * a.stage_bytes;
-                    const uint64_t ad = sdesc(sa), bd = sdesc(sa + A_BYTES);
+                    const uint32_t sa = a_stage(s);
+                    const uint64_t ad = sdesc(sa), bd = sdesc(resident ? res_base + (uint32_t)kb * res_panel : sa + A_BYTES);
 #pragma unroll
                     for (int k = 0; k < 4; k++)
                         umma_warp<FP8>(d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), ID, (kb | k) != 0 ? 1u : 0u);
@@ -325,17 +345,43 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                         }
                     }
                 }
+                if (!L.out_part && !L.resid && Lt.relu) {
+                    // a plain conv layer: bias (FP8: and the scales) four columns to a load, no
+                    // shortcut (this loop bounded the first layer's phase at c5)
+                    const float4 *b4 = reinterpret_cast<const float4 *>(t_bias + col0);
+                    const float4 *s4 = reinterpret_cast<const float4 *>(t_scale + col0);
+                    const float4 *o4 = reinterpret_cast<const float4 *>(t_oscale + col0);
 #pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    float x = __uint_as_float(r[j]);
-                    if (FP8) x *= t_scale[col0 + j];
-                    if (L.out_part) x += s_cst[col0 + j];   // FC1: the constant rows past the extent
-                    // BF16 bits to FP32: the value's 16 bits as the high half of an FP32 word
-                    const float rv = __uint_as_float((j & 1) ? (rs[j >> 1] & 0xffff0000u) : (rs[j >> 1] << 16));
-                    x += t_bias[col0 + j] + rv;
-                    if (Lt.relu) x = fmaxf(x, 0.f);
-                    if (FP8 && !L.out_part) x *= t_oscale[col0 + j];
-                    v[j] = x;
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 bb = b4[j4];
+                        float x0 = __uint_as_float(r[4 * j4]), x1 = __uint_as_float(r[4 * j4 + 1]);
+                        float x2 = __uint_as_float(r[4 * j4 + 2]), x3 = __uint_as_float(r[4 * j4 + 3]);
+                        if constexpr (FP8) {
+                            const float4 sc = s4[j4], os = o4[j4];
+                            v[4 * j4] = fmaxf(x0 * sc.x + bb.x, 0.f) * os.x;
+                            v[4 * j4 + 1] = fmaxf(x1 * sc.y + bb.y, 0.f) * os.y;
+                            v[4 * j4 + 2] = fmaxf(x2 * sc.z + bb.z, 0.f) * os.z;
+                            v[4 * j4 + 3] = fmaxf(x3 * sc.w + bb.w, 0.f) * os.w;
+                        } else {
+                            v[4 * j4] = fmaxf(x0 + bb.x, 0.f);
+                            v[4 * j4 + 1] = fmaxf(x1 + bb.y, 0.f);
+                            v[4 * j4 + 2] = fmaxf(x2 + bb.z, 0.f);
+                            v[4 * j4 + 3] = fmaxf(x3 + bb.w, 0.f);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        float x = __uint_as_float(r[j]);
+                        if (FP8) x *= t_scale[col0 + j];
+                        if (L.out_part) x += s_cst[col0 + j];   // FC1: the constant rows past the extent
+                        // BF16 bits to FP32: the value's 16 bits as the high half of an FP32 word
+                        const float rv = __uint_as_float((j & 1) ? (rs[j >> 1] & 0xffff0000u) : (rs[j >> 1] << 16));
+                        x += t_bias[col0 + j] + rv;
+                        if (Lt.relu) x = fmaxf(x, 0.f);
+                        if (FP8 && !L.out_part) x *= t_oscale[col0 + j];
+                        v[j] = x;
+                    }
                 }
                 if (L.out_part) {
                     if constexpr (NO == 2) {
@@ -456,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             mbar_init(smem_u32(&bars[2 * S + x]), 1);
             mbar_init(smem_u32(&bars[2 * S + 2 + x]), 32 * kEpiWarps);
         }
+        mbar_init(smem_u32(&bars[2 * S + 5]), 1);   // resident weights (after tmem_slot and cta_abort)
         *cta_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
