@@ -504,6 +504,34 @@ def run_ours(args):
     print(json.dumps(out), flush=True)
 
 
+def executed_work(w, prec, n_inst, ms_per_call, blob, rec, off):
+    """The grid-persistent kernel computes only the positions below the padding
+    extent: one more call with the kernel's row counters on gives the GEMM rows
+    each layer computed, hence the executed FLOPs (conv1 with its 64 padded
+    feature channels, FC2 from the instruction count)."""
+    from paper_2105_05821_b300.simnet import Simnet
+    a = w.arch
+    sim = Simnet.for_arch(a, precision=prec, retire_width=w.retire_width, kernel_events=True, cluster=False)
+    sim.load_weights(blob.astype(np.float32))
+    sim.simulate(rec, off, stats=True)
+    d = sim.phase_detail(8).reshape(-1)   # 8 x 4 counters from the persistent block
+    sim.close()
+    rows = [int(x) for x in d[24:24 + a.n_conv + 1]]
+    exe = 0.0
+    for l in range(a.n_conv):
+        k = 2 * 64 if l == 0 else 2 * a.channels
+        exe += 2.0 * rows[l] * k * a.channels
+    exe += 2.0 * rows[a.n_conv] * a.channels * a.hidden   # FC1: last-layer positions x slots
+    exe += 2.0 * a.n_out * a.hidden * n_inst              # FC2
+    _, _, bf16_sus, src = peaks()
+    peak = bf16_sus * (2.0 if prec == "fp8" else 1.0)
+    tf = exe / (ms_per_call / 1e3) / 1e12
+    return {"executed_flop": exe, "executed_tflops": tf, "executed_frac": tf / peak,
+            "executed_note": f"GEMM rows per layer {rows} (output positions x active slots over the call, "
+                             f"FC1: last-layer positions x slots) from the kernel's counters; frac against "
+                             f"the {src} sustained peak" + (" x2" if prec == "fp8" else "")}
+
+
 def run_extra(args, timer):
     """c5 (65,536 sub-traces, 100M instructions, W=128, 5 x Conv256, FC1024) at
     BF16 and FP8, and c4 (4,096 log-normal sub-traces, about 40M instructions,
@@ -525,6 +553,8 @@ def run_extra(args, timer):
         r["roofline"] = whole_call_roofline(w5, prec, t5.n_instructions, r["ms_per_step"],
                                             PATH_KERNEL.get(r["kernel_mode"], r["kernel_mode"]),
                                             TRAFFIC.get(("c5", prec, PATH_KERNEL.get(r["kernel_mode"]))))
+        if r["kernel_mode"] == "persistent":
+            r["roofline"].update(executed_work(w5, prec, t5.n_instructions, r["ms_per_step"], b5, rec, off))
         res[f"c5_{prec}"] = {"record": r, "cycles": c, "check": (w5, t5, b5, ids5)}
     del rec, off
     torch.cuda.empty_cache()

@@ -76,6 +76,8 @@ struct PArgs {
     int32_t *status;
     unsigned long long *phase_ns; // [SIMNET_KERNEL_KINDS] summed phase times (CTA 0), or null
     unsigned long long *phase_n;  // [SIMNET_KERNEL_KINDS] phase counts
+    unsigned long long *exec;     // [layer] GEMM rows computed over the steps, on request: output
+                                  // positions x active slots (FC1: last-layer positions x slots)
     unsigned long long *detail;   // [kMaxConv+1][4] CTA 0, ns after each GEMM phase starts: first data,
                                   // last MMA commit, epilogue done, barrier passed (or null)
     int64_t n_steps;
@@ -197,6 +199,11 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
     const int T0 = n_pos * n_sb * L.n_tiles_n;
     const int n_tiles = T0 + (l2 >= 0 ? n_pos * n_sb * a.layer[l2].n_tiles_n : 0);
     const int KB = L.out_part ? e * L.cin / BK : L.K / BK;   // the paired layer has the same K
+    if (a.exec && blockIdx.x == 0 && threadIdx.x == 0) {   // the padding extent's saving, counted
+        const unsigned long long rows = (unsigned long long)(L.out_part ? e : n_now) * (unsigned long long)M;
+        atomicAdd(&a.exec[l], rows);
+        if (l2 >= 0) atomicAdd(&a.exec[l2], rows);
+    }
     // tile t -> its layer (0: l, 1: l2), input position (pair), slot block, column block
     auto tile_of = [&](int t, int &which, int &pos, int &sb, int &nt) {
         which = (!FP8 && t >= T0) ? 1 : 0;   // residual blocks (the only pairs) are BF16
@@ -707,6 +714,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.phase_n = c->phase_on ? c->phase_n : nullptr;
     // per-GEMM detail has room for the layers of a plain CNN (4 counters each)
     a.detail = c->phase_on && c->n_layers <= kMaxConv + 1 ? c->phase_ns + 16 : nullptr;
+    a.exec = c->phase_on && c->n_layers <= 8 ? c->phase_ns + 40 : nullptr;
     a.n_steps = n_steps;
     a.spin_ns = c->cfg.spin_limit_ns;
     a.bar_spin_ns = c->cfg.barrier_limit_us > 0 ? (int64_t)c->cfg.barrier_limit_us * 1000 : c->cfg.spin_limit_ns;
