@@ -408,7 +408,15 @@ bool make_tg_plan(TgPlan &p, int epi, const void *A, bool a_mn, const void *B, b
     if (M <= 0 || N <= 0 || R <= 0) { why = "empty training GEMM"; return false; }
     if (N % 64 != 0) { why = "training GEMM: N not a multiple of 64"; return false; }
     if (a_mn && !b_mn) { why = "training GEMM: layout pair not built"; return false; }
-    p.BN = N % 256 == 0 ? 256 : N % 128 == 0 ? 128 : 64;
+    // the widest column tile that still gives three tiles for every four SMs; narrower tiles
+    // before a split reduction (a split writes FP32 partial tiles and needs a reduction
+    // kernel: FC1's forward of the training step went from 32 tiles x 4 splits to 128 tiles)
+    {
+        const int mt = (M + BM - 1) / BM, want = 3 * num_sms() / 4;
+        p.BN = 64;
+        for (int bn : {256, 128})
+            if (N % bn == 0 && mt * (N / bn) >= want) { p.BN = bn; break; }
+    }
     p.epi = epi;
     p.a_mn = a_mn;
     p.b_mn = b_mn;
