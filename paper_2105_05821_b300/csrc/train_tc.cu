@@ -444,7 +444,7 @@ bool make_tg_plan(TgPlan &p, int epi, const void *A, bool a_mn, const void *B, b
     const int KB = (R + 63) / 64, base = p.m_tiles * p.n_tiles_n, sms = num_sms();
     p.splits = 1;
     p.kb_per_split = KB;
-    if ((epi == TG_WGRAD || epi == TG_FWD_F32) && base < sms) {   // split the reduction until the tiles fill the GPU
+    if ((epi == TG_WGRAD || epi == TG_FWD_F32) && base < 3 * sms / 4) {   // split the reduction until the tiles fill the GPU
         int splits = std::min(KB, (sms + base - 1) / base);
         p.kb_per_split = (KB + splits - 1) / splits;
         p.splits = (KB + p.kb_per_split - 1) / p.kb_per_split;
