@@ -117,6 +117,11 @@ typedef enum {
                                           calls with the same batch size, compaction and weights.
                                           Paths differ only in FP32 summation order;
                                           simulate_stats.path reports the last one used. */
+#define SIMNET_FLAG_NO_FUSE 0x400u     /* BF16/FP8 persistent kernel: run the first two conv layers
+                                          as two phases (conv1's output through device memory).
+                                          By default a plain CNN of 256 channels runs them as one
+                                          phase whose conv1 output stays in tensor memory as
+                                          conv2's operand; both give the same values. */
 
 /*
  * Model and simulator shape.  The CNN sees `window` rows: the current
@@ -353,7 +358,11 @@ simnet_status simnet_kernel_times(simnet_ctx *ctx, float *ms_out, int64_t *launc
  * entries) receives, for GEMM layer l, out[4l + k] = summed nanoseconds from
  * the start of the layer's phase in CTA 0 to k = 0 its first operand tile
  * arriving, 1 its last MMA commit, 2 its epilogue done, 3 the grid barrier
- * passed.  For the cluster kernel (SIMNET_PATH_CLUSTER) out[k], k < 32, is
+ * passed.  When the first two conv layers run as one phase (SIMNET_FLAG_NO_FUSE
+ * not set), layer 1's row times that phase and layer 0's row holds its waits:
+ * 0 the MMA warp waiting for a free accumulator, 1 for an operand unit, 2 for
+ * a quarter of conv2's A operand, 3 the first epilogue warp waiting for a full
+ * accumulator.  For the cluster kernel (SIMNET_PATH_CLUSTER) out[k], k < 32, is
  * the summed SM clock cycles of CTA 0's phase k instead: 0 step start (extent exchange),
  * 1 feature rows, 2/4/6 waiting for conv layer 1/2/3, 3/5/7 their epilogues
  * (7 includes the exchange of the last layer's rows), 8 waiting for FC1,

@@ -88,6 +88,14 @@ struct PArgs {
     int w2h_off;                  // hybrid / store heads: per-epilogue-warp FC2 row slices at prm + w2h_off
     int cst_off;                  // FC1's padding row S[e] of the current step at prm + cst_off
     int rows_n, e_round;          // last conv rows; FC1 k-block rows (extent granularity)
+    // Fused first two conv layers (plain CNN, 256 channels): one phase computes each tile
+    // of 128 slots at one output position of conv2 from conv1's two positions under it;
+    // conv1's output goes from its accumulator into tensor memory as conv2's A operand
+    // and never reaches device memory.
+    int fuse, fu;                 // fused phase on; its operand units (16 KB each) in the stage ring
+    int ring_bytes;               // shared memory before the barrier area: the stage ring, or the
+                                  // fused phase's units and resident weights where they need more
+    CUtensorMap tW1, tW2h;        // conv1's and conv2's weights in 128-row boxes
 };
 
 namespace {
@@ -145,7 +153,16 @@ static_assert(sizeof(PArgs) <= 32000, "persistent kernel arguments too large");
 struct Pipe {  // pipeline counters that carry over between GEMM phases
     int prod_it = 0, mma_it = 0, mma_tc = 0, epi_tc = 0;
     int res = 0;   // phases that loaded their weights once (resident), for that barrier's parity
+    int fprod = 0, fmma = 0, fz = 0, fw1 = 0;   // fused phase: operand units, tiles, weight loads,
+    int fpc = 0, fe = 0;                        // pieces issued, pieces drained by this warpgroup
 };
+
+// Shared-memory barrier area: S full and S empty stage barriers, two accumulator
+// full and two empty barriers, the TMEM address and abort flag, the resident-weight
+// barrier; from kFuBar(S): the fused phase's unit full / empty barriers, its four
+// A-operand quarters and its resident-weight barrier.
+constexpr int kBarBytes = 512;
+__host__ __device__ constexpr int kFuBar(int S) { return 2 * S + 6; }
 
 // Positions [lo, hi) of every slot below M in a layer's pair-major output tile
 // get the layer's constant row; the epilogue warps of the grid share the work.
@@ -321,7 +338,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
             const int m0 = L.rows_plain ? 2 * (pos * a.B + sb * (BM / 2)) : sb * BM, n0 = nt * BN;
             const int acc = pp.epi_tc & 1;
             const uint32_t aph = (uint32_t)(pp.epi_tc >> 1) & 1u;
-            if (!mbar_wait(tfull(acc), aph, lim, cta_abort, a.status)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(tfull(acc), aph, lim, cta_abort, a.status))) break;
             tc_fence_after();
             const int row = m0 + q * 32 + lane;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * 256 + half * (BN / 2));
@@ -480,9 +497,309 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                 }
             }
             tc_fence_before();
-            mbar_arrive(tempty(acc));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty(acc));
         }
         if (det && warp == 2 && lane == 0) atomicAdd(&a.detail[4 * l + 2], gtimer() - t_phase);
+    }
+    return t_phase;
+}
+
+// The first two conv layers as one phase (plain CNN, 256 channels, k=2 / stride-2,
+// Sec. 2.3).  A tile is 128 slots at one output position p of conv2; it needs conv1's
+// output at positions 2p and 2p+1 of the same slots, which the tile computes itself:
+// four conv1 pieces (position x 128-channel half; A from the pair-major feature rows,
+// conv1's weights resident in shared memory) whose epilogues apply bias and ReLU
+// (FP8: the scales) and store the values, in the layer's storage type, into tensor
+// memory columns [0, 256) (BF16: two to a column; FP8: four), which is exactly
+// conv2's K-major A operand [posbit * 256 + channel]; then two conv2 pieces (output
+// channel halves) as MMAs with A in tensor memory and B streamed in 128-row units.
+// Positions past conv1's extent read padding rows (zero features), so they come out
+// as conv1's constant row, as in the unfused phases.  The six pieces of a tile use
+// the two 128-column accumulators at columns 256 and 384 in turn, and each
+// accumulator has its own epilogue warpgroup (warps 2-5: the first, 6-9: the
+// second), so two pieces' epilogues overlap.
+constexpr uint32_t kFuAcc = 256;
+constexpr uint32_t kUnit = A_BYTES;   // one operand unit: 128 rows x 128 bytes
+constexpr int kFuBars = 9;            // per fused phase beyond the units: 4 A quarters, weights, 2 + 2 accumulator
+
+template <bool FP8>
+__device__ uint64_t fused_phase(const PArgs &a, int l, int n2, int n2_prev, uint8_t *smem, uint64_t *bars, float *prm,
+                                uint8_t *staging, uint32_t tmem_base, volatile int *cta_abort, Pipe &pp) {
+    using T = typename std::conditional<FP8, __nv_fp8_e4m3, __nv_bfloat16>::type;
+    const PLayer &L1 = a.layer[l], &L2 = a.layer[l + 1];
+    constexpr int BK = FP8 ? 128 : 64;   // K elements per 128-byte row
+    constexpr int KB1 = 128 / BK;        // conv1: K = 2 rows x 64 features
+    constexpr int KB2 = 512 / BK;        // conv2: K = 2 positions x 256 channels
+    constexpr int EPC = FP8 ? 4 : 2;     // A-operand elements per tensor-memory column
+    const int S = a.stages, U = a.fu, F0 = kFuBar(S);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t smem_base = smem_u32(smem), w1 = smem_base + (uint32_t)U * kUnit;
+    auto ffull = [&](int u) { return smem_u32(&bars[F0 + u]); };
+    auto fempty = [&](int u) { return smem_u32(&bars[F0 + U + u]); };
+    auto a2full = [&](int i) { return smem_u32(&bars[F0 + 2 * U + i]); };
+    const uint32_t w1bar = smem_u32(&bars[F0 + 2 * U + 4]);
+    auto afull = [&](int x) { return smem_u32(&bars[F0 + 2 * U + 5 + x]); };
+    auto aempty = [&](int x) { return smem_u32(&bars[F0 + 2 * U + 7 + x]); };
+    const int M = min(*a.A->n_active, a.B);
+    const int n_sb = (M + BM - 1) / BM, n_tiles = n2 * n_sb;
+    const int64_t lim = a.spin_ns;
+    const bool det = a.detail && blockIdx.x == 0;
+    const uint64_t t_phase = det ? gtimer() : 0;
+    if (a.exec && blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(&a.exec[l], (unsigned long long)(2 * n2) * (unsigned long long)M);
+        atomicAdd(&a.exec[l + 1], (unsigned long long)n2 * (unsigned long long)M);
+    }
+    const bool any = (int)blockIdx.x < n_tiles;
+    if (warp == 0) {
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            bool ok = true;
+            if (any) {   // conv1's weights, 128-row halves of each K-block, for the phase
+                mbar_expect_tx(w1bar, (uint32_t)(2 * KB1) * kUnit);
+                for (int kb = 0; kb < KB1; kb++)
+                    for (int h = 0; h < 2; h++)
+                        tma_load_2d(w1 + (uint32_t)(kb * 2 + h) * kUnit, &a.tW1, w1bar, kb * BK, h * 128);
+            }
+            auto unit = [&](const CUtensorMap *m, int x, int y) {
+                const int u = pp.fprod % U;
+                if (!mbar_wait(fempty(u), ((uint32_t)(pp.fprod / U) & 1u) ^ 1u, lim, cta_abort, a.status)) return false;
+                mbar_expect_tx(ffull(u), kUnit);
+                tma_load_2d(smem_base + (uint32_t)u * kUnit, m, ffull(u), x, y);
+                pp.fprod++;
+                return true;
+            };
+            // conv1's input pairs 2p and 2p+1 of a tile's slots (pair-major rows [pair * B + slot])
+            auto a1_row = [&](int t, int pb) { return (2 * (t / n_sb) + pb) * a.B + (t % n_sb) * BM; };
+            for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                // this CTA's next tile reads its feature rows from device memory: start them into L2
+                const int tn = t + (int)gridDim.x;
+                if (tn < n_tiles)
+                    for (int pb = 0; pb < 2; pb++)
+                        for (int kb = 0; kb < KB1; kb++) tma_prefetch_2d(&L1.tA, kb * BK, a1_row(tn, pb));
+                for (int pb = 0; pb < 2 && ok; pb++)
+                    for (int kb = 0; kb < KB1 && ok; kb++) ok = unit(&L1.tA, kb * BK, a1_row(t, pb));
+                // conv2's weights: output-channel half h, K-block kb
+                for (int h = 0; h < 2 && ok; h++)
+                    for (int kb = 0; kb < KB2 && ok; kb++) ok = unit(&a.tW2h, kb * BK, h * 128);
+            }
+        }
+    } else if (warp == 1) {
+        const uint32_t ID = idesc_rt(128, FP8);
+        bool ok = true;
+        if (any) {
+            ok = __all_sync(0xffffffffu, mbar_wait(w1bar, (uint32_t)pp.fw1 & 1u, lim, cta_abort, a.status));
+            pp.fw1++;
+            tc_fence_after();
+        }
+        // CTA 0 sums the MMA warp's waits: accumulator free, operand unit, A-operand quarter
+        uint64_t w_acc = 0, w_unit = 0, w_a2 = 0;
+        // the next accumulator of the running piece count, once its warpgroup has drained it
+        auto take = [&](uint32_t &d, int &acc) {
+            acc = pp.fpc & 1;
+            const uint64_t t0 = det ? gtimer() : 0;
+            const bool got = __all_sync(0xffffffffu, mbar_wait(aempty(acc), ((uint32_t)(pp.fpc >> 1) & 1u) ^ 1u, lim,
+                                                               cta_abort, a.status));
+            if (det) w_acc += gtimer() - t0;
+            if (!got) return false;
+            tc_fence_after();
+            d = tmem_base + kFuAcc + (uint32_t)acc * 128;
+            return true;
+        };
+        auto wait_unit = [&](int it) {
+            const uint64_t t0 = det ? gtimer() : 0;
+            const bool got = __all_sync(0xffffffffu,
+                                        mbar_wait(ffull(it % U), (uint32_t)(it / U) & 1u, lim, cta_abort, a.status));
+            if (det) w_unit += gtimer() - t0;
+            if (got) tc_fence_after();
+            return got;
+        };
+        for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+            if (det && lane == 0 && t == (int)blockIdx.x) atomicAdd(&a.detail[4 * (l + 1) + 0], gtimer() - t_phase);
+            // conv1: per input pair, both channel halves from the same A units
+#pragma unroll
+            for (int pb = 0; pb < 2; pb++) {
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    uint32_t d;
+                    int acc;
+                    if (ok) ok = take(d, acc);
+                    if (!ok) break;
+#pragma unroll
+                    for (int kb = 0; kb < KB1; kb++) {
+                        const int it = pp.fmma + kb, u = it % U;
+                        if (h == 0 && !(ok = wait_unit(it))) break;
+                        const uint32_t a_lo = sdesc_lo(smem_base + (uint32_t)u * kUnit);
+                        const uint32_t b_lo = sdesc_lo(w1 + (uint32_t)(kb * 2 + h) * kUnit);
+#pragma unroll
+                        for (int k = 0; k < 4; k++)
+                            umma_lo<FP8>(d, a_lo + 2u * k, b_lo + 2u * k, ID, (kb | k) != 0 ? 1u : 0u);
+                        if (h == 1) umma_commit_warp(fempty(u));
+                    }
+                    if (!ok) break;
+                    umma_commit_warp(afull(acc));
+                    pp.fpc++;
+                }
+                if (!ok) break;
+                pp.fmma += KB1;
+            }
+            // conv2: A = tensor-memory columns [0, 256), B = unit per K-block
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                uint32_t d;
+                int acc;
+                if (ok) ok = take(d, acc);
+                if (!ok) break;
+#pragma unroll
+                for (int kb = 0; kb < KB2; kb++) {
+                    if (h == 0 && (kb * BK) % 128 == 0) {   // this K-block's quarter of the A operand is stored
+                        const uint64_t t0 = det ? gtimer() : 0;
+                        ok = __all_sync(0xffffffffu, mbar_wait(a2full(kb * BK / 128), (uint32_t)pp.fz & 1u, lim,
+                                                               cta_abort, a.status));
+                        if (det) w_a2 += gtimer() - t0;
+                        if (!ok) break;
+                        tc_fence_after();
+                    }
+                    const int u = pp.fmma % U;
+                    if (!(ok = wait_unit(pp.fmma))) break;
+                    const uint32_t b_lo = sdesc_lo(smem_base + (uint32_t)u * kUnit);
+#pragma unroll
+                    for (int k = 0; k < 4; k++)
+                        umma_ts<FP8>(d, tmem_base + (uint32_t)(kb * 32 + k * 8), b_lo + 2u * k, ID,
+                                     (kb | k) != 0 ? 1u : 0u);
+                    umma_commit_warp(fempty(u));
+                    pp.fmma++;
+                }
+                if (!ok) break;
+                umma_commit_warp(afull(acc));
+                pp.fpc++;
+            }
+            pp.fz++;
+        }
+        if (det && lane == 0) {
+            atomicAdd(&a.detail[4 * (l + 1) + 1], gtimer() - t_phase);
+            // the first layer's row (it has no phase of its own): the waits
+            atomicAdd(&a.detail[4 * l + 0], w_acc);
+            atomicAdd(&a.detail[4 * l + 1], w_unit);
+            atomicAdd(&a.detail[4 * l + 2], w_a2);
+        }
+        __syncwarp();
+    } else {
+        fill_const<T>(a, L2, n2, n2_prev, M);   // conv2 positions this step no longer computes
+        // warpgroup x = (warp - 2) / 4 drains accumulator x: the tile's pieces x, x + 2, x + 4;
+        // its warp q = warp % 4 reads lanes 32q .. 32q + 31 (the hardware's lane quarters)
+        const int q = warp & 3, x = (warp - 2) >> 2;
+        const uint32_t lanes = (uint32_t)(q * 32) << 16;
+        const uint32_t src = tmem_base + lanes + kFuAcc + (uint32_t)x * 128;
+        const float *b1 = prm + L1.prm_off, *s1 = b1 + L1.N, *o1 = b1 + 2 * L1.N;
+        const float *b2 = prm + L2.prm_off, *s2 = b2 + L2.N, *o2 = b2 + 2 * L2.N;
+        constexpr int OES = FP8 ? 1 : 2;
+        constexpr int CB = 32 * OES, SROW = CB + 16;
+        uint8_t *stg = staging + (warp - 2) * 32 * SROW;
+        // 64 accumulator columns from c0 in the storage type, lowest column in the low bits:
+        // bias (FP8: dequant scale before it, requant multiplier after it), then the ReLU,
+        // which the rounding conversion applies (it commutes with round-to-nearest).
+        // BF16: 32 words of two; FP8: 16 words of four.
+        auto act_pack = [&](const uint32_t (&r)[64], const float *bb, const float *sc, const float *os, int c0,
+                            uint32_t (&w)[32]) {
+            const float4 *b4 = reinterpret_cast<const float4 *>(bb + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < 16; j4++) {
+                const float4 b = b4[j4];
+                float x0 = __uint_as_float(r[4 * j4]), x1 = __uint_as_float(r[4 * j4 + 1]);
+                float x2 = __uint_as_float(r[4 * j4 + 2]), x3 = __uint_as_float(r[4 * j4 + 3]);
+                if constexpr (FP8) {
+                    const float4 s = reinterpret_cast<const float4 *>(sc + c0)[j4];
+                    const float4 o = reinterpret_cast<const float4 *>(os + c0)[j4];
+                    x0 = (x0 * s.x + b.x) * o.x;
+                    x1 = (x1 * s.y + b.y) * o.y;
+                    x2 = (x2 * s.z + b.z) * o.z;
+                    x3 = (x3 * s.w + b.w) * o.w;
+                    w[j4] = e4m3x2_relu(x0, x1) | (e4m3x2_relu(x2, x3) << 16);
+                } else {
+                    w[2 * j4] = bf16x2_relu(x0 + b.x, x1 + b.y);
+                    w[2 * j4 + 1] = bf16x2_relu(x2 + b.z, x3 + b.w);
+                }
+            }
+        };
+        // every lane's tensor-memory accesses are complete (fence, warp sync): one arrival a warp
+        auto release = [&](uint32_t bar) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar);
+        };
+        uint64_t w_full = 0;   // CTA 0, warp 2: waits for a full accumulator
+        auto wait_full = [&]() {
+            const uint64_t t0 = det ? gtimer() : 0;
+            const bool got = __all_sync(0xffffffffu,
+                                        mbar_wait(afull(x), (uint32_t)pp.fe & 1u, lim, cta_abort, a.status));
+            if (det) w_full += gtimer() - t0;
+            pp.fe++;
+            if (got) tc_fence_after();
+            return got;
+        };
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            const int p2 = t / n_sb, sb = t % n_sb;
+            bool ok = true;
+            // conv1 pieces i = x, x + 2: position pb = i / 2, channel half h = x, in two 64-column
+            // chunks, each to its A-operand columns
+            for (int pb = 0; pb < 2 && ok; pb++) {
+                if (!(ok = wait_full())) break;
+#pragma unroll 1
+                for (int c = 0; c < 2; c++) {
+                    const int ch = x * 128 + c * 64;
+                    uint32_t r[64], w[32];
+                    tmem_ld64(src + (uint32_t)(c * 64), r);
+                    if (c == 1) release(aempty(x));   // the accumulator is in registers
+                    act_pack(r, b1, s1, o1, ch, w);
+                    const uint32_t dst = tmem_base + lanes + (uint32_t)((pb * 256 + ch) / EPC);
+                    if constexpr (FP8) tmem_st16(dst, *reinterpret_cast<const uint32_t(*)[16]>(w));
+                    else tmem_st32(dst, w);
+                }
+                tmem_st_wait();
+                release(a2full(2 * pb + x));
+            }
+            if (!ok) break;
+            // conv2 piece 4 + x: output channels x * 128 + [0, 128) of position p2, two 64-column
+            // chunks, each in two 32-column halves through the warp's staging rows to the
+            // pair-major destination of position p2 of each slot (16-byte pieces in row passes)
+            if (!(ok = wait_full())) break;
+#pragma unroll 1
+            for (int c = 0; c < 2; c++) {
+                const int ch = x * 128 + c * 64;
+                uint32_t r[64], w[32];
+                tmem_ld64(src + (uint32_t)(c * 64), r);
+                if (c == 1) release(aempty(x));   // the accumulator is in registers
+                act_pack(r, b2, s2, o2, ch, w);
+                constexpr int WPH = 32 / EPC;   // words per 32-column half
+                constexpr int UU = CB / 16, RPP = 32 / UU;
+                const int rr = lane / UU, uu = lane % UU;
+#pragma unroll
+                for (int hf = 0; hf < 2; hf++) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(stg + lane * SROW);
+#pragma unroll
+                    for (int j = 0; j < WPH / 4; j++)
+                        dst[j] = make_uint4(w[hf * WPH + 4 * j], w[hf * WPH + 4 * j + 1], w[hf * WPH + 4 * j + 2],
+                                            w[hf * WPH + 4 * j + 3]);
+                    __syncwarp();
+                    uint8_t *gbase = reinterpret_cast<uint8_t *>(L2.out) +
+                                     ((size_t)(p2 >> 1) * a.B * 2 * L2.N + (size_t)(p2 & 1) * L2.N + ch + 32 * hf) * OES +
+                                     uu * 16;
+#pragma unroll
+                    for (int pass = 0; pass < UU; pass++) {
+                        const int r_in = pass * RPP + rr;
+                        const int slot = sb * BM + q * 32 + r_in;
+                        const uint4 val = *reinterpret_cast<const uint4 *>(stg + r_in * SROW + uu * 16);
+                        if (slot < M) *reinterpret_cast<uint4 *>(gbase + (size_t)slot * 2 * L2.N * OES) = val;
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        if (det && warp == 2 && lane == 0) {
+            atomicAdd(&a.detail[4 * (l + 1) + 2], gtimer() - t_phase);
+            atomicAdd(&a.detail[4 * l + 3], w_full);
+        }
     }
     return t_phase;
 }
@@ -493,10 +810,10 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int S = a.stages;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * a.stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + a.ring_bytes);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 4);
     volatile int *cta_abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
-    float *prm = reinterpret_cast<float *>(smem + S * a.stage_bytes + (2 * S + 4) * 8 + 16);
+    float *prm = reinterpret_cast<float *>(smem + a.ring_bytes + kBarBytes);
     uint8_t *staging = reinterpret_cast<uint8_t *>(prm + a.prm_floats);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -507,9 +824,23 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         }
         for (int x = 0; x < 2; x++) {
             mbar_init(smem_u32(&bars[2 * S + x]), 1);
-            mbar_init(smem_u32(&bars[2 * S + 2 + x]), 32 * kEpiWarps);
+            mbar_init(smem_u32(&bars[2 * S + 2 + x]), kEpiWarps);   // one arrival per epilogue warp
         }
         mbar_init(smem_u32(&bars[2 * S + 5]), 1);   // resident weights (after tmem_slot and cta_abort)
+        if (a.fuse) {
+            const int F0 = kFuBar(S);
+            for (int u = 0; u < a.fu; u++) {
+                mbar_init(smem_u32(&bars[F0 + u]), 1);
+                mbar_init(smem_u32(&bars[F0 + a.fu + u]), 1);
+            }
+            // A-operand quarters and accumulator-free barriers: one arrival per warp of a warpgroup
+            for (int i = 0; i < 4; i++) mbar_init(smem_u32(&bars[F0 + 2 * a.fu + i]), kEpiWarps / 2);
+            mbar_init(smem_u32(&bars[F0 + 2 * a.fu + 4]), 1);
+            for (int x = 0; x < 2; x++) {
+                mbar_init(smem_u32(&bars[F0 + 2 * a.fu + 5 + x]), 1);
+                mbar_init(smem_u32(&bars[F0 + 2 * a.fu + 7 + x]), kEpiWarps / 2);
+            }
+        }
         *cta_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -571,6 +902,15 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         if (blockIdx.x == 0 && threadIdx.x == 0) *ext_next = 0;   // the head phase raises it
         for (int l = 0; l < a.n_layers && ok; l++) {
             const PLayer &L = a.layer[l];
+            if (l == 0 && a.fuse) {   // conv1 and conv2 in one phase
+                const int n2 = layer_pos(a.layer[1], ext), n2_prev = layer_pos(a.layer[1], ext_prev);
+                const uint64_t tp = fused_phase<FP8>(a, 0, n2, n2_prev, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+                l = 1;
+                ok = grid_sync(a, target, cta_abort);
+                if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
+                mark(SIMNET_KERNEL_LAYER0 + a.layer[l].kind);
+                continue;
+            }
             const int n_now = L.out_part ? 1 : layer_pos(L, ext), n_prev = L.out_part ? 1 : layer_pos(L, ext_prev);
             const int l2 = L.pair_next ? l + 1 : -1;   // a residual block's conv takes its projection along
             const uint64_t tp =
@@ -737,7 +1077,7 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
     a.w2h_off = (off + 3) & ~3;
     a.prm_floats = a.w2h_off + (c->n_out == 2 ? 0 : kEpiWarps * c->n_out * 32);
     const size_t staging = (size_t)kEpiWarps * 32 * (32 * (fp8 ? 1 : 2) + 16);
-    const size_t fixed = 1024 + 256 + (size_t)a.prm_floats * 4 + staging;
+    const size_t fixed = 1024 + kBarBytes + (size_t)a.prm_floats * 4 + staging;
     const size_t budget = 232448 - 1024;   // minus the static shared memory of the compaction
     a.stages = (int)std::min<size_t>(6, (budget - fixed) / a.stage_bytes);
     // the head phase reuses the stage ring as 10 x 256 queue entries: fewest stages that hold them
@@ -750,7 +1090,29 @@ bool launch_persistent(simnet_ctx *c, int B, int64_t n_steps, bool uneven, cudaS
         why = "ring too small for the head and gather scratch";
         return false;
     }
-    const size_t smem = (size_t)a.stages * a.stage_bytes + fixed;
+    // conv1 + conv2 in one phase: conv1's weights stay in shared memory for the phase,
+    // and 16 KB operand units fill the room left (the ring and the shared memory the
+    // stages leave unused)
+    a.fuse = 0;
+    if (!(c->cfg.flags & SIMNET_FLAG_NO_FUSE) && !c->residual && c->cfg.n_conv >= 2 && C == 256 &&
+        c->layer[0].K == 2 * kNFP && c->layer[0].N == C && c->layer[1].K == 2 * C && c->layer[1].N == C &&
+        c->n_layers > 2) {
+        const int w1_units = 2 * (2 * kNFP * (int)es / ROW_BYTES);
+        // as many units as the shared memory left beside the fixed part holds, within the barrier area
+        const int room = (int)((budget - fixed) / A_BYTES), cap = (kBarBytes / 8 - kFuBar(a.stages) - kFuBars) / 2;
+        const int U = std::min(cap, room - w1_units);
+        if (U >= 3) {
+            if (!encode_map_2d(a.tW1, c->cfg.precision, c->layer[0].B, (uint64_t)c->layer[0].K, (uint64_t)C, BK, 128,
+                               why) ||
+                !encode_map_2d(a.tW2h, c->cfg.precision, c->layer[1].B, (uint64_t)c->layer[1].K, (uint64_t)C, BK, 128,
+                               why))
+                return false;
+            a.fuse = 1;
+            a.fu = U;
+        }
+    }
+    a.ring_bytes = std::max(a.stages * a.stage_bytes, a.fuse ? (a.fu + 2 * (int)es) * A_BYTES : 0);
+    const size_t smem = (size_t)a.ring_bytes + fixed;
     void (*k)(PArgs) = nullptr;
     switch (c->n_out) {
         case 3: k = fp8 ? persist_kernel<true, 3> : persist_kernel<false, 3>; break;

@@ -29,6 +29,7 @@ FLAG_HYBRID_HEAD = 0x40
 FLAG_STORE_QUEUE = 0x80
 FLAG_RESIDUAL = 0x100
 FLAG_FIXED_PATH = 0x200
+FLAG_NO_FUSE = 0x400
 MAX_GEMMS = 25          # GEMMs of the deepest CNN: 3 per residual block (up to 8) + FC1
 PATHS = {0: "none", 1: "layerwise", 2: "persistent", 3: "cluster"}
 KERNEL_KINDS = 12
@@ -170,14 +171,15 @@ class Simnet:
                  graph: bool = True, spin_limit_ns: int = 0, kernel_events: bool = False,
                  pdl: bool = True, persistent: bool = True, barrier_limit_us: int = 0,
                  cluster: bool = True, hybrid: bool = False, store_queue: bool = False,
-                 residual: bool = False, auto_path: bool = True):
+                 residual: bool = False, auto_path: bool = True, fuse: bool = True):
         L = lib()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         flags = ((FLAG_RETIRE_STRICT if strict else 0) | (0 if graph else FLAG_NO_GRAPH)
                  | (FLAG_KERNEL_EVENTS if kernel_events else 0) | (0 if pdl else FLAG_NO_PDL)
                  | (0 if persistent else FLAG_LAYERWISE) | (0 if cluster else FLAG_NO_CLUSTER)
                  | (FLAG_HYBRID_HEAD if hybrid else 0) | (FLAG_STORE_QUEUE if store_queue else 0)
-                 | (FLAG_RESIDUAL if residual else 0) | (0 if auto_path else FLAG_FIXED_PATH))
+                 | (FLAG_RESIDUAL if residual else 0) | (0 if auto_path else FLAG_FIXED_PATH)
+                 | (0 if fuse else FLAG_NO_FUSE))
         self._cfg = _Config(window, n_conv, channels, hidden, retire_width, prec, flags, barrier_limit_us,
                             spin_limit_ns)
         self.window = window
