@@ -198,7 +198,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
     const int S = a.stages, N = L.N;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // parameters were staged at the start of the call; only FC1's padding row changes per step
-    float *s_bias = prm + L.prm_off, *s_scale = s_bias + N, *s_oscale = s_bias + 2 * N;
+    float *s_bias = prm + L.prm_off;
     float *s_w2 = s_bias + (FP8 ? 3 * N : N), *s_cst = prm + a.cst_off;
     if (L.out_part) {
         for (int i = threadIdx.x; i < N; i += blockDim.x) s_cst[i] = a.fc1_const[(size_t)e * N + i];
@@ -374,18 +374,17 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                     // shortcut (this loop bounded the first layer's phase at c5)
                     const float4 *b4 = reinterpret_cast<const float4 *>(t_bias + col0);
                     const float4 *s4 = reinterpret_cast<const float4 *>(t_scale + col0);
-                    const float4 *o4 = reinterpret_cast<const float4 *>(t_oscale + col0);
 #pragma unroll
                     for (int j4 = 0; j4 < 8; j4++) {
                         const float4 bb = b4[j4];
                         float x0 = __uint_as_float(r[4 * j4]), x1 = __uint_as_float(r[4 * j4 + 1]);
                         float x2 = __uint_as_float(r[4 * j4 + 2]), x3 = __uint_as_float(r[4 * j4 + 3]);
-                        if constexpr (FP8) {
-                            const float4 sc = s4[j4], os = o4[j4];
-                            v[4 * j4] = fmaxf(x0 * sc.x + bb.x, 0.f) * os.x;
-                            v[4 * j4 + 1] = fmaxf(x1 * sc.y + bb.y, 0.f) * os.y;
-                            v[4 * j4 + 2] = fmaxf(x2 * sc.z + bb.z, 0.f) * os.z;
-                            v[4 * j4 + 3] = fmaxf(x3 * sc.w + bb.w, 0.f) * os.w;
+                        if constexpr (FP8) {   // scale and bias carry the requant multiplier
+                            const float4 sc = s4[j4];
+                            v[4 * j4] = fmaxf(x0 * sc.x + bb.x, 0.f);
+                            v[4 * j4 + 1] = fmaxf(x1 * sc.y + bb.y, 0.f);
+                            v[4 * j4 + 2] = fmaxf(x2 * sc.z + bb.z, 0.f);
+                            v[4 * j4 + 3] = fmaxf(x3 * sc.w + bb.w, 0.f);
                         } else {
                             v[4 * j4] = fmaxf(x0 + bb.x, 0.f);
                             v[4 * j4 + 1] = fmaxf(x1 + bb.y, 0.f);
@@ -691,16 +690,16 @@ __device__ uint64_t fused_phase(const PArgs &a, int l, int n2, int n2_prev, uint
         const int q = warp & 3, x = (warp - 2) >> 2;
         const uint32_t lanes = (uint32_t)(q * 32) << 16;
         const uint32_t src = tmem_base + lanes + kFuAcc + (uint32_t)x * 128;
-        const float *b1 = prm + L1.prm_off, *s1 = b1 + L1.N, *o1 = b1 + 2 * L1.N;
-        const float *b2 = prm + L2.prm_off, *s2 = b2 + L2.N, *o2 = b2 + 2 * L2.N;
+        const float *b1 = prm + L1.prm_off, *s1 = b1 + L1.N;   // FP8: scale and bias folded with the
+        const float *b2 = prm + L2.prm_off, *s2 = b2 + L2.N;   // requant multiplier
         constexpr int OES = FP8 ? 1 : 2;
         constexpr int CB = 32 * OES, SROW = CB + 16;
         uint8_t *stg = staging + (warp - 2) * 32 * SROW;
         // 64 accumulator columns from c0 in the storage type, lowest column in the low bits:
-        // bias (FP8: dequant scale before it, requant multiplier after it), then the ReLU,
+        // bias (FP8: dequant scale before it, both times the requant multiplier), then the ReLU,
         // which the rounding conversion applies (it commutes with round-to-nearest).
         // BF16: 32 words of two; FP8: 16 words of four.
-        auto act_pack = [&](const uint32_t (&r)[64], const float *bb, const float *sc, const float *os, int c0,
+        auto act_pack = [&](const uint32_t (&r)[64], const float *bb, const float *sc, int c0,
                             uint32_t (&w)[32]) {
             const float4 *b4 = reinterpret_cast<const float4 *>(bb + c0);
 #pragma unroll
@@ -708,14 +707,9 @@ __device__ uint64_t fused_phase(const PArgs &a, int l, int n2, int n2_prev, uint
                 const float4 b = b4[j4];
                 float x0 = __uint_as_float(r[4 * j4]), x1 = __uint_as_float(r[4 * j4 + 1]);
                 float x2 = __uint_as_float(r[4 * j4 + 2]), x3 = __uint_as_float(r[4 * j4 + 3]);
-                if constexpr (FP8) {
+                if constexpr (FP8) {   // scale and bias carry the requant multiplier
                     const float4 s = reinterpret_cast<const float4 *>(sc + c0)[j4];
-                    const float4 o = reinterpret_cast<const float4 *>(os + c0)[j4];
-                    x0 = (x0 * s.x + b.x) * o.x;
-                    x1 = (x1 * s.y + b.y) * o.y;
-                    x2 = (x2 * s.z + b.z) * o.z;
-                    x3 = (x3 * s.w + b.w) * o.w;
-                    w[j4] = e4m3x2_relu(x0, x1) | (e4m3x2_relu(x2, x3) << 16);
+                    w[j4] = e4m3x2_relu(x0 * s.x + b.x, x1 * s.y + b.y) | (e4m3x2_relu(x2 * s.z + b.z, x3 * s.w + b.w) << 16);
                 } else {
                     w[2 * j4] = bf16x2_relu(x0 + b.x, x1 + b.y);
                     w[2 * j4 + 1] = bf16x2_relu(x2 + b.z, x3 + b.w);
@@ -751,7 +745,7 @@ __device__ uint64_t fused_phase(const PArgs &a, int l, int n2, int n2_prev, uint
                     uint32_t r[64], w[32];
                     tmem_ld64(src + (uint32_t)(c * 64), r);
                     if (c == 1) release(aempty(x));   // the accumulator is in registers
-                    act_pack(r, b1, s1, o1, ch, w);
+                    act_pack(r, b1, s1, ch, w);
                     const uint32_t dst = tmem_base + lanes + (uint32_t)((pb * 256 + ch) / EPC);
                     if constexpr (FP8) tmem_st16(dst, *reinterpret_cast<const uint32_t(*)[16]>(w));
                     else tmem_st32(dst, w);
@@ -770,7 +764,7 @@ __device__ uint64_t fused_phase(const PArgs &a, int l, int n2, int n2_prev, uint
                 uint32_t r[64], w[32];
                 tmem_ld64(src + (uint32_t)(c * 64), r);
                 if (c == 1) release(aempty(x));   // the accumulator is in registers
-                act_pack(r, b2, s2, o2, ch, w);
+                act_pack(r, b2, s2, ch, w);
                 constexpr int WPH = 32 / EPC;   // words per 32-column half
                 constexpr int UU = CB / 16, RPP = 32 / UU;
                 const int rr = lane / UU, uu = lane % UU;
@@ -874,8 +868,13 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
             pb[i] = L.bias[i];
             if (FP8) {
-                pb[N + i] = L.scale[i];
-                pb[2 * N + i] = L.oscale ? L.oscale[i] : 1.f;
+                // a conv layer's requant multiplier o (> 0) is folded in: max(x s + b, 0) o =
+                // max(x (s o) + b o, 0), one FMA before the saturating conversion
+                const float o = L.oscale ? L.oscale[i] : 1.f;
+                const bool fold = !L.out_part && L.relu;
+                pb[N + i] = fold ? L.scale[i] * o : L.scale[i];
+                pb[2 * N + i] = o;
+                if (fold) pb[i] = L.bias[i] * o;
             }
             if (NO == 2 && L.out_part) {   // the hybrid / store heads stage their FC2 rows per warp
                 float *w = pb + (FP8 ? 3 * N : N);
