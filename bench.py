@@ -43,7 +43,18 @@ TRAFFIC = {
     # chip and in L2 (profiles/cluster_kernel_c2_bf16_traffic.md, ..._fp8_traffic.md)
     ("c2", "bf16", "cluster_kernel"): 2.256896e6 + 5.301504e6,
     ("c2", "fp8", "cluster_kernel"): 1.857792e6 + 5.340160e6,
+    # persist_kernel, c5 (conv1 and conv2 in one phase): 164.81 GB (BF16) and 78.85 GB (FP8)
+    # over one call of 65,536 sub-traces cut to 100 instructions (ncu, one pass;
+    # profiles/persist_kernel_c5_fused.md), scaled by instructions to the 100M-instruction
+    # launch (the traffic a step follows the active sub-traces: one instruction each)
+    ("c5", "bf16", "persist_kernel"): 164.814706944e9 * 1e8 / 6_553_600,
+    ("c5", "fp8", "persist_kernel"): 78.846094848e9 * 1e8 / 6_553_600,
 }
+
+
+def traffic_of(args, workload, prec, kernel):
+    """TRAFFIC's figure for a launch of the whole workload; none for a cut one."""
+    return None if getattr(args, "subtrace_len", 0) else TRAFFIC.get((workload, prec, kernel))
 
 
 def peaks():
@@ -423,7 +434,7 @@ def run_ours(args):
     if not args.no_breakdown and path == "cluster":
         # one launch does every step: the whole call's algorithmic work over its device time
         out["roofline"] = whole_call_roofline(w, args.precision, N, main["ms_per_step"], "cluster_kernel",
-                                              TRAFFIC.get((w.name, args.precision, "cluster_kernel")))
+                                              traffic_of(args, w.name, args.precision, "cluster_kernel"))
         ph = cluster_phases(w, args, blob32, rec, off, clocks.get("sm_mhz") or 2032.0)
         out["phases_us_per_step"] = ph
         # the padding extent: the kernel computes only the last-conv positions below
@@ -444,7 +455,7 @@ def run_ours(args):
             # one launch does every step: its roofline is the whole call's work over its
             # device time; the per-phase table explains the split
             out["roofline"] = whole_call_roofline(w, args.precision, N, main["ms_per_step"], "persist_kernel",
-                                                  TRAFFIC.get((w.name, args.precision, "persist_kernel")))
+                                                  traffic_of(args, w.name, args.precision, "persist_kernel"))
             out["roofline"]["dominant_phase"] = roof
 
     forms = {}
@@ -460,7 +471,7 @@ def run_ours(args):
         s8.close()
         r8["note"] = "FP8 e4m3 tcgen05 path, same workload and timing"
         k8 = PATH_KERNEL.get(r8["kernel_mode"], r8["kernel_mode"])
-        r8["roofline"] = whole_call_roofline(w, "fp8", N, r8["ms_per_step"], k8, TRAFFIC.get((w.name, "fp8", k8)))
+        r8["roofline"] = whole_call_roofline(w, "fp8", N, r8["ms_per_step"], k8, traffic_of(args, w.name, "fp8", k8))
         out["fp8_form"] = r8
         forms["fp8_form"] = c8
     if train_info:
@@ -552,7 +563,7 @@ def run_extra(args, timer):
         r["workload"] = f"c5: {w5.description}; weights: {I.weight_recipe(w5)}"
         r["roofline"] = whole_call_roofline(w5, prec, t5.n_instructions, r["ms_per_step"],
                                             PATH_KERNEL.get(r["kernel_mode"], r["kernel_mode"]),
-                                            TRAFFIC.get(("c5", prec, PATH_KERNEL.get(r["kernel_mode"]))))
+                                            traffic_of(args, "c5", prec, PATH_KERNEL.get(r["kernel_mode"])))
         if r["kernel_mode"] == "persistent":
             r["roofline"].update(executed_work(w5, prec, t5.n_instructions, r["ms_per_step"], b5, rec, off))
         res[f"c5_{prec}"] = {"record": r, "cycles": c, "check": (w5, t5, b5, ids5)}
@@ -632,18 +643,40 @@ def roofline(w, args, blob32, rec, off, B, path):
         sim.autotune(B)
     sim.simulate(rec, off, cycles_out=cyc, stats=True)
     ms, n = sim.kernel_times()
+    # the persistent kernel runs conv1 and conv2 of a 256-channel CNN as one phase,
+    # timed under conv2's kind (conv1's kind then has no phases); CTA 0 sums that
+    # phase's waits in conv1's row of the phase detail
+    fused = n[1] == 0 and n[2] > 0
+    waits = None
+    if fused:
+        d = sim.phase_detail(2)
+        waits = {"mma_warp_free_accumulator": d[0][0] / 1e6, "mma_warp_operand_unit": d[0][1] / 1e6,
+                 "mma_warp_a_operand_quarter": d[0][2] / 1e6, "epilogue_full_accumulator": d[0][3] / 1e6,
+                 "phase_to_last_mma_commit": d[1][1] / 1e6, "phase_to_epilogue_done": d[1][2] / 1e6}
     sim.close()
     total = sum(ms)
     steps = max(n[10], 1)   # head/update: one launch (or phase) a step
+
+    def units(k):
+        amt, unit, bound = algorithmic_units(w, k, B, args.precision)
+        if fused and k == 2:
+            amt += algorithmic_units(w, 1, B, args.precision)[0]
+        return amt, unit, bound
+
+    def name(k):
+        return "conv1_conv2_gemms_one_phase" if fused and k == 2 else kind_name(w, k)
+
     kernels = {}
     for k in range(len(ms)):
         if n[k] == 0:
             continue
-        amt, unit, bound = algorithmic_units(w, k, B, args.precision)
-        kernels[kind_name(w, k)] = {"launches": n[k], "ms_total": ms[k], "share": ms[k] / total,
-                                    "avg_us": 1e3 * ms[k] / n[k], "bound": bound}
+        amt, unit, bound = units(k)
+        kernels[name(k)] = {"launches": n[k], "ms_total": ms[k], "share": ms[k] / total,
+                            "avg_us": 1e3 * ms[k] / n[k], "bound": bound}
+        if fused and k == 2:   # CTA 0's summed milliseconds
+            kernels[name(k)]["cta0_ms"] = waits
     dom = max(range(len(ms)), key=lambda k: ms[k])
-    amt, unit, bound = algorithmic_units(w, dom, B, args.precision)
+    amt, unit, bound = units(dom)
     # per launch: the kind's per-step work over its launches (or phases) a step
     amt = amt * steps / n[dom]
     avg_s = ms[dom] / n[dom] / 1e3
@@ -658,8 +691,8 @@ def roofline(w, args, blob32, rec, off, B, path):
     else:
         achieved = amt / avg_s / 1e9
         peak, punit, note = hbm, "GB/s", f"{src} HBM copy"
-    traffic = TRAFFIC.get((w.name, args.precision, kind_name(w, dom)))
-    roof = {"kernel": kind_name(w, dom), "bound": bound, "achieved": achieved, "peak": peak,
+    traffic = traffic_of(args, w.name, args.precision, name(dom))
+    roof = {"kernel": name(dom), "bound": bound, "achieved": achieved, "peak": peak,
             "unit": punit, "frac": achieved / peak, "peak_source": note, "traffic": traffic,
             "avg_launch_us": avg_s * 1e6, "algorithmic_per_launch": amt, "algorithmic_unit": unit,
             "share_of_step": ms[dom] / total, "steps_timed": steps}

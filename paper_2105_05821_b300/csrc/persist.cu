@@ -930,6 +930,8 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             const int n_act = *a.A->n_active, stride = gridDim.x * kWarps;
             int slot = blockIdx.x * kWarps + warp;
             HeadState cur;
+            int ext_run = 0;   // this warp's largest next-step extent, published once (one atomic
+                               // per warp: an atomic per slot on one address serialises in L2)
             if (slot < n_act) head_load<NO>(a.A, slot, a.A->active[slot], lane, a.part, a.P, a.B, cur);
             int b_next = slot + stride < n_act ? a.A->active[slot + stride] : 0;
             for (; slot < n_act; slot += stride) {
@@ -938,10 +940,11 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
                 HeadState nxt;
                 if (s1 < n_act) head_load<NO>(a.A, s1, b_next, lane, a.part, a.P, a.B, nxt);
                 head_update_state<T, NO>(a.A, slot, lane, cur, a.part, a.P, a.B, a.b2, reinterpret_cast<T *>(a.X),
-                                         reinterpret_cast<uint64_t *>(mine), mine + 256 * 8, a.B, ext_next);
+                                         reinterpret_cast<uint64_t *>(mine), mine + 256 * 8, a.B, &ext_run);
                 cur = nxt;
                 b_next = b_after;
             }
+            if (lane == 0 && ext_run > 0) atomicMax(ext_next, ext_run);
         }
         ok = grid_sync(a, target, cta_abort);
         mark(SIMNET_KERNEL_HEAD_UPDATE);

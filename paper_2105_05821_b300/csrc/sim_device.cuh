@@ -461,8 +461,9 @@ __device__ __forceinline__ int stores_to_write_queue(const uint64_t *__restrict_
 // shared-memory scratch of 256 queue entries.
 // With `pm_slots` > 0 the feature tile is pair-major over that many slots:
 // only rows 0 .. max(old, new context length) are written (rows past the
-// context are kept zero) and the next step's batch extent `ext` is raised to
-// the new context length + 1.
+// context are kept zero) and `*ext`, the caller's running maximum of the next
+// step's batch extent (a register of the calling warp, which publishes it once),
+// is raised to the new context length + 1.
 // What the head of one slot reads before any arithmetic of its own: the
 // sub-trace, its state and (regression head) this lane's share of the FC2
 // partial sums.  Loaded one slot ahead by head phases that walk many slots, so
@@ -662,7 +663,7 @@ __device__ __forceinline__ void head_update_state(const StepArgs *__restrict__ A
         constexpr int SR = stage_row_bytes<T>();
         const int ctx_new = ql + ml;
         const int rows = pm_slots > 0 ? min(W, max(ctx_old, ctx_new) + 1) : W;
-        if (pm_slots > 0 && lane == 0) atomicMax(ext, ctx_new + 1);
+        if (pm_slots > 0) *ext = max(*ext, ctx_new + 1);   // the caller's running maximum
         for (int r0 = 0; r0 < rows; r0 += 32) {   // a lane builds a row, the warp stores rows whole
             const int r = r0 + lane;
             T *row = reinterpret_cast<T *>(stg + lane * SR);
