@@ -43,12 +43,12 @@ TRAFFIC = {
     # chip and in L2 (profiles/cluster_kernel_c2_bf16_traffic.md, ..._fp8_traffic.md)
     ("c2", "bf16", "cluster_kernel"): 2.256896e6 + 5.301504e6,
     ("c2", "fp8", "cluster_kernel"): 1.857792e6 + 5.340160e6,
-    # persist_kernel, c5 (conv1 and conv2 in one phase): 164.81 GB (BF16) and 78.85 GB (FP8)
+    # persist_kernel, c5 (conv1 and conv2 in one phase): 164.76 GB (BF16) and 78.86 GB (FP8)
     # over one call of 65,536 sub-traces cut to 100 instructions (ncu, one pass;
     # profiles/persist_kernel_c5_fused.md), scaled by instructions to the 100M-instruction
     # launch (the traffic a step follows the active sub-traces: one instruction each)
-    ("c5", "bf16", "persist_kernel"): 164.814706944e9 * 1e8 / 6_553_600,
-    ("c5", "fp8", "persist_kernel"): 78.846094848e9 * 1e8 / 6_553_600,
+    ("c5", "bf16", "persist_kernel"): 164.7619008e9 * 1e8 / 6_553_600,
+    ("c5", "fp8", "persist_kernel"): 78.856364288e9 * 1e8 / 6_553_600,
 }
 
 
