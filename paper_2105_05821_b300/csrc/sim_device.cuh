@@ -397,6 +397,23 @@ __device__ __forceinline__ void flush_rows_pm(const uint8_t *__restrict__ stg, T
     }
 }
 
+// Store n staged rows of one slot (its rows r0 ..) into the pair-major tile, U
+// lanes per row (the head's path: no division to recover slot and row).
+template <typename T>
+__device__ __forceinline__ void flush_slot_rows_pm(const uint8_t *__restrict__ stg, T *__restrict__ X, int Bs,
+                                                   int slot, int r0, int n, int lane) {
+    constexpr int RB = kNFP * (int)sizeof(T), SR = stage_row_bytes<T>(), U = RB / 16, RPP = 32 / U;
+    const int rr = lane / U, u = lane % U;
+#pragma unroll 4
+    for (int pass = 0; pass < U; pass++) {
+        const int r = pass * RPP + rr;
+        if (r < n) {
+            uint8_t *g = reinterpret_cast<uint8_t *>(pm_row<T>(X, Bs, slot, r0 + r)) + u * 16;
+            *reinterpret_cast<uint4 *>(g) = *reinterpret_cast<const uint4 *>(stg + r * SR + u * 16);
+        }
+    }
+}
+
 // Dense gather of 32 rows into the pair-major tile; the lane holding row 0 of
 // an active sub-trace raises the batch extent to its queue length + 1.
 template <typename T>
@@ -679,7 +696,7 @@ __device__ __forceinline__ void head_update_state(const StepArgs *__restrict__ A
             }
             __syncwarp();
             if (pm_slots > 0)
-                flush_rows_pm<T>(stg, X, pm_slots, W, (int64_t)slot * W + r0, min(32, rows - r0), lane);
+                flush_slot_rows_pm<T>(stg, X, pm_slots, slot, r0, min(32, rows - r0), lane);
             else
                 flush_rows<T>(stg, X, (int64_t)slot * W + r0, min(32, rows - r0), lane);
             __syncwarp();
