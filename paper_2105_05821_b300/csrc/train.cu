@@ -423,46 +423,62 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const float *__restrict__
 }
 
 // Column sums out[c] = sum over rows of d[r][c] in two passes with no atomics:
-// block g sums its share of the rows into part[g][c] (a thread takes one column
-// pair, 256 / (C / 2) rows at a time, then the block adds its row lanes), and
-// one thread per column adds the blocks' sums.  C even, at most 512.
+// block g sums its share of the rows into part[g][c], then one thread per column
+// adds the blocks' sums.  In a block a thread takes one 16-byte column vector
+// (V = 8 BF16 or 4 FP32 columns) of every rpb-th row, four rows in flight, and
+// the block adds its rpb row lanes in a fixed order through shared memory (the
+// sums do not depend on scheduling).  The C columns are a row's first C of ld
+// (the caller splits wider rows); C a multiple of V, at most 512; threads past
+// the last whole row lane stay idle.
 constexpr int kColBlocks = 2 * 148;
 template <typename T>
-__global__ void __launch_bounds__(256) colsum_part_kernel(const T *__restrict__ d, int64_t rows, int C,
+__global__ void __launch_bounds__(256) colsum_part_kernel(const T *__restrict__ d, int64_t rows, int C, int ld,
                                                           float *__restrict__ part) {
-    __shared__ float sh[512];
-    const int CP = C / 2, cp = threadIdx.x % CP, rl = threadIdx.x / CP, rpb = blockDim.x / CP;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) sh[c] = 0.f;
-    __syncthreads();
-    if (rl < rpb) {
-        auto ld = [&](int64_t r) -> float2 {
-            if constexpr (sizeof(T) == 4) {
-                return reinterpret_cast<const float2 *>(d + r * C)[cp];
-            } else {
-                const __nv_bfloat162 v = reinterpret_cast<const __nv_bfloat162 *>(d + r * C)[cp];
-                return make_float2(__bfloat162float(v.x), __bfloat162float(v.y));
+    constexpr int V = 16 / (int)sizeof(T);
+    __shared__ float sh[256 * V];   // [row lane][C]: rpb * C = 256 * V floats
+    const int CV = C / V, cv = threadIdx.x % CV, rl = threadIdx.x / CV, rpb = blockDim.x / CV;
+    const bool on = rl < rpb;
+    float acc[V];
+#pragma unroll
+    for (int k = 0; k < V; k++) acc[k] = 0.f;
+    auto add = [&](const uint4 &u) {
+        if constexpr (sizeof(T) == 4) {
+            acc[0] += __uint_as_float(u.x);
+            acc[1] += __uint_as_float(u.y);
+            acc[2] += __uint_as_float(u.z);
+            acc[3] += __uint_as_float(u.w);
+        } else {
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                // BF16 pair to FP32: each value's 16 bits as the high half of a word
+                acc[2 * k] += __uint_as_float(w[k] << 16);
+                acc[2 * k + 1] += __uint_as_float(w[k] & 0xffff0000u);
             }
-        };
-        float2 a = make_float2(0.f, 0.f), b = a;   // two rows in flight per iteration
-        const int64_t step = (int64_t)gridDim.x * rpb;
-        int64_t r = (int64_t)blockIdx.x * rpb + rl;
-        for (; r + step < rows; r += 2 * step) {
-            const float2 u = ld(r), v = ld(r + step);
-            a.x += u.x;
-            a.y += u.y;
-            b.x += v.x;
-            b.y += v.y;
         }
-        if (r < rows) {
-            const float2 u = ld(r);
-            a.x += u.x;
-            a.y += u.y;
-        }
-        atomicAdd(&sh[2 * cp], a.x + b.x);   // shared-memory sums of the block's row lanes
-        atomicAdd(&sh[2 * cp + 1], a.y + b.y);
+    };
+    const uint4 *base = reinterpret_cast<const uint4 *>(d) + cv;
+    const int64_t LV = ld / V;   // 16-byte vectors a row
+    const int64_t step = (int64_t)gridDim.x * rpb;
+    int64_t r = on ? (int64_t)blockIdx.x * rpb + rl : rows;
+    for (; r + 3 * step < rows; r += 4 * step) {
+        const uint4 u0 = base[r * LV], u1 = base[(r + step) * LV];
+        const uint4 u2 = base[(r + 2 * step) * LV], u3 = base[(r + 3 * step) * LV];
+        add(u0);
+        add(u1);
+        add(u2);
+        add(u3);
     }
+    for (; r < rows; r += step) add(base[r * LV]);
+    if (on)
+#pragma unroll
+        for (int k = 0; k < V; k++) sh[rl * C + cv * V + k] = acc[k];
     __syncthreads();
-    for (int c = threadIdx.x; c < C; c += blockDim.x) part[(size_t)blockIdx.x * C + c] = sh[c];
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float t = 0.f;
+        for (int q = 0; q < rpb; q++) t += sh[q * C + c];
+        part[(size_t)blockIdx.x * C + c] = t;
+    }
 }
 
 // A block takes 32 columns; its 8 warps sum every 8th block's sums (four loads in
@@ -744,13 +760,17 @@ static void launch_head_bwd(const float *Hh, const float *dz, const float *w2, i
     }
 }
 
-// out[c] = column sums of d [rows][C] (overwritten); part: kColBlocks * C floats.
+// out[c] = column sums of d [rows][C] (overwritten), C a multiple of 16 bytes
+// worth of columns; part: kColBlocks * 512 floats.  Rows wider than 512 columns
+// go in pieces of at most 512.
 template <typename T>
 static void launch_colsum(const T *d, int64_t rows, int C, float *part, float *out, cudaStream_t s) {
-    const int rpb = 256 / (C / 2);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpb - 1) / rpb, kColBlocks));
-    colsum_part_kernel<T><<<g, 256, 0, s>>>(d, rows, C, part);
-    colsum_final_kernel<<<(C + 31) / 32, 256, 0, s>>>(part, g, C, out);
+    for (int c0 = 0; c0 < C; c0 += 512) {
+        const int w = std::min(512, C - c0), rpb = 256 / (w / (16 / (int)sizeof(T)));
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rows + rpb - 1) / rpb, kColBlocks));
+        colsum_part_kernel<T><<<g, 256, 0, s>>>(d + c0, rows, w, C, part);
+        colsum_final_kernel<<<(w + 31) / 32, 256, 0, s>>>(part, g, w, out + c0);
+    }
 }
 
 // Backward from t.dz through the saved activations; gradients (GEMM layout) in t.g*.

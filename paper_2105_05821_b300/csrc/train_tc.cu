@@ -342,6 +342,52 @@ template <int BN> constexpr int tg_stages() { return BN == 256 ? 4 : BN == 128 ?
 // out[i] = sum over s of part[s][i], then (forward) + bias[i % N] and ReLU: the
 // splits of a reduction, summed in a fixed order.  A block takes 32 consecutive
 // elements; its 8 warps sum every 8th split each, then one warp adds the 8.
+// The same four columns at a time (count a multiple of 4): 16-byte loads, a block
+// covers 128 consecutive outputs.
+__global__ void __launch_bounds__(256) tg_reduce4_kernel(const float *__restrict__ part, int splits, int64_t count,
+                                                         float *__restrict__ out, const float *__restrict__ bias, int N,
+                                                         int relu) {
+    __shared__ float4 sh[8][32];
+    const int e = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t i4 = (int64_t)blockIdx.x * 32 + e, c4 = count / 4;
+    const float4 *p4 = reinterpret_cast<const float4 *>(part);
+    auto add = [](float4 &a, const float4 &b) {
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+    };
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i4 < c4) {   // four independent loads in flight per thread
+        float4 s1 = s, s2 = s, s3 = s;
+        int k = g;
+        for (; k + 24 < splits; k += 32) {
+            add(s, p4[(size_t)k * c4 + i4]);
+            add(s1, p4[(size_t)(k + 8) * c4 + i4]);
+            add(s2, p4[(size_t)(k + 16) * c4 + i4]);
+            add(s3, p4[(size_t)(k + 24) * c4 + i4]);
+        }
+        for (; k < splits; k += 8) add(s, p4[(size_t)k * c4 + i4]);
+        add(s, s1);
+        add(s2, s3);
+        add(s, s2);
+    }
+    sh[g][e] = s;
+    __syncthreads();
+    if (g == 0 && i4 < c4) {
+        float4 t = sh[0][e];
+#pragma unroll
+        for (int q = 1; q < 8; q++) add(t, sh[q][e]);
+        float v[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (bias) v[j] += bias[(4 * i4 + j) % N];
+            if (relu) v[j] = fmaxf(v[j], 0.f);
+        }
+        reinterpret_cast<float4 *>(out)[i4] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 __global__ void __launch_bounds__(256) tg_reduce_kernel(const float *__restrict__ part, int splits, int64_t count,
                                                         float *__restrict__ out, const float *__restrict__ bias, int N,
                                                         int relu) {
@@ -481,9 +527,13 @@ void launch_tg(const TgPlan &p, int64_t spin_ns, int32_t *status, cudaStream_t s
     if (a.part) {
         const bool fwd = p.epi == TG_FWD_F32;
         const int64_t count = fwd ? (int64_t)p.M * p.N : (int64_t)p.N * p.ldo;
-        tg_reduce_kernel<<<(unsigned)((count + 31) / 32), 256, 0, s>>>(a.part, p.splits, count,
-                                                                       reinterpret_cast<float *>(p.out),
-                                                                       fwd ? p.bias : nullptr, p.N, fwd ? 1 : 0);
+        if (count % 4 == 0)
+            tg_reduce4_kernel<<<(unsigned)((count / 4 + 31) / 32), 256, 0, s>>>(
+                a.part, p.splits, count, reinterpret_cast<float *>(p.out), fwd ? p.bias : nullptr, p.N, fwd ? 1 : 0);
+        else
+            tg_reduce_kernel<<<(unsigned)((count + 31) / 32), 256, 0, s>>>(a.part, p.splits, count,
+                                                                           reinterpret_cast<float *>(p.out),
+                                                                           fwd ? p.bias : nullptr, p.N, fwd ? 1 : 0);
     }
 }
 
