@@ -392,6 +392,39 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                             v[4 * j4 + 3] = fmaxf(x3 + bb.w, 0.f);
                         }
                     }
+                } else if (L.out_part) {
+                    // FC1: dequant scale (FP8), the constant rows past the extent, bias, ReLU,
+                    // four columns to a load (the general path's order of operations)
+                    const float4 *c4 = reinterpret_cast<const float4 *>(s_cst + col0);
+                    const float4 *b4 = reinterpret_cast<const float4 *>(t_bias + col0);
+                    const float4 *s4 = reinterpret_cast<const float4 *>(t_scale + col0);
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 cc = c4[j4], bb = b4[j4];
+                        float x0 = __uint_as_float(r[4 * j4]), x1 = __uint_as_float(r[4 * j4 + 1]);
+                        float x2 = __uint_as_float(r[4 * j4 + 2]), x3 = __uint_as_float(r[4 * j4 + 3]);
+                        if constexpr (FP8) {
+                            const float4 sc = s4[j4];
+                            x0 *= sc.x;
+                            x1 *= sc.y;
+                            x2 *= sc.z;
+                            x3 *= sc.w;
+                        }
+                        x0 = (x0 + cc.x) + bb.x;
+                        x1 = (x1 + cc.y) + bb.y;
+                        x2 = (x2 + cc.z) + bb.z;
+                        x3 = (x3 + cc.w) + bb.w;
+                        if (Lt.relu) {
+                            x0 = fmaxf(x0, 0.f);
+                            x1 = fmaxf(x1, 0.f);
+                            x2 = fmaxf(x2, 0.f);
+                            x3 = fmaxf(x3, 0.f);
+                        }
+                        v[4 * j4] = x0;
+                        v[4 * j4 + 1] = x1;
+                        v[4 * j4 + 2] = x2;
+                        v[4 * j4 + 3] = x3;
+                    }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
@@ -407,11 +440,20 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                     }
                 }
                 if (L.out_part) {
-                    if constexpr (NO == 2) {
+                    if constexpr (NO == 2) {   // the two FC2 rows four columns to a load
+                        const float4 *wa = reinterpret_cast<const float4 *>(s_w2 + col0);
+                        const float4 *wb = reinterpret_cast<const float4 *>(s_w2 + N + col0);
 #pragma unroll
-                        for (int j = 0; j < 32; j++) {
-                            pf = fmaf(v[j], s_w2[col0 + j], pf);
-                            pe = fmaf(v[j], s_w2[N + col0 + j], pe);
+                        for (int j4 = 0; j4 < 8; j4++) {
+                            const float4 fa = wa[j4], fb = wb[j4];
+                            pf = fmaf(v[4 * j4], fa.x, pf);
+                            pe = fmaf(v[4 * j4], fb.x, pe);
+                            pf = fmaf(v[4 * j4 + 1], fa.y, pf);
+                            pe = fmaf(v[4 * j4 + 1], fb.y, pe);
+                            pf = fmaf(v[4 * j4 + 2], fa.z, pf);
+                            pe = fmaf(v[4 * j4 + 2], fb.z, pe);
+                            pf = fmaf(v[4 * j4 + 3], fa.w, pf);
+                            pe = fmaf(v[4 * j4 + 3], fb.w, pe);
                         }
                     } else {
                         // this warp's 32 columns of the NH FC2 rows, staged in its own shared
