@@ -192,7 +192,7 @@ __device__ void fill_const(const PArgs &a, const PLayer &L, int lo, int hi, int 
 template <bool FP8, int NO>
 __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, int n_prev, uint8_t *smem,
                                uint64_t *bars, float *prm, uint8_t *staging, uint32_t tmem_base,
-                               volatile int *cta_abort, Pipe &pp) {
+                               volatile int *cta_abort, Pipe &pp, bool rev) {
     const PLayer &L = a.layer[l];
     constexpr int BK = FP8 ? 128 : 64;
     const int S = a.stages, N = L.N;
@@ -216,6 +216,9 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
     const int T0 = n_pos * n_sb * L.n_tiles_n;
     const int n_tiles = T0 + (l2 >= 0 ? n_pos * n_sb * a.layer[l2].n_tiles_n : 0);
     const int KB = L.out_part ? e * L.cin / BK : L.K / BK;   // the paired layer has the same K
+    // Consecutive phases walk their tiles in opposite orders, so a phase starts on the
+    // input the previous one wrote last, which is likeliest still in L2.
+    auto vt = [&](int t) { return rev ? n_tiles - 1 - t : t; };
     if (a.exec && blockIdx.x == 0 && threadIdx.x == 0) {   // the padding extent's saving, counted
         const unsigned long long rows = (unsigned long long)(L.out_part ? e : n_now) * (unsigned long long)M;
         atomicAdd(&a.exec[l], rows);
@@ -254,7 +257,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
             }
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
                 int which, pos, sb, nt;
-                tile_of(t, which, pos, sb, nt);
+                tile_of(vt(t), which, pos, sb, nt);
                 const PLayer &Lt = which ? a.layer[l2] : L;
                 const int n0 = nt * Lt.BN;
                 const uint32_t stage_tx = (uint32_t)(A_BYTES + (resident ? 0 : Lt.BN * ROW_BYTES));
@@ -291,7 +294,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
                 tc_fence_after();
             }
             for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, pp.mma_tc++) {
-                const uint32_t ID = idesc_rt((!FP8 && t >= T0) ? a.layer[l2].BN : L.BN, FP8);
+                const uint32_t ID = idesc_rt((!FP8 && vt(t) >= T0) ? a.layer[l2].BN : L.BN, FP8);
                 const int acc = pp.mma_tc & 1;
                 const uint32_t aph = (uint32_t)(pp.mma_tc >> 1) & 1u;
                 if (!__all_sync(0xffffffffu, mbar_wait(tempty(acc), aph ^ 1u, lim, cta_abort, a.status))) break;
@@ -330,7 +333,7 @@ __device__ uint64_t gemm_phase(const PArgs &a, int l, int l2, int e, int n_now, 
         uint8_t *stg = staging + (warp - 2) * 32 * SROW;
         for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, pp.epi_tc++) {
             int which, pos, sb, nt;
-            tile_of(t, which, pos, sb, nt);
+            tile_of(vt(t), which, pos, sb, nt);
             const PLayer &Lt = which ? a.layer[l2] : L;
             const int BN = Lt.BN, CPW = BN / 64;
             // this tile's layer parameters
@@ -941,7 +944,8 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
         e = (e + a.e_round - 1) / a.e_round * a.e_round;
         e = max(1, min(e, a.rows_n));
         if (blockIdx.x == 0 && threadIdx.x == 0) *ext_next = 0;   // the head phase raises it
-        for (int l = 0; l < a.n_layers && ok; l++) {
+        int ph = 0;   // GEMM phases of this step so far (odd ones walk their tiles backwards)
+        for (int l = 0; l < a.n_layers && ok; l++, ph++) {
             const PLayer &L = a.layer[l];
             if (l == 0 && a.fuse) {   // conv1 and conv2 in one phase
                 const int n2 = layer_pos(a.layer[1], ext), n2_prev = layer_pos(a.layer[1], ext_prev);
@@ -955,7 +959,8 @@ __global__ void __launch_bounds__(kThreads, 1) persist_kernel(const __grid_const
             const int n_now = L.out_part ? 1 : layer_pos(L, ext), n_prev = L.out_part ? 1 : layer_pos(L, ext_prev);
             const int l2 = L.pair_next ? l + 1 : -1;   // a residual block's conv takes its projection along
             const uint64_t tp =
-                gemm_phase<FP8, NO>(a, l, l2, e, n_now, n_prev, smem, bars, prm, staging, tmem_base, cta_abort, pp);
+                gemm_phase<FP8, NO>(a, l, l2, e, n_now, n_prev, smem, bars, prm, staging, tmem_base, cta_abort, pp,
+                                    (ph & 1) != 0);
             if (l2 >= 0) l++;
             ok = grid_sync(a, target, cta_abort);
             if (a.detail && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.detail[4 * l + 3], gtimer() - tp);
