@@ -707,7 +707,7 @@ __device__ __forceinline__ void head_update_state(const StepArgs *__restrict__ A
         A->pos[b] = p;
         A->qstart[b] = qs;
         A->qlen[b] = ql;
-        A->evict[b] += ev;
+        if (ev) A->evict[b] += ev;   // rare: a read-modify-write only when it changes
         if constexpr (SQ) {
             A->mstart[b] = ms;
             A->mlen[b] = ml;
