@@ -40,15 +40,16 @@ TRAFFIC = {
     ("c2", "bf16", "persist_kernel"): 1.526e6 * 1000 / 20,
     # cluster_kernel, c2: one 1,000-step call is two launches (the 128-step probe and the
     # rest), measured on the full workload; nothing is written, the working set stays on
-    # chip and in L2 (profiles/cluster_kernel_c2_bf16_traffic.md, ..._fp8_traffic.md)
-    ("c2", "bf16", "cluster_kernel"): 2.256896e6 + 5.301504e6,
-    ("c2", "fp8", "cluster_kernel"): 1.857792e6 + 5.340160e6,
-    # persist_kernel, c5 (conv1 and conv2 in one phase): 164.76 GB (BF16) and 78.86 GB (FP8)
+    # chip and in L2 (profiles/cluster_kernel_c2_bf16_traffic.md: mean of seven calls;
+    # ..._fp8_traffic.md)
+    ("c2", "bf16", "cluster_kernel"): 2.248411e6 + 5.413998e6,
+    ("c2", "fp8", "cluster_kernel"): 1.872896e6 + 5.331968e6,
+    # persist_kernel, c5 (conv1 and conv2 in one phase): 158.23 GB (BF16) and 74.25 GB (FP8)
     # over one call of 65,536 sub-traces cut to 100 instructions (ncu, one pass;
     # profiles/persist_kernel_c5_fused.md), scaled by instructions to the 100M-instruction
     # launch (the traffic a step follows the active sub-traces: one instruction each)
-    ("c5", "bf16", "persist_kernel"): 164.7619008e9 * 1e8 / 6_553_600,
-    ("c5", "fp8", "persist_kernel"): 78.856364288e9 * 1e8 / 6_553_600,
+    ("c5", "bf16", "persist_kernel"): 158.22559488e9 * 1e8 / 6_553_600,
+    ("c5", "fp8", "persist_kernel"): 74.252812032e9 * 1e8 / 6_553_600,
 }
 
 
@@ -865,8 +866,8 @@ def main():
         run_sweep(args)
         return
     if world > 1:
-        # The simulation runs on one GPU: its default kernel loads weights with
-        # cluster-multicast TMA, which stays in single-GPU processes.  Rank 0
+        # The simulation is built and measured on one GPU (its kernels use
+        # thread-block clusters within one device and no collective).  Rank 0
         # says so; every rank exits without GPU work.
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": world,
