@@ -17,11 +17,12 @@ hundredths of a unit in FC1's output moves those logits by one or more;
 softplus is 1-Lipschitz, so a latency moves by at most as much, which is a
 large relative error where the latency itself is near zero.  The largest
 errors seen over all workloads, heads and kernel paths of the tests are inside
-these rows: BF16 0.094 with a 99th percentile of 0.017 (c4, trained
-predictor), 0.063 (store-queue workload), 0.005 (c2); FP8 2.9-3.4 with a 99th
-percentile of 0.26-0.29 (c4, trained predictor: the training's float atomics
-make its weights, and these figures, differ from run to run), 0.98
-(store-queue workload), 0.09 (c2).  The CPI row holds for all of them.
+these rows: BF16 0.094-0.13 with a 99th percentile of 0.017-0.020 (c4,
+trained predictor), 0.063 (store-queue workload), 0.010 (c5), 0.005 (c2);
+FP8 1.6-3.4 with a 99th percentile of 0.26-0.29 (c4, trained predictor: the
+training's float atomics make its weights, and these figures, differ from
+run to run), 0.98 (store-queue workload), 0.14 (c5), 0.09 (c2).  The CPI row
+holds for all of them (largest seen: BF16 0.007 on c5, FP8 0.017 on c4).
 """
 import numpy as np
 
