@@ -263,6 +263,10 @@ simnet_status simnet_load_weights(simnet_ctx *ctx, const float *blob, int64_t n_
  *               queue use these latencies.
  *   stats       host, or NULL.  When given the call synchronises `stream`.
  * Workspaces are (re)allocated on the first call with a larger batch.
+ * A trace of no sub-traces returns SIMNET_OK at once (cycles_out may then be
+ * NULL); a sub-trace of no instructions finishes with 0 cycles.  A sub-trace
+ * may hold at most 4,194,303 instructions, which keeps its 32-bit clock
+ * (at most 255 cycles an instruction, then the drain) below 2^31.
  * Errors: EINVAL (bad trace, sub-trace longer than the limit), ESTATE (no
  * weights loaded), ENOMEM, ECUDA, ETIMEOUT.
  */

@@ -725,7 +725,7 @@ extern "C" simnet_status simnet_simulate_steps(simnet_ctx *c, const simnet_trace
                                                int64_t max_steps, int32_t resume, simnet_stats *stats,
                                                void *stream) {
     if (!c) return SIMNET_EINVAL;
-    if (!t || !cycles_out || t->n_subtraces < 0 || t->n_instructions < 0)
+    if (!t || t->n_subtraces < 0 || t->n_instructions < 0 || (t->n_subtraces > 0 && !cycles_out))
         return fail(c, SIMNET_EINVAL, "simulate: null trace/cycles_out or negative sizes");
     if (!c->has_weights) return fail(c, SIMNET_ESTATE, "simulate: no weights loaded");
     if (t->n_subtraces > 0 && (!t->offsets || (t->n_instructions > 0 && !t->records)))
